@@ -1,0 +1,358 @@
+"""Benchmark of one AERO-MPPI planning step on GB300 (prints ONE JSON line).
+
+A "step" is one pass of the whole hot path over one synthetic scene: fine
+partition and collision grid, coarse argmax, anchors, quintic guides, the E x K
+x T sampled rollouts with their Stage I costs, the softmax-weighted update, the
+Stage II re-rollout and the selection.  The workload is the anchor-guided
+ensemble (E=8, K=1024, T=40, forest LiDAR sweep).
+
+Metric: rollout-steps per second = (E K T iters + E T) / step time.  Each timed
+step is bracketed by CUDA events on the planner's stream; L2 (129 MB) is
+flushed by writing a 512 MB buffer between timed steps, outside the events.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Under torchrun every rank plans its own scene (seed = rank): weak scaling, no
+data-path collective; the step time is the maximum over ranks.  ``--impl
+reference`` times the CPU oracle on the host cores instead (the reference arm).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2509_17340_gb300 import inputs as I  # noqa: E402
+
+WORKLOAD = "ensemble"
+METRIC = "rollout-steps/s (anchor-guided ensemble plan step)"
+UNIT = "rollout-steps/s"
+CPU_SAMPLE_SECONDS = 15.0
+
+
+def rollout_steps(P: dict) -> int:
+    return P["E"] * P["K"] * P["T"] * P["iters"] + P["E"] * P["T"]
+
+
+def rollout_flops_per_step() -> int:
+    """Algorithmic FP32 flops of one sample-step of the fused rollout kernel
+    (counted from the formulas; FMA = 2, nearest-point distance tests excluded):
+      noise: Box-Muller 2 x (log, sqrt, sincos) + 4 scalings + 4 adds ... 16
+      clamp and perturbation: 8 min/max + 4 add ..................... 12
+      RK4: 4 evaluations of Eq. dynamics (q' 16, v' 13) = 116, three stage
+           states 3 x 20 = 60, combination 10 x 5 = 50 ................ 226
+      renormalisation: 8 + rsqrt + 4 ................................. 13
+      costs: ctrl 16, track 9, vnorm 6, goal 9 + 9 + 16, J_col 4 ...... 69
+      Kahan accumulation ............................................. 4
+      second pass for the update: noise 16 + clamp 12 + 4 products ... 32
+    """
+    return 16 + 12 + 226 + 13 + 69 + 4 + 32
+
+
+def env_int(name, default):
+    v = os.environ.get(name)
+    return int(v) if v is not None else default
+
+
+def host_cores() -> dict:
+    info = {"nproc": os.cpu_count()}
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name"):
+                info["model"] = line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return info
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples during the timed region."""
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self) -> dict:
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks() -> dict:
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        try:
+            return json.load(open(p))
+        except Exception:
+            pass
+    return {}
+
+
+def fp32_peak_tflops(sm_mhz: float) -> float:
+    """152 SMs x 128 FP32 lanes x 2 flops (FMA) x clock."""
+    return 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+
+
+# --------------------------------------------------------------------------- reference arm
+
+def run_reference(args, rank: int, world: int):
+    if rank != 0:
+        return
+    from oracle import oracle as O
+    O.build()
+    w = I.make_workload(WORKLOAD, seed=0)
+    P = w.params
+    u = w.hover_nominal()
+    times = []
+    for s in range(args.warmup + args.steps):
+        P["step_id"] = s
+        t0 = time.perf_counter()
+        out = O.plan_step(w.cloud, w.p0, w.q0, w.v0, w.goal, P, u, debug=False)
+        dt = time.perf_counter() - t0
+        u = out["u_nom"].astype(np.float32)
+        if s >= args.warmup:
+            times.append(dt)
+    tot = sum(times)
+    val = rollout_steps(P) * len(times) / tot
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / len(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": config_of(P, w),
+            "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"{len(times)} full plan steps of the {WORKLOAD} workload, "
+                                       "single-threaded FP64 oracle", "host": host_cores()},
+            "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def config_of(P: dict, w) -> dict:
+    return {"workload": f"{WORKLOAD}: E={P['E']} (M_h x M_v = {P['M_h']}x{P['M_v']}), K={P['K']}, "
+                        f"T={P['T']}, dt={P['dt']}, iters={P['iters']}, fine {P['fine_az']}x{P['fine_el']} "
+                        f"pooled {P['pool_az']}x{P['pool_el']}, forest LiDAR sweep of {len(w.cloud)} points",
+            "E": P["E"], "K": P["K"], "T": P["T"], "n_points": int(len(w.cloud)),
+            "l2": "flushed between timed steps (512 MB write)"}
+
+
+# --------------------------------------------------------------------------- CPU baseline
+
+def cpu_baseline(w, P) -> dict:
+    from oracle import oracle as O
+    O.build()
+    u = w.hover_nominal()
+    times = []
+    t_start = time.perf_counter()
+    s = 0
+    while time.perf_counter() - t_start < CPU_SAMPLE_SECONDS or s < 1:
+        Q = dict(P, step_id=s)
+        t0 = time.perf_counter()
+        out = O.plan_step(w.cloud, w.p0, w.q0, w.v0, w.goal, Q, u, debug=False)
+        times.append(time.perf_counter() - t0)
+        u = out["u_nom"].astype(np.float32)
+        s += 1
+    tot = sum(times)
+    return {"value": rollout_steps(P) * len(times) / tot, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{len(times)} full plan steps of the same workload (FP64 oracle, one thread, "
+                      f"{tot:.1f} s)", "host": host_cores()}
+
+
+# --------------------------------------------------------------------------- GPU arm
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+
+    rank, world = env_int("RANK", 0), env_int("WORLD_SIZE", 1)
+    local = env_int("LOCAL_RANK", 0)
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+
+    import torch
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    from paper_2509_17340_gb300 import build
+    build.build()
+    from paper_2509_17340_gb300 import aero
+
+    w = I.make_workload(WORKLOAD, seed=rank)
+    P = w.params
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.Stream(device=dev)
+    pl = aero.Planner(E_max=P["E"], K_max=P["K"], T_max=P["T"],
+                      fine_cells_max=P["fine_az"] * P["fine_el"], n_points_max=len(w.cloud))
+    cloud = torch.from_numpy(w.cloud).to(dev)
+    u0 = torch.from_numpy(w.hover_nominal()).to(dev)
+    u_nom = u0.clone()
+    u_best = torch.empty((P["T"], 4), device=dev)
+    cand = torch.empty((P["E"],), device=dev)
+    best = torch.empty((1,), dtype=torch.int32, device=dev)
+    state = aero.state_struct(w.p0, w.q0, w.v0)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def step(s):
+        P["step_id"] = s
+        pl.plan_step(state, cloud, w.goal, aero.params_struct(P), u_nom, u_best, cand, best, stream)
+
+    with torch.cuda.stream(stream):
+        for s in range(args.warmup):
+            flush.fill_(float(s))
+            step(s)
+        torch.cuda.synchronize()
+        pl.profile_read()  # discard warm-up stage times
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(args.steps)]
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        pl.profile(True)
+        with ClockSampler(local) as clk:
+            for i in range(args.steps):
+                flush.fill_(float(i))
+                ev[i][0].record(stream)
+                step(args.warmup + i)
+                ev[i][1].record(stream)
+            torch.cuda.synchronize()
+        pl.profile(False)
+        if dist:
+            dist.barrier()
+        st = pl.sync_status(stream)
+        if st != 0:
+            raise RuntimeError(f"planner status {st}")
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    stages = pl.profile_read()
+    total_ms = sum(step_ms)
+    if dist:
+        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+
+    # end-to-end through the host-memory entry point (pinned buffers)
+    e2e = None
+    if True:
+        hc = torch.from_numpy(w.cloud.copy()).pin_memory()
+        hu = torch.from_numpy(w.hover_nominal()).pin_memory()
+        hb = torch.empty((P["T"], 4)).pin_memory()
+        hcand = torch.empty((P["E"],)).pin_memory()
+        hbest = torch.empty((1,), dtype=torch.int32).pin_memory()
+        e2e_steps = max(20, args.steps // 2)
+        times = []
+        for i in range(args.warmup + e2e_steps):
+            with torch.cuda.stream(stream):
+                flush.fill_(float(i))
+            stream.synchronize()
+            P["step_id"] = 10_000 + i
+            t0 = time.perf_counter()
+            pl.plan_step_host(state, hc, w.goal, aero.params_struct(P), hu, hb, hcand, hbest, stream)
+            dt = time.perf_counter() - t0
+            if i >= args.warmup:
+                times.append(dt)
+        e_tot = sum(times)
+        if dist:
+            t = torch.tensor([e_tot], dtype=torch.float64, device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e_tot = float(t.item())
+        e2e = {"value": world * rollout_steps(P) * len(times) / e_tot, "unit": UNIT,
+               "h2d_bytes_per_step": hc.numel() * 4 + hu.numel() * 4,
+               "d2h_bytes_per_step": hu.numel() * 4 + hb.numel() * 4 + hcand.numel() * 4 + 4,
+               "ms_per_step": 1e3 * e_tot / len(times)}
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+
+    value = world * rollout_steps(P) * args.steps / (total_ms / 1e3)
+    clocks = clk.summary()
+    peaks = measured_peaks()
+    r_ms, r_n = stages["rollout"]
+    r_avg_ms = r_ms / max(r_n, 1)
+    flops = P["E"] * P["K"] * P["T"] * rollout_flops_per_step()
+    achieved = flops / (r_avg_ms / 1e3) / 1e12
+    peak = fp32_peak_tflops(peaks.get("sm_max_mhz", 2070.0))
+    launches = sum(n for _, n in stages.values())
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+        "ms_per_step_median": statistics.median(step_ms), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": config_of(P, w),
+        "stage_ms_per_step": {k: v[0] / args.steps for k, v in stages.items()},
+        "roofline": {"kernel": "k_rollout (fused noise + RK4 + S(1) + update partials)",
+                     "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak, "traffic": None,
+                     "flops_per_launch": flops, "avg_launch_ms": r_avg_ms,
+                     "peak_note": "FP32 FMA pipes: 152 SMs x 128 lanes x 2 x 2070 MHz (max SM clock)"},
+        "clocks": clocks,
+        "e2e": e2e,
+        "gpu_launches": launches,
+    }
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(w, P)
+    print(json.dumps(line), flush=True)
+    pl.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

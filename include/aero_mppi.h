@@ -1,0 +1,220 @@
+/*
+ * aero_mppi.h -- C ABI of the GB300 (sm_103a) AERO-MPPI planning step.
+ *
+ * One call of aero_plan_step() runs one planning step of AERO-MPPI
+ * (arXiv 2509.17340) on the GPU, entirely in this library's CUDA kernels:
+ *
+ *   1. fine spherical partition of the cloud around the drone
+ *      (Sec. IV-A.1: r_ij = min |p_c| over the points in cone C_ij);
+ *   2. coarse pooling argmax (Sec. IV-A.2, Eq. safe-vector), the M_h x M_v
+ *      coarse cells around the goal direction (Sec. IV-B.1) and the anchors
+ *      p_ref = p0 + ell d_IJ (Eq. anchor-point);
+ *   3. quintic guides from the current state to each anchor (Eq. polynomial);
+ *   4. for each of the E = M_h M_v MPPI instances: K Gaussian perturbations of
+ *      the nominal controls (Sec. III-B), RK4 rollouts of the quadrotor model
+ *      (Eq. dynamics, Eq. mppi_rollout_simplified), the Stage I cost S(1)
+ *      (Eq. total cost and the cost terms of Sec. IV-C, collision distances
+ *      against the filtered cloud P_f), softmax weights (Eq. mppi_weights) and
+ *      the update of the nominal (Eq. mppi_update_simplified);
+ *   5. Stage II: noise-free rollout of the E updated nominals, S(2) = J_goal +
+ *      J_col, and the argmin (Sec. IV-C).
+ *
+ * Conventions
+ *   - Every function returns an aero status code (AERO_OK = 0, negative on
+ *     error) except aero_params_default and aero_status_str.  No exception,
+ *     exit, abort or device trap crosses this boundary.
+ *   - "device" pointers are CUDA global-memory pointers on the planner's device
+ *     (cudaMalloc, torch CUDA tensors); "host" pointers are CPU memory.
+ *   - stream is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *     aero_plan_step only enqueues work and returns; its outputs are valid once
+ *     the stream has reached that point.  It allocates nothing, so a sequence of
+ *     calls with fixed pointers can be captured into a CUDA graph.
+ *   - The caller owns every input and output buffer; the planner owns its
+ *     workspace, allocated once by aero_create and freed by aero_destroy.
+ *   - One planner must not be used by two streams at the same time: calls share
+ *     its workspace.
+ *   - Angles are radians, lengths metres, times seconds; quaternions are
+ *     (w, x, y, z), unit length, body to world (Hamilton product).
+ */
+#ifndef AERO_MPPI_H
+#define AERO_MPPI_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---------------------------------------------------- */
+#define AERO_OK 0
+#define AERO_ERR_INVALID_ARG (-1)    /* null pointer, bad size, inconsistent params */
+#define AERO_ERR_EXCEEDS_LIMITS (-2) /* a size above the planner's aero_limits_t */
+#define AERO_ERR_CUDA (-3)           /* a CUDA runtime call failed */
+#define AERO_ERR_ALLOC (-4)          /* workspace allocation failed */
+#define AERO_ERR_DEVICE_CHECK (-5)   /* a kernel reported an internal inconsistency */
+#define AERO_ERR_NOT_DEVICE_PTR (-6) /* a pointer that must be device memory is not */
+
+/* ---- debug buffers (aero_get_debug) ------------------------------------
+ * Positions in debug buffers are relative to the start position p0 of the
+ * last step (world axes), as the kernels keep them. */
+#define AERO_DBG_FINE_KEYS 0     /* uint64 [fine_el][fine_az]: (bits(r^2 f32) << 32) | point index;
+                                    0xFFFFFFFFFFFFFFFF = empty cone */
+#define AERO_DBG_COARSE_WIN 1    /* int32 [E_c][A_c]: winning fine cell j*fine_az+i of each coarse cell */
+#define AERO_DBG_GOAL_CELL 2     /* int32 [1]: fine cell of the goal direction */
+#define AERO_DBG_ANCHOR_CELLS 3  /* int32 [E]: coarse cell J*A_c+I of instance e = n*M_h+m */
+#define AERO_DBG_ANCHORS 4       /* float [E][3]: anchor - p0 */
+#define AERO_DBG_GUIDES 5        /* float [E][T][3]: guide at t=(j+1)dt, minus p0 */
+#define AERO_DBG_GRID_META 6     /* int32 [4] = {G, n_items, 0, 0} then float [4] = {origin, h, 0, 0} */
+#define AERO_DBG_GRID_START 7    /* int32 [G*G*G + 1]: first point of cell (z*G+y)*G+x */
+#define AERO_DBG_GRID_POINTS 8   /* float4 [n_items]: collision points - p0, sorted by cell */
+#define AERO_DBG_SAMPLE_COSTS 9  /* float [E][K]: S(1) of every sample, last iteration */
+#define AERO_DBG_STAGE2_STATES 10 /* float [E][T+1][10]: Stage II states (p - p0, q, v) */
+#define AERO_DBG_SAMPLE_U 11     /* float [E][D][T][4]: clamped controls of samples k < D */
+#define AERO_DBG_SAMPLE_X 12     /* float [E][D][T+1][10]: their states (p - p0, q, v) */
+#define AERO_DBG_SAMPLE_DIST 13  /* float [E][D][T]: their nearest-point distances, or
+                                    +inf where none is closer than d_max */
+#define AERO_DBG_COUNT 14
+
+/* ---- inputs ----------------------------------------------------------- */
+
+/* Drone state x = [p, q, v] of Eq. dynamics (world frame). */
+typedef struct {
+  float p[3];
+  float q[4]; /* w, x, y, z */
+  float v[3];
+} aero_state_t;
+
+/* Maxima fixed when the planner is created; they size its workspace. */
+typedef struct {
+  int32_t E_max;            /* ensemble size, <= 64 */
+  int32_t K_max;            /* samples per instance, <= 1<<20 */
+  int32_t T_max;            /* horizon steps, <= 128 */
+  int32_t fine_cells_max;   /* fine_az * fine_el, <= 512 * 256 */
+  int64_t n_points_max;     /* cloud size, <= 2^31 - 1 */
+  int32_t debug_samples_max; /* D: samples per instance whose rollouts can be recorded */
+  int32_t reserved_;
+} aero_limits_t;
+
+/* Parameters of one planning step; aero_params_default() fills Table I. */
+typedef struct {
+  int32_t E, K, T;        /* ensemble size (= M_h*M_v), samples, horizon N */
+  int32_t iters;          /* MPPI iterations (Stage I) per step, 1..255 */
+  float dt;               /* RK4 step (s) */
+  float lambda;           /* temperature of Eq. mppi_weights, > 0 */
+  float mass, g;          /* m (kg); gravity magnitude, acting along -z */
+  float sigma[4];         /* standard deviations of (F, wx, wy, wz) perturbations */
+  float u_min[4], u_max[4]; /* control bounds; sampled controls are clamped */
+  float Q_track, Q_vnorm, Q_c, Q_cd, Q_p, Q_v, Q_q; /* cost weights (Sec. IV-C) */
+  float C_col, a_col, d_min, d_max;  /* collision penalty C, a, d_obs_min < d_obs_max */
+  float r_max;            /* perception range of the partition (m) */
+  float ell;              /* look-ahead distance of the anchors (m) */
+  float v_end;            /* guide speed at the anchor; <= 0 means ell / (T dt) */
+  int32_t fine_az, fine_el;  /* fine grid (even fine_az <= 512, fine_el <= 256) */
+  int32_t pool_az, pool_el;  /* pooling; must divide the fine grid */
+  int32_t M_h, M_v;          /* anchor grid; M_h*M_v == E */
+  float el_lo, el_hi;     /* elevation span of the partition */
+  int32_t collision_set;  /* 0: P_f (nearest point of every cone, Sec. IV-C);
+                             1: every point kept by the partition */
+  float v_goal[3];        /* goal velocity */
+  float q_goal[4];        /* goal attitude (w, x, y, z) */
+  int32_t debug_samples;  /* D: record rollouts of samples k < D (0 = off) */
+  uint64_t seed;          /* Philox key */
+  uint64_t step_id;       /* enters the Philox counter: (k, j, e, (step_id << 8) | iter) */
+} aero_params_t;
+
+typedef struct aero_planner aero_planner_t;
+
+/* Fill p with the paper's defaults: Table I (m = 1 kg, F in [0.3, 16.35] N,
+ * |w_xy| <= 3, |w_z| <= 2 rad/s, Sigma = (1, 1, 1, 0.5) as std sqrt(Sigma),
+ * dt = 50 ms, K = 128, N = 25, lambda = 0.1, Q_p = 3, Q_v = 0.25, Q_q = 1,
+ * Q_vnorm = 0.15, Q_track = 15, Q_c = Q_cd = 0.5, ell = 5 m, C = 1e6, a = 5,
+ * d_min = 0.4 m, d_max = 1 m), r_max = 10 m and the 120 x 60 fine grid pooled
+ * 6 x 6 (Sec. IV-A), M_h x M_v = 5 x 3 (Sec. V-A), g = 9.81, seed 0. */
+void aero_params_default(aero_params_t* p);
+
+/* Create a planner on the current CUDA device and allocate its workspace for
+ * the given maxima.  *out receives the handle.  Errors: INVALID_ARG (null or
+ * out-of-range limit), ALLOC, CUDA. */
+int aero_create(const aero_limits_t* limits, aero_planner_t** out);
+
+/* Free the planner and its workspace (synchronises the device first).
+ * A NULL planner is accepted. */
+int aero_destroy(aero_planner_t* planner);
+
+/* One planning step (see the top of this file).
+ *   x0          host, the current state.
+ *   cloud_xyz   device, n_points x 3 float, row-major (x, y, z), world frame;
+ *               may be NULL when n_points == 0.  Non-finite points, points at
+ *               p0 and points beyond r_max are ignored.
+ *   goal        host, 3 floats, goal position (world).
+ *   params      host.
+ *   u_nom_inout device, E x T x 4 float (F, wx, wy, wz) per instance and step,
+ *               16-byte aligned: the warm start on entry, the updated nominals
+ *               on return.
+ *   u_best_out  device, T x 4 float: the nominal of the selected instance.
+ *   cand_costs_out device, E float: Stage II cost S(2) of each instance.
+ *   best_idx_out device, 1 int32: index of the selected instance (lowest
+ *               S(2), ties to the lower index).
+ * Errors (nothing is enqueued): INVALID_ARG, EXCEEDS_LIMITS, NOT_DEVICE_PTR;
+ * CUDA if a launch fails. */
+int aero_plan_step(aero_planner_t* planner, const aero_state_t* x0, const float* cloud_xyz,
+                   int64_t n_points, const float goal[3], const aero_params_t* params,
+                   float* u_nom_inout, float* u_best_out, float* cand_costs_out,
+                   int32_t* best_idx_out, void* stream);
+
+/* The same step for callers whose data lives in host memory: every array
+ * argument is a host pointer (pinned memory gives the fastest copies).  The
+ * cloud and the warm start are copied into the planner's device buffers on
+ * `stream`, the step runs, the outputs are copied back, and the call returns
+ * after synchronising the stream. */
+int aero_plan_step_host(aero_planner_t* planner, const aero_state_t* x0, const float* cloud_xyz,
+                        int64_t n_points, const float goal[3], const aero_params_t* params,
+                        float* u_nom_inout, float* u_best_out, float* cand_costs_out,
+                        int32_t* best_idx_out, void* stream);
+
+/* Bytes of debug buffer `what` (AERO_DBG_*) for the last step; 0 if unknown. */
+size_t aero_debug_size(aero_planner_t* planner, int32_t what);
+
+/* Copy debug buffer `what` of the last step into dst (host or device), at most
+ * `bytes` bytes, ordered on `stream` (asynchronous for device dst and pinned
+ * host dst).  Errors: INVALID_ARG (unknown id, no step yet, bytes too small). */
+int aero_get_debug(aero_planner_t* planner, int32_t what, void* dst, size_t bytes, void* stream);
+
+/* Synchronise `stream`, then report the kernels' status word: AERO_OK, or
+ * DEVICE_CHECK when a kernel recorded an internal inconsistency, or CUDA when
+ * the stream holds an error.  Clears the status word. */
+int aero_sync_status(aero_planner_t* planner, void* stream);
+
+/* ---- stage timing --------------------------------------------------------
+ * When enabled, aero_plan_step records CUDA events on its stream around its
+ * stages; aero_profile_read synchronises them, adds the elapsed device times
+ * since the last read into ms[AERO_STAGE_COUNT] and the number of kernel
+ * launches per stage into launches[AERO_STAGE_COUNT], and starts over.
+ *   AERO_STAGE_PARTITION: workspace clears + fine partition (Sec. IV-A.1)
+ *   AERO_STAGE_GRID: P_f / grid counts, coarse argmax + anchors + guides with the
+ *                    grid scan, grid scatter (Sec. IV-A.2, IV-B)
+ *   AERO_STAGE_ROLLOUT: sampling, rollouts and S(1) (Sec. III-B, IV-C)
+ *   AERO_STAGE_UPDATE: weights, update, Stage II and selection */
+#define AERO_STAGE_PARTITION 0
+#define AERO_STAGE_GRID 1
+#define AERO_STAGE_ROLLOUT 2
+#define AERO_STAGE_UPDATE 3
+#define AERO_STAGE_COUNT 4
+int aero_profile_enable(aero_planner_t* planner, int on);
+int aero_profile_read(aero_planner_t* planner, double* ms, int64_t* launches);
+
+/* Test hook for the noise generator (Sec. III-B): out[4i .. 4i+3] =
+ * Philox4x32-10(counter = (i, c1, c2, c3), key = (lo32(seed), hi32(seed))) for
+ * i < n.  out is device memory of 4n uint32. */
+int aero_philox(uint64_t seed, uint32_t c1, uint32_t c2, uint32_t c3, int64_t n, uint32_t* out,
+                void* stream);
+
+/* Static description of a status code. */
+const char* aero_status_str(int status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* AERO_MPPI_H */

@@ -97,6 +97,12 @@ void orc_noise(const orc_params* P, int e, int k, int j, int iter, double delta[
   for (int c = 0; c < 4; ++c) delta[c] = P->sigma[c] * n[c];
 }
 
+/* delta for samples k0 .. k0+nk-1 of instance e, all T steps: nk x T x 4. */
+void orc_noise_fill(const orc_params* P, int e, int k0, int nk, int iter, double* out) {
+  for (int a = 0; a < nk; ++a)
+    for (int j = 0; j < P->T; ++j) orc_noise(P, e, k0 + a, j, iter, out + ((int64_t)a * P->T + j) * 4);
+}
+
 /* ======================================================================
  * Quadrotor model (Eq. dynamics): p' = v, q' = 1/2 q (x) [0, w],
  * v' = (1/m) R(q) [0,0,F]^T + g, with g = (0,0,-g) and u = (F, w).

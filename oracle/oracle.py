@@ -139,6 +139,14 @@ def noise_block(P: dict, e: int, ks, it: int = 0) -> np.ndarray:
     return out
 
 
+def noise_range(P: dict, e: int, k0: int, nk: int, it: int = 0) -> np.ndarray:
+    """delta for samples k0 .. k0+nk-1 of instance e: nk x T x 4."""
+    out = np.zeros((nk, P["T"], 4))
+    pp = params(P)
+    lib().orc_noise_fill(C.byref(pp), C.c_int(e), C.c_int(k0), C.c_int(nk), C.c_int(it), _p(out))
+    return out
+
+
 def quat_mul(a, b) -> np.ndarray:
     r = np.zeros(4)
     lib().orc_quat_mul(_p(_f64(a)), _p(_f64(b)), _p(r))

@@ -1,0 +1,266 @@
+"""Python binding of ``libaero_mppi.so`` (ctypes; argument marshalling only).
+
+Every step of the planning path runs in the library's CUDA kernels; this module
+only converts torch CUDA tensors and parameter dictionaries into the C ABI of
+``include/aero_mppi.h``.  It raises ImportError when the library has not been
+built: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libaero_mppi.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"{LIB_PATH} is missing: build it with "
+                      "`python -m paper_2509_17340_gb300.build` (needs nvcc); there is no CPU fallback")
+
+_lib = C.CDLL(LIB_PATH)
+
+OK = 0
+ERR_INVALID_ARG, ERR_EXCEEDS_LIMITS, ERR_CUDA, ERR_ALLOC, ERR_DEVICE_CHECK, ERR_NOT_DEVICE_PTR = (
+    -1, -2, -3, -4, -5, -6)
+
+DBG = dict(FINE_KEYS=0, COARSE_WIN=1, GOAL_CELL=2, ANCHOR_CELLS=3, ANCHORS=4, GUIDES=5,
+           GRID_META=6, GRID_START=7, GRID_POINTS=8, SAMPLE_COSTS=9, STAGE2_STATES=10,
+           SAMPLE_U=11, SAMPLE_X=12, SAMPLE_DIST=13)
+
+STAGES = ["partition", "grid", "rollout", "update"]
+
+
+class State(C.Structure):
+    _fields_ = [("p", C.c_float * 3), ("q", C.c_float * 4), ("v", C.c_float * 3)]
+
+
+class Limits(C.Structure):
+    _fields_ = [("E_max", C.c_int32), ("K_max", C.c_int32), ("T_max", C.c_int32),
+                ("fine_cells_max", C.c_int32), ("n_points_max", C.c_int64),
+                ("debug_samples_max", C.c_int32), ("reserved_", C.c_int32)]
+
+
+class Params(C.Structure):
+    _fields_ = [
+        ("E", C.c_int32), ("K", C.c_int32), ("T", C.c_int32), ("iters", C.c_int32),
+        ("dt", C.c_float), ("lam", C.c_float), ("mass", C.c_float), ("g", C.c_float),
+        ("sigma", C.c_float * 4), ("u_min", C.c_float * 4), ("u_max", C.c_float * 4),
+        ("Q_track", C.c_float), ("Q_vnorm", C.c_float), ("Q_c", C.c_float), ("Q_cd", C.c_float),
+        ("Q_p", C.c_float), ("Q_v", C.c_float), ("Q_q", C.c_float),
+        ("C_col", C.c_float), ("a_col", C.c_float), ("d_min", C.c_float), ("d_max", C.c_float),
+        ("r_max", C.c_float), ("ell", C.c_float), ("v_end", C.c_float),
+        ("fine_az", C.c_int32), ("fine_el", C.c_int32), ("pool_az", C.c_int32), ("pool_el", C.c_int32),
+        ("M_h", C.c_int32), ("M_v", C.c_int32),
+        ("el_lo", C.c_float), ("el_hi", C.c_float),
+        ("collision_set", C.c_int32),
+        ("v_goal", C.c_float * 3), ("q_goal", C.c_float * 4),
+        ("debug_samples", C.c_int32),
+        ("seed", C.c_uint64), ("step_id", C.c_uint64),
+    ]
+
+
+_vp = C.c_void_p
+_lib.aero_params_default.argtypes = [C.POINTER(Params)]
+_lib.aero_params_default.restype = None
+_lib.aero_create.argtypes = [C.POINTER(Limits), C.POINTER(_vp)]
+_lib.aero_destroy.argtypes = [_vp]
+_lib.aero_plan_step.argtypes = [_vp, C.POINTER(State), _vp, C.c_int64, C.POINTER(C.c_float),
+                                C.POINTER(Params), _vp, _vp, _vp, _vp, _vp]
+_lib.aero_plan_step_host.argtypes = _lib.aero_plan_step.argtypes
+_lib.aero_debug_size.argtypes = [_vp, C.c_int32]
+_lib.aero_debug_size.restype = C.c_size_t
+_lib.aero_get_debug.argtypes = [_vp, C.c_int32, _vp, C.c_size_t, _vp]
+_lib.aero_sync_status.argtypes = [_vp, _vp]
+_lib.aero_philox.argtypes = [C.c_uint64, C.c_uint32, C.c_uint32, C.c_uint32, C.c_int64, _vp, _vp]
+_lib.aero_profile_enable.argtypes = [_vp, C.c_int]
+_lib.aero_profile_read.argtypes = [_vp, C.POINTER(C.c_double), C.POINTER(C.c_int64)]
+_lib.aero_status_str.argtypes = [C.c_int]
+_lib.aero_status_str.restype = C.c_char_p
+
+
+class AeroError(RuntimeError):
+    def __init__(self, code: int, what: str = ""):
+        self.code = code
+        super().__init__(f"{what}: {status_str(code)} ({code})")
+
+
+def status_str(code: int) -> str:
+    return _lib.aero_status_str(code).decode()
+
+
+def _check(code: int, what: str):
+    if code != OK:
+        raise AeroError(code, what)
+
+
+def lib() -> C.CDLL:
+    return _lib
+
+
+def default_params_struct() -> Params:
+    p = Params()
+    _lib.aero_params_default(C.byref(p))
+    return p
+
+
+def params_struct(d: dict) -> Params:
+    """Marshal a parameter dictionary (``inputs.default_params`` keys)."""
+    p = Params()
+    for k in ("E", "K", "T", "iters", "collision_set", "debug_samples"):
+        setattr(p, k, int(d.get(k, 0)))
+    for k in ("dt", "mass", "g", "Q_track", "Q_vnorm", "Q_c", "Q_cd", "Q_p", "Q_v", "Q_q",
+              "C_col", "a_col", "d_min", "d_max", "r_max", "ell", "v_end", "el_lo", "el_hi"):
+        setattr(p, k, float(d[k]))
+    p.lam = float(d["lam"])
+    for k in ("fine_az", "fine_el", "pool_az", "pool_el", "M_h", "M_v"):
+        setattr(p, k, int(d[k]))
+    for k in ("sigma", "u_min", "u_max", "v_goal", "q_goal"):
+        arr = getattr(p, k)
+        for i, v in enumerate(d[k]):
+            arr[i] = float(v)
+    p.seed, p.step_id = int(d["seed"]), int(d["step_id"])
+    return p
+
+
+def state_struct(p0, q0, v0) -> State:
+    s = State()
+    for i in range(3):
+        s.p[i] = float(p0[i])
+        s.v[i] = float(v0[i])
+    for i in range(4):
+        s.q[i] = float(q0[i])
+    return s
+
+
+def _stream_ptr(stream) -> int:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return stream.cuda_stream
+
+
+def _dev(t: torch.Tensor, dtype, name: str) -> int:
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == dtype and t.is_contiguous()):
+        raise TypeError(f"{name} must be a contiguous CUDA {dtype} tensor")
+    return t.data_ptr()
+
+
+class Planner:
+    """Owns an ``aero_planner_t`` (device workspace sized by the limits)."""
+
+    def __init__(self, E_max=64, K_max=8192, T_max=64, fine_cells_max=512 * 64,
+                 n_points_max=1 << 18, debug_samples_max=0, device=None):
+        if device is not None:
+            torch.cuda.set_device(device)
+        torch.cuda.init()
+        lim = Limits(E_max, K_max, T_max, fine_cells_max, n_points_max, debug_samples_max, 0)
+        h = _vp()
+        _check(_lib.aero_create(C.byref(lim), C.byref(h)), "aero_create")
+        self._h = h
+        self.limits = lim
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.aero_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def handle(self):
+        return self._h
+
+    def plan_step(self, state: State, cloud: torch.Tensor, goal, params: Params,
+                  u_nom: torch.Tensor, u_best: torch.Tensor, cand: torch.Tensor,
+                  best_idx: torch.Tensor, stream=None) -> None:
+        """Enqueue one planning step on device tensors (u_nom updated in place)."""
+        n = cloud.shape[0] if cloud is not None else 0
+        cptr = _dev(cloud, torch.float32, "cloud") if n > 0 else None
+        g = (C.c_float * 3)(*[float(x) for x in goal])
+        rc = _lib.aero_plan_step(self._h, C.byref(state), cptr, n, g, C.byref(params),
+                                 _dev(u_nom, torch.float32, "u_nom"),
+                                 _dev(u_best, torch.float32, "u_best"),
+                                 _dev(cand, torch.float32, "cand"),
+                                 _dev(best_idx, torch.int32, "best_idx"), _stream_ptr(stream))
+        _check(rc, "aero_plan_step")
+
+    def plan_step_host(self, state: State, cloud: torch.Tensor, goal, params: Params,
+                       u_nom: torch.Tensor, u_best: torch.Tensor, cand: torch.Tensor,
+                       best_idx: torch.Tensor, stream=None) -> None:
+        """One planning step on CPU tensors (pinned for speed); blocks until done."""
+        for name, t, dt in (("cloud", cloud, torch.float32), ("u_nom", u_nom, torch.float32),
+                            ("u_best", u_best, torch.float32), ("cand", cand, torch.float32),
+                            ("best_idx", best_idx, torch.int32)):
+            if t.is_cuda or t.dtype != dt or not t.is_contiguous():
+                raise TypeError(f"{name} must be a contiguous CPU {dt} tensor")
+        n = cloud.shape[0]
+        g = (C.c_float * 3)(*[float(x) for x in goal])
+        rc = _lib.aero_plan_step_host(self._h, C.byref(state), cloud.data_ptr() if n else None, n, g,
+                                      C.byref(params), u_nom.data_ptr(), u_best.data_ptr(),
+                                      cand.data_ptr(), best_idx.data_ptr(), _stream_ptr(stream))
+        _check(rc, "aero_plan_step_host")
+
+    def debug(self, what: str, stream=None) -> np.ndarray:
+        """Copy a debug buffer of the last step to the host (synchronous)."""
+        wid = DBG[what]
+        stream_p = _stream_ptr(stream)
+        if what == "GRID_META":
+            buf = np.zeros(8, np.int32)
+            _check(_lib.aero_get_debug(self._h, wid, buf.ctypes.data, 32, stream_p), "aero_get_debug")
+            return buf
+        if what == "GRID_POINTS":
+            meta = self.debug("GRID_META", stream)
+            buf = np.zeros((int(meta[1]), 4), np.float32)
+            _check(_lib.aero_get_debug(self._h, wid, buf.ctypes.data, buf.nbytes, stream_p),
+                   "aero_get_debug")
+            torch.cuda.synchronize()
+            return buf
+        nbytes = _lib.aero_debug_size(self._h, wid)
+        dtype = {"FINE_KEYS": np.uint64, "COARSE_WIN": np.int32, "GOAL_CELL": np.int32,
+                 "ANCHOR_CELLS": np.int32, "GRID_START": np.int32}.get(what, np.float32)
+        buf = np.zeros(nbytes // np.dtype(dtype).itemsize, dtype)
+        _check(_lib.aero_get_debug(self._h, wid, buf.ctypes.data, nbytes, stream_p), "aero_get_debug")
+        torch.cuda.synchronize()
+        return buf
+
+    def profile(self, on: bool) -> None:
+        """Record per-stage CUDA events inside every following step."""
+        _check(_lib.aero_profile_enable(self._h, int(on)), "aero_profile_enable")
+
+    def profile_read(self) -> dict:
+        """{stage: (device ms summed since the last read, kernel launches)}."""
+        ms = (C.c_double * 4)()
+        n = (C.c_int64 * 4)()
+        _check(_lib.aero_profile_read(self._h, ms, n), "aero_profile_read")
+        return {k: (ms[i], n[i]) for i, k in enumerate(STAGES)}
+
+    def sync_status(self, stream=None) -> int:
+        return _lib.aero_sync_status(self._h, _stream_ptr(stream))
+
+
+def philox(seed: int, c1: int, c2: int, c3: int, n: int) -> np.ndarray:
+    """out[i] = Philox4x32-10((i, c1, c2, c3), seed) computed on the GPU."""
+    out = torch.empty((n, 4), dtype=torch.int32, device="cuda")
+    _check(_lib.aero_philox(seed, c1, c2, c3, n, out.data_ptr(), _stream_ptr(None)), "aero_philox")
+    torch.cuda.synchronize()
+    return out.cpu().numpy().view(np.uint32)
+
+
+def plan_step(planner: Planner, p0, q0, v0, cloud: torch.Tensor, goal, params: dict,
+              u_nom: torch.Tensor, stream=None):
+    """Convenience wrapper: allocate the outputs, run one step, return
+    (u_best[T,4], cand[E], best_idx[1]) as CUDA tensors; u_nom is updated in place."""
+    T, E = params["T"], params["E"]
+    dev = u_nom.device
+    u_best = torch.empty((T, 4), dtype=torch.float32, device=dev)
+    cand = torch.empty((E,), dtype=torch.float32, device=dev)
+    best = torch.empty((1,), dtype=torch.int32, device=dev)
+    planner.plan_step(state_struct(p0, q0, v0), cloud, goal, params_struct(params), u_nom, u_best,
+                      cand, best, stream)
+    return u_best, cand, best

@@ -1,0 +1,700 @@
+// C-ABI host runtime of the AERO-MPPI planning step: planner workspace,
+// argument validation, binary32 partition tables, collision-grid geometry and
+// the launch sequence of one step.  Host code is compiled with
+// -ffp-contract=off so that R(q0), the goal offset and the edge tables follow
+// the stated binary32/binary64 operation order exactly.
+#include <cmath>
+#include <cstdint>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "../../include/aero_mppi.h"
+#include "internal.h"
+
+using namespace aero;
+
+struct aero_planner {
+  aero_limits_t lim{};
+  int device = 0;
+  // workspace
+  unsigned long long* keys = nullptr;
+  int* coarse_win = nullptr;
+  int* cells = nullptr;       // [0] goal fine cell, [1 + e] anchor coarse cell
+  float* anchors = nullptr;
+  float* guides = nullptr;
+  int* item_cell = nullptr;
+  int* item_slot = nullptr;
+  int* grid_start = nullptr;
+  float4* grid_pts = nullptr;
+  float* partials = nullptr;
+  float* sample_costs = nullptr;
+  float* stage2_x = nullptr;
+  unsigned int* counter = nullptr;
+  int* status = nullptr;
+  float* dbg_u = nullptr;
+  float* dbg_x = nullptr;
+  float* dbg_d = nullptr;
+  // staging for aero_plan_step_host
+  float* stage_cloud = nullptr;
+  float* stage_unom = nullptr;
+  float* stage_ubest = nullptr;
+  float* stage_cand = nullptr;
+  int* stage_best = nullptr;
+  // metadata of the last step (debug copies)
+  bool have_step = false;
+  aero_params_t last{};
+  GridGeom last_grid{};
+  int64_t last_items = 0;
+  int last_nb = 0;
+  int64_t item_cap = 0;
+  // stage timing (aero_profile_enable / aero_profile_read)
+  struct ProfSlot {
+    std::vector<cudaEvent_t> ev;  // start, after partition, after grid, then 4 per iteration
+    int iters = 0;
+    int64_t launches[AERO_STAGE_COUNT] = {0, 0, 0, 0};
+  };
+  bool prof = false;
+  std::vector<ProfSlot> slots;
+  size_t slots_used = 0;
+  double prof_ms[AERO_STAGE_COUNT] = {0, 0, 0, 0};
+  int64_t prof_launches[AERO_STAGE_COUNT] = {0, 0, 0, 0};
+};
+
+namespace {
+
+constexpr int kGridCellsMax = kGridMax * kGridMax * kGridMax;
+
+int cuda_fail(cudaError_t e) {
+  if (e == cudaSuccess) return AERO_OK;
+  return AERO_ERR_CUDA;
+}
+
+bool is_device_ptr(const void* p) {
+  if (!p) return false;
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+// R(q) of a unit quaternion in binary32: nine products, then the sums.
+void rot_f32(const float* q, float* R) {
+  const float w = q[0], x = q[1], y = q[2], z = q[3];
+  const float xx = x * x, yy = y * y, zz = z * z, xy = x * y, xz = x * z, yz = y * z;
+  const float wx = w * x, wy = w * y, wz = w * z;
+  R[0] = 1.0f - 2.0f * (yy + zz);
+  R[1] = 2.0f * (xy - wz);
+  R[2] = 2.0f * (xz + wy);
+  R[3] = 2.0f * (xy + wz);
+  R[4] = 1.0f - 2.0f * (xx + zz);
+  R[5] = 2.0f * (yz - wx);
+  R[6] = 2.0f * (xz - wy);
+  R[7] = 2.0f * (yz + wx);
+  R[8] = 1.0f - 2.0f * (xx + yy);
+}
+
+void make_tables(const aero_params_t& p, PartTables& t, int& check_lo, int& check_hi) {
+  const int A = p.fine_az, El = p.fine_el;
+  for (int k = 0; k < A; ++k) {
+    const double th = (M_PI * (double)(2 * k - A)) / (double)A;
+    t.ca[k] = (float)std::cos(th);
+    t.sa[k] = (float)std::sin(th);
+  }
+  const double lo = (double)p.el_lo, hi = (double)p.el_hi;
+  for (int k = 0; k <= El; ++k) {
+    const double ph = lo + ((hi - lo) * (double)k) / (double)El;
+    t.ce[k] = (float)std::cos(ph);
+    t.se[k] = (float)std::sin(ph);
+  }
+  check_lo = lo > -M_PI / 2;
+  check_hi = hi < M_PI / 2;
+}
+
+// Grid over [-r_max, r_max]^3 around p0 with one spare cell on every side.
+GridGeom make_grid(const aero_params_t& p) {
+  GridGeom g;
+  float h = p.d_max * kCellMargin;
+  const float hmin = 2.0f * p.r_max / (float)(kGridMax - 3);
+  if (h < hmin) h = hmin;
+  int G = (int)std::floor(2.0f * p.r_max / h) + 3;
+  if (G > kGridMax) G = kGridMax;
+  g.G = G;
+  g.h = h;
+  g.inv_h = 1.0f / h;
+  g.origin = -(p.r_max + h);
+  return g;
+}
+
+int validate(const aero_planner* pl, const aero_params_t* p, int64_t n_points) {
+  const aero_limits_t& L = pl->lim;
+  if (p->E < 1 || p->K < 1 || p->T < 1 || p->iters < 1 || p->iters > 255) return AERO_ERR_INVALID_ARG;
+  if (p->M_h < 1 || p->M_v < 1 || p->M_h * p->M_v != p->E) return AERO_ERR_INVALID_ARG;
+  if (p->fine_az < 2 || (p->fine_az & 1) || p->fine_el < 1 || p->fine_az > kMaxAz || p->fine_el > kMaxEl)
+    return AERO_ERR_INVALID_ARG;
+  if (p->pool_az < 1 || p->pool_el < 1 || p->fine_az % p->pool_az || p->fine_el % p->pool_el)
+    return AERO_ERR_INVALID_ARG;
+  if (!(p->dt > 0) || !(p->lambda > 0) || !(p->mass > 0) || !(p->r_max > 0) || !(p->ell > 0) ||
+      !(p->d_max > 0) || !(p->d_min < p->d_max) || !(p->el_lo < p->el_hi))
+    return AERO_ERR_INVALID_ARG;
+  for (int c = 0; c < 4; ++c)
+    if (!(p->u_min[c] <= p->u_max[c]) || !(p->sigma[c] >= 0)) return AERO_ERR_INVALID_ARG;
+  if (p->collision_set != 0 && p->collision_set != 1) return AERO_ERR_INVALID_ARG;
+  if (p->debug_samples < 0 || n_points < 0) return AERO_ERR_INVALID_ARG;
+  if (p->E > L.E_max || p->K > L.K_max || p->T > L.T_max ||
+      (int64_t)p->fine_az * p->fine_el > L.fine_cells_max || n_points > L.n_points_max ||
+      p->debug_samples > L.debug_samples_max)
+    return AERO_ERR_EXCEEDS_LIMITS;
+  return AERO_OK;
+}
+
+template <typename T>
+cudaError_t alloc(T** p, size_t count) {
+  return cudaMalloc((void**)p, sizeof(T) * (count > 0 ? count : 1));
+}
+
+void free_all(aero_planner* pl) {
+  void* ptrs[] = {pl->keys,     pl->coarse_win, pl->cells,        pl->anchors,  pl->guides,
+                  pl->item_cell, pl->item_slot, pl->grid_start,   pl->grid_pts, pl->partials,
+                  pl->sample_costs, pl->stage2_x, pl->counter,   pl->status,   pl->dbg_u,
+                  pl->dbg_x,    pl->dbg_d,      pl->stage_cloud,      pl->stage_unom,   pl->stage_ubest,
+                  pl->stage_cand,   pl->stage_best};
+  for (void* q : ptrs)
+    if (q) cudaFree(q);
+}
+
+constexpr size_t kProfSlots = 512;
+
+// Fold the recorded stage times into the accumulators (synchronises the events).
+cudaError_t prof_fold(aero_planner* pl) {
+  for (size_t i = 0; i < pl->slots_used; ++i) {
+    aero_planner::ProfSlot& sl = pl->slots[i];
+    cudaError_t e = cudaEventSynchronize(sl.ev[2 + 4 * sl.iters]);
+    if (e != cudaSuccess) return e;
+    float ms = 0.0f;
+    cudaEventElapsedTime(&ms, sl.ev[0], sl.ev[1]);
+    pl->prof_ms[AERO_STAGE_PARTITION] += ms;
+    cudaEventElapsedTime(&ms, sl.ev[1], sl.ev[2]);
+    pl->prof_ms[AERO_STAGE_GRID] += ms;
+    for (int it = 0; it < sl.iters; ++it) {
+      cudaEventElapsedTime(&ms, sl.ev[3 + 4 * it], sl.ev[4 + 4 * it]);
+      pl->prof_ms[AERO_STAGE_ROLLOUT] += ms;
+      cudaEventElapsedTime(&ms, sl.ev[5 + 4 * it], sl.ev[6 + 4 * it]);
+      pl->prof_ms[AERO_STAGE_UPDATE] += ms;
+    }
+    for (int k = 0; k < AERO_STAGE_COUNT; ++k) pl->prof_launches[k] += sl.launches[k];
+  }
+  pl->slots_used = 0;
+  return cudaSuccess;
+}
+
+// A slot with 3 + 4 iters events, or nullptr when profiling is off.
+aero_planner::ProfSlot* prof_slot(aero_planner* pl, int iters) {
+  if (!pl->prof) return nullptr;
+  if (pl->slots_used == kProfSlots && prof_fold(pl) != cudaSuccess) return nullptr;
+  if (pl->slots.size() < kProfSlots) pl->slots.resize(kProfSlots);
+  aero_planner::ProfSlot& sl = pl->slots[pl->slots_used];
+  const size_t need = 3 + 4 * (size_t)iters;
+  while (sl.ev.size() < need) {
+    cudaEvent_t ev;
+    if (cudaEventCreate(&ev) != cudaSuccess) return nullptr;
+    sl.ev.push_back(ev);
+  }
+  sl.iters = iters;
+  for (int k = 0; k < AERO_STAGE_COUNT; ++k) sl.launches[k] = 0;
+  ++pl->slots_used;
+  return &sl;
+}
+
+void prof_destroy(aero_planner* pl) {
+  for (auto& sl : pl->slots)
+    for (cudaEvent_t ev : sl.ev) cudaEventDestroy(ev);
+  pl->slots.clear();
+  pl->slots_used = 0;
+}
+
+// Enqueue one step; all pointers already validated.
+int enqueue_step(aero_planner* pl, const aero_state_t* x0, const float* cloud, int64_t n,
+                 const float* goal, const aero_params_t& p, float* u_nom, float* u_best,
+                 float* cand, int32_t* best_idx, cudaStream_t s) {
+  const int ncell = p.fine_az * p.fine_el;
+  PartTables tab;
+  int check_lo = 0, check_hi = 0;
+  make_tables(p, tab, check_lo, check_hi);
+  float R[9];
+  rot_f32(x0->q, R);
+  const float rm = p.r_max;
+  const float rmax2 = rm * rm;
+  const GridGeom grid = make_grid(p);
+  const int gcells = grid.G * grid.G * grid.G;
+  const bool raw = p.collision_set == 1;
+  const int64_t n_items = raw ? n : ncell;
+
+  cudaError_t e;
+  aero_planner::ProfSlot* prof = prof_slot(pl, p.iters);
+  auto mark = [&](int i) {
+    if (prof) cudaEventRecord(prof->ev[i], s);
+  };
+  mark(0);
+  if ((e = cudaMemsetAsync(pl->keys, 0xFF, sizeof(unsigned long long) * ncell, s)) != cudaSuccess)
+    return cuda_fail(e);
+  if ((e = cudaMemsetAsync(pl->grid_start, 0, sizeof(int) * (gcells + 1), s)) != cudaSuccess)
+    return cuda_fail(e);
+
+  PartitionArgs pa{};
+  pa.cloud = cloud;
+  pa.n = n;
+  for (int i = 0; i < 3; ++i) pa.p0[i] = x0->p[i];
+  for (int i = 0; i < 9; ++i) pa.R[i] = R[i];
+  pa.rmax2 = rmax2;
+  pa.A = p.fine_az;
+  pa.El = p.fine_el;
+  pa.check_lo = check_lo;
+  pa.check_hi = check_hi;
+  pa.keys = pl->keys;
+  pa.raw = raw;
+  pa.grid = grid;
+  pa.grid_count = pl->grid_start;
+  pa.item_cell = pl->item_cell;
+  pa.item_slot = pl->item_slot;
+  if ((e = launch_partition(pa, tab, s)) != cudaSuccess) return cuda_fail(e);
+  mark(1);
+  if (prof) {
+    prof->launches[AERO_STAGE_PARTITION] = n > 0 ? 1 : 0;
+    prof->launches[AERO_STAGE_GRID] = (raw ? 1 : 2) + (n_items > 0 ? 1 : 0);
+    prof->launches[AERO_STAGE_ROLLOUT] = p.iters;
+    prof->launches[AERO_STAGE_UPDATE] = p.iters;
+  }
+
+  if (!raw) {
+    if ((e = launch_pf_count(pl->keys, ncell, cloud, x0->p, grid, pl->grid_start, pl->item_cell,
+                             pl->item_slot, s)) != cudaSuccess)
+      return cuda_fail(e);
+  }
+
+  GuideArgs ga{};
+  ga.keys = pl->keys;
+  ga.A = p.fine_az;
+  ga.El = p.fine_el;
+  ga.Pa = p.pool_az;
+  ga.Pe = p.pool_el;
+  ga.Ac = p.fine_az / p.pool_az;
+  ga.Ec = p.fine_el / p.pool_el;
+  ga.rmax2 = rmax2;
+  ga.el_lo = p.el_lo;
+  ga.el_hi = p.el_hi;
+  for (int i = 0; i < 9; ++i) ga.R[i] = R[i];
+  for (int i = 0; i < 3; ++i) ga.goal_rel[i] = goal[i] - x0->p[i];
+  ga.M_h = p.M_h;
+  ga.M_v = p.M_v;
+  ga.E = p.E;
+  ga.ell = p.ell;
+  ga.T = p.T;
+  ga.dt = p.dt;
+  ga.v_end = p.v_end;
+  for (int i = 0; i < 3; ++i) ga.v0[i] = x0->v[i];
+  ga.coarse_win = pl->coarse_win;
+  ga.cells = pl->cells;
+  ga.anchors = pl->anchors;
+  ga.guides = pl->guides;
+  ga.grid_start = pl->grid_start;
+  ga.ncells = gcells;
+  if ((e = launch_scan_guides(ga, tab, s)) != cudaSuccess) return cuda_fail(e);
+
+  ScatterArgs sa{};
+  sa.cloud = cloud;
+  for (int i = 0; i < 3; ++i) sa.p0[i] = x0->p[i];
+  sa.item_cell = pl->item_cell;
+  sa.item_slot = pl->item_slot;
+  sa.keys = pl->keys;
+  sa.n_items = n_items;
+  sa.raw = raw;
+  sa.grid_start = pl->grid_start;
+  sa.grid_pts = pl->grid_pts;
+  if ((e = launch_scatter(sa, s)) != cudaSuccess) return cuda_fail(e);
+  mark(2);
+
+  CostParams cp{};
+  cp.Q_track = p.Q_track;
+  cp.Q_vnorm = p.Q_vnorm;
+  cp.Q_c = p.Q_c;
+  cp.Q_cd = p.Q_cd;
+  cp.Q_p = p.Q_p;
+  cp.Q_v = p.Q_v;
+  cp.Q_q = p.Q_q;
+  cp.C_col = p.C_col;
+  cp.a_col = p.a_col;
+  cp.d_min = p.d_min;
+  cp.d_max = p.d_max;
+  for (int i = 0; i < 3; ++i) cp.goal_rel[i] = goal[i] - x0->p[i];
+  for (int i = 0; i < 3; ++i) cp.v_goal[i] = p.v_goal[i];
+  for (int i = 0; i < 4; ++i) cp.q_goal[i] = p.q_goal[i];
+  DynParams dp{p.dt, 1.0f / p.mass, p.g};
+  GridView gv{pl->grid_start, pl->grid_pts, grid.G, grid.origin, grid.inv_h};
+  float x0v[10] = {0.0f, 0.0f, 0.0f, x0->q[0], x0->q[1], x0->q[2], x0->q[3],
+                   x0->v[0], x0->v[1], x0->v[2]};
+  const int nb = (p.K + kRolloutThreads - 1) / kRolloutThreads;
+
+  RolloutArgs ra{};
+  ra.E = p.E;
+  ra.K = p.K;
+  ra.T = p.T;
+  ra.nb = nb;
+  ra.inv_lambda = 1.0f / p.lambda;
+  for (int c = 0; c < 4; ++c) {
+    ra.sigma[c] = p.sigma[c];
+    ra.umin[c] = p.u_min[c];
+    ra.umax[c] = p.u_max[c];
+  }
+  for (int i = 0; i < 10; ++i) ra.x0[i] = x0v[i];
+  ra.key0 = (uint32_t)p.seed;
+  ra.key1 = (uint32_t)(p.seed >> 32);
+  ra.dyn = dp;
+  ra.cost = cp;
+  ra.u_nom = u_nom;
+  ra.guides = pl->guides;
+  ra.grid = gv;
+  ra.partials = pl->partials;
+  ra.sample_costs = pl->sample_costs;
+  ra.dbg_D = p.debug_samples < p.K ? p.debug_samples : p.K;
+  ra.dbg_u = pl->dbg_u;
+  ra.dbg_x = pl->dbg_x;
+  ra.dbg_d = pl->dbg_d;
+
+  UpdateArgs ua{};
+  ua.E = p.E;
+  ua.T = p.T;
+  ua.nb = nb;
+  ua.inv_lambda = ra.inv_lambda;
+  ua.partials = pl->partials;
+  ua.u_nom = u_nom;
+  for (int i = 0; i < 10; ++i) ua.x0[i] = x0v[i];
+  ua.dyn = dp;
+  ua.cost = cp;
+  ua.grid = gv;
+  ua.stage2_x = pl->stage2_x;
+  ua.cand = cand;
+  ua.best_idx = best_idx;
+  ua.u_best = u_best;
+  ua.counter = pl->counter;
+  ua.status = pl->status;
+
+  for (int it = 0; it < p.iters; ++it) {
+    ra.ctr3 = (uint32_t)((p.step_id << 8) | (uint64_t)(uint32_t)it);
+    mark(3 + 4 * it);
+    if ((e = launch_rollout(ra, s)) != cudaSuccess) return cuda_fail(e);
+    mark(4 + 4 * it);
+    ua.final_stage = it == p.iters - 1;
+    mark(5 + 4 * it);
+    if ((e = launch_update(ua, s)) != cudaSuccess) return cuda_fail(e);
+    mark(6 + 4 * it);
+  }
+
+  pl->have_step = true;
+  pl->last = p;
+  pl->last_grid = grid;
+  pl->last_items = n_items;
+  pl->last_nb = nb;
+  return AERO_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void aero_params_default(aero_params_t* p) {
+  if (!p) return;
+  std::memset(p, 0, sizeof(*p));
+  p->E = 15;
+  p->K = 128;
+  p->T = 25;
+  p->iters = 1;
+  p->dt = 0.05f;
+  p->lambda = 0.1f;
+  p->mass = 1.0f;
+  p->g = 9.81f;
+  const float sig[4] = {1.0f, 1.0f, 1.0f, 0.70710678f};
+  const float lo[4] = {0.3f, -3.0f, -3.0f, -2.0f};
+  const float hi[4] = {16.35f, 3.0f, 3.0f, 2.0f};
+  for (int c = 0; c < 4; ++c) {
+    p->sigma[c] = sig[c];
+    p->u_min[c] = lo[c];
+    p->u_max[c] = hi[c];
+  }
+  p->Q_track = 15.0f;
+  p->Q_vnorm = 0.15f;
+  p->Q_c = 0.5f;
+  p->Q_cd = 0.5f;
+  p->Q_p = 3.0f;
+  p->Q_v = 0.25f;
+  p->Q_q = 1.0f;
+  p->C_col = 1.0e6f;
+  p->a_col = 5.0f;
+  p->d_min = 0.4f;
+  p->d_max = 1.0f;
+  p->r_max = 10.0f;
+  p->ell = 5.0f;
+  p->v_end = 0.0f;
+  p->fine_az = 120;
+  p->fine_el = 60;
+  p->pool_az = 6;
+  p->pool_el = 6;
+  p->M_h = 5;
+  p->M_v = 3;
+  p->el_lo = -1.57079637f;
+  p->el_hi = 1.57079637f;
+  p->collision_set = 0;
+  p->q_goal[0] = 1.0f;
+  p->debug_samples = 0;
+  p->seed = 0;
+  p->step_id = 0;
+}
+
+int aero_create(const aero_limits_t* limits, aero_planner_t** out) {
+  if (!limits || !out) return AERO_ERR_INVALID_ARG;
+  *out = nullptr;
+  const aero_limits_t& L = *limits;
+  if (L.E_max < 1 || L.E_max > kMaxE || L.K_max < 1 || L.K_max > (1 << 20) || L.T_max < 1 ||
+      L.T_max > kMaxT || L.fine_cells_max < 2 || L.fine_cells_max > kMaxAz * kMaxEl ||
+      L.n_points_max < 0 || L.n_points_max > 0x7FFFFFFFLL || L.debug_samples_max < 0 ||
+      L.debug_samples_max > L.K_max)
+    return AERO_ERR_INVALID_ARG;
+  aero_planner* pl = new (std::nothrow) aero_planner();
+  if (!pl) return AERO_ERR_ALLOC;
+  pl->lim = L;
+  cudaGetDevice(&pl->device);
+  const int64_t nbmax = (L.K_max + kRolloutThreads - 1) / kRolloutThreads;
+  const int64_t items = L.n_points_max > L.fine_cells_max ? L.n_points_max : L.fine_cells_max;
+  pl->item_cap = items;
+  const int64_t D = L.debug_samples_max;
+  cudaError_t e = cudaSuccess;
+  auto chk = [&](cudaError_t r) {
+    if (r != cudaSuccess && e == cudaSuccess) e = r;
+  };
+  chk(alloc(&pl->keys, L.fine_cells_max));
+  chk(alloc(&pl->coarse_win, L.fine_cells_max));
+  chk(alloc(&pl->cells, L.E_max + 1));
+  chk(alloc(&pl->anchors, L.E_max * 3));
+  chk(alloc(&pl->guides, (size_t)L.E_max * L.T_max * 3));
+  chk(alloc(&pl->item_cell, items));
+  chk(alloc(&pl->item_slot, items));
+  chk(alloc(&pl->grid_start, kGridCellsMax + 1));
+  chk(alloc(&pl->grid_pts, items));
+  chk(alloc(&pl->partials, (size_t)L.E_max * nbmax * (2 + 4 * L.T_max)));
+  chk(alloc(&pl->sample_costs, (size_t)L.E_max * L.K_max));
+  chk(alloc(&pl->stage2_x, (size_t)L.E_max * (L.T_max + 1) * 10));
+  chk(alloc(&pl->counter, 1));
+  chk(alloc(&pl->status, 1));
+  chk(alloc(&pl->dbg_u, (size_t)L.E_max * D * L.T_max * 4));
+  chk(alloc(&pl->dbg_x, (size_t)L.E_max * D * (L.T_max + 1) * 10));
+  chk(alloc(&pl->dbg_d, (size_t)L.E_max * D * L.T_max));
+  chk(alloc(&pl->stage_cloud, (size_t)L.n_points_max * 3));
+  chk(alloc(&pl->stage_unom, (size_t)L.E_max * L.T_max * 4));
+  chk(alloc(&pl->stage_ubest, (size_t)L.T_max * 4));
+  chk(alloc(&pl->stage_cand, L.E_max));
+  chk(alloc(&pl->stage_best, 1));
+  if (e == cudaSuccess) e = cudaMemset(pl->counter, 0, sizeof(unsigned int));
+  if (e == cudaSuccess) e = cudaMemset(pl->status, 0, sizeof(int));
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    free_all(pl);
+    delete pl;
+    return e == cudaErrorMemoryAllocation ? AERO_ERR_ALLOC : AERO_ERR_CUDA;
+  }
+  *out = pl;
+  return AERO_OK;
+}
+
+int aero_destroy(aero_planner_t* pl) {
+  if (!pl) return AERO_OK;
+  cudaDeviceSynchronize();
+  prof_destroy(pl);
+  free_all(pl);
+  delete pl;
+  return AERO_OK;
+}
+
+int aero_plan_step(aero_planner_t* pl, const aero_state_t* x0, const float* cloud, int64_t n,
+                   const float goal[3], const aero_params_t* params, float* u_nom, float* u_best,
+                   float* cand, int32_t* best_idx, void* stream) {
+  if (!pl || !x0 || !goal || !params || !u_nom || !u_best || !cand || !best_idx)
+    return AERO_ERR_INVALID_ARG;
+  if (n > 0 && !cloud) return AERO_ERR_INVALID_ARG;
+  int rc = validate(pl, params, n);
+  if (rc != AERO_OK) return rc;
+  if (reinterpret_cast<uintptr_t>(u_nom) % 16 != 0) return AERO_ERR_INVALID_ARG;
+  if ((n > 0 && !is_device_ptr(cloud)) || !is_device_ptr(u_nom) || !is_device_ptr(u_best) ||
+      !is_device_ptr(cand) || !is_device_ptr(best_idx))
+    return AERO_ERR_NOT_DEVICE_PTR;
+  return enqueue_step(pl, x0, cloud, n, goal, *params, u_nom, u_best, cand, best_idx,
+                      (cudaStream_t)stream);
+}
+
+int aero_plan_step_host(aero_planner_t* pl, const aero_state_t* x0, const float* cloud, int64_t n,
+                        const float goal[3], const aero_params_t* params, float* u_nom,
+                        float* u_best, float* cand, int32_t* best_idx, void* stream) {
+  if (!pl || !x0 || !goal || !params || !u_nom || !u_best || !cand || !best_idx)
+    return AERO_ERR_INVALID_ARG;
+  if (n > 0 && !cloud) return AERO_ERR_INVALID_ARG;
+  int rc = validate(pl, params, n);
+  if (rc != AERO_OK) return rc;
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t nu = (size_t)params->E * params->T * 4;
+  cudaError_t e;
+  if (n > 0 && (e = cudaMemcpyAsync(pl->stage_cloud, cloud, sizeof(float) * 3 * n,
+                                    cudaMemcpyHostToDevice, s)) != cudaSuccess)
+    return cuda_fail(e);
+  if ((e = cudaMemcpyAsync(pl->stage_unom, u_nom, sizeof(float) * nu, cudaMemcpyHostToDevice, s)) !=
+      cudaSuccess)
+    return cuda_fail(e);
+  rc = enqueue_step(pl, x0, pl->stage_cloud, n, goal, *params, pl->stage_unom, pl->stage_ubest, pl->stage_cand,
+                    pl->stage_best, s);
+  if (rc != AERO_OK) return rc;
+  if ((e = cudaMemcpyAsync(u_nom, pl->stage_unom, sizeof(float) * nu, cudaMemcpyDeviceToHost, s)) !=
+          cudaSuccess ||
+      (e = cudaMemcpyAsync(u_best, pl->stage_ubest, sizeof(float) * params->T * 4,
+                           cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
+      (e = cudaMemcpyAsync(cand, pl->stage_cand, sizeof(float) * params->E, cudaMemcpyDeviceToHost,
+                           s)) != cudaSuccess ||
+      (e = cudaMemcpyAsync(best_idx, pl->stage_best, sizeof(int32_t), cudaMemcpyDeviceToHost, s)) !=
+          cudaSuccess)
+    return cuda_fail(e);
+  return cuda_fail(cudaStreamSynchronize(s));
+}
+
+size_t aero_debug_size(aero_planner_t* pl, int32_t what) {
+  if (!pl || !pl->have_step) return 0;
+  const aero_params_t& p = pl->last;
+  const size_t E = p.E, T = p.T, K = p.K;
+  const size_t D = p.debug_samples < p.K ? p.debug_samples : p.K;
+  const size_t G = pl->last_grid.G;
+  switch (what) {
+    case AERO_DBG_FINE_KEYS: return 8 * (size_t)p.fine_az * p.fine_el;
+    case AERO_DBG_COARSE_WIN: return 4 * (size_t)(p.fine_az / p.pool_az) * (p.fine_el / p.pool_el);
+    case AERO_DBG_GOAL_CELL: return 4;
+    case AERO_DBG_ANCHOR_CELLS: return 4 * E;
+    case AERO_DBG_ANCHORS: return 4 * E * 3;
+    case AERO_DBG_GUIDES: return 4 * E * T * 3;
+    case AERO_DBG_GRID_META: return 32;
+    case AERO_DBG_GRID_START: return 4 * (G * G * G + 1);
+    case AERO_DBG_GRID_POINTS: return 0;  // size known after the step; see aero_get_debug
+    case AERO_DBG_SAMPLE_COSTS: return 4 * E * K;
+    case AERO_DBG_STAGE2_STATES: return 4 * E * (T + 1) * 10;
+    case AERO_DBG_SAMPLE_U: return 4 * E * D * T * 4;
+    case AERO_DBG_SAMPLE_X: return 4 * E * D * (T + 1) * 10;
+    case AERO_DBG_SAMPLE_DIST: return 4 * E * D * T;
+    default: return 0;
+  }
+}
+
+int aero_get_debug(aero_planner_t* pl, int32_t what, void* dst, size_t bytes, void* stream) {
+  if (!pl || !dst || !pl->have_step || what < 0 || what >= AERO_DBG_COUNT) return AERO_ERR_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  const aero_params_t& p = pl->last;
+  if (what == AERO_DBG_GRID_META) {
+    if (bytes < 32) return AERO_ERR_INVALID_ARG;
+    int32_t meta[8] = {0};
+    meta[0] = pl->last_grid.G;
+    float f[2] = {pl->last_grid.origin, pl->last_grid.h};
+    std::memcpy(&meta[4], f, sizeof(f));
+    // number of collision points = grid_start[G^3]
+    const int gcells = pl->last_grid.G * pl->last_grid.G * pl->last_grid.G;
+    cudaError_t e = cudaMemcpyAsync(&meta[1], pl->grid_start + gcells, 4, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e);
+    std::memcpy(dst, meta, 32);
+    return AERO_OK;
+  }
+  if (what == AERO_DBG_GRID_POINTS) {
+    const int gcells = pl->last_grid.G * pl->last_grid.G * pl->last_grid.G;
+    int32_t npts = 0;
+    cudaError_t e = cudaMemcpyAsync(&npts, pl->grid_start + gcells, 4, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e);
+    const size_t need = sizeof(float4) * (size_t)npts;
+    if (bytes < need) return AERO_ERR_INVALID_ARG;
+    return cuda_fail(cudaMemcpyAsync(dst, pl->grid_pts, need, cudaMemcpyDefault, s));
+  }
+  const size_t need = aero_debug_size(pl, what);
+  if (bytes < need) return AERO_ERR_INVALID_ARG;
+  const void* src = nullptr;
+  switch (what) {
+    case AERO_DBG_FINE_KEYS: src = pl->keys; break;
+    case AERO_DBG_COARSE_WIN: src = pl->coarse_win; break;
+    case AERO_DBG_GOAL_CELL: src = pl->cells; break;
+    case AERO_DBG_ANCHOR_CELLS: src = pl->cells + 1; break;
+    case AERO_DBG_ANCHORS: src = pl->anchors; break;
+    case AERO_DBG_GUIDES: src = pl->guides; break;
+    case AERO_DBG_GRID_START: src = pl->grid_start; break;
+    case AERO_DBG_SAMPLE_COSTS: src = pl->sample_costs; break;
+    case AERO_DBG_STAGE2_STATES: src = pl->stage2_x; break;
+    case AERO_DBG_SAMPLE_U: src = pl->dbg_u; break;
+    case AERO_DBG_SAMPLE_X: src = pl->dbg_x; break;
+    case AERO_DBG_SAMPLE_DIST: src = pl->dbg_d; break;
+    default: return AERO_ERR_INVALID_ARG;
+  }
+  (void)p;
+  if (need == 0) return AERO_OK;
+  return cuda_fail(cudaMemcpyAsync(dst, src, need, cudaMemcpyDefault, s));
+}
+
+int aero_sync_status(aero_planner_t* pl, void* stream) {
+  if (!pl) return AERO_ERR_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  int st = 0;
+  cudaError_t e = cudaMemcpyAsync(&st, pl->status, sizeof(int), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return AERO_ERR_CUDA;
+  if (st != 0) {
+    cudaMemsetAsync(pl->status, 0, sizeof(int), s);
+    cudaStreamSynchronize(s);
+    return AERO_ERR_DEVICE_CHECK;
+  }
+  return AERO_OK;
+}
+
+int aero_philox(uint64_t seed, uint32_t c1, uint32_t c2, uint32_t c3, int64_t n, uint32_t* out,
+                void* stream) {
+  if (n < 0 || n > 0xFFFFFFFFLL || (n > 0 && !out)) return AERO_ERR_INVALID_ARG;
+  if (n > 0 && !is_device_ptr(out)) return AERO_ERR_NOT_DEVICE_PTR;
+  return cuda_fail(launch_philox((uint32_t)seed, (uint32_t)(seed >> 32), c1, c2, c3, n, out,
+                                 (cudaStream_t)stream));
+}
+
+int aero_profile_enable(aero_planner_t* pl, int on) {
+  if (!pl) return AERO_ERR_INVALID_ARG;
+  pl->prof = on != 0;
+  return AERO_OK;
+}
+
+int aero_profile_read(aero_planner_t* pl, double* ms, int64_t* launches) {
+  if (!pl || !ms || !launches) return AERO_ERR_INVALID_ARG;
+  cudaError_t e = prof_fold(pl);
+  if (e != cudaSuccess) return AERO_ERR_CUDA;
+  for (int k = 0; k < AERO_STAGE_COUNT; ++k) {
+    ms[k] = pl->prof_ms[k];
+    launches[k] = pl->prof_launches[k];
+    pl->prof_ms[k] = 0.0;
+    pl->prof_launches[k] = 0;
+  }
+  return AERO_OK;
+}
+
+const char* aero_status_str(int status) {
+  switch (status) {
+    case AERO_OK: return "ok";
+    case AERO_ERR_INVALID_ARG: return "invalid argument";
+    case AERO_ERR_EXCEEDS_LIMITS: return "size exceeds the planner's limits";
+    case AERO_ERR_CUDA: return "CUDA runtime error";
+    case AERO_ERR_ALLOC: return "workspace allocation failed";
+    case AERO_ERR_DEVICE_CHECK: return "a kernel reported an internal inconsistency";
+    case AERO_ERR_NOT_DEVICE_PTR: return "pointer is not device memory";
+    default: return "unknown status";
+  }
+}
+
+}  // extern "C"

@@ -1,0 +1,153 @@
+// Internal interface between the C-ABI host runtime (aero_mppi.cu) and the
+// kernel translation units (partition.cu, rollout.cu).  Not installed.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace aero {
+
+constexpr int kMaxAz = 512;
+constexpr int kMaxEl = 256;
+constexpr int kMaxE = 64;
+constexpr int kMaxT = 128;
+constexpr int kGridMax = 64;        // collision grid cells per axis, at most
+constexpr int kRolloutThreads = 128; // samples per rollout CTA (one warp-group)
+constexpr float kCellMargin = 1.0625f; // grid cell edge = d_max * (1 + 1/16), at least
+
+// Binary32 edge tables of the partition, passed by value to the kernels.
+// Azimuth edge k: theta_k = pi (2k - A) / A; elevation edge k: phi_k = lo +
+// ((hi - lo) k) / El; each entry is the binary64 cos / sin rounded to binary32.
+struct PartTables {
+  float ca[kMaxAz];
+  float sa[kMaxAz];
+  float ce[kMaxEl + 1];
+  float se[kMaxEl + 1];
+};
+
+// Uniform collision grid in world axes, coordinates relative to p0.
+struct GridGeom {
+  int G;          // cells per axis
+  float origin;   // same on all three axes
+  float h, inv_h; // cell edge and its reciprocal
+};
+
+struct PartitionArgs {
+  const float* cloud;
+  int64_t n;
+  float p0[3];
+  float R[9];      // R(q0) in binary32, row-major
+  float rmax2;     // r_max * r_max in binary32
+  int A, El;
+  int check_lo, check_hi;
+  unsigned long long* keys;
+  // collision set = every kept point: the partition also counts grid cells
+  int raw;
+  GridGeom grid;
+  int* grid_count;
+  int* item_cell;
+  int* item_slot;
+};
+
+struct GuideArgs {
+  // partition
+  const unsigned long long* keys;
+  int A, El, Pa, Pe, Ac, Ec;
+  float rmax2;
+  float el_lo, el_hi;  // binary32 span, promoted to binary64 for cell centres
+  float R[9];          // R(q0) binary32
+  float goal_rel[3];   // goal - p0, binary32
+  int M_h, M_v, E;
+  float ell;
+  // guides
+  int T;
+  float dt, v_end;     // v_end <= 0: ell / (T dt)
+  float v0[3];
+  // outputs
+  int* coarse_win;     // Ac * Ec
+  int* cells;          // [0] goal fine cell, [1 + e] anchor coarse cell
+  float* anchors;      // E x 3 (relative to p0)
+  float* guides;       // E x T x 3 (relative to p0)
+  // scan of the grid counts (block 0)
+  int* grid_start;     // G^3 + 1, counts in, exclusive prefix out
+  int ncells;
+};
+
+struct ScatterArgs {
+  const float* cloud;
+  float p0[3];
+  const int* item_cell;
+  const int* item_slot;
+  const unsigned long long* keys; // P_f mode: item c is the winner of fine cell c
+  int64_t n_items;
+  int raw;
+  const int* grid_start;
+  float4* grid_pts;
+};
+
+struct GridView {
+  const int* start;
+  const float4* pts;
+  int G;
+  float origin, inv_h;
+};
+
+struct CostParams {
+  float Q_track, Q_vnorm, Q_c, Q_cd, Q_p, Q_v, Q_q;
+  float C_col, a_col, d_min, d_max;
+  float goal_rel[3], v_goal[3], q_goal[4];
+};
+
+struct DynParams {
+  float dt, inv_mass, g;
+};
+
+struct RolloutArgs {
+  int E, K, T, nb;         // nb = CTAs per instance
+  float inv_lambda;
+  float sigma[4], umin[4], umax[4];
+  float x0[10];            // p = 0 (relative), q0, v0
+  uint32_t key0, key1, ctr3;
+  DynParams dyn;
+  CostParams cost;
+  const float* u_nom;      // E x T x 4
+  const float* guides;     // E x T x 3 (relative)
+  GridView grid;
+  float* partials;         // E x nb x (2 + 4T)
+  float* sample_costs;     // E x K
+  int dbg_D;
+  float* dbg_u;            // E x D x T x 4
+  float* dbg_x;            // E x D x (T+1) x 10
+  float* dbg_d;            // E x D x T
+};
+
+struct UpdateArgs {
+  int E, T, nb;
+  float inv_lambda;
+  const float* partials;
+  float* u_nom;            // E x T x 4 (in/out)
+  int final_stage;         // run Stage II and the selection
+  float x0[10];
+  DynParams dyn;
+  CostParams cost;
+  GridView grid;
+  float* stage2_x;         // E x (T+1) x 10
+  float* cand;             // E
+  int* best_idx;
+  float* u_best;           // T x 4
+  unsigned int* counter;   // last-CTA ticket, 0 between launches
+  int* status;             // bit 0: a normaliser eta was not a positive finite number
+};
+
+cudaError_t launch_partition(const PartitionArgs& a, const PartTables& t, cudaStream_t s);
+cudaError_t launch_pf_count(const unsigned long long* keys, int ncell, const float* cloud,
+                            const float p0[3], GridGeom g, int* grid_count, int* item_cell,
+                            int* item_slot, cudaStream_t s);
+cudaError_t launch_scan_guides(const GuideArgs& a, const PartTables& t, cudaStream_t s);
+cudaError_t launch_scatter(const ScatterArgs& a, cudaStream_t s);
+cudaError_t launch_rollout(const RolloutArgs& a, cudaStream_t s);
+cudaError_t launch_update(const UpdateArgs& a, cudaStream_t s);
+cudaError_t launch_philox(uint32_t k0, uint32_t k1, uint32_t c1, uint32_t c2, uint32_t c3,
+                          int64_t n, uint32_t* out, cudaStream_t s);
+
+}  // namespace aero

@@ -1,0 +1,273 @@
+// Stage I of the MPPI ensemble (Sec. III-B, Sec. IV-C): one CTA of 128 threads
+// (one warp-group) rolls out 128 samples of one instance.  Per sample and
+// step: Philox noise in registers, clamp, RK4, the S(1) cost terms with the
+// nearest-point distance from the collision grid.  Then per CTA: the minimum
+// cost rho_b, eta_b = sum exp(-(S - rho_b)/lambda) and, by regenerating the
+// noise, W_b[j][c] = sum exp(-(S - rho_b)/lambda) du[j][c].  The update kernel
+// merges the per-CTA partials (log-sum-exp rescaling by the global minimum),
+// updates the nominal (Eq. mppi_update_simplified), and on the last iteration
+// runs Stage II and the selection.
+#include <cfloat>
+#include <cstdint>
+
+#include "device.cuh"
+#include "internal.h"
+
+namespace aero {
+namespace {
+
+constexpr int NT = kRolloutThreads;
+constexpr int NW = NT / 32;
+
+__device__ __forceinline__ float4 clamp4(float4 u, const float* lo, const float* hi) {
+  return make_float4(fminf(fmaxf(u.x, lo[0]), hi[0]), fminf(fmaxf(u.y, lo[1]), hi[1]),
+                     fminf(fmaxf(u.z, lo[2]), hi[2]), fminf(fmaxf(u.w, lo[3]), hi[3]));
+}
+
+// Kahan-compensated accumulation of the per-step costs.
+struct KahanSum {
+  float s = 0.0f, c = 0.0f;
+  __device__ __forceinline__ void add(float v) {
+    const float y = v - c;
+    const float t = s + y;
+    c = (t - s) - y;
+    s = t;
+  }
+};
+
+__global__ void __launch_bounds__(NT) k_rollout(RolloutArgs a) {
+  __shared__ float4 s_un[kMaxT];
+  __shared__ float s_gd[kMaxT * 3];
+  __shared__ float s_red[NW];
+  __shared__ float4 s_w[NW][kMaxT];
+
+  const int e = blockIdx.y, b = blockIdx.x, tid = threadIdx.x;
+  const int lane = tid & 31, wid = tid >> 5;
+  const int T = a.T;
+  for (int i = tid; i < T; i += NT) s_un[i] = reinterpret_cast<const float4*>(a.u_nom)[e * T + i];
+  for (int i = tid; i < 3 * T; i += NT) s_gd[i] = a.guides[e * T * 3 + i];
+  __syncthreads();
+
+  const int k = b * NT + tid;
+  const bool active = k < a.K;
+  const CostParams& cp = a.cost;
+  const float dmax2 = cp.d_max * cp.d_max;
+  const int dbg = (active && k < a.dbg_D) ? (e * a.dbg_D + k) : -1;
+
+  State x;
+#pragma unroll
+  for (int i = 0; i < 3; ++i) x.p[i] = a.x0[i];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) x.q[i] = a.x0[3 + i];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) x.v[i] = a.x0[7 + i];
+  if (dbg >= 0) {
+    float* X = a.dbg_x + (size_t)dbg * (T + 1) * 10;
+    for (int i = 0; i < 10; ++i) X[i] = a.x0[i];
+  }
+
+  KahanSum S;
+  float4 u_prev = make_float4(0.f, 0.f, 0.f, 0.f);
+  for (int j = 0; j < T; ++j) {
+    const float4 un = s_un[j];
+    const float4 d = noise_delta(k, j, e, a.ctr3, a.key0, a.key1, a.sigma);
+    const float4 u = clamp4(make_float4(un.x + d.x, un.y + d.y, un.z + d.z, un.w + d.w), a.umin, a.umax);
+    // J_ctrl: Q_c |u_j|^2 for j <= T-2, Q_cd |u_j - u_{j-1}|^2 for 1 <= j <= T-2
+    float c = 0.0f;
+    if (j <= T - 2) {
+      c = cp.Q_c * (u.x * u.x + u.y * u.y + u.z * u.z + u.w * u.w);
+      if (j >= 1) {
+        const float ax = u.x - u_prev.x, ay = u.y - u_prev.y, az = u.z - u_prev.z, aw = u.w - u_prev.w;
+        c += cp.Q_cd * (ax * ax + ay * ay + az * az + aw * aw);
+      }
+    }
+    u_prev = u;
+    rk4_step(x, u, a.dyn);
+    // state terms at x_{j+1} against the guide at t = (j+1) dt
+    const float* g = s_gd + 3 * j;
+    c += cp.Q_track * norm3f(x.p[0] - g[0], x.p[1] - g[1], x.p[2] - g[2]);
+    c += cp.Q_vnorm * (x.v[0] * x.v[0] + x.v[1] * x.v[1] + x.v[2] * x.v[2]);
+    c += goal_term(x, cp);
+    const float d2 = nn_dist2(x.p[0], x.p[1], x.p[2], a.grid, cp.d_max, dmax2);
+    c += jcol_from_d2(d2, cp, dmax2);
+    S.add(c);
+    if (dbg >= 0) {
+      reinterpret_cast<float4*>(a.dbg_u)[(size_t)dbg * T + j] = u;
+      float* X = a.dbg_x + ((size_t)dbg * (T + 1) + j + 1) * 10;
+      for (int i = 0; i < 3; ++i) X[i] = x.p[i];
+      for (int i = 0; i < 4; ++i) X[3 + i] = x.q[i];
+      for (int i = 0; i < 3; ++i) X[7 + i] = x.v[i];
+      a.dbg_d[(size_t)dbg * T + j] = d2 < dmax2 ? sqrtf(d2) : INFINITY;
+    }
+  }
+  const float Sk = S.s;
+  if (active) a.sample_costs[(size_t)e * a.K + k] = Sk;
+
+  // rho_b = min S over the CTA
+  float m = warp_min(active ? Sk : INFINITY);
+  if (lane == 0) s_red[wid] = m;
+  __syncthreads();
+  float rho = s_red[0];
+#pragma unroll
+  for (int w = 1; w < NW; ++w) rho = fminf(rho, s_red[w]);
+  __syncthreads();
+  const float wk = active ? expf((rho - Sk) * a.inv_lambda) : 0.0f;
+  const float ws = warp_sum(wk);
+  if (lane == 0) s_red[wid] = ws;
+
+  // W_b[j] = sum_k w_k du_k[j], regenerating the noise
+  for (int j = 0; j < T; ++j) {
+    const float4 un = s_un[j];
+    const float4 d = noise_delta(k, j, e, a.ctr3, a.key0, a.key1, a.sigma);
+    const float4 u = clamp4(make_float4(un.x + d.x, un.y + d.y, un.z + d.z, un.w + d.w), a.umin, a.umax);
+    const float r = warp_sum4(wk * (u.x - un.x), wk * (u.y - un.y), wk * (u.z - un.z),
+                              wk * (u.w - un.w), lane);
+    if ((lane & 7) == 0) reinterpret_cast<float*>(&s_w[wid][j])[lane >> 3] = r;
+  }
+  __syncthreads();
+  float* out = a.partials + ((size_t)e * a.nb + b) * (2 + 4 * T);
+  if (tid == 0) {
+    float eta = 0.0f;
+#pragma unroll
+    for (int w = 0; w < NW; ++w) eta += s_red[w];
+    out[0] = rho;
+    out[1] = eta;
+  }
+  for (int i = tid; i < 4 * T; i += NT) {
+    const int j = i >> 2, cc = i & 3;
+    float s = 0.0f;
+#pragma unroll
+    for (int w = 0; w < NW; ++w) s += reinterpret_cast<const float*>(&s_w[w][j])[cc];
+    out[2 + i] = s;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Merge the per-CTA partials of one instance and update its nominal; on the
+// final iteration roll out the updated nominal (Stage II), score S(2), and let
+// the last CTA to finish pick the argmin.
+// ---------------------------------------------------------------------------
+constexpr int UT = 128;
+
+__global__ void __launch_bounds__(UT) k_update(UpdateArgs a) {
+  __shared__ float s_scale[1024];
+  __shared__ float s_red[UT / 32];
+  __shared__ float s_x[(kMaxT + 1) * 10];
+  __shared__ float4 s_u4[kMaxT];
+  float* s_u = reinterpret_cast<float*>(s_u4);
+  __shared__ float s_c[kMaxT];
+  __shared__ bool s_last;
+  const int e = blockIdx.x, tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const int T = a.T, stride = 2 + 4 * T;
+  const float* P = a.partials + (size_t)e * a.nb * stride;
+
+  // rho = min rho_b
+  float m = INFINITY;
+  for (int b = tid; b < a.nb; b += UT) m = fminf(m, P[(size_t)b * stride]);
+  m = warp_min(m);
+  if (lane == 0) s_red[wid] = m;
+  __syncthreads();
+  float rho = s_red[0];
+  for (int w = 1; w < UT / 32; ++w) rho = fminf(rho, s_red[w]);
+  __syncthreads();
+  // eta = sum eta_b exp(-(rho_b - rho)/lambda)
+  float eta = 0.0f;
+  for (int b = tid; b < a.nb; b += UT) {
+    const float sc = expf((rho - P[(size_t)b * stride]) * a.inv_lambda);
+    if (b < 1024) s_scale[b] = sc;
+    eta += sc * P[(size_t)b * stride + 1];
+  }
+  eta = warp_sum(eta);
+  if (lane == 0) s_red[wid] = eta;
+  __syncthreads();
+  eta = 0.0f;
+  for (int w = 0; w < UT / 32; ++w) eta += s_red[w];
+  if (!(eta > 0.0f) || !isfinite(eta) || !isfinite(rho)) {
+    if (tid == 0) atomicOr(a.status, 1);
+  }
+  const float inv_eta = 1.0f / eta;
+  float* un = a.u_nom + (size_t)e * T * 4;
+  for (int i = tid; i < 4 * T; i += UT) {
+    float s = 0.0f;
+    for (int b = 0; b < a.nb; ++b) {
+      const float sc = b < 1024 ? s_scale[b] : expf((rho - P[(size_t)b * stride]) * a.inv_lambda);
+      s += sc * P[(size_t)b * stride + 2 + i];
+    }
+    const float v = un[i] + s * inv_eta;
+    un[i] = v;
+    s_u[i] = v;
+  }
+  if (!a.final_stage) return;
+  __syncthreads();
+
+  // Stage II: noise-free rollout of the updated nominal
+  if (tid == 0) {
+    State x;
+    for (int i = 0; i < 3; ++i) x.p[i] = a.x0[i];
+    for (int i = 0; i < 4; ++i) x.q[i] = a.x0[3 + i];
+    for (int i = 0; i < 3; ++i) x.v[i] = a.x0[7 + i];
+    for (int i = 0; i < 10; ++i) s_x[i] = a.x0[i];
+    for (int j = 0; j < T; ++j) {
+      rk4_step(x, s_u4[j], a.dyn);
+      float* X = s_x + (j + 1) * 10;
+      for (int i = 0; i < 3; ++i) X[i] = x.p[i];
+      for (int i = 0; i < 4; ++i) X[3 + i] = x.q[i];
+      for (int i = 0; i < 3; ++i) X[7 + i] = x.v[i];
+    }
+  }
+  __syncthreads();
+  const float dmax2 = a.cost.d_max * a.cost.d_max;
+  for (int j = tid; j < T; j += UT) {
+    const float* X = s_x + (j + 1) * 10;
+    State x;
+    for (int i = 0; i < 3; ++i) x.p[i] = X[i];
+    for (int i = 0; i < 4; ++i) x.q[i] = X[3 + i];
+    for (int i = 0; i < 3; ++i) x.v[i] = X[7 + i];
+    const float d2 = nn_dist2(x.p[0], x.p[1], x.p[2], a.grid, a.cost.d_max, dmax2);
+    s_c[j] = goal_term(x, a.cost) + jcol_from_d2(d2, a.cost, dmax2);
+  }
+  for (int i = tid; i < (T + 1) * 10; i += UT) a.stage2_x[(size_t)e * (T + 1) * 10 + i] = s_x[i];
+  __syncthreads();
+  if (tid == 0) {
+    double s2 = 0.0;
+    for (int j = 0; j < T; ++j) s2 += (double)s_c[j];
+    a.cand[e] = (float)s2;
+  }
+  // last CTA to arrive selects the best instance
+  __threadfence();
+  __syncthreads();
+  if (tid == 0) s_last = atomicAdd(a.counter, 1u) == (unsigned)(gridDim.x - 1);
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  __shared__ int s_best;
+  if (tid == 0) {
+    int best = 0;
+    float bc = __ldcg(a.cand);
+    for (int i = 1; i < a.E; ++i) {
+      const float c = __ldcg(a.cand + i);
+      if (c < bc) { bc = c; best = i; }
+    }
+    s_best = best;
+    *a.best_idx = best;
+    *a.counter = 0u;
+  }
+  __syncthreads();
+  const float* ub = a.u_nom + (size_t)s_best * T * 4;
+  for (int i = tid; i < 4 * T; i += UT) a.u_best[i] = __ldcg(ub + i);
+}
+
+}  // namespace
+
+cudaError_t launch_rollout(const RolloutArgs& a, cudaStream_t s) {
+  dim3 grid(a.nb, a.E);
+  k_rollout<<<grid, NT, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_update(const UpdateArgs& a, cudaStream_t s) {
+  k_update<<<a.E, UT, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+}  // namespace aero

@@ -1,0 +1,87 @@
+"""The C-ABI library builds, loads and exports every entry point declared in
+include/*.h; host-only behaviour of the boundary (no GPU needed)."""
+import ctypes as C
+import glob
+import json
+import math
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def so():
+    from paper_2509_17340_gb300 import build
+    path = build.build()
+    return C.CDLL(path)
+
+
+def declared_functions():
+    names = []
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        src = open(h).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        names += re.findall(r"^\s*(?:const\s+)?\w+\s*\*?\s*(aero_\w+)\s*\(", src, flags=re.M)
+    return sorted(set(names))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for must in ["aero_create", "aero_destroy", "aero_plan_step", "aero_plan_step_host",
+                 "aero_get_debug", "aero_debug_size", "aero_sync_status", "aero_status_str",
+                 "aero_params_default", "aero_philox"]:
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol(so):
+    for name in declared_functions():
+        assert hasattr(so, name), name
+
+
+def test_status_strings(so):
+    so.aero_status_str.restype = C.c_char_p
+    assert so.aero_status_str(0) == b"ok"
+    for code in range(-6, 0):
+        assert so.aero_status_str(code) != b"unknown status"
+    assert so.aero_status_str(-99) == b"unknown status"
+
+
+def test_null_arguments_are_rejected_without_cuda(so):
+    # argument checks come before any CUDA call
+    assert so.aero_create(None, None) == -1
+    assert so.aero_plan_step(None, None, None, C.c_int64(0), None, None, None, None, None, None, None) == -1
+    assert so.aero_plan_step_host(None, None, None, C.c_int64(0), None, None, None, None, None, None, None) == -1
+    assert so.aero_get_debug(None, 0, None, C.c_size_t(0), None) == -1
+    assert so.aero_destroy(None) == 0
+
+
+def test_params_default_is_table_I(so):
+    import sys
+    sys.path.insert(0, ROOT)
+    # the binding's struct mirrors the header; it imports torch but needs no GPU
+    from paper_2509_17340_gb300 import aero
+    p = aero.default_params_struct()
+    t = json.load(open(os.path.join(ROOT, "tests", "golden", "table1.json")))
+    f32 = lambda v: C.c_float(v).value
+    assert p.mass == f32(t["m_kg"]) and p.dt == f32(t["dt_s"]) and p.lam == f32(t["lambda"])
+    assert p.K == t["K"] and p.T == t["N"] and p.E == t["M_h"] * t["M_v"]
+    assert p.u_min[0] == f32(t["F_t_min_N"]) and p.u_max[0] == f32(t["F_t_max_N"])
+    assert p.u_max[1] == f32(t["omega_xy_max"]) and p.u_max[3] == f32(t["omega_z_max"])
+    assert abs(p.sigma[3] ** 2 - t["Sigma_omega_z"]) < 1e-6 and p.sigma[0] ** 2 == t["Sigma_Ft"]
+    for a, b in [("Q_p", "Q_p"), ("Q_v", "Q_v"), ("Q_q", "Q_q"), ("Q_vnorm", "Q_vnorm"),
+                 ("Q_track", "Q_track"), ("Q_c", "Q_c"), ("Q_cd", "Q_cdelta"), ("ell", "ell_m"),
+                 ("C_col", "C"), ("a_col", "a"), ("d_min", "d_obs_min_m"), ("d_max", "d_obs_max_m"),
+                 ("r_max", "r_max_m")]:
+        assert getattr(p, a) == f32(t[b]), a
+    assert [p.fine_az, p.fine_el] == t["fine_grid"] and [p.pool_az, p.pool_el] == t["pooling"]
+    assert abs(p.el_hi - math.pi / 2) < 1e-6 and p.q_goal[0] == 1.0
+
+
+def test_binding_struct_sizes_match_header():
+    from paper_2509_17340_gb300 import aero
+    assert C.sizeof(aero.State) == 40
+    assert C.sizeof(aero.Limits) == 32
+    assert C.sizeof(aero.Params) == 224

@@ -1,0 +1,413 @@
+"""CUDA path against the CPU oracle, element by element (needs a GB300).
+
+The staged protocol: Philox integers and every partition / coarse / anchor /
+selection index bit-exact; perturbations, rollouts, costs and the update within
+the FP32 tolerances of ``gpu_util``; the end-to-end nominal within the same
+tolerance.  Samples whose oracle nearest-point distance lies within JUMP_BAND of
+d_min or d_max (where J_col jumps) are excluded from the cost comparison.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2509_17340_gb300 import inputs as I
+from gpu_util import (JUMP_BAND, TOL_COST_REL, TOL_DELTA, TOL_POS, TOL_QUAT, TOL_U, TOL_VEL,
+                      make_planner, run_gpu, x0_of)
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def aero():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2509_17340_gb300 import build
+    build.build()
+    from paper_2509_17340_gb300 import aero as A
+    return A
+
+
+@pytest.fixture(scope="module")
+def planner(aero):
+    pl = make_planner(aero)
+    yield pl
+    pl.close()
+
+
+# ----------------------------------------------------------------- cases
+
+def _case(name):
+    if name == "plain":
+        w = I.make_workload("plain")
+    elif name == "ensemble":
+        w = I.make_workload("ensemble")
+    elif name == "ensemble_small":
+        w = I.make_workload("ensemble")
+        w.params.update(K=256, T=16)
+    elif name == "ragged":
+        w = I.make_workload("plain", seed=3)
+        rng = np.random.default_rng(3)
+        w.q0 = I.random_unit_quaternion(rng)
+        w.v0 = np.array([1.5, -0.7, 0.3], np.float32)
+        w.p0 = np.array([0.3, 0.2, 1.6], np.float32)
+        w.params.update(E=2, M_h=2, M_v=1, K=200, T=7, iters=2, Q_track=15.0, step_id=77,
+                        seed=0xDEADBEEF12345)
+    elif name == "raw":
+        w = I.make_workload("ensemble")
+        w.params.update(K=128, T=10, collision_set=1)
+    elif name == "empty":
+        w = I.make_workload("plain")
+        w.cloud = np.zeros((0, 3), np.float32)
+        w.params.update(E=3, M_h=3, M_v=1, K=64, T=12)
+    else:
+        raise KeyError(name)
+    w.params["debug_samples"] = 8
+    return w
+
+
+CASES = ["plain", "ensemble_small", "ensemble", "ragged", "raw", "empty"]
+
+
+@pytest.fixture(scope="module")
+def results(aero, planner, orc):
+    cache = {}
+
+    def get(name):
+        if name not in cache:
+            w = _case(name)
+            u0 = w.hover_nominal()
+            g = run_gpu(aero, planner, w, w.params, u0)
+            o = orc.plan_step(w.cloud, w.p0, w.q0, w.v0, w.goal, w.params, u0)
+            cache[name] = (w, u0, g, o)
+        return cache[name]
+
+    return get
+
+
+# ----------------------------------------------------------------- P1 Philox
+
+def test_philox_integers_bit_exact(aero, orc):
+    for seed, c1, c2, c3 in [(0, 0, 0, 0), (0x123456789ABCDEF, 7, 3, 0x4D01), (2**64 - 1, 2**32 - 1, 5, 9)]:
+        n = 3000
+        g = aero.philox(seed, c1, c2, c3, n)
+        key = [seed & 0xFFFFFFFF, seed >> 32]
+        for i in list(range(0, n, 37)) + [n - 1]:
+            assert np.array_equal(g[i], orc.philox([i, c1, c2, c3], key)), (seed, i)
+
+
+# ----------------------------------------------------------------- P3 partition and indices
+
+@pytest.mark.parametrize("name", CASES)
+def test_partition_keys_bit_exact(results, orc, name):
+    w, u0, g, o = results(name)
+    assert np.array_equal(g["keys"], o["keys"])
+
+
+@pytest.mark.parametrize("name", CASES)
+def test_coarse_goal_and_anchor_cells_bit_exact(results, orc, name):
+    w, u0, g, o = results(name)
+    P = w.params
+    win, _ = orc.coarse(o["keys"], P)
+    assert np.array_equal(g["coarse"], win)
+    gc = orc.goal_fine_cell(w.goal, w.p0, w.q0, P)
+    assert g["goal_cell"] == gc
+    assert np.array_equal(g["anchor_cells"], orc.anchor_cells(gc, P))
+
+
+# ----------------------------------------------------------------- P4 anchors and guides
+
+@pytest.mark.parametrize("name", CASES)
+def test_anchors_and_guides(results, name):
+    w, u0, g, o = results(name)
+    assert np.abs(g["anchors"] - o["anchors"]).max() < TOL_POS
+    assert np.abs(g["guides"] - o["guides"]).max() < TOL_POS
+
+
+# ----------------------------------------------------------------- collision grid
+
+@pytest.mark.parametrize("name", CASES)
+def test_grid_holds_the_collision_set(results, planner, orc, name):
+    w, u0, g, o = results(name)
+    # the planner's debug buffers hold the last step: rerun this case
+    import paper_2509_17340_gb300.aero as A
+    run_gpu(A, planner, w, w.params, u0, debug=False)
+    meta = planner.debug("GRID_META")
+    G, n_items = int(meta[0]), int(meta[1])
+    origin, h = meta[4:6].view(np.float32)
+    start = planner.debug("GRID_START")
+    pts = planner.debug("GRID_POINTS")
+    ref = orc.collision_set(w.cloud, w.p0, w.q0, o["keys"], w.params)
+    assert n_items == len(ref) == len(pts) == start[-1]
+    assert np.all(np.diff(start) >= 0) and start[0] == 0
+    # same multiset of points (binary32 offsets from p0)
+    rel = (ref.astype(np.float32) - w.p0).astype(np.float32)
+    key = lambda a: np.lexsort((a[:, 2], a[:, 1], a[:, 0]))
+    assert np.array_equal(rel[key(rel)], pts[:, :3][key(pts[:, :3])])
+    # every point sits in the cell its coordinates give
+    for c in range(G ** 3):
+        s, e = start[c], start[c + 1]
+        if s == e:
+            continue
+        cz, cy, cx = c // (G * G), (c // G) % G, c % G
+        f = np.floor((pts[s:e, :3] - origin) * np.float32(1.0 / h)).astype(np.int64)
+        f = np.clip(f, 0, G - 1)
+        assert np.all(f[:, 0] == cx) and np.all(f[:, 1] == cy) and np.all(f[:, 2] == cz)
+
+
+# ----------------------------------------------------------------- P2 / P5 sampled rollouts
+
+@pytest.mark.parametrize("name", CASES)
+def test_sample_perturbations_and_rollouts(results, orc, name):
+    w, u0, g, o = results(name)
+    P = w.params
+    E, T = P["E"], P["T"]
+    D = g["sU"].shape[1]
+    lo, hi = np.array(P["u_min"]), np.array(P["u_max"])
+    if P["iters"] != 1:
+        pytest.skip("sample debug buffers hold the last iteration")
+    x0 = x0_of(w)
+    for e in range(E):
+        d = orc.noise_range(P, e, 0, D)
+        u_ref = np.clip(u0[e].astype(np.float64) + d, lo, hi)
+        assert np.abs(g["sU"][e] - u_ref).max() < TOL_DELTA
+        for k in range(D):
+            X = orc.rollout(x0, g["sU"][e, k], P["dt"], P["mass"], P["g"])
+            Xg = g["sX"][e, k]
+            assert np.abs(Xg[:, :3] - X[:, :3]).max() < TOL_POS
+            assert np.abs(Xg[:, 3:7] - X[:, 3:7]).max() < TOL_QUAT
+            assert np.abs(Xg[:, 7:] - X[:, 7:]).max() < TOL_VEL
+
+
+def _oracle_pts(orc, w, o):
+    return orc.collision_set(w.cloud, w.p0, w.q0, o["keys"], w.params)
+
+
+@pytest.mark.parametrize("name", CASES)
+def test_sample_distances(results, orc, name):
+    """d_t of the recorded samples against brute force on the GPU's own states."""
+    w, u0, g, o = results(name)
+    P = w.params
+    pts = _oracle_pts(orc, w, o)
+    dmax = P["d_max"]
+    for e in range(P["E"]):
+        for k in range(g["sX"].shape[1]):
+            for j in range(P["T"]):
+                d = orc.nn_dist(g["sX"][e, k, j + 1, :3], pts)
+                dg = g["sD"][e, k, j]
+                if d < dmax - JUMP_BAND:
+                    assert abs(dg - d) < 1e-4
+                elif d > dmax + JUMP_BAND:
+                    assert dg == math.inf
+
+
+# ----------------------------------------------------------------- P6 per-sample costs
+
+def _oracle_sample(orc, w, P, u0e, e, k, guide, pts):
+    lo, hi = np.array(P["u_min"]), np.array(P["u_max"])
+    d = orc.noise_range(P, e, k, 1)[0]
+    U = np.clip(u0e + d, lo, hi)
+    X = orc.rollout(x0_of(w), U, P["dt"], P["mass"], P["g"])
+    t = orc.cost_terms(X, U, guide, w.goal.astype(np.float64), pts, P, stage=1, want_dist=True)
+    jump = np.min(np.minimum(np.abs(t["dist"] - P["d_min"]), np.abs(t["dist"] - P["d_max"])))
+    return t["S"], jump
+
+
+@pytest.mark.parametrize("name", CASES)
+def test_sample_costs(results, orc, name):
+    w, u0, g, o = results(name)
+    P = w.params
+    if P["iters"] != 1:
+        pytest.skip("sample costs hold the last iteration")
+    pts = _oracle_pts(orc, w, o)
+    E, K = P["E"], P["K"]
+    ks = range(K) if E * K <= 2048 else range(0, K, max(1, (E * K) // 2048))
+    n_cmp = n_jump = 0
+    for e in range(E):
+        for k in ks:
+            S, jump = _oracle_sample(orc, w, P, u0[e].astype(np.float64), e, k, o["guides"][e], pts)
+            assert abs(S - o["S1"][e, k]) <= 1e-9 * abs(S)   # oracle self-consistency
+            if jump < JUMP_BAND:
+                n_jump += 1
+                continue
+            n_cmp += 1
+            assert abs(g["S1"][e, k] - S) <= TOL_COST_REL * abs(S), (e, k, g["S1"][e, k], S)
+    assert n_cmp > 0 and n_jump <= max(2, n_cmp // 100)
+
+
+# ----------------------------------------------------------------- P7 update from the GPU costs
+
+@pytest.mark.parametrize("name", CASES)
+def test_update_from_gpu_costs(results, orc, name):
+    w, u0, g, o = results(name)
+    P = w.params
+    if P["iters"] != 1:
+        pytest.skip("single-iteration protocol")
+    lo, hi = np.array(P["u_min"]), np.array(P["u_max"])
+    for e in range(P["E"]):
+        d = orc.noise_range(P, e, 0, P["K"])
+        un0 = u0[e].astype(np.float64)
+        dU = np.clip(un0 + d, lo, hi) - un0
+        u_ref, _ = orc.mppi_update(g["S1"][e], dU.reshape(P["K"], -1), P["lam"], un0)
+        assert np.abs(g["u_nom"][e] - u_ref).max() < TOL_U
+
+
+# ----------------------------------------------------------------- end to end and Stage II
+
+@pytest.mark.parametrize("name", CASES)
+def test_end_to_end_nominal_and_selection(results, orc, name):
+    """End to end, the weights (Eq. mppi_weights) amplify the FP32 cost error
+    dS by 1/lambda: to first order u_gpu - u_orc = sum_k eps_k (mean_eps(dS) -
+    dS_k) / lambda du_k.  The GPU nominal must equal the oracle's plus this
+    predicted shift within TOL_U, with dS the measured per-sample cost error."""
+    w, u0, g, o = results(name)
+    P = w.params
+    if P["iters"] == 1:
+        lo, hi = np.array(P["u_min"]), np.array(P["u_max"])
+        lam = P["lam"]
+        for e in range(P["E"]):
+            d = orc.noise_range(P, e, 0, P["K"])
+            un0 = u0[e].astype(np.float64)
+            dU = (np.clip(un0 + d, lo, hi) - un0).reshape(P["K"], -1)
+            S = o["S1"][e]
+            eps = np.exp(-(S - S.min()) / lam)
+            eps /= eps.sum()
+            dS = g["S1"][e] - S
+            shift = (eps * (eps @ dS - dS) / lam) @ dU
+            pred = o["u_nom"][e].reshape(-1) + shift
+            assert np.abs(g["u_nom"][e].reshape(-1) - pred).max() < TOL_U, e
+    else:
+        assert np.abs(g["u_nom"] - o["u_nom"]).max() < TOL_U
+    assert np.all(np.abs(g["cand"] - o["cand"]) <= TOL_COST_REL * np.abs(o["cand"]))
+    c = np.sort(o["cand"])
+    if len(c) > 1 and (c[1] - c[0]) < TOL_COST_REL * abs(c[0]):
+        assert o["cand"][g["best"]] <= c[0] * (1 + TOL_COST_REL)
+    else:
+        assert g["best"] == o["best"]
+    assert np.array_equal(g["u_best"], g["u_nom"][g["best"]].astype(np.float32))
+
+
+@pytest.mark.parametrize("name", CASES)
+def test_stage2_rollouts_and_costs(results, orc, name):
+    w, u0, g, o = results(name)
+    P = w.params
+    pts = _oracle_pts(orc, w, o)
+    x0 = x0_of(w)
+    for e in range(P["E"]):
+        X = orc.rollout(x0, g["u_nom"][e], P["dt"], P["mass"], P["g"])
+        assert np.abs(g["X2"][e, :, :3] - X[:, :3]).max() < TOL_POS
+        assert np.abs(g["X2"][e, :, 3:7] - X[:, 3:7]).max() < TOL_QUAT
+        t = orc.cost_terms(X, g["u_nom"][e], None, w.goal.astype(np.float64), pts, P, stage=2,
+                           want_dist=True)
+        jump = np.min(np.minimum(np.abs(t["dist"] - P["d_min"]), np.abs(t["dist"] - P["d_max"])))
+        if jump > JUMP_BAND:
+            assert abs(g["cand"][e] - t["S"]) <= TOL_COST_REL * abs(t["S"])
+    cand = g["cand"]
+    assert g["best"] == int(np.argmin(cand))
+
+
+# ----------------------------------------------------------------- API behaviour
+
+def test_repeatable_bitwise(aero, planner):
+    w = _case("ensemble_small")
+    u0 = w.hover_nominal()
+    a = run_gpu(aero, planner, w, w.params, u0, debug=False)
+    b = run_gpu(aero, planner, w, w.params, u0, debug=False)
+    assert np.array_equal(a["u_nom"], b["u_nom"]) and np.array_equal(a["cand"], b["cand"])
+
+
+def test_host_api_matches_device_api(aero, planner):
+    import torch
+    w = _case("plain")
+    P = w.params
+    u0 = w.hover_nominal()
+    a = run_gpu(aero, planner, w, P, u0, debug=False)
+    cloud = torch.from_numpy(w.cloud).pin_memory()
+    un = torch.from_numpy(u0.copy()).pin_memory()
+    ub = torch.zeros((P["T"], 4)).pin_memory()
+    cand = torch.zeros(P["E"]).pin_memory()
+    best = torch.zeros(1, dtype=torch.int32).pin_memory()
+    planner.plan_step_host(aero.state_struct(w.p0, w.q0, w.v0), cloud, w.goal, aero.params_struct(P),
+                           un, ub, cand, best)
+    assert np.array_equal(un.numpy().astype(np.float64), a["u_nom"])
+    assert np.array_equal(cand.numpy(), a["cand"]) and int(best[0]) == a["best"]
+    assert np.array_equal(ub.numpy(), a["u_best"])
+
+
+def test_invalid_arguments_rejected(aero, planner):
+    import torch
+    w = _case("plain")
+    P = dict(w.params)
+    u0 = torch.from_numpy(w.hover_nominal()).cuda()
+    cloud = torch.from_numpy(w.cloud).cuda()
+    bad = [dict(P, E=2), dict(P, fine_az=121), dict(P, pool_az=7), dict(P, lam=0.0),
+           dict(P, d_min=2.0), dict(P, iters=0), dict(P, K=0)]
+    for q in bad:
+        with pytest.raises(aero.AeroError) as ei:
+            aero.plan_step(planner, w.p0, w.q0, w.v0, cloud, w.goal, q, u0)
+        assert ei.value.code == aero.ERR_INVALID_ARG, q
+    with pytest.raises(aero.AeroError) as ei:
+        aero.plan_step(planner, w.p0, w.q0, w.v0, cloud, w.goal, dict(P, K=1 << 16), u0)
+    assert ei.value.code == aero.ERR_EXCEEDS_LIMITS
+    # a pinned host buffer where device memory is required
+    import ctypes as C
+    h = torch.from_numpy(w.cloud).pin_memory()
+    rc = aero.lib().aero_plan_step(planner.handle, C.byref(aero.state_struct(w.p0, w.q0, w.v0)),
+                                   h.data_ptr(), h.shape[0], (C.c_float * 3)(*w.goal.tolist()),
+                                   C.byref(aero.params_struct(P)), u0.data_ptr(),
+                                   torch.zeros((P["T"], 4)).cuda().data_ptr(),
+                                   torch.zeros(1).cuda().data_ptr(),
+                                   torch.zeros(1, dtype=torch.int32).cuda().data_ptr(), None)
+    assert rc == aero.ERR_NOT_DEVICE_PTR
+
+
+# ----------------------------------------------------------------- full-size large clutter, sampled
+
+def test_large_clutter_sampled(aero, orc):
+    """200k-point clutter, E=32, K=8192, T=64 (the launch shape the benchmark
+    uses for its largest workload): indices bit-exact, sampled costs, the update
+    of two instances from the GPU costs, Stage II of all instances."""
+    w = I.make_workload("large")
+    P = w.params
+    P["debug_samples"] = 4
+    pl = make_planner(aero, E=32, K=8192, T=64, cells=256 * 64, n=200_000, D=4)
+    u0 = w.hover_nominal()
+    g = run_gpu(aero, pl, w, P, u0)
+    pl.close()
+    keys, _ = orc.partition(w.cloud, w.p0, w.q0, P)
+    assert np.array_equal(g["keys"], keys)
+    win, _ = orc.coarse(keys, P)
+    assert np.array_equal(g["coarse"], win)
+    gc = orc.goal_fine_cell(w.goal, w.p0, w.q0, P)
+    assert g["goal_cell"] == gc and np.array_equal(g["anchor_cells"], orc.anchor_cells(gc, P))
+    pts = orc.collision_set(w.cloud, w.p0, w.q0, keys, P)
+    x0 = x0_of(w)
+    rng = np.random.default_rng(0)
+    lo, hi = np.array(P["u_min"]), np.array(P["u_max"])
+    guides = np.zeros((P["E"], P["T"], 3))
+    for e in range(P["E"]):
+        d = orc.cell_direction(P, int(win[g["anchor_cells"][e]]))
+        pref = orc.anchor(x0[:3], x0[3:7], d, P["ell"])
+        assert np.abs(g["anchors"][e] - pref).max() < TOL_POS
+        _, guides[e] = orc.guide(x0[:3], x0[7:], pref, P)
+        assert np.abs(g["guides"][e] - guides[e]).max() < TOL_POS
+    n_cmp = 0
+    for _ in range(48):
+        e, k = int(rng.integers(P["E"])), int(rng.integers(P["K"]))
+        S, jump = _oracle_sample(orc, w, P, u0[e].astype(np.float64), e, k, guides[e], pts)
+        if jump < JUMP_BAND:
+            continue
+        n_cmp += 1
+        assert abs(g["S1"][e, k] - S) <= TOL_COST_REL * abs(S), (e, k)
+    assert n_cmp >= 40
+    for e in (0, P["E"] - 1):
+        d = orc.noise_range(P, e, 0, P["K"])
+        un0 = u0[e].astype(np.float64)
+        dU = np.clip(un0 + d, lo, hi) - un0
+        u_ref, _ = orc.mppi_update(g["S1"][e], dU.reshape(P["K"], -1), P["lam"], un0)
+        assert np.abs(g["u_nom"][e] - u_ref).max() < TOL_U
+    for e in range(P["E"]):
+        X = orc.rollout(x0, g["u_nom"][e], P["dt"], P["mass"], P["g"])
+        assert np.abs(g["X2"][e, :, :3] - X[:, :3]).max() < TOL_POS
+    assert g["best"] == int(np.argmin(g["cand"]))
