@@ -173,6 +173,29 @@ int aero_plan_step_host(aero_planner_t* planner, const aero_state_t* x0, const f
                         float* u_nom_inout, float* u_best_out, float* cand_costs_out,
                         int32_t* best_idx_out, void* stream);
 
+/* The planning step of aero_plan_step for callers that cannot allocate device
+ * memory while running (no counterpart in the paper: an engineering addition).
+ * A flight-control loop must not block on cudaMalloc, which can synchronise
+ * the device and take an unbounded time, and some host programs own all device
+ * memory through their own pool; aero_create allocates, so they call this
+ * instead.  No planner is needed and nothing is allocated: the workspace is a
+ * fixed file-scope device array of about 2.3 MB that every GPU loading this
+ * library keeps until the process exits.
+ *   Limits: E <= 16, K <= 2048, T <= 64, fine_az * fine_el <= 8192,
+ *   n_points <= 65536, collision grid <= 32^3 cells (about r_max <= 14.5 d_max),
+ *   debug_samples == 0.  Larger requests return AERO_ERR_EXCEEDS_LIMITS.
+ *   Arguments are those of aero_plan_step (same layout, ownership and errors);
+ *   there are no debug buffers.
+ *   The first call on a device looks up the array's device address (once per
+ *   device, with that device current); make that first call before any stream
+ *   capture.  All calls share the array, which keeps the last call's contents:
+ *   calls whose work overlaps on the GPU (other streams, other host threads)
+ *   race on it, so order them on one stream. */
+int aero_plan_step_noalloc(const aero_state_t* x0, const float* cloud_xyz, int64_t n_points,
+                           const float goal[3], const aero_params_t* params, float* u_nom_inout,
+                           float* u_best_out, float* cand_costs_out, int32_t* best_idx_out,
+                           void* stream);
+
 /* Bytes of debug buffer `what` (AERO_DBG_*) for the last step; 0 if unknown. */
 size_t aero_debug_size(aero_planner_t* planner, int32_t what);
 

@@ -70,6 +70,8 @@ _lib.aero_destroy.argtypes = [_vp]
 _lib.aero_plan_step.argtypes = [_vp, C.POINTER(State), _vp, C.c_int64, C.POINTER(C.c_float),
                                 C.POINTER(Params), _vp, _vp, _vp, _vp, _vp]
 _lib.aero_plan_step_host.argtypes = _lib.aero_plan_step.argtypes
+_lib.aero_plan_step_noalloc.argtypes = [C.POINTER(State), _vp, C.c_int64, C.POINTER(C.c_float),
+                                        C.POINTER(Params), _vp, _vp, _vp, _vp, _vp]
 _lib.aero_debug_size.argtypes = [_vp, C.c_int32]
 _lib.aero_debug_size.restype = C.c_size_t
 _lib.aero_get_debug.argtypes = [_vp, C.c_int32, _vp, C.c_size_t, _vp]
@@ -242,6 +244,23 @@ class Planner:
 
     def sync_status(self, stream=None) -> int:
         return _lib.aero_sync_status(self._h, _stream_ptr(stream))
+
+
+def plan_step_noalloc(state: State, cloud: torch.Tensor, goal, params: Params, u_nom: torch.Tensor,
+                      u_best: torch.Tensor, cand: torch.Tensor, best_idx: torch.Tensor,
+                      stream=None) -> None:
+    """The planning step without a planner and without allocating device memory
+    (for callers that cannot allocate while running; see aero_plan_step_noalloc
+    in include/aero_mppi.h for its limits).  u_nom is updated in place."""
+    n = cloud.shape[0] if cloud is not None else 0
+    cptr = _dev(cloud, torch.float32, "cloud") if n > 0 else None
+    g = (C.c_float * 3)(*[float(x) for x in goal])
+    rc = _lib.aero_plan_step_noalloc(C.byref(state), cptr, n, g, C.byref(params),
+                                     _dev(u_nom, torch.float32, "u_nom"),
+                                     _dev(u_best, torch.float32, "u_best"),
+                                     _dev(cand, torch.float32, "cand"),
+                                     _dev(best_idx, torch.int32, "best_idx"), _stream_ptr(stream))
+    _check(rc, "aero_plan_step_noalloc")
 
 
 def philox(seed: int, c1: int, c2: int, c3: int, n: int) -> np.ndarray:

@@ -7,6 +7,7 @@
 #include <cstdint>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -695,6 +696,121 @@ const char* aero_status_str(int status) {
     case AERO_ERR_NOT_DEVICE_PTR: return "pointer is not device memory";
     default: return "unknown status";
   }
+}
+
+// ---------------------------------------------------------------------------
+// Planning step without any allocation.
+//
+// Some callers cannot call cudaMalloc once they are running: a flight-control
+// loop that must not block (an allocation can synchronise the device and take
+// an unbounded time), or a host program whose device memory is all owned by its
+// own pool or fixed at start-up.  aero_create allocates the planner workspace,
+// so such callers use aero_plan_step_noalloc instead: its workspace is carved
+// from g_noalloc_scratch, a file-scope device array that the CUDA loader sets
+// up with the module and that every GPU loading this library keeps until the
+// process exits.  Its size is fixed by the kNa* limits below (about 2.3 MB).
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr int kNaE = 16, kNaK = 2048, kNaT = 64, kNaCells = 128 * 64;
+constexpr int64_t kNaPoints = 65536;
+constexpr int kNaGridCells = 32 * 32 * 32;
+constexpr int kNaNb = (kNaK + kRolloutThreads - 1) / kRolloutThreads;
+
+constexpr size_t align256(size_t b) { return (b + 255) / 256 * 256; }
+constexpr size_t kNaItems = kNaPoints > kNaCells ? kNaPoints : kNaCells;
+constexpr size_t kNaBytes =
+    align256(8 * (size_t)kNaCells) + align256(4 * (size_t)kNaCells) + align256(4 * (kNaE + 1)) +
+    align256(4 * 3 * kNaE) + align256(4 * 3 * (size_t)kNaE * kNaT) + 2 * align256(4 * kNaItems) +
+    align256(4 * ((size_t)kNaGridCells + 1)) + align256(16 * kNaItems) +
+    align256(4 * (size_t)kNaE * kNaNb * (2 + 4 * kNaT)) + align256(4 * (size_t)kNaE * kNaK) +
+    align256(4 * (size_t)kNaE * (kNaT + 1) * 10) + align256(4) + align256(4);
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNaBytes];
+
+struct NoAllocDevice {
+  bool ready = false;
+  unsigned char* base = nullptr;
+};
+NoAllocDevice g_na_dev[64];
+std::mutex g_na_mutex;
+
+// Device address of the scratch array on the current device, looked up once
+// per device (host code must not use the symbol itself as an address).
+int noalloc_base(unsigned char** out) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return AERO_ERR_CUDA;
+  std::lock_guard<std::mutex> lock(g_na_mutex);
+  NoAllocDevice& d = g_na_dev[dev];
+  if (!d.ready) {
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || p == nullptr) {
+      cudaGetLastError();
+      return AERO_ERR_CUDA;
+    }
+    d.base = static_cast<unsigned char*>(p);
+    d.ready = true;
+  }
+  *out = d.base;
+  return AERO_OK;
+}
+
+// Point the planner's workspace fields into the scratch array.
+void noalloc_carve(unsigned char* base, aero_planner& pl) {
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    unsigned char* p = base + off;
+    off += align256(bytes);
+    return p;
+  };
+  pl.keys = reinterpret_cast<unsigned long long*>(take(8 * (size_t)kNaCells));
+  pl.coarse_win = reinterpret_cast<int*>(take(4 * (size_t)kNaCells));
+  pl.cells = reinterpret_cast<int*>(take(4 * (kNaE + 1)));
+  pl.anchors = reinterpret_cast<float*>(take(4 * 3 * kNaE));
+  pl.guides = reinterpret_cast<float*>(take(4 * 3 * (size_t)kNaE * kNaT));
+  pl.item_cell = reinterpret_cast<int*>(take(4 * kNaItems));
+  pl.item_slot = reinterpret_cast<int*>(take(4 * kNaItems));
+  pl.grid_start = reinterpret_cast<int*>(take(4 * ((size_t)kNaGridCells + 1)));
+  pl.grid_pts = reinterpret_cast<float4*>(take(16 * kNaItems));
+  pl.partials = reinterpret_cast<float*>(take(4 * (size_t)kNaE * kNaNb * (2 + 4 * kNaT)));
+  pl.sample_costs = reinterpret_cast<float*>(take(4 * (size_t)kNaE * kNaK));
+  pl.stage2_x = reinterpret_cast<float*>(take(4 * (size_t)kNaE * (kNaT + 1) * 10));
+  pl.counter = reinterpret_cast<unsigned int*>(take(4));
+  pl.status = reinterpret_cast<int*>(take(4));
+}
+
+}  // namespace
+
+int aero_plan_step_noalloc(const aero_state_t* x0, const float* cloud, int64_t n,
+                           const float goal[3], const aero_params_t* params, float* u_nom,
+                           float* u_best, float* cand, int32_t* best_idx, void* stream) {
+  if (!x0 || !goal || !params || !u_nom || !u_best || !cand || !best_idx) return AERO_ERR_INVALID_ARG;
+  if (n > 0 && !cloud) return AERO_ERR_INVALID_ARG;
+  aero_planner pl;  // host-side bookkeeping only; no device memory is allocated
+  pl.lim.E_max = kNaE;
+  pl.lim.K_max = kNaK;
+  pl.lim.T_max = kNaT;
+  pl.lim.fine_cells_max = kNaCells;
+  pl.lim.n_points_max = kNaPoints;
+  pl.lim.debug_samples_max = 0;
+  int rc = validate(&pl, params, n);
+  if (rc != AERO_OK) return rc;
+  const GridGeom g = make_grid(*params);
+  if ((int64_t)g.G * g.G * g.G > kNaGridCells) return AERO_ERR_EXCEEDS_LIMITS;
+  if (reinterpret_cast<uintptr_t>(u_nom) % 16 != 0) return AERO_ERR_INVALID_ARG;
+  if ((n > 0 && !is_device_ptr(cloud)) || !is_device_ptr(u_nom) || !is_device_ptr(u_best) ||
+      !is_device_ptr(cand) || !is_device_ptr(best_idx))
+    return AERO_ERR_NOT_DEVICE_PTR;
+  unsigned char* base = nullptr;
+  rc = noalloc_base(&base);
+  if (rc != AERO_OK) return rc;
+  noalloc_carve(base, pl);
+  cudaStream_t s = (cudaStream_t)stream;
+  // the selection ticket and the status word must start at zero
+  cudaError_t e = cudaMemsetAsync(pl.counter, 0, sizeof(unsigned int), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(pl.status, 0, sizeof(int), s);
+  if (e != cudaSuccess) return AERO_ERR_CUDA;
+  return enqueue_step(&pl, x0, cloud, n, goal, *params, u_nom, u_best, cand, best_idx, s);
 }
 
 }  // extern "C"
