@@ -9,6 +9,8 @@ ensemble (E=8, K=1024, T=40, forest LiDAR sweep).
 Metric: rollout-steps per second = (E K T iters + E T) / step time.  Each timed
 step is bracketed by CUDA events on the planner's stream; L2 (129 MB) is
 flushed by writing a 512 MB buffer between timed steps, outside the events.
+Every step plans from the same state and hover warm start (a fresh Philox
+step_id each time), so the timed work does not drift with the step index.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
@@ -37,6 +39,8 @@ from paper_2509_17340_gb300 import inputs as I  # noqa: E402
 
 WORKLOAD = "ensemble"
 METRIC = "rollout-steps/s (anchor-guided ensemble plan step)"
+METRICS = {"ensemble": METRIC, "large": "rollout-steps/s (large-clutter ensemble plan step)",
+           "plain": "rollout-steps/s (plain single-MPPI plan step)"}
 UNIT = "rollout-steps/s"
 CPU_SAMPLE_SECONDS = 15.0
 
@@ -58,6 +62,11 @@ def rollout_flops_per_step() -> int:
       second pass for the update: noise 16 + clamp 12 + 4 products ... 32
     """
     return 16 + 12 + 226 + 13 + 69 + 4 + 32
+
+
+def set_workload(name: str) -> None:
+    global WORKLOAD, METRIC
+    WORKLOAD, METRIC = name, METRICS[name]
 
 
 def env_int(name, default):
@@ -216,7 +225,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default=WORKLOAD, choices=sorted(METRICS))
     args = ap.parse_args()
+    set_workload(args.workload)
 
     rank, world = env_int("RANK", 0), env_int("WORLD_SIZE", 1)
     local = env_int("LOCAL_RANK", 0)
@@ -256,6 +267,7 @@ def main():
     with torch.cuda.stream(stream):
         for s in range(args.warmup):
             flush.fill_(float(s))
+            u_nom.copy_(u0)
             step(s)
         torch.cuda.synchronize()
         pl.profile_read()  # discard warm-up stage times
@@ -268,6 +280,7 @@ def main():
         with ClockSampler(local) as clk:
             for i in range(args.steps):
                 flush.fill_(float(i))
+                u_nom.copy_(u0)   # every step plans from the same warm start
                 ev[i][0].record(stream)
                 step(args.warmup + i)
                 ev[i][1].record(stream)
@@ -300,6 +313,7 @@ def main():
             with torch.cuda.stream(stream):
                 flush.fill_(float(i))
             stream.synchronize()
+            hu.copy_(torch.from_numpy(w.hover_nominal()))
             P["step_id"] = 10_000 + i
             t0 = time.perf_counter()
             pl.plan_step_host(state, hc, w.goal, aero.params_struct(P), hu, hb, hcand, hbest, stream)

@@ -65,9 +65,12 @@ extern "C" {
 #define AERO_DBG_ANCHOR_CELLS 3  /* int32 [E]: coarse cell J*A_c+I of instance e = n*M_h+m */
 #define AERO_DBG_ANCHORS 4       /* float [E][3]: anchor - p0 */
 #define AERO_DBG_GUIDES 5        /* float [E][T][3]: guide at t=(j+1)dt, minus p0 */
-#define AERO_DBG_GRID_META 6     /* int32 [4] = {G, n_items, 0, 0} then float [4] = {origin, h, 0, 0} */
-#define AERO_DBG_GRID_START 7    /* int32 [G*G*G + 1]: first point of cell (z*G+y)*G+x */
-#define AERO_DBG_GRID_POINTS 8   /* float4 [n_items]: collision points - p0, sorted by cell */
+#define AERO_DBG_GRID_META 6     /* int32 [4] = {G, n_entries, capacity, 0} then float [4] =
+                                    {origin, h, reach, 0}: G^3 cells of edge h from origin
+                                    (all axes); cell c lists every collision point closer
+                                    than reach (>= d_max) to its box */
+#define AERO_DBG_GRID_START 7    /* int32 [G*G*G + 1]: first entry of cell (z*G+y)*G+x */
+#define AERO_DBG_GRID_POINTS 8   /* float4 [n_entries]: candidate points - p0, grouped by cell */
 #define AERO_DBG_SAMPLE_COSTS 9  /* float [E][K]: S(1) of every sample, last iteration */
 #define AERO_DBG_STAGE2_STATES 10 /* float [E][T+1][10]: Stage II states (p - p0, q, v) */
 #define AERO_DBG_SAMPLE_U 11     /* float [E][D][T][4]: clamped controls of samples k < D */
@@ -179,11 +182,12 @@ int aero_plan_step_host(aero_planner_t* planner, const aero_state_t* x0, const f
  * the device and take an unbounded time, and some host programs own all device
  * memory through their own pool; aero_create allocates, so they call this
  * instead.  No planner is needed and nothing is allocated: the workspace is a
- * fixed file-scope device array of about 2.3 MB that every GPU loading this
+ * fixed file-scope device array of about 6.5 MB that every GPU loading this
  * library keeps until the process exits.
  *   Limits: E <= 16, K <= 2048, T <= 64, fine_az * fine_el <= 8192,
- *   n_points <= 65536, collision grid <= 32^3 cells (about r_max <= 14.5 d_max),
- *   debug_samples == 0.  Larger requests return AERO_ERR_EXCEEDS_LIMITS.
+ *   n_points <= 65536, collision_set == 0 (P_f), debug_samples == 0; the
+ *   collision grid has at most 32^3 cells (coarser cells for a large r_max, which
+ *   keeps the distances exact).  Larger requests return AERO_ERR_EXCEEDS_LIMITS.
  *   Arguments are those of aero_plan_step (same layout, ownership and errors);
  *   there are no debug buffers.
  *   The first call on a device looks up the array's device address (once per

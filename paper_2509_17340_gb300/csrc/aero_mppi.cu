@@ -25,12 +25,17 @@ struct aero_planner {
   int* cells = nullptr;       // [0] goal fine cell, [1 + e] anchor coarse cell
   float* anchors = nullptr;
   float* guides = nullptr;
-  int* item_cell = nullptr;
-  int* item_slot = nullptr;
-  int* grid_start = nullptr;
-  float4* grid_pts = nullptr;
+  int* item_flag = nullptr;   // per point: kept by the partition (collision set = kept points)
+  int* grid_count = nullptr;  // G^3 + 1 candidate counts, then fill cursors
+  int* grid_local = nullptr;  // G^3 + 1 tile-local exclusive prefix
+  int* tile_sum = nullptr;
+  int* tile_off = nullptr;
+  float4* cand = nullptr;     // candidate entries
+  int cand_cap = 0;
+  int grid_max = kGridMax;    // cells per axis the grid arrays can hold
   float* partials = nullptr;
   float* sample_costs = nullptr;
+  float4* dU = nullptr;       // sampled perturbations, when the planner is small enough
   float* stage2_x = nullptr;
   unsigned int* counter = nullptr;
   int* status = nullptr;
@@ -47,9 +52,8 @@ struct aero_planner {
   bool have_step = false;
   aero_params_t last{};
   GridGeom last_grid{};
-  int64_t last_items = 0;
+  int last_ntiles = 0;
   int last_nb = 0;
-  int64_t item_cap = 0;
   // stage timing (aero_profile_enable / aero_profile_read)
   struct ProfSlot {
     std::vector<cudaEvent_t> ev;  // start, after partition, after grid, then 4 per iteration
@@ -66,6 +70,11 @@ struct aero_planner {
 namespace {
 
 constexpr int kGridCellsMax = kGridMax * kGridMax * kGridMax;
+constexpr int kMaxTiles = (kGridCellsMax + 1 + kScanTile - 1) / kScanTile;
+// A point joins the lists of the cells within `reach` (just above d_max) of it:
+// at most 6^3 cells of edge d_max / 2, at most 3^3 of edge d_max (1 + 1/16).
+constexpr int kFineDup = 216, kCoarseDup = 27;
+constexpr size_t kMaxStoredPerturbationBytes = size_t(2) << 30;
 
 int cuda_fail(cudaError_t e) {
   if (e == cudaSuccess) return AERO_OK;
@@ -115,18 +124,30 @@ void make_tables(const aero_params_t& p, PartTables& t, int& check_lo, int& chec
   check_hi = hi < M_PI / 2;
 }
 
-// Grid over [-r_max, r_max]^3 around p0 with one spare cell on every side.
-GridGeom make_grid(const aero_params_t& p) {
+// Candidate grid over [-E, E)^3 around p0, E = r_max + reach + h: every
+// collision point lies within r_max of p0, so queries outside the grid are
+// farther than d_max from all of them.  Cells of edge d_max / 2 when the
+// candidate array can hold 216 entries per collision item, else d_max (1 + 1/16);
+// never more than kGridMax cells per axis.  `margin` covers binary32 rounding
+// of the cell coordinates.
+GridGeom make_grid(const aero_params_t& p, int64_t n_items, int64_t cap, int gmax) {
   GridGeom g;
-  float h = p.d_max * kCellMargin;
-  const float hmin = 2.0f * p.r_max / (float)(kGridMax - 3);
-  if (h < hmin) h = hmin;
-  int G = (int)std::floor(2.0f * p.r_max / h) + 3;
-  if (G > kGridMax) G = kGridMax;
+  g.reach = p.d_max * (1.0f + 1e-3f) + 1e-4f;
+  float h = (int64_t)kFineDup * n_items <= cap ? 0.5f * p.d_max : p.d_max * 1.0625f;
+  float E = p.r_max + g.reach + h;
+  int G = (int)std::ceil(2.0f * E / h);
+  if (G > gmax) {
+    // coarser cells: E grows with h, so solve h = 2 (r_max + reach + h) / gmax
+    h = 2.0f * (p.r_max + g.reach) / ((float)gmax - 2.5f);
+    E = p.r_max + g.reach + h;
+    G = (int)std::ceil(2.0f * E / h);
+    if (G > gmax) G = gmax;
+  }
   g.G = G;
   g.h = h;
   g.inv_h = 1.0f / h;
-  g.origin = -(p.r_max + h);
+  g.origin = -E;
+  g.cap = (int)cap;
   return g;
 }
 
@@ -159,8 +180,9 @@ cudaError_t alloc(T** p, size_t count) {
 
 void free_all(aero_planner* pl) {
   void* ptrs[] = {pl->keys,     pl->coarse_win, pl->cells,        pl->anchors,  pl->guides,
-                  pl->item_cell, pl->item_slot, pl->grid_start,   pl->grid_pts, pl->partials,
-                  pl->sample_costs, pl->stage2_x, pl->counter,   pl->status,   pl->dbg_u,
+                  pl->item_flag, pl->grid_count, pl->grid_local, pl->tile_sum, pl->tile_off,
+                  pl->cand,     pl->partials,
+                  pl->sample_costs, pl->dU,      pl->stage2_x, pl->counter,   pl->status,   pl->dbg_u,
                   pl->dbg_x,    pl->dbg_d,      pl->stage_cloud,      pl->stage_unom,   pl->stage_ubest,
                   pl->stage_cand,   pl->stage_best};
   for (void* q : ptrs)
@@ -229,10 +251,11 @@ int enqueue_step(aero_planner* pl, const aero_state_t* x0, const float* cloud, i
   rot_f32(x0->q, R);
   const float rm = p.r_max;
   const float rmax2 = rm * rm;
-  const GridGeom grid = make_grid(p);
-  const int gcells = grid.G * grid.G * grid.G;
   const bool raw = p.collision_set == 1;
   const int64_t n_items = raw ? n : ncell;
+  const GridGeom grid = make_grid(p, n_items, pl->cand_cap, pl->grid_max);
+  const int gcells = grid.G * grid.G * grid.G;
+  const int ntiles = (gcells + 1 + kScanTile - 1) / kScanTile;
 
   cudaError_t e;
   aero_planner::ProfSlot* prof = prof_slot(pl, p.iters);
@@ -242,7 +265,7 @@ int enqueue_step(aero_planner* pl, const aero_state_t* x0, const float* cloud, i
   mark(0);
   if ((e = cudaMemsetAsync(pl->keys, 0xFF, sizeof(unsigned long long) * ncell, s)) != cudaSuccess)
     return cuda_fail(e);
-  if ((e = cudaMemsetAsync(pl->grid_start, 0, sizeof(int) * (gcells + 1), s)) != cudaSuccess)
+  if ((e = cudaMemsetAsync(pl->grid_count, 0, sizeof(int) * (gcells + 1), s)) != cudaSuccess)
     return cuda_fail(e);
 
   PartitionArgs pa{};
@@ -256,25 +279,33 @@ int enqueue_step(aero_planner* pl, const aero_state_t* x0, const float* cloud, i
   pa.check_lo = check_lo;
   pa.check_hi = check_hi;
   pa.keys = pl->keys;
-  pa.raw = raw;
-  pa.grid = grid;
-  pa.grid_count = pl->grid_start;
-  pa.item_cell = pl->item_cell;
-  pa.item_slot = pl->item_slot;
+  pa.item_flag = raw ? pl->item_flag : nullptr;
   if ((e = launch_partition(pa, tab, s)) != cudaSuccess) return cuda_fail(e);
   mark(1);
   if (prof) {
     prof->launches[AERO_STAGE_PARTITION] = n > 0 ? 1 : 0;
-    prof->launches[AERO_STAGE_GRID] = (raw ? 1 : 2) + (n_items > 0 ? 1 : 0);
+    prof->launches[AERO_STAGE_GRID] = 2 + (n_items > 0 ? 2 : 0);
     prof->launches[AERO_STAGE_ROLLOUT] = p.iters;
     prof->launches[AERO_STAGE_UPDATE] = p.iters;
   }
 
-  if (!raw) {
-    if ((e = launch_pf_count(pl->keys, ncell, cloud, x0->p, grid, pl->grid_start, pl->item_cell,
-                             pl->item_slot, s)) != cudaSuccess)
-      return cuda_fail(e);
-  }
+  CandArgs ca{};
+  ca.cloud = cloud;
+  for (int i = 0; i < 3; ++i) ca.p0[i] = x0->p[i];
+  ca.keys = pl->keys;
+  ca.item_flag = pl->item_flag;
+  ca.n_items = n_items;
+  ca.raw = raw;
+  ca.grid = grid;
+  ca.count = pl->grid_count;
+  ca.local = pl->grid_local;
+  ca.tile_off = pl->tile_off;
+  ca.cand = pl->cand;
+  ca.status = pl->status;
+  if ((e = launch_cand_count(ca, s)) != cudaSuccess) return cuda_fail(e);
+  if ((e = launch_scan_tiles(pl->grid_count, pl->grid_local, pl->tile_sum, gcells + 1, ntiles, s)) !=
+      cudaSuccess)
+    return cuda_fail(e);
 
   GuideArgs ga{};
   ga.keys = pl->keys;
@@ -301,21 +332,12 @@ int enqueue_step(aero_planner* pl, const aero_state_t* x0, const float* cloud, i
   ga.cells = pl->cells;
   ga.anchors = pl->anchors;
   ga.guides = pl->guides;
-  ga.grid_start = pl->grid_start;
-  ga.ncells = gcells;
+  ga.tile_sum = pl->tile_sum;
+  ga.tile_off = pl->tile_off;
+  ga.ntiles = ntiles;
   if ((e = launch_scan_guides(ga, tab, s)) != cudaSuccess) return cuda_fail(e);
 
-  ScatterArgs sa{};
-  sa.cloud = cloud;
-  for (int i = 0; i < 3; ++i) sa.p0[i] = x0->p[i];
-  sa.item_cell = pl->item_cell;
-  sa.item_slot = pl->item_slot;
-  sa.keys = pl->keys;
-  sa.n_items = n_items;
-  sa.raw = raw;
-  sa.grid_start = pl->grid_start;
-  sa.grid_pts = pl->grid_pts;
-  if ((e = launch_scatter(sa, s)) != cudaSuccess) return cuda_fail(e);
+  if ((e = launch_cand_scatter(ca, s)) != cudaSuccess) return cuda_fail(e);
   mark(2);
 
   CostParams cp{};
@@ -334,7 +356,7 @@ int enqueue_step(aero_planner* pl, const aero_state_t* x0, const float* cloud, i
   for (int i = 0; i < 3; ++i) cp.v_goal[i] = p.v_goal[i];
   for (int i = 0; i < 4; ++i) cp.q_goal[i] = p.q_goal[i];
   DynParams dp{p.dt, 1.0f / p.mass, p.g};
-  GridView gv{pl->grid_start, pl->grid_pts, grid.G, grid.origin, grid.inv_h};
+  GridView gv{pl->grid_local, pl->tile_off, pl->cand, grid.G, grid.cap, grid.origin, grid.inv_h};
   float x0v[10] = {0.0f, 0.0f, 0.0f, x0->q[0], x0->q[1], x0->q[2], x0->q[3],
                    x0->v[0], x0->v[1], x0->v[2]};
   const int nb = (p.K + kRolloutThreads - 1) / kRolloutThreads;
@@ -360,6 +382,7 @@ int enqueue_step(aero_planner* pl, const aero_state_t* x0, const float* cloud, i
   ra.grid = gv;
   ra.partials = pl->partials;
   ra.sample_costs = pl->sample_costs;
+  ra.dU = pl->dU;
   ra.dbg_D = p.debug_samples < p.K ? p.debug_samples : p.K;
   ra.dbg_u = pl->dbg_u;
   ra.dbg_x = pl->dbg_x;
@@ -397,7 +420,7 @@ int enqueue_step(aero_planner* pl, const aero_state_t* x0, const float* cloud, i
   pl->have_step = true;
   pl->last = p;
   pl->last_grid = grid;
-  pl->last_items = n_items;
+  pl->last_ntiles = ntiles;
   pl->last_nb = nb;
   return AERO_OK;
 }
@@ -468,8 +491,11 @@ int aero_create(const aero_limits_t* limits, aero_planner_t** out) {
   pl->lim = L;
   cudaGetDevice(&pl->device);
   const int64_t nbmax = (L.K_max + kRolloutThreads - 1) / kRolloutThreads;
-  const int64_t items = L.n_points_max > L.fine_cells_max ? L.n_points_max : L.fine_cells_max;
-  pl->item_cap = items;
+  const int64_t cap_fine = (int64_t)kFineDup * L.fine_cells_max;
+  const int64_t cap_raw = (int64_t)kCoarseDup * L.n_points_max;
+  int64_t cap = cap_fine > cap_raw ? cap_fine : cap_raw;
+  if (cap > 0x7FFFFFFFLL) cap = 0x7FFFFFFFLL;
+  pl->cand_cap = (int)cap;
   const int64_t D = L.debug_samples_max;
   cudaError_t e = cudaSuccess;
   auto chk = [&](cudaError_t r) {
@@ -480,12 +506,18 @@ int aero_create(const aero_limits_t* limits, aero_planner_t** out) {
   chk(alloc(&pl->cells, L.E_max + 1));
   chk(alloc(&pl->anchors, L.E_max * 3));
   chk(alloc(&pl->guides, (size_t)L.E_max * L.T_max * 3));
-  chk(alloc(&pl->item_cell, items));
-  chk(alloc(&pl->item_slot, items));
-  chk(alloc(&pl->grid_start, kGridCellsMax + 1));
-  chk(alloc(&pl->grid_pts, items));
+  chk(alloc(&pl->item_flag, L.n_points_max));
+  chk(alloc(&pl->grid_count, kGridCellsMax + 1));
+  chk(alloc(&pl->grid_local, kGridCellsMax + 1));
+  chk(alloc(&pl->tile_sum, kMaxTiles));
+  chk(alloc(&pl->tile_off, kMaxTiles + 1));
+  chk(alloc(&pl->cand, cap));
   chk(alloc(&pl->partials, (size_t)L.E_max * nbmax * (2 + 4 * L.T_max)));
   chk(alloc(&pl->sample_costs, (size_t)L.E_max * L.K_max));
+  // the sampled perturbations are kept for the update when they take at most
+  // kMaxStoredPerturbationBytes; larger planners regenerate them from Philox
+  const size_t du_bytes = sizeof(float4) * (size_t)L.E_max * L.K_max * L.T_max;
+  if (du_bytes <= kMaxStoredPerturbationBytes) chk(alloc(&pl->dU, (size_t)L.E_max * L.K_max * L.T_max));
   chk(alloc(&pl->stage2_x, (size_t)L.E_max * (L.T_max + 1) * 10));
   chk(alloc(&pl->counter, 1));
   chk(alloc(&pl->status, 1));
@@ -581,7 +613,7 @@ size_t aero_debug_size(aero_planner_t* pl, int32_t what) {
     case AERO_DBG_ANCHORS: return 4 * E * 3;
     case AERO_DBG_GUIDES: return 4 * E * T * 3;
     case AERO_DBG_GRID_META: return 32;
-    case AERO_DBG_GRID_START: return 4 * (G * G * G + 1);
+    case AERO_DBG_GRID_START: return 4 * (G * G * G + 1);  // computed on the host
     case AERO_DBG_GRID_POINTS: return 0;  // size known after the step; see aero_get_debug
     case AERO_DBG_SAMPLE_COSTS: return 4 * E * K;
     case AERO_DBG_STAGE2_STATES: return 4 * E * (T + 1) * 10;
@@ -596,29 +628,37 @@ int aero_get_debug(aero_planner_t* pl, int32_t what, void* dst, size_t bytes, vo
   if (!pl || !dst || !pl->have_step || what < 0 || what >= AERO_DBG_COUNT) return AERO_ERR_INVALID_ARG;
   cudaStream_t s = (cudaStream_t)stream;
   const aero_params_t& p = pl->last;
-  if (what == AERO_DBG_GRID_META) {
-    if (bytes < 32) return AERO_ERR_INVALID_ARG;
-    int32_t meta[8] = {0};
-    meta[0] = pl->last_grid.G;
-    float f[2] = {pl->last_grid.origin, pl->last_grid.h};
-    std::memcpy(&meta[4], f, sizeof(f));
-    // number of collision points = grid_start[G^3]
-    const int gcells = pl->last_grid.G * pl->last_grid.G * pl->last_grid.G;
-    cudaError_t e = cudaMemcpyAsync(&meta[1], pl->grid_start + gcells, 4, cudaMemcpyDeviceToHost, s);
+  if (what == AERO_DBG_GRID_META || what == AERO_DBG_GRID_POINTS || what == AERO_DBG_GRID_START) {
+    // synchronous: the number of candidate entries and the cell starts are
+    // assembled on the host
+    const GridGeom& g = pl->last_grid;
+    const int gcells = g.G * g.G * g.G;
+    int32_t n_entries = 0;
+    cudaError_t e = cudaMemcpyAsync(&n_entries, pl->tile_off + pl->last_ntiles, 4,
+                                    cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return cuda_fail(e);
-    std::memcpy(dst, meta, 32);
-    return AERO_OK;
-  }
-  if (what == AERO_DBG_GRID_POINTS) {
-    const int gcells = pl->last_grid.G * pl->last_grid.G * pl->last_grid.G;
-    int32_t npts = 0;
-    cudaError_t e = cudaMemcpyAsync(&npts, pl->grid_start + gcells, 4, cudaMemcpyDeviceToHost, s);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    if (e != cudaSuccess) return cuda_fail(e);
-    const size_t need = sizeof(float4) * (size_t)npts;
+    if (what == AERO_DBG_GRID_META) {
+      if (bytes < 32) return AERO_ERR_INVALID_ARG;
+      int32_t meta[8] = {g.G, n_entries, g.cap, 0, 0, 0, 0, 0};
+      const float f[3] = {g.origin, g.h, g.reach};
+      std::memcpy(&meta[4], f, sizeof(f));
+      return cuda_fail(cudaMemcpy(dst, meta, 32, cudaMemcpyDefault));
+    }
+    if (what == AERO_DBG_GRID_POINTS) {
+      const size_t need = sizeof(float4) * (size_t)(n_entries < g.cap ? n_entries : g.cap);
+      if (bytes < need) return AERO_ERR_INVALID_ARG;
+      return cuda_fail(cudaMemcpy(dst, pl->cand, need, cudaMemcpyDefault));
+    }
+    const size_t need = sizeof(int32_t) * ((size_t)gcells + 1);
     if (bytes < need) return AERO_ERR_INVALID_ARG;
-    return cuda_fail(cudaMemcpyAsync(dst, pl->grid_pts, need, cudaMemcpyDefault, s));
+    std::vector<int32_t> local((size_t)gcells + 1), off((size_t)pl->last_ntiles + 1);
+    e = cudaMemcpy(local.data(), pl->grid_local, need, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess)
+      e = cudaMemcpy(off.data(), pl->tile_off, 4 * off.size(), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(e);
+    for (size_t c = 0; c <= (size_t)gcells; ++c) local[c] += off[c >> kScanTileShift];
+    return cuda_fail(cudaMemcpy(dst, local.data(), need, cudaMemcpyDefault));
   }
   const size_t need = aero_debug_size(pl, what);
   if (bytes < need) return AERO_ERR_INVALID_ARG;
@@ -630,7 +670,6 @@ int aero_get_debug(aero_planner_t* pl, int32_t what, void* dst, size_t bytes, vo
     case AERO_DBG_ANCHOR_CELLS: src = pl->cells + 1; break;
     case AERO_DBG_ANCHORS: src = pl->anchors; break;
     case AERO_DBG_GUIDES: src = pl->guides; break;
-    case AERO_DBG_GRID_START: src = pl->grid_start; break;
     case AERO_DBG_SAMPLE_COSTS: src = pl->sample_costs; break;
     case AERO_DBG_STAGE2_STATES: src = pl->stage2_x; break;
     case AERO_DBG_SAMPLE_U: src = pl->dbg_u; break;
@@ -708,21 +747,23 @@ const char* aero_status_str(int status) {
 // so such callers use aero_plan_step_noalloc instead: its workspace is carved
 // from g_noalloc_scratch, a file-scope device array that the CUDA loader sets
 // up with the module and that every GPU loading this library keeps until the
-// process exits.  Its size is fixed by the kNa* limits below (about 2.3 MB).
+// process exits.  Its size is fixed by the kNa* limits below (about 6.5 MB).
 // ---------------------------------------------------------------------------
 namespace {
 
 constexpr int kNaE = 16, kNaK = 2048, kNaT = 64, kNaCells = 128 * 64;
 constexpr int64_t kNaPoints = 65536;
-constexpr int kNaGridCells = 32 * 32 * 32;
+constexpr int kNaGrid = 32, kNaGridCells = kNaGrid * kNaGrid * kNaGrid;
+constexpr int kNaTiles = (kNaGridCells + 1 + kScanTile - 1) / kScanTile;
+constexpr int kNaCand = 1 << 18;  // candidate entries: 27 per P_f point of 8192 cones
 constexpr int kNaNb = (kNaK + kRolloutThreads - 1) / kRolloutThreads;
 
 constexpr size_t align256(size_t b) { return (b + 255) / 256 * 256; }
-constexpr size_t kNaItems = kNaPoints > kNaCells ? kNaPoints : kNaCells;
 constexpr size_t kNaBytes =
     align256(8 * (size_t)kNaCells) + align256(4 * (size_t)kNaCells) + align256(4 * (kNaE + 1)) +
-    align256(4 * 3 * kNaE) + align256(4 * 3 * (size_t)kNaE * kNaT) + 2 * align256(4 * kNaItems) +
-    align256(4 * ((size_t)kNaGridCells + 1)) + align256(16 * kNaItems) +
+    align256(4 * 3 * kNaE) + align256(4 * 3 * (size_t)kNaE * kNaT) + align256(4 * (size_t)kNaPoints) +
+    2 * align256(4 * ((size_t)kNaGridCells + 1)) + align256(4 * (size_t)kNaTiles) +
+    align256(4 * ((size_t)kNaTiles + 1)) + align256(16 * (size_t)kNaCand) +
     align256(4 * (size_t)kNaE * kNaNb * (2 + 4 * kNaT)) + align256(4 * (size_t)kNaE * kNaK) +
     align256(4 * (size_t)kNaE * (kNaT + 1) * 10) + align256(4) + align256(4);
 
@@ -768,10 +809,14 @@ void noalloc_carve(unsigned char* base, aero_planner& pl) {
   pl.cells = reinterpret_cast<int*>(take(4 * (kNaE + 1)));
   pl.anchors = reinterpret_cast<float*>(take(4 * 3 * kNaE));
   pl.guides = reinterpret_cast<float*>(take(4 * 3 * (size_t)kNaE * kNaT));
-  pl.item_cell = reinterpret_cast<int*>(take(4 * kNaItems));
-  pl.item_slot = reinterpret_cast<int*>(take(4 * kNaItems));
-  pl.grid_start = reinterpret_cast<int*>(take(4 * ((size_t)kNaGridCells + 1)));
-  pl.grid_pts = reinterpret_cast<float4*>(take(16 * kNaItems));
+  pl.item_flag = reinterpret_cast<int*>(take(4 * (size_t)kNaPoints));
+  pl.grid_count = reinterpret_cast<int*>(take(4 * ((size_t)kNaGridCells + 1)));
+  pl.grid_local = reinterpret_cast<int*>(take(4 * ((size_t)kNaGridCells + 1)));
+  pl.tile_sum = reinterpret_cast<int*>(take(4 * (size_t)kNaTiles));
+  pl.tile_off = reinterpret_cast<int*>(take(4 * ((size_t)kNaTiles + 1)));
+  pl.cand = reinterpret_cast<float4*>(take(16 * (size_t)kNaCand));
+  pl.cand_cap = kNaCand;
+  pl.grid_max = kNaGrid;
   pl.partials = reinterpret_cast<float*>(take(4 * (size_t)kNaE * kNaNb * (2 + 4 * kNaT)));
   pl.sample_costs = reinterpret_cast<float*>(take(4 * (size_t)kNaE * kNaK));
   pl.stage2_x = reinterpret_cast<float*>(take(4 * (size_t)kNaE * (kNaT + 1) * 10));
@@ -795,8 +840,7 @@ int aero_plan_step_noalloc(const aero_state_t* x0, const float* cloud, int64_t n
   pl.lim.debug_samples_max = 0;
   int rc = validate(&pl, params, n);
   if (rc != AERO_OK) return rc;
-  const GridGeom g = make_grid(*params);
-  if ((int64_t)g.G * g.G * g.G > kNaGridCells) return AERO_ERR_EXCEEDS_LIMITS;
+  if (params->collision_set != 0) return AERO_ERR_EXCEEDS_LIMITS;
   if (reinterpret_cast<uintptr_t>(u_nom) % 16 != 0) return AERO_ERR_INVALID_ARG;
   if ((n > 0 && !is_device_ptr(cloud)) || !is_device_ptr(u_nom) || !is_device_ptr(u_best) ||
       !is_device_ptr(cand) || !is_device_ptr(best_idx))

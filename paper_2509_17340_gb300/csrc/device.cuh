@@ -44,107 +44,141 @@ __device__ __forceinline__ float4 normals4(uint4 w) {
 
 // Perturbation delta for sample k, step j, instance e (Sec. III-B).
 __device__ __forceinline__ float4 noise_delta(uint32_t k, uint32_t j, uint32_t e, uint32_t c3,
-                                              uint32_t k0, uint32_t k1, const float* sigma) {
+                                              uint32_t k0, uint32_t k1, float4 sigma) {
   const float4 n = normals4(philox4x32_10(make_uint4(k, j, e, c3), k0, k1));
-  return make_float4(sigma[0] * n.x, sigma[1] * n.y, sigma[2] * n.z, sigma[3] * n.w);
+  return make_float4(sigma.x * n.x, sigma.y * n.y, sigma.z * n.z, sigma.w * n.w);
 }
 
 // ---------------------------------------------------------------------------
-// Quadrotor model (Eq. dynamics) and one RK4 step with renormalisation.
+// Quadrotor model (Eq. dynamics) integrated by one classical RK4 step with the
+// control held over the step (Eq. mppi_rollout_simplified), then the
+// quaternion renormalised.
+//
+// The RK4 stages are evaluated in closed form.  With the body rate w held,
+// q' = A q with A q = 1/2 q (x) [0, w] and A^2 = -s I, s = |w|^2 / 4, so every
+// stage quaternion is a combination of q and A q:
+//   q1 = q,  q2 = q + h/2 Aq,  q3 = (1 - h^2 s/4) q + h/2 Aq,
+//   q4 = (1 - h^2 s/2) q + h (1 - h^2 s/4) Aq,
+//   q+ = (1 - h^2 s/2 + h^4 s^2/24) q + (h - h^3 s/6) Aq.
+// v' = a(q) = (F/m) R(q) e3 - g e3 does not depend on p or v, so with
+// a_i = a(q_i):  p+ = p + h v + h^2/6 (a1 + a2 + a3),
+//                v+ = v + h/6 (a1 + 2 a2 + 2 a3 + a4).
+// These are the RK4 stage sums of the textbook scheme, regrouped.
 // ---------------------------------------------------------------------------
 struct State {
   float p[3], q[4], v[3];
 };
 
-__device__ __forceinline__ void dynamics(const State& x, float F, float wx, float wy, float wz,
-                                         const DynParams& dp, State& d) {
-  d.p[0] = x.v[0];
-  d.p[1] = x.v[1];
-  d.p[2] = x.v[2];
-  // q' = 1/2 q (x) [0, w]
-  d.q[0] = 0.5f * (-x.q[1] * wx - x.q[2] * wy - x.q[3] * wz);
-  d.q[1] = 0.5f * (x.q[0] * wx + x.q[2] * wz - x.q[3] * wy);
-  d.q[2] = 0.5f * (x.q[0] * wy - x.q[1] * wz + x.q[3] * wx);
-  d.q[3] = 0.5f * (x.q[0] * wz + x.q[1] * wy - x.q[2] * wx);
-  // v' = (F/m) R(q) e3 + g
-  const float a = F * dp.inv_mass;
-  d.v[0] = a * (2.0f * (x.q[1] * x.q[3] + x.q[0] * x.q[2]));
-  d.v[1] = a * (2.0f * (x.q[2] * x.q[3] - x.q[0] * x.q[1]));
-  d.v[2] = a * (1.0f - 2.0f * (x.q[1] * x.q[1] + x.q[2] * x.q[2])) - dp.g;
-}
-
-__device__ __forceinline__ void axpy_state(const State& x, float h, const State& k, State& o) {
-#pragma unroll
-  for (int i = 0; i < 3; ++i) o.p[i] = x.p[i] + h * k.p[i];
-#pragma unroll
-  for (int i = 0; i < 4; ++i) o.q[i] = x.q[i] + h * k.q[i];
-#pragma unroll
-  for (int i = 0; i < 3; ++i) o.v[i] = x.v[i] + h * k.v[i];
+// Third column of R(q) (unit-quaternion formula), i.e. R(q) e3.
+__device__ __forceinline__ void r_e3(float w, float x, float y, float z, float& rx, float& ry,
+                                     float& rz) {
+  rx = 2.0f * (x * z + w * y);
+  ry = 2.0f * (y * z - w * x);
+  rz = 1.0f - 2.0f * (x * x + y * y);
 }
 
 __device__ __forceinline__ void rk4_step(State& x, float4 u, const DynParams& dp) {
-  State k1, k2, k3, k4, t;
-  const float h = dp.dt, hh = 0.5f * dp.dt, h6 = dp.dt * (1.0f / 6.0f);
-  dynamics(x, u.x, u.y, u.z, u.w, dp, k1);
-  axpy_state(x, hh, k1, t);
-  dynamics(t, u.x, u.y, u.z, u.w, dp, k2);
-  axpy_state(x, hh, k2, t);
-  dynamics(t, u.x, u.y, u.z, u.w, dp, k3);
-  axpy_state(x, h, k3, t);
-  dynamics(t, u.x, u.y, u.z, u.w, dp, k4);
-#pragma unroll
-  for (int i = 0; i < 3; ++i) x.p[i] += h6 * (k1.p[i] + 2.0f * (k2.p[i] + k3.p[i]) + k4.p[i]);
-#pragma unroll
-  for (int i = 0; i < 4; ++i) x.q[i] += h6 * (k1.q[i] + 2.0f * (k2.q[i] + k3.q[i]) + k4.q[i]);
-#pragma unroll
-  for (int i = 0; i < 3; ++i) x.v[i] += h6 * (k1.v[i] + 2.0f * (k2.v[i] + k3.v[i]) + k4.v[i]);
-  const float inv = rsqrtf(x.q[0] * x.q[0] + x.q[1] * x.q[1] + x.q[2] * x.q[2] + x.q[3] * x.q[3]);
-#pragma unroll
-  for (int i = 0; i < 4; ++i) x.q[i] *= inv;
+  const float h = dp.dt;
+  const float wx = u.y, wy = u.z, wz = u.w;
+  const float* q = x.q;
+  // A q = 1/2 q (x) [0, w]
+  const float a0 = 0.5f * (-q[1] * wx - q[2] * wy - q[3] * wz);
+  const float a1 = 0.5f * (q[0] * wx + q[2] * wz - q[3] * wy);
+  const float a2 = 0.5f * (q[0] * wy - q[1] * wz + q[3] * wx);
+  const float a3 = 0.5f * (q[0] * wz + q[1] * wy - q[2] * wx);
+  const float s = 0.25f * (wx * wx + wy * wy + wz * wz);
+  const float hh = h * h * s;
+  const float c3 = 1.0f - 0.25f * hh, c4 = 1.0f - 0.5f * hh;
+  const float hb = 0.5f * h, h4 = h * c3;
+  float r1x, r1y, r1z, r2x, r2y, r2z, r3x, r3y, r3z, r4x, r4y, r4z;
+  r_e3(q[0], q[1], q[2], q[3], r1x, r1y, r1z);
+  r_e3(q[0] + hb * a0, q[1] + hb * a1, q[2] + hb * a2, q[3] + hb * a3, r2x, r2y, r2z);
+  r_e3(c3 * q[0] + hb * a0, c3 * q[1] + hb * a1, c3 * q[2] + hb * a2, c3 * q[3] + hb * a3, r3x,
+       r3y, r3z);
+  r_e3(c4 * q[0] + h4 * a0, c4 * q[1] + h4 * a1, c4 * q[2] + h4 * a2, c4 * q[3] + h4 * a3, r4x,
+       r4y, r4z);
+  const float f = u.x * dp.inv_mass;
+  const float fp = h * h * (1.0f / 6.0f) * f, fv = h * (1.0f / 6.0f) * f;
+  const float gp = 0.5f * h * h * dp.g, gv = h * dp.g;
+  x.p[0] += h * x.v[0] + fp * (r1x + r2x + r3x);
+  x.p[1] += h * x.v[1] + fp * (r1y + r2y + r3y);
+  x.p[2] += h * x.v[2] + fp * (r1z + r2z + r3z) - gp;
+  x.v[0] += fv * (r1x + 2.0f * (r2x + r3x) + r4x);
+  x.v[1] += fv * (r1y + 2.0f * (r2y + r3y) + r4y);
+  x.v[2] += fv * (r1z + 2.0f * (r2z + r3z) + r4z) - gv;
+  const float cq = 1.0f - 0.5f * hh + hh * hh * (1.0f / 24.0f);
+  const float ca = h * (1.0f - hh * (1.0f / 6.0f));
+  const float n0 = cq * q[0] + ca * a0, n1 = cq * q[1] + ca * a1;
+  const float n2 = cq * q[2] + ca * a2, n3 = cq * q[3] + ca * a3;
+  const float inv = rsqrtf(n0 * n0 + n1 * n1 + n2 * n2 + n3 * n3);
+  x.q[0] = n0 * inv;
+  x.q[1] = n1 * inv;
+  x.q[2] = n2 * inv;
+  x.q[3] = n3 * inv;
 }
 
 // ---------------------------------------------------------------------------
-// Collision grid query: squared distance to the nearest collision point if it
-// is below d_max^2, else d_max^2.  Cells have edge h >= d_max (1 + 1/16), so
-// every point within d_max lies in the 3x3x3 block around the query's cell.
-// Rows of the block whose slab is farther than d_max are skipped; along x the
-// neighbours are taken only when they can be within d_max.
+// Collision queries on the candidate lists.  The list of the query's cell holds
+// every collision point closer than d_max to that cell's box, so the nearest
+// point, when closer than d_max, is in it.  Queries outside the grid are
+// farther than d_max from every point.  The result is the squared distance to
+// the nearest point if that is below d_max^2, else d_max^2.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ float nn_dist2(float px, float py, float pz, const GridView& g,
-                                          float dmax, float dmax2) {
+__device__ __forceinline__ void cand_range(float px, float py, float pz, const GridView& g, int& s,
+                                           int& e) {
   const float fx = (px - g.origin) * g.inv_h;
   const float fy = (py - g.origin) * g.inv_h;
   const float fz = (pz - g.origin) * g.inv_h;
+  s = e = 0;
+  const float Gf = (float)g.G;
+  if (fx >= 0.0f && fy >= 0.0f && fz >= 0.0f && fx < Gf && fy < Gf && fz < Gf) {
+    const int c = ((int)fz * g.G + (int)fy) * g.G + (int)fx;
+    s = __ldg(g.local + c) + __ldg(g.tile_off + (c >> kScanTileShift));
+    e = __ldg(g.local + c + 1) + __ldg(g.tile_off + ((c + 1) >> kScanTileShift));
+    s = min(s, g.cap);  // an overflowed candidate array is reported by the status word
+    e = min(e, g.cap);
+  }
+}
+
+__device__ __forceinline__ float dist2_to(const float4 q, float px, float py, float pz) {
+  const float ax = px - q.x, ay = py - q.y, az = pz - q.z;
+  return ax * ax + ay * ay + az * az;
+}
+
+// One thread, one query.
+__device__ __forceinline__ float nn_dist2(float px, float py, float pz, const GridView& g,
+                                          float dmax2) {
+  int s, e;
+  cand_range(px, py, pz, g, s, e);
   float best = dmax2;
-  if (!(fx > -1.0f && fy > -1.0f && fz > -1.0f && fx < g.G + 1.0f && fy < g.G + 1.0f &&
-        fz < g.G + 1.0f))
-    return best;  // farther than one cell from every point (or not finite)
-  const int cx = __float2int_rd(fx), cy = __float2int_rd(fy), cz = __float2int_rd(fz);
-  const float h = 1.0f / g.inv_h;
-  // distances from the query to the lower / upper faces of its cell
-  const float lx = (fx - cx) * h, ux = h - lx;
-  const float ly = (fy - cy) * h, uy = h - ly;
-  const float lz = (fz - cz) * h, uz = h - lz;
-  const int x0 = max(lx < dmax ? cx - 1 : cx, 0);
-  const int x1 = min(ux < dmax ? cx + 1 : cx, g.G - 1);
-  if (x0 > x1) return best;
-  for (int dz = -1; dz <= 1; ++dz) {
-    const int z = cz + dz;
-    if (z < 0 || z >= g.G) continue;
-    const float ez = dz < 0 ? lz : (dz > 0 ? uz : 0.0f);
-    for (int dy = -1; dy <= 1; ++dy) {
-      const int y = cy + dy;
-      if (y < 0 || y >= g.G) continue;
-      const float ey = dy < 0 ? ly : (dy > 0 ? uy : 0.0f);
-      if (ey * ey + ez * ez >= dmax2) continue;
-      const int row = (z * g.G + y) * g.G;
-      const int s = __ldg(g.start + row + x0), e = __ldg(g.start + row + x1 + 1);
-      for (int i = s; i < e; ++i) {
-        const float4 q = __ldg(g.pts + i);
-        const float ax = px - q.x, ay = py - q.y, az = pz - q.z;
-        best = fminf(best, ax * ax + ay * ay + az * az);
-      }
-    }
+  for (int i = s; i < e; ++i) best = fminf(best, dist2_to(__ldg(g.pts + i), px, py, pz));
+  return best;
+}
+
+// One query per lane; every lane of the warp must call.  Each lane scans up to
+// kLightCandidates of its own candidates; the rest of a longer list is scanned
+// by the whole warp, one such lane at a time, and reduced with a warp minimum.
+__device__ __forceinline__ float nn_dist2_warp(float px, float py, float pz, const GridView& g,
+                                               float dmax2, int lane) {
+  int s, e;
+  cand_range(px, py, pz, g, s, e);
+  float best = dmax2;
+  const int m = min(e - s, kLightCandidates);
+  for (int i = 0; i < m; ++i) best = fminf(best, dist2_to(__ldg(g.pts + s + i), px, py, pz));
+  unsigned heavy = __ballot_sync(0xffffffffu, e - s > kLightCandidates);
+  while (heavy) {
+    const int l = __ffs(heavy) - 1;
+    heavy &= heavy - 1;
+    const float qx = __shfl_sync(0xffffffffu, px, l);
+    const float qy = __shfl_sync(0xffffffffu, py, l);
+    const float qz = __shfl_sync(0xffffffffu, pz, l);
+    const int hs = __shfl_sync(0xffffffffu, s, l) + kLightCandidates;
+    const int he = __shfl_sync(0xffffffffu, e, l);
+    float b = dmax2;
+    for (int i = hs + lane; i < he; i += 32) b = fminf(b, dist2_to(__ldg(g.pts + i), qx, qy, qz));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) b = fminf(b, __shfl_xor_sync(0xffffffffu, b, o));
+    if (lane == l) best = fminf(best, b);
   }
   return best;
 }

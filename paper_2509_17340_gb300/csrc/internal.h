@@ -11,9 +11,11 @@ constexpr int kMaxAz = 512;
 constexpr int kMaxEl = 256;
 constexpr int kMaxE = 64;
 constexpr int kMaxT = 128;
-constexpr int kGridMax = 64;        // collision grid cells per axis, at most
+constexpr int kGridMax = 96;         // collision-grid cells per axis, at most
+constexpr int kScanTile = 4096;      // cells per scan tile (1024 threads x 4)
+constexpr int kScanTileShift = 12;
 constexpr int kRolloutThreads = 128; // samples per rollout CTA (one warp-group)
-constexpr float kCellMargin = 1.0625f; // grid cell edge = d_max * (1 + 1/16), at least
+constexpr int kLightCandidates = 4;  // candidates a lane checks alone; more go to the warp
 
 // Binary32 edge tables of the partition, passed by value to the kernels.
 // Azimuth edge k: theta_k = pi (2k - A) / A; elevation edge k: phi_k = lo +
@@ -25,11 +27,17 @@ struct PartTables {
   float se[kMaxEl + 1];
 };
 
-// Uniform collision grid in world axes, coordinates relative to p0.
+// Collision grid in world axes, coordinates relative to p0.  Cell (x, y, z)
+// is the box [origin + x h, origin + (x+1) h) x ... and its candidate list holds
+// every collision point whose distance to that box is below `reach` = d_max
+// plus a rounding margin, so the nearest point of any query closer than d_max
+// is in the list of the query's cell.
 struct GridGeom {
   int G;          // cells per axis
-  float origin;   // same on all three axes
+  float origin;   // lower corner, same on all three axes
   float h, inv_h; // cell edge and its reciprocal
+  float reach;    // d_max + margin
+  int cap;        // capacity of the candidate array (entries)
 };
 
 struct PartitionArgs {
@@ -41,12 +49,23 @@ struct PartitionArgs {
   int A, El;
   int check_lo, check_hi;
   unsigned long long* keys;
-  // collision set = every kept point: the partition also counts grid cells
+  int* item_flag;  // collision set = every kept point: 1 where the point is kept, else 0
+};
+
+// Count and scatter passes of the candidate lists.
+struct CandArgs {
+  const float* cloud;
+  float p0[3];
+  const unsigned long long* keys;  // collision set = P_f: item c is the winner of fine cell c
+  const int* item_flag;            // collision set = kept points: item i is point i
+  int64_t n_items;
   int raw;
   GridGeom grid;
-  int* grid_count;
-  int* item_cell;
-  int* item_slot;
+  int* count;          // G^3 + 1: entries per cell (count pass); fill cursor (scatter pass)
+  const int* local;    // tile-local exclusive prefix of the counts (scatter pass)
+  const int* tile_off; // exclusive prefix of the tile totals (scatter pass)
+  float4* cand;        // candidate entries (scatter pass)
+  int* status;
 };
 
 struct GuideArgs {
@@ -68,27 +87,18 @@ struct GuideArgs {
   int* cells;          // [0] goal fine cell, [1 + e] anchor coarse cell
   float* anchors;      // E x 3 (relative to p0)
   float* guides;       // E x T x 3 (relative to p0)
-  // scan of the grid counts (block 0)
-  int* grid_start;     // G^3 + 1, counts in, exclusive prefix out
-  int ncells;
-};
-
-struct ScatterArgs {
-  const float* cloud;
-  float p0[3];
-  const int* item_cell;
-  const int* item_slot;
-  const unsigned long long* keys; // P_f mode: item c is the winner of fine cell c
-  int64_t n_items;
-  int raw;
-  const int* grid_start;
-  float4* grid_pts;
+  // block 0: exclusive scan of the tile totals of the candidate counts
+  const int* tile_sum;
+  int* tile_off;       // ntiles + 1 entries; tile_off[ntiles] = number of entries
+  int ntiles;
 };
 
 struct GridView {
-  const int* start;
-  const float4* pts;
+  const int* local;    // G^3 + 1: start of cell c = local[c] + tile_off[c >> kScanTileShift]
+  const int* tile_off;
+  const float4* pts;   // candidate entries, grouped by cell
   int G;
+  int cap;             // entries the array holds (reads are clamped to it)
   float origin, inv_h;
 };
 
@@ -115,6 +125,7 @@ struct RolloutArgs {
   GridView grid;
   float* partials;         // E x nb x (2 + 4T)
   float* sample_costs;     // E x K
+  float4* dU;              // E x T x K clamped perturbations, or null: regenerate them
   int dbg_D;
   float* dbg_u;            // E x D x T x 4
   float* dbg_x;            // E x D x (T+1) x 10
@@ -140,11 +151,11 @@ struct UpdateArgs {
 };
 
 cudaError_t launch_partition(const PartitionArgs& a, const PartTables& t, cudaStream_t s);
-cudaError_t launch_pf_count(const unsigned long long* keys, int ncell, const float* cloud,
-                            const float p0[3], GridGeom g, int* grid_count, int* item_cell,
-                            int* item_slot, cudaStream_t s);
+cudaError_t launch_cand_count(const CandArgs& a, cudaStream_t s);
+cudaError_t launch_scan_tiles(int* count, int* local, int* tile_sum, int ncells, int ntiles,
+                              cudaStream_t s);
 cudaError_t launch_scan_guides(const GuideArgs& a, const PartTables& t, cudaStream_t s);
-cudaError_t launch_scatter(const ScatterArgs& a, cudaStream_t s);
+cudaError_t launch_cand_scatter(const CandArgs& a, cudaStream_t s);
 cudaError_t launch_rollout(const RolloutArgs& a, cudaStream_t s);
 cudaError_t launch_update(const UpdateArgs& a, cudaStream_t s);
 cudaError_t launch_philox(uint32_t k0, uint32_t k1, uint32_t c1, uint32_t c2, uint32_t c3,

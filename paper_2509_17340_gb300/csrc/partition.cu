@@ -1,5 +1,6 @@
 // Multi-resolution partition (Sec. IV-A), anchors (Sec. IV-B.1-2), quintic
-// guides (Sec. IV-B.3) and the uniform collision grid over the collision set.
+// guides (Sec. IV-B.3) and the collision grid: per-cell candidate lists over
+// the collision set (P_f of Sec. IV-C, or every kept point).
 //
 // Integer decisions (cone of a point, its range key, the coarse winner, the
 // goal's cone) are taken in binary32 with explicitly rounded operations
@@ -50,16 +51,6 @@ __device__ __forceinline__ int el_bin(const float* ce, const float* se, int El, 
   return lo;
 }
 
-__device__ __forceinline__ int grid_cell(float dx, float dy, float dz, const GridGeom& g) {
-  int cx = __float2int_rd((dx - g.origin) * g.inv_h);
-  int cy = __float2int_rd((dy - g.origin) * g.inv_h);
-  int cz = __float2int_rd((dz - g.origin) * g.inv_h);
-  cx = min(max(cx, 0), g.G - 1);
-  cy = min(max(cy, 0), g.G - 1);
-  cz = min(max(cz, 0), g.G - 1);
-  return (cz * g.G + cy) * g.G + cx;
-}
-
 // ---------------------------------------------------------------------------
 // K1: cone of every point and atomic minimum of its key per cone.
 // ---------------------------------------------------------------------------
@@ -98,89 +89,154 @@ __global__ void __launch_bounds__(256) k_partition(PartitionArgs a, PartTables t
               ((unsigned long long)__float_as_uint(r2) << 32) | (unsigned long long)(uint32_t)i;
           atomicMin(a.keys + c, key);
           cell = c;
-          if (a.raw) {
-            const int gc = grid_cell(dx, dy, dz, a.grid);
-            a.item_cell[i] = gc;
-            a.item_slot[i] = atomicAdd(a.grid_count + gc, 1);
-          }
         }
       }
     }
-    if (a.raw && cell < 0) a.item_cell[i] = -1;
+    if (a.item_flag) a.item_flag[i] = cell >= 0 ? 1 : 0;
   }
 }
 
 // ---------------------------------------------------------------------------
-// K2a (collision set = P_f): grid cell of the winner of every non-empty cone.
+// K2a / K2d: candidate lists.  For every collision point p, every cell whose
+// box is closer to p than `reach` gets p: the count pass adds to the cell's
+// counter, the scatter pass writes p at start(cell) + its fill ticket.  Order
+// within a cell depends on the atomics, but only the minimum distance is used.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_pf_count(const unsigned long long* __restrict__ keys,
-                                                  int ncell, const float* __restrict__ cloud,
-                                                  float p0x, float p0y, float p0z, GridGeom g,
-                                                  int* grid_count, int* item_cell,
-                                                  int* item_slot) {
-  const int c = blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= ncell) return;
-  const unsigned long long key = keys[c];
-  if (key == kEmpty) {
-    item_cell[c] = -1;
-    return;
+__device__ __forceinline__ bool cand_item(const CandArgs& a, int64_t it, float& px, float& py,
+                                          float& pz) {
+  int64_t i;
+  if (a.raw) {
+    if (!a.item_flag[it]) return false;
+    i = it;
+  } else {
+    const unsigned long long key = a.keys[it];
+    if (key == kEmpty) return false;
+    i = (int64_t)(key & 0xFFFFFFFFull);
   }
-  const int64_t i = (int64_t)(key & 0xFFFFFFFFull);
-  const float dx = sub(__ldg(cloud + 3 * i), p0x), dy = sub(__ldg(cloud + 3 * i + 1), p0y),
-              dz = sub(__ldg(cloud + 3 * i + 2), p0z);
-  const int gc = grid_cell(dx, dy, dz, g);
-  item_cell[c] = gc;
-  item_slot[c] = atomicAdd(grid_count + gc, 1);
+  px = sub(__ldg(a.cloud + 3 * i), a.p0[0]);
+  py = sub(__ldg(a.cloud + 3 * i + 1), a.p0[1]);
+  pz = sub(__ldg(a.cloud + 3 * i + 2), a.p0[2]);
+  return true;
+}
+
+// Squared distance from v to the interval [lo, lo + h].
+__device__ __forceinline__ float gap2(float v, float lo, float h) {
+  const float d = fmaxf(fmaxf(lo - v, v - (lo + h)), 0.0f);
+  return d * d;
+}
+
+// One warp per collision item; its lanes share the item's block of cells.
+template <bool kScatter>
+__global__ void __launch_bounds__(256) k_cand(CandArgs a) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  const GridGeom& g = a.grid;
+  const float r2 = g.reach * g.reach;
+  for (int64_t it = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; it < a.n_items;
+       it += warps) {
+    float px, py, pz;
+    if (!cand_item(a, it, px, py, pz)) continue;  // uniform across the warp
+    const int x0 = max(__float2int_rd((px - g.reach - g.origin) * g.inv_h), 0);
+    const int x1 = min(__float2int_rd((px + g.reach - g.origin) * g.inv_h), g.G - 1);
+    const int y0 = max(__float2int_rd((py - g.reach - g.origin) * g.inv_h), 0);
+    const int y1 = min(__float2int_rd((py + g.reach - g.origin) * g.inv_h), g.G - 1);
+    const int z0 = max(__float2int_rd((pz - g.reach - g.origin) * g.inv_h), 0);
+    const int z1 = min(__float2int_rd((pz + g.reach - g.origin) * g.inv_h), g.G - 1);
+    const int nx = x1 - x0 + 1, ny = y1 - y0 + 1, nz = z1 - z0 + 1;
+    if (nx <= 0 || ny <= 0 || nz <= 0) continue;
+    const int ncand = nx * ny * nz;
+    for (int o = lane; o < ncand; o += 32) {
+      const int x = x0 + o % nx, y = y0 + (o / nx) % ny, z = z0 + o / (nx * ny);
+      const float d2 = gap2(px, g.origin + x * g.h, g.h) + gap2(py, g.origin + y * g.h, g.h) +
+                       gap2(pz, g.origin + z * g.h, g.h);
+      if (d2 >= r2) continue;
+      const int c = (z * g.G + y) * g.G + x;
+      if (!kScatter) {
+        atomicAdd(a.count + c, 1);
+      } else {
+        const int pos = a.local[c] + a.tile_off[c >> kScanTileShift] + atomicAdd(a.count + c, 1);
+        if (pos < g.cap)
+          a.cand[pos] = make_float4(px, py, pz, 0.0f);
+        else
+          atomicOr(a.status, 2);
+      }
+    }
+  }
 }
 
 // ---------------------------------------------------------------------------
-// K2b + K3: block 0 turns the grid counts into cell starts (exclusive scan);
-// block 1 runs the coarse argmax, the goal cone, the anchor cells, the anchors
-// and the quintic guides.
+// K2b: tile-local exclusive scan of the counts (4096 cells per block); the
+// counts are cleared for reuse as fill cursors by the scatter pass.
 // ---------------------------------------------------------------------------
 constexpr int kScanThreads = 1024;
 
-__device__ void scan_block(int* data, int n) {
-  __shared__ int s_warp[32];
-  __shared__ int s_carry;
-  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-  if (tid == 0) s_carry = 0;
-  __syncthreads();
-  for (int base = 0; base < n; base += 4 * kScanThreads) {
-    const int i0 = base + 4 * tid;
-    int v[4];
+__device__ __forceinline__ int block_exclusive_scan(int v, int* s_warp, int& total) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  int incl = v;
 #pragma unroll
-    for (int u = 0; u < 4; ++u) v[u] = (i0 + u < n) ? data[i0 + u] : 0;
-    const int tsum = v[0] + v[1] + v[2] + v[3];
-    int incl = tsum;
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += y;
+  }
+  if (lane == 31) s_warp[wid] = incl;
+  __syncthreads();
+  if (wid == 0) {
+    int w = lane < (int)(blockDim.x >> 5) ? s_warp[lane] : 0;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-      const int y = __shfl_up_sync(0xffffffffu, incl, o);
-      if (lane >= o) incl += y;
+      const int y = __shfl_up_sync(0xffffffffu, w, o);
+      if (lane >= o) w += y;
     }
-    if (lane == 31) s_warp[wid] = incl;
-    __syncthreads();
-    if (wid == 0) {
-      int w = s_warp[lane];
+    s_warp[lane] = w;  // inclusive over warps
+  }
+  __syncthreads();
+  total = s_warp[(blockDim.x >> 5) - 1];
+  const int r = (wid > 0 ? s_warp[wid - 1] : 0) + incl - v;
+  __syncthreads();
+  return r;
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_tiles(int* count, int* local, int* tile_sum,
+                                                             int ncells) {
+  __shared__ int s_warp[32];
+  const int i0 = blockIdx.x * kScanTile + 4 * threadIdx.x;
+  int v[4];
 #pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const int y = __shfl_up_sync(0xffffffffu, w, o);
-        if (lane >= o) w += y;
-      }
-      s_warp[lane] = w;  // inclusive over warps
-    }
-    __syncthreads();
-    int run = s_carry + (wid > 0 ? s_warp[wid - 1] : 0) + incl - tsum;
+  for (int u = 0; u < 4; ++u) v[u] = (i0 + u < ncells) ? count[i0 + u] : 0;
+  int total;
+  int run = block_exclusive_scan(v[0] + v[1] + v[2] + v[3], s_warp, total);
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      if (i0 + u < n) data[i0 + u] = run;
-      run += v[u];
+  for (int u = 0; u < 4; ++u) {
+    if (i0 + u < ncells) {
+      local[i0 + u] = run;
+      count[i0 + u] = 0;
     }
+    run += v[u];
+  }
+  if (threadIdx.x == 0) tile_sum[blockIdx.x] = total;
+}
+
+// ---------------------------------------------------------------------------
+// K2c + K3: block 0 scans the tile totals into tile offsets; block 1 runs the
+// coarse argmax, the goal cone, the anchor cells, the anchors and the quintic
+// guides.
+// ---------------------------------------------------------------------------
+__device__ void scan_tile_offsets(const int* tile_sum, int* tile_off, int ntiles) {
+  __shared__ int s_warp[32];
+  __shared__ int s_carry;
+  if (threadIdx.x == 0) s_carry = 0;
+  __syncthreads();
+  for (int base = 0; base < ntiles; base += kScanThreads) {
+    const int i = base + threadIdx.x;
+    const int v = i < ntiles ? tile_sum[i] : 0;
+    int total;
+    const int r = block_exclusive_scan(v, s_warp, total);
+    if (i < ntiles) tile_off[i] = s_carry + r;
     __syncthreads();
-    if (tid == kScanThreads - 1) s_carry = run;
+    if (threadIdx.x == 0) s_carry += total;
     __syncthreads();
   }
-  if (tid == 0) data[n] = s_carry;
+  if (threadIdx.x == 0) tile_off[ntiles] = s_carry;
 }
 
 __device__ void coarse_guides_block(const GuideArgs& a, const PartTables& t) {
@@ -199,23 +255,38 @@ __device__ void coarse_guides_block(const GuideArgs& a, const PartTables& t) {
   // then lower fine index; empty cones count as r_max.
   const uint32_t empty_bits = __float_as_uint(a.rmax2);
   const int ncoarse = a.Ac * a.Ec;
-  for (int cc = threadIdx.x; cc < ncoarse; cc += blockDim.x) {
+  const int lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
+  const int npool = a.Pa * a.Pe;
+  // one warp per coarse cell: each lane takes a strided share of the pooled
+  // cones, then the warp reduces (r key, centre distance, fine index)
+  for (int cc = threadIdx.x >> 5; cc < ncoarse; cc += nwarp) {
     const int I = cc % a.Ac, J = cc / a.Ac;
-    int best = -1, bdist = 0;
     uint32_t bkey = 0;
-    for (int b = 0; b < a.Pe; ++b)
-      for (int q = 0; q < a.Pa; ++q) {
-        const int c = (J * a.Pe + b) * a.A + I * a.Pa + q;
-        const unsigned long long k = a.keys[c];
-        const uint32_t rk = k == kEmpty ? empty_bits : (uint32_t)(k >> 32);
-        const int dist = abs(2 * q + 1 - a.Pa) + abs(2 * b + 1 - a.Pe);
-        if (best < 0 || rk > bkey || (rk == bkey && (dist < bdist || (dist == bdist && c < best)))) {
-          best = c;
-          bkey = rk;
-          bdist = dist;
-        }
+    int bdist = 0x7fffffff, best = 0x7fffffff;
+    for (int m = lane; m < npool; m += 32) {
+      const int q = m % a.Pa, b = m / a.Pa;
+      const int c = (J * a.Pe + b) * a.A + I * a.Pa + q;
+      const unsigned long long k = a.keys[c];
+      const uint32_t rk = k == kEmpty ? empty_bits : (uint32_t)(k >> 32);
+      const int dist = abs(2 * q + 1 - a.Pa) + abs(2 * b + 1 - a.Pe);
+      if (rk > bkey || (rk == bkey && (dist < bdist || (dist == bdist && c < best)))) {
+        best = c;
+        bkey = rk;
+        bdist = dist;
       }
-    a.coarse_win[cc] = best;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const uint32_t ok = __shfl_xor_sync(0xffffffffu, bkey, o);
+      const int od = __shfl_xor_sync(0xffffffffu, bdist, o);
+      const int oc = __shfl_xor_sync(0xffffffffu, best, o);
+      if (ok > bkey || (ok == bkey && (od < bdist || (od == bdist && oc < best)))) {
+        best = oc;
+        bkey = ok;
+        bdist = od;
+      }
+    }
+    if (lane == 0) a.coarse_win[cc] = best;
   }
   __syncthreads();
   // goal cone and the M_h x M_v anchor cells around it (Sec. IV-B.1)
@@ -289,25 +360,9 @@ __device__ void coarse_guides_block(const GuideArgs& a, const PartTables& t) {
 
 __global__ void __launch_bounds__(kScanThreads) k_scan_guides(GuideArgs a, PartTables t) {
   if (blockIdx.x == 0)
-    scan_block(a.grid_start, a.ncells);
+    scan_tile_offsets(a.tile_sum, a.tile_off, a.ntiles);
   else
     coarse_guides_block(a, t);
-}
-
-// ---------------------------------------------------------------------------
-// K2c: place every collision point at start[cell] + slot.
-// ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_scatter(ScatterArgs a) {
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < a.n_items; c += stride) {
-    const int gc = a.item_cell[c];
-    if (gc < 0) continue;
-    const int64_t i = a.raw ? c : (int64_t)(a.keys[c] & 0xFFFFFFFFull);
-    const float dx = sub(__ldg(a.cloud + 3 * i), a.p0[0]);
-    const float dy = sub(__ldg(a.cloud + 3 * i + 1), a.p0[1]);
-    const float dz = sub(__ldg(a.cloud + 3 * i + 2), a.p0[2]);
-    a.grid_pts[a.grid_start[gc] + a.item_slot[c]] = make_float4(dx, dy, dz, 0.0f);
-  }
 }
 
 __global__ void k_philox(uint32_t k0, uint32_t k1, uint32_t c1, uint32_t c2, uint32_t c3,
@@ -331,12 +386,15 @@ cudaError_t launch_partition(const PartitionArgs& a, const PartTables& t, cudaSt
   return cudaGetLastError();
 }
 
-cudaError_t launch_pf_count(const unsigned long long* keys, int ncell, const float* cloud,
-                            const float p0[3], GridGeom g, int* grid_count, int* item_cell,
-                            int* item_slot, cudaStream_t s) {
-  k_pf_count<<<blocks_for(ncell, 256, 1 << 20), 256, 0, s>>>(keys, ncell, cloud, p0[0], p0[1],
-                                                             p0[2], g, grid_count, item_cell,
-                                                             item_slot);
+cudaError_t launch_cand_count(const CandArgs& a, cudaStream_t s) {
+  if (a.n_items == 0) return cudaSuccess;
+  k_cand<false><<<blocks_for(a.n_items * 32, 256, 152 * 32), 256, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_scan_tiles(int* count, int* local, int* tile_sum, int ncells, int ntiles,
+                              cudaStream_t s) {
+  k_scan_tiles<<<ntiles, kScanThreads, 0, s>>>(count, local, tile_sum, ncells);
   return cudaGetLastError();
 }
 
@@ -345,9 +403,9 @@ cudaError_t launch_scan_guides(const GuideArgs& a, const PartTables& t, cudaStre
   return cudaGetLastError();
 }
 
-cudaError_t launch_scatter(const ScatterArgs& a, cudaStream_t s) {
+cudaError_t launch_cand_scatter(const CandArgs& a, cudaStream_t s) {
   if (a.n_items == 0) return cudaSuccess;
-  k_scatter<<<blocks_for(a.n_items, 256, 152 * 16), 256, 0, s>>>(a);
+  k_cand<true><<<blocks_for(a.n_items * 32, 256, 152 * 32), 256, 0, s>>>(a);
   return cudaGetLastError();
 }
 

@@ -19,9 +19,9 @@ namespace {
 constexpr int NT = kRolloutThreads;
 constexpr int NW = NT / 32;
 
-__device__ __forceinline__ float4 clamp4(float4 u, const float* lo, const float* hi) {
-  return make_float4(fminf(fmaxf(u.x, lo[0]), hi[0]), fminf(fmaxf(u.y, lo[1]), hi[1]),
-                     fminf(fmaxf(u.z, lo[2]), hi[2]), fminf(fmaxf(u.w, lo[3]), hi[3]));
+__device__ __forceinline__ float4 clamp4(float4 u, float4 lo, float4 hi) {
+  return make_float4(fminf(fmaxf(u.x, lo.x), hi.x), fminf(fmaxf(u.y, lo.y), hi.y),
+                     fminf(fmaxf(u.z, lo.z), hi.z), fminf(fmaxf(u.w, lo.w), hi.w));
 }
 
 // Kahan-compensated accumulation of the per-step costs.
@@ -53,6 +53,10 @@ __global__ void __launch_bounds__(NT) k_rollout(RolloutArgs a) {
   const CostParams& cp = a.cost;
   const float dmax2 = cp.d_max * cp.d_max;
   const int dbg = (active && k < a.dbg_D) ? (e * a.dbg_D + k) : -1;
+  const float4 sigma = make_float4(a.sigma[0], a.sigma[1], a.sigma[2], a.sigma[3]);
+  const float4 umin = make_float4(a.umin[0], a.umin[1], a.umin[2], a.umin[3]);
+  const float4 umax = make_float4(a.umax[0], a.umax[1], a.umax[2], a.umax[3]);
+  float4* dU = a.dU ? a.dU + (size_t)e * T * a.K + k : nullptr;  // [e][j][k]
 
   State x;
 #pragma unroll
@@ -68,10 +72,15 @@ __global__ void __launch_bounds__(NT) k_rollout(RolloutArgs a) {
 
   KahanSum S;
   float4 u_prev = make_float4(0.f, 0.f, 0.f, 0.f);
+  float4 d_next = noise_delta(k, 0, e, a.ctr3, a.key0, a.key1, sigma);
   for (int j = 0; j < T; ++j) {
     const float4 un = s_un[j];
-    const float4 d = noise_delta(k, j, e, a.ctr3, a.key0, a.key1, a.sigma);
-    const float4 u = clamp4(make_float4(un.x + d.x, un.y + d.y, un.z + d.z, un.w + d.w), a.umin, a.umax);
+    const float4 d = d_next;
+    // next step's noise does not depend on the state: computed here for ILP
+    if (j + 1 < T) d_next = noise_delta(k, j + 1, e, a.ctr3, a.key0, a.key1, sigma);
+    const float4 u = clamp4(make_float4(un.x + d.x, un.y + d.y, un.z + d.z, un.w + d.w), umin, umax);
+    if (dU && active)
+      dU[(size_t)j * a.K] = make_float4(u.x - un.x, u.y - un.y, u.z - un.z, u.w - un.w);
     // J_ctrl: Q_c |u_j|^2 for j <= T-2, Q_cd |u_j - u_{j-1}|^2 for 1 <= j <= T-2
     float c = 0.0f;
     if (j <= T - 2) {
@@ -88,7 +97,7 @@ __global__ void __launch_bounds__(NT) k_rollout(RolloutArgs a) {
     c += cp.Q_track * norm3f(x.p[0] - g[0], x.p[1] - g[1], x.p[2] - g[2]);
     c += cp.Q_vnorm * (x.v[0] * x.v[0] + x.v[1] * x.v[1] + x.v[2] * x.v[2]);
     c += goal_term(x, cp);
-    const float d2 = nn_dist2(x.p[0], x.p[1], x.p[2], a.grid, cp.d_max, dmax2);
+    const float d2 = nn_dist2_warp(x.p[0], x.p[1], x.p[2], a.grid, dmax2, lane);
     c += jcol_from_d2(d2, cp, dmax2);
     S.add(c);
     if (dbg >= 0) {
@@ -115,13 +124,18 @@ __global__ void __launch_bounds__(NT) k_rollout(RolloutArgs a) {
   const float ws = warp_sum(wk);
   if (lane == 0) s_red[wid] = ws;
 
-  // W_b[j] = sum_k w_k du_k[j], regenerating the noise
+  // W_b[j] = sum_k w_k du_k[j]: the stored perturbations, or the noise regenerated
   for (int j = 0; j < T; ++j) {
-    const float4 un = s_un[j];
-    const float4 d = noise_delta(k, j, e, a.ctr3, a.key0, a.key1, a.sigma);
-    const float4 u = clamp4(make_float4(un.x + d.x, un.y + d.y, un.z + d.z, un.w + d.w), a.umin, a.umax);
-    const float r = warp_sum4(wk * (u.x - un.x), wk * (u.y - un.y), wk * (u.z - un.z),
-                              wk * (u.w - un.w), lane);
+    float4 du;
+    if (dU) {
+      du = active ? dU[(size_t)j * a.K] : make_float4(0.f, 0.f, 0.f, 0.f);
+    } else {
+      const float4 un = s_un[j];
+      const float4 d = noise_delta(k, j, e, a.ctr3, a.key0, a.key1, sigma);
+      const float4 u = clamp4(make_float4(un.x + d.x, un.y + d.y, un.z + d.z, un.w + d.w), umin, umax);
+      du = make_float4(u.x - un.x, u.y - un.y, u.z - un.z, u.w - un.w);
+    }
+    const float r = warp_sum4(wk * du.x, wk * du.y, wk * du.z, wk * du.w, lane);
     if ((lane & 7) == 0) reinterpret_cast<float*>(&s_w[wid][j])[lane >> 3] = r;
   }
   __syncthreads();
@@ -223,7 +237,7 @@ __global__ void __launch_bounds__(UT) k_update(UpdateArgs a) {
     for (int i = 0; i < 3; ++i) x.p[i] = X[i];
     for (int i = 0; i < 4; ++i) x.q[i] = X[3 + i];
     for (int i = 0; i < 3; ++i) x.v[i] = X[7 + i];
-    const float d2 = nn_dist2(x.p[0], x.p[1], x.p[2], a.grid, a.cost.d_max, dmax2);
+    const float d2 = nn_dist2(x.p[0], x.p[1], x.p[2], a.grid, dmax2);
     s_c[j] = goal_term(x, a.cost) + jcol_from_d2(d2, a.cost, dmax2);
   }
   for (int i = tid; i < (T + 1) * 10; i += UT) a.stage2_x[(size_t)e * (T + 1) * 10 + i] = s_x[i];

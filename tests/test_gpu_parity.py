@@ -128,32 +128,47 @@ def test_anchors_and_guides(results, name):
 # ----------------------------------------------------------------- collision grid
 
 @pytest.mark.parametrize("name", CASES)
-def test_grid_holds_the_collision_set(results, planner, orc, name):
+def test_grid_candidate_lists(results, planner, orc, name):
+    """Cell c lists exactly the collision points closer than `reach` to its box
+    (sound: no entry farther; complete: every point clearly closer is there),
+    so a query's nearest point within d_max is in its cell's list."""
     w, u0, g, o = results(name)
     # the planner's debug buffers hold the last step: rerun this case
     import paper_2509_17340_gb300.aero as A
     run_gpu(A, planner, w, w.params, u0, debug=False)
     meta = planner.debug("GRID_META")
-    G, n_items = int(meta[0]), int(meta[1])
-    origin, h = meta[4:6].view(np.float32)
-    start = planner.debug("GRID_START")
-    pts = planner.debug("GRID_POINTS")
+    G, n_entries, cap = int(meta[0]), int(meta[1]), int(meta[2])
+    origin, h, reach = (float(v) for v in meta[4:7].view(np.float32))
+    assert reach >= w.params["d_max"] and n_entries <= cap
+    start = planner.debug("GRID_START").astype(np.int64)
+    pts = planner.debug("GRID_POINTS")[:, :3]
+    assert start[0] == 0 and start[-1] == n_entries == len(pts) and np.all(np.diff(start) >= 0)
     ref = orc.collision_set(w.cloud, w.p0, w.q0, o["keys"], w.params)
-    assert n_items == len(ref) == len(pts) == start[-1]
-    assert np.all(np.diff(start) >= 0) and start[0] == 0
-    # same multiset of points (binary32 offsets from p0)
     rel = (ref.astype(np.float32) - w.p0).astype(np.float32)
-    key = lambda a: np.lexsort((a[:, 2], a[:, 1], a[:, 0]))
-    assert np.array_equal(rel[key(rel)], pts[:, :3][key(pts[:, :3])])
-    # every point sits in the cell its coordinates give
-    for c in range(G ** 3):
-        s, e = start[c], start[c + 1]
-        if s == e:
-            continue
-        cz, cy, cx = c // (G * G), (c // G) % G, c % G
-        f = np.floor((pts[s:e, :3] - origin) * np.float32(1.0 / h)).astype(np.int64)
-        f = np.clip(f, 0, G - 1)
-        assert np.all(f[:, 0] == cx) and np.all(f[:, 1] == cy) and np.all(f[:, 2] == cz)
+    # every entry is a collision point, at most once per cell
+    index = {tuple(p): i for i, p in enumerate(rel.tolist())}
+    ids = np.array([index[tuple(p)] for p in pts.tolist()], np.int64)
+    cells = np.repeat(np.arange(G ** 3, dtype=np.int64), np.diff(start))
+    pair = cells * max(len(rel), 1) + ids
+    assert len(np.unique(pair)) == len(pair)
+    def box_dist(c, p):
+        lo = origin + np.stack([c % G, (c // G) % G, c // (G * G)], 1).astype(np.float64) * h
+        d = np.maximum(np.maximum(lo - p, p - (lo + h)), 0.0)
+        return np.sqrt((d * d).sum(1))
+    if len(pts):
+        assert box_dist(cells, pts.astype(np.float64)).max() < reach + 1e-4
+    # completeness over the 7^3 cells around every collision point
+    if len(rel):
+        f = np.floor((rel.astype(np.float64) - origin) / h).astype(np.int64)
+        off = np.stack(np.meshgrid(*[np.arange(-3, 4)] * 3, indexing="ij"), -1).reshape(-1, 3)
+        cc = f[:, None, :] + off[None]
+        ok = np.all((cc >= 0) & (cc < G), -1)
+        cid = (cc[..., 2] * G + cc[..., 1]) * G + cc[..., 0]
+        pid = np.broadcast_to(np.arange(len(rel))[:, None], cid.shape)
+        cid, pid = cid[ok], pid[ok]
+        bd = box_dist(cid, rel.astype(np.float64)[pid])
+        need = bd < reach - 1e-4
+        assert np.all(np.isin(cid[need] * len(rel) + pid[need], pair))
 
 
 # ----------------------------------------------------------------- P2 / P5 sampled rollouts

@@ -70,7 +70,7 @@ def test_noalloc_rejects_sizes_beyond_its_array(aero):
     state = aero.state_struct(w.p0, w.q0, w.v0)
     for upd in [dict(K=4096), dict(T=65), dict(debug_samples=1),
                 dict(E=32, M_h=8, M_v=4, fine_az=256, pool_az=4, pool_el=8, fine_el=64),
-                dict(r_max=20.0)]:
+                dict(collision_set=1)]:
         P = dict(w.params, **upd)
         u = torch.zeros((P["E"], P["T"], 4), device=dev)
         ub, c, b = _outputs(P, dev)
