@@ -31,6 +31,7 @@ struct aero_planner {
   int* tile_sum = nullptr;
   int* tile_off = nullptr;
   float4* cand = nullptr;     // candidate entries
+  int2* grid_range = nullptr; // G^3 {first entry, count}
   int cand_cap = 0;
   int grid_max = kGridMax;    // cells per axis the grid arrays can hold
   float* partials = nullptr;
@@ -181,7 +182,7 @@ cudaError_t alloc(T** p, size_t count) {
 void free_all(aero_planner* pl) {
   void* ptrs[] = {pl->keys,     pl->coarse_win, pl->cells,        pl->anchors,  pl->guides,
                   pl->item_flag, pl->grid_count, pl->grid_local, pl->tile_sum, pl->tile_off,
-                  pl->cand,     pl->partials,
+                  pl->cand,     pl->grid_range, pl->partials,
                   pl->sample_costs, pl->dU,      pl->stage2_x, pl->counter,   pl->status,   pl->dbg_u,
                   pl->dbg_x,    pl->dbg_d,      pl->stage_cloud,      pl->stage_unom,   pl->stage_ubest,
                   pl->stage_cand,   pl->stage_best};
@@ -284,7 +285,7 @@ int enqueue_step(aero_planner* pl, const aero_state_t* x0, const float* cloud, i
   mark(1);
   if (prof) {
     prof->launches[AERO_STAGE_PARTITION] = n > 0 ? 1 : 0;
-    prof->launches[AERO_STAGE_GRID] = 2 + (n_items > 0 ? 2 : 0);
+    prof->launches[AERO_STAGE_GRID] = 3 + (n_items > 0 ? 2 : 0);
     prof->launches[AERO_STAGE_ROLLOUT] = p.iters;
     prof->launches[AERO_STAGE_UPDATE] = p.iters;
   }
@@ -338,6 +339,9 @@ int enqueue_step(aero_planner* pl, const aero_state_t* x0, const float* cloud, i
   if ((e = launch_scan_guides(ga, tab, s)) != cudaSuccess) return cuda_fail(e);
 
   if ((e = launch_cand_scatter(ca, s)) != cudaSuccess) return cuda_fail(e);
+  if ((e = launch_cell_ranges(pl->grid_local, pl->tile_off, gcells, grid.cap, pl->grid_range, s)) !=
+      cudaSuccess)
+    return cuda_fail(e);
   mark(2);
 
   CostParams cp{};
@@ -356,7 +360,7 @@ int enqueue_step(aero_planner* pl, const aero_state_t* x0, const float* cloud, i
   for (int i = 0; i < 3; ++i) cp.v_goal[i] = p.v_goal[i];
   for (int i = 0; i < 4; ++i) cp.q_goal[i] = p.q_goal[i];
   DynParams dp{p.dt, 1.0f / p.mass, p.g};
-  GridView gv{pl->grid_local, pl->tile_off, pl->cand, grid.G, grid.cap, grid.origin, grid.inv_h};
+  GridView gv{pl->grid_range, pl->cand, grid.G, grid.origin, grid.inv_h};
   float x0v[10] = {0.0f, 0.0f, 0.0f, x0->q[0], x0->q[1], x0->q[2], x0->q[3],
                    x0->v[0], x0->v[1], x0->v[2]};
   const int nb = (p.K + kRolloutThreads - 1) / kRolloutThreads;
@@ -512,6 +516,7 @@ int aero_create(const aero_limits_t* limits, aero_planner_t** out) {
   chk(alloc(&pl->tile_sum, kMaxTiles));
   chk(alloc(&pl->tile_off, kMaxTiles + 1));
   chk(alloc(&pl->cand, cap));
+  chk(alloc(&pl->grid_range, kGridCellsMax));
   chk(alloc(&pl->partials, (size_t)L.E_max * nbmax * (2 + 4 * L.T_max)));
   chk(alloc(&pl->sample_costs, (size_t)L.E_max * L.K_max));
   // the sampled perturbations are kept for the update when they take at most
@@ -747,7 +752,7 @@ const char* aero_status_str(int status) {
 // so such callers use aero_plan_step_noalloc instead: its workspace is carved
 // from g_noalloc_scratch, a file-scope device array that the CUDA loader sets
 // up with the module and that every GPU loading this library keeps until the
-// process exits.  Its size is fixed by the kNa* limits below (about 6.5 MB).
+// process exits.  Its size is fixed by the kNa* limits below (about 5.3 MB).
 // ---------------------------------------------------------------------------
 namespace {
 
@@ -764,6 +769,7 @@ constexpr size_t kNaBytes =
     align256(4 * 3 * kNaE) + align256(4 * 3 * (size_t)kNaE * kNaT) + align256(4 * (size_t)kNaPoints) +
     2 * align256(4 * ((size_t)kNaGridCells + 1)) + align256(4 * (size_t)kNaTiles) +
     align256(4 * ((size_t)kNaTiles + 1)) + align256(16 * (size_t)kNaCand) +
+    align256(8 * (size_t)kNaGridCells) +
     align256(4 * (size_t)kNaE * kNaNb * (2 + 4 * kNaT)) + align256(4 * (size_t)kNaE * kNaK) +
     align256(4 * (size_t)kNaE * (kNaT + 1) * 10) + align256(4) + align256(4);
 
@@ -815,6 +821,7 @@ void noalloc_carve(unsigned char* base, aero_planner& pl) {
   pl.tile_sum = reinterpret_cast<int*>(take(4 * (size_t)kNaTiles));
   pl.tile_off = reinterpret_cast<int*>(take(4 * ((size_t)kNaTiles + 1)));
   pl.cand = reinterpret_cast<float4*>(take(16 * (size_t)kNaCand));
+  pl.grid_range = reinterpret_cast<int2*>(take(8 * (size_t)kNaGridCells));
   pl.cand_cap = kNaCand;
   pl.grid_max = kNaGrid;
   pl.partials = reinterpret_cast<float*>(take(4 * (size_t)kNaE * kNaNb * (2 + 4 * kNaT)));

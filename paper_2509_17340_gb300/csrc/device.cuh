@@ -20,9 +20,10 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1
       k0 += 0x9E3779B9u;
       k1 += 0xBB67AE85u;
     }
-    const uint32_t hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
-    const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
-    c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+    const uint64_t p0 = (uint64_t)0xD2511F53u * c.x;  // one 32x32->64 multiply each
+    const uint64_t p1 = (uint64_t)0xCD9E8D57u * c.z;
+    c = make_uint4((uint32_t)(p1 >> 32) ^ c.y ^ k0, (uint32_t)p1, (uint32_t)(p0 >> 32) ^ c.w ^ k1,
+                   (uint32_t)p0);
   }
   return c;
 }
@@ -32,10 +33,13 @@ __device__ __forceinline__ float uniform01(uint32_t w) {
   return static_cast<float>(2u * (w >> 9) + 1u) * 5.9604644775390625e-8f;
 }
 
+// sqrt(x) for x >= 0 as x * rsqrt(x): a few ulp, three instructions.
+__device__ __forceinline__ float fast_sqrt(float x) { return x > 0.0f ? x * rsqrtf(x) : 0.0f; }
+
 // Four standard normals from one Philox block (Box-Muller on (u0,u1), (u2,u3)).
 __device__ __forceinline__ float4 normals4(uint4 w) {
-  const float ra = sqrtf(-2.0f * logf(uniform01(w.x)));
-  const float rb = sqrtf(-2.0f * logf(uniform01(w.z)));
+  const float ra = fast_sqrt(-2.0f * logf(uniform01(w.x)));
+  const float rb = fast_sqrt(-2.0f * logf(uniform01(w.z)));
   float sa, ca, sb, cb;
   sincospif(2.0f * uniform01(w.y), &sa, &ca);
   sincospif(2.0f * uniform01(w.w), &sb, &cb);
@@ -121,23 +125,17 @@ __device__ __forceinline__ void rk4_step(State& x, float4 u, const DynParams& dp
 // Collision queries on the candidate lists.  The list of the query's cell holds
 // every collision point closer than d_max to that cell's box, so the nearest
 // point, when closer than d_max, is in it.  Queries outside the grid are
-// farther than d_max from every point.  The result is the squared distance to
+// farther than d_max from every point.  Results are the squared distance to
 // the nearest point if that is below d_max^2, else d_max^2.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void cand_range(float px, float py, float pz, const GridView& g, int& s,
-                                           int& e) {
+__device__ __forceinline__ int2 cell_range(float px, float py, float pz, const GridView& g) {
   const float fx = (px - g.origin) * g.inv_h;
   const float fy = (py - g.origin) * g.inv_h;
   const float fz = (pz - g.origin) * g.inv_h;
-  s = e = 0;
   const float Gf = (float)g.G;
-  if (fx >= 0.0f && fy >= 0.0f && fz >= 0.0f && fx < Gf && fy < Gf && fz < Gf) {
-    const int c = ((int)fz * g.G + (int)fy) * g.G + (int)fx;
-    s = __ldg(g.local + c) + __ldg(g.tile_off + (c >> kScanTileShift));
-    e = __ldg(g.local + c + 1) + __ldg(g.tile_off + ((c + 1) >> kScanTileShift));
-    s = min(s, g.cap);  // an overflowed candidate array is reported by the status word
-    e = min(e, g.cap);
-  }
+  if (fx >= 0.0f && fy >= 0.0f && fz >= 0.0f && fx < Gf && fy < Gf && fz < Gf)
+    return __ldg(g.range + ((int)fz * g.G + (int)fy) * g.G + (int)fx);
+  return make_int2(0, 0);
 }
 
 __device__ __forceinline__ float dist2_to(const float4 q, float px, float py, float pz) {
@@ -148,40 +146,62 @@ __device__ __forceinline__ float dist2_to(const float4 q, float px, float py, fl
 // One thread, one query.
 __device__ __forceinline__ float nn_dist2(float px, float py, float pz, const GridView& g,
                                           float dmax2) {
-  int s, e;
-  cand_range(px, py, pz, g, s, e);
+  const int2 r = cell_range(px, py, pz, g);
   float best = dmax2;
-  for (int i = s; i < e; ++i) best = fminf(best, dist2_to(__ldg(g.pts + i), px, py, pz));
+  for (int i = 0; i < r.y; ++i) best = fminf(best, dist2_to(__ldg(g.pts + r.x + i), px, py, pz));
   return best;
 }
 
-// One query per lane; every lane of the warp must call.  Each lane scans up to
-// kLightCandidates of its own candidates; the rest of a longer list is scanned
-// by the whole warp, one such lane at a time, and reduced with a warp minimum.
-__device__ __forceinline__ float nn_dist2_warp(float px, float py, float pz, const GridView& g,
-                                               float dmax2, int lane) {
-  int s, e;
-  cand_range(px, py, pz, g, s, e);
-  float best = dmax2;
-  const int m = min(e - s, kLightCandidates);
-  for (int i = 0; i < m; ++i) best = fminf(best, dist2_to(__ldg(g.pts + s + i), px, py, pz));
-  unsigned heavy = __ballot_sync(0xffffffffu, e - s > kLightCandidates);
-  while (heavy) {
-    const int l = __ffs(heavy) - 1;
-    heavy &= heavy - 1;
-    const float qx = __shfl_sync(0xffffffffu, px, l);
-    const float qy = __shfl_sync(0xffffffffu, py, l);
-    const float qz = __shfl_sync(0xffffffffu, pz, l);
-    const int hs = __shfl_sync(0xffffffffu, s, l) + kLightCandidates;
-    const int he = __shfl_sync(0xffffffffu, e, l);
-    float b = dmax2;
-    for (int i = hs + lane; i < he; i += 32) b = fminf(b, dist2_to(__ldg(g.pts + i), qx, qy, qz));
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) b = fminf(b, __shfl_xor_sync(0xffffffffu, b, o));
-    if (lane == l) best = fminf(best, b);
-  }
-  return best;
+// Asynchronous 16-byte global -> shared copy (cp.async, cached in L1).
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const unsigned dst = static_cast<unsigned>(__cvta_generic_to_shared(smem));
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 16;\n" ::"r"(dst), "l"(gmem) : "memory");
 }
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+// One query per lane, all 32 lanes together, in two halves so that the memory
+// latency overlaps independent work: stage() lays the candidate lists of the 32
+// lanes end to end in the warp's shared buffer (an exclusive scan of the
+// counts) with asynchronous copies; scan() waits for them and gives each lane
+// the minimum over its own list.  Lists that do not fit in the buffer are read
+// from global memory instead.
+struct WarpQuery {
+  int n, start, excl;
+  bool staged;
+
+  __device__ __forceinline__ void stage(int2 r, int lane, float4* buf, const float4* pts) {
+    n = r.y;
+    start = r.x;
+    int incl = n;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += y;
+    }
+    const int total = __shfl_sync(0xffffffffu, incl, 31);
+    excl = incl - n;
+    staged = total <= kWarpStage;  // same for every lane
+    __syncwarp();                  // the previous step's scans are done with buf
+    if (staged) {
+      for (int i = 0; i < n; ++i) cp_async16(buf + excl + i, pts + start + i);
+      cp_async_commit();
+    }
+  }
+
+  // Each lane reads back only the entries it copied itself.
+  __device__ __forceinline__ float scan(const float4* buf, const float4* pts, float px, float py,
+                                        float pz, float dmax2) const {
+    float best = dmax2;
+    if (staged) {
+      cp_async_wait_all();
+      for (int i = 0; i < n; ++i) best = fminf(best, dist2_to(buf[excl + i], px, py, pz));
+    } else {
+      for (int i = 0; i < n; ++i) best = fminf(best, dist2_to(__ldg(pts + start + i), px, py, pz));
+    }
+    return best;
+  }
+};
 
 // Piecewise collision penalty from a squared distance (d >= d_max -> 0).
 __device__ __forceinline__ float jcol_from_d2(float d2, const CostParams& c, float dmax2) {
@@ -195,11 +215,11 @@ __device__ __forceinline__ float attitude_err(const float* q, const float* g) {
   const float r1 = -q[0] * g[1] + q[1] * g[0] - q[2] * g[3] + q[3] * g[2];
   const float r2 = -q[0] * g[2] + q[1] * g[3] + q[2] * g[0] - q[3] * g[1];
   const float r3 = -q[0] * g[3] - q[1] * g[2] + q[2] * g[1] + q[3] * g[0];
-  return 2.8284271247461903f * sqrtf(r1 * r1 + r2 * r2 + r3 * r3);
+  return 2.8284271247461903f * fast_sqrt(r1 * r1 + r2 * r2 + r3 * r3);
 }
 
 __device__ __forceinline__ float norm3f(float a, float b, float c) {
-  return sqrtf(a * a + b * b + c * c);
+  return fast_sqrt(a * a + b * b + c * c);
 }
 
 // Goal term of one step: Q_p |p - p_goal| + Q_v |v - v_goal| + Q_q ||R R_g^T - I||_F.

@@ -15,7 +15,7 @@ constexpr int kGridMax = 96;         // collision-grid cells per axis, at most
 constexpr int kScanTile = 4096;      // cells per scan tile (1024 threads x 4)
 constexpr int kScanTileShift = 12;
 constexpr int kRolloutThreads = 128; // samples per rollout CTA (one warp-group)
-constexpr int kLightCandidates = 4;  // candidates a lane checks alone; more go to the warp
+constexpr int kWarpStage = 256;     // candidate entries a warp stages in shared memory per step
 
 // Binary32 edge tables of the partition, passed by value to the kernels.
 // Azimuth edge k: theta_k = pi (2k - A) / A; elevation edge k: phi_k = lo +
@@ -93,12 +93,11 @@ struct GuideArgs {
   int ntiles;
 };
 
+// What the queries read: per cell {first entry, number of entries}.
 struct GridView {
-  const int* local;    // G^3 + 1: start of cell c = local[c] + tile_off[c >> kScanTileShift]
-  const int* tile_off;
+  const int2* range;   // G^3 cell ranges into pts
   const float4* pts;   // candidate entries, grouped by cell
   int G;
-  int cap;             // entries the array holds (reads are clamped to it)
   float origin, inv_h;
 };
 
@@ -156,6 +155,8 @@ cudaError_t launch_scan_tiles(int* count, int* local, int* tile_sum, int ncells,
                               cudaStream_t s);
 cudaError_t launch_scan_guides(const GuideArgs& a, const PartTables& t, cudaStream_t s);
 cudaError_t launch_cand_scatter(const CandArgs& a, cudaStream_t s);
+cudaError_t launch_cell_ranges(const int* local, const int* tile_off, int ncells, int cap,
+                               int2* range, cudaStream_t s);
 cudaError_t launch_rollout(const RolloutArgs& a, cudaStream_t s);
 cudaError_t launch_update(const UpdateArgs& a, cudaStream_t s);
 cudaError_t launch_philox(uint32_t k0, uint32_t k1, uint32_t c1, uint32_t c2, uint32_t c3,

@@ -365,6 +365,19 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_guides(GuideArgs a, PartT
     coarse_guides_block(a, t);
 }
 
+// ---------------------------------------------------------------------------
+// K2e: final {start, count} of every cell (the queries read one int2).
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_cell_ranges(const int* __restrict__ local,
+                                                     const int* __restrict__ tile_off, int ncells,
+                                                     int cap, int2* __restrict__ range) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= ncells) return;
+  const int s = min(local[c] + tile_off[c >> kScanTileShift], cap);
+  const int e = min(local[c + 1] + tile_off[(c + 1) >> kScanTileShift], cap);
+  range[c] = make_int2(s, e - s);
+}
+
 __global__ void k_philox(uint32_t k0, uint32_t k1, uint32_t c1, uint32_t c2, uint32_t c3,
                          int64_t n, uint4* out) {
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -406,6 +419,12 @@ cudaError_t launch_scan_guides(const GuideArgs& a, const PartTables& t, cudaStre
 cudaError_t launch_cand_scatter(const CandArgs& a, cudaStream_t s) {
   if (a.n_items == 0) return cudaSuccess;
   k_cand<true><<<blocks_for(a.n_items * 32, 256, 152 * 32), 256, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_cell_ranges(const int* local, const int* tile_off, int ncells, int cap,
+                               int2* range, cudaStream_t s) {
+  k_cell_ranges<<<blocks_for(ncells, 256, 1 << 24), 256, 0, s>>>(local, tile_off, ncells, cap, range);
   return cudaGetLastError();
 }
 

@@ -40,6 +40,7 @@ __global__ void __launch_bounds__(NT) k_rollout(RolloutArgs a) {
   __shared__ float s_gd[kMaxT * 3];
   __shared__ float s_red[NW];
   __shared__ float4 s_w[NW][kMaxT];
+  __shared__ float4 s_cand[NW][kWarpStage];
 
   const int e = blockIdx.y, b = blockIdx.x, tid = threadIdx.x;
   const int lane = tid & 31, wid = tid >> 5;
@@ -71,43 +72,69 @@ __global__ void __launch_bounds__(NT) k_rollout(RolloutArgs a) {
   }
 
   KahanSum S;
-  float4 u_prev = make_float4(0.f, 0.f, 0.f, 0.f);
+  // step j's control: prefetched noise, clamp, the stored perturbation, J_ctrl's
+  // terms Q_c |u_j|^2 (j <= T-2) and Q_cd |u_j - u_{j-1}|^2 (1 <= j <= T-2)
   float4 d_next = noise_delta(k, 0, e, a.ctr3, a.key0, a.key1, sigma);
-  for (int j = 0; j < T; ++j) {
-    const float4 un = s_un[j];
-    const float4 d = d_next;
-    // next step's noise does not depend on the state: computed here for ILP
-    if (j + 1 < T) d_next = noise_delta(k, j + 1, e, a.ctr3, a.key0, a.key1, sigma);
+  float4 un_next = s_un[0];
+  float4 u_prev = make_float4(0.f, 0.f, 0.f, 0.f);
+  auto control = [&](int j, float& c_ctrl) -> float4 {
+    const float4 un = un_next, d = d_next;
+    if (j + 1 < T) {
+      d_next = noise_delta(k, j + 1, e, a.ctr3, a.key0, a.key1, sigma);
+      un_next = s_un[j + 1];
+    }
     const float4 u = clamp4(make_float4(un.x + d.x, un.y + d.y, un.z + d.z, un.w + d.w), umin, umax);
     if (dU && active)
       dU[(size_t)j * a.K] = make_float4(u.x - un.x, u.y - un.y, u.z - un.z, u.w - un.w);
-    // J_ctrl: Q_c |u_j|^2 for j <= T-2, Q_cd |u_j - u_{j-1}|^2 for 1 <= j <= T-2
-    float c = 0.0f;
+    c_ctrl = 0.0f;
     if (j <= T - 2) {
-      c = cp.Q_c * (u.x * u.x + u.y * u.y + u.z * u.z + u.w * u.w);
+      c_ctrl = cp.Q_c * (u.x * u.x + u.y * u.y + u.z * u.z + u.w * u.w);
       if (j >= 1) {
         const float ax = u.x - u_prev.x, ay = u.y - u_prev.y, az = u.z - u_prev.z, aw = u.w - u_prev.w;
-        c += cp.Q_cd * (ax * ax + ay * ay + az * az + aw * aw);
+        c_ctrl += cp.Q_cd * (ax * ax + ay * ay + az * az + aw * aw);
       }
     }
     u_prev = u;
-    rk4_step(x, u, a.dyn);
-    // state terms at x_{j+1} against the guide at t = (j+1) dt
-    const float* g = s_gd + 3 * j;
-    c += cp.Q_track * norm3f(x.p[0] - g[0], x.p[1] - g[1], x.p[2] - g[2]);
+    return u;
+  };
+
+  // x holds x_j; its candidate range was loaded one iteration earlier, and its
+  // candidates are copied to shared memory while the next RK4 step runs
+  float c_ctrl;
+  float4 u_j = control(0, c_ctrl);
+  rk4_step(x, u_j, a.dyn);
+  int2 range = cell_range(x.p[0], x.p[1], x.p[2], a.grid);
+  for (int j = 1; j <= T; ++j) {
+    WarpQuery q;
+    q.stage(range, lane, s_cand[wid], a.grid.pts);
+    State xn = x;
+    float c_next = 0.0f;
+    float4 u_next = u_j;
+    if (j < T) {
+      u_next = control(j, c_next);
+      rk4_step(xn, u_next, a.dyn);
+      range = cell_range(xn.p[0], xn.p[1], xn.p[2], a.grid);
+    }
+    const float d2 = q.scan(s_cand[wid], a.grid.pts, x.p[0], x.p[1], x.p[2], dmax2);
+    // state terms at x_j against the guide at t = j dt
+    const float gx = s_gd[3 * (j - 1)], gy = s_gd[3 * (j - 1) + 1], gz = s_gd[3 * (j - 1) + 2];
+    float c = c_ctrl;
+    c += cp.Q_track * norm3f(x.p[0] - gx, x.p[1] - gy, x.p[2] - gz);
     c += cp.Q_vnorm * (x.v[0] * x.v[0] + x.v[1] * x.v[1] + x.v[2] * x.v[2]);
     c += goal_term(x, cp);
-    const float d2 = nn_dist2_warp(x.p[0], x.p[1], x.p[2], a.grid, dmax2, lane);
     c += jcol_from_d2(d2, cp, dmax2);
     S.add(c);
     if (dbg >= 0) {
-      reinterpret_cast<float4*>(a.dbg_u)[(size_t)dbg * T + j] = u;
-      float* X = a.dbg_x + ((size_t)dbg * (T + 1) + j + 1) * 10;
+      reinterpret_cast<float4*>(a.dbg_u)[(size_t)dbg * T + j - 1] = u_j;
+      float* X = a.dbg_x + ((size_t)dbg * (T + 1) + j) * 10;
       for (int i = 0; i < 3; ++i) X[i] = x.p[i];
       for (int i = 0; i < 4; ++i) X[3 + i] = x.q[i];
       for (int i = 0; i < 3; ++i) X[7 + i] = x.v[i];
-      a.dbg_d[(size_t)dbg * T + j] = d2 < dmax2 ? sqrtf(d2) : INFINITY;
+      a.dbg_d[(size_t)dbg * T + j - 1] = d2 < dmax2 ? sqrtf(d2) : INFINITY;
     }
+    x = xn;
+    u_j = u_next;
+    c_ctrl = c_next;
   }
   const float Sk = S.s;
   if (active) a.sample_costs[(size_t)e * a.K + k] = Sk;
