@@ -330,6 +330,7 @@ int enqueue_step(aero_planner* pl, const aero_state_t* x0, const float* cloud, i
   ga.v_end = p.v_end;
   for (int i = 0; i < 3; ++i) ga.v0[i] = x0->v[i];
   ga.coarse_win = pl->coarse_win;
+  ga.counter = pl->counter + 1;
   ga.cells = pl->cells;
   ga.anchors = pl->anchors;
   ga.guides = pl->guides;
@@ -517,14 +518,14 @@ int aero_create(const aero_limits_t* limits, aero_planner_t** out) {
   chk(alloc(&pl->tile_off, kMaxTiles + 1));
   chk(alloc(&pl->cand, cap));
   chk(alloc(&pl->grid_range, kGridCellsMax));
-  chk(alloc(&pl->partials, (size_t)L.E_max * nbmax * (2 + 4 * L.T_max)));
+  chk(alloc(&pl->partials, (size_t)L.E_max * nbmax * (4 + 4 * L.T_max)));
   chk(alloc(&pl->sample_costs, (size_t)L.E_max * L.K_max));
   // the sampled perturbations are kept for the update when they take at most
   // kMaxStoredPerturbationBytes; larger planners regenerate them from Philox
   const size_t du_bytes = sizeof(float4) * (size_t)L.E_max * L.K_max * L.T_max;
   if (du_bytes <= kMaxStoredPerturbationBytes) chk(alloc(&pl->dU, (size_t)L.E_max * L.K_max * L.T_max));
   chk(alloc(&pl->stage2_x, (size_t)L.E_max * (L.T_max + 1) * 10));
-  chk(alloc(&pl->counter, 1));
+  chk(alloc(&pl->counter, 2));
   chk(alloc(&pl->status, 1));
   chk(alloc(&pl->dbg_u, (size_t)L.E_max * D * L.T_max * 4));
   chk(alloc(&pl->dbg_x, (size_t)L.E_max * D * (L.T_max + 1) * 10));
@@ -534,7 +535,7 @@ int aero_create(const aero_limits_t* limits, aero_planner_t** out) {
   chk(alloc(&pl->stage_ubest, (size_t)L.T_max * 4));
   chk(alloc(&pl->stage_cand, L.E_max));
   chk(alloc(&pl->stage_best, 1));
-  if (e == cudaSuccess) e = cudaMemset(pl->counter, 0, sizeof(unsigned int));
+  if (e == cudaSuccess) e = cudaMemset(pl->counter, 0, 2 * sizeof(unsigned int));
   if (e == cudaSuccess) e = cudaMemset(pl->status, 0, sizeof(int));
   if (e == cudaSuccess) e = cudaDeviceSynchronize();
   if (e != cudaSuccess) {
@@ -770,7 +771,7 @@ constexpr size_t kNaBytes =
     2 * align256(4 * ((size_t)kNaGridCells + 1)) + align256(4 * (size_t)kNaTiles) +
     align256(4 * ((size_t)kNaTiles + 1)) + align256(16 * (size_t)kNaCand) +
     align256(8 * (size_t)kNaGridCells) +
-    align256(4 * (size_t)kNaE * kNaNb * (2 + 4 * kNaT)) + align256(4 * (size_t)kNaE * kNaK) +
+    align256(4 * (size_t)kNaE * kNaNb * (4 + 4 * kNaT)) + align256(4 * (size_t)kNaE * kNaK) +
     align256(4 * (size_t)kNaE * (kNaT + 1) * 10) + align256(4) + align256(4);
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNaBytes];
@@ -824,10 +825,10 @@ void noalloc_carve(unsigned char* base, aero_planner& pl) {
   pl.grid_range = reinterpret_cast<int2*>(take(8 * (size_t)kNaGridCells));
   pl.cand_cap = kNaCand;
   pl.grid_max = kNaGrid;
-  pl.partials = reinterpret_cast<float*>(take(4 * (size_t)kNaE * kNaNb * (2 + 4 * kNaT)));
+  pl.partials = reinterpret_cast<float*>(take(4 * (size_t)kNaE * kNaNb * (4 + 4 * kNaT)));
   pl.sample_costs = reinterpret_cast<float*>(take(4 * (size_t)kNaE * kNaK));
   pl.stage2_x = reinterpret_cast<float*>(take(4 * (size_t)kNaE * (kNaT + 1) * 10));
-  pl.counter = reinterpret_cast<unsigned int*>(take(4));
+  pl.counter = reinterpret_cast<unsigned int*>(take(8));
   pl.status = reinterpret_cast<int*>(take(4));
 }
 
@@ -857,8 +858,8 @@ int aero_plan_step_noalloc(const aero_state_t* x0, const float* cloud, int64_t n
   if (rc != AERO_OK) return rc;
   noalloc_carve(base, pl);
   cudaStream_t s = (cudaStream_t)stream;
-  // the selection ticket and the status word must start at zero
-  cudaError_t e = cudaMemsetAsync(pl.counter, 0, sizeof(unsigned int), s);
+  // the two last-block tickets and the status word must start at zero
+  cudaError_t e = cudaMemsetAsync(pl.counter, 0, 2 * sizeof(unsigned int), s);
   if (e == cudaSuccess) e = cudaMemsetAsync(pl.status, 0, sizeof(int), s);
   if (e != cudaSuccess) return AERO_ERR_CUDA;
   return enqueue_step(&pl, x0, cloud, n, goal, *params, u_nom, u_best, cand, best_idx, s);

@@ -84,6 +84,7 @@ struct GuideArgs {
   float v0[3];
   // outputs
   int* coarse_win;     // Ac * Ec
+  unsigned int* counter; // last-block ticket of the coarse blocks, 0 between launches
   int* cells;          // [0] goal fine cell, [1 + e] anchor coarse cell
   float* anchors;      // E x 3 (relative to p0)
   float* guides;       // E x T x 3 (relative to p0)
@@ -122,7 +123,7 @@ struct RolloutArgs {
   const float* u_nom;      // E x T x 4
   const float* guides;     // E x T x 3 (relative)
   GridView grid;
-  float* partials;         // E x nb x (2 + 4T)
+  float* partials;         // E x nb x (4 + 4T): rho, eta, 2 pad, W (16-byte aligned)
   float* sample_costs;     // E x K
   float4* dU;              // E x T x K clamped perturbations, or null: regenerate them
   int dbg_D;

@@ -239,27 +239,22 @@ __device__ void scan_tile_offsets(const int* tile_sum, int* tile_off, int ntiles
   if (threadIdx.x == 0) tile_off[ntiles] = s_carry;
 }
 
+// Blocks 1 .. gridDim.x-1: one warp per coarse cell.  The last of these blocks
+// to finish continues with the goal cone, anchors and guides.
 __device__ void coarse_guides_block(const GuideArgs& a, const PartTables& t) {
   __shared__ float s_ca[kMaxAz], s_sa[kMaxAz], s_ce[kMaxEl + 1], s_se[kMaxEl + 1];
   __shared__ float s_coef[kMaxE][3][6];
-  for (int i = threadIdx.x; i < a.A; i += blockDim.x) {
-    s_ca[i] = t.ca[i];
-    s_sa[i] = t.sa[i];
-  }
-  for (int i = threadIdx.x; i <= a.El; i += blockDim.x) {
-    s_ce[i] = t.ce[i];
-    s_se[i] = t.se[i];
-  }
-  __syncthreads();
+  __shared__ bool s_last;
   // coarse argmax (Eq. safe-vector): larger r, then nearer the coarse centre,
   // then lower fine index; empty cones count as r_max.
   const uint32_t empty_bits = __float_as_uint(a.rmax2);
   const int ncoarse = a.Ac * a.Ec;
-  const int lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
+  const int lane = threadIdx.x & 31, nwarp = (gridDim.x - 1) * (blockDim.x >> 5);
   const int npool = a.Pa * a.Pe;
   // one warp per coarse cell: each lane takes a strided share of the pooled
   // cones, then the warp reduces (r key, centre distance, fine index)
-  for (int cc = threadIdx.x >> 5; cc < ncoarse; cc += nwarp) {
+  for (int cc = (blockIdx.x - 1) * (blockDim.x >> 5) + (threadIdx.x >> 5); cc < ncoarse;
+       cc += nwarp) {
     const int I = cc % a.Ac, J = cc / a.Ac;
     uint32_t bkey = 0;
     int bdist = 0x7fffffff, best = 0x7fffffff;
@@ -288,6 +283,21 @@ __device__ void coarse_guides_block(const GuideArgs& a, const PartTables& t) {
     }
     if (lane == 0) a.coarse_win[cc] = best;
   }
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) s_last = atomicAdd(a.counter, 1u) == gridDim.x - 2;
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  for (int i = threadIdx.x; i < a.A; i += blockDim.x) {
+    s_ca[i] = t.ca[i];
+    s_sa[i] = t.sa[i];
+  }
+  for (int i = threadIdx.x; i <= a.El; i += blockDim.x) {
+    s_ce[i] = t.ce[i];
+    s_se[i] = t.se[i];
+  }
+  if (threadIdx.x == 0) *a.counter = 0u;
   __syncthreads();
   // goal cone and the M_h x M_v anchor cells around it (Sec. IV-B.1)
   __shared__ int s_goal;
@@ -306,16 +316,15 @@ __device__ void coarse_guides_block(const GuideArgs& a, const PartTables& t) {
     const int J = min(max(Jg + n - a.M_v / 2, 0), a.Ec - 1);
     const int cc = J * a.Ac + I;
     a.cells[1 + e] = cc;
-    // direction of the winning cone's centre (Eq. unit direction), binary64
-    const int w = a.coarse_win[cc];
+    // direction of the winning cone's centre (Eq. unit direction); the azimuth
+    // in units of pi is -1 + (2i + 1) / A
+    const int w = __ldcg(a.coarse_win + cc);
     const int i = w % a.A, j = w / a.A;
-    const double lo = (double)a.el_lo, hi = (double)a.el_hi;
-    const double al = -3.141592653589793 + (i + 0.5) * (2.0 * 3.141592653589793 / a.A);
-    const double be = lo + (j + 0.5) * ((hi - lo) / a.El);
-    double sa, ca, sb, cb;
-    sincos(al, &sa, &ca);
-    sincos(be, &sb, &cb);
-    const float db[3] = {(float)(cb * ca), (float)(cb * sa), (float)sb};
+    const float be = a.el_lo + (j + 0.5f) * ((a.el_hi - a.el_lo) / a.El);
+    float sa, ca, sb, cb;
+    sincospif(-1.0f + (float)(2 * i + 1) / (float)a.A, &sa, &ca);
+    sincosf(be, &sb, &cb);
+    const float db[3] = {cb * ca, cb * sa, sb};
     // anchor p_ref - p0 = ell R(q0) d (Eq. anchor-point)
     float pr[3];
 #pragma unroll
@@ -412,7 +421,9 @@ cudaError_t launch_scan_tiles(int* count, int* local, int* tile_sum, int ncells,
 }
 
 cudaError_t launch_scan_guides(const GuideArgs& a, const PartTables& t, cudaStream_t s) {
-  k_scan_guides<<<2, kScanThreads, 0, s>>>(a, t);
+  const int ncoarse = a.Ac * a.Ec;
+  const int coarse_blocks = (ncoarse + (kScanThreads / 32) - 1) / (kScanThreads / 32);
+  k_scan_guides<<<1 + coarse_blocks, kScanThreads, 0, s>>>(a, t);
   return cudaGetLastError();
 }
 

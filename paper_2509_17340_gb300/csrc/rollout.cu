@@ -84,8 +84,8 @@ __global__ void __launch_bounds__(NT) k_rollout(RolloutArgs a) {
       un_next = s_un[j + 1];
     }
     const float4 u = clamp4(make_float4(un.x + d.x, un.y + d.y, un.z + d.z, un.w + d.w), umin, umax);
-    if (dU && active)
-      dU[(size_t)j * a.K] = make_float4(u.x - un.x, u.y - un.y, u.z - un.z, u.w - un.w);
+    if (dU && active)  // streaming store: read once, by this thread, after the rollout
+      __stcs(dU + (size_t)j * a.K, make_float4(u.x - un.x, u.y - un.y, u.z - un.z, u.w - un.w));
     c_ctrl = 0.0f;
     if (j <= T - 2) {
       c_ctrl = cp.Q_c * (u.x * u.x + u.y * u.y + u.z * u.z + u.w * u.w);
@@ -155,7 +155,7 @@ __global__ void __launch_bounds__(NT) k_rollout(RolloutArgs a) {
   for (int j = 0; j < T; ++j) {
     float4 du;
     if (dU) {
-      du = active ? dU[(size_t)j * a.K] : make_float4(0.f, 0.f, 0.f, 0.f);
+      du = active ? __ldcs(dU + (size_t)j * a.K) : make_float4(0.f, 0.f, 0.f, 0.f);
     } else {
       const float4 un = s_un[j];
       const float4 d = noise_delta(k, j, e, a.ctr3, a.key0, a.key1, sigma);
@@ -166,7 +166,7 @@ __global__ void __launch_bounds__(NT) k_rollout(RolloutArgs a) {
     if ((lane & 7) == 0) reinterpret_cast<float*>(&s_w[wid][j])[lane >> 3] = r;
   }
   __syncthreads();
-  float* out = a.partials + ((size_t)e * a.nb + b) * (2 + 4 * T);
+  float* out = a.partials + ((size_t)e * a.nb + b) * (4 + 4 * T);
   if (tid == 0) {
     float eta = 0.0f;
 #pragma unroll
@@ -179,7 +179,7 @@ __global__ void __launch_bounds__(NT) k_rollout(RolloutArgs a) {
     float s = 0.0f;
 #pragma unroll
     for (int w = 0; w < NW; ++w) s += reinterpret_cast<const float*>(&s_w[w][j])[cc];
-    out[2 + i] = s;
+    out[4 + i] = s;
   }
 }
 
@@ -197,9 +197,10 @@ __global__ void __launch_bounds__(UT) k_update(UpdateArgs a) {
   __shared__ float4 s_u4[kMaxT];
   float* s_u = reinterpret_cast<float*>(s_u4);
   __shared__ float s_c[kMaxT];
+  __shared__ float4 s_acc[UT / 32][kMaxT];
   __shared__ bool s_last;
   const int e = blockIdx.x, tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-  const int T = a.T, stride = 2 + 4 * T;
+  const int T = a.T, stride = 4 + 4 * T;
   const float* P = a.partials + (size_t)e * a.nb * stride;
 
   // rho = min rho_b
@@ -227,14 +228,43 @@ __global__ void __launch_bounds__(UT) k_update(UpdateArgs a) {
     if (tid == 0) atomicOr(a.status, 1);
   }
   const float inv_eta = 1.0f / eta;
+  auto scale = [&](int b) {
+    return b < 1024 ? s_scale[b] : expf((rho - P[(size_t)b * stride]) * a.inv_lambda);
+  };
+  __syncthreads();  // s_scale complete
+  // sum_b scale_b W_b: warp w takes the rows b = w (mod 4), lane the float4
+  // columns lane, lane + 32, ...; all of a thread's loads are independent
+  constexpr int kCol = kMaxT / 32;
+  float4 acc[kCol];
+#pragma unroll
+  for (int q = 0; q < kCol; ++q) acc[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll 4
+  for (int b = wid; b < a.nb; b += UT / 32) {
+    const float sc = scale(b);
+    const float4* row = reinterpret_cast<const float4*>(P + (size_t)b * stride + 4);
+#pragma unroll
+    for (int q = 0; q < kCol; ++q) {
+      const int c4 = lane + 32 * q;
+      if (c4 < T) {
+        const float4 w4 = row[c4];
+        acc[q].x += sc * w4.x;
+        acc[q].y += sc * w4.y;
+        acc[q].z += sc * w4.z;
+        acc[q].w += sc * w4.w;
+      }
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < kCol; ++q)
+    if (lane + 32 * q < T) s_acc[wid][lane + 32 * q] = acc[q];
+  __syncthreads();
   float* un = a.u_nom + (size_t)e * T * 4;
   for (int i = tid; i < 4 * T; i += UT) {
-    float s = 0.0f;
-    for (int b = 0; b < a.nb; ++b) {
-      const float sc = b < 1024 ? s_scale[b] : expf((rho - P[(size_t)b * stride]) * a.inv_lambda);
-      s += sc * P[(size_t)b * stride + 2 + i];
-    }
-    const float v = un[i] + s * inv_eta;
+    const int j = i >> 2, c = i & 3;
+    float sum = 0.0f;
+#pragma unroll
+    for (int w = 0; w < UT / 32; ++w) sum += reinterpret_cast<const float*>(&s_acc[w][j])[c];
+    const float v = un[i] + sum * inv_eta;
     un[i] = v;
     s_u[i] = v;
   }
@@ -269,10 +299,12 @@ __global__ void __launch_bounds__(UT) k_update(UpdateArgs a) {
   }
   for (int i = tid; i < (T + 1) * 10; i += UT) a.stage2_x[(size_t)e * (T + 1) * 10 + i] = s_x[i];
   __syncthreads();
-  if (tid == 0) {
-    double s2 = 0.0;
-    for (int j = 0; j < T; ++j) s2 += (double)s_c[j];
-    a.cand[e] = (float)s2;
+  if (wid == 0) {
+    // S(2): fixed-order sum (strided per lane, then a shuffle tree)
+    float s2 = 0.0f;
+    for (int j = lane; j < T; j += 32) s2 += s_c[j];
+    s2 = warp_sum(s2);
+    if (lane == 0) a.cand[e] = s2;
   }
   // last CTA to arrive selects the best instance
   __threadfence();
@@ -282,16 +314,25 @@ __global__ void __launch_bounds__(UT) k_update(UpdateArgs a) {
   if (!s_last) return;
   __threadfence();
   __shared__ int s_best;
-  if (tid == 0) {
-    int best = 0;
-    float bc = __ldcg(a.cand);
-    for (int i = 1; i < a.E; ++i) {
+  if (wid == 0) {
+    // argmin over the instances, ties to the lower index (E <= 64: two per lane)
+    float bc = INFINITY;
+    int best = 0x7fffffff;
+    for (int i = lane; i < a.E; i += 32) {
       const float c = __ldcg(a.cand + i);
       if (c < bc) { bc = c; best = i; }
     }
-    s_best = best;
-    *a.best_idx = best;
-    *a.counter = 0u;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const float oc = __shfl_xor_sync(0xffffffffu, bc, o);
+      const int ob = __shfl_xor_sync(0xffffffffu, best, o);
+      if (oc < bc || (oc == bc && ob < best)) { bc = oc; best = ob; }
+    }
+    if (lane == 0) {
+      s_best = best;
+      *a.best_idx = best;
+      *a.counter = 0u;
+    }
   }
   __syncthreads();
   const float* ub = a.u_nom + (size_t)s_best * T * 4;
