@@ -69,6 +69,26 @@ def set_workload(name: str) -> None:
     WORKLOAD, METRIC = name, METRICS[name]
 
 
+def rank_seed(rank: int) -> int:
+    """Scene seed of a rank: every rank plans its own scene (weak scaling)."""
+    return rank
+
+
+def max_over_ranks(x: float, dist=None, device=None) -> float:
+    """The slowest rank's time (an all-reduce of the timing only, no data path)."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(P: dict, world: int, steps: int, seconds: float) -> float:
+    """Whole-job rollout-steps/s: the units all ranks processed over the slowest time."""
+    return world * rollout_steps(P) * steps / seconds
+
+
 def env_int(name, default):
     v = os.environ.get(name)
     return int(v) if v is not None else default
@@ -137,6 +157,23 @@ class ClockSampler:
                     reasons.add(n)
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
                 "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def rollout_traffic(workload: str):
+    """DRAM bytes per k_rollout launch from the committed ncu summary, or None
+    when the kernel's source changed since those counters were taken."""
+    import hashlib
+    p = os.path.join(ROOT, "profiles", "k_rollout_traffic.json")
+    try:
+        d = json.load(open(p))
+        h = hashlib.sha256()
+        for f in d["source_files"]:
+            h.update(open(os.path.join(ROOT, f), "rb").read())
+        if h.hexdigest() != d["source_sha256"]:
+            return None
+        return d["workloads"][workload]["bytes_per_launch"]
+    except Exception:
+        return None
 
 
 def measured_peaks() -> dict:
@@ -245,7 +282,7 @@ def main():
     build.build()
     from paper_2509_17340_gb300 import aero
 
-    w = I.make_workload(WORKLOAD, seed=rank)
+    w = I.make_workload(WORKLOAD, seed=rank_seed(rank))
     P = w.params
     dev = torch.device("cuda", local)
     stream = torch.cuda.Stream(device=dev)
@@ -293,11 +330,7 @@ def main():
             raise RuntimeError(f"planner status {st}")
     step_ms = [a.elapsed_time(b) for a, b in ev]
     stages = pl.profile_read()
-    total_ms = sum(step_ms)
-    if dist:
-        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(sum(step_ms), dist, dev)
 
     # end-to-end through the host-memory entry point (pinned buffers)
     e2e = None
@@ -320,12 +353,8 @@ def main():
             dt = time.perf_counter() - t0
             if i >= args.warmup:
                 times.append(dt)
-        e_tot = sum(times)
-        if dist:
-            t = torch.tensor([e_tot], dtype=torch.float64, device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e_tot = float(t.item())
-        e2e = {"value": world * rollout_steps(P) * len(times) / e_tot, "unit": UNIT,
+        e_tot = max_over_ranks(sum(times), dist, dev)
+        e2e = {"value": job_value(P, world, len(times), e_tot), "unit": UNIT,
                "h2d_bytes_per_step": hc.numel() * 4 + hu.numel() * 4,
                "d2h_bytes_per_step": hu.numel() * 4 + hb.numel() * 4 + hcand.numel() * 4 + 4,
                "ms_per_step": 1e3 * e_tot / len(times)}
@@ -335,7 +364,7 @@ def main():
             dist.destroy_process_group()
         return
 
-    value = world * rollout_steps(P) * args.steps / (total_ms / 1e3)
+    value = job_value(P, world, args.steps, total_ms / 1e3)
     clocks = clk.summary()
     peaks = measured_peaks()
     r_ms, r_n = stages["rollout"]
@@ -353,7 +382,7 @@ def main():
         "stage_ms_per_step": {k: v[0] / args.steps for k, v in stages.items()},
         "roofline": {"kernel": "k_rollout (fused noise + RK4 + S(1) + update partials)",
                      "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                     "frac": achieved / peak, "traffic": None,
+                     "frac": achieved / peak, "traffic": rollout_traffic(WORKLOAD),
                      "flops_per_launch": flops, "avg_launch_ms": r_avg_ms,
                      "peak_note": "FP32 FMA pipes: 152 SMs x 128 lanes x 2 x 2070 MHz (max SM clock)"},
         "clocks": clocks,
