@@ -214,10 +214,13 @@ int aero_get_debug(aero_planner_t* planner, int32_t what, void* dst, size_t byte
 int aero_sync_status(aero_planner_t* planner, void* stream);
 
 /* ---- stage timing --------------------------------------------------------
- * When enabled, aero_plan_step records CUDA events on its stream around its
- * stages; aero_profile_read synchronises them, adds the elapsed device times
- * since the last read into ms[AERO_STAGE_COUNT] and the number of kernel
- * launches per stage into launches[AERO_STAGE_COUNT], and starts over.
+ * aero_profile_enable(planner, stages): `stages` is a bitmask of
+ * (1 << AERO_STAGE_*); aero_plan_step then records a pair of CUDA events on its
+ * stream around each selected stage (every event costs a little device time,
+ * so select only the stages you need; 0 turns timing off).  aero_profile_read
+ * synchronises them, adds the elapsed device times since the last read into
+ * ms[AERO_STAGE_COUNT] and the number of kernel launches per timed stage into
+ * launches[AERO_STAGE_COUNT], and starts over.
  *   AERO_STAGE_PARTITION: workspace clears + fine partition (Sec. IV-A.1)
  *   AERO_STAGE_GRID: P_f / grid counts, coarse argmax + anchors + guides with the
  *                    grid scan, grid scatter (Sec. IV-A.2, IV-B)
@@ -228,7 +231,7 @@ int aero_sync_status(aero_planner_t* planner, void* stream);
 #define AERO_STAGE_ROLLOUT 2
 #define AERO_STAGE_UPDATE 3
 #define AERO_STAGE_COUNT 4
-int aero_profile_enable(aero_planner_t* planner, int on);
+int aero_profile_enable(aero_planner_t* planner, int stages);
 int aero_profile_read(aero_planner_t* planner, double* ms, int64_t* launches);
 
 /* Test hook for the noise generator (Sec. III-B): out[4i .. 4i+3] =

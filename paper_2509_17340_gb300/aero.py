@@ -231,9 +231,16 @@ class Planner:
         torch.cuda.synchronize()
         return buf
 
-    def profile(self, on: bool) -> None:
-        """Record per-stage CUDA events inside every following step."""
-        _check(_lib.aero_profile_enable(self._h, int(on)), "aero_profile_enable")
+    def profile(self, stages) -> None:
+        """Time the given stages (names from STAGES, True = all, False = none)
+        with CUDA events inside every following step."""
+        if stages is True:
+            mask = (1 << len(STAGES)) - 1
+        elif not stages:
+            mask = 0
+        else:
+            mask = sum(1 << STAGES.index(n) for n in stages)
+        _check(_lib.aero_profile_enable(self._h, mask), "aero_profile_enable")
 
     def profile_read(self) -> dict:
         """{stage: (device ms summed since the last read, kernel launches)}."""

@@ -57,11 +57,14 @@ struct aero_planner {
   int last_nb = 0;
   // stage timing (aero_profile_enable / aero_profile_read)
   struct ProfSlot {
-    std::vector<cudaEvent_t> ev;  // start, after partition, after grid, then 4 per iteration
+    // start/end of: partition, grid, then rollout and update of every iteration
+    std::vector<cudaEvent_t> ev;
     int iters = 0;
+    int mask = 0;
+    int last = -1;  // last event recorded
     int64_t launches[AERO_STAGE_COUNT] = {0, 0, 0, 0};
   };
-  bool prof = false;
+  int prof = 0;  // bitmask of timed stages
   std::vector<ProfSlot> slots;
   size_t slots_used = 0;
   double prof_ms[AERO_STAGE_COUNT] = {0, 0, 0, 0};
@@ -196,38 +199,43 @@ constexpr size_t kProfSlots = 512;
 cudaError_t prof_fold(aero_planner* pl) {
   for (size_t i = 0; i < pl->slots_used; ++i) {
     aero_planner::ProfSlot& sl = pl->slots[i];
-    cudaError_t e = cudaEventSynchronize(sl.ev[2 + 4 * sl.iters]);
+    if (sl.last < 0) continue;
+    cudaError_t e = cudaEventSynchronize(sl.ev[sl.last]);
     if (e != cudaSuccess) return e;
-    float ms = 0.0f;
-    cudaEventElapsedTime(&ms, sl.ev[0], sl.ev[1]);
-    pl->prof_ms[AERO_STAGE_PARTITION] += ms;
-    cudaEventElapsedTime(&ms, sl.ev[1], sl.ev[2]);
-    pl->prof_ms[AERO_STAGE_GRID] += ms;
+    auto add = [&](int stage, int a, int b) {
+      if (!(sl.mask & (1 << stage))) return;
+      float ms = 0.0f;
+      cudaEventElapsedTime(&ms, sl.ev[a], sl.ev[b]);
+      pl->prof_ms[stage] += ms;
+    };
+    add(AERO_STAGE_PARTITION, 0, 1);
+    add(AERO_STAGE_GRID, 2, 3);
     for (int it = 0; it < sl.iters; ++it) {
-      cudaEventElapsedTime(&ms, sl.ev[3 + 4 * it], sl.ev[4 + 4 * it]);
-      pl->prof_ms[AERO_STAGE_ROLLOUT] += ms;
-      cudaEventElapsedTime(&ms, sl.ev[5 + 4 * it], sl.ev[6 + 4 * it]);
-      pl->prof_ms[AERO_STAGE_UPDATE] += ms;
+      add(AERO_STAGE_ROLLOUT, 4 + 4 * it, 5 + 4 * it);
+      add(AERO_STAGE_UPDATE, 6 + 4 * it, 7 + 4 * it);
     }
-    for (int k = 0; k < AERO_STAGE_COUNT; ++k) pl->prof_launches[k] += sl.launches[k];
+    for (int k = 0; k < AERO_STAGE_COUNT; ++k)
+      if (sl.mask & (1 << k)) pl->prof_launches[k] += sl.launches[k];
   }
   pl->slots_used = 0;
   return cudaSuccess;
 }
 
-// A slot with 3 + 4 iters events, or nullptr when profiling is off.
+// A slot with 4 + 4 iters events, or nullptr when profiling is off.
 aero_planner::ProfSlot* prof_slot(aero_planner* pl, int iters) {
   if (!pl->prof) return nullptr;
   if (pl->slots_used == kProfSlots && prof_fold(pl) != cudaSuccess) return nullptr;
   if (pl->slots.size() < kProfSlots) pl->slots.resize(kProfSlots);
   aero_planner::ProfSlot& sl = pl->slots[pl->slots_used];
-  const size_t need = 3 + 4 * (size_t)iters;
+  const size_t need = 4 + 4 * (size_t)iters;
   while (sl.ev.size() < need) {
     cudaEvent_t ev;
     if (cudaEventCreate(&ev) != cudaSuccess) return nullptr;
     sl.ev.push_back(ev);
   }
   sl.iters = iters;
+  sl.mask = pl->prof;
+  sl.last = -1;
   for (int k = 0; k < AERO_STAGE_COUNT; ++k) sl.launches[k] = 0;
   ++pl->slots_used;
   return &sl;
@@ -260,10 +268,14 @@ int enqueue_step(aero_planner* pl, const aero_state_t* x0, const float* cloud, i
 
   cudaError_t e;
   aero_planner::ProfSlot* prof = prof_slot(pl, p.iters);
-  auto mark = [&](int i) {
-    if (prof) cudaEventRecord(prof->ev[i], s);
+  // event i of the slot, recorded only when its stage is timed
+  auto mark = [&](int stage, int i) {
+    if (prof && (prof->mask & (1 << stage))) {
+      cudaEventRecord(prof->ev[i], s);
+      prof->last = i;
+    }
   };
-  mark(0);
+  mark(AERO_STAGE_PARTITION, 0);
   if ((e = cudaMemsetAsync(pl->keys, 0xFF, sizeof(unsigned long long) * ncell, s)) != cudaSuccess)
     return cuda_fail(e);
   if ((e = cudaMemsetAsync(pl->grid_count, 0, sizeof(int) * (gcells + 1), s)) != cudaSuccess)
@@ -282,7 +294,8 @@ int enqueue_step(aero_planner* pl, const aero_state_t* x0, const float* cloud, i
   pa.keys = pl->keys;
   pa.item_flag = raw ? pl->item_flag : nullptr;
   if ((e = launch_partition(pa, tab, s)) != cudaSuccess) return cuda_fail(e);
-  mark(1);
+  mark(AERO_STAGE_PARTITION, 1);
+  mark(AERO_STAGE_GRID, 2);
   if (prof) {
     prof->launches[AERO_STAGE_PARTITION] = n > 0 ? 1 : 0;
     prof->launches[AERO_STAGE_GRID] = 3 + (n_items > 0 ? 2 : 0);
@@ -343,7 +356,7 @@ int enqueue_step(aero_planner* pl, const aero_state_t* x0, const float* cloud, i
   if ((e = launch_cell_ranges(pl->grid_local, pl->tile_off, gcells, grid.cap, pl->grid_range, s)) !=
       cudaSuccess)
     return cuda_fail(e);
-  mark(2);
+  mark(AERO_STAGE_GRID, 3);
 
   CostParams cp{};
   cp.Q_track = p.Q_track;
@@ -413,13 +426,13 @@ int enqueue_step(aero_planner* pl, const aero_state_t* x0, const float* cloud, i
 
   for (int it = 0; it < p.iters; ++it) {
     ra.ctr3 = (uint32_t)((p.step_id << 8) | (uint64_t)(uint32_t)it);
-    mark(3 + 4 * it);
+    mark(AERO_STAGE_ROLLOUT, 4 + 4 * it);
     if ((e = launch_rollout(ra, s)) != cudaSuccess) return cuda_fail(e);
-    mark(4 + 4 * it);
+    mark(AERO_STAGE_ROLLOUT, 5 + 4 * it);
     ua.final_stage = it == p.iters - 1;
-    mark(5 + 4 * it);
+    mark(AERO_STAGE_UPDATE, 6 + 4 * it);
     if ((e = launch_update(ua, s)) != cudaSuccess) return cuda_fail(e);
-    mark(6 + 4 * it);
+    mark(AERO_STAGE_UPDATE, 7 + 4 * it);
   }
 
   pl->have_step = true;
@@ -711,9 +724,9 @@ int aero_philox(uint64_t seed, uint32_t c1, uint32_t c2, uint32_t c3, int64_t n,
                                  (cudaStream_t)stream));
 }
 
-int aero_profile_enable(aero_planner_t* pl, int on) {
-  if (!pl) return AERO_ERR_INVALID_ARG;
-  pl->prof = on != 0;
+int aero_profile_enable(aero_planner_t* pl, int stages) {
+  if (!pl || stages < 0 || stages >= (1 << AERO_STAGE_COUNT)) return AERO_ERR_INVALID_ARG;
+  pl->prof = stages;
   return AERO_OK;
 }
 
