@@ -122,6 +122,8 @@ typedef struct {
   float v_goal[3];        /* goal velocity */
   float q_goal[4];        /* goal attitude (w, x, y, z) */
   int32_t debug_samples;  /* D: record rollouts of samples k < D (0 = off) */
+  int32_t lanes_per_sample; /* threads per sample in the rollout kernel: 0 = automatic
+                             (4 when E*K <= 32768, else 1), or 1 or 4 */
   uint64_t seed;          /* Philox key */
   uint64_t step_id;       /* enters the Philox counter: (k, j, e, (step_id << 8) | iter) */
 } aero_params_t;

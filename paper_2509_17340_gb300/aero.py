@@ -57,7 +57,7 @@ class Params(C.Structure):
         ("el_lo", C.c_float), ("el_hi", C.c_float),
         ("collision_set", C.c_int32),
         ("v_goal", C.c_float * 3), ("q_goal", C.c_float * 4),
-        ("debug_samples", C.c_int32),
+        ("debug_samples", C.c_int32), ("lanes_per_sample", C.c_int32),
         ("seed", C.c_uint64), ("step_id", C.c_uint64),
     ]
 
@@ -111,7 +111,7 @@ def default_params_struct() -> Params:
 def params_struct(d: dict) -> Params:
     """Marshal a parameter dictionary (``inputs.default_params`` keys)."""
     p = Params()
-    for k in ("E", "K", "T", "iters", "collision_set", "debug_samples"):
+    for k in ("E", "K", "T", "iters", "collision_set", "debug_samples", "lanes_per_sample"):
         setattr(p, k, int(d.get(k, 0)))
     for k in ("dt", "mass", "g", "Q_track", "Q_vnorm", "Q_c", "Q_cd", "Q_p", "Q_v", "Q_q",
               "C_col", "a_col", "d_min", "d_max", "r_max", "ell", "v_end", "el_lo", "el_hi"):

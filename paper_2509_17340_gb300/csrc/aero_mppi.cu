@@ -170,6 +170,8 @@ int validate(const aero_planner* pl, const aero_params_t* p, int64_t n_points) {
     if (!(p->u_min[c] <= p->u_max[c]) || !(p->sigma[c] >= 0)) return AERO_ERR_INVALID_ARG;
   if (p->collision_set != 0 && p->collision_set != 1) return AERO_ERR_INVALID_ARG;
   if (p->debug_samples < 0 || n_points < 0) return AERO_ERR_INVALID_ARG;
+  if (p->lanes_per_sample != 0 && p->lanes_per_sample != 1 && p->lanes_per_sample != 4)
+    return AERO_ERR_INVALID_ARG;
   if (p->E > L.E_max || p->K > L.K_max || p->T > L.T_max ||
       (int64_t)p->fine_az * p->fine_el > L.fine_cells_max || n_points > L.n_points_max ||
       p->debug_samples > L.debug_samples_max)
@@ -377,13 +379,17 @@ int enqueue_step(aero_planner* pl, const aero_state_t* x0, const float* cloud, i
   GridView gv{pl->grid_range, pl->cand, grid.G, grid.origin, grid.inv_h};
   float x0v[10] = {0.0f, 0.0f, 0.0f, x0->q[0], x0->q[1], x0->q[2], x0->q[3],
                    x0->v[0], x0->v[1], x0->v[2]};
-  const int nb = (p.K + kRolloutThreads - 1) / kRolloutThreads;
+  const int lanes = p.lanes_per_sample == 0 ? ((int64_t)p.E * p.K <= kQuadMaxSamples ? 4 : 1)
+                                            : p.lanes_per_sample;
+  const int per_cta = kRolloutThreads / lanes;
+  const int nb = (p.K + per_cta - 1) / per_cta;
 
   RolloutArgs ra{};
   ra.E = p.E;
   ra.K = p.K;
   ra.T = p.T;
   ra.nb = nb;
+  ra.lanes_per_sample = lanes;
   ra.inv_lambda = 1.0f / p.lambda;
   for (int c = 0; c < 4; ++c) {
     ra.sigma[c] = p.sigma[c];
@@ -508,7 +514,8 @@ int aero_create(const aero_limits_t* limits, aero_planner_t** out) {
   if (!pl) return AERO_ERR_ALLOC;
   pl->lim = L;
   cudaGetDevice(&pl->device);
-  const int64_t nbmax = (L.K_max + kRolloutThreads - 1) / kRolloutThreads;
+  // partial rows: one per rollout CTA, whose smallest sample count is 128 / 4
+  const int64_t nbmax = (L.K_max + kRolloutThreads / 4 - 1) / (kRolloutThreads / 4);
   const int64_t cap_fine = (int64_t)kFineDup * L.fine_cells_max;
   const int64_t cap_raw = (int64_t)kCoarseDup * L.n_points_max;
   int64_t cap = cap_fine > cap_raw ? cap_fine : cap_raw;
@@ -775,7 +782,7 @@ constexpr int64_t kNaPoints = 65536;
 constexpr int kNaGrid = 32, kNaGridCells = kNaGrid * kNaGrid * kNaGrid;
 constexpr int kNaTiles = (kNaGridCells + 1 + kScanTile - 1) / kScanTile;
 constexpr int kNaCand = 1 << 18;  // candidate entries: 27 per P_f point of 8192 cones
-constexpr int kNaNb = (kNaK + kRolloutThreads - 1) / kRolloutThreads;
+constexpr int kNaNb = (kNaK + kRolloutThreads / 4 - 1) / (kRolloutThreads / 4);
 
 constexpr size_t align256(size_t b) { return (b + 255) / 256 * 256; }
 constexpr size_t kNaBytes =

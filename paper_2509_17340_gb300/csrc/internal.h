@@ -16,6 +16,7 @@ constexpr int kScanTile = 4096;      // cells per scan tile (1024 threads x 4)
 constexpr int kScanTileShift = 12;
 constexpr int kRolloutThreads = 128; // samples per rollout CTA (one warp-group)
 constexpr int kWarpStage = 256;     // candidate entries a warp stages in shared memory per step
+constexpr int kQuadMaxSamples = 32768;  // E*K up to which four lanes carry one sample
 
 // Binary32 edge tables of the partition, passed by value to the kernels.
 // Azimuth edge k: theta_k = pi (2k - A) / A; elevation edge k: phi_k = lo +
@@ -114,6 +115,7 @@ struct DynParams {
 
 struct RolloutArgs {
   int E, K, T, nb;         // nb = CTAs per instance
+  int lanes_per_sample;    // 1, or 4 (k_rollout_quad) for small E*K
   float inv_lambda;
   float sigma[4], umin[4], umax[4];
   float x0[10];            // p = 0 (relative), q0, v0

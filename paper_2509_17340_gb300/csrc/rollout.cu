@@ -184,6 +184,210 @@ __global__ void __launch_bounds__(NT) k_rollout(RolloutArgs a) {
 }
 
 // ---------------------------------------------------------------------------
+// The same Stage I pass with four lanes per sample (a quad), for problems too
+// small to fill the GPU with one lane per sample.  The quad's lanes hold the
+// same state (RK4 and the clamp run on all four, with identical results) and
+// split the rest: lane q draws the perturbation of step 4m + q of every block of
+// four steps (one block ahead) and the quad shares it by shuffles; the lanes
+// scan every fourth candidate; each lane evaluates one group of cost terms
+// (q = 0: guide tracking, velocity norm, control; 1: goal position; 2: goal
+// velocity; 3: attitude and collision) and a butterfly sum, bitwise the same on
+// the four lanes, adds them; for the update lane q handles component q.
+// ---------------------------------------------------------------------------
+constexpr int QS = NT / 4;  // samples per CTA
+
+__global__ void __launch_bounds__(NT) k_rollout_quad(RolloutArgs a) {
+  __shared__ float4 s_un[kMaxT];
+  __shared__ float s_gd[kMaxT * 3];
+  __shared__ float s_red[NW];
+  __shared__ float4 s_w[NW][kMaxT];
+  __shared__ float4 s_cand[NW][kWarpStage];
+
+  const int e = blockIdx.y, b = blockIdx.x, tid = threadIdx.x;
+  const int lane = tid & 31, wid = tid >> 5, q = lane & 3, qbase = lane & ~3;
+  const int T = a.T;
+  for (int i = tid; i < T; i += NT) s_un[i] = reinterpret_cast<const float4*>(a.u_nom)[e * T + i];
+  for (int i = tid; i < 3 * T; i += NT) s_gd[i] = a.guides[e * T * 3 + i];
+  __syncthreads();
+
+  const int k = b * QS + (tid >> 2);
+  const bool active = k < a.K;
+  const CostParams& cp = a.cost;
+  const float dmax2 = cp.d_max * cp.d_max;
+  const int dbg = (active && q == 0 && k < a.dbg_D) ? (e * a.dbg_D + k) : -1;
+  const float4 sigma = make_float4(a.sigma[0], a.sigma[1], a.sigma[2], a.sigma[3]);
+  const float4 umin = make_float4(a.umin[0], a.umin[1], a.umin[2], a.umin[3]);
+  const float4 umax = make_float4(a.umax[0], a.umax[1], a.umax[2], a.umax[3]);
+  float* dUf = a.dU ? reinterpret_cast<float*>(a.dU + (size_t)e * T * a.K + k) + q : nullptr;
+
+  State x;
+#pragma unroll
+  for (int i = 0; i < 3; ++i) x.p[i] = a.x0[i];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) x.q[i] = a.x0[3 + i];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) x.v[i] = a.x0[7 + i];
+  if (dbg >= 0) {
+    float* X = a.dbg_x + (size_t)dbg * (T + 1) * 10;
+    for (int i = 0; i < 10; ++i) X[i] = a.x0[i];
+  }
+
+  // lane-specific cost weights
+  const float w_norm = q == 0 ? cp.Q_track : q == 1 ? cp.Q_p : q == 2 ? cp.Q_v : cp.Q_q;
+
+  KahanSum S;
+  float4 d_cur = make_float4(0.f, 0.f, 0.f, 0.f);
+  float4 d_nxt = q < T ? noise_delta(k, q, e, a.ctr3, a.key0, a.key1, sigma) : d_cur;
+  float4 u_prev = make_float4(0.f, 0.f, 0.f, 0.f);
+  auto control = [&](int j, float& c_ctrl) -> float4 {
+    if ((j & 3) == 0) {
+      d_cur = d_nxt;
+      if (j + 4 + q < T) d_nxt = noise_delta(k, j + 4 + q, e, a.ctr3, a.key0, a.key1, sigma);
+    }
+    const int src = qbase + (j & 3);
+    const float4 d = make_float4(__shfl_sync(0xffffffffu, d_cur.x, src),
+                                 __shfl_sync(0xffffffffu, d_cur.y, src),
+                                 __shfl_sync(0xffffffffu, d_cur.z, src),
+                                 __shfl_sync(0xffffffffu, d_cur.w, src));
+    const float4 un = s_un[j];
+    const float4 u = clamp4(make_float4(un.x + d.x, un.y + d.y, un.z + d.z, un.w + d.w), umin, umax);
+    if (dUf && active) {
+      const float du = q == 0 ? u.x - un.x : q == 1 ? u.y - un.y : q == 2 ? u.z - un.z : u.w - un.w;
+      __stcs(dUf + (size_t)j * a.K * 4, du);
+    }
+    c_ctrl = 0.0f;
+    if (j <= T - 2) {
+      c_ctrl = cp.Q_c * (u.x * u.x + u.y * u.y + u.z * u.z + u.w * u.w);
+      if (j >= 1) {
+        const float ax = u.x - u_prev.x, ay = u.y - u_prev.y, az = u.z - u_prev.z, aw = u.w - u_prev.w;
+        c_ctrl += cp.Q_cd * (ax * ax + ay * ay + az * az + aw * aw);
+      }
+    }
+    u_prev = u;
+    return u;
+  };
+
+  float c_ctrl;
+  float4 u_j = control(0, c_ctrl);
+  rk4_step(x, u_j, a.dyn);
+  int2 range = cell_range(x.p[0], x.p[1], x.p[2], a.grid);
+  float4* buf = s_cand[wid];
+  for (int j = 1; j <= T; ++j) {
+    // stage x_j's candidates: quads laid end to end, lane q copies every fourth
+    const int n = range.y;
+    int incl = n;
+#pragma unroll
+    for (int o = 4; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += y;
+    }
+    const int total = __shfl_sync(0xffffffffu, incl, 31);
+    const int excl = incl - n;
+    const bool staged = total <= kWarpStage;
+    __syncwarp();
+    if (staged) {
+      for (int i = q; i < n; i += 4) cp_async16(buf + excl + i, a.grid.pts + range.x + i);
+      cp_async_commit();
+    }
+    const int2 range_j = range;
+    State xn = x;
+    float c_next = 0.0f;
+    float4 u_next = u_j;
+    if (j < T) {
+      u_next = control(j, c_next);
+      rk4_step(xn, u_next, a.dyn);
+      range = cell_range(xn.p[0], xn.p[1], xn.p[2], a.grid);
+    }
+    float best = dmax2;
+    if (staged) {
+      cp_async_wait_all();
+      for (int i = q; i < n; i += 4) best = fminf(best, dist2_to(buf[excl + i], x.p[0], x.p[1], x.p[2]));
+    } else {
+      for (int i = q; i < n; i += 4)
+        best = fminf(best, dist2_to(__ldg(a.grid.pts + range_j.x + i), x.p[0], x.p[1], x.p[2]));
+    }
+    best = fminf(best, __shfl_xor_sync(0xffffffffu, best, 1));
+    const float d2 = fminf(best, __shfl_xor_sync(0xffffffffu, best, 2));
+    // this lane's cost terms at x_j (guide at t = j dt)
+    const float gx = s_gd[3 * (j - 1)], gy = s_gd[3 * (j - 1) + 1], gz = s_gd[3 * (j - 1) + 2];
+    const float* qg = cp.q_goal;
+    const float r1 = -x.q[0] * qg[1] + x.q[1] * qg[0] - x.q[2] * qg[3] + x.q[3] * qg[2];
+    const float r2 = -x.q[0] * qg[2] + x.q[1] * qg[3] + x.q[2] * qg[0] - x.q[3] * qg[1];
+    const float r3 = -x.q[0] * qg[3] - x.q[1] * qg[2] + x.q[2] * qg[1] + x.q[3] * qg[0];
+    float vx, vy, vz;
+    if (q == 0) { vx = x.p[0] - gx; vy = x.p[1] - gy; vz = x.p[2] - gz; }
+    else if (q == 1) { vx = x.p[0] - cp.goal_rel[0]; vy = x.p[1] - cp.goal_rel[1]; vz = x.p[2] - cp.goal_rel[2]; }
+    else if (q == 2) { vx = x.v[0] - cp.v_goal[0]; vy = x.v[1] - cp.v_goal[1]; vz = x.v[2] - cp.v_goal[2]; }
+    else { vx = r1; vy = r2; vz = r3; }
+    float c = w_norm * norm3f(vx, vy, vz);
+    if (q == 3) c = w_norm * 2.8284271247461903f * fast_sqrt(vx * vx + vy * vy + vz * vz) +
+                    jcol_from_d2(d2, cp, dmax2);
+    if (q == 0) c += cp.Q_vnorm * (x.v[0] * x.v[0] + x.v[1] * x.v[1] + x.v[2] * x.v[2]) + c_ctrl;
+    c += __shfl_xor_sync(0xffffffffu, c, 1);
+    c += __shfl_xor_sync(0xffffffffu, c, 2);
+    S.add(c);
+    if (dbg >= 0) {
+      reinterpret_cast<float4*>(a.dbg_u)[(size_t)dbg * T + j - 1] = u_j;
+      float* X = a.dbg_x + ((size_t)dbg * (T + 1) + j) * 10;
+      for (int i = 0; i < 3; ++i) X[i] = x.p[i];
+      for (int i = 0; i < 4; ++i) X[3 + i] = x.q[i];
+      for (int i = 0; i < 3; ++i) X[7 + i] = x.v[i];
+      a.dbg_d[(size_t)dbg * T + j - 1] = d2 < dmax2 ? sqrtf(d2) : INFINITY;
+    }
+    x = xn;
+    u_j = u_next;
+    c_ctrl = c_next;
+  }
+  const float Sk = S.s;
+  if (active && q == 0) a.sample_costs[(size_t)e * a.K + k] = Sk;
+
+  float m = warp_min(active ? Sk : INFINITY);
+  if (lane == 0) s_red[wid] = m;
+  __syncthreads();
+  float rho = s_red[0];
+#pragma unroll
+  for (int w = 1; w < NW; ++w) rho = fminf(rho, s_red[w]);
+  __syncthreads();
+  const float wk = active ? expf((rho - Sk) * a.inv_lambda) : 0.0f;
+  const float ws = warp_sum(q == 0 ? wk : 0.0f);
+  if (lane == 0) s_red[wid] = ws;
+
+  // W_b[j][q] = sum over the CTA's samples of w_k du_k[j][q]
+  for (int j = 0; j < T; ++j) {
+    float du;
+    if (dUf) {
+      du = active ? __ldcs(dUf + (size_t)j * a.K * 4) : 0.0f;
+    } else {
+      const float4 un = s_un[j];
+      const float4 d = noise_delta(k, j, e, a.ctr3, a.key0, a.key1, sigma);
+      const float4 u = clamp4(make_float4(un.x + d.x, un.y + d.y, un.z + d.z, un.w + d.w), umin, umax);
+      du = active ? (q == 0 ? u.x - un.x : q == 1 ? u.y - un.y : q == 2 ? u.z - un.z : u.w - un.w) : 0.0f;
+    }
+    float v = wk * du;
+    v += __shfl_xor_sync(0xffffffffu, v, 4);
+    v += __shfl_xor_sync(0xffffffffu, v, 8);
+    v += __shfl_xor_sync(0xffffffffu, v, 16);
+    if (lane < 4) reinterpret_cast<float*>(&s_w[wid][j])[lane] = v;
+  }
+  __syncthreads();
+  float* out = a.partials + ((size_t)e * a.nb + b) * (4 + 4 * T);
+  if (tid == 0) {
+    float eta = 0.0f;
+#pragma unroll
+    for (int w = 0; w < NW; ++w) eta += s_red[w];
+    out[0] = rho;
+    out[1] = eta;
+  }
+  for (int i = tid; i < 4 * T; i += NT) {
+    const int j = i >> 2, cc = i & 3;
+    float sum = 0.0f;
+#pragma unroll
+    for (int w = 0; w < NW; ++w) sum += reinterpret_cast<const float*>(&s_w[w][j])[cc];
+    out[4 + i] = sum;
+  }
+}
+
+// ---------------------------------------------------------------------------
 // Merge the per-CTA partials of one instance and update its nominal; on the
 // final iteration roll out the updated nominal (Stage II), score S(2), and let
 // the last CTA to finish pick the argmin.
@@ -343,7 +547,10 @@ __global__ void __launch_bounds__(UT) k_update(UpdateArgs a) {
 
 cudaError_t launch_rollout(const RolloutArgs& a, cudaStream_t s) {
   dim3 grid(a.nb, a.E);
-  k_rollout<<<grid, NT, 0, s>>>(a);
+  if (a.lanes_per_sample == 4)
+    k_rollout_quad<<<grid, NT, 0, s>>>(a);
+  else
+    k_rollout<<<grid, NT, 0, s>>>(a);
   return cudaGetLastError();
 }
 

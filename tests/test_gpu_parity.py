@@ -46,6 +46,9 @@ def _case(name):
     elif name == "ensemble_small":
         w = I.make_workload("ensemble")
         w.params.update(K=256, T=16)
+    elif name == "ensemble_small_l1":     # the one-lane-per-sample rollout kernel
+        w = I.make_workload("ensemble")
+        w.params.update(K=256, T=16, lanes_per_sample=1)
     elif name == "ragged":
         w = I.make_workload("plain", seed=3)
         rng = np.random.default_rng(3)
@@ -54,6 +57,9 @@ def _case(name):
         w.p0 = np.array([0.3, 0.2, 1.6], np.float32)
         w.params.update(E=2, M_h=2, M_v=1, K=200, T=7, iters=2, Q_track=15.0, step_id=77,
                         seed=0xDEADBEEF12345)
+    elif name == "ragged_l1":
+        w = _case("ragged")
+        w.params["lanes_per_sample"] = 1
     elif name == "raw":
         w = I.make_workload("ensemble")
         w.params.update(K=128, T=10, collision_set=1)
@@ -67,7 +73,8 @@ def _case(name):
     return w
 
 
-CASES = ["plain", "ensemble_small", "ensemble", "ragged", "raw", "empty"]
+CASES = ["plain", "ensemble_small", "ensemble_small_l1", "ensemble", "ragged", "ragged_l1", "raw",
+         "empty"]
 
 
 @pytest.fixture(scope="module")
@@ -379,13 +386,15 @@ def test_invalid_arguments_rejected(aero, planner):
 
 # ----------------------------------------------------------------- full-size large clutter, sampled
 
-def test_large_clutter_sampled(aero, orc):
+@pytest.mark.parametrize("lanes", [0, 4])
+def test_large_clutter_sampled(aero, orc, lanes):
     """200k-point clutter, E=32, K=8192, T=64 (the launch shape the benchmark
     uses for its largest workload): indices bit-exact, sampled costs, the update
     of two instances from the GPU costs, Stage II of all instances."""
     w = I.make_workload("large")
     P = w.params
     P["debug_samples"] = 4
+    P["lanes_per_sample"] = lanes
     pl = make_planner(aero, E=32, K=8192, T=64, cells=256 * 64, n=200_000, D=4)
     u0 = w.hover_nominal()
     g = run_gpu(aero, pl, w, P, u0)
