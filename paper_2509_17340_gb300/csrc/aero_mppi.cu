@@ -300,7 +300,7 @@ int enqueue_step(aero_planner* pl, const aero_state_t* x0, const float* cloud, i
   mark(AERO_STAGE_GRID, 2);
   if (prof) {
     prof->launches[AERO_STAGE_PARTITION] = n > 0 ? 1 : 0;
-    prof->launches[AERO_STAGE_GRID] = 3 + (n_items > 0 ? 2 : 0);
+    prof->launches[AERO_STAGE_GRID] = 3;
     prof->launches[AERO_STAGE_ROLLOUT] = p.iters;
     prof->launches[AERO_STAGE_UPDATE] = p.iters;
   }
@@ -318,10 +318,6 @@ int enqueue_step(aero_planner* pl, const aero_state_t* x0, const float* cloud, i
   ca.tile_off = pl->tile_off;
   ca.cand = pl->cand;
   ca.status = pl->status;
-  if ((e = launch_cand_count(ca, s)) != cudaSuccess) return cuda_fail(e);
-  if ((e = launch_scan_tiles(pl->grid_count, pl->grid_local, pl->tile_sum, gcells + 1, ntiles, s)) !=
-      cudaSuccess)
-    return cuda_fail(e);
 
   GuideArgs ga{};
   ga.keys = pl->keys;
@@ -349,15 +345,13 @@ int enqueue_step(aero_planner* pl, const aero_state_t* x0, const float* cloud, i
   ga.cells = pl->cells;
   ga.anchors = pl->anchors;
   ga.guides = pl->guides;
-  ga.tile_sum = pl->tile_sum;
-  ga.tile_off = pl->tile_off;
-  ga.ntiles = ntiles;
-  if ((e = launch_scan_guides(ga, tab, s)) != cudaSuccess) return cuda_fail(e);
-
-  if ((e = launch_cand_scatter(ca, s)) != cudaSuccess) return cuda_fail(e);
-  if ((e = launch_cell_ranges(pl->grid_local, pl->tile_off, gcells, grid.cap, pl->grid_range, s)) !=
-      cudaSuccess)
+  // count pass + coarse argmax/anchors/guides, scan, scatter + cell ranges
+  if ((e = launch_grid_count(ca, ga, tab, s)) != cudaSuccess) return cuda_fail(e);
+  if ((e = launch_grid_scan(pl->grid_count, pl->grid_local, pl->tile_sum, pl->tile_off, gcells + 1,
+                            ntiles, pl->counter + 2, s)) != cudaSuccess)
     return cuda_fail(e);
+
+  if ((e = launch_grid_scatter(ca, pl->grid_range, gcells, s)) != cudaSuccess) return cuda_fail(e);
   mark(AERO_STAGE_GRID, 3);
 
   CostParams cp{};
@@ -545,7 +539,7 @@ int aero_create(const aero_limits_t* limits, aero_planner_t** out) {
   const size_t du_bytes = sizeof(float4) * (size_t)L.E_max * L.K_max * L.T_max;
   if (du_bytes <= kMaxStoredPerturbationBytes) chk(alloc(&pl->dU, (size_t)L.E_max * L.K_max * L.T_max));
   chk(alloc(&pl->stage2_x, (size_t)L.E_max * (L.T_max + 1) * 10));
-  chk(alloc(&pl->counter, 2));
+  chk(alloc(&pl->counter, 3));
   chk(alloc(&pl->status, 1));
   chk(alloc(&pl->dbg_u, (size_t)L.E_max * D * L.T_max * 4));
   chk(alloc(&pl->dbg_x, (size_t)L.E_max * D * (L.T_max + 1) * 10));
@@ -555,7 +549,7 @@ int aero_create(const aero_limits_t* limits, aero_planner_t** out) {
   chk(alloc(&pl->stage_ubest, (size_t)L.T_max * 4));
   chk(alloc(&pl->stage_cand, L.E_max));
   chk(alloc(&pl->stage_best, 1));
-  if (e == cudaSuccess) e = cudaMemset(pl->counter, 0, 2 * sizeof(unsigned int));
+  if (e == cudaSuccess) e = cudaMemset(pl->counter, 0, 3 * sizeof(unsigned int));
   if (e == cudaSuccess) e = cudaMemset(pl->status, 0, sizeof(int));
   if (e == cudaSuccess) e = cudaDeviceSynchronize();
   if (e != cudaSuccess) {
@@ -848,7 +842,7 @@ void noalloc_carve(unsigned char* base, aero_planner& pl) {
   pl.partials = reinterpret_cast<float*>(take(4 * (size_t)kNaE * kNaNb * (4 + 4 * kNaT)));
   pl.sample_costs = reinterpret_cast<float*>(take(4 * (size_t)kNaE * kNaK));
   pl.stage2_x = reinterpret_cast<float*>(take(4 * (size_t)kNaE * (kNaT + 1) * 10));
-  pl.counter = reinterpret_cast<unsigned int*>(take(8));
+  pl.counter = reinterpret_cast<unsigned int*>(take(12));
   pl.status = reinterpret_cast<int*>(take(4));
 }
 
@@ -878,8 +872,8 @@ int aero_plan_step_noalloc(const aero_state_t* x0, const float* cloud, int64_t n
   if (rc != AERO_OK) return rc;
   noalloc_carve(base, pl);
   cudaStream_t s = (cudaStream_t)stream;
-  // the two last-block tickets and the status word must start at zero
-  cudaError_t e = cudaMemsetAsync(pl.counter, 0, 2 * sizeof(unsigned int), s);
+  // the three last-block tickets and the status word must start at zero
+  cudaError_t e = cudaMemsetAsync(pl.counter, 0, 3 * sizeof(unsigned int), s);
   if (e == cudaSuccess) e = cudaMemsetAsync(pl.status, 0, sizeof(int), s);
   if (e != cudaSuccess) return AERO_ERR_CUDA;
   return enqueue_step(&pl, x0, cloud, n, goal, *params, u_nom, u_best, cand, best_idx, s);

@@ -89,13 +89,8 @@ struct GuideArgs {
   int* cells;          // [0] goal fine cell, [1 + e] anchor coarse cell
   float* anchors;      // E x 3 (relative to p0)
   float* guides;       // E x T x 3 (relative to p0)
-  // block 0: exclusive scan of the tile totals of the candidate counts
-  const int* tile_sum;
-  int* tile_off;       // ntiles + 1 entries; tile_off[ntiles] = number of entries
-  int ntiles;
 };
 
-// What the queries read: per cell {first entry, number of entries}.
 struct GridView {
   const int2* range;   // G^3 cell ranges into pts
   const float4* pts;   // candidate entries, grouped by cell
@@ -153,13 +148,11 @@ struct UpdateArgs {
 };
 
 cudaError_t launch_partition(const PartitionArgs& a, const PartTables& t, cudaStream_t s);
-cudaError_t launch_cand_count(const CandArgs& a, cudaStream_t s);
-cudaError_t launch_scan_tiles(int* count, int* local, int* tile_sum, int ncells, int ntiles,
+cudaError_t launch_grid_count(const CandArgs& ca, const GuideArgs& ga, const PartTables& t,
                               cudaStream_t s);
-cudaError_t launch_scan_guides(const GuideArgs& a, const PartTables& t, cudaStream_t s);
-cudaError_t launch_cand_scatter(const CandArgs& a, cudaStream_t s);
-cudaError_t launch_cell_ranges(const int* local, const int* tile_off, int ncells, int cap,
-                               int2* range, cudaStream_t s);
+cudaError_t launch_grid_scan(int* count, int* local, int* tile_sum, int* tile_off, int ncells,
+                             int ntiles, unsigned int* counter, cudaStream_t s);
+cudaError_t launch_grid_scatter(const CandArgs& ca, int2* range, int ncells, cudaStream_t s);
 cudaError_t launch_rollout(const RolloutArgs& a, cudaStream_t s);
 cudaError_t launch_update(const UpdateArgs& a, cudaStream_t s);
 cudaError_t launch_philox(uint32_t k0, uint32_t k1, uint32_t c1, uint32_t c2, uint32_t c3,

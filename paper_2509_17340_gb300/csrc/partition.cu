@@ -126,13 +126,14 @@ __device__ __forceinline__ float gap2(float v, float lo, float h) {
 }
 
 // One warp per collision item; its lanes share the item's block of cells.
+// `block` / `nblocks`: this block's index within the blocks given to the pass.
 template <bool kScatter>
-__global__ void __launch_bounds__(256) k_cand(CandArgs a) {
+__device__ void cand_pass(const CandArgs& a, int block, int nblocks) {
   const int lane = threadIdx.x & 31;
-  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  const int64_t warps = (int64_t)nblocks * (blockDim.x >> 5);
   const GridGeom& g = a.grid;
   const float r2 = g.reach * g.reach;
-  for (int64_t it = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; it < a.n_items;
+  for (int64_t it = ((int64_t)block * blockDim.x + threadIdx.x) >> 5; it < a.n_items;
        it += warps) {
     float px, py, pz;
     if (!cand_item(a, it, px, py, pz)) continue;  // uniform across the warp
@@ -196,9 +197,32 @@ __device__ __forceinline__ int block_exclusive_scan(int v, int* s_warp, int& tot
   return r;
 }
 
-__global__ void __launch_bounds__(kScanThreads) k_scan_tiles(int* count, int* local, int* tile_sum,
-                                                             int ncells) {
+__device__ void scan_tile_offsets(const int* tile_sum, int* tile_off, int ntiles) {
   __shared__ int s_warp[32];
+  __shared__ int s_carry;
+  if (threadIdx.x == 0) s_carry = 0;
+  __syncthreads();
+  for (int base = 0; base < ntiles; base += kScanThreads) {
+    const int i = base + threadIdx.x;
+    const int v = i < ntiles ? __ldcg(tile_sum + i) : 0;
+    int total;
+    const int r = block_exclusive_scan(v, s_warp, total);
+    if (i < ntiles) tile_off[i] = s_carry + r;
+    __syncthreads();
+    if (threadIdx.x == 0) s_carry += total;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) tile_off[ntiles] = s_carry;
+}
+
+// K2b: tile-local exclusive scan of the counts (4096 cells per block, the
+// counts cleared for reuse as fill cursors by the scatter); the last block to
+// finish scans the tile totals into tile offsets.
+__global__ void __launch_bounds__(kScanThreads) k_grid_scan(int* count, int* local, int* tile_sum,
+                                                            int* tile_off, int ncells, int ntiles,
+                                                            unsigned int* counter) {
+  __shared__ int s_warp[32];
+  __shared__ bool s_last;
   const int i0 = blockIdx.x * kScanTile + 4 * threadIdx.x;
   int v[4];
 #pragma unroll
@@ -214,34 +238,19 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_tiles(int* count, int* lo
     run += v[u];
   }
   if (threadIdx.x == 0) tile_sum[blockIdx.x] = total;
-}
-
-// ---------------------------------------------------------------------------
-// K2c + K3: block 0 scans the tile totals into tile offsets; block 1 runs the
-// coarse argmax, the goal cone, the anchor cells, the anchors and the quintic
-// guides.
-// ---------------------------------------------------------------------------
-__device__ void scan_tile_offsets(const int* tile_sum, int* tile_off, int ntiles) {
-  __shared__ int s_warp[32];
-  __shared__ int s_carry;
-  if (threadIdx.x == 0) s_carry = 0;
+  __threadfence();
   __syncthreads();
-  for (int base = 0; base < ntiles; base += kScanThreads) {
-    const int i = base + threadIdx.x;
-    const int v = i < ntiles ? tile_sum[i] : 0;
-    int total;
-    const int r = block_exclusive_scan(v, s_warp, total);
-    if (i < ntiles) tile_off[i] = s_carry + r;
-    __syncthreads();
-    if (threadIdx.x == 0) s_carry += total;
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) tile_off[ntiles] = s_carry;
+  if (threadIdx.x == 0) s_last = atomicAdd(counter, 1u) == gridDim.x - 1;
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  if (threadIdx.x == 0) *counter = 0u;
+  scan_tile_offsets(tile_sum, tile_off, ntiles);
 }
 
-// Blocks 1 .. gridDim.x-1: one warp per coarse cell.  The last of these blocks
-// to finish continues with the goal cone, anchors and guides.
-__device__ void coarse_guides_block(const GuideArgs& a, const PartTables& t) {
+// `ncb` blocks, one warp per coarse cell; the last of them to finish continues
+// with the goal cone, anchors and guides.
+__device__ void coarse_guides_block(const GuideArgs& a, const PartTables& t, int cb, int ncb) {
   __shared__ float s_ca[kMaxAz], s_sa[kMaxAz], s_ce[kMaxEl + 1], s_se[kMaxEl + 1];
   __shared__ float s_coef[kMaxE][3][6];
   __shared__ bool s_last;
@@ -249,12 +258,11 @@ __device__ void coarse_guides_block(const GuideArgs& a, const PartTables& t) {
   // then lower fine index; empty cones count as r_max.
   const uint32_t empty_bits = __float_as_uint(a.rmax2);
   const int ncoarse = a.Ac * a.Ec;
-  const int lane = threadIdx.x & 31, nwarp = (gridDim.x - 1) * (blockDim.x >> 5);
+  const int lane = threadIdx.x & 31, nwarp = ncb * (blockDim.x >> 5);
   const int npool = a.Pa * a.Pe;
   // one warp per coarse cell: each lane takes a strided share of the pooled
   // cones, then the warp reduces (r key, centre distance, fine index)
-  for (int cc = (blockIdx.x - 1) * (blockDim.x >> 5) + (threadIdx.x >> 5); cc < ncoarse;
-       cc += nwarp) {
+  for (int cc = cb * (blockDim.x >> 5) + (threadIdx.x >> 5); cc < ncoarse; cc += nwarp) {
     const int I = cc % a.Ac, J = cc / a.Ac;
     uint32_t bkey = 0;
     int bdist = 0x7fffffff, best = 0x7fffffff;
@@ -285,7 +293,7 @@ __device__ void coarse_guides_block(const GuideArgs& a, const PartTables& t) {
   }
   __threadfence();
   __syncthreads();
-  if (threadIdx.x == 0) s_last = atomicAdd(a.counter, 1u) == gridDim.x - 2;
+  if (threadIdx.x == 0) s_last = atomicAdd(a.counter, 1u) == (unsigned)(ncb - 1);
   __syncthreads();
   if (!s_last) return;
   __threadfence();
@@ -367,23 +375,28 @@ __device__ void coarse_guides_block(const GuideArgs& a, const PartTables& t) {
   }
 }
 
-__global__ void __launch_bounds__(kScanThreads) k_scan_guides(GuideArgs a, PartTables t) {
-  if (blockIdx.x == 0)
-    scan_tile_offsets(a.tile_sum, a.tile_off, a.ntiles);
+// K2a + K3: the count pass of the candidate lists and, in the remaining blocks,
+// the coarse argmax, goal cone, anchors and guides (they need only the keys).
+__global__ void __launch_bounds__(256) k_grid_count(CandArgs ca, GuideArgs ga, PartTables t,
+                                                    int count_blocks) {
+  if ((int)blockIdx.x < count_blocks)
+    cand_pass<false>(ca, blockIdx.x, count_blocks);
   else
-    coarse_guides_block(a, t);
+    coarse_guides_block(ga, t, blockIdx.x - count_blocks, gridDim.x - count_blocks);
 }
 
-// ---------------------------------------------------------------------------
-// K2e: final {start, count} of every cell (the queries read one int2).
-// ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_cell_ranges(const int* __restrict__ local,
-                                                     const int* __restrict__ tile_off, int ncells,
-                                                     int cap, int2* __restrict__ range) {
-  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+// K2c: the scatter pass and, in the remaining blocks, the {start, count} of
+// every cell (which needs only the scan).
+__global__ void __launch_bounds__(256) k_grid_scatter(CandArgs ca, int scatter_blocks,
+                                                      int2* __restrict__ range, int ncells) {
+  if ((int)blockIdx.x < scatter_blocks) {
+    cand_pass<true>(ca, blockIdx.x, scatter_blocks);
+    return;
+  }
+  const int c = (blockIdx.x - scatter_blocks) * blockDim.x + threadIdx.x;
   if (c >= ncells) return;
-  const int s = min(local[c] + tile_off[c >> kScanTileShift], cap);
-  const int e = min(local[c + 1] + tile_off[(c + 1) >> kScanTileShift], cap);
+  const int s = min(ca.local[c] + ca.tile_off[c >> kScanTileShift], ca.grid.cap);
+  const int e = min(ca.local[c + 1] + ca.tile_off[(c + 1) >> kScanTileShift], ca.grid.cap);
   range[c] = make_int2(s, e - s);
 }
 
@@ -408,34 +421,25 @@ cudaError_t launch_partition(const PartitionArgs& a, const PartTables& t, cudaSt
   return cudaGetLastError();
 }
 
-cudaError_t launch_cand_count(const CandArgs& a, cudaStream_t s) {
-  if (a.n_items == 0) return cudaSuccess;
-  k_cand<false><<<blocks_for(a.n_items * 32, 256, 152 * 32), 256, 0, s>>>(a);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_scan_tiles(int* count, int* local, int* tile_sum, int ncells, int ntiles,
+cudaError_t launch_grid_count(const CandArgs& ca, const GuideArgs& ga, const PartTables& t,
                               cudaStream_t s) {
-  k_scan_tiles<<<ntiles, kScanThreads, 0, s>>>(count, local, tile_sum, ncells);
+  const int count_blocks = ca.n_items > 0 ? blocks_for(ca.n_items * 32, 256, 152 * 32) : 0;
+  const int coarse_blocks = (ga.Ac * ga.Ec + 7) / 8;  // 8 warps per block
+  k_grid_count<<<count_blocks + coarse_blocks, 256, 0, s>>>(ca, ga, t, count_blocks);
   return cudaGetLastError();
 }
 
-cudaError_t launch_scan_guides(const GuideArgs& a, const PartTables& t, cudaStream_t s) {
-  const int ncoarse = a.Ac * a.Ec;
-  const int coarse_blocks = (ncoarse + (kScanThreads / 32) - 1) / (kScanThreads / 32);
-  k_scan_guides<<<1 + coarse_blocks, kScanThreads, 0, s>>>(a, t);
+cudaError_t launch_grid_scan(int* count, int* local, int* tile_sum, int* tile_off, int ncells,
+                             int ntiles, unsigned int* counter, cudaStream_t s) {
+  k_grid_scan<<<ntiles, kScanThreads, 0, s>>>(count, local, tile_sum, tile_off, ncells, ntiles,
+                                               counter);
   return cudaGetLastError();
 }
 
-cudaError_t launch_cand_scatter(const CandArgs& a, cudaStream_t s) {
-  if (a.n_items == 0) return cudaSuccess;
-  k_cand<true><<<blocks_for(a.n_items * 32, 256, 152 * 32), 256, 0, s>>>(a);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_cell_ranges(const int* local, const int* tile_off, int ncells, int cap,
-                               int2* range, cudaStream_t s) {
-  k_cell_ranges<<<blocks_for(ncells, 256, 1 << 24), 256, 0, s>>>(local, tile_off, ncells, cap, range);
+cudaError_t launch_grid_scatter(const CandArgs& ca, int2* range, int ncells, cudaStream_t s) {
+  const int scatter_blocks = ca.n_items > 0 ? blocks_for(ca.n_items * 32, 256, 152 * 32) : 0;
+  const int range_blocks = (ncells + 255) / 256;
+  k_grid_scatter<<<scatter_blocks + range_blocks, 256, 0, s>>>(ca, scatter_blocks, range, ncells);
   return cudaGetLastError();
 }
 
