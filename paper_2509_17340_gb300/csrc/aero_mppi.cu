@@ -26,7 +26,9 @@ struct aero_planner {
   float* anchors = nullptr;
   float* guides = nullptr;
   int* item_flag = nullptr;   // per point: kept by the partition (collision set = kept points)
-  int* grid_count = nullptr;  // G^3 + 1 candidate counts, then fill cursors
+  int* grid_count = nullptr;  // G^3 + 1 candidate counts, zero between steps
+  int* grid_fill = nullptr;   // G^3 + 1 fill cursors of the scatter
+  bool grid_dirty = true;     // counts possibly non-zero (new planner, interrupted step)
   int* grid_local = nullptr;  // G^3 + 1 tile-local exclusive prefix
   int* tile_sum = nullptr;
   int* tile_off = nullptr;
@@ -34,6 +36,7 @@ struct aero_planner {
   int2* grid_range = nullptr; // G^3 {first entry, count}
   int cand_cap = 0;
   int grid_max = kGridMax;    // cells per axis the grid arrays can hold
+  int grid_cells_cap = kGridMax * kGridMax * kGridMax;
   float* partials = nullptr;
   float* sample_costs = nullptr;
   float4* dU = nullptr;       // sampled perturbations, when the planner is small enough
@@ -186,7 +189,8 @@ cudaError_t alloc(T** p, size_t count) {
 
 void free_all(aero_planner* pl) {
   void* ptrs[] = {pl->keys,     pl->coarse_win, pl->cells,        pl->anchors,  pl->guides,
-                  pl->item_flag, pl->grid_count, pl->grid_local, pl->tile_sum, pl->tile_off,
+                  pl->item_flag, pl->grid_count, pl->grid_fill, pl->grid_local, pl->tile_sum,
+                  pl->tile_off,
                   pl->cand,     pl->grid_range, pl->partials,
                   pl->sample_costs, pl->dU,      pl->stage2_x, pl->counter,   pl->status,   pl->dbg_u,
                   pl->dbg_x,    pl->dbg_d,      pl->stage_cloud,      pl->stage_unom,   pl->stage_ubest,
@@ -280,8 +284,14 @@ int enqueue_step(aero_planner* pl, const aero_state_t* x0, const float* cloud, i
   mark(AERO_STAGE_PARTITION, 0);
   if ((e = cudaMemsetAsync(pl->keys, 0xFF, sizeof(unsigned long long) * ncell, s)) != cudaSuccess)
     return cuda_fail(e);
-  if ((e = cudaMemsetAsync(pl->grid_count, 0, sizeof(int) * (gcells + 1), s)) != cudaSuccess)
-    return cuda_fail(e);
+  if (pl->grid_dirty) {
+    // the scan leaves the counts at zero; clear them only when a step may have
+    // stopped between the count pass and the scan
+    if ((e = cudaMemsetAsync(pl->grid_count, 0, sizeof(int) * (pl->grid_cells_cap + 1), s)) !=
+        cudaSuccess)
+      return cuda_fail(e);
+  }
+  pl->grid_dirty = true;
 
   PartitionArgs pa{};
   pa.cloud = cloud;
@@ -314,6 +324,7 @@ int enqueue_step(aero_planner* pl, const aero_state_t* x0, const float* cloud, i
   ca.raw = raw;
   ca.grid = grid;
   ca.count = pl->grid_count;
+  ca.fill = pl->grid_fill;
   ca.local = pl->grid_local;
   ca.tile_off = pl->tile_off;
   ca.cand = pl->cand;
@@ -347,8 +358,8 @@ int enqueue_step(aero_planner* pl, const aero_state_t* x0, const float* cloud, i
   ga.guides = pl->guides;
   // count pass + coarse argmax/anchors/guides, scan, scatter + cell ranges
   if ((e = launch_grid_count(ca, ga, tab, s)) != cudaSuccess) return cuda_fail(e);
-  if ((e = launch_grid_scan(pl->grid_count, pl->grid_local, pl->tile_sum, pl->tile_off, gcells + 1,
-                            ntiles, pl->counter + 2, s)) != cudaSuccess)
+  if ((e = launch_grid_scan(pl->grid_count, pl->grid_fill, pl->grid_local, pl->tile_sum,
+                            pl->tile_off, gcells + 1, ntiles, pl->counter + 2, s)) != cudaSuccess)
     return cuda_fail(e);
 
   if ((e = launch_grid_scatter(ca, pl->grid_range, gcells, s)) != cudaSuccess) return cuda_fail(e);
@@ -435,6 +446,7 @@ int enqueue_step(aero_planner* pl, const aero_state_t* x0, const float* cloud, i
     mark(AERO_STAGE_UPDATE, 7 + 4 * it);
   }
 
+  pl->grid_dirty = false;
   pl->have_step = true;
   pl->last = p;
   pl->last_grid = grid;
@@ -527,6 +539,7 @@ int aero_create(const aero_limits_t* limits, aero_planner_t** out) {
   chk(alloc(&pl->guides, (size_t)L.E_max * L.T_max * 3));
   chk(alloc(&pl->item_flag, L.n_points_max));
   chk(alloc(&pl->grid_count, kGridCellsMax + 1));
+  chk(alloc(&pl->grid_fill, kGridCellsMax + 1));
   chk(alloc(&pl->grid_local, kGridCellsMax + 1));
   chk(alloc(&pl->tile_sum, kMaxTiles));
   chk(alloc(&pl->tile_off, kMaxTiles + 1));
@@ -782,7 +795,7 @@ constexpr size_t align256(size_t b) { return (b + 255) / 256 * 256; }
 constexpr size_t kNaBytes =
     align256(8 * (size_t)kNaCells) + align256(4 * (size_t)kNaCells) + align256(4 * (kNaE + 1)) +
     align256(4 * 3 * kNaE) + align256(4 * 3 * (size_t)kNaE * kNaT) + align256(4 * (size_t)kNaPoints) +
-    2 * align256(4 * ((size_t)kNaGridCells + 1)) + align256(4 * (size_t)kNaTiles) +
+    3 * align256(4 * ((size_t)kNaGridCells + 1)) + align256(4 * (size_t)kNaTiles) +
     align256(4 * ((size_t)kNaTiles + 1)) + align256(16 * (size_t)kNaCand) +
     align256(8 * (size_t)kNaGridCells) +
     align256(4 * (size_t)kNaE * kNaNb * (4 + 4 * kNaT)) + align256(4 * (size_t)kNaE * kNaK) +
@@ -832,6 +845,7 @@ void noalloc_carve(unsigned char* base, aero_planner& pl) {
   pl.guides = reinterpret_cast<float*>(take(4 * 3 * (size_t)kNaE * kNaT));
   pl.item_flag = reinterpret_cast<int*>(take(4 * (size_t)kNaPoints));
   pl.grid_count = reinterpret_cast<int*>(take(4 * ((size_t)kNaGridCells + 1)));
+  pl.grid_fill = reinterpret_cast<int*>(take(4 * ((size_t)kNaGridCells + 1)));
   pl.grid_local = reinterpret_cast<int*>(take(4 * ((size_t)kNaGridCells + 1)));
   pl.tile_sum = reinterpret_cast<int*>(take(4 * (size_t)kNaTiles));
   pl.tile_off = reinterpret_cast<int*>(take(4 * ((size_t)kNaTiles + 1)));
@@ -839,6 +853,7 @@ void noalloc_carve(unsigned char* base, aero_planner& pl) {
   pl.grid_range = reinterpret_cast<int2*>(take(8 * (size_t)kNaGridCells));
   pl.cand_cap = kNaCand;
   pl.grid_max = kNaGrid;
+  pl.grid_cells_cap = kNaGridCells;
   pl.partials = reinterpret_cast<float*>(take(4 * (size_t)kNaE * kNaNb * (4 + 4 * kNaT)));
   pl.sample_costs = reinterpret_cast<float*>(take(4 * (size_t)kNaE * kNaK));
   pl.stage2_x = reinterpret_cast<float*>(take(4 * (size_t)kNaE * (kNaT + 1) * 10));

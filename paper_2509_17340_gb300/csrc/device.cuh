@@ -160,49 +160,6 @@ __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
-// One query per lane, all 32 lanes together, in two halves so that the memory
-// latency overlaps independent work: stage() lays the candidate lists of the 32
-// lanes end to end in the warp's shared buffer (an exclusive scan of the
-// counts) with asynchronous copies; scan() waits for them and gives each lane
-// the minimum over its own list.  Lists that do not fit in the buffer are read
-// from global memory instead.
-struct WarpQuery {
-  int n, start, excl;
-  bool staged;
-
-  __device__ __forceinline__ void stage(int2 r, int lane, float4* buf, const float4* pts) {
-    n = r.y;
-    start = r.x;
-    int incl = n;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const int y = __shfl_up_sync(0xffffffffu, incl, o);
-      if (lane >= o) incl += y;
-    }
-    const int total = __shfl_sync(0xffffffffu, incl, 31);
-    excl = incl - n;
-    staged = total <= kWarpStage;  // same for every lane
-    __syncwarp();                  // the previous step's scans are done with buf
-    if (staged) {
-      for (int i = 0; i < n; ++i) cp_async16(buf + excl + i, pts + start + i);
-      cp_async_commit();
-    }
-  }
-
-  // Each lane reads back only the entries it copied itself.
-  __device__ __forceinline__ float scan(const float4* buf, const float4* pts, float px, float py,
-                                        float pz, float dmax2) const {
-    float best = dmax2;
-    if (staged) {
-      cp_async_wait_all();
-      for (int i = 0; i < n; ++i) best = fminf(best, dist2_to(buf[excl + i], px, py, pz));
-    } else {
-      for (int i = 0; i < n; ++i) best = fminf(best, dist2_to(__ldg(pts + start + i), px, py, pz));
-    }
-    return best;
-  }
-};
-
 // Piecewise collision penalty from a squared distance (d >= d_max -> 0).
 __device__ __forceinline__ float jcol_from_d2(float d2, const CostParams& c, float dmax2) {
   if (!(d2 < dmax2)) return 0.0f;

@@ -62,7 +62,8 @@ struct CandArgs {
   int64_t n_items;
   int raw;
   GridGeom grid;
-  int* count;          // G^3 + 1: entries per cell (count pass); fill cursor (scatter pass)
+  int* count;          // G^3 + 1: entries per cell (count pass); zero between steps
+  int* fill;           // G^3 + 1: fill cursors of the scatter pass; zeroed by the scan
   const int* local;    // tile-local exclusive prefix of the counts (scatter pass)
   const int* tile_off; // exclusive prefix of the tile totals (scatter pass)
   float4* cand;        // candidate entries (scatter pass)
@@ -150,8 +151,8 @@ struct UpdateArgs {
 cudaError_t launch_partition(const PartitionArgs& a, const PartTables& t, cudaStream_t s);
 cudaError_t launch_grid_count(const CandArgs& ca, const GuideArgs& ga, const PartTables& t,
                               cudaStream_t s);
-cudaError_t launch_grid_scan(int* count, int* local, int* tile_sum, int* tile_off, int ncells,
-                             int ntiles, unsigned int* counter, cudaStream_t s);
+cudaError_t launch_grid_scan(int* count, int* fill, int* local, int* tile_sum, int* tile_off,
+                             int ncells, int ntiles, unsigned int* counter, cudaStream_t s);
 cudaError_t launch_grid_scatter(const CandArgs& ca, int2* range, int ncells, cudaStream_t s);
 cudaError_t launch_rollout(const RolloutArgs& a, cudaStream_t s);
 cudaError_t launch_update(const UpdateArgs& a, cudaStream_t s);

@@ -155,7 +155,7 @@ __device__ void cand_pass(const CandArgs& a, int block, int nblocks) {
       if (!kScatter) {
         atomicAdd(a.count + c, 1);
       } else {
-        const int pos = a.local[c] + a.tile_off[c >> kScanTileShift] + atomicAdd(a.count + c, 1);
+        const int pos = a.local[c] + a.tile_off[c >> kScanTileShift] + atomicAdd(a.fill + c, 1);
         if (pos < g.cap)
           a.cand[pos] = make_float4(px, py, pz, 0.0f);
         else
@@ -218,29 +218,45 @@ __device__ void scan_tile_offsets(const int* tile_sum, int* tile_off, int ntiles
 // K2b: tile-local exclusive scan of the counts (4096 cells per block, the
 // counts cleared for reuse as fill cursors by the scatter); the last block to
 // finish scans the tile totals into tile offsets.
-__global__ void __launch_bounds__(kScanThreads) k_grid_scan(int* count, int* local, int* tile_sum,
-                                                            int* tile_off, int ncells, int ntiles,
-                                                            unsigned int* counter) {
+__global__ void __launch_bounds__(kScanThreads) k_grid_scan(int* count, int* fill, int* local,
+                                                            int* tile_sum, int* tile_off, int ncells,
+                                                            int ntiles, unsigned int* counter) {
   __shared__ int s_warp[32];
   __shared__ bool s_last;
-  const int i0 = blockIdx.x * kScanTile + 4 * threadIdx.x;
+  const int i0 = blockIdx.x * kScanTile + 4 * threadIdx.x;  // a multiple of 4: int4-aligned
+  const bool full = i0 + 3 < ncells;
   int v[4];
+  if (full) {
+    const int4 c4 = *reinterpret_cast<const int4*>(count + i0);
+    v[0] = c4.x; v[1] = c4.y; v[2] = c4.z; v[3] = c4.w;
+  } else {
 #pragma unroll
-  for (int u = 0; u < 4; ++u) v[u] = (i0 + u < ncells) ? count[i0 + u] : 0;
-  int total;
-  int run = block_exclusive_scan(v[0] + v[1] + v[2] + v[3], s_warp, total);
-#pragma unroll
-  for (int u = 0; u < 4; ++u) {
-    if (i0 + u < ncells) {
-      local[i0 + u] = run;
-      count[i0 + u] = 0;
-    }
-    run += v[u];
+    for (int u = 0; u < 4; ++u) v[u] = (i0 + u < ncells) ? count[i0 + u] : 0;
   }
-  if (threadIdx.x == 0) tile_sum[blockIdx.x] = total;
-  __threadfence();
-  __syncthreads();
-  if (threadIdx.x == 0) s_last = atomicAdd(counter, 1u) == gridDim.x - 1;
+  int total;
+  const int run = block_exclusive_scan(v[0] + v[1] + v[2] + v[3], s_warp, total);
+  // counts and fill cursors are left at zero: the next step counts from zero
+  const int r1 = run + v[0], r2 = r1 + v[1], r3 = r2 + v[2];
+  if (full) {
+    *reinterpret_cast<int4*>(local + i0) = make_int4(run, r1, r2, r3);
+    *reinterpret_cast<int4*>(count + i0) = make_int4(0, 0, 0, 0);
+    *reinterpret_cast<int4*>(fill + i0) = make_int4(0, 0, 0, 0);
+  } else {
+    const int r[4] = {run, r1, r2, r3};
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+      if (i0 + u < ncells) {
+        local[i0 + u] = r[u];
+        count[i0 + u] = 0;
+        fill[i0 + u] = 0;
+      }
+  }
+  // the last block reads only the tile totals: only their writer fences
+  if (threadIdx.x == 0) {
+    tile_sum[blockIdx.x] = total;
+    __threadfence();
+    s_last = atomicAdd(counter, 1u) == gridDim.x - 1;
+  }
   __syncthreads();
   if (!s_last) return;
   __threadfence();
@@ -291,7 +307,7 @@ __device__ void coarse_guides_block(const GuideArgs& a, const PartTables& t, int
     }
     if (lane == 0) a.coarse_win[cc] = best;
   }
-  __threadfence();
+  if (lane == 0) __threadfence();  // the winners' writers publish them
   __syncthreads();
   if (threadIdx.x == 0) s_last = atomicAdd(a.counter, 1u) == (unsigned)(ncb - 1);
   __syncthreads();
@@ -429,9 +445,9 @@ cudaError_t launch_grid_count(const CandArgs& ca, const GuideArgs& ga, const Par
   return cudaGetLastError();
 }
 
-cudaError_t launch_grid_scan(int* count, int* local, int* tile_sum, int* tile_off, int ncells,
-                             int ntiles, unsigned int* counter, cudaStream_t s) {
-  k_grid_scan<<<ntiles, kScanThreads, 0, s>>>(count, local, tile_sum, tile_off, ncells, ntiles,
+cudaError_t launch_grid_scan(int* count, int* fill, int* local, int* tile_sum, int* tile_off,
+                             int ncells, int ntiles, unsigned int* counter, cudaStream_t s) {
+  k_grid_scan<<<ntiles, kScanThreads, 0, s>>>(count, fill, local, tile_sum, tile_off, ncells, ntiles,
                                                counter);
   return cudaGetLastError();
 }

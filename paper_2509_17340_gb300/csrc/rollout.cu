@@ -40,7 +40,6 @@ __global__ void __launch_bounds__(NT) k_rollout(RolloutArgs a) {
   __shared__ float s_gd[kMaxT * 3];
   __shared__ float s_red[NW];
   __shared__ float4 s_w[NW][kMaxT];
-  __shared__ float4 s_cand[NW][kWarpStage];
 
   const int e = blockIdx.y, b = blockIdx.x, tid = threadIdx.x;
   const int lane = tid & 31, wid = tid >> 5;
@@ -98,15 +97,15 @@ __global__ void __launch_bounds__(NT) k_rollout(RolloutArgs a) {
     return u;
   };
 
-  // x holds x_j; its candidate range was loaded one iteration earlier, and its
-  // candidates are copied to shared memory while the next RK4 step runs
+  // x holds x_j; its candidate range was loaded one iteration earlier, so the
+  // load overlaps the next RK4 step (with one lane per sample the GPU holds
+  // enough warps to hide the candidate loads themselves)
   float c_ctrl;
   float4 u_j = control(0, c_ctrl);
   rk4_step(x, u_j, a.dyn);
   int2 range = cell_range(x.p[0], x.p[1], x.p[2], a.grid);
   for (int j = 1; j <= T; ++j) {
-    WarpQuery q;
-    q.stage(range, lane, s_cand[wid], a.grid.pts);
+    const int2 range_j = range;
     State xn = x;
     float c_next = 0.0f;
     float4 u_next = u_j;
@@ -115,7 +114,9 @@ __global__ void __launch_bounds__(NT) k_rollout(RolloutArgs a) {
       rk4_step(xn, u_next, a.dyn);
       range = cell_range(xn.p[0], xn.p[1], xn.p[2], a.grid);
     }
-    const float d2 = q.scan(s_cand[wid], a.grid.pts, x.p[0], x.p[1], x.p[2], dmax2);
+    float d2 = dmax2;
+    for (int i = 0; i < range_j.y; ++i)
+      d2 = fminf(d2, dist2_to(__ldg(a.grid.pts + range_j.x + i), x.p[0], x.p[1], x.p[2]));
     // state terms at x_j against the guide at t = j dt
     const float gx = s_gd[3 * (j - 1)], gy = s_gd[3 * (j - 1) + 1], gz = s_gd[3 * (j - 1) + 2];
     float c = c_ctrl;
