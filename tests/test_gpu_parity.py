@@ -31,7 +31,7 @@ def aero():
 
 @pytest.fixture(scope="module")
 def planner(aero):
-    pl = make_planner(aero)
+    pl = make_planner(aero, T=128, cells=512 * 256)
     yield pl
     pl.close()
 
@@ -67,6 +67,37 @@ def _case(name):
         w = I.make_workload("plain")
         w.cloud = np.zeros((0, 3), np.float32)
         w.params.update(E=3, M_h=3, M_v=1, K=64, T=12)
+    elif name == "single_point":
+        w = I.make_workload("plain")
+        w.cloud = np.array([[1.2, 0.1, 1.6]], np.float32)
+        w.params.update(E=2, M_h=2, M_v=1, K=96, T=10)
+    elif name == "k1_t1":                  # one sample, one step: weights are 1, ctrl sums empty
+        w = I.make_workload("plain")
+        w.params.update(K=1, T=1)
+    elif name == "degenerate":             # cloud with the partition's corner cases
+        w = I.make_workload("plain")
+        p0 = w.p0
+        extra = np.array([p0, [np.nan, 0, 0], [np.inf, 1, 1], w.cloud[5], w.cloud[5],
+                          p0 + [2, 0, 0], p0 + [-2, 0, 0], p0 + [0, 0, 3], p0 + [0, 0, -1.4],
+                          p0 + [10, 0, 0], p0 + [10.001, 0, 0], p0 + [0, 2.5, 0], p0 + [0, -2.5, 0]],
+                         np.float32)
+        w.cloud = np.concatenate([w.cloud, extra]).astype(np.float32)
+        w.params.update(E=4, M_h=2, M_v=2, K=64, T=8)
+    elif name == "goal_behind_iters3":     # anchors wrap in azimuth; three Stage I iterations
+        w = I.make_workload("plain", seed=5)
+        w.goal = np.array([-15.0, 4.0, 2.5], np.float32)
+        rng = np.random.default_rng(11)
+        w.q0 = I.random_unit_quaternion(rng)
+        w.params.update(E=6, M_h=3, M_v=2, K=128, T=9, iters=3)
+    elif name == "el_span":                # partition over a narrow elevation span
+        w = I.make_workload("ensemble")
+        w.params.update(K=128, T=8, el_lo=-0.5, el_hi=0.7)
+    elif name == "max_sizes":              # E, T and the fine grid at their maxima
+        w = I.make_workload("plain")
+        c = I.random_cloud(8000, seed=9, centre=(0.0, 0.0, 1.5), spread=7.0)
+        w.cloud = c[np.linalg.norm(c - w.p0, axis=1) > 3.0]   # free space around the start
+        w.params.update(E=64, M_h=16, M_v=4, K=32, T=128, dt=0.01, fine_az=512, fine_el=256,
+                        pool_az=8, pool_el=16)
     else:
         raise KeyError(name)
     w.params["debug_samples"] = 8
@@ -74,7 +105,8 @@ def _case(name):
 
 
 CASES = ["plain", "ensemble_small", "ensemble_small_l1", "ensemble", "ragged", "ragged_l1", "raw",
-         "empty"]
+         "empty", "single_point", "k1_t1", "degenerate", "goal_behind_iters3", "el_span",
+         "max_sizes"]
 
 
 @pytest.fixture(scope="module")
