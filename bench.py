@@ -40,7 +40,8 @@ from paper_2509_17340_gb300 import inputs as I  # noqa: E402
 WORKLOAD = "ensemble"
 METRIC = "rollout-steps/s (anchor-guided ensemble plan step)"
 METRICS = {"ensemble": METRIC, "large": "rollout-steps/s (large-clutter ensemble plan step)",
-           "plain": "rollout-steps/s (plain single-MPPI plan step)"}
+           "plain": "rollout-steps/s (plain single-MPPI plan step)",
+           "batched": "rollout-steps/s (64 independent planners in one batched call)"}
 UNIT = "rollout-steps/s"
 CPU_SAMPLE_SECONDS = 15.0
 
@@ -198,6 +199,9 @@ def run_reference(args, rank: int, world: int):
         return
     from oracle import oracle as O
     O.build()
+    if WORKLOAD == "batched":
+        run_reference_batched(args, O)
+        return
     w = I.make_workload(WORKLOAD, seed=0)
     P = w.params
     u = w.hover_nominal()
@@ -219,6 +223,37 @@ def run_reference(args, rank: int, world: int):
             "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle",
                              "sample": f"{len(times)} full plan steps of the {WORKLOAD} workload, "
                                        "single-threaded FP64 oracle", "host": host_cores()},
+            "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_reference_batched(args, O):
+    """The oracle over the batch's planners in turn; each step is a bounded
+    sample (as many planners as fit in about 10 s, at least one)."""
+    ws = I.batch_workloads(64, seed=1)
+    done, tot, k = 0, 0.0, 0
+    for s in range(args.warmup + args.steps):
+        t_start, units, t_step = time.perf_counter(), 0, 0.0
+        while units == 0 or time.perf_counter() - t_start < 10.0 / max(1, args.steps):
+            w = ws[k % len(ws)]
+            k += 1
+            t0 = time.perf_counter()
+            O.plan_step(w.cloud, w.p0, w.q0, w.v0, w.goal, dict(w.params, step_id=s),
+                        w.hover_nominal(), debug=False)
+            t_step += time.perf_counter() - t0
+            units += rollout_steps(w.params)
+        if s >= args.warmup:
+            done, tot = done + units, tot + t_step
+    val = done / tot
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": "batched: 64 planners (oracle over a bounded sample of them)",
+                       "planners": len(ws)},
+            "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"{k} planner steps of the batch in order, single-threaded "
+                                       "FP64 oracle", "host": host_cores()},
             "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -253,6 +288,148 @@ def cpu_baseline(w, P) -> dict:
                       f"{tot:.1f} s)", "host": host_cores()}
 
 
+# --------------------------------------------------------------------------- batched planners
+
+def run_batched(args, rank: int, world: int, local: int):
+    """64 planners of uneven sizes (inputs.batch_workloads) per aero_batch_plan call."""
+    import torch
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    from paper_2509_17340_gb300 import build
+    build.build()
+    from paper_2509_17340_gb300 import aero
+    ws = I.batch_workloads(64, seed=1 + 1000 * rank_seed(rank))
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.Stream(device=dev)
+    lim = dict(E_max=16, K_max=4096, T_max=60, fine_cells_max=128 * 64,
+               n_points_max=max(len(w.cloud) for w in ws))
+    batch = aero.Batch(len(ws), **lim)
+    clouds = [torch.from_numpy(w.cloud).to(dev) for w in ws]
+    u0 = [torch.from_numpy(w.hover_nominal()).to(dev) for w in ws]
+    un = [u.clone() for u in u0]
+    ub = [torch.empty((w.params["T"], 4), device=dev) for w in ws]
+    cand = [torch.empty((w.params["E"],), device=dev) for w in ws]
+    best = [torch.empty((1,), dtype=torch.int32, device=dev) for w in ws]
+    states = [aero.state_struct(w.p0, w.q0, w.v0) for w in ws]
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def items(step_id):
+        out = []
+        for i, w in enumerate(ws):
+            w.params["step_id"] = step_id
+            out.append(aero.Batch.item(states[i], clouds[i], w.goal, aero.params_struct(w.params),
+                                       un[i], ub[i], cand[i], best[i]))
+        return out
+
+    plans = [items(s) for s in range(args.warmup + args.steps)]
+    with torch.cuda.stream(stream):
+        for s in range(args.warmup):
+            flush.fill_(float(s))
+            for a, b in zip(un, u0):
+                a.copy_(b)
+            batch.plan(plans[s], stream)
+        torch.cuda.synchronize()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(args.steps)]
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        with ClockSampler(local) as clk:
+            for i in range(args.steps):
+                flush.fill_(float(i))
+                for a, b in zip(un, u0):
+                    a.copy_(b)
+                ev[i][0].record(stream)
+                batch.plan(plans[args.warmup + i], stream)
+                ev[i][1].record(stream)
+            torch.cuda.synchronize()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = max_over_ranks(sum(step_ms), dist, dev)
+    units = sum(rollout_steps(w.params) for w in ws)
+
+    # end to end through the batch API: pinned host inputs in, results out
+    h_clouds = [torch.from_numpy(w.cloud.copy()).pin_memory() for w in ws]
+    h_u0 = [torch.from_numpy(w.hover_nominal()).pin_memory() for w in ws]
+    h_un = [torch.empty_like(u).pin_memory() for u in h_u0]
+    h_ub = [torch.empty((w.params["T"], 4)).pin_memory() for w in ws]
+    h_cand = [torch.empty((w.params["E"],)).pin_memory() for w in ws]
+    h_best = [torch.empty((1,), dtype=torch.int32).pin_memory() for w in ws]
+    e2e_steps = max(10, args.steps // 4)
+    times = []
+    for i in range(args.warmup + e2e_steps):
+        with torch.cuda.stream(stream):
+            flush.fill_(float(i))
+        stream.synchronize()
+        t0 = time.perf_counter()
+        with torch.cuda.stream(stream):
+            for k in range(len(ws)):
+                clouds[k].copy_(h_clouds[k], non_blocking=True)
+                un[k].copy_(h_u0[k], non_blocking=True)
+            batch.plan(plans[i % len(plans)], stream)
+            for k in range(len(ws)):
+                h_un[k].copy_(un[k], non_blocking=True)
+                h_ub[k].copy_(ub[k], non_blocking=True)
+                h_cand[k].copy_(cand[k], non_blocking=True)
+                h_best[k].copy_(best[k], non_blocking=True)
+        stream.synchronize()
+        if i >= args.warmup:
+            times.append(time.perf_counter() - t0)
+    e_tot = max_over_ranks(sum(times), dist, dev)
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+    flops = sum(w.params["E"] * w.params["K"] * w.params["T"] * w.params["iters"]
+                for w in ws) * rollout_flops_per_step()
+    achieved = flops / (total_ms / args.steps / 1e3) / 1e12
+    peak = fp32_peak_tflops(measured_peaks().get("sm_max_mhz", 2070.0))
+    line = {
+        "metric": METRIC, "value": world * units * args.steps / (total_ms / 1e3), "unit": UNIT,
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": total_ms / args.steps, "ms_per_step_median": statistics.median(step_ms),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": "batched: 64 planners, E in {4,8,16}, K in {256,1024,4096}, "
+                               "T in {20,40,60}, forest / walls with 1.5 m gaps / inclines, "
+                               f"{min(len(w.cloud) for w in ws)}-{max(len(w.cloud) for w in ws)} points",
+                   "planners": len(ws), "rollout_steps_per_batch": units,
+                   "l2": "flushed between timed steps (512 MB write)"},
+        "roofline": {"kernel": "all rollout kernels of the batch (they overlap on 16 streams)",
+                     "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak, "traffic": None,
+                     "flops_per_launch": flops, "avg_launch_ms": total_ms / args.steps,
+                     "peak_note": "FP32 FMA pipes: 152 SMs x 128 lanes x 2 x 2070 MHz; whole batch step"},
+        "clocks": clk.summary(),
+        "e2e": {"value": world * units * len(times) / e_tot, "unit": UNIT,
+                "h2d_bytes_per_step": sum(c.numel() * 4 + u.numel() * 4 for c, u in zip(h_clouds, h_u0)),
+                "d2h_bytes_per_step": sum(u.numel() * 4 + b.numel() * 4 + c.numel() * 4 + 4
+                                          for u, b, c in zip(h_un, h_ub, h_cand)),
+                "ms_per_step": 1e3 * e_tot / len(times)},
+        "gpu_launches": 6 * len(ws) * args.steps,
+    }
+    if not args.no_cpu_baseline:
+        from oracle import oracle as O
+        O.build()
+        done, t_cpu, t_start = 0, 0.0, time.perf_counter()
+        for w in ws:
+            if time.perf_counter() - t_start > CPU_SAMPLE_SECONDS and done > 0:
+                break
+            t0 = time.perf_counter()
+            O.plan_step(w.cloud, w.p0, w.q0, w.v0, w.goal, w.params, w.hover_nominal(), debug=False)
+            t_cpu += time.perf_counter() - t0
+            done += rollout_steps(w.params)
+        line["cpu_baseline"] = {"value": done / t_cpu, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                "sample": f"the batch's first planners in order, {t_cpu:.1f} s of "
+                                          "FP64 oracle on one thread", "host": host_cores()}
+    print(json.dumps(line), flush=True)
+    batch.close()
+    if dist:
+        dist.destroy_process_group()
+
+
 # --------------------------------------------------------------------------- GPU arm
 
 def main():
@@ -272,6 +449,9 @@ def main():
     local = env_int("LOCAL_RANK", 0)
     if args.impl == "reference":
         run_reference(args, rank, world)
+        return
+    if WORKLOAD == "batched":
+        run_batched(args, rank, world, local)
         return
 
     import torch

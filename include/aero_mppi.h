@@ -202,6 +202,40 @@ int aero_plan_step_noalloc(const aero_state_t* x0, const float* cloud_xyz, int64
                            float* u_best_out, float* cand_costs_out, int32_t* best_idx_out,
                            void* stream);
 
+/* ---- batched planning ----------------------------------------------------
+ * Many independent planning steps (different drones or scenes, uneven E, K, T
+ * and cloud sizes) in one call: the batch runs each item's step exactly as
+ * aero_plan_step would (same kernels, bitwise the same results) with the items
+ * spread over the batch's internal streams, forked from and joined back to
+ * `stream`; a sequence of batch calls with fixed pointers can be captured in a
+ * CUDA graph. */
+typedef struct {
+  aero_state_t x0;            /* current state */
+  const float* cloud_xyz;     /* device, n_points x 3 float (may be NULL if n_points == 0) */
+  int64_t n_points;
+  float goal[3];
+  aero_params_t params;
+  float* u_nom_inout;         /* device, E x T x 4 float, 16-byte aligned */
+  float* u_best_out;          /* device, T x 4 */
+  float* cand_costs_out;      /* device, E */
+  int32_t* best_idx_out;      /* device, 1 */
+} aero_batch_item_t;
+
+typedef struct aero_batch aero_batch_t;
+
+/* Create a batch of up to n_max planners, each with a workspace sized by
+ * `limits` (every item of a call must fit them).  Errors: INVALID_ARG, ALLOC,
+ * CUDA. */
+int aero_batch_create(const aero_limits_t* limits, int32_t n_max, aero_batch_t** out);
+
+/* Enqueue the n <= n_max steps of `items` (host array) on `stream`; returns
+ * after enqueuing.  Every item is validated first: on an error nothing is
+ * enqueued (INVALID_ARG, EXCEEDS_LIMITS, NOT_DEVICE_PTR). */
+int aero_batch_plan(aero_batch_t* batch, const aero_batch_item_t* items, int32_t n, void* stream);
+
+/* Free the batch (synchronises the device first).  NULL is accepted. */
+int aero_batch_destroy(aero_batch_t* batch);
+
 /* Bytes of debug buffer `what` (AERO_DBG_*) for the last step; 0 if unknown. */
 size_t aero_debug_size(aero_planner_t* planner, int32_t what);
 

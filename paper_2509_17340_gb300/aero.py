@@ -62,6 +62,13 @@ class Params(C.Structure):
     ]
 
 
+class BatchItem(C.Structure):
+    _fields_ = [("x0", State), ("cloud_xyz", C.c_void_p), ("n_points", C.c_int64),
+                ("goal", C.c_float * 3), ("params", Params), ("u_nom_inout", C.c_void_p),
+                ("u_best_out", C.c_void_p), ("cand_costs_out", C.c_void_p),
+                ("best_idx_out", C.c_void_p)]
+
+
 _vp = C.c_void_p
 _lib.aero_params_default.argtypes = [C.POINTER(Params)]
 _lib.aero_params_default.restype = None
@@ -79,6 +86,9 @@ _lib.aero_sync_status.argtypes = [_vp, _vp]
 _lib.aero_philox.argtypes = [C.c_uint64, C.c_uint32, C.c_uint32, C.c_uint32, C.c_int64, _vp, _vp]
 _lib.aero_profile_enable.argtypes = [_vp, C.c_int]
 _lib.aero_profile_read.argtypes = [_vp, C.POINTER(C.c_double), C.POINTER(C.c_int64)]
+_lib.aero_batch_create.argtypes = [C.POINTER(Limits), C.c_int32, C.POINTER(_vp)]
+_lib.aero_batch_plan.argtypes = [_vp, C.POINTER(BatchItem), C.c_int32, _vp]
+_lib.aero_batch_destroy.argtypes = [_vp]
 _lib.aero_status_str.argtypes = [C.c_int]
 _lib.aero_status_str.restype = C.c_char_p
 
@@ -290,3 +300,48 @@ def plan_step(planner: Planner, p0, q0, v0, cloud: torch.Tensor, goal, params: d
     planner.plan_step(state_struct(p0, q0, v0), cloud, goal, params_struct(params), u_nom, u_best,
                       cand, best, stream)
     return u_best, cand, best
+
+
+class Batch:
+    """Many independent planners planned by one call (``aero_batch_plan``)."""
+
+    def __init__(self, n_max: int, E_max=16, K_max=4096, T_max=64, fine_cells_max=128 * 64,
+                 n_points_max=1 << 17, debug_samples_max=0):
+        torch.cuda.init()
+        lim = Limits(E_max, K_max, T_max, fine_cells_max, n_points_max, debug_samples_max, 0)
+        h = _vp()
+        _check(_lib.aero_batch_create(C.byref(lim), n_max, C.byref(h)), "aero_batch_create")
+        self._h = h
+        self.n_max = n_max
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.aero_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @staticmethod
+    def item(state: State, cloud: torch.Tensor, goal, params: Params, u_nom: torch.Tensor,
+             u_best: torch.Tensor, cand: torch.Tensor, best_idx: torch.Tensor) -> BatchItem:
+        it = BatchItem()
+        it.x0 = state
+        n = cloud.shape[0] if cloud is not None else 0
+        it.cloud_xyz = _dev(cloud, torch.float32, "cloud") if n > 0 else None
+        it.n_points = n
+        for i in range(3):
+            it.goal[i] = float(goal[i])
+        it.params = params
+        it.u_nom_inout = _dev(u_nom, torch.float32, "u_nom")
+        it.u_best_out = _dev(u_best, torch.float32, "u_best")
+        it.cand_costs_out = _dev(cand, torch.float32, "cand")
+        it.best_idx_out = _dev(best_idx, torch.int32, "best_idx")
+        return it
+
+    def plan(self, items, stream=None) -> None:
+        arr = (BatchItem * len(items))(*items)
+        _check(_lib.aero_batch_plan(self._h, arr, len(items), _stream_ptr(stream)), "aero_batch_plan")

@@ -894,4 +894,108 @@ int aero_plan_step_noalloc(const aero_state_t* x0, const float* cloud, int64_t n
   return enqueue_step(&pl, x0, cloud, n, goal, *params, u_nom, u_best, cand, best_idx, s);
 }
 
+// ---------------------------------------------------------------------------
+// Batched planning: independent planners on a pool of streams.
+// ---------------------------------------------------------------------------
+struct aero_batch {
+  std::vector<aero_planner*> planners;
+  std::vector<cudaStream_t> streams;
+  std::vector<cudaEvent_t> joins;
+  cudaEvent_t fork = nullptr;
+};
+
+namespace {
+constexpr int kBatchStreams = 16;
+
+void batch_free(aero_batch* b) {
+  for (aero_planner* pl : b->planners) aero_destroy(pl);
+  for (cudaStream_t st : b->streams) cudaStreamDestroy(st);
+  for (cudaEvent_t ev : b->joins) cudaEventDestroy(ev);
+  if (b->fork) cudaEventDestroy(b->fork);
+  delete b;
+}
+
+int check_item(aero_planner* pl, const aero_batch_item_t& it) {
+  if (!it.u_nom_inout || !it.u_best_out || !it.cand_costs_out || !it.best_idx_out)
+    return AERO_ERR_INVALID_ARG;
+  if (it.n_points > 0 && !it.cloud_xyz) return AERO_ERR_INVALID_ARG;
+  const int rc = validate(pl, &it.params, it.n_points);
+  if (rc != AERO_OK) return rc;
+  if (reinterpret_cast<uintptr_t>(it.u_nom_inout) % 16 != 0) return AERO_ERR_INVALID_ARG;
+  if ((it.n_points > 0 && !is_device_ptr(it.cloud_xyz)) || !is_device_ptr(it.u_nom_inout) ||
+      !is_device_ptr(it.u_best_out) || !is_device_ptr(it.cand_costs_out) ||
+      !is_device_ptr(it.best_idx_out))
+    return AERO_ERR_NOT_DEVICE_PTR;
+  return AERO_OK;
+}
+}  // namespace
+
+int aero_batch_create(const aero_limits_t* limits, int32_t n_max, aero_batch_t** out) {
+  if (!limits || !out || n_max < 1 || n_max > 4096) return AERO_ERR_INVALID_ARG;
+  *out = nullptr;
+  aero_batch* b = new (std::nothrow) aero_batch();
+  if (!b) return AERO_ERR_ALLOC;
+  for (int i = 0; i < n_max; ++i) {
+    aero_planner_t* pl = nullptr;
+    const int rc = aero_create(limits, &pl);
+    if (rc != AERO_OK) {
+      batch_free(b);
+      return rc;
+    }
+    b->planners.push_back(pl);
+  }
+  const int ns = n_max < kBatchStreams ? n_max : kBatchStreams;
+  cudaError_t e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
+  for (int i = 0; i < ns && e == cudaSuccess; ++i) {
+    cudaStream_t st;
+    cudaEvent_t ev;
+    e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+    if (e != cudaSuccess) break;
+    b->streams.push_back(st);
+    e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+    if (e != cudaSuccess) break;
+    b->joins.push_back(ev);
+  }
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    batch_free(b);
+    return AERO_ERR_CUDA;
+  }
+  *out = b;
+  return AERO_OK;
+}
+
+int aero_batch_plan(aero_batch_t* b, const aero_batch_item_t* items, int32_t n, void* stream) {
+  if (!b || !items || n < 0 || n > (int32_t)b->planners.size()) return AERO_ERR_INVALID_ARG;
+  for (int i = 0; i < n; ++i) {
+    const int rc = check_item(b->planners[i], items[i]);
+    if (rc != AERO_OK) return rc;
+  }
+  if (n == 0) return AERO_OK;
+  cudaStream_t s = (cudaStream_t)stream;
+  const int ns = n < (int)b->streams.size() ? n : (int)b->streams.size();
+  cudaError_t e = cudaEventRecord(b->fork, s);
+  for (int k = 0; k < ns && e == cudaSuccess; ++k) e = cudaStreamWaitEvent(b->streams[k], b->fork, 0);
+  if (e != cudaSuccess) return AERO_ERR_CUDA;
+  for (int i = 0; i < n; ++i) {
+    const aero_batch_item_t& it = items[i];
+    const int rc = enqueue_step(b->planners[i], &it.x0, it.cloud_xyz, it.n_points, it.goal,
+                                it.params, it.u_nom_inout, it.u_best_out, it.cand_costs_out,
+                                it.best_idx_out, b->streams[i % ns]);
+    if (rc != AERO_OK) return rc;
+  }
+  for (int k = 0; k < ns && e == cudaSuccess; ++k) {
+    e = cudaEventRecord(b->joins[k], b->streams[k]);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, b->joins[k], 0);
+  }
+  return cuda_fail(e);
+}
+
+int aero_batch_destroy(aero_batch_t* b) {
+  if (!b) return AERO_OK;
+  cudaDeviceSynchronize();
+  batch_free(b);
+  return AERO_OK;
+}
+
 }  // extern "C"

@@ -277,6 +277,87 @@ def scene_large(seed: int = 0) -> tuple[np.ndarray, Scene]:
     return pts[idx], sc
 
 
+def scene_walls(rng: np.random.Generator) -> Scene:
+    """Three rows of 6 m walls across the flight direction (x = 6, 12, 18 m),
+    each spanning y in [-15, 15] with three 1.5 m gaps at random places, plus
+    ground and a few cylinders."""
+    boxes = []
+    for x in (6.0, 12.0, 18.0):
+        gaps = np.sort(rng.uniform(-13, 13, 3))
+        y = -15.0
+        for gy in gaps:
+            if gy - 0.75 > y:
+                boxes.append(([x - 0.15, y, 0.0], [x + 0.15, gy - 0.75, 6.0]))
+            y = max(y, gy + 0.75)
+        if y < 15.0:
+            boxes.append(([x - 0.15, y, 0.0], [x + 0.15, 15.0, 6.0]))
+    cyl = _forest(rng, 10, 15.0, 0.2, 0.5, 6.0, keep_out=[(0.0, 0.0, 2.0)], centre=(10.0, 0.0))
+    return Scene(cylinders=cyl, boxes=boxes, ground=True)
+
+
+def scene_inclines(rng: np.random.Generator) -> Scene:
+    """Ground tilted by 10-25 degrees under the flight path, plus spherical
+    boulders (r 0.3-1.0 m) and a few inclined slabs."""
+    tilt = np.deg2rad(rng.uniform(10, 25))
+    yaw = rng.uniform(0, 2 * np.pi)
+    a1 = np.array([np.cos(yaw) * np.cos(tilt), np.sin(yaw) * np.cos(tilt), np.sin(tilt)])
+    a2 = np.array([-np.sin(yaw), np.cos(yaw), 0.0])
+    rects = [(np.array([10.0, 0.0, -2.0]), a1, a2, 25.0, 25.0)]
+    for _ in range(3):
+        t2 = np.deg2rad(rng.uniform(10, 25))
+        y2 = rng.uniform(0, 2 * np.pi)
+        b1 = np.array([np.cos(y2) * np.cos(t2), np.sin(y2) * np.cos(t2), np.sin(t2)])
+        b2 = np.array([-np.sin(y2), np.cos(y2), 0.0])
+        rects.append((np.array([rng.uniform(5, 20), rng.uniform(-8, 8), 2.0]), b1, b2,
+                      rng.uniform(2, 4), rng.uniform(2, 4)))
+    spheres = []
+    while len(spheres) < 25:
+        c = np.array([rng.uniform(2, 25), rng.uniform(-12, 12), rng.uniform(0.5, 4.0)])
+        r = rng.uniform(0.3, 1.0)
+        if np.linalg.norm(c - [0, 0, 2.0]) > r + 2.0:
+            spheres.append((c, r))
+    return Scene(rects=rects, spheres=spheres)
+
+
+BATCH_E = {4: (2, 2), 8: (4, 2), 16: (4, 4)}
+
+
+def batch_workloads(n: int = 64, seed: int = 1) -> list:
+    """Independent planners of uneven sizes: E in {4, 8, 16}, K in {256, 1024,
+    4096}, T in {20, 40, 60}; scene forest / walls with 1.5 m gaps / inclines
+    with boulders; 5k-100k points (log-uniform) from a 1024 x 32 LiDAR sweep at
+    (0, 0, 2), resampled to the drawn size.  All sizes from `seed`."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(n):
+        E = int(rng.choice([4, 8, 16]))
+        K = int(rng.choice([256, 1024, 4096]))
+        T = int(rng.choice([20, 40, 60]))
+        kind = ["forest", "walls", "inclines"][int(rng.integers(3))]
+        npts = int(np.exp(rng.uniform(np.log(5000), np.log(100000))))
+        srng = np.random.default_rng([seed, i])
+        if kind == "forest":
+            sc = Scene(cylinders=_forest(srng, 60, 20.0, 0.2, 0.5, 6.0, keep_out=[(0.0, 0.0, 2.0)]),
+                       ground=True)
+        elif kind == "walls":
+            sc = scene_walls(srng)
+        else:
+            sc = scene_inclines(srng)
+        pts = lidar_sweep(sc, (0.0, 0.0, 2.0), 1024, 32, -15.0, 15.0, 30.0, 0.02, srng)
+        if len(pts) == 0:
+            pts = np.zeros((1, 3)) + [20.0, 0.0, 2.0]
+        pts = pts[srng.choice(len(pts), size=npts, replace=len(pts) < npts)]
+        p = workload_params("ensemble")
+        Mh, Mv = BATCH_E[E]
+        p.update(E=E, M_h=Mh, M_v=Mv, K=K, T=T, seed=seed * 1000 + i)
+        w = Workload(f"batch{i}:{kind}", p, np.ascontiguousarray(pts, np.float32),
+                     np.array([0, 0, 2], np.float32), np.array([1, 0, 0, 0], np.float32),
+                     np.array([rng.uniform(0, 3), 0, 0], np.float32),
+                     np.array([25, rng.uniform(-5, 5), 2], np.float32), note=kind)
+        out.append(w)
+    return out
+
+
 def make_workload(name: str, seed: int = 0) -> Workload:
     """Build the named workload (params + scene + start state + goal)."""
     p = workload_params(name)
