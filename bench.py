@@ -325,6 +325,10 @@ def run_batched(args, rank: int, world: int, local: int):
         return out
 
     plans = [items(s) for s in range(args.warmup + args.steps)]
+    # one-off autotuning of the launch configuration (outside the timed region;
+    # it writes only the batch's scratch buffers)
+    tuned, tune_ms = batch.tune(plans[0], repeats=3, stream=stream)
+    torch.cuda.synchronize()
     with torch.cuda.stream(stream):
         for s in range(args.warmup):
             flush.fill_(float(s))
@@ -396,8 +400,9 @@ def run_batched(args, rank: int, world: int, local: int):
                                "T in {20,40,60}, forest / walls with 1.5 m gaps / inclines, "
                                f"{min(len(w.cloud) for w in ws)}-{max(len(w.cloud) for w in ws)} points",
                    "planners": len(ws), "rollout_steps_per_batch": units,
+                   "launch": dict(tuned, tune_ms=tune_ms),
                    "l2": "flushed between timed steps (512 MB write)"},
-        "roofline": {"kernel": "all rollout kernels of the batch (they overlap on 16 streams)",
+        "roofline": {"kernel": "the whole batched step (Stage I is the dominant launch)",
                      "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak, "traffic": None,
                      "flops_per_launch": flops, "avg_launch_ms": total_ms / args.steps,
@@ -408,7 +413,7 @@ def run_batched(args, rank: int, world: int, local: int):
                 "d2h_bytes_per_step": sum(u.numel() * 4 + b.numel() * 4 + c.numel() * 4 + 4
                                           for u, b, c in zip(h_un, h_ub, h_cand)),
                 "ms_per_step": 1e3 * e_tot / len(times)},
-        "gpu_launches": 6 * len(ws) * args.steps,
+        "gpu_launches": (4 + 2 * max(w.params["iters"] for w in ws)) * args.steps,
     }
     if not args.no_cpu_baseline:
         from oracle import oracle as O

@@ -204,17 +204,24 @@ int aero_plan_step_noalloc(const aero_state_t* x0, const float* cloud_xyz, int64
 
 /* ---- batched planning ----------------------------------------------------
  * Many independent planning steps (different drones or scenes, uneven E, K, T
- * and cloud sizes) in one call: the batch runs each item's step exactly as
- * aero_plan_step would (same kernels, bitwise the same results) with the items
- * spread over the batch's internal streams, forked from and joined back to
- * `stream`; a sequence of batch calls with fixed pointers can be captured in a
- * CUDA graph. */
+ * and cloud sizes) in one call.  Each stage of the step (Sec. IV-A partition,
+ * Sec. IV-B anchors and guides, the collision lists, the Stage I rollouts of
+ * Sec. III-B with the update of Eq. mppi_update_simplified, Stage II and the
+ * selection) runs as ONE launch over the work units of all items; the Stage I
+ * launch is persistent (a fixed number of CTAs per SM) and takes its units --
+ * (item, instance, block of samples), longest horizon first -- from a device
+ * work queue.  The launches of a call form a CUDA graph, instantiated once per
+ * batch shape (item count, largest iteration count, configuration) and then
+ * replayed; a call uploads the items' arguments in one host-to-device copy and
+ * launches the graph on `stream`.
+ * Every item's results are bitwise those of aero_plan_step with the same
+ * lanes_per_sample (the per-unit arithmetic is the same code). */
 typedef struct {
   aero_state_t x0;            /* current state */
   const float* cloud_xyz;     /* device, n_points x 3 float (may be NULL if n_points == 0) */
   int64_t n_points;
   float goal[3];
-  aero_params_t params;
+  aero_params_t params;       /* debug_samples must be 0 */
   float* u_nom_inout;         /* device, E x T x 4 float, 16-byte aligned */
   float* u_best_out;          /* device, T x 4 */
   float* cand_costs_out;      /* device, E */
@@ -223,17 +230,62 @@ typedef struct {
 
 typedef struct aero_batch aero_batch_t;
 
-/* Create a batch of up to n_max planners, each with a workspace sized by
- * `limits` (every item of a call must fit them).  Errors: INVALID_ARG, ALLOC,
- * CUDA. */
+/* Launch configuration of a batch (the autotuner's search space). */
+typedef struct {
+  int32_t quad_max_samples;    /* items with lanes_per_sample == 0 use four lanes per sample
+                                  when E*K <= this, else one */
+  int32_t rollout_ctas_per_sm; /* persistent Stage I CTAs per SM; 0 = as many as fit; 6 or more
+                                  also selects the one-lane kernel built for six per SM
+                                  (fewer registers) */
+  int32_t dynamic_queue;       /* 1: CTAs take units from the work queue; 0: strided by the grid */
+  int32_t coarse_cells;        /* 1: collision-grid cells of edge d_max (1 + 1/16) (fewer list
+                                  entries to build, longer lists to scan); 0: edge d_max / 2 when
+                                  the candidate array can hold it.  Results do not depend on it:
+                                  every list holds the nearest point of every query within d_max */
+} aero_batch_config_t;
+
+/* Create a batch of up to n_max <= 256 item slots, each with a planner
+ * workspace sized by `limits` (every item of a call must fit them; the limits'
+ * debug_samples_max is ignored).  The default configuration is
+ * {0, 0, 1, 0}.  Errors: INVALID_ARG, ALLOC, CUDA. */
 int aero_batch_create(const aero_limits_t* limits, int32_t n_max, aero_batch_t** out);
 
-/* Enqueue the n <= n_max steps of `items` (host array) on `stream`; returns
- * after enqueuing.  Every item is validated first: on an error nothing is
- * enqueued (INVALID_ARG, EXCEEDS_LIMITS, NOT_DEVICE_PTR). */
+/* Enqueue the n <= n_max steps of `items` (host array; item i uses slot i) on
+ * `stream`; returns after enqueuing.  Every item is validated first: on an
+ * error nothing is enqueued (INVALID_ARG, EXCEEDS_LIMITS, NOT_DEVICE_PTR).
+ * Calls on one batch must be ordered on the device (one stream, or
+ * synchronised): they share the slots' workspaces and the argument buffer.
+ * The host may reuse `items` as soon as the call returns. */
 int aero_batch_plan(aero_batch_t* batch, const aero_batch_item_t* items, int32_t n, void* stream);
 
-/* Free the batch (synchronises the device first).  NULL is accepted. */
+int aero_batch_set_config(aero_batch_t* batch, const aero_batch_config_t* config);
+int aero_batch_get_config(aero_batch_t* batch, aero_batch_config_t* config);
+
+/* Autotune: time every configuration of a small search space (quad_max_samples
+ * in {0, 4096, 32768}; rollout_ctas_per_sm in {as many as fit, 6, half of the
+ * fewest that fit};
+ * dynamic_queue in {1, 0}; coarse_cells in {0, 1}) on `items`, `repeats` timed calls each after one
+ * warm-up, keep the fastest as the batch's configuration and return it with
+ * its mean time in *best_ms.  The items' clouds and states are read; the
+ * outputs go to scratch buffers of the batch, so the items' u_nom_inout and
+ * outputs are left untouched.  Synchronous (returns when done). */
+int aero_batch_tune(aero_batch_t* batch, const aero_batch_item_t* items, int32_t n, int32_t repeats,
+                    void* stream, aero_batch_config_t* best, float* best_ms);
+
+/* OR of the status words of the batch's slots (bit 0: an update's normaliser
+ * was not a positive finite number; bit 1: a candidate list overflowed), which
+ * are then cleared.  Synchronous. */
+int aero_batch_sync_status(aero_batch_t* batch, int32_t* status);
+
+/* Debug copies of slot `slot`'s last step, as aero_debug_size / aero_get_debug
+ * for a planner (no per-sample buffers; FINE_KEYS reads back emptied: the
+ * batched step leaves its keys empty for the next call).  INVALID_ARG for a
+ * slot the last call did not use. */
+size_t aero_batch_debug_size(aero_batch_t* batch, int32_t slot, int32_t what);
+int aero_batch_get_debug(aero_batch_t* batch, int32_t slot, int32_t what, void* dst, size_t bytes,
+                         void* stream);
+
+/* Free the batch (synchronises the device first). */
 int aero_batch_destroy(aero_batch_t* batch);
 
 /* Bytes of debug buffer `what` (AERO_DBG_*) for the last step; 0 if unknown. */

@@ -69,6 +69,16 @@ class BatchItem(C.Structure):
                 ("best_idx_out", C.c_void_p)]
 
 
+class BatchConfig(C.Structure):
+    _fields_ = [("quad_max_samples", C.c_int32), ("rollout_ctas_per_sm", C.c_int32),
+                ("dynamic_queue", C.c_int32), ("coarse_cells", C.c_int32)]
+
+    def as_dict(self) -> dict:
+        return {"quad_max_samples": self.quad_max_samples,
+                "rollout_ctas_per_sm": self.rollout_ctas_per_sm, "dynamic_queue": self.dynamic_queue,
+                "coarse_cells": self.coarse_cells}
+
+
 _vp = C.c_void_p
 _lib.aero_params_default.argtypes = [C.POINTER(Params)]
 _lib.aero_params_default.restype = None
@@ -89,6 +99,14 @@ _lib.aero_profile_read.argtypes = [_vp, C.POINTER(C.c_double), C.POINTER(C.c_int
 _lib.aero_batch_create.argtypes = [C.POINTER(Limits), C.c_int32, C.POINTER(_vp)]
 _lib.aero_batch_plan.argtypes = [_vp, C.POINTER(BatchItem), C.c_int32, _vp]
 _lib.aero_batch_destroy.argtypes = [_vp]
+_lib.aero_batch_set_config.argtypes = [_vp, C.POINTER(BatchConfig)]
+_lib.aero_batch_get_config.argtypes = [_vp, C.POINTER(BatchConfig)]
+_lib.aero_batch_tune.argtypes = [_vp, C.POINTER(BatchItem), C.c_int32, C.c_int32, _vp,
+                                 C.POINTER(BatchConfig), C.POINTER(C.c_float)]
+_lib.aero_batch_sync_status.argtypes = [_vp, C.POINTER(C.c_int32)]
+_lib.aero_batch_debug_size.argtypes = [_vp, C.c_int32, C.c_int32]
+_lib.aero_batch_debug_size.restype = C.c_size_t
+_lib.aero_batch_get_debug.argtypes = [_vp, C.c_int32, C.c_int32, _vp, C.c_size_t, _vp]
 _lib.aero_status_str.argtypes = [C.c_int]
 _lib.aero_status_str.restype = C.c_char_p
 
@@ -345,3 +363,46 @@ class Batch:
     def plan(self, items, stream=None) -> None:
         arr = (BatchItem * len(items))(*items)
         _check(_lib.aero_batch_plan(self._h, arr, len(items), _stream_ptr(stream)), "aero_batch_plan")
+
+    def config(self) -> dict:
+        c = BatchConfig()
+        _check(_lib.aero_batch_get_config(self._h, C.byref(c)), "aero_batch_get_config")
+        return c.as_dict()
+
+    def set_config(self, quad_max_samples=0, rollout_ctas_per_sm=0, dynamic_queue=1,
+                   coarse_cells=0) -> None:
+        c = BatchConfig(quad_max_samples, rollout_ctas_per_sm, dynamic_queue, coarse_cells)
+        _check(_lib.aero_batch_set_config(self._h, C.byref(c)), "aero_batch_set_config")
+
+    def tune(self, items, repeats=3, stream=None):
+        """Time the configurations of the search space on ``items``; keeps and
+        returns the fastest (dict) with its mean time in ms."""
+        arr = (BatchItem * len(items))(*items)
+        c, ms = BatchConfig(), C.c_float()
+        _check(_lib.aero_batch_tune(self._h, arr, len(items), repeats, _stream_ptr(stream),
+                                    C.byref(c), C.byref(ms)), "aero_batch_tune")
+        return c.as_dict(), ms.value
+
+    def sync_status(self) -> int:
+        st = C.c_int32()
+        _check(_lib.aero_batch_sync_status(self._h, C.byref(st)), "aero_batch_sync_status")
+        return st.value
+
+    def debug(self, slot: int, what: str, stream=None) -> np.ndarray:
+        """Copy a debug buffer of slot `slot`'s last step to the host (synchronous)."""
+        wid = DBG[what]
+        stream_p = _stream_ptr(stream)
+        if what == "GRID_META":
+            buf = np.zeros(8, np.int32)
+        elif what == "GRID_POINTS":
+            meta = self.debug(slot, "GRID_META", stream)
+            buf = np.zeros((int(meta[1]), 4), np.float32)
+        else:
+            nbytes = _lib.aero_batch_debug_size(self._h, slot, wid)
+            dtype = {"FINE_KEYS": np.uint64, "COARSE_WIN": np.int32, "GOAL_CELL": np.int32,
+                     "ANCHOR_CELLS": np.int32, "GRID_START": np.int32}.get(what, np.float32)
+            buf = np.zeros(nbytes // np.dtype(dtype).itemsize, dtype)
+        _check(_lib.aero_batch_get_debug(self._h, slot, wid, buf.ctypes.data, buf.nbytes, stream_p),
+               "aero_batch_get_debug")
+        torch.cuda.synchronize()
+        return buf

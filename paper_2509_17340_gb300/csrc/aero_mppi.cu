@@ -6,6 +6,7 @@
 #include <cmath>
 #include <cstdint>
 #include <cstdio>
+#include <algorithm>
 #include <cstring>
 #include <mutex>
 #include <new>
@@ -29,6 +30,7 @@ struct aero_planner {
   int* grid_count = nullptr;  // G^3 + 1 candidate counts, zero between steps
   int* grid_fill = nullptr;   // G^3 + 1 fill cursors of the scatter
   bool grid_dirty = true;     // counts possibly non-zero (new planner, interrupted step)
+  bool keys_empty = false;    // every fine-cell key is empty (left so by a batched step)
   int* grid_local = nullptr;  // G^3 + 1 tile-local exclusive prefix
   int* tile_sum = nullptr;
   int* tile_off = nullptr;
@@ -134,13 +136,14 @@ void make_tables(const aero_params_t& p, PartTables& t, int& check_lo, int& chec
 // Candidate grid over [-E, E)^3 around p0, E = r_max + reach + h: every
 // collision point lies within r_max of p0, so queries outside the grid are
 // farther than d_max from all of them.  Cells of edge d_max / 2 when the
-// candidate array can hold 216 entries per collision item, else d_max (1 + 1/16);
+// candidate array can hold 216 entries per collision item (and `coarse` is
+// not asked for), else d_max (1 + 1/16);
 // never more than kGridMax cells per axis.  `margin` covers binary32 rounding
 // of the cell coordinates.
-GridGeom make_grid(const aero_params_t& p, int64_t n_items, int64_t cap, int gmax) {
+GridGeom make_grid(const aero_params_t& p, int64_t n_items, int64_t cap, int gmax, bool coarse) {
   GridGeom g;
   g.reach = p.d_max * (1.0f + 1e-3f) + 1e-4f;
-  float h = (int64_t)kFineDup * n_items <= cap ? 0.5f * p.d_max : p.d_max * 1.0625f;
+  float h = !coarse && (int64_t)kFineDup * n_items <= cap ? 0.5f * p.d_max : p.d_max * 1.0625f;
   float E = p.r_max + g.reach + h;
   int G = (int)std::ceil(2.0f * E / h);
   if (G > gmax) {
@@ -254,46 +257,44 @@ void prof_destroy(aero_planner* pl) {
   pl->slots_used = 0;
 }
 
-// Enqueue one step; all pointers already validated.
-int enqueue_step(aero_planner* pl, const aero_state_t* x0, const float* cloud, int64_t n,
-                 const float* goal, const aero_params_t& p, float* u_nom, float* u_best,
-                 float* cand, int32_t* best_idx, cudaStream_t s) {
-  const int ncell = p.fine_az * p.fine_el;
+// Every kernel argument of one step of planner `pl`.
+struct StepArgs {
   PartTables tab;
   int check_lo = 0, check_hi = 0;
-  make_tables(p, tab, check_lo, check_hi);
+  PartitionArgs pa{};
+  CandArgs ca{};
+  GuideArgs ga{};
+  RolloutArgs ra{};  // ctr3 = step_id << 8; the iteration is ored in at launch
+  UpdateArgs ua{};
+  GridGeom grid{};
+  int ncell = 0, gcells = 0, ntiles = 0, nb = 0, lanes = 1;
+  int64_t n_items = 0;
+  bool raw = false;
+};
+
+// Lanes per sample of a step: the explicit choice, else four when E*K is at
+// most `quad_max`.
+int lanes_of(const aero_params_t& p, int64_t quad_max) {
+  if (p.lanes_per_sample != 0) return p.lanes_per_sample;
+  return (int64_t)p.E * p.K <= quad_max ? 4 : 1;
+}
+
+void make_step_args(aero_planner* pl, const aero_state_t* x0, const float* cloud, int64_t n,
+                    const float* goal, const aero_params_t& p, float* u_nom, float* u_best,
+                    float* cand, int32_t* best_idx, int lanes, bool coarse, StepArgs& a) {
+  a.ncell = p.fine_az * p.fine_el;
+  make_tables(p, a.tab, a.check_lo, a.check_hi);
   float R[9];
   rot_f32(x0->q, R);
   const float rm = p.r_max;
   const float rmax2 = rm * rm;
-  const bool raw = p.collision_set == 1;
-  const int64_t n_items = raw ? n : ncell;
-  const GridGeom grid = make_grid(p, n_items, pl->cand_cap, pl->grid_max);
-  const int gcells = grid.G * grid.G * grid.G;
-  const int ntiles = (gcells + 1 + kScanTile - 1) / kScanTile;
+  a.raw = p.collision_set == 1;
+  a.n_items = a.raw ? n : a.ncell;
+  a.grid = make_grid(p, a.n_items, pl->cand_cap, pl->grid_max, coarse);
+  a.gcells = a.grid.G * a.grid.G * a.grid.G;
+  a.ntiles = (a.gcells + 1 + kScanTile - 1) / kScanTile;
 
-  cudaError_t e;
-  aero_planner::ProfSlot* prof = prof_slot(pl, p.iters);
-  // event i of the slot, recorded only when its stage is timed
-  auto mark = [&](int stage, int i) {
-    if (prof && (prof->mask & (1 << stage))) {
-      cudaEventRecord(prof->ev[i], s);
-      prof->last = i;
-    }
-  };
-  mark(AERO_STAGE_PARTITION, 0);
-  if ((e = cudaMemsetAsync(pl->keys, 0xFF, sizeof(unsigned long long) * ncell, s)) != cudaSuccess)
-    return cuda_fail(e);
-  if (pl->grid_dirty) {
-    // the scan leaves the counts at zero; clear them only when a step may have
-    // stopped between the count pass and the scan
-    if ((e = cudaMemsetAsync(pl->grid_count, 0, sizeof(int) * (pl->grid_cells_cap + 1), s)) !=
-        cudaSuccess)
-      return cuda_fail(e);
-  }
-  pl->grid_dirty = true;
-
-  PartitionArgs pa{};
+  PartitionArgs& pa = a.pa;
   pa.cloud = cloud;
   pa.n = n;
   for (int i = 0; i < 3; ++i) pa.p0[i] = x0->p[i];
@@ -301,36 +302,28 @@ int enqueue_step(aero_planner* pl, const aero_state_t* x0, const float* cloud, i
   pa.rmax2 = rmax2;
   pa.A = p.fine_az;
   pa.El = p.fine_el;
-  pa.check_lo = check_lo;
-  pa.check_hi = check_hi;
+  pa.check_lo = a.check_lo;
+  pa.check_hi = a.check_hi;
   pa.keys = pl->keys;
-  pa.item_flag = raw ? pl->item_flag : nullptr;
-  if ((e = launch_partition(pa, tab, s)) != cudaSuccess) return cuda_fail(e);
-  mark(AERO_STAGE_PARTITION, 1);
-  mark(AERO_STAGE_GRID, 2);
-  if (prof) {
-    prof->launches[AERO_STAGE_PARTITION] = n > 0 ? 1 : 0;
-    prof->launches[AERO_STAGE_GRID] = 3;
-    prof->launches[AERO_STAGE_ROLLOUT] = p.iters;
-    prof->launches[AERO_STAGE_UPDATE] = p.iters;
-  }
+  pa.item_flag = a.raw ? pl->item_flag : nullptr;
 
-  CandArgs ca{};
+  CandArgs& ca = a.ca;
   ca.cloud = cloud;
   for (int i = 0; i < 3; ++i) ca.p0[i] = x0->p[i];
   ca.keys = pl->keys;
   ca.item_flag = pl->item_flag;
-  ca.n_items = n_items;
-  ca.raw = raw;
-  ca.grid = grid;
+  ca.n_items = a.n_items;
+  ca.raw = a.raw;
+  ca.grid = a.grid;
   ca.count = pl->grid_count;
   ca.fill = pl->grid_fill;
   ca.local = pl->grid_local;
   ca.tile_off = pl->tile_off;
   ca.cand = pl->cand;
   ca.status = pl->status;
+  ca.reset_keys = nullptr;
 
-  GuideArgs ga{};
+  GuideArgs& ga = a.ga;
   ga.keys = pl->keys;
   ga.A = p.fine_az;
   ga.El = p.fine_el;
@@ -356,14 +349,6 @@ int enqueue_step(aero_planner* pl, const aero_state_t* x0, const float* cloud, i
   ga.cells = pl->cells;
   ga.anchors = pl->anchors;
   ga.guides = pl->guides;
-  // count pass + coarse argmax/anchors/guides, scan, scatter + cell ranges
-  if ((e = launch_grid_count(ca, ga, tab, s)) != cudaSuccess) return cuda_fail(e);
-  if ((e = launch_grid_scan(pl->grid_count, pl->grid_fill, pl->grid_local, pl->tile_sum,
-                            pl->tile_off, gcells + 1, ntiles, pl->counter + 2, s)) != cudaSuccess)
-    return cuda_fail(e);
-
-  if ((e = launch_grid_scatter(ca, pl->grid_range, gcells, s)) != cudaSuccess) return cuda_fail(e);
-  mark(AERO_STAGE_GRID, 3);
 
   CostParams cp{};
   cp.Q_track = p.Q_track;
@@ -381,19 +366,18 @@ int enqueue_step(aero_planner* pl, const aero_state_t* x0, const float* cloud, i
   for (int i = 0; i < 3; ++i) cp.v_goal[i] = p.v_goal[i];
   for (int i = 0; i < 4; ++i) cp.q_goal[i] = p.q_goal[i];
   DynParams dp{p.dt, 1.0f / p.mass, p.g};
-  GridView gv{pl->grid_range, pl->cand, grid.G, grid.origin, grid.inv_h};
-  float x0v[10] = {0.0f, 0.0f, 0.0f, x0->q[0], x0->q[1], x0->q[2], x0->q[3],
-                   x0->v[0], x0->v[1], x0->v[2]};
-  const int lanes = p.lanes_per_sample == 0 ? ((int64_t)p.E * p.K <= kQuadMaxSamples ? 4 : 1)
-                                            : p.lanes_per_sample;
+  GridView gv{pl->grid_range, pl->cand, a.grid.G, a.grid.origin, a.grid.inv_h};
+  const float x0v[10] = {0.0f, 0.0f, 0.0f, x0->q[0], x0->q[1], x0->q[2], x0->q[3],
+                         x0->v[0], x0->v[1], x0->v[2]};
+  a.lanes = lanes;
   const int per_cta = kRolloutThreads / lanes;
-  const int nb = (p.K + per_cta - 1) / per_cta;
+  a.nb = (p.K + per_cta - 1) / per_cta;
 
-  RolloutArgs ra{};
+  RolloutArgs& ra = a.ra;
   ra.E = p.E;
   ra.K = p.K;
   ra.T = p.T;
-  ra.nb = nb;
+  ra.nb = a.nb;
   ra.lanes_per_sample = lanes;
   ra.inv_lambda = 1.0f / p.lambda;
   for (int c = 0; c < 4; ++c) {
@@ -404,6 +388,7 @@ int enqueue_step(aero_planner* pl, const aero_state_t* x0, const float* cloud, i
   for (int i = 0; i < 10; ++i) ra.x0[i] = x0v[i];
   ra.key0 = (uint32_t)p.seed;
   ra.key1 = (uint32_t)(p.seed >> 32);
+  ra.ctr3 = (uint32_t)(p.step_id << 8);
   ra.dyn = dp;
   ra.cost = cp;
   ra.u_nom = u_nom;
@@ -417,10 +402,10 @@ int enqueue_step(aero_planner* pl, const aero_state_t* x0, const float* cloud, i
   ra.dbg_x = pl->dbg_x;
   ra.dbg_d = pl->dbg_d;
 
-  UpdateArgs ua{};
+  UpdateArgs& ua = a.ua;
   ua.E = p.E;
   ua.T = p.T;
-  ua.nb = nb;
+  ua.nb = a.nb;
   ua.inv_lambda = ra.inv_lambda;
   ua.partials = pl->partials;
   ua.u_nom = u_nom;
@@ -434,24 +419,78 @@ int enqueue_step(aero_planner* pl, const aero_state_t* x0, const float* cloud, i
   ua.u_best = u_best;
   ua.counter = pl->counter;
   ua.status = pl->status;
+}
 
-  for (int it = 0; it < p.iters; ++it) {
-    ra.ctr3 = (uint32_t)((p.step_id << 8) | (uint64_t)(uint32_t)it);
-    mark(AERO_STAGE_ROLLOUT, 4 + 4 * it);
-    if ((e = launch_rollout(ra, s)) != cudaSuccess) return cuda_fail(e);
-    mark(AERO_STAGE_ROLLOUT, 5 + 4 * it);
-    ua.final_stage = it == p.iters - 1;
-    mark(AERO_STAGE_UPDATE, 6 + 4 * it);
-    if ((e = launch_update(ua, s)) != cudaSuccess) return cuda_fail(e);
-    mark(AERO_STAGE_UPDATE, 7 + 4 * it);
-  }
-
+// The planner's state after a step has been enqueued.
+void note_step(aero_planner* pl, const aero_params_t& p, const StepArgs& a) {
   pl->grid_dirty = false;
   pl->have_step = true;
   pl->last = p;
-  pl->last_grid = grid;
-  pl->last_ntiles = ntiles;
-  pl->last_nb = nb;
+  pl->last_grid = a.grid;
+  pl->last_ntiles = a.ntiles;
+  pl->last_nb = a.nb;
+}
+
+// Enqueue one step; all pointers already validated.
+int enqueue_step(aero_planner* pl, const aero_state_t* x0, const float* cloud, int64_t n,
+                 const float* goal, const aero_params_t& p, float* u_nom, float* u_best,
+                 float* cand, int32_t* best_idx, cudaStream_t s) {
+  StepArgs a;
+  make_step_args(pl, x0, cloud, n, goal, p, u_nom, u_best, cand, best_idx,
+                 lanes_of(p, kQuadMaxSamples), false, a);
+
+  cudaError_t e;
+  aero_planner::ProfSlot* prof = prof_slot(pl, p.iters);
+  // event i of the slot, recorded only when its stage is timed
+  auto mark = [&](int stage, int i) {
+    if (prof && (prof->mask & (1 << stage))) {
+      cudaEventRecord(prof->ev[i], s);
+      prof->last = i;
+    }
+  };
+  mark(AERO_STAGE_PARTITION, 0);
+  if ((e = cudaMemsetAsync(pl->keys, 0xFF, sizeof(unsigned long long) * a.ncell, s)) != cudaSuccess)
+    return cuda_fail(e);
+  pl->keys_empty = false;
+  if (pl->grid_dirty) {
+    // the scan leaves the counts at zero; clear them only when a step may have
+    // stopped between the count pass and the scan
+    if ((e = cudaMemsetAsync(pl->grid_count, 0, sizeof(int) * (pl->grid_cells_cap + 1), s)) !=
+        cudaSuccess)
+      return cuda_fail(e);
+  }
+  pl->grid_dirty = true;
+
+  if ((e = launch_partition(a.pa, a.tab, s)) != cudaSuccess) return cuda_fail(e);
+  mark(AERO_STAGE_PARTITION, 1);
+  mark(AERO_STAGE_GRID, 2);
+  if (prof) {
+    prof->launches[AERO_STAGE_PARTITION] = n > 0 ? 1 : 0;
+    prof->launches[AERO_STAGE_GRID] = 3;
+    prof->launches[AERO_STAGE_ROLLOUT] = p.iters;
+    prof->launches[AERO_STAGE_UPDATE] = p.iters;
+  }
+  // count pass + coarse argmax/anchors/guides, scan, scatter + cell ranges
+  if ((e = launch_grid_count(a.ca, a.ga, a.tab, s)) != cudaSuccess) return cuda_fail(e);
+  if ((e = launch_grid_scan(pl->grid_count, pl->grid_fill, pl->grid_local, pl->tile_sum,
+                            pl->tile_off, a.gcells + 1, a.ntiles, pl->counter + 2, s)) != cudaSuccess)
+    return cuda_fail(e);
+  if ((e = launch_grid_scatter(a.ca, pl->grid_range, a.gcells, s)) != cudaSuccess)
+    return cuda_fail(e);
+  mark(AERO_STAGE_GRID, 3);
+
+  const uint32_t ctr_base = a.ra.ctr3;
+  for (int it = 0; it < p.iters; ++it) {
+    a.ra.ctr3 = ctr_base | (uint32_t)it;
+    mark(AERO_STAGE_ROLLOUT, 4 + 4 * it);
+    if ((e = launch_rollout(a.ra, s)) != cudaSuccess) return cuda_fail(e);
+    mark(AERO_STAGE_ROLLOUT, 5 + 4 * it);
+    a.ua.final_stage = it == p.iters - 1;
+    mark(AERO_STAGE_UPDATE, 6 + 4 * it);
+    if ((e = launch_update(a.ua, s)) != cudaSuccess) return cuda_fail(e);
+    mark(AERO_STAGE_UPDATE, 7 + 4 * it);
+  }
+  note_step(pl, p, a);
   return AERO_OK;
 }
 
@@ -898,20 +937,93 @@ int aero_plan_step_noalloc(const aero_state_t* x0, const float* cloud, int64_t n
 // Batched planning: independent planners on a pool of streams.
 // ---------------------------------------------------------------------------
 struct aero_batch {
-  std::vector<aero_planner*> planners;
-  std::vector<cudaStream_t> streams;
-  std::vector<cudaEvent_t> joins;
-  cudaEvent_t fork = nullptr;
+  std::vector<aero_planner*> planners;  // one workspace per item slot
+  aero_limits_t lim{};
+  int sms = 0;
+  aero_batch_config_t cfg{0, 0, 1, 0};
+  int last_n = 0;  // items of the last call (debug copies)
+  // resident CTAs per SM of the batched kernels
+  int occ_grid[4] = {1, 1, 1, 1};  // partition, count, scan, scatter
+  int occ_roll[4] = {1, 1, 1, 1};  // rollout (1 lane), rollout (4 lanes), update, rollout (1 lane, 6/SM)
+  // device: the call's arguments (items, unit prefixes, rollout orders), the
+  // slots' edge tables, the rollout work queues
+  unsigned char* d_args = nullptr;
+  PartTables* d_tabs = nullptr;
+  unsigned int* d_queue = nullptr;
+  // pinned staging: a ring of argument buffers, the slots' tables
+  static constexpr int kRing = 4;
+  unsigned char* h_args[kRing] = {};
+  cudaEvent_t h_done[kRing] = {};
+  int ring = 0;
+  PartTables* h_tabs = nullptr;
+  cudaEvent_t tabs_done = nullptr;
+  struct TabKey {
+    int A = -1, El = -1;
+    float lo = 0.0f, hi = 0.0f;
+    bool operator==(const TabKey& o) const { return A == o.A && El == o.El && lo == o.lo && hi == o.hi; }
+  };
+  std::vector<TabKey> tab_key;
+  // instantiated graphs, one per shape and configuration
+  struct Graph {
+    int n, max_iters, has1, has4;
+    aero_batch_config_t cfg;
+    cudaGraphExec_t exec;
+  };
+  std::vector<Graph> graphs;
+  cudaStream_t cap = nullptr, cap2 = nullptr;
+  cudaEvent_t fork = nullptr, join = nullptr;
+  // tuning outputs, one block of floats per slot
+  float* scratch = nullptr;
+  size_t scratch_stride = 0;
 };
 
 namespace {
-constexpr int kBatchStreams = 16;
+
+struct ArgsLayout {
+  size_t items, pre, order1, order4, bytes;
+};
+
+size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
+
+ArgsLayout layout_for(int n) {
+  ArgsLayout L;
+  L.items = 0;
+  L.pre = align16(sizeof(BatchItem) * n);
+  L.order1 = L.pre + sizeof(long long) * kPreCount * (n + 1);
+  L.order4 = L.order1 + sizeof(int) * n;
+  L.bytes = align16(L.order4 + sizeof(int) * n);
+  return L;
+}
+
+BatchView view_of(aero_batch* b, int n) {
+  const ArgsLayout L = layout_for(n);
+  BatchView v;
+  v.items = reinterpret_cast<const BatchItem*>(b->d_args + L.items);
+  v.pre = reinterpret_cast<const long long*>(b->d_args + L.pre);
+  v.order1 = reinterpret_cast<const int*>(b->d_args + L.order1);
+  v.order4 = reinterpret_cast<const int*>(b->d_args + L.order4);
+  v.n = n;
+  v.queue = b->d_queue;
+  return v;
+}
 
 void batch_free(aero_batch* b) {
   for (aero_planner* pl : b->planners) aero_destroy(pl);
-  for (cudaStream_t st : b->streams) cudaStreamDestroy(st);
-  for (cudaEvent_t ev : b->joins) cudaEventDestroy(ev);
+  for (auto& g : b->graphs) cudaGraphExecDestroy(g.exec);
+  if (b->d_args) cudaFree(b->d_args);
+  if (b->d_tabs) cudaFree(b->d_tabs);
+  if (b->d_queue) cudaFree(b->d_queue);
+  if (b->scratch) cudaFree(b->scratch);
+  for (int r = 0; r < aero_batch::kRing; ++r) {
+    if (b->h_args[r]) cudaFreeHost(b->h_args[r]);
+    if (b->h_done[r]) cudaEventDestroy(b->h_done[r]);
+  }
+  if (b->h_tabs) cudaFreeHost(b->h_tabs);
+  if (b->tabs_done) cudaEventDestroy(b->tabs_done);
+  if (b->cap) cudaStreamDestroy(b->cap);
+  if (b->cap2) cudaStreamDestroy(b->cap2);
   if (b->fork) cudaEventDestroy(b->fork);
+  if (b->join) cudaEventDestroy(b->join);
   delete b;
 }
 
@@ -919,6 +1031,7 @@ int check_item(aero_planner* pl, const aero_batch_item_t& it) {
   if (!it.u_nom_inout || !it.u_best_out || !it.cand_costs_out || !it.best_idx_out)
     return AERO_ERR_INVALID_ARG;
   if (it.n_points > 0 && !it.cloud_xyz) return AERO_ERR_INVALID_ARG;
+  if (it.params.debug_samples != 0) return AERO_ERR_INVALID_ARG;
   const int rc = validate(pl, &it.params, it.n_points);
   if (rc != AERO_OK) return rc;
   if (reinterpret_cast<uintptr_t>(it.u_nom_inout) % 16 != 0) return AERO_ERR_INVALID_ARG;
@@ -928,67 +1041,379 @@ int check_item(aero_planner* pl, const aero_batch_item_t& it) {
     return AERO_ERR_NOT_DEVICE_PTR;
   return AERO_OK;
 }
+
+int check_config(const aero_batch_config_t& c) {
+  if (c.quad_max_samples < 0 || c.rollout_ctas_per_sm < 0 || c.rollout_ctas_per_sm > 64 ||
+      (c.dynamic_queue != 0 && c.dynamic_queue != 1) || (c.coarse_cells != 0 && c.coarse_cells != 1))
+    return AERO_ERR_INVALID_ARG;
+  return AERO_OK;
+}
+
+bool same_cfg(const aero_batch_config_t& a, const aero_batch_config_t& b) {
+  return a.quad_max_samples == b.quad_max_samples && a.rollout_ctas_per_sm == b.rollout_ctas_per_sm &&
+         a.dynamic_queue == b.dynamic_queue && a.coarse_cells == b.coarse_cells;
+}
+
+// The graph of one call shape: the four grid-stage launches, then per
+// iteration the Stage I launch(es) -- both lane widths side by side when both
+// occur -- and the update.
+cudaError_t batch_graph(aero_batch* b, int n, int max_iters, int has1, int has4,
+                        const aero_batch_config_t& cfg, cudaGraphExec_t* out) {
+  for (auto& g : b->graphs)
+    if (g.n == n && g.max_iters == max_iters && g.has1 == has1 && g.has4 == has4 &&
+        same_cfg(g.cfg, cfg)) {
+      *out = g.exec;
+      return cudaSuccess;
+    }
+  const BatchView v = view_of(b, n);
+  const int S = b->sms;
+  // rollout_ctas_per_sm >= 6 selects the one-lane kernel built for six CTAs per SM
+  const int six = cfg.rollout_ctas_per_sm >= 6 && b->occ_roll[3] >= 6;
+  auto roll_blocks = [&](int k) {
+    const int occ = k == 0 && six ? b->occ_roll[3] : b->occ_roll[k];
+    const int per = cfg.rollout_ctas_per_sm == 0 ? occ : cfg.rollout_ctas_per_sm;
+    return S * (per < 1 ? 1 : per);
+  };
+  cudaStream_t c = b->cap;
+  cudaError_t e = cudaStreamBeginCapture(c, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) return e;
+  cudaError_t le = launch_batch_partition(v, S * b->occ_grid[0], c);
+  if (le == cudaSuccess) le = launch_batch_count(v, S * b->occ_grid[1], c);
+  if (le == cudaSuccess) le = launch_batch_scan(v, S * b->occ_grid[2], c);
+  if (le == cudaSuccess) le = launch_batch_scatter(v, S * b->occ_grid[3], c);
+  for (int it = 0; it < max_iters && le == cudaSuccess; ++it) {
+    if (has1 && has4) {
+      le = cudaEventRecord(b->fork, c);
+      if (le == cudaSuccess) le = cudaStreamWaitEvent(b->cap2, b->fork, 0);
+      if (le == cudaSuccess)
+        le = launch_batch_rollout(v, 4, it, roll_blocks(1), cfg.dynamic_queue, 0, b->cap2);
+      if (le == cudaSuccess) le = launch_batch_rollout(v, 1, it, roll_blocks(0), cfg.dynamic_queue, six, c);
+      if (le == cudaSuccess) le = cudaEventRecord(b->join, b->cap2);
+      if (le == cudaSuccess) le = cudaStreamWaitEvent(c, b->join, 0);
+    } else {
+      le = launch_batch_rollout(v, has4 ? 4 : 1, it, roll_blocks(has4 ? 1 : 0), cfg.dynamic_queue,
+                                has4 ? 0 : six, c);
+    }
+    if (le == cudaSuccess) le = launch_batch_update(v, it, S * b->occ_roll[2], c);
+  }
+  cudaGraph_t graph = nullptr;
+  e = cudaStreamEndCapture(c, &graph);
+  if (le != cudaSuccess || e != cudaSuccess) {
+    if (graph) cudaGraphDestroy(graph);
+    cudaGetLastError();
+    return le != cudaSuccess ? le : e;
+  }
+  cudaGraphExec_t exec = nullptr;
+  e = cudaGraphInstantiate(&exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) return e;
+  b->graphs.push_back({n, max_iters, has1, has4, cfg, exec});
+  *out = exec;
+  return cudaSuccess;
+}
+
+// Enqueue one batched step of the n (validated) items on s.  scratch: write
+// every item's nominal and outputs to the batch's scratch slots instead (the
+// caller has copied the nominals there).
+int batch_enqueue(aero_batch* b, const aero_batch_item_t* items, int n, cudaStream_t s,
+                  const aero_batch_config_t& cfg, bool scratch) {
+  const ArgsLayout L = layout_for(n);
+  const int r = b->ring;
+  b->ring = (b->ring + 1) % aero_batch::kRing;
+  cudaError_t e = cudaEventSynchronize(b->h_done[r]);  // the slot's previous upload is done
+  if (e != cudaSuccess) return cuda_fail(e);
+  unsigned char* h = b->h_args[r];
+  BatchItem* hi = reinterpret_cast<BatchItem*>(h + L.items);
+  long long* pre = reinterpret_cast<long long*>(h + L.pre);
+  int* ord1 = reinterpret_cast<int*>(h + L.order1);
+  int* ord4 = reinterpret_cast<int*>(h + L.order4);
+  std::vector<long long> roll_units(n);
+  struct Meta {
+    GridGeom grid;
+    int ntiles, nb;
+  };
+  std::vector<Meta> meta(n);
+  std::vector<int> lanes(n), T(n);
+  std::vector<int> tab_changed;
+  int max_iters = 0, has1 = 0, has4 = 0;
+  for (int k = 0; k < kPreCount; ++k) pre[k * (n + 1)] = 0;
+  for (int i = 0; i < n; ++i) {
+    const aero_batch_item_t& it = items[i];
+    const aero_params_t& p = it.params;
+    aero_planner* pl = b->planners[i];
+    float* u_nom = it.u_nom_inout;
+    float* u_best = it.u_best_out;
+    float* cand = it.cand_costs_out;
+    int32_t* best = it.best_idx_out;
+    if (scratch) {
+      float* sc = b->scratch + b->scratch_stride * i;
+      u_nom = sc;
+      u_best = sc + (size_t)b->lim.E_max * b->lim.T_max * 4;
+      cand = u_best + (size_t)b->lim.T_max * 4;
+      best = reinterpret_cast<int32_t*>(cand + b->lim.E_max);
+    }
+    StepArgs a;
+    make_step_args(pl, &it.x0, it.cloud_xyz, it.n_points, it.goal, p, u_nom, u_best, cand, best,
+                   lanes_of(p, cfg.quad_max_samples), cfg.coarse_cells != 0, a);
+    BatchItem& bi = hi[i];
+    bi.pa = a.pa;
+    bi.ca = a.ca;
+    bi.ca.reset_keys = pl->keys;
+    bi.ga = a.ga;
+    bi.ra = a.ra;
+    bi.ua = a.ua;
+    bi.ua.final_stage = 0;
+    bi.tab = b->d_tabs + i;
+    bi.count = pl->grid_count;
+    bi.fill = pl->grid_fill;
+    bi.local = pl->grid_local;
+    bi.tile_sum = pl->tile_sum;
+    bi.tile_off = pl->tile_off;
+    bi.scan_counter = pl->counter + 2;
+    bi.range = pl->grid_range;
+    bi.keys = pl->keys;
+    bi.iters = p.iters;
+    bi.gcells = a.gcells;
+    bi.ntiles = a.ntiles;
+    bi.raw_keys = a.raw ? a.ncell : 0;
+    const aero_batch::TabKey key{p.fine_az, p.fine_el, p.el_lo, p.el_hi};
+    if (!(b->tab_key[i] == key)) {
+      if (tab_changed.empty() && (e = cudaEventSynchronize(b->tabs_done)) != cudaSuccess)
+        return cuda_fail(e);
+      b->h_tabs[i] = a.tab;
+      b->tab_key[i] = key;
+      tab_changed.push_back(i);
+    }
+    auto set = [&](int k, long long units) { pre[k * (n + 1) + i + 1] = pre[k * (n + 1) + i] + units; };
+    set(kPrePoints, (it.n_points + kPartChunk - 1) / kPartChunk);
+    set(kPreItems, a.n_items);
+    set(kPreCoarse, (long long)a.ga.Ac * a.ga.Ec);
+    set(kPreTiles, a.ntiles);
+    set(kPreCells, (long long)a.gcells + bi.raw_keys);
+    set(kPreUpdate, p.E);
+    roll_units[i] = (long long)p.E * a.nb;
+    meta[i] = {a.grid, a.ntiles, a.nb};
+    lanes[i] = a.lanes;
+    T[i] = p.T;
+    if (p.iters > max_iters) max_iters = p.iters;
+    (a.lanes == 4 ? has4 : has1) = 1;
+  }
+  // rollout order: longest horizon first, then more units, then slot index
+  std::vector<int> order(n);
+  for (int i = 0; i < n; ++i) order[i] = i;
+  std::sort(order.begin(), order.end(), [&](int x, int y) {
+    if (T[x] != T[y]) return T[x] > T[y];
+    if (roll_units[x] != roll_units[y]) return roll_units[x] > roll_units[y];
+    return x < y;
+  });
+  long long* p1 = pre + kPreRoll1 * (n + 1);
+  long long* p4 = pre + kPreRoll4 * (n + 1);
+  for (int q = 0; q < n; ++q) {
+    const int i = order[q];
+    ord1[q] = i;
+    ord4[q] = i;
+    p1[q + 1] = p1[q] + (lanes[i] == 1 ? roll_units[i] : 0);
+    p4[q + 1] = p4[q] + (lanes[i] == 4 ? roll_units[i] : 0);
+  }
+
+  cudaGraphExec_t exec = nullptr;
+  if ((e = batch_graph(b, n, max_iters, has1, has4, cfg, &exec)) != cudaSuccess) return cuda_fail(e);
+  // workspaces whose counts or keys may be stale (new slot, interrupted step)
+  for (int i = 0; i < n; ++i) {
+    aero_planner* pl = b->planners[i];
+    if (pl->grid_dirty &&
+        (e = cudaMemsetAsync(pl->grid_count, 0, sizeof(int) * (pl->grid_cells_cap + 1), s)) != cudaSuccess)
+      return cuda_fail(e);
+    if (!pl->keys_empty &&
+        (e = cudaMemsetAsync(pl->keys, 0xFF, sizeof(unsigned long long) * pl->lim.fine_cells_max, s)) !=
+            cudaSuccess)
+      return cuda_fail(e);
+    pl->grid_dirty = true;
+    pl->keys_empty = false;
+  }
+  for (int i : tab_changed)
+    if ((e = cudaMemcpyAsync(b->d_tabs + i, b->h_tabs + i, sizeof(PartTables), cudaMemcpyHostToDevice,
+                             s)) != cudaSuccess)
+      return cuda_fail(e);
+  if (!tab_changed.empty() && (e = cudaEventRecord(b->tabs_done, s)) != cudaSuccess) return cuda_fail(e);
+  if ((e = cudaMemcpyAsync(b->d_args, h, L.bytes, cudaMemcpyHostToDevice, s)) != cudaSuccess ||
+      (e = cudaEventRecord(b->h_done[r], s)) != cudaSuccess)
+    return cuda_fail(e);
+  if ((e = cudaGraphLaunch(exec, s)) != cudaSuccess) return cuda_fail(e);
+  for (int i = 0; i < n; ++i) {
+    aero_planner* pl = b->planners[i];
+    pl->grid_dirty = false;
+    pl->keys_empty = true;
+    pl->have_step = true;
+    pl->last = items[i].params;
+    pl->last_grid = meta[i].grid;
+    pl->last_ntiles = meta[i].ntiles;
+    pl->last_nb = meta[i].nb;
+  }
+  b->last_n = n;
+  return AERO_OK;
+}
+
+int check_items(aero_batch* b, const aero_batch_item_t* items, int32_t n) {
+  if (!b || (n > 0 && !items) || n < 0 || n > (int32_t)b->planners.size()) return AERO_ERR_INVALID_ARG;
+  for (int i = 0; i < n; ++i) {
+    const int rc = check_item(b->planners[i], items[i]);
+    if (rc != AERO_OK) return rc;
+  }
+  return AERO_OK;
+}
 }  // namespace
 
 int aero_batch_create(const aero_limits_t* limits, int32_t n_max, aero_batch_t** out) {
-  if (!limits || !out || n_max < 1 || n_max > 4096) return AERO_ERR_INVALID_ARG;
+  if (!limits || !out || n_max < 1 || n_max > kBatchMax) return AERO_ERR_INVALID_ARG;
   *out = nullptr;
   aero_batch* b = new (std::nothrow) aero_batch();
   if (!b) return AERO_ERR_ALLOC;
+  b->lim = *limits;
+  b->lim.debug_samples_max = 0;
   for (int i = 0; i < n_max; ++i) {
     aero_planner_t* pl = nullptr;
-    const int rc = aero_create(limits, &pl);
+    const int rc = aero_create(&b->lim, &pl);
     if (rc != AERO_OK) {
       batch_free(b);
       return rc;
     }
     b->planners.push_back(pl);
   }
-  const int ns = n_max < kBatchStreams ? n_max : kBatchStreams;
-  cudaError_t e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
-  for (int i = 0; i < ns && e == cudaSuccess; ++i) {
-    cudaStream_t st;
-    cudaEvent_t ev;
-    e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
-    if (e != cudaSuccess) break;
-    b->streams.push_back(st);
-    e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
-    if (e != cudaSuccess) break;
-    b->joins.push_back(ev);
+  b->tab_key.assign(n_max, aero_batch::TabKey{});
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e == cudaSuccess) e = batch_grid_occupancy(b->occ_grid);
+  if (e == cudaSuccess) e = batch_rollout_occupancy(b->occ_roll);
+  const size_t bytes = layout_for(n_max).bytes;
+  if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_args, bytes);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_tabs, sizeof(PartTables) * n_max);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_queue, 4 * sizeof(unsigned int));
+  if (e == cudaSuccess) e = cudaMemset(b->d_queue, 0, 4 * sizeof(unsigned int));
+  b->scratch_stride = align16(sizeof(float) * ((size_t)b->lim.E_max * b->lim.T_max * 4 +
+                                               (size_t)b->lim.T_max * 4 + b->lim.E_max + 1)) /
+                      sizeof(float);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&b->scratch, sizeof(float) * b->scratch_stride * n_max);
+  for (int r = 0; r < aero_batch::kRing && e == cudaSuccess; ++r) {
+    e = cudaMallocHost((void**)&b->h_args[r], bytes);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->h_done[r], cudaEventDisableTiming);
   }
+  if (e == cudaSuccess) e = cudaMallocHost((void**)&b->h_tabs, sizeof(PartTables) * n_max);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->tabs_done, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->cap2, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->join, cudaEventDisableTiming);
   if (e != cudaSuccess) {
     cudaGetLastError();
     batch_free(b);
-    return AERO_ERR_CUDA;
+    return e == cudaErrorMemoryAllocation ? AERO_ERR_ALLOC : AERO_ERR_CUDA;
   }
   *out = b;
   return AERO_OK;
 }
 
 int aero_batch_plan(aero_batch_t* b, const aero_batch_item_t* items, int32_t n, void* stream) {
-  if (!b || !items || n < 0 || n > (int32_t)b->planners.size()) return AERO_ERR_INVALID_ARG;
-  for (int i = 0; i < n; ++i) {
-    const int rc = check_item(b->planners[i], items[i]);
-    if (rc != AERO_OK) return rc;
-  }
-  if (n == 0) return AERO_OK;
+  int rc = check_items(b, items, n);
+  if (rc != AERO_OK || n == 0) return rc;
+  return batch_enqueue(b, items, n, (cudaStream_t)stream, b->cfg, false);
+}
+
+int aero_batch_set_config(aero_batch_t* b, const aero_batch_config_t* c) {
+  if (!b || !c) return AERO_ERR_INVALID_ARG;
+  const int rc = check_config(*c);
+  if (rc != AERO_OK) return rc;
+  b->cfg = *c;
+  return AERO_OK;
+}
+
+int aero_batch_get_config(aero_batch_t* b, aero_batch_config_t* c) {
+  if (!b || !c) return AERO_ERR_INVALID_ARG;
+  *c = b->cfg;
+  return AERO_OK;
+}
+
+int aero_batch_tune(aero_batch_t* b, const aero_batch_item_t* items, int32_t n, int32_t repeats,
+                    void* stream, aero_batch_config_t* best, float* best_ms) {
+  if (repeats < 1 || repeats > 1000) return AERO_ERR_INVALID_ARG;
+  int rc = check_items(b, items, n);
+  if (rc != AERO_OK) return rc;
+  if (n == 0) return AERO_ERR_INVALID_ARG;
   cudaStream_t s = (cudaStream_t)stream;
-  const int ns = n < (int)b->streams.size() ? n : (int)b->streams.size();
-  cudaError_t e = cudaEventRecord(b->fork, s);
-  for (int k = 0; k < ns && e == cudaSuccess; ++k) e = cudaStreamWaitEvent(b->streams[k], b->fork, 0);
-  if (e != cudaSuccess) return AERO_ERR_CUDA;
-  for (int i = 0; i < n; ++i) {
-    const aero_batch_item_t& it = items[i];
-    const int rc = enqueue_step(b->planners[i], &it.x0, it.cloud_xyz, it.n_points, it.goal,
-                                it.params, it.u_nom_inout, it.u_best_out, it.cand_costs_out,
-                                it.best_idx_out, b->streams[i % ns]);
-    if (rc != AERO_OK) return rc;
+  cudaEvent_t t0 = nullptr, t1 = nullptr;
+  cudaError_t e = cudaEventCreate(&t0);
+  if (e == cudaSuccess) e = cudaEventCreate(&t1);
+  auto fail = [&](int code) {
+    if (t0) cudaEventDestroy(t0);
+    if (t1) cudaEventDestroy(t1);
+    return code;
+  };
+  if (e != cudaSuccess) return fail(AERO_ERR_CUDA);
+  aero_batch_config_t chosen = b->cfg;
+  float chosen_ms = INFINITY;
+  const int quad[3] = {0, 4096, 32768};
+  const int lo = b->occ_roll[0] < b->occ_roll[1] ? b->occ_roll[0] : b->occ_roll[1];
+  const int ctas[3] = {0, 6, lo / 2 > 0 ? lo / 2 : 1};
+  for (int qi = 0; qi < 3; ++qi)
+    for (int ci = 0; ci < 3; ++ci)
+      for (int dyn = 1; dyn >= 0; --dyn)
+        for (int coarse = 0; coarse < 2; ++coarse) {
+          const aero_batch_config_t c{quad[qi], ctas[ci], dyn, coarse};
+          float total = 0.0f;
+          for (int rep = 0; rep <= repeats; ++rep) {
+            for (int i = 0; i < n; ++i) {
+              const aero_params_t& p = items[i].params;
+              if ((e = cudaMemcpyAsync(b->scratch + b->scratch_stride * i, items[i].u_nom_inout,
+                                       sizeof(float) * p.E * p.T * 4, cudaMemcpyDeviceToDevice, s)) !=
+                  cudaSuccess)
+                return fail(AERO_ERR_CUDA);
+            }
+            if ((e = cudaEventRecord(t0, s)) != cudaSuccess) return fail(AERO_ERR_CUDA);
+            rc = batch_enqueue(b, items, n, s, c, true);
+            if (rc != AERO_OK) return fail(rc);
+            if ((e = cudaEventRecord(t1, s)) != cudaSuccess || (e = cudaEventSynchronize(t1)) != cudaSuccess)
+              return fail(AERO_ERR_CUDA);
+            float ms = 0.0f;
+            cudaEventElapsedTime(&ms, t0, t1);
+            if (rep > 0) total += ms;  // the first run warms up (and instantiates the graph)
+          }
+          const float mean = total / repeats;
+          if (mean < chosen_ms) {
+            chosen_ms = mean;
+            chosen = c;
+          }
+        }
+  b->cfg = chosen;
+  if (best) *best = chosen;
+  if (best_ms) *best_ms = chosen_ms;
+  return fail(AERO_OK);
+}
+
+int aero_batch_sync_status(aero_batch_t* b, int32_t* status) {
+  if (!b || !status) return AERO_ERR_INVALID_ARG;
+  if (cudaDeviceSynchronize() != cudaSuccess) return AERO_ERR_CUDA;
+  int32_t acc = 0;
+  for (aero_planner* pl : b->planners) {
+    int st = 0;
+    if (cudaMemcpy(&st, pl->status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+      return AERO_ERR_CUDA;
+    if (st != 0 && cudaMemset(pl->status, 0, sizeof(int)) != cudaSuccess) return AERO_ERR_CUDA;
+    acc |= st;
   }
-  for (int k = 0; k < ns && e == cudaSuccess; ++k) {
-    e = cudaEventRecord(b->joins[k], b->streams[k]);
-    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, b->joins[k], 0);
-  }
-  return cuda_fail(e);
+  *status = acc;
+  return AERO_OK;
+}
+
+size_t aero_batch_debug_size(aero_batch_t* b, int32_t slot, int32_t what) {
+  if (!b || slot < 0 || slot >= b->last_n) return 0;
+  return aero_debug_size(b->planners[slot], what);
+}
+
+int aero_batch_get_debug(aero_batch_t* b, int32_t slot, int32_t what, void* dst, size_t bytes,
+                         void* stream) {
+  if (!b || slot < 0 || slot >= b->last_n) return AERO_ERR_INVALID_ARG;
+  return aero_get_debug(b->planners[slot], what, dst, bytes, stream);
 }
 
 int aero_batch_destroy(aero_batch_t* b) {

@@ -220,4 +220,39 @@ __device__ __forceinline__ float warp_sum4(float a0, float a1, float a2, float a
   return c;
 }
 
+// ---------------------------------------------------------------------------
+// Batched launches: unit -> planner lookup and block-wide copies of arguments.
+// ---------------------------------------------------------------------------
+// Largest i in [0, n) with pre[i] <= u (pre ascending from pre[0] = 0, u < pre[n]).
+__device__ __forceinline__ int find_unit(const long long* pre, int n, long long u) {
+  int lo = 0, hi = n - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (pre[mid] <= u) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+// The block copies n + 1 prefix entries (or n order entries) to shared memory.
+__device__ __forceinline__ void load_prefix(long long* dst, const long long* src, int n) {
+  for (int i = threadIdx.x; i <= n; i += blockDim.x) dst[i] = __ldg(src + i);
+}
+
+template <typename T>
+__device__ __forceinline__ void block_copy(T* dst, const T* src) {
+  static_assert(sizeof(T) % 4 == 0, "word copy");
+  const uint32_t* s = reinterpret_cast<const uint32_t*>(src);
+  uint32_t* d = reinterpret_cast<uint32_t*>(dst);
+  for (int i = threadIdx.x; i < (int)(sizeof(T) / 4); i += blockDim.x) d[i] = __ldg(s + i);
+}
+
+// Copy of a kernel parameter (no __ldg: parameters are not in global memory).
+template <typename T>
+__device__ __forceinline__ void block_copy_param(T* dst, const T* src) {
+  static_assert(sizeof(T) % 4 == 0, "word copy");
+  const uint32_t* s = reinterpret_cast<const uint32_t*>(src);
+  uint32_t* d = reinterpret_cast<uint32_t*>(dst);
+  for (int i = threadIdx.x; i < (int)(sizeof(T) / 4); i += blockDim.x) d[i] = s[i];
+}
+
 }  // namespace aero

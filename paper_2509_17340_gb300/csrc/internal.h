@@ -68,6 +68,7 @@ struct CandArgs {
   const int* tile_off; // exclusive prefix of the tile totals (scatter pass)
   float4* cand;        // candidate entries (scatter pass)
   int* status;
+  unsigned long long* reset_keys;  // non-null: the scatter pass empties each key it reads
 };
 
 struct GuideArgs {
@@ -147,6 +148,74 @@ struct UpdateArgs {
   unsigned int* counter;   // last-CTA ticket, 0 between launches
   int* status;             // bit 0: a normaliser eta was not a positive finite number
 };
+
+// ---------------------------------------------------------------------------
+// Batched step: the planning steps of many independent planners, each stage one
+// launch over the work units of all of them.  A unit maps to its planner through
+// an exclusive prefix of the per-planner unit counts (binary search in shared
+// memory); the rollout takes its units from a device work queue in the order of
+// `order1` / `order4` (longest horizon first).
+// ---------------------------------------------------------------------------
+constexpr int kBatchMax = 256;       // planners per batched call
+constexpr int kPartChunk = 1024;     // points per partition unit
+
+enum BatchPrefix {
+  kPrePoints = 0,  // partition units (kPartChunk points)
+  kPreItems,       // collision items (count and scatter tasks, one warp each)
+  kPreCoarse,      // coarse cells (one warp each)
+  kPreTiles,       // scan tiles
+  kPreCells,       // grid cells (range of each) and, after them, raw-set keys to reset
+  kPreRoll1,       // rollout units, one lane per sample, in order1
+  kPreRoll4,       // rollout units, four lanes per sample, in order4
+  kPreUpdate,      // (planner, instance) units of the update
+  kPreCount
+};
+
+struct BatchItem {
+  PartitionArgs pa;
+  CandArgs ca;
+  GuideArgs ga;
+  RolloutArgs ra;            // ctr3 = step_id << 8: the launch ors in the iteration
+  UpdateArgs ua;             // final_stage unused: iteration it is final when it == iters - 1
+  const PartTables* tab;     // device copy of the planner's tables
+  int* count;
+  int* fill;
+  int* local;
+  int* tile_sum;
+  int* tile_off;
+  unsigned int* scan_counter;
+  int2* range;
+  unsigned long long* keys;  // fine-cell keys, left empty (all ones) by the step
+  int iters;
+  int gcells;                // G^3
+  int ntiles;
+  int raw_keys;              // fine cells whose keys the scatter launch resets (raw set), else 0
+};
+
+struct BatchView {
+  const BatchItem* items;
+  const long long* pre;      // kPreCount x (n + 1) exclusive prefixes of unit counts
+  const int* order1;         // rollout position -> planner (one lane per sample)
+  const int* order4;         // (four lanes per sample)
+  int n;
+  unsigned int* queue;       // per rollout kernel: {next unit, exit ticket}, zero between launches
+};
+
+cudaError_t launch_batch_partition(const BatchView& v, int blocks, cudaStream_t s);
+cudaError_t launch_batch_count(const BatchView& v, int blocks, cudaStream_t s);
+cudaError_t launch_batch_scan(const BatchView& v, int blocks, cudaStream_t s);
+cudaError_t launch_batch_scatter(const BatchView& v, int blocks, cudaStream_t s);
+// lanes 1 or 4; dynamic: take units from the work queue, else stride by the grid;
+// six: the one-lane kernel compiled for six resident CTAs per SM (fewer
+// registers) instead of five
+cudaError_t launch_batch_rollout(const BatchView& v, int lanes, int it, int blocks, int dynamic,
+                                 int six, cudaStream_t s);
+cudaError_t launch_batch_update(const BatchView& v, int it, int blocks, cudaStream_t s);
+
+// Resident CTAs per SM: {partition, count, scan, scatter} and {rollout with one
+// lane per sample, with four, update, rollout with one lane compiled for six}.
+cudaError_t batch_grid_occupancy(int out[4]);
+cudaError_t batch_rollout_occupancy(int out[4]);
 
 cudaError_t launch_partition(const PartitionArgs& a, const PartTables& t, cudaStream_t s);
 cudaError_t launch_grid_count(const CandArgs& ca, const GuideArgs& ga, const PartTables& t,

@@ -54,46 +54,59 @@ __device__ __forceinline__ int el_bin(const float* ce, const float* se, int El, 
 // ---------------------------------------------------------------------------
 // K1: cone of every point and atomic minimum of its key per cone.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_partition(PartitionArgs a, PartTables t) {
-  __shared__ float s_ca[kMaxAz], s_sa[kMaxAz], s_ce[kMaxEl + 1], s_se[kMaxEl + 1];
-  for (int i = threadIdx.x; i < a.A; i += blockDim.x) {
-    s_ca[i] = t.ca[i];
-    s_sa[i] = t.sa[i];
+// Edge tables in shared memory.
+struct SmemTables {
+  float ca[kMaxAz], sa[kMaxAz], ce[kMaxEl + 1], se[kMaxEl + 1];
+};
+
+__device__ __forceinline__ void load_tables(const PartTables& t, int A, int El, SmemTables& s) {
+  for (int i = threadIdx.x; i < A; i += blockDim.x) {
+    s.ca[i] = t.ca[i];
+    s.sa[i] = t.sa[i];
   }
-  for (int i = threadIdx.x; i <= a.El; i += blockDim.x) {
-    s_ce[i] = t.ce[i];
-    s_se[i] = t.se[i];
+  for (int i = threadIdx.x; i <= El; i += blockDim.x) {
+    s.ce[i] = t.ce[i];
+    s.se[i] = t.se[i];
   }
-  __syncthreads();
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += stride) {
-    const float px = __ldg(a.cloud + 3 * i), py = __ldg(a.cloud + 3 * i + 1),
-                pz = __ldg(a.cloud + 3 * i + 2);
-    int cell = -1;
-    if (isfinite(px) && isfinite(py) && isfinite(pz)) {
-      const float dx = sub(px, a.p0[0]), dy = sub(py, a.p0[1]), dz = sub(pz, a.p0[2]);
-      float b[3];
-      to_body(a.R, dx, dy, dz, b);
-      const float rxy2 = add(mul(b[0], b[0]), mul(b[1], b[1]));
-      const float r2 = add(rxy2, mul(b[2], b[2]));
-      if (r2 > 0.0f && r2 <= a.rmax2) {
-        const float rho = __fsqrt_rn(rxy2);
-        bool ok = true;
-        if (a.check_lo && !(sub(mul(b[2], s_ce[0]), mul(rho, s_se[0])) >= 0.0f)) ok = false;
-        if (a.check_hi && (sub(mul(b[2], s_ce[a.El]), mul(rho, s_se[a.El])) > 0.0f)) ok = false;
-        if (ok) {
-          const int ia = az_bin(s_ca, s_sa, a.A, b[0], b[1]);
-          const int je = el_bin(s_ce, s_se, a.El, b[2], rho);
-          const int c = je * a.A + ia;
-          const unsigned long long key =
-              ((unsigned long long)__float_as_uint(r2) << 32) | (unsigned long long)(uint32_t)i;
-          atomicMin(a.keys + c, key);
-          cell = c;
-        }
+}
+
+__device__ __forceinline__ void partition_point(const PartitionArgs& a, const SmemTables& st,
+                                                int64_t i) {
+  const float px = __ldg(a.cloud + 3 * i), py = __ldg(a.cloud + 3 * i + 1),
+              pz = __ldg(a.cloud + 3 * i + 2);
+  int cell = -1;
+  if (isfinite(px) && isfinite(py) && isfinite(pz)) {
+    const float dx = sub(px, a.p0[0]), dy = sub(py, a.p0[1]), dz = sub(pz, a.p0[2]);
+    float b[3];
+    to_body(a.R, dx, dy, dz, b);
+    const float rxy2 = add(mul(b[0], b[0]), mul(b[1], b[1]));
+    const float r2 = add(rxy2, mul(b[2], b[2]));
+    if (r2 > 0.0f && r2 <= a.rmax2) {
+      const float rho = __fsqrt_rn(rxy2);
+      bool ok = true;
+      if (a.check_lo && !(sub(mul(b[2], st.ce[0]), mul(rho, st.se[0])) >= 0.0f)) ok = false;
+      if (a.check_hi && (sub(mul(b[2], st.ce[a.El]), mul(rho, st.se[a.El])) > 0.0f)) ok = false;
+      if (ok) {
+        const int ia = az_bin(st.ca, st.sa, a.A, b[0], b[1]);
+        const int je = el_bin(st.ce, st.se, a.El, b[2], rho);
+        const int c = je * a.A + ia;
+        const unsigned long long key =
+            ((unsigned long long)__float_as_uint(r2) << 32) | (unsigned long long)(uint32_t)i;
+        atomicMin(a.keys + c, key);
+        cell = c;
       }
     }
-    if (a.item_flag) a.item_flag[i] = cell >= 0 ? 1 : 0;
   }
+  if (a.item_flag) a.item_flag[i] = cell >= 0 ? 1 : 0;
+}
+
+__global__ void __launch_bounds__(256) k_partition(PartitionArgs a, PartTables t) {
+  __shared__ SmemTables st;
+  load_tables(t, a.A, a.El, st);
+  __syncthreads();
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += stride)
+    partition_point(a, st, i);
 }
 
 // ---------------------------------------------------------------------------
@@ -126,43 +139,51 @@ __device__ __forceinline__ float gap2(float v, float lo, float h) {
 }
 
 // One warp per collision item; its lanes share the item's block of cells.
+template <bool kScatter>
+__device__ __forceinline__ void cand_task(const CandArgs& a, int64_t it, int lane) {
+  const GridGeom& g = a.grid;
+  const float r2 = g.reach * g.reach;
+  float px, py, pz;
+  if (!cand_item(a, it, px, py, pz)) return;  // uniform across the warp
+  if (kScatter && a.reset_keys && !a.raw) {
+    // the scatter pass is the key's last reader in a step
+    __syncwarp();
+    if (lane == 0) a.reset_keys[it] = kEmpty;
+  }
+  const int x0 = max(__float2int_rd((px - g.reach - g.origin) * g.inv_h), 0);
+  const int x1 = min(__float2int_rd((px + g.reach - g.origin) * g.inv_h), g.G - 1);
+  const int y0 = max(__float2int_rd((py - g.reach - g.origin) * g.inv_h), 0);
+  const int y1 = min(__float2int_rd((py + g.reach - g.origin) * g.inv_h), g.G - 1);
+  const int z0 = max(__float2int_rd((pz - g.reach - g.origin) * g.inv_h), 0);
+  const int z1 = min(__float2int_rd((pz + g.reach - g.origin) * g.inv_h), g.G - 1);
+  const int nx = x1 - x0 + 1, ny = y1 - y0 + 1, nz = z1 - z0 + 1;
+  if (nx <= 0 || ny <= 0 || nz <= 0) return;
+  const int ncand = nx * ny * nz;
+  for (int o = lane; o < ncand; o += 32) {
+    const int x = x0 + o % nx, y = y0 + (o / nx) % ny, z = z0 + o / (nx * ny);
+    const float d2 = gap2(px, g.origin + x * g.h, g.h) + gap2(py, g.origin + y * g.h, g.h) +
+                     gap2(pz, g.origin + z * g.h, g.h);
+    if (d2 >= r2) continue;
+    const int c = (z * g.G + y) * g.G + x;
+    if (!kScatter) {
+      atomicAdd(a.count + c, 1);
+    } else {
+      const int pos = a.local[c] + a.tile_off[c >> kScanTileShift] + atomicAdd(a.fill + c, 1);
+      if (pos < g.cap)
+        a.cand[pos] = make_float4(px, py, pz, 0.0f);
+      else
+        atomicOr(a.status, 2);
+    }
+  }
+}
+
 // `block` / `nblocks`: this block's index within the blocks given to the pass.
 template <bool kScatter>
 __device__ void cand_pass(const CandArgs& a, int block, int nblocks) {
   const int lane = threadIdx.x & 31;
   const int64_t warps = (int64_t)nblocks * (blockDim.x >> 5);
-  const GridGeom& g = a.grid;
-  const float r2 = g.reach * g.reach;
-  for (int64_t it = ((int64_t)block * blockDim.x + threadIdx.x) >> 5; it < a.n_items;
-       it += warps) {
-    float px, py, pz;
-    if (!cand_item(a, it, px, py, pz)) continue;  // uniform across the warp
-    const int x0 = max(__float2int_rd((px - g.reach - g.origin) * g.inv_h), 0);
-    const int x1 = min(__float2int_rd((px + g.reach - g.origin) * g.inv_h), g.G - 1);
-    const int y0 = max(__float2int_rd((py - g.reach - g.origin) * g.inv_h), 0);
-    const int y1 = min(__float2int_rd((py + g.reach - g.origin) * g.inv_h), g.G - 1);
-    const int z0 = max(__float2int_rd((pz - g.reach - g.origin) * g.inv_h), 0);
-    const int z1 = min(__float2int_rd((pz + g.reach - g.origin) * g.inv_h), g.G - 1);
-    const int nx = x1 - x0 + 1, ny = y1 - y0 + 1, nz = z1 - z0 + 1;
-    if (nx <= 0 || ny <= 0 || nz <= 0) continue;
-    const int ncand = nx * ny * nz;
-    for (int o = lane; o < ncand; o += 32) {
-      const int x = x0 + o % nx, y = y0 + (o / nx) % ny, z = z0 + o / (nx * ny);
-      const float d2 = gap2(px, g.origin + x * g.h, g.h) + gap2(py, g.origin + y * g.h, g.h) +
-                       gap2(pz, g.origin + z * g.h, g.h);
-      if (d2 >= r2) continue;
-      const int c = (z * g.G + y) * g.G + x;
-      if (!kScatter) {
-        atomicAdd(a.count + c, 1);
-      } else {
-        const int pos = a.local[c] + a.tile_off[c >> kScanTileShift] + atomicAdd(a.fill + c, 1);
-        if (pos < g.cap)
-          a.cand[pos] = make_float4(px, py, pz, 0.0f);
-        else
-          atomicOr(a.status, 2);
-      }
-    }
-  }
+  for (int64_t it = ((int64_t)block * blockDim.x + threadIdx.x) >> 5; it < a.n_items; it += warps)
+    cand_task<kScatter>(a, it, lane);
 }
 
 // ---------------------------------------------------------------------------
@@ -218,12 +239,14 @@ __device__ void scan_tile_offsets(const int* tile_sum, int* tile_off, int ntiles
 // K2b: tile-local exclusive scan of the counts (4096 cells per block, the
 // counts cleared for reuse as fill cursors by the scatter); the last block to
 // finish scans the tile totals into tile offsets.
-__global__ void __launch_bounds__(kScanThreads) k_grid_scan(int* count, int* fill, int* local,
-                                                            int* tile_sum, int* tile_off, int ncells,
-                                                            int ntiles, unsigned int* counter) {
+// One tile: writes the tile-local prefix and the tile total; returns whether
+// this block finished the last tile of the grid (then it has scanned the tile
+// totals into tile offsets).
+__device__ bool scan_tile(int* count, int* fill, int* local, int* tile_sum, int* tile_off,
+                          int ncells, int ntiles, int tile, unsigned int* counter) {
   __shared__ int s_warp[32];
   __shared__ bool s_last;
-  const int i0 = blockIdx.x * kScanTile + 4 * threadIdx.x;  // a multiple of 4: int4-aligned
+  const int i0 = tile * kScanTile + 4 * threadIdx.x;  // a multiple of 4: int4-aligned
   const bool full = i0 + 3 < ncells;
   int v[4];
   if (full) {
@@ -253,83 +276,71 @@ __global__ void __launch_bounds__(kScanThreads) k_grid_scan(int* count, int* fil
   }
   // the last block reads only the tile totals: only their writer fences
   if (threadIdx.x == 0) {
-    tile_sum[blockIdx.x] = total;
+    tile_sum[tile] = total;
     __threadfence();
-    s_last = atomicAdd(counter, 1u) == gridDim.x - 1;
+    s_last = atomicAdd(counter, 1u) == (unsigned)(ntiles - 1);
   }
   __syncthreads();
-  if (!s_last) return;
+  if (!s_last) return false;
   __threadfence();
   if (threadIdx.x == 0) *counter = 0u;
   scan_tile_offsets(tile_sum, tile_off, ntiles);
+  return true;
 }
 
-// `ncb` blocks, one warp per coarse cell; the last of them to finish continues
-// with the goal cone, anchors and guides.
-__device__ void coarse_guides_block(const GuideArgs& a, const PartTables& t, int cb, int ncb) {
-  __shared__ float s_ca[kMaxAz], s_sa[kMaxAz], s_ce[kMaxEl + 1], s_se[kMaxEl + 1];
-  __shared__ float s_coef[kMaxE][3][6];
-  __shared__ bool s_last;
-  // coarse argmax (Eq. safe-vector): larger r, then nearer the coarse centre,
-  // then lower fine index; empty cones count as r_max.
+__global__ void __launch_bounds__(kScanThreads) k_grid_scan(int* count, int* fill, int* local,
+                                                            int* tile_sum, int* tile_off, int ncells,
+                                                            int ntiles, unsigned int* counter) {
+  scan_tile(count, fill, local, tile_sum, tile_off, ncells, ntiles, blockIdx.x, counter);
+}
+
+// Coarse argmax of one coarse cell (Eq. safe-vector) by one warp: larger r,
+// then nearer the coarse centre, then lower fine index; empty cones count as
+// r_max.  Each lane takes a strided share of the pooled cones, then the warp
+// reduces (r key, centre distance, fine index).
+__device__ __forceinline__ void coarse_cell(const GuideArgs& a, int cc, int lane) {
   const uint32_t empty_bits = __float_as_uint(a.rmax2);
-  const int ncoarse = a.Ac * a.Ec;
-  const int lane = threadIdx.x & 31, nwarp = ncb * (blockDim.x >> 5);
   const int npool = a.Pa * a.Pe;
-  // one warp per coarse cell: each lane takes a strided share of the pooled
-  // cones, then the warp reduces (r key, centre distance, fine index)
-  for (int cc = cb * (blockDim.x >> 5) + (threadIdx.x >> 5); cc < ncoarse; cc += nwarp) {
-    const int I = cc % a.Ac, J = cc / a.Ac;
-    uint32_t bkey = 0;
-    int bdist = 0x7fffffff, best = 0x7fffffff;
-    for (int m = lane; m < npool; m += 32) {
-      const int q = m % a.Pa, b = m / a.Pa;
-      const int c = (J * a.Pe + b) * a.A + I * a.Pa + q;
-      const unsigned long long k = a.keys[c];
-      const uint32_t rk = k == kEmpty ? empty_bits : (uint32_t)(k >> 32);
-      const int dist = abs(2 * q + 1 - a.Pa) + abs(2 * b + 1 - a.Pe);
-      if (rk > bkey || (rk == bkey && (dist < bdist || (dist == bdist && c < best)))) {
-        best = c;
-        bkey = rk;
-        bdist = dist;
-      }
+  const int I = cc % a.Ac, J = cc / a.Ac;
+  uint32_t bkey = 0;
+  int bdist = 0x7fffffff, best = 0x7fffffff;
+  for (int m = lane; m < npool; m += 32) {
+    const int q = m % a.Pa, b = m / a.Pa;
+    const int c = (J * a.Pe + b) * a.A + I * a.Pa + q;
+    const unsigned long long k = a.keys[c];
+    const uint32_t rk = k == kEmpty ? empty_bits : (uint32_t)(k >> 32);
+    const int dist = abs(2 * q + 1 - a.Pa) + abs(2 * b + 1 - a.Pe);
+    if (rk > bkey || (rk == bkey && (dist < bdist || (dist == bdist && c < best)))) {
+      best = c;
+      bkey = rk;
+      bdist = dist;
     }
+  }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      const uint32_t ok = __shfl_xor_sync(0xffffffffu, bkey, o);
-      const int od = __shfl_xor_sync(0xffffffffu, bdist, o);
-      const int oc = __shfl_xor_sync(0xffffffffu, best, o);
-      if (ok > bkey || (ok == bkey && (od < bdist || (od == bdist && oc < best)))) {
-        best = oc;
-        bkey = ok;
-        bdist = od;
-      }
+  for (int o = 16; o > 0; o >>= 1) {
+    const uint32_t ok = __shfl_xor_sync(0xffffffffu, bkey, o);
+    const int od = __shfl_xor_sync(0xffffffffu, bdist, o);
+    const int oc = __shfl_xor_sync(0xffffffffu, best, o);
+    if (ok > bkey || (ok == bkey && (od < bdist || (od == bdist && oc < best)))) {
+      best = oc;
+      bkey = ok;
+      bdist = od;
     }
-    if (lane == 0) a.coarse_win[cc] = best;
   }
-  if (lane == 0) __threadfence();  // the winners' writers publish them
-  __syncthreads();
-  if (threadIdx.x == 0) s_last = atomicAdd(a.counter, 1u) == (unsigned)(ncb - 1);
-  __syncthreads();
-  if (!s_last) return;
-  __threadfence();
-  for (int i = threadIdx.x; i < a.A; i += blockDim.x) {
-    s_ca[i] = t.ca[i];
-    s_sa[i] = t.sa[i];
-  }
-  for (int i = threadIdx.x; i <= a.El; i += blockDim.x) {
-    s_ce[i] = t.ce[i];
-    s_se[i] = t.se[i];
-  }
-  if (threadIdx.x == 0) *a.counter = 0u;
-  __syncthreads();
-  // goal cone and the M_h x M_v anchor cells around it (Sec. IV-B.1)
+  if (lane == 0) a.coarse_win[cc] = best;
+}
+
+// Goal cone, anchors and guides of one planner by one block, after every
+// coarse winner is written; `st` holds the edge tables.
+__device__ void guides_block(const GuideArgs& a, const SmemTables& st) {
+  __shared__ float s_coef[kMaxE][3][6];
   __shared__ int s_goal;
+  // goal cone and the M_h x M_v anchor cells around it (Sec. IV-B.1)
   if (threadIdx.x == 0) {
     float b[3];
     to_body(a.R, a.goal_rel[0], a.goal_rel[1], a.goal_rel[2], b);
     const float rho = __fsqrt_rn(add(mul(b[0], b[0]), mul(b[1], b[1])));
-    s_goal = el_bin(s_ce, s_se, a.El, b[2], rho) * a.A + az_bin(s_ca, s_sa, a.A, b[0], b[1]);
+    s_goal = el_bin(st.ce, st.se, a.El, b[2], rho) * a.A + az_bin(st.ca, st.sa, a.A, b[0], b[1]);
     a.cells[0] = s_goal;
   }
   __syncthreads();
@@ -391,6 +402,27 @@ __device__ void coarse_guides_block(const GuideArgs& a, const PartTables& t, int
   }
 }
 
+// `ncb` blocks, one warp per coarse cell; the last of them to finish continues
+// with the goal cone, anchors and guides.
+__device__ void coarse_guides_block(const GuideArgs& a, const PartTables& t, int cb, int ncb) {
+  __shared__ SmemTables st;
+  __shared__ bool s_last;
+  const int ncoarse = a.Ac * a.Ec;
+  const int lane = threadIdx.x & 31, nwarp = ncb * (blockDim.x >> 5);
+  for (int cc = cb * (blockDim.x >> 5) + (threadIdx.x >> 5); cc < ncoarse; cc += nwarp)
+    coarse_cell(a, cc, lane);
+  if (lane == 0) __threadfence();  // the winners' writers publish them
+  __syncthreads();
+  if (threadIdx.x == 0) s_last = atomicAdd(a.counter, 1u) == (unsigned)(ncb - 1);
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  load_tables(t, a.A, a.El, st);
+  if (threadIdx.x == 0) *a.counter = 0u;
+  __syncthreads();
+  guides_block(a, st);
+}
+
 // K2a + K3: the count pass of the candidate lists and, in the remaining blocks,
 // the coarse argmax, goal cone, anchors and guides (they need only the keys).
 __global__ void __launch_bounds__(256) k_grid_count(CandArgs ca, GuideArgs ga, PartTables t,
@@ -399,6 +431,14 @@ __global__ void __launch_bounds__(256) k_grid_count(CandArgs ca, GuideArgs ga, P
     cand_pass<false>(ca, blockIdx.x, count_blocks);
   else
     coarse_guides_block(ga, t, blockIdx.x - count_blocks, gridDim.x - count_blocks);
+}
+
+// {first entry, count} of cell c from the scanned counts.
+__device__ __forceinline__ void range_cell(const int* local, const int* tile_off, int cap,
+                                           int2* range, int c) {
+  const int s = min(local[c] + tile_off[c >> kScanTileShift], cap);
+  const int e = min(local[c + 1] + tile_off[(c + 1) >> kScanTileShift], cap);
+  range[c] = make_int2(s, e - s);
 }
 
 // K2c: the scatter pass and, in the remaining blocks, the {start, count} of
@@ -410,10 +450,7 @@ __global__ void __launch_bounds__(256) k_grid_scatter(CandArgs ca, int scatter_b
     return;
   }
   const int c = (blockIdx.x - scatter_blocks) * blockDim.x + threadIdx.x;
-  if (c >= ncells) return;
-  const int s = min(ca.local[c] + ca.tile_off[c >> kScanTileShift], ca.grid.cap);
-  const int e = min(ca.local[c + 1] + ca.tile_off[(c + 1) >> kScanTileShift], ca.grid.cap);
-  range[c] = make_int2(s, e - s);
+  if (c < ncells) range_cell(ca.local, ca.tile_off, ca.grid.cap, range, c);
 }
 
 __global__ void k_philox(uint32_t k0, uint32_t k1, uint32_t c1, uint32_t c2, uint32_t c3,
@@ -421,6 +458,141 @@ __global__ void k_philox(uint32_t k0, uint32_t k1, uint32_t c1, uint32_t c2, uin
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
     out[i] = philox4x32_10(make_uint4((uint32_t)i, c1, c2, c3), k0, k1);
+}
+
+// ---------------------------------------------------------------------------
+// Batched launches: the same stages over the units of many planners.  Work
+// that depends on the planner (tables, arguments) is reloaded into shared
+// memory only when a block moves on to another planner.
+// ---------------------------------------------------------------------------
+// Contiguous share [t, t1) of `total` tasks for worker w of nw.
+__device__ __forceinline__ void share_of(long long total, long long w, long long nw, long long& t,
+                                         long long& t1) {
+  const long long per = (total + nw - 1) / nw;
+  t = w * per;
+  t1 = min(total, t + per);
+}
+
+__global__ void __launch_bounds__(256) k_b_partition(BatchView v) {
+  __shared__ long long s_pre[kBatchMax + 1];
+  __shared__ SmemTables st;
+  __shared__ PartitionArgs s_pa;
+  const int n = v.n;
+  load_prefix(s_pre, v.pre + kPrePoints * (n + 1), n);
+  __syncthreads();
+  long long u, u1;
+  share_of(s_pre[n], blockIdx.x, gridDim.x, u, u1);
+  int cur = -1;
+  for (; u < u1; ++u) {
+    const int it = find_unit(s_pre, n, u);
+    if (it != cur) {
+      __syncthreads();  // the previous planner's tables are no longer read
+      const BatchItem* bi = v.items + it;
+      block_copy(&s_pa, &bi->pa);
+      load_tables(*bi->tab, bi->pa.A, bi->pa.El, st);
+      __syncthreads();
+      cur = it;
+    }
+    const int64_t base = (u - s_pre[it]) * kPartChunk;
+    for (int r = threadIdx.x; r < kPartChunk; r += blockDim.x)
+      if (base + r < s_pa.n) partition_point(s_pa, st, base + r);
+  }
+}
+
+// Collision-item tasks (one warp each) in chunks of kTaskChunk consecutive
+// tasks, chunks dealt to the warps round robin (balances dense and empty
+// stretches of the fine partition).  kScatter: the scatter pass, else the count.
+constexpr int kTaskChunk = 4;
+
+template <bool kScatter>
+__device__ __forceinline__ void cand_tasks(const BatchView& v, const long long* s_pi, int n,
+                                           long long w, long long nw, int lane) {
+  const long long ni = s_pi[n];
+  const long long nch = (ni + kTaskChunk - 1) / kTaskChunk;
+  for (long long q = w; q < nch; q += nw) {
+    long long t = q * kTaskChunk;
+    const long long t1 = min(ni, t + kTaskChunk);
+    int it = find_unit(s_pi, n, t);
+    CandArgs a = v.items[it].ca;
+    for (; t < t1; ++t) {
+      if (t >= s_pi[it + 1]) {
+        while (t >= s_pi[it + 1]) ++it;
+        a = v.items[it].ca;
+      }
+      cand_task<kScatter>(a, t - s_pi[it], lane);
+    }
+  }
+}
+
+// Count tasks, then the coarse cells (one warp each).
+__global__ void __launch_bounds__(256) k_b_count(BatchView v) {
+  __shared__ long long s_pi[kBatchMax + 1], s_pc[kBatchMax + 1];
+  const int n = v.n;
+  load_prefix(s_pi, v.pre + kPreItems * (n + 1), n);
+  load_prefix(s_pc, v.pre + kPreCoarse * (n + 1), n);
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const long long w = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const long long nw = (long long)gridDim.x * (blockDim.x >> 5);
+  cand_tasks<false>(v, s_pi, n, w, nw, lane);
+  for (long long c = w; c < s_pc[n]; c += nw) {
+    const int it = find_unit(s_pc, n, c);
+    coarse_cell(v.items[it].ga, (int)(c - s_pc[it]), lane);
+  }
+}
+
+// Units [0, n): goal cone, anchors and guides of planner u; then the scan tiles.
+__global__ void __launch_bounds__(kScanThreads) k_b_scan(BatchView v) {
+  __shared__ long long s_pre[kBatchMax + 1];
+  __shared__ SmemTables st;
+  __shared__ GuideArgs s_ga;
+  const int n = v.n;
+  load_prefix(s_pre, v.pre + kPreTiles * (n + 1), n);
+  __syncthreads();
+  const long long total = n + s_pre[n];
+  for (long long u = blockIdx.x; u < total; u += gridDim.x) {
+    __syncthreads();
+    if (u < n) {
+      const BatchItem* bi = v.items + u;
+      block_copy(&s_ga, &bi->ga);
+      load_tables(*bi->tab, bi->ga.A, bi->ga.El, st);
+      __syncthreads();
+      guides_block(s_ga, st);
+    } else {
+      const long long t = u - n;
+      const int it = find_unit(s_pre, n, t);
+      const BatchItem* bi = v.items + it;
+      scan_tile(bi->count, bi->fill, bi->local, bi->tile_sum, bi->tile_off, bi->gcells + 1,
+                bi->ntiles, (int)(t - s_pre[it]), bi->scan_counter);
+    }
+  }
+}
+
+// Scatter tasks (emptying the keys they read); then the cell ranges and the
+// keys of planners whose collision set is every kept point (read only by the
+// coarse pass, so emptied here).
+__global__ void __launch_bounds__(256) k_b_scatter(BatchView v) {
+  __shared__ long long s_pi[kBatchMax + 1], s_pc[kBatchMax + 1];
+  const int n = v.n;
+  load_prefix(s_pi, v.pre + kPreItems * (n + 1), n);
+  load_prefix(s_pc, v.pre + kPreCells * (n + 1), n);
+  __syncthreads();
+  cand_tasks<true>(v, s_pi, n, ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5,
+                   (long long)gridDim.x * (blockDim.x >> 5), threadIdx.x & 31);
+  const long long total = s_pc[n];
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long c0 = (long long)blockIdx.x * blockDim.x; c0 < total; c0 += stride) {
+    const long long c = c0 + threadIdx.x;
+    if (c >= total) break;
+    int it = find_unit(s_pc, n, c0);
+    while (c >= s_pc[it + 1]) ++it;
+    const BatchItem* bi = v.items + it;
+    const long long l = c - s_pc[it];
+    if (l < bi->gcells)
+      range_cell(bi->local, bi->tile_off, bi->ca.grid.cap, bi->range, (int)l);
+    else
+      bi->keys[l - bi->gcells] = kEmpty;
+  }
 }
 
 int blocks_for(int64_t n, int threads, int cap) {
@@ -456,6 +628,37 @@ cudaError_t launch_grid_scatter(const CandArgs& ca, int2* range, int ncells, cud
   const int scatter_blocks = ca.n_items > 0 ? blocks_for(ca.n_items * 32, 256, 152 * 32) : 0;
   const int range_blocks = (ncells + 255) / 256;
   k_grid_scatter<<<scatter_blocks + range_blocks, 256, 0, s>>>(ca, scatter_blocks, range, ncells);
+  return cudaGetLastError();
+}
+
+cudaError_t batch_grid_occupancy(int out[4]) {
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(out + 0, k_b_partition, 256, 0);
+  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(out + 1, k_b_count, 256, 0);
+  if (e == cudaSuccess)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(out + 2, k_b_scan, kScanThreads, 0);
+  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(out + 3, k_b_scatter, 256, 0);
+  for (int i = 0; i < 4; ++i)
+    if (out[i] < 1) out[i] = 1;
+  return e;
+}
+
+cudaError_t launch_batch_partition(const BatchView& v, int blocks, cudaStream_t s) {
+  k_b_partition<<<blocks, 256, 0, s>>>(v);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_batch_count(const BatchView& v, int blocks, cudaStream_t s) {
+  k_b_count<<<blocks, 256, 0, s>>>(v);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_batch_scan(const BatchView& v, int blocks, cudaStream_t s) {
+  k_b_scan<<<blocks, kScanThreads, 0, s>>>(v);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_batch_scatter(const BatchView& v, int blocks, cudaStream_t s) {
+  k_b_scatter<<<blocks, 256, 0, s>>>(v);
   return cudaGetLastError();
 }
 

@@ -35,13 +35,15 @@ struct KahanSum {
   }
 };
 
-__global__ void __launch_bounds__(NT) k_rollout(RolloutArgs a) {
+// Samples [b * NT, (b + 1) * NT) of instance e; ctr3: the noise counter's
+// last word, (step_id << 8) | iteration.
+__device__ __forceinline__ void rollout_unit(const RolloutArgs& a, int e, int b, uint32_t ctr3) {
   __shared__ float4 s_un[kMaxT];
   __shared__ float s_gd[kMaxT * 3];
   __shared__ float s_red[NW];
   __shared__ float4 s_w[NW][kMaxT];
 
-  const int e = blockIdx.y, b = blockIdx.x, tid = threadIdx.x;
+  const int tid = threadIdx.x;
   const int lane = tid & 31, wid = tid >> 5;
   const int T = a.T;
   for (int i = tid; i < T; i += NT) s_un[i] = reinterpret_cast<const float4*>(a.u_nom)[e * T + i];
@@ -73,13 +75,13 @@ __global__ void __launch_bounds__(NT) k_rollout(RolloutArgs a) {
   KahanSum S;
   // step j's control: prefetched noise, clamp, the stored perturbation, J_ctrl's
   // terms Q_c |u_j|^2 (j <= T-2) and Q_cd |u_j - u_{j-1}|^2 (1 <= j <= T-2)
-  float4 d_next = noise_delta(k, 0, e, a.ctr3, a.key0, a.key1, sigma);
+  float4 d_next = noise_delta(k, 0, e, ctr3, a.key0, a.key1, sigma);
   float4 un_next = s_un[0];
   float4 u_prev = make_float4(0.f, 0.f, 0.f, 0.f);
   auto control = [&](int j, float& c_ctrl) -> float4 {
     const float4 un = un_next, d = d_next;
     if (j + 1 < T) {
-      d_next = noise_delta(k, j + 1, e, a.ctr3, a.key0, a.key1, sigma);
+      d_next = noise_delta(k, j + 1, e, ctr3, a.key0, a.key1, sigma);
       un_next = s_un[j + 1];
     }
     const float4 u = clamp4(make_float4(un.x + d.x, un.y + d.y, un.z + d.z, un.w + d.w), umin, umax);
@@ -159,7 +161,7 @@ __global__ void __launch_bounds__(NT) k_rollout(RolloutArgs a) {
       du = active ? __ldcs(dU + (size_t)j * a.K) : make_float4(0.f, 0.f, 0.f, 0.f);
     } else {
       const float4 un = s_un[j];
-      const float4 d = noise_delta(k, j, e, a.ctr3, a.key0, a.key1, sigma);
+      const float4 d = noise_delta(k, j, e, ctr3, a.key0, a.key1, sigma);
       const float4 u = clamp4(make_float4(un.x + d.x, un.y + d.y, un.z + d.z, un.w + d.w), umin, umax);
       du = make_float4(u.x - un.x, u.y - un.y, u.z - un.z, u.w - un.w);
     }
@@ -197,14 +199,15 @@ __global__ void __launch_bounds__(NT) k_rollout(RolloutArgs a) {
 // ---------------------------------------------------------------------------
 constexpr int QS = NT / 4;  // samples per CTA
 
-__global__ void __launch_bounds__(NT) k_rollout_quad(RolloutArgs a) {
+__device__ __forceinline__ void rollout_quad_unit(const RolloutArgs& a, int e, int b,
+                                                  uint32_t ctr3) {
   __shared__ float4 s_un[kMaxT];
   __shared__ float s_gd[kMaxT * 3];
   __shared__ float s_red[NW];
   __shared__ float4 s_w[NW][kMaxT];
   __shared__ float4 s_cand[NW][kWarpStage];
 
-  const int e = blockIdx.y, b = blockIdx.x, tid = threadIdx.x;
+  const int tid = threadIdx.x;
   const int lane = tid & 31, wid = tid >> 5, q = lane & 3, qbase = lane & ~3;
   const int T = a.T;
   for (int i = tid; i < T; i += NT) s_un[i] = reinterpret_cast<const float4*>(a.u_nom)[e * T + i];
@@ -238,12 +241,12 @@ __global__ void __launch_bounds__(NT) k_rollout_quad(RolloutArgs a) {
 
   KahanSum S;
   float4 d_cur = make_float4(0.f, 0.f, 0.f, 0.f);
-  float4 d_nxt = q < T ? noise_delta(k, q, e, a.ctr3, a.key0, a.key1, sigma) : d_cur;
+  float4 d_nxt = q < T ? noise_delta(k, q, e, ctr3, a.key0, a.key1, sigma) : d_cur;
   float4 u_prev = make_float4(0.f, 0.f, 0.f, 0.f);
   auto control = [&](int j, float& c_ctrl) -> float4 {
     if ((j & 3) == 0) {
       d_cur = d_nxt;
-      if (j + 4 + q < T) d_nxt = noise_delta(k, j + 4 + q, e, a.ctr3, a.key0, a.key1, sigma);
+      if (j + 4 + q < T) d_nxt = noise_delta(k, j + 4 + q, e, ctr3, a.key0, a.key1, sigma);
     }
     const int src = qbase + (j & 3);
     const float4 d = make_float4(__shfl_sync(0xffffffffu, d_cur.x, src),
@@ -360,7 +363,7 @@ __global__ void __launch_bounds__(NT) k_rollout_quad(RolloutArgs a) {
       du = active ? __ldcs(dUf + (size_t)j * a.K * 4) : 0.0f;
     } else {
       const float4 un = s_un[j];
-      const float4 d = noise_delta(k, j, e, a.ctr3, a.key0, a.key1, sigma);
+      const float4 d = noise_delta(k, j, e, ctr3, a.key0, a.key1, sigma);
       const float4 u = clamp4(make_float4(un.x + d.x, un.y + d.y, un.z + d.z, un.w + d.w), umin, umax);
       du = active ? (q == 0 ? u.x - un.x : q == 1 ? u.y - un.y : q == 2 ? u.z - un.z : u.w - un.w) : 0.0f;
     }
@@ -395,7 +398,7 @@ __global__ void __launch_bounds__(NT) k_rollout_quad(RolloutArgs a) {
 // ---------------------------------------------------------------------------
 constexpr int UT = 128;
 
-__global__ void __launch_bounds__(UT) k_update(UpdateArgs a) {
+__device__ __forceinline__ void update_unit(const UpdateArgs& a, int e, bool final_stage) {
   __shared__ float s_scale[1024];
   __shared__ float s_red[UT / 32];
   __shared__ float s_x[(kMaxT + 1) * 10];
@@ -404,7 +407,7 @@ __global__ void __launch_bounds__(UT) k_update(UpdateArgs a) {
   __shared__ float s_c[kMaxT];
   __shared__ float4 s_acc[UT / 32][kMaxT];
   __shared__ bool s_last;
-  const int e = blockIdx.x, tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const int T = a.T, stride = 4 + 4 * T;
   const float* P = a.partials + (size_t)e * a.nb * stride;
 
@@ -473,7 +476,7 @@ __global__ void __launch_bounds__(UT) k_update(UpdateArgs a) {
     un[i] = v;
     s_u[i] = v;
   }
-  if (!a.final_stage) return;
+  if (!final_stage) return;
   __syncthreads();
 
   // Stage II: noise-free rollout of the updated nominal
@@ -514,7 +517,7 @@ __global__ void __launch_bounds__(UT) k_update(UpdateArgs a) {
   // last CTA to arrive selects the best instance
   __threadfence();
   __syncthreads();
-  if (tid == 0) s_last = atomicAdd(a.counter, 1u) == (unsigned)(gridDim.x - 1);
+  if (tid == 0) s_last = atomicAdd(a.counter, 1u) == (unsigned)(a.E - 1);
   __syncthreads();
   if (!s_last) return;
   __threadfence();
@@ -544,7 +547,134 @@ __global__ void __launch_bounds__(UT) k_update(UpdateArgs a) {
   for (int i = tid; i < 4 * T; i += UT) a.u_best[i] = __ldcg(ub + i);
 }
 
+__global__ void __launch_bounds__(NT) k_rollout(RolloutArgs a) {
+  rollout_unit(a, blockIdx.y, blockIdx.x, a.ctr3);
+}
+
+__global__ void __launch_bounds__(NT) k_rollout_quad(RolloutArgs a) {
+  rollout_quad_unit(a, blockIdx.y, blockIdx.x, a.ctr3);
+}
+
+// The single-planner update reads its arguments from shared memory, as the
+// batched one does, so that both compile the same code (the Stage II costs
+// then agree bit for bit; from kernel parameters the compiler contracts some
+// products differently).
+__global__ void __launch_bounds__(UT) k_update(UpdateArgs a) {
+  __shared__ UpdateArgs s_a;
+  block_copy_param(&s_a, &a);
+  __syncthreads();
+  update_unit(s_a, blockIdx.x, s_a.final_stage != 0);
+}
+
+// ---------------------------------------------------------------------------
+// Batched Stage I: units (planner, instance, block of samples) in the order of
+// the planners' positions (longest horizon first).  dynamic: every CTA takes its
+// next unit from the work queue (an atomic counter; the last CTA to leave
+// resets it), else units are strided by the grid.  Planners whose iteration
+// count is at most `it` skip their units.
+// ---------------------------------------------------------------------------
+template <int kLanes, int kMinCtas>
+__global__ void __launch_bounds__(NT, kMinCtas) k_b_rollout(BatchView v, int it, int dynamic) {
+  __shared__ long long s_pre[kBatchMax + 1];
+  __shared__ int s_order[kBatchMax];
+  __shared__ RolloutArgs s_a;
+  __shared__ int s_iters;
+  __shared__ unsigned int s_u;
+  const int n = v.n;
+  load_prefix(s_pre, v.pre + (kLanes == 1 ? kPreRoll1 : kPreRoll4) * (n + 1), n);
+  const int* order = kLanes == 1 ? v.order1 : v.order4;
+  for (int i = threadIdx.x; i < n; i += NT) s_order[i] = __ldg(order + i);
+  unsigned int* queue = v.queue + (kLanes == 1 ? 0 : 2);
+  __syncthreads();
+  const long long total = s_pre[n];
+  int cur = -1;
+  long long u = blockIdx.x;
+  for (;;) {
+    if (dynamic) {
+      if (threadIdx.x == 0) s_u = atomicAdd(queue, 1u);
+      __syncthreads();
+      u = s_u;
+    }
+    if (u >= total) break;
+    const int pos = find_unit(s_pre, n, u);
+    const int item = s_order[pos];
+    if (item != cur) {
+      block_copy(&s_a, &v.items[item].ra);
+      if (threadIdx.x == 0) s_iters = v.items[item].iters;
+      __syncthreads();
+      cur = item;
+    }
+    if (it < s_iters) {
+      const long long l = u - s_pre[pos];
+      const int e = (int)(l / s_a.nb), b = (int)(l % s_a.nb);
+      if (kLanes == 1)
+        rollout_unit(s_a, e, b, s_a.ctr3 | (uint32_t)it);
+      else
+        rollout_quad_unit(s_a, e, b, s_a.ctr3 | (uint32_t)it);
+    }
+    if (!dynamic) u += gridDim.x;
+    __syncthreads();  // the unit's shared memory is free again
+  }
+  if (dynamic && threadIdx.x == 0) {
+    // every CTA has drawn past the end before it counts itself out
+    if (atomicAdd(queue + 1, 1u) == gridDim.x - 1) {
+      queue[0] = 0u;
+      queue[1] = 0u;
+    }
+  }
+}
+
+// Batched merge and update: units (planner, instance); the last iteration of a
+// planner runs its Stage II and selection.
+__global__ void __launch_bounds__(UT) k_b_update(BatchView v, int it) {
+  __shared__ long long s_pre[kBatchMax + 1];
+  __shared__ UpdateArgs s_a;
+  __shared__ int s_iters;
+  const int n = v.n;
+  load_prefix(s_pre, v.pre + kPreUpdate * (n + 1), n);
+  __syncthreads();
+  const long long total = s_pre[n];
+  int cur = -1;
+  for (long long u = blockIdx.x; u < total; u += gridDim.x) {
+    const int item = find_unit(s_pre, n, u);
+    if (item != cur) {
+      block_copy(&s_a, &v.items[item].ua);
+      if (threadIdx.x == 0) s_iters = v.items[item].iters;
+      __syncthreads();
+      cur = item;
+    }
+    if (it < s_iters) update_unit(s_a, (int)(u - s_pre[item]), it == s_iters - 1);
+    __syncthreads();
+  }
+}
+
 }  // namespace
+
+cudaError_t batch_rollout_occupancy(int out[4]) {
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(out + 0, k_b_rollout<1, 5>, NT, 0);
+  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(out + 1, k_b_rollout<4, 4>, NT, 0);
+  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(out + 2, k_b_update, UT, 0);
+  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(out + 3, k_b_rollout<1, 6>, NT, 0);
+  for (int i = 0; i < 4; ++i)
+    if (out[i] < 1) out[i] = 1;
+  return e;
+}
+
+cudaError_t launch_batch_rollout(const BatchView& v, int lanes, int it, int blocks, int dynamic,
+                                 int six, cudaStream_t s) {
+  if (lanes == 4)
+    k_b_rollout<4, 4><<<blocks, NT, 0, s>>>(v, it, dynamic);
+  else if (six)
+    k_b_rollout<1, 6><<<blocks, NT, 0, s>>>(v, it, dynamic);
+  else
+    k_b_rollout<1, 5><<<blocks, NT, 0, s>>>(v, it, dynamic);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_batch_update(const BatchView& v, int it, int blocks, cudaStream_t s) {
+  k_b_update<<<blocks, UT, 0, s>>>(v, it);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_rollout(const RolloutArgs& a, cudaStream_t s) {
   dim3 grid(a.nb, a.E);

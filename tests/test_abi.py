@@ -85,3 +85,5 @@ def test_binding_struct_sizes_match_header():
     assert C.sizeof(aero.State) == 40
     assert C.sizeof(aero.Limits) == 32
     assert C.sizeof(aero.Params) == 224
+    assert C.sizeof(aero.BatchItem) == 328
+    assert C.sizeof(aero.BatchConfig) == 16
