@@ -301,7 +301,7 @@ def run_batched(args, rank: int, world: int, local: int):
     from paper_2509_17340_gb300 import build
     build.build()
     from paper_2509_17340_gb300 import aero
-    ws = I.batch_workloads(64, seed=1 + 1000 * rank_seed(rank))
+    ws = I.batch_workloads(args.batch_planners, seed=1 + 1000 * rank_seed(rank))
     dev = torch.device("cuda", local)
     stream = torch.cuda.Stream(device=dev)
     lim = dict(E_max=16, K_max=4096, T_max=60, fine_cells_max=128 * 64,
@@ -327,7 +327,12 @@ def run_batched(args, rank: int, world: int, local: int):
     plans = [items(s) for s in range(args.warmup + args.steps)]
     # one-off autotuning of the launch configuration (outside the timed region;
     # it writes only the batch's scratch buffers)
-    tuned, tune_ms = batch.tune(plans[0], repeats=3, stream=stream)
+    if args.batch_config:
+        q, c, d, g = (int(x) for x in args.batch_config.split(","))
+        batch.set_config(q, c, d, g)
+        tuned, tune_ms = batch.config(), None
+    else:
+        tuned, tune_ms = batch.tune(plans[0], repeats=3, stream=stream)
     torch.cuda.synchronize()
     with torch.cuda.stream(stream):
         for s in range(args.warmup):
@@ -396,7 +401,7 @@ def run_batched(args, rank: int, world: int, local: int):
         "ms_per_step": total_ms / args.steps, "ms_per_step_median": statistics.median(step_ms),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic",
-        "config": {"workload": "batched: 64 planners, E in {4,8,16}, K in {256,1024,4096}, "
+        "config": {"workload": f"batched: {len(ws)} planners, E in {{4,8,16}}, K in {{256,1024,4096}}, "
                                "T in {20,40,60}, forest / walls with 1.5 m gaps / inclines, "
                                f"{min(len(w.cloud) for w in ws)}-{max(len(w.cloud) for w in ws)} points",
                    "planners": len(ws), "rollout_steps_per_batch": units,
@@ -445,6 +450,11 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default=WORKLOAD, choices=sorted(METRICS))
+    ap.add_argument("--batch-planners", type=int, default=64,
+                    help="batched workload: number of planners (64 is the measured configuration)")
+    ap.add_argument("--batch-config", default="",
+                    help="batched workload: fixed launch configuration 'quad_max,ctas_per_sm,"
+                         "dynamic,coarse' instead of autotuning")
     ap.add_argument("--no-stage-timing", action="store_true",
                     help="diagnostic: no per-stage events in the timed steps (no roofline)")
     args = ap.parse_args()
