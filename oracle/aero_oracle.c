@@ -50,6 +50,9 @@ typedef struct {
   int32_t pad_;
   double v_goal[3], q_goal[4];
   uint64_t seed, step_id;
+  int32_t refine_steps;  /* gradient steps on each updated nominal before Stage II */
+  int32_t pad2_;
+  double refine_step;    /* their step size */
 } orc_params;
 
 #define ORC_EMPTY 0xFFFFFFFFFFFFFFFFull
@@ -524,6 +527,219 @@ void orc_cost_terms(const double* X, const double* U, const double* guide, const
   terms[5] = stage == 1 ? jt + jv + jc + jg + jl : jg + jl;
 }
 
+/* ======================================================================
+ * Gradient of S^(1) with respect to the controls, by reverse mode through
+ * the rollout (not a step of the paper: it serves the gradient refinement of
+ * the updated nominals before Stage II).  Written out from the definitions
+ * above: the dynamics, the literal RK4 stages, the renormalisation, and the
+ * cost terms of orc_cost_terms with stage 1.  Where a term is not
+ * differentiable (a norm at zero, J_col at d_min and d_max, a tie between
+ * nearest points) its gradient is taken from the piece in use: zero for a
+ * zero norm, the collision term's own branch.
+ * ====================================================================== */
+
+/* w^T d(xd)/dx added to gx and w^T d(xd)/du added to gu, for xd = f(x, u) of
+ * orc_dynamics. */
+static void dyn_vjp(const double x[10], const double u[4], double m, const double w[10],
+                    double gx[10], double gu[4]) {
+  const double qw = x[3], qx = x[4], qy = x[5], qz = x[6];
+  const double ox = u[1], oy = u[2], oz = u[3];
+  /* p' = v */
+  for (int i = 0; i < 3; ++i) gx[7 + i] += w[i];
+  /* q' = 1/2 q (x) [0, w]: components
+   *   r0 = -qx ox - qy oy - qz oz,  r1 = qw ox + qy oz - qz oy,
+   *   r2 = qw oy - qx oz + qz ox,   r3 = qw oz + qx oy - qy ox */
+  const double W0 = 0.5 * w[3], W1 = 0.5 * w[4], W2 = 0.5 * w[5], W3 = 0.5 * w[6];
+  gx[3] += W1 * ox + W2 * oy + W3 * oz;
+  gx[4] += -W0 * ox - W2 * oz + W3 * oy;
+  gx[5] += -W0 * oy + W1 * oz - W3 * ox;
+  gx[6] += -W0 * oz - W1 * oy + W2 * ox;
+  gu[1] += -W0 * qx + W1 * qw + W2 * qz - W3 * qy;
+  gu[2] += -W0 * qy - W1 * qz + W2 * qw + W3 * qx;
+  gu[3] += -W0 * qz + W1 * qy - W2 * qx + W3 * qw;
+  /* v' = (F/m) (R[2], R[5], R[8]) + (0, 0, -g) with
+   *   R[2] = 2(xz + wy), R[5] = 2(yz - wx), R[8] = 1 - 2(x^2 + y^2) */
+  const double V0 = w[7], V1 = w[8], V2 = w[9];
+  const double r2 = 2 * (qx * qz + qw * qy), r5 = 2 * (qy * qz - qw * qx), r8 = 1 - 2 * (qx * qx + qy * qy);
+  gu[0] += (V0 * r2 + V1 * r5 + V2 * r8) / m;
+  const double s = u[0] / m;
+  gx[3] += s * (2 * qy * V0 - 2 * qx * V1);
+  gx[4] += s * (2 * qz * V0 - 2 * qw * V1 - 4 * qx * V2);
+  gx[5] += s * (2 * qw * V0 + 2 * qz * V1 - 4 * qy * V2);
+  gx[6] += s * (2 * qx * V0 + 2 * qy * V1);
+}
+
+/* Reverse of one orc_rk4_step: given lam = dS/d(xn), set gx = dS/dx through
+ * this step and add dS/du to gu. */
+static void rk4_vjp(const double x[10], const double u[4], double dt, double m, double g,
+                    const double lam[10], double gx[10], double gu[4]) {
+  double k1[10], k2[10], k3[10], k4[10], t2[10], t3[10], t4[10], y[10];
+  orc_dynamics(x, u, m, g, k1);
+  for (int i = 0; i < 10; ++i) t2[i] = x[i] + 0.5 * dt * k1[i];
+  orc_dynamics(t2, u, m, g, k2);
+  for (int i = 0; i < 10; ++i) t3[i] = x[i] + 0.5 * dt * k2[i];
+  orc_dynamics(t3, u, m, g, k3);
+  for (int i = 0; i < 10; ++i) t4[i] = x[i] + dt * k3[i];
+  orc_dynamics(t4, u, m, g, k4);
+  for (int i = 0; i < 10; ++i) y[i] = x[i] + dt / 6.0 * (k1[i] + 2 * k2[i] + 2 * k3[i] + k4[i]);
+  /* renormalisation qn = y_q / |y_q|: dqn/dy_q = (I - qn qn^T) / |y_q| */
+  double ly[10];
+  memcpy(ly, lam, sizeof(ly));
+  const double nq = sqrt(y[3] * y[3] + y[4] * y[4] + y[5] * y[5] + y[6] * y[6]);
+  double dot = 0.0;
+  for (int i = 3; i < 7; ++i) dot += (y[i] / nq) * lam[i];
+  for (int i = 3; i < 7; ++i) ly[i] = (lam[i] - (y[i] / nq) * dot) / nq;
+  /* y = x + dt/6 (k1 + 2 k2 + 2 k3 + k4) */
+  double l1[10], l2[10], l3[10], l4[10], lt[10];
+  for (int i = 0; i < 10; ++i) {
+    gx[i] = ly[i];
+    l1[i] = dt / 6.0 * ly[i];
+    l2[i] = dt / 3.0 * ly[i];
+    l3[i] = dt / 3.0 * ly[i];
+    l4[i] = dt / 6.0 * ly[i];
+  }
+  /* k4 = f(t4), t4 = x + dt k3 */
+  memset(lt, 0, sizeof(lt));
+  dyn_vjp(t4, u, m, l4, lt, gu);
+  for (int i = 0; i < 10; ++i) { gx[i] += lt[i]; l3[i] += dt * lt[i]; }
+  /* k3 = f(t3), t3 = x + dt/2 k2 */
+  memset(lt, 0, sizeof(lt));
+  dyn_vjp(t3, u, m, l3, lt, gu);
+  for (int i = 0; i < 10; ++i) { gx[i] += lt[i]; l2[i] += 0.5 * dt * lt[i]; }
+  /* k2 = f(t2), t2 = x + dt/2 k1 */
+  memset(lt, 0, sizeof(lt));
+  dyn_vjp(t2, u, m, l2, lt, gu);
+  for (int i = 0; i < 10; ++i) { gx[i] += lt[i]; l1[i] += 0.5 * dt * lt[i]; }
+  /* k1 = f(x) */
+  dyn_vjp(x, u, m, l1, gx, gu);
+}
+
+/* dR[k][i] = d R[k] / d q_i of orc_rotation (q = (w, x, y, z)). */
+static void rotation_grad(const double q[4], double dR[9][4]) {
+  const double w = q[0], x = q[1], y = q[2], z = q[3];
+  const double t[9][4] = {
+      {0, 0, -4 * y, -4 * z},          {-2 * z, 2 * y, 2 * x, -2 * w}, {2 * y, 2 * z, 2 * w, 2 * x},
+      {2 * z, 2 * y, 2 * x, 2 * w},    {0, -4 * x, 0, -4 * z},         {-2 * x, -2 * w, 2 * z, 2 * y},
+      {-2 * y, 2 * z, -2 * w, 2 * x},  {2 * x, 2 * w, 2 * z, 2 * y},   {0, -4 * x, -4 * y, 0}};
+  memcpy(dR, t, sizeof(t));
+}
+
+static void add_unit(double* g, const double* e, double n, double wgt) {
+  if (n > 0)
+    for (int i = 0; i < 3; ++i) g[i] += wgt * e[i] / n;
+}
+
+/* Stage I state terms at the post-step state x (guide sample gj or NULL) and
+ * their gradient gx (overwritten); returns the terms' value. */
+static double state_cost_grad(const double* x, const double* gj, const double goal[3],
+                              const double* pts, int64_t npts, const orc_params* P, double gx[10]) {
+  double c = 0.0;
+  memset(gx, 0, 10 * sizeof(double));
+  if (gj) {
+    double e[3] = {x[0] - gj[0], x[1] - gj[1], x[2] - gj[2]};
+    double n = norm3(e);
+    c += P->Q_track * n;
+    add_unit(gx, e, n, P->Q_track);
+  }
+  c += P->Q_vnorm * (x[7] * x[7] + x[8] * x[8] + x[9] * x[9]);
+  for (int i = 0; i < 3; ++i) gx[7 + i] += 2 * P->Q_vnorm * x[7 + i];
+  double dp[3] = {x[0] - goal[0], x[1] - goal[1], x[2] - goal[2]};
+  double dv[3] = {x[7] - P->v_goal[0], x[8] - P->v_goal[1], x[9] - P->v_goal[2]};
+  double np = norm3(dp), nv = norm3(dv);
+  c += P->Q_p * np + P->Q_v * nv;
+  add_unit(gx, dp, np, P->Q_p);
+  add_unit(gx + 7, dv, nv, P->Q_v);
+  /* ||R(q) R_g^T - I||_F */
+  double R[9], Rg[9], M[9], dR[9][4], a2 = 0.0;
+  orc_rotation(x + 3, R);
+  orc_rotation(P->q_goal, Rg);
+  for (int r = 0; r < 3; ++r)
+    for (int cc = 0; cc < 3; ++cc) {
+      double m = -((r == cc) ? 1.0 : 0.0);
+      for (int k = 0; k < 3; ++k) m += R[3 * r + k] * Rg[3 * cc + k];
+      M[3 * r + cc] = m;
+      a2 += m * m;
+    }
+  double att = sqrt(a2);
+  c += P->Q_q * att;
+  if (att > 0) {
+    rotation_grad(x + 3, dR);
+    for (int i = 0; i < 4; ++i) {
+      double s = 0.0;
+      for (int r = 0; r < 3; ++r)
+        for (int cc = 0; cc < 3; ++cc)
+          for (int k = 0; k < 3; ++k) s += M[3 * r + cc] * dR[3 * r + k][i] * Rg[3 * cc + k];
+      gx[3 + i] += P->Q_q * s / att;
+    }
+  }
+  /* J_col at the nearest point (brute force; the lowest index among ties) */
+  double best = INFINITY;
+  int64_t arg = -1;
+  for (int64_t i = 0; i < npts; ++i) {
+    double ex = x[0] - pts[3 * i], ey = x[1] - pts[3 * i + 1], ez = x[2] - pts[3 * i + 2];
+    double d = sqrt(ex * ex + ey * ey + ez * ez);
+    if (d < best) { best = d; arg = i; }
+  }
+  c += orc_jcol(best, P);
+  if (arg >= 0 && best >= P->d_min && best < P->d_max && best > 0) {
+    double e[3] = {x[0] - pts[3 * arg], x[1] - pts[3 * arg + 1], x[2] - pts[3 * arg + 2]};
+    add_unit(gx, e, best, -P->a_col * orc_jcol(best, P));
+  }
+  return c;
+}
+
+/* S^(1) of the noise-free rollout of U (T x 4) from x0, with guide (T x 3 or
+ * NULL); G (T x 4) gets dS/dU.  Returns S. */
+double orc_cost_grad(const double x0[10], const double* U, const double* guide, const double goal[3],
+                     const double* pts, int64_t npts, const orc_params* P, double* G) {
+  const int T = P->T;
+  double* X = malloc(sizeof(double) * (T + 1) * 10);
+  orc_rollout(x0, U, T, P->dt, P->mass, P->g, X);
+  double S = 0.0, lam[10] = {0}, gs[10], gx[10];
+  for (int j = T - 1; j >= 0; --j) {
+    S += state_cost_grad(X + 10 * (j + 1), guide ? guide + 3 * j : NULL, goal, pts, npts, P, gs);
+    for (int i = 0; i < 10; ++i) lam[i] += gs[i];
+    double gu[4] = {0, 0, 0, 0};
+    rk4_vjp(X + 10 * j, U + 4 * j, P->dt, P->mass, P->g, lam, gx, gu);
+    for (int c = 0; c < 4; ++c) G[4 * j + c] = gu[c];
+    memcpy(lam, gx, sizeof(lam));
+  }
+  /* J_ctrl: Q_c |u_t|^2 (t <= T-2) and Q_cd |u_t - u_{t-1}|^2 (1 <= t <= T-2) */
+  for (int t = 0; t <= T - 2; ++t)
+    for (int c = 0; c < 4; ++c) {
+      S += P->Q_c * U[4 * t + c] * U[4 * t + c];
+      G[4 * t + c] += 2 * P->Q_c * U[4 * t + c];
+    }
+  for (int t = 1; t <= T - 2; ++t)
+    for (int c = 0; c < 4; ++c) {
+      double d = U[4 * t + c] - U[4 * (t - 1) + c];
+      S += P->Q_cd * d * d;
+      G[4 * t + c] += 2 * P->Q_cd * d;
+      G[4 * (t - 1) + c] -= 2 * P->Q_cd * d;
+    }
+  free(X);
+  return S;
+}
+
+/* refine_steps gradient steps u <- clamp(u - refine_step dS/du, u_min, u_max)
+ * on one nominal (T x 4). */
+void orc_refine(const double x0[10], double* u, const double* guide, const double goal[3],
+                const double* pts, int64_t npts, const orc_params* P) {
+  const int T = P->T;
+  double* G = malloc(sizeof(double) * T * 4);
+  for (int r = 0; r < P->refine_steps; ++r) {
+    orc_cost_grad(x0, u, guide, goal, pts, npts, P, G);
+    for (int j = 0; j < T; ++j)
+      for (int c = 0; c < 4; ++c) {
+        double v = u[4 * j + c] - P->refine_step * G[4 * j + c];
+        if (v < P->u_min[c]) v = P->u_min[c];
+        if (v > P->u_max[c]) v = P->u_max[c];
+        u[4 * j + c] = v;
+      }
+  }
+  free(G);
+}
+
 /* Eq. mppi_weights and Eq. mppi_update_simplified for one instance:
  * rho = min S, eta = sum exp(-(S-rho)/lam), eps_k = exp(-(S_k-rho)/lam)/eta,
  * u_nom += sum_k eps_k du^k.  dU is K x (T*4). */
@@ -643,6 +859,11 @@ int orc_plan_step(const float* cloud, int64_t n, const float p0f[3], const float
       }
       orc_mppi_update(S, dU, K, T, P->lam, un, NULL);
     }
+
+  /* optional gradient refinement of each updated nominal */
+  if (P->refine_steps > 0)
+    for (int e = 0; e < E; ++e)
+      orc_refine(x0, u_nom + (int64_t)e * T * 4, guides + (int64_t)e * T * 3, goal, pts, npts, P);
 
   /* Stage II: roll out each updated nominal, score S^(2), keep the argmin. */
   int best = 0;

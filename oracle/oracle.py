@@ -49,6 +49,7 @@ class Params(C.Structure):
         ("collision_set", C.c_int32), ("pad_", C.c_int32),
         ("v_goal", C.c_double * 3), ("q_goal", C.c_double * 4),
         ("seed", C.c_uint64), ("step_id", C.c_uint64),
+        ("refine_steps", C.c_int32), ("pad2_", C.c_int32), ("refine_step", C.c_double),
     ]
 
 
@@ -68,6 +69,8 @@ def params(d: dict) -> Params:
         for i, v in enumerate(d[k]):
             arr[i] = float(v)
     p.seed, p.step_id = int(d["seed"]), int(d["step_id"])
+    p.refine_steps = int(d.get("refine_steps", 0))
+    p.refine_step = float(d.get("refine_step", 0.05))
     return p
 
 
@@ -269,6 +272,31 @@ def cost_terms(X, U, guide_, goal, pts, P: dict, stage: int = 1, want_dist=False
     if want_dist:
         out["dist"] = dist
     return out
+
+
+def cost_grad(x0, U, guide_, goal, pts, P: dict) -> tuple[float, np.ndarray]:
+    """S^(1) of the noise-free rollout of U (T x 4) and dS/dU (reverse mode)."""
+    U = _f64(U).reshape(-1, 4)
+    pts = _f64(pts).reshape(-1, 3)
+    G = np.zeros_like(U)
+    pp = params(P)
+    gp = _p(_f64(guide_)) if guide_ is not None else None
+    L = lib()
+    L.orc_cost_grad.restype = C.c_double
+    S = L.orc_cost_grad(_p(_f64(x0)), _p(U), gp, _p(_f64(goal)), _p(pts), C.c_int64(len(pts)),
+                        C.byref(pp), _p(G))
+    return float(S), G
+
+
+def refine(x0, U, guide_, goal, pts, P: dict) -> np.ndarray:
+    """P["refine_steps"] clamped gradient steps of size P["refine_step"] on U."""
+    U = _f64(U).reshape(-1, 4).copy()
+    pts = _f64(pts).reshape(-1, 3)
+    pp = params(P)
+    gp = _p(_f64(guide_)) if guide_ is not None else None
+    lib().orc_refine(_p(_f64(x0)), _p(U), gp, _p(_f64(goal)), _p(pts), C.c_int64(len(pts)),
+                     C.byref(pp))
+    return U
 
 
 def mppi_update(S, dU, lam, u_nom) -> tuple[np.ndarray, np.ndarray]:
