@@ -41,7 +41,8 @@ WORKLOAD = "ensemble"
 METRIC = "rollout-steps/s (anchor-guided ensemble plan step)"
 METRICS = {"ensemble": METRIC, "large": "rollout-steps/s (large-clutter ensemble plan step)",
            "plain": "rollout-steps/s (plain single-MPPI plan step)",
-           "batched": "rollout-steps/s (64 independent planners in one batched call)"}
+           "batched": "rollout-steps/s (64 independent planners in one batched call)",
+           "refined": "rollout-steps/s (ensemble plan step with 5 gradient-refinement steps)"}
 UNIT = "rollout-steps/s"
 CPU_SAMPLE_SECONDS = 15.0
 
@@ -261,7 +262,8 @@ def run_reference_batched(args, O):
 def config_of(P: dict, w) -> dict:
     return {"workload": f"{WORKLOAD}: E={P['E']} (M_h x M_v = {P['M_h']}x{P['M_v']}), K={P['K']}, "
                         f"T={P['T']}, dt={P['dt']}, iters={P['iters']}, fine {P['fine_az']}x{P['fine_el']} "
-                        f"pooled {P['pool_az']}x{P['pool_el']}, forest LiDAR sweep of {len(w.cloud)} points",
+                        f"pooled {P['pool_az']}x{P['pool_el']}, refine {P.get('refine_steps', 0)} x {P.get('refine_step', 0)}, "
+                        f"scene of {len(w.cloud)} points",
             "E": P["E"], "K": P["K"], "T": P["T"], "n_points": int(len(w.cloud)),
             "l2": "flushed between timed steps (512 MB write)"}
 

@@ -77,7 +77,9 @@ extern "C" {
 #define AERO_DBG_SAMPLE_X 12     /* float [E][D][T+1][10]: their states (p - p0, q, v) */
 #define AERO_DBG_SAMPLE_DIST 13  /* float [E][D][T]: their nearest-point distances, or
                                     +inf where none is closer than d_max */
-#define AERO_DBG_COUNT 14
+#define AERO_DBG_PRE_REFINE 14   /* float [E][T][4]: nominals after the last update, before the
+                                    gradient refinement (written when refine_steps > 0) */
+#define AERO_DBG_COUNT 15
 
 /* ---- inputs ----------------------------------------------------------- */
 
@@ -126,6 +128,10 @@ typedef struct {
                              (4 when E*K <= 32768, else 1), or 1 or 4 */
   uint64_t seed;          /* Philox key */
   uint64_t step_id;       /* enters the Philox counter: (k, j, e, (step_id << 8) | iter) */
+  int32_t refine_steps;   /* gradient refinement of every updated nominal before Stage II:
+                             this many steps u <- clamp(u - refine_step dS(1)/du, u_min, u_max),
+                             dS(1)/du of the noise-free rollout (0 = off, at most 64) */
+  float refine_step;      /* their step size (default 0.05) */
 } aero_params_t;
 
 typedef struct aero_planner aero_planner_t;
@@ -290,6 +296,22 @@ int aero_batch_destroy(aero_batch_t* batch);
 
 /* Bytes of debug buffer `what` (AERO_DBG_*) for the last step; 0 if unknown. */
 size_t aero_debug_size(aero_planner_t* planner, int32_t what);
+
+/* S(1) and its gradient for n control sequences of instance `instance`, in the
+ * context of the planner's last step (state, guide of that instance, collision
+ * grid, parameters): S = the Stage I cost of the noise-free rollout of each
+ * sequence (the terms of Sec. IV-C: tracking, velocity norm, control, goal,
+ * collision) and dS/dU by the adjoint of the rollout (reverse mode through
+ * the RK4 steps, checkpoints every 8 steps) -- the gradient the refinement
+ * (refine_steps) follows.  U: device, n x T x 4 float, 16-byte aligned;
+ * S_out: device, n; dSdU_out: device, n x T x 4 (16-byte aligned), or NULL for
+ * the costs only.  Enqueued on `stream`; the context is valid until the
+ * planner's next step.  Where a term is not differentiable (a norm at zero,
+ * J_col at d_min and d_max, a tie of nearest points) the gradient of the piece
+ * in use is taken.  Errors: INVALID_ARG (no step yet, instance >= E, n < 0,
+ * misaligned), NOT_DEVICE_PTR. */
+int aero_cost_grad(aero_planner_t* planner, int32_t instance, const float* U, int32_t n,
+                   float* S_out, float* dSdU_out, void* stream);
 
 /* Copy debug buffer `what` of the last step into dst (host or device), at most
  * `bytes` bytes, ordered on `stream` (asynchronous for device dst and pinned

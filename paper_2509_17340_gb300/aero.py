@@ -28,7 +28,7 @@ ERR_INVALID_ARG, ERR_EXCEEDS_LIMITS, ERR_CUDA, ERR_ALLOC, ERR_DEVICE_CHECK, ERR_
 
 DBG = dict(FINE_KEYS=0, COARSE_WIN=1, GOAL_CELL=2, ANCHOR_CELLS=3, ANCHORS=4, GUIDES=5,
            GRID_META=6, GRID_START=7, GRID_POINTS=8, SAMPLE_COSTS=9, STAGE2_STATES=10,
-           SAMPLE_U=11, SAMPLE_X=12, SAMPLE_DIST=13)
+           SAMPLE_U=11, SAMPLE_X=12, SAMPLE_DIST=13, PRE_REFINE=14)
 
 STAGES = ["partition", "grid", "rollout", "update"]
 
@@ -59,6 +59,7 @@ class Params(C.Structure):
         ("v_goal", C.c_float * 3), ("q_goal", C.c_float * 4),
         ("debug_samples", C.c_int32), ("lanes_per_sample", C.c_int32),
         ("seed", C.c_uint64), ("step_id", C.c_uint64),
+        ("refine_steps", C.c_int32), ("refine_step", C.c_float),
     ]
 
 
@@ -93,6 +94,7 @@ _lib.aero_debug_size.argtypes = [_vp, C.c_int32]
 _lib.aero_debug_size.restype = C.c_size_t
 _lib.aero_get_debug.argtypes = [_vp, C.c_int32, _vp, C.c_size_t, _vp]
 _lib.aero_sync_status.argtypes = [_vp, _vp]
+_lib.aero_cost_grad.argtypes = [_vp, C.c_int32, _vp, C.c_int32, _vp, _vp, _vp]
 _lib.aero_philox.argtypes = [C.c_uint64, C.c_uint32, C.c_uint32, C.c_uint32, C.c_int64, _vp, _vp]
 _lib.aero_profile_enable.argtypes = [_vp, C.c_int]
 _lib.aero_profile_read.argtypes = [_vp, C.POINTER(C.c_double), C.POINTER(C.c_int64)]
@@ -152,6 +154,8 @@ def params_struct(d: dict) -> Params:
         for i, v in enumerate(d[k]):
             arr[i] = float(v)
     p.seed, p.step_id = int(d["seed"]), int(d["step_id"])
+    p.refine_steps = int(d.get("refine_steps", 0))
+    p.refine_step = float(d.get("refine_step", 0.05))
     return p
 
 
@@ -258,6 +262,16 @@ class Planner:
         _check(_lib.aero_get_debug(self._h, wid, buf.ctypes.data, nbytes, stream_p), "aero_get_debug")
         torch.cuda.synchronize()
         return buf
+
+    def cost_grad(self, instance: int, U: torch.Tensor, S: torch.Tensor,
+                  G: torch.Tensor | None = None, stream=None) -> None:
+        """S(1) of the noise-free rollouts of U (n x T x 4) for instance
+        `instance` of the last step, and dS/dU into G (``aero_cost_grad``)."""
+        n = U.shape[0]
+        _check(_lib.aero_cost_grad(self._h, instance, _dev(U, torch.float32, "U"), n,
+                                   _dev(S, torch.float32, "S"),
+                                   _dev(G, torch.float32, "G") if G is not None else None,
+                                   _stream_ptr(stream)), "aero_cost_grad")
 
     def profile(self, stages) -> None:
         """Time the given stages (names from STAGES, True = all, False = none)
@@ -406,3 +420,25 @@ class Batch:
                "aero_batch_get_debug")
         torch.cuda.synchronize()
         return buf
+
+
+class RolloutCost(torch.autograd.Function):
+    """S(1) of noise-free rollouts as a differentiable torch function:
+    forward runs ``aero_cost_grad`` (cost and adjoint gradient in one kernel),
+    backward scales the saved gradient.  ``RolloutCost.apply(U, planner,
+    instance)`` with U an (n, T, 4) float32 CUDA tensor returns S (n,); the
+    planner's last step supplies the state, guide, collision grid and weights."""
+
+    @staticmethod
+    def forward(ctx, U, planner, instance):
+        U = U.detach().contiguous()
+        S = torch.empty(U.shape[0], dtype=torch.float32, device=U.device)
+        G = torch.empty_like(U)
+        planner.cost_grad(int(instance), U, S, G, torch.cuda.current_stream(U.device))
+        ctx.save_for_backward(G)
+        return S
+
+    @staticmethod
+    def backward(ctx, gS):
+        (G,) = ctx.saved_tensors
+        return gS[:, None, None] * G, None, None

@@ -1,0 +1,324 @@
+// Gradient of the Stage I cost S(1) of a noise-free rollout with respect to
+// its T x 4 controls, by reverse mode (adjoint) through the rollout: the
+// dynamics' vector-Jacobian products at the stages of the classical RK4
+// step, the quaternion renormalisation, and the cost terms (tracking, velocity
+// norm, control, goal, collision).  Not a step of the paper: it serves the
+// gradient refinement of the updated nominals before Stage II.
+//
+// One warp per control sequence.  Every lane runs the same serial chain on the
+// same operands (so all lanes hold the same values); the nearest-point scans
+// are split across the lanes.  The forward pass keeps a checkpoint every 8
+// steps; the backward pass recomputes each 8-step segment from its checkpoint.
+#pragma once
+
+#include "device.cuh"
+#include "internal.h"
+
+namespace aero {
+
+constexpr int kCkpt = 8;  // steps per checkpoint segment
+
+// Scratch of one warp in shared memory.
+struct AdjScratch {
+  float ck[(kMaxT / kCkpt + 1) * 10];  // checkpoints x_0, x_8, x_16, ...
+  float seg[(kCkpt + 1) * 10];         // the states of one segment
+};
+
+__device__ __forceinline__ void state_store(float* d, const State& x) {
+#pragma unroll
+  for (int i = 0; i < 3; ++i) d[i] = x.p[i];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) d[3 + i] = x.q[i];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) d[7 + i] = x.v[i];
+}
+
+__device__ __forceinline__ State state_load(const float* d) {
+  State x;
+#pragma unroll
+  for (int i = 0; i < 3; ++i) x.p[i] = d[i];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) x.q[i] = d[3 + i];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) x.v[i] = d[7 + i];
+  return x;
+}
+
+// Nearest collision point of p by the warp: squared distance (d_max^2 when
+// none is closer) and the entry of the nearest point (lowest entry among ties).
+__device__ __forceinline__ float warp_nn(float px, float py, float pz, const GridView& g,
+                                         float dmax2, int lane, float4& nearest) {
+  const int2 r = cell_range(px, py, pz, g);
+  float best = dmax2;
+  int bi = 0x7fffffff;
+  for (int i = lane; i < r.y; i += 32) {
+    const float d2 = dist2_to(__ldg(g.pts + r.x + i), px, py, pz);
+    if (d2 < best) {
+      best = d2;
+      bi = r.x + i;
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const float ob = __shfl_xor_sync(0xffffffffu, best, o);
+    const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+    if (ob < best || (ob == best && oi < bi)) {
+      best = ob;
+      bi = oi;
+    }
+  }
+  if (bi != 0x7fffffff) nearest = __ldg(g.pts + bi);
+  return best;
+}
+
+// Stage I state terms at the post-step state x against guide sample (gx, gy,
+// gz), the form the rollout kernels use.  grad: add the gradient to gs[10].
+template <bool kGrad>
+__device__ __forceinline__ float state_terms(const State& x, float gx, float gy, float gz,
+                                             const CostParams& cp, const GridView& grid,
+                                             float dmax2, int lane, float* gs) {
+  float4 nearest = make_float4(0.f, 0.f, 0.f, 0.f);
+  const float d2 = warp_nn(x.p[0], x.p[1], x.p[2], grid, dmax2, lane, nearest);
+  const float ex = x.p[0] - gx, ey = x.p[1] - gy, ez = x.p[2] - gz;
+  const float et = norm3f(ex, ey, ez);
+  const float px = x.p[0] - cp.goal_rel[0], py = x.p[1] - cp.goal_rel[1], pz = x.p[2] - cp.goal_rel[2];
+  const float np = norm3f(px, py, pz);
+  const float vx = x.v[0] - cp.v_goal[0], vy = x.v[1] - cp.v_goal[1], vz = x.v[2] - cp.v_goal[2];
+  const float nv = norm3f(vx, vy, vz);
+  const float* q = x.q;
+  const float* qg = cp.q_goal;
+  const float r1 = -q[0] * qg[1] + q[1] * qg[0] - q[2] * qg[3] + q[3] * qg[2];
+  const float r2 = -q[0] * qg[2] + q[1] * qg[3] + q[2] * qg[0] - q[3] * qg[1];
+  const float r3 = -q[0] * qg[3] - q[1] * qg[2] + q[2] * qg[1] + q[3] * qg[0];
+  const float nr = fast_sqrt(r1 * r1 + r2 * r2 + r3 * r3);
+  const float jc = jcol_from_d2(d2, cp, dmax2);
+  const float c = cp.Q_track * et + cp.Q_vnorm * (x.v[0] * x.v[0] + x.v[1] * x.v[1] + x.v[2] * x.v[2]) +
+                  cp.Q_p * np + cp.Q_v * nv + cp.Q_q * 2.8284271247461903f * nr + jc;
+  if (kGrad) {
+    if (et > 0.0f) {
+      const float s = cp.Q_track / et;
+      gs[0] += s * ex; gs[1] += s * ey; gs[2] += s * ez;
+    }
+    if (np > 0.0f) {
+      const float s = cp.Q_p / np;
+      gs[0] += s * px; gs[1] += s * py; gs[2] += s * pz;
+    }
+    gs[7] += 2.0f * cp.Q_vnorm * x.v[0];
+    gs[8] += 2.0f * cp.Q_vnorm * x.v[1];
+    gs[9] += 2.0f * cp.Q_vnorm * x.v[2];
+    if (nv > 0.0f) {
+      const float s = cp.Q_v / nv;
+      gs[7] += s * vx; gs[8] += s * vy; gs[9] += s * vz;
+    }
+    if (nr > 0.0f) {
+      // d r / d q: r1 (-g1, g0, -g3, g2), r2 (-g2, g3, g0, -g1), r3 (-g3, -g2, g1, g0)
+      const float s = cp.Q_q * 2.8284271247461903f / nr;
+      const float a = s * r1, b = s * r2, e = s * r3;
+      gs[3] += -a * qg[1] - b * qg[2] - e * qg[3];
+      gs[4] += a * qg[0] + b * qg[3] - e * qg[2];
+      gs[5] += -a * qg[3] + b * qg[0] + e * qg[1];
+      gs[6] += a * qg[2] - b * qg[1] + e * qg[0];
+    }
+    if (d2 < dmax2) {
+      const float d = sqrtf(d2);
+      if (d >= cp.d_min && d > 0.0f) {
+        const float s = -cp.a_col * jc / d;
+        gs[0] += s * (x.p[0] - nearest.x);
+        gs[1] += s * (x.p[1] - nearest.y);
+        gs[2] += s * (x.p[2] - nearest.z);
+      }
+    }
+  }
+  return c;
+}
+
+// xd = f(x, u) of the quadrotor model (Eq. dynamics) at a stage state.
+__device__ __forceinline__ void dyn_f(const float* x, float4 u, const DynParams& dp, float* xd) {
+  const float qw = x[3], qx = x[4], qy = x[5], qz = x[6];
+  xd[0] = x[7]; xd[1] = x[8]; xd[2] = x[9];
+  xd[3] = 0.5f * (-qx * u.y - qy * u.z - qz * u.w);
+  xd[4] = 0.5f * (qw * u.y + qy * u.w - qz * u.z);
+  xd[5] = 0.5f * (qw * u.z - qx * u.w + qz * u.y);
+  xd[6] = 0.5f * (qw * u.w + qx * u.z - qy * u.y);
+  float rx, ry, rz;
+  r_e3(qw, qx, qy, qz, rx, ry, rz);
+  const float f = u.x * dp.inv_mass;
+  xd[7] = f * rx; xd[8] = f * ry; xd[9] = f * rz - dp.g;
+}
+
+// w^T df/dx added to gx, w^T df/du added to gu, at stage state x.
+__device__ __forceinline__ void dyn_vjp(const float* x, float4 u, const DynParams& dp,
+                                        const float* w, float* gx, float* gu) {
+  const float qw = x[3], qx = x[4], qy = x[5], qz = x[6];
+  const float ox = u.y, oy = u.z, oz = u.w;
+  gx[7] += w[0]; gx[8] += w[1]; gx[9] += w[2];
+  const float W0 = 0.5f * w[3], W1 = 0.5f * w[4], W2 = 0.5f * w[5], W3 = 0.5f * w[6];
+  gx[3] += W1 * ox + W2 * oy + W3 * oz;
+  gx[4] += -W0 * ox - W2 * oz + W3 * oy;
+  gx[5] += -W0 * oy + W1 * oz - W3 * ox;
+  gx[6] += -W0 * oz - W1 * oy + W2 * ox;
+  gu[1] += -W0 * qx + W1 * qw + W2 * qz - W3 * qy;
+  gu[2] += -W0 * qy - W1 * qz + W2 * qw + W3 * qx;
+  gu[3] += -W0 * qz + W1 * qy - W2 * qx + W3 * qw;
+  const float V0 = w[7], V1 = w[8], V2 = w[9];
+  float rx, ry, rz;
+  r_e3(qw, qx, qy, qz, rx, ry, rz);
+  gu[0] += (V0 * rx + V1 * ry + V2 * rz) * dp.inv_mass;
+  const float s = u.x * dp.inv_mass;
+  gx[3] += s * (2.0f * qy * V0 - 2.0f * qx * V1);
+  gx[4] += s * (2.0f * qz * V0 - 2.0f * qw * V1 - 4.0f * qx * V2);
+  gx[5] += s * (2.0f * qw * V0 + 2.0f * qz * V1 - 4.0f * qy * V2);
+  gx[6] += s * (2.0f * qx * V0 + 2.0f * qy * V1);
+}
+
+// Reverse of one RK4 step from x with control u: lam holds dS/dx_{j+1} on
+// entry and dS/dx_j on return; gu gets dS/du_j from the dynamics.
+__device__ __forceinline__ void rk4_vjp(const float* x, float4 u, const DynParams& dp, float* lam,
+                                        float* gu) {
+  const float h = dp.dt;
+  float k1[10], k2[10], k3[10], k4[10], t2[10], t3[10], t4[10];
+  dyn_f(x, u, dp, k1);
+#pragma unroll
+  for (int i = 0; i < 10; ++i) t2[i] = x[i] + 0.5f * h * k1[i];
+  dyn_f(t2, u, dp, k2);
+#pragma unroll
+  for (int i = 0; i < 10; ++i) t3[i] = x[i] + 0.5f * h * k2[i];
+  dyn_f(t3, u, dp, k3);
+#pragma unroll
+  for (int i = 0; i < 10; ++i) t4[i] = x[i] + h * k3[i];
+  dyn_f(t4, u, dp, k4);
+  // the quaternion before renormalisation, and the projection (I - q q^T)/|y|
+  float y[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+    y[i] = x[3 + i] + h * (1.0f / 6.0f) * (k1[3 + i] + 2.0f * k2[3 + i] + 2.0f * k3[3 + i] + k4[3 + i]);
+  const float inv = rsqrtf(y[0] * y[0] + y[1] * y[1] + y[2] * y[2] + y[3] * y[3]);
+  const float dot = (y[0] * lam[3] + y[1] * lam[4] + y[2] * lam[5] + y[3] * lam[6]) * inv;
+  float ly[10];
+#pragma unroll
+  for (int i = 0; i < 10; ++i) ly[i] = lam[i];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) ly[3 + i] = (lam[3 + i] - y[i] * inv * dot) * inv;
+  float l1[10], l2[10], l3[10], l4[10], lt[10];
+#pragma unroll
+  for (int i = 0; i < 10; ++i) {
+    lam[i] = ly[i];
+    l1[i] = h * (1.0f / 6.0f) * ly[i];
+    l2[i] = h * (1.0f / 3.0f) * ly[i];
+    l3[i] = l2[i];
+    l4[i] = l1[i];
+  }
+#pragma unroll
+  for (int i = 0; i < 10; ++i) lt[i] = 0.0f;
+  dyn_vjp(t4, u, dp, l4, lt, gu);
+#pragma unroll
+  for (int i = 0; i < 10; ++i) { lam[i] += lt[i]; l3[i] += h * lt[i]; lt[i] = 0.0f; }
+  dyn_vjp(t3, u, dp, l3, lt, gu);
+#pragma unroll
+  for (int i = 0; i < 10; ++i) { lam[i] += lt[i]; l2[i] += 0.5f * h * lt[i]; lt[i] = 0.0f; }
+  dyn_vjp(t2, u, dp, l2, lt, gu);
+#pragma unroll
+  for (int i = 0; i < 10; ++i) { lam[i] += lt[i]; l1[i] += 0.5f * h * lt[i]; }
+  dyn_vjp(x, u, dp, l1, lam, gu);
+}
+
+// S(1) of the noise-free rollout of u (shared, T entries) from x0 and, with
+// kGrad, dS/du into g (shared, T entries).  guide: T x 3 (shared or global).
+// Called by all 32 lanes of one warp; returns S on every lane.
+template <bool kGrad>
+__device__ float warp_cost_grad(const float4* u, float4* g, const float* guide, int T,
+                                const float* x0, const DynParams& dp, const CostParams& cp,
+                                const GridView& grid, AdjScratch& sc, int lane) {
+  const float dmax2 = cp.d_max * cp.d_max;
+  State x = state_load(x0);
+  float S = 0.0f;
+  for (int j = 0; j < T; ++j) {
+    if (kGrad && (j % kCkpt) == 0 && lane == 0) state_store(sc.ck + (j / kCkpt) * 10, x);
+    rk4_step(x, u[j], dp);
+    S += state_terms<false>(x, guide[3 * j], guide[3 * j + 1], guide[3 * j + 2], cp, grid, dmax2,
+                            lane, nullptr);
+  }
+  // J_ctrl: Q_c |u_t|^2 (t <= T-2) and Q_cd |u_t - u_{t-1}|^2 (1 <= t <= T-2)
+  float jc = 0.0f;
+  for (int t = lane; t <= T - 2; t += 32) {
+    const float4 a = u[t];
+    jc += cp.Q_c * (a.x * a.x + a.y * a.y + a.z * a.z + a.w * a.w);
+    if (t >= 1) {
+      const float4 b = u[t - 1];
+      const float dx = a.x - b.x, dy = a.y - b.y, dz = a.z - b.z, dw = a.w - b.w;
+      jc += cp.Q_cd * (dx * dx + dy * dy + dz * dz + dw * dw);
+    }
+  }
+  S += warp_sum(jc);
+  if (!kGrad) return S;
+
+  __syncwarp();
+  float lam[10];
+#pragma unroll
+  for (int i = 0; i < 10; ++i) lam[i] = 0.0f;
+  const int nseg = (T + kCkpt - 1) / kCkpt;
+  for (int s = nseg - 1; s >= 0; --s) {
+    const int j0 = s * kCkpt, j1 = min(T, j0 + kCkpt);
+    // recompute the segment's states from its checkpoint
+    State y = state_load(sc.ck + s * 10);
+    if (lane == 0) state_store(sc.seg, y);
+    for (int j = j0; j < j1; ++j) {
+      rk4_step(y, u[j], dp);
+      if (lane == 0) state_store(sc.seg + (j - j0 + 1) * 10, y);
+    }
+    __syncwarp();
+    for (int j = j1 - 1; j >= j0; --j) {
+      const State xn = state_load(sc.seg + (j - j0 + 1) * 10);
+      state_terms<true>(xn, guide[3 * j], guide[3 * j + 1], guide[3 * j + 2], cp, grid, dmax2, lane,
+                        lam);
+      float gu[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+      rk4_vjp(sc.seg + (j - j0) * 10, u[j], dp, lam, gu);
+      if (lane == 0) g[j] = make_float4(gu[0], gu[1], gu[2], gu[3]);
+    }
+    __syncwarp();
+  }
+  // control terms
+  for (int t = lane; t < T; t += 32) {
+    float4 a = g[t];
+    const float4 ut = u[t];
+    if (t <= T - 2) {
+      a.x += 2.0f * cp.Q_c * ut.x; a.y += 2.0f * cp.Q_c * ut.y;
+      a.z += 2.0f * cp.Q_c * ut.z; a.w += 2.0f * cp.Q_c * ut.w;
+    }
+    if (t >= 1 && t <= T - 2) {
+      const float4 b = u[t - 1];
+      a.x += 2.0f * cp.Q_cd * (ut.x - b.x); a.y += 2.0f * cp.Q_cd * (ut.y - b.y);
+      a.z += 2.0f * cp.Q_cd * (ut.z - b.z); a.w += 2.0f * cp.Q_cd * (ut.w - b.w);
+    }
+    if (t + 1 >= 1 && t + 1 <= T - 2) {
+      const float4 c = u[t + 1];
+      a.x -= 2.0f * cp.Q_cd * (c.x - ut.x); a.y -= 2.0f * cp.Q_cd * (c.y - ut.y);
+      a.z -= 2.0f * cp.Q_cd * (c.z - ut.z); a.w -= 2.0f * cp.Q_cd * (c.w - ut.w);
+    }
+    g[t] = a;
+  }
+  __syncwarp();
+  return S;
+}
+
+// refine_steps clamped gradient steps u <- clamp(u - refine_step dS/du) on
+// the shared nominal u, by one warp (g: shared scratch of T entries).
+__device__ __forceinline__ void warp_refine(float4* u, float4* g, const float* guide, int T,
+                                            const float* x0, const DynParams& dp,
+                                            const CostParams& cp, const GridView& grid,
+                                            const float* umin, const float* umax, int steps,
+                                            float alpha, AdjScratch& sc, int lane) {
+  for (int r = 0; r < steps; ++r) {
+    warp_cost_grad<true>(u, g, guide, T, x0, dp, cp, grid, sc, lane);
+    for (int t = lane; t < T; t += 32) {
+      const float4 a = u[t], d = g[t];
+      u[t] = make_float4(fminf(fmaxf(a.x - alpha * d.x, umin[0]), umax[0]),
+                         fminf(fmaxf(a.y - alpha * d.y, umin[1]), umax[1]),
+                         fminf(fmaxf(a.z - alpha * d.z, umin[2]), umax[2]),
+                         fminf(fmaxf(a.w - alpha * d.w, umin[3]), umax[3]));
+    }
+    __syncwarp();
+  }
+}
+
+}  // namespace aero

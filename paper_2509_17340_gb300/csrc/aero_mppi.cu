@@ -48,6 +48,7 @@ struct aero_planner {
   float* dbg_u = nullptr;
   float* dbg_x = nullptr;
   float* dbg_d = nullptr;
+  float* dbg_pre = nullptr;   // nominals before the gradient refinement
   // staging for aero_plan_step_host
   float* stage_cloud = nullptr;
   float* stage_unom = nullptr;
@@ -58,6 +59,7 @@ struct aero_planner {
   bool have_step = false;
   aero_params_t last{};
   GridGeom last_grid{};
+  UpdateArgs last_ctx{};  // state, dynamics, costs, grid and guides of the last step
   int last_ntiles = 0;
   int last_nb = 0;
   // stage timing (aero_profile_enable / aero_profile_read)
@@ -178,6 +180,9 @@ int validate(const aero_planner* pl, const aero_params_t* p, int64_t n_points) {
   if (p->debug_samples < 0 || n_points < 0) return AERO_ERR_INVALID_ARG;
   if (p->lanes_per_sample != 0 && p->lanes_per_sample != 1 && p->lanes_per_sample != 4)
     return AERO_ERR_INVALID_ARG;
+  if (p->refine_steps < 0 || p->refine_steps > 64 || !(p->refine_step >= 0.0f) ||
+      !std::isfinite(p->refine_step))
+    return AERO_ERR_INVALID_ARG;
   if (p->E > L.E_max || p->K > L.K_max || p->T > L.T_max ||
       (int64_t)p->fine_az * p->fine_el > L.fine_cells_max || n_points > L.n_points_max ||
       p->debug_samples > L.debug_samples_max)
@@ -197,7 +202,7 @@ void free_all(aero_planner* pl) {
                   pl->cand,     pl->grid_range, pl->partials,
                   pl->sample_costs, pl->dU,      pl->stage2_x, pl->counter,   pl->status,   pl->dbg_u,
                   pl->dbg_x,    pl->dbg_d,      pl->stage_cloud,      pl->stage_unom,   pl->stage_ubest,
-                  pl->stage_cand,   pl->stage_best};
+                  pl->stage_cand,   pl->stage_best,   pl->dbg_pre};
   for (void* q : ptrs)
     if (q) cudaFree(q);
 }
@@ -414,6 +419,14 @@ void make_step_args(aero_planner* pl, const aero_state_t* x0, const float* cloud
   ua.cost = cp;
   ua.grid = gv;
   ua.stage2_x = pl->stage2_x;
+  ua.guides = pl->guides;
+  for (int c = 0; c < 4; ++c) {
+    ua.umin[c] = p.u_min[c];
+    ua.umax[c] = p.u_max[c];
+  }
+  ua.refine_steps = p.refine_steps;
+  ua.refine_step = p.refine_step;
+  ua.dbg_pre = p.refine_steps > 0 ? pl->dbg_pre : nullptr;
   ua.cand = cand;
   ua.best_idx = best_idx;
   ua.u_best = u_best;
@@ -423,6 +436,7 @@ void make_step_args(aero_planner* pl, const aero_state_t* x0, const float* cloud
 
 // The planner's state after a step has been enqueued.
 void note_step(aero_planner* pl, const aero_params_t& p, const StepArgs& a) {
+  pl->last_ctx = a.ua;
   pl->grid_dirty = false;
   pl->have_step = true;
   pl->last = p;
@@ -544,6 +558,8 @@ void aero_params_default(aero_params_t* p) {
   p->debug_samples = 0;
   p->seed = 0;
   p->step_id = 0;
+  p->refine_steps = 0;
+  p->refine_step = 0.05f;
 }
 
 int aero_create(const aero_limits_t* limits, aero_planner_t** out) {
@@ -596,6 +612,7 @@ int aero_create(const aero_limits_t* limits, aero_planner_t** out) {
   chk(alloc(&pl->dbg_u, (size_t)L.E_max * D * L.T_max * 4));
   chk(alloc(&pl->dbg_x, (size_t)L.E_max * D * (L.T_max + 1) * 10));
   chk(alloc(&pl->dbg_d, (size_t)L.E_max * D * L.T_max));
+  chk(alloc(&pl->dbg_pre, (size_t)L.E_max * L.T_max * 4));
   chk(alloc(&pl->stage_cloud, (size_t)L.n_points_max * 3));
   chk(alloc(&pl->stage_unom, (size_t)L.E_max * L.T_max * 4));
   chk(alloc(&pl->stage_ubest, (size_t)L.T_max * 4));
@@ -692,6 +709,7 @@ size_t aero_debug_size(aero_planner_t* pl, int32_t what) {
     case AERO_DBG_SAMPLE_U: return 4 * E * D * T * 4;
     case AERO_DBG_SAMPLE_X: return 4 * E * D * (T + 1) * 10;
     case AERO_DBG_SAMPLE_DIST: return 4 * E * D * T;
+    case AERO_DBG_PRE_REFINE: return p.refine_steps > 0 ? 4 * E * T * 4 : 0;
     default: return 0;
   }
 }
@@ -747,6 +765,7 @@ int aero_get_debug(aero_planner_t* pl, int32_t what, void* dst, size_t bytes, vo
     case AERO_DBG_SAMPLE_U: src = pl->dbg_u; break;
     case AERO_DBG_SAMPLE_X: src = pl->dbg_x; break;
     case AERO_DBG_SAMPLE_DIST: src = pl->dbg_d; break;
+    case AERO_DBG_PRE_REFINE: src = pl->dbg_pre; break;
     default: return AERO_ERR_INVALID_ARG;
   }
   (void)p;
@@ -767,6 +786,26 @@ int aero_sync_status(aero_planner_t* pl, void* stream) {
     return AERO_ERR_DEVICE_CHECK;
   }
   return AERO_OK;
+}
+
+int aero_cost_grad(aero_planner_t* pl, int32_t instance, const float* U, int32_t n, float* S_out,
+                   float* dSdU_out, void* stream) {
+  if (!pl || n < 0 || (n > 0 && (!U || !S_out)) || !pl->have_step) return AERO_ERR_INVALID_ARG;
+  if (instance < 0 || instance >= pl->last.E) return AERO_ERR_INVALID_ARG;
+  if (n == 0) return AERO_OK;
+  if (reinterpret_cast<uintptr_t>(U) % 16 != 0 ||
+      (dSdU_out && reinterpret_cast<uintptr_t>(dSdU_out) % 16 != 0))
+    return AERO_ERR_INVALID_ARG;
+  if (!is_device_ptr(U) || !is_device_ptr(S_out) || (dSdU_out && !is_device_ptr(dSdU_out)))
+    return AERO_ERR_NOT_DEVICE_PTR;
+  CostGradArgs a{};
+  a.ctx = pl->last_ctx;
+  a.instance = instance;
+  a.U = reinterpret_cast<const float4*>(U);
+  a.n = n;
+  a.S = S_out;
+  a.G = reinterpret_cast<float4*>(dSdU_out);
+  return cuda_fail(launch_cost_grad(a, (cudaStream_t)stream));
 }
 
 int aero_philox(uint64_t seed, uint32_t c1, uint32_t c2, uint32_t c3, int64_t n, uint32_t* out,

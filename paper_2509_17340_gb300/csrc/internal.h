@@ -142,6 +142,11 @@ struct UpdateArgs {
   CostParams cost;
   GridView grid;
   float* stage2_x;         // E x (T+1) x 10
+  const float* guides;     // E x T x 3 (relative): the tracking term of the refinement
+  float umin[4], umax[4];
+  int refine_steps;        // gradient steps on each updated nominal before Stage II
+  float refine_step;
+  float* dbg_pre;          // E x T x 4: the nominals before the refinement (refine_steps > 0)
   float* cand;             // E
   int* best_idx;
   float* u_best;           // T x 4
@@ -223,7 +228,18 @@ cudaError_t launch_grid_count(const CandArgs& ca, const GuideArgs& ga, const Par
 cudaError_t launch_grid_scan(int* count, int* fill, int* local, int* tile_sum, int* tile_off,
                              int ncells, int ntiles, unsigned int* counter, cudaStream_t s);
 cudaError_t launch_grid_scatter(const CandArgs& ca, int2* range, int ncells, cudaStream_t s);
+// S(1) of n noise-free rollouts of instance `instance` and their gradients.
+struct CostGradArgs {
+  UpdateArgs ctx;          // x0, dynamics, costs, grid, guides, T of the last step
+  int instance;
+  const float4* U;         // n x T
+  int n;
+  float* S;                // n
+  float4* G;               // n x T, or null
+};
+
 cudaError_t launch_rollout(const RolloutArgs& a, cudaStream_t s);
+cudaError_t launch_cost_grad(const CostGradArgs& a, cudaStream_t s);
 cudaError_t launch_update(const UpdateArgs& a, cudaStream_t s);
 cudaError_t launch_philox(uint32_t k0, uint32_t k1, uint32_t c1, uint32_t c2, uint32_t c3,
                           int64_t n, uint32_t* out, cudaStream_t s);

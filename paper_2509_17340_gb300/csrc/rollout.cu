@@ -10,6 +10,7 @@
 #include <cfloat>
 #include <cstdint>
 
+#include "adjoint.cuh"
 #include "device.cuh"
 #include "internal.h"
 
@@ -479,7 +480,21 @@ __device__ __forceinline__ void update_unit(const UpdateArgs& a, int e, bool fin
   if (!final_stage) return;
   __syncthreads();
 
-  // Stage II: noise-free rollout of the updated nominal
+  // gradient refinement of the updated nominal (warp 0; s_x and s_acc serve
+  // as its scratch before Stage II fills s_x)
+  if (a.refine_steps > 0) {
+    if (a.dbg_pre)
+      for (int i = tid; i < 4 * T; i += UT) a.dbg_pre[(size_t)e * T * 4 + i] = s_u[i];
+    if (wid == 0)
+      warp_refine(s_u4, s_acc[0], a.guides + (size_t)e * T * 3, T, a.x0, a.dyn, a.cost, a.grid,
+                  a.umin, a.umax, a.refine_steps, a.refine_step,
+                  *reinterpret_cast<AdjScratch*>(s_x), lane);
+    __syncthreads();
+    for (int i = tid; i < 4 * T; i += UT) un[i] = s_u[i];
+    __syncthreads();
+  }
+
+  // Stage II: noise-free rollout of the (updated, refined) nominal
   if (tid == 0) {
     State x;
     for (int i = 0; i < 3; ++i) x.p[i] = a.x0[i];
@@ -648,7 +663,39 @@ __global__ void __launch_bounds__(UT) k_b_update(BatchView v, int it) {
   }
 }
 
+// One warp per control sequence: S(1) of its noise-free rollout and dS/dU.
+constexpr int kCgWarps = 4;
+
+__global__ void __launch_bounds__(32 * kCgWarps) k_cost_grad(CostGradArgs a) {
+  __shared__ float4 s_u[kCgWarps][kMaxT];
+  __shared__ float4 s_g[kCgWarps][kMaxT];
+  __shared__ AdjScratch s_sc[kCgWarps];
+  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int i = blockIdx.x * kCgWarps + wid;
+  if (i >= a.n) return;  // uniform over the warp
+  const int T = a.ctx.T;
+  for (int t = lane; t < T; t += 32) s_u[wid][t] = a.U[(size_t)i * T + t];
+  __syncwarp();
+  const float* guide = a.ctx.guides + (size_t)a.instance * T * 3;
+  float S;
+  if (a.G)
+    S = warp_cost_grad<true>(s_u[wid], s_g[wid], guide, T, a.ctx.x0, a.ctx.dyn, a.ctx.cost,
+                             a.ctx.grid, s_sc[wid], lane);
+  else
+    S = warp_cost_grad<false>(s_u[wid], s_g[wid], guide, T, a.ctx.x0, a.ctx.dyn, a.ctx.cost,
+                              a.ctx.grid, s_sc[wid], lane);
+  if (lane == 0) a.S[i] = S;
+  if (a.G)
+    for (int t = lane; t < T; t += 32) a.G[(size_t)i * T + t] = s_g[wid][t];
+}
+
 }  // namespace
+
+cudaError_t launch_cost_grad(const CostGradArgs& a, cudaStream_t s) {
+  if (a.n == 0) return cudaSuccess;
+  k_cost_grad<<<(a.n + kCgWarps - 1) / kCgWarps, 32 * kCgWarps, 0, s>>>(a);
+  return cudaGetLastError();
+}
 
 cudaError_t batch_rollout_occupancy(int out[4]) {
   cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(out + 0, k_b_rollout<1, 5>, NT, 0);

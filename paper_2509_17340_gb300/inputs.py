@@ -51,6 +51,7 @@ def default_params() -> dict:
         collision_set=0,
         v_goal=[0.0, 0.0, 0.0], q_goal=[1.0, 0.0, 0.0, 0.0],
         seed=0, step_id=0, debug_samples=0,
+        refine_steps=0, refine_step=0.05,
     )
     return p
 
@@ -64,6 +65,8 @@ def workload_params(name: str) -> dict:
                8x16 to a 16x4 coarse grid.
     large    : E=32 (8x4 anchors), K=8192, T=64, dt=0.03, fine 256x64 pooled
                4x8 to a 64x8 coarse grid, r_max=20 m.
+    refined  : the ensemble sizes with 5 gradient-refinement steps of 0.05 on
+               every updated nominal before Stage II (on the plain scene).
     """
     p = default_params()
     common = dict(lam=1.0, sigma=[2.0, 1.5, 1.5, 1.5],
@@ -79,6 +82,10 @@ def workload_params(name: str) -> dict:
         p.update(common)
         p.update(E=32, K=8192, T=64, dt=0.03, fine_az=256, fine_el=64,
                  pool_az=4, pool_el=8, M_h=8, M_v=4, r_max=20.0)
+    elif name == "refined":
+        p.update(common)
+        p.update(E=8, K=1024, T=40, dt=0.05, fine_az=128, fine_el=64,
+                 pool_az=8, pool_el=16, M_h=4, M_v=2, refine_steps=5, refine_step=0.05)
     else:
         raise KeyError(name)
     return p
@@ -363,7 +370,7 @@ def make_workload(name: str, seed: int = 0) -> Workload:
     p = workload_params(name)
     p["seed"] = seed
     q0 = np.array([1, 0, 0, 0], np.float32)
-    if name == "plain":
+    if name in ("plain", "refined"):
         pts, _ = scene_plain(seed)
         p0, v0, goal = (0, 0, 1.5), (0, 0, 0), (18, 0, 1.5)
     elif name == "ensemble":

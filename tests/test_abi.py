@@ -84,6 +84,6 @@ def test_binding_struct_sizes_match_header():
     from paper_2509_17340_gb300 import aero
     assert C.sizeof(aero.State) == 40
     assert C.sizeof(aero.Limits) == 32
-    assert C.sizeof(aero.Params) == 224
-    assert C.sizeof(aero.BatchItem) == 328
+    assert C.sizeof(aero.Params) == 232
+    assert C.sizeof(aero.BatchItem) == 336
     assert C.sizeof(aero.BatchConfig) == 16
