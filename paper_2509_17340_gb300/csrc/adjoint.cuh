@@ -5,10 +5,11 @@
 // norm, control, goal, collision).  Not a step of the paper: it serves the
 // gradient refinement of the updated nominals before Stage II.
 //
-// One warp per control sequence.  Every lane runs the same serial chain on the
-// same operands (so all lanes hold the same values); the nearest-point scans
-// are split across the lanes.  The forward pass keeps a checkpoint every 8
-// steps; the backward pass recomputes each 8-step segment from its checkpoint.
+// One warp per control sequence.  Every lane runs the same serial RK4 chain on
+// the same operands (so all lanes hold the same values); the nearest-point
+// queries and the state terms of each 8-step segment run side by side on the
+// lanes.  The forward pass keeps a checkpoint every 8 steps; the backward pass
+// recomputes each 8-step segment from its checkpoint.
 #pragma once
 
 #include "device.cuh"
@@ -22,6 +23,9 @@ constexpr int kCkpt = 8;  // steps per checkpoint segment
 struct AdjScratch {
   float ck[(kMaxT / kCkpt + 1) * 10];  // checkpoints x_0, x_8, x_16, ...
   float seg[(kCkpt + 1) * 10];         // the states of one segment
+  float gs[kCkpt][10];                 // state-term gradients of the segment's states
+  float d2[kCkpt];                     // their nearest-point squared distances
+  float4 nearest[kCkpt];               // and nearest points
 };
 
 __device__ __forceinline__ void state_store(float* d, const State& x) {
@@ -44,22 +48,27 @@ __device__ __forceinline__ State state_load(const float* d) {
   return x;
 }
 
-// Nearest collision point of p by the warp: squared distance (d_max^2 when
-// none is closer) and the entry of the nearest point (lowest entry among ties).
-__device__ __forceinline__ float warp_nn(float px, float py, float pz, const GridView& g,
-                                         float dmax2, int lane, float4& nearest) {
-  const int2 r = cell_range(px, py, pz, g);
+// Nearest collision points of the n <= 8 states seg[1..n] by the warp, four
+// lanes per state: squared distances (d_max^2 when none is closer) and the
+// nearest points (lowest entry among ties) into sc.d2 / sc.nearest.
+__device__ __forceinline__ void warp_nn_segment(AdjScratch& sc, int n, const GridView& g,
+                                                float dmax2, int lane) {
+  const int k = lane >> 2, q = lane & 3;
   float best = dmax2;
   int bi = 0x7fffffff;
-  for (int i = lane; i < r.y; i += 32) {
-    const float d2 = dist2_to(__ldg(g.pts + r.x + i), px, py, pz);
-    if (d2 < best) {
-      best = d2;
-      bi = r.x + i;
+  if (k < n) {
+    const float* x = sc.seg + (k + 1) * 10;
+    const int2 r = cell_range(x[0], x[1], x[2], g);
+    for (int i = q; i < r.y; i += 4) {
+      const float d2 = dist2_to(__ldg(g.pts + r.x + i), x[0], x[1], x[2]);
+      if (d2 < best) {
+        best = d2;
+        bi = r.x + i;
+      }
     }
   }
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
+  for (int o = 1; o < 4; o <<= 1) {
     const float ob = __shfl_xor_sync(0xffffffffu, best, o);
     const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
     if (ob < best || (ob == best && oi < bi)) {
@@ -67,18 +76,19 @@ __device__ __forceinline__ float warp_nn(float px, float py, float pz, const Gri
       bi = oi;
     }
   }
-  if (bi != 0x7fffffff) nearest = __ldg(g.pts + bi);
-  return best;
+  if (k < n && q == 0) {
+    sc.d2[k] = best;
+    sc.nearest[k] = bi != 0x7fffffff ? __ldg(g.pts + bi) : make_float4(0.f, 0.f, 0.f, 0.f);
+  }
 }
 
 // Stage I state terms at the post-step state x against guide sample (gx, gy,
-// gz), the form the rollout kernels use.  grad: add the gradient to gs[10].
+// gz), given its nearest-point squared distance d2 and nearest point; the
+// form the rollout kernels use.  kGrad: the gradient into gs[10] (overwritten).
 template <bool kGrad>
 __device__ __forceinline__ float state_terms(const State& x, float gx, float gy, float gz,
-                                             const CostParams& cp, const GridView& grid,
-                                             float dmax2, int lane, float* gs) {
-  float4 nearest = make_float4(0.f, 0.f, 0.f, 0.f);
-  const float d2 = warp_nn(x.p[0], x.p[1], x.p[2], grid, dmax2, lane, nearest);
+                                             float d2, float4 nearest, const CostParams& cp,
+                                             float dmax2, float* gs) {
   const float ex = x.p[0] - gx, ey = x.p[1] - gy, ez = x.p[2] - gz;
   const float et = norm3f(ex, ey, ez);
   const float px = x.p[0] - cp.goal_rel[0], py = x.p[1] - cp.goal_rel[1], pz = x.p[2] - cp.goal_rel[2];
@@ -95,6 +105,8 @@ __device__ __forceinline__ float state_terms(const State& x, float gx, float gy,
   const float c = cp.Q_track * et + cp.Q_vnorm * (x.v[0] * x.v[0] + x.v[1] * x.v[1] + x.v[2] * x.v[2]) +
                   cp.Q_p * np + cp.Q_v * nv + cp.Q_q * 2.8284271247461903f * nr + jc;
   if (kGrad) {
+#pragma unroll
+    for (int i = 0; i < 10; ++i) gs[i] = 0.0f;
     if (et > 0.0f) {
       const float s = cp.Q_track / et;
       gs[0] += s * ex; gs[1] += s * ey; gs[2] += s * ez;
@@ -225,18 +237,41 @@ __device__ __forceinline__ void rk4_vjp(const float* x, float4 u, const DynParam
 // S(1) of the noise-free rollout of u (shared, T entries) from x0 and, with
 // kGrad, dS/du into g (shared, T entries).  guide: T x 3 (shared or global).
 // Called by all 32 lanes of one warp; returns S on every lane.
+//
+// Per 8-step segment: the serial RK4 steps (every lane, identical), the
+// segment's nearest-point queries side by side (four lanes per state), its
+// state terms side by side (one lane per state).  The backward pass
+// recomputes the segment from its checkpoint and runs only the serial
+// vector-Jacobian products in order.
 template <bool kGrad>
 __device__ float warp_cost_grad(const float4* u, float4* g, const float* guide, int T,
                                 const float* x0, const DynParams& dp, const CostParams& cp,
                                 const GridView& grid, AdjScratch& sc, int lane) {
   const float dmax2 = cp.d_max * cp.d_max;
+  const int nseg = (T + kCkpt - 1) / kCkpt;
   State x = state_load(x0);
   float S = 0.0f;
-  for (int j = 0; j < T; ++j) {
-    if (kGrad && (j % kCkpt) == 0 && lane == 0) state_store(sc.ck + (j / kCkpt) * 10, x);
-    rk4_step(x, u[j], dp);
-    S += state_terms<false>(x, guide[3 * j], guide[3 * j + 1], guide[3 * j + 2], cp, grid, dmax2,
-                            lane, nullptr);
+  for (int s = 0; s < nseg; ++s) {
+    const int j0 = s * kCkpt, n = min(T, j0 + kCkpt) - j0;
+    if (lane == 0) {
+      state_store(sc.ck + s * 10, x);
+      state_store(sc.seg, x);
+    }
+    for (int k = 0; k < n; ++k) {
+      rk4_step(x, u[j0 + k], dp);
+      if (lane == 0) state_store(sc.seg + (k + 1) * 10, x);
+    }
+    __syncwarp();
+    warp_nn_segment(sc, n, grid, dmax2, lane);
+    __syncwarp();
+    float c = 0.0f;
+    if (lane < n) {
+      const int j = j0 + lane;
+      c = state_terms<false>(state_load(sc.seg + (lane + 1) * 10), guide[3 * j], guide[3 * j + 1],
+                             guide[3 * j + 2], sc.d2[lane], sc.nearest[lane], cp, dmax2, nullptr);
+    }
+    S += warp_sum(c);
+    __syncwarp();
   }
   // J_ctrl: Q_c |u_t|^2 (t <= T-2) and Q_cd |u_t - u_{t-1}|^2 (1 <= t <= T-2)
   float jc = 0.0f;
@@ -252,28 +287,36 @@ __device__ float warp_cost_grad(const float4* u, float4* g, const float* guide, 
   S += warp_sum(jc);
   if (!kGrad) return S;
 
-  __syncwarp();
   float lam[10];
 #pragma unroll
   for (int i = 0; i < 10; ++i) lam[i] = 0.0f;
-  const int nseg = (T + kCkpt - 1) / kCkpt;
   for (int s = nseg - 1; s >= 0; --s) {
-    const int j0 = s * kCkpt, j1 = min(T, j0 + kCkpt);
+    const int j0 = s * kCkpt, n = min(T, j0 + kCkpt) - j0;
     // recompute the segment's states from its checkpoint
     State y = state_load(sc.ck + s * 10);
     if (lane == 0) state_store(sc.seg, y);
-    for (int j = j0; j < j1; ++j) {
-      rk4_step(y, u[j], dp);
-      if (lane == 0) state_store(sc.seg + (j - j0 + 1) * 10, y);
+    for (int k = 0; k < n; ++k) {
+      rk4_step(y, u[j0 + k], dp);
+      if (lane == 0) state_store(sc.seg + (k + 1) * 10, y);
     }
     __syncwarp();
-    for (int j = j1 - 1; j >= j0; --j) {
-      const State xn = state_load(sc.seg + (j - j0 + 1) * 10);
-      state_terms<true>(xn, guide[3 * j], guide[3 * j + 1], guide[3 * j + 2], cp, grid, dmax2, lane,
-                        lam);
+    warp_nn_segment(sc, n, grid, dmax2, lane);
+    __syncwarp();
+    if (lane < n) {
+      const int j = j0 + lane;
+      float gs[10];
+      state_terms<true>(state_load(sc.seg + (lane + 1) * 10), guide[3 * j], guide[3 * j + 1],
+                        guide[3 * j + 2], sc.d2[lane], sc.nearest[lane], cp, dmax2, gs);
+#pragma unroll
+      for (int i = 0; i < 10; ++i) sc.gs[lane][i] = gs[i];
+    }
+    __syncwarp();
+    for (int k = n - 1; k >= 0; --k) {
+#pragma unroll
+      for (int i = 0; i < 10; ++i) lam[i] += sc.gs[k][i];
       float gu[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-      rk4_vjp(sc.seg + (j - j0) * 10, u[j], dp, lam, gu);
-      if (lane == 0) g[j] = make_float4(gu[0], gu[1], gu[2], gu[3]);
+      rk4_vjp(sc.seg + k * 10, u[j0 + k], dp, lam, gu);
+      if (lane == 0) g[j0 + k] = make_float4(gu[0], gu[1], gu[2], gu[3]);
     }
     __syncwarp();
   }

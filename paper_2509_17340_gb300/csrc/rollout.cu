@@ -402,7 +402,7 @@ constexpr int UT = 128;
 __device__ __forceinline__ void update_unit(const UpdateArgs& a, int e, bool final_stage) {
   __shared__ float s_scale[1024];
   __shared__ float s_red[UT / 32];
-  __shared__ float s_x[(kMaxT + 1) * 10];
+  __shared__ __align__(16) float s_x[(kMaxT + 1) * 10];  // also the refinement's AdjScratch
   __shared__ float4 s_u4[kMaxT];
   float* s_u = reinterpret_cast<float*>(s_u4);
   __shared__ float s_c[kMaxT];
@@ -662,6 +662,9 @@ __global__ void __launch_bounds__(UT) k_b_update(BatchView v, int it) {
     __syncthreads();
   }
 }
+
+static_assert(sizeof(AdjScratch) <= sizeof(float) * (kMaxT + 1) * 10,
+              "the update kernel's Stage II state array holds the refinement scratch");
 
 // One warp per control sequence: S(1) of its noise-free rollout and dS/dU.
 constexpr int kCgWarps = 4;
