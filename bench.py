@@ -42,7 +42,8 @@ METRIC = "rollout-steps/s (anchor-guided ensemble plan step)"
 METRICS = {"ensemble": METRIC, "large": "rollout-steps/s (large-clutter ensemble plan step)",
            "plain": "rollout-steps/s (plain single-MPPI plan step)",
            "batched": "rollout-steps/s (64 independent planners in one batched call)",
-           "refined": "rollout-steps/s (ensemble plan step with 5 gradient-refinement steps)"}
+           "refined": "rollout-steps/s (ensemble plan step with 5 gradient-refinement steps)",
+           "accumulate": "points/s (LiDAR frame push + 10-frame gather)"}
 UNIT = "rollout-steps/s"
 CPU_SAMPLE_SECONDS = 15.0
 
@@ -290,6 +291,103 @@ def cpu_baseline(w, P) -> dict:
                       f"{tot:.1f} s)", "host": host_cores()}
 
 
+# --------------------------------------------------------------------------- accumulation
+
+def run_accumulate(args, rank: int, world: int, local: int):
+    """Sec. IV-A.1 accumulation: per step one 20k-point sensor-frame sweep is
+    pushed into a 10-frame ring (transform by its capture pose) and the 10 live
+    frames (200k points) are gathered compacted in world coordinates."""
+    import torch
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    from paper_2509_17340_gb300 import build
+    build.build()
+    from paper_2509_17340_gb300 import aero
+    F, N = 10, 20000
+    rng = np.random.default_rng(1 + rank_seed(rank))
+    dev = torch.device("cuda", local)
+    frames = []
+    for f in range(16):
+        pts = torch.from_numpy(rng.normal(0, 8, (N, 3)).astype(np.float32)).to(dev)
+        q = rng.normal(size=4)
+        frames.append((pts, rng.normal(0, 2, 3), q / np.linalg.norm(q)))
+    acc = aero.Accumulator(F, N)
+    dst = torch.empty((F * N, 3), device=dev)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    for f in range(F):
+        acc.push(frames[f][0], frames[f][1], frames[f][2])
+    for s in range(args.warmup):
+        acc.push(*frames[s % 16])
+        acc.gather(dst)
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    if dist:
+        dist.barrier()
+    with ClockSampler(local) as clk:
+        for i in range(args.steps):
+            flush.fill_(float(i))
+            ev[i][0].record(stream)
+            acc.push(*frames[i % 16])
+            n = acc.gather(dst)
+            ev[i][1].record(stream)
+        torch.cuda.synchronize()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = max_over_ranks(sum(step_ms), dist, dev)
+    units = N + F * N
+    # end to end: the sweep copied from pinned host memory, the gathered cloud read back
+    h_pts = [f[0].cpu().pin_memory() for f in frames]
+    h_out = torch.empty((F * N, 3)).pin_memory()
+    d_in = torch.empty((N, 3), device=dev)
+    times = []
+    for i in range(args.warmup + max(10, args.steps // 4)):
+        stream.synchronize()
+        t0 = time.perf_counter()
+        d_in.copy_(h_pts[i % 16], non_blocking=True)
+        acc.push(d_in, frames[i % 16][1], frames[i % 16][2])
+        n = acc.gather(dst)
+        h_out[:n].copy_(dst[:n], non_blocking=True)
+        stream.synchronize()
+        if i >= args.warmup:
+            times.append(time.perf_counter() - t0)
+    e_tot = max_over_ranks(sum(times), dist, dev)
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+    avg_s = total_ms / args.steps / 1e3
+    bytes_step = 24 * units      # push: 12 B read + 12 B written per slot point; gather: 12 + 12 per point
+    peaks = measured_peaks()
+    peak = float(peaks.get("hbm_gbs", 6800.0))
+    line = {
+        "metric": METRIC, "value": world * units * args.steps / (total_ms / 1e3), "unit": "points/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": total_ms / args.steps, "ms_per_step_median": statistics.median(step_ms),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": f"accumulate: {F} frames x {N} points, push one frame + gather all",
+                   "l2": "flushed between timed steps (512 MB write)"},
+        "roofline": {"kernel": "k_accum_push + k_accum_gather", "bound": "hbm",
+                     "achieved": bytes_step / avg_s / 1e9, "peak": peak, "unit": "GB/s",
+                     "frac": bytes_step / avg_s / 1e9 / peak, "traffic": None,
+                     "bytes_per_step": bytes_step,
+                     "peak_note": "measured copy bandwidth" if "hbm_gbs" in peaks else "fallback"},
+        "clocks": clk.summary(),
+        "e2e": {"value": world * units * len(times) / e_tot, "unit": "points/s",
+                "h2d_bytes_per_step": 12 * N, "d2h_bytes_per_step": 12 * F * N,
+                "ms_per_step": 1e3 * e_tot / len(times)},
+        "gpu_launches": 2 * args.steps,
+    }
+    print(json.dumps(line), flush=True)
+    acc.close()
+    if dist:
+        dist.destroy_process_group()
+
+
 # --------------------------------------------------------------------------- batched planners
 
 def run_batched(args, rank: int, world: int, local: int):
@@ -469,6 +567,9 @@ def main():
         return
     if WORKLOAD == "batched":
         run_batched(args, rank, world, local)
+        return
+    if WORKLOAD == "accumulate":
+        run_accumulate(args, rank, world, local)
         return
 
     import torch

@@ -313,6 +313,43 @@ size_t aero_debug_size(aero_planner_t* planner, int32_t what);
 int aero_cost_grad(aero_planner_t* planner, int32_t instance, const float* U, int32_t n,
                    float* S_out, float* dSdU_out, void* stream);
 
+/* ---- multi-sweep accumulation (Sec. IV-A.1) ------------------------------
+ * The partition of a step sees the most recent LiDAR frames, each taken from
+ * its own pose and brought into common coordinates with the transforms of state
+ * estimation (the paper accumulates 10 frames, about 200,000 points).  An
+ * accumulator keeps a ring of `frames` slots of `points_per_frame` points on
+ * the device, in world coordinates (float x, y, z per point):
+ *  - aero_accum_push transforms a frame's sensor-frame points p_s (device, n x 3,
+ *    n <= points_per_frame) by the capture pose (p, q): p_w = p + R(q) p_s with
+ *    q normalised and R(q) in binary32, into the oldest slot, and fills the
+ *    slot's remaining points with NaN;
+ *  - aero_accum_view returns the ring itself (frames x points_per_frame points):
+ *    a valid cloud for aero_plan_step, whose partition drops the NaN padding;
+ *  - aero_accum_gather writes the live frames' points, oldest frame first and
+ *    in push order within a frame, compacted into dst (device, capacity points
+ *    x 3): in world coordinates when p0 and q0 are NULL, else projected into the
+ *    body frame R(q0)^T (p_w - p0) (host p0[3], q0[4]); *n_out gets the count.
+ * All work is enqueued on `stream`; the caller orders pushes and readers.
+ * Errors: INVALID_ARG (sizes, a zero quaternion, capacity), NOT_DEVICE_PTR,
+ * ALLOC, CUDA. */
+typedef struct aero_accum aero_accum_t;
+int aero_accum_create(int32_t frames, int64_t points_per_frame, aero_accum_t** out);
+int aero_accum_push(aero_accum_t* acc, const float* pts_sensor, int64_t n, const float pose_p[3],
+                    const float pose_q[4], void* stream);
+int aero_accum_view(aero_accum_t* acc, const float** cloud, int64_t* n_points, int64_t* n_valid);
+int aero_accum_gather(aero_accum_t* acc, const float* p0, const float* q0, float* dst,
+                      int64_t dst_capacity, int64_t* n_out, void* stream);
+int aero_accum_reset(aero_accum_t* acc, void* stream);  /* forget every frame */
+int aero_accum_destroy(aero_accum_t* acc);
+
+/* Receding-horizon warm start: after `shift` executed steps, every instance's
+ * nominal moves forward, u[e][j] = u[e][min(j + shift, T - 1)] (the last control
+ * repeated).  u_nom: device E x T x 4, in place; scratch: device, E x T x 4
+ * floats the call may overwrite.  Enqueued on `stream`.  Errors: INVALID_ARG,
+ * NOT_DEVICE_PTR, CUDA. */
+int aero_shift_nominal(float* u_nom, int32_t E, int32_t T, int32_t shift, float* scratch,
+                       void* stream);
+
 /* Copy debug buffer `what` of the last step into dst (host or device), at most
  * `bytes` bytes, ordered on `stream` (asynchronous for device dst and pinned
  * host dst).  Errors: INVALID_ARG (unknown id, no step yet, bytes too small). */

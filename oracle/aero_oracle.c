@@ -740,6 +740,30 @@ void orc_refine(const double x0[10], double* u, const double* guide, const doubl
   free(G);
 }
 
+/* ======================================================================
+ * Multi-sweep accumulation (Sec. IV-A.1): a frame's sensor-frame points
+ * brought into world coordinates by the capture pose, p_w = p + R(q/|q|) p_s;
+ * and the projection of world points into a body frame, R(q0)^T (p_w - p0).
+ * ====================================================================== */
+void orc_accumulate(const double* ps, int64_t n, const double p[3], const double q[4], double* pw) {
+  double nq = sqrt(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
+  double qu[4] = {q[0] / nq, q[1] / nq, q[2] / nq, q[3] / nq}, R[9];
+  orc_rotation(qu, R);
+  for (int64_t i = 0; i < n; ++i)
+    for (int r = 0; r < 3; ++r)
+      pw[3 * i + r] = p[r] + R[3 * r] * ps[3 * i] + R[3 * r + 1] * ps[3 * i + 1] + R[3 * r + 2] * ps[3 * i + 2];
+}
+
+void orc_project(const double* pw, int64_t n, const double p0[3], const double q0[4], double* pb) {
+  double nq = sqrt(q0[0] * q0[0] + q0[1] * q0[1] + q0[2] * q0[2] + q0[3] * q0[3]);
+  double qu[4] = {q0[0] / nq, q0[1] / nq, q0[2] / nq, q0[3] / nq}, R[9];
+  orc_rotation(qu, R);
+  for (int64_t i = 0; i < n; ++i) {
+    double d[3] = {pw[3 * i] - p0[0], pw[3 * i + 1] - p0[1], pw[3 * i + 2] - p0[2]};
+    for (int c = 0; c < 3; ++c) pb[3 * i + c] = R[c] * d[0] + R[3 + c] * d[1] + R[6 + c] * d[2];
+  }
+}
+
 /* Eq. mppi_weights and Eq. mppi_update_simplified for one instance:
  * rho = min S, eta = sum exp(-(S-rho)/lam), eps_k = exp(-(S_k-rho)/lam)/eta,
  * u_nom += sum_k eps_k du^k.  dU is K x (T*4). */

@@ -299,6 +299,22 @@ def refine(x0, U, guide_, goal, pts, P: dict) -> np.ndarray:
     return U
 
 
+def accumulate(ps, p, q) -> np.ndarray:
+    """World coordinates p + R(q/|q|) p_s of a frame's sensor-frame points."""
+    ps = _f64(ps).reshape(-1, 3)
+    out = np.zeros_like(ps)
+    lib().orc_accumulate(_p(ps), C.c_int64(len(ps)), _p(_f64(p)), _p(_f64(q)), _p(out))
+    return out
+
+
+def project(pw, p0, q0) -> np.ndarray:
+    """Body-frame coordinates R(q0/|q0|)^T (p_w - p0)."""
+    pw = _f64(pw).reshape(-1, 3)
+    out = np.zeros_like(pw)
+    lib().orc_project(_p(pw), C.c_int64(len(pw)), _p(_f64(p0)), _p(_f64(q0)), _p(out))
+    return out
+
+
 def mppi_update(S, dU, lam, u_nom) -> tuple[np.ndarray, np.ndarray]:
     S = _f64(S)
     K = len(S)

@@ -109,6 +109,14 @@ _lib.aero_batch_sync_status.argtypes = [_vp, C.POINTER(C.c_int32)]
 _lib.aero_batch_debug_size.argtypes = [_vp, C.c_int32, C.c_int32]
 _lib.aero_batch_debug_size.restype = C.c_size_t
 _lib.aero_batch_get_debug.argtypes = [_vp, C.c_int32, C.c_int32, _vp, C.c_size_t, _vp]
+_lib.aero_accum_create.argtypes = [C.c_int32, C.c_int64, C.POINTER(_vp)]
+_lib.aero_accum_push.argtypes = [_vp, _vp, C.c_int64, C.POINTER(C.c_float), C.POINTER(C.c_float), _vp]
+_lib.aero_accum_view.argtypes = [_vp, C.POINTER(_vp), C.POINTER(C.c_int64), C.POINTER(C.c_int64)]
+_lib.aero_accum_gather.argtypes = [_vp, C.POINTER(C.c_float), C.POINTER(C.c_float), _vp, C.c_int64,
+                                   C.POINTER(C.c_int64), _vp]
+_lib.aero_accum_reset.argtypes = [_vp, _vp]
+_lib.aero_accum_destroy.argtypes = [_vp]
+_lib.aero_shift_nominal.argtypes = [_vp, C.c_int32, C.c_int32, C.c_int32, _vp, _vp]
 _lib.aero_status_str.argtypes = [C.c_int]
 _lib.aero_status_str.restype = C.c_char_p
 
@@ -175,7 +183,17 @@ def _stream_ptr(stream) -> int:
     return stream.cuda_stream
 
 
-def _dev(t: torch.Tensor, dtype, name: str) -> int:
+class RawCloud:
+    """A device cloud owned by the library (an accumulator's ring): pointer and
+    point count, accepted wherever a cloud tensor is."""
+
+    def __init__(self, ptr: int, n: int, owner=None):
+        self.ptr, self.shape, self.owner = int(ptr), (int(n), 3), owner
+
+
+def _dev(t, dtype, name: str) -> int:
+    if isinstance(t, RawCloud) and dtype == torch.float32:
+        return t.ptr
     if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == dtype and t.is_contiguous()):
         raise TypeError(f"{name} must be a contiguous CUDA {dtype} tensor")
     return t.data_ptr()
@@ -420,6 +438,69 @@ class Batch:
                "aero_batch_get_debug")
         torch.cuda.synchronize()
         return buf
+
+
+def shift_nominal(u_nom: torch.Tensor, shift: int, scratch: torch.Tensor | None = None,
+                  stream=None) -> None:
+    """Receding-horizon warm start in place (``aero_shift_nominal``): u_nom
+    (E x T x 4 CUDA tensor) advanced by `shift` steps, the last control repeated."""
+    E, T = u_nom.shape[0], u_nom.shape[1]
+    if scratch is None:
+        scratch = torch.empty_like(u_nom)
+    _check(_lib.aero_shift_nominal(_dev(u_nom, torch.float32, "u_nom"), E, T, int(shift),
+                                   _dev(scratch, torch.float32, "scratch"), _stream_ptr(stream)),
+           "aero_shift_nominal")
+
+
+class Accumulator:
+    """Ring of LiDAR frames in world coordinates on the device (``aero_accum_*``,
+    Sec. IV-A.1): push sensor-frame sweeps with their capture poses; plan on
+    ``view()`` (the NaN-padded ring) or on a compacted ``gather``."""
+
+    def __init__(self, frames: int = 10, points_per_frame: int = 20000):
+        torch.cuda.init()
+        h = _vp()
+        _check(_lib.aero_accum_create(frames, points_per_frame, C.byref(h)), "aero_accum_create")
+        self._h = h
+        self.frames, self.points_per_frame = frames, points_per_frame
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.aero_accum_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def push(self, pts: torch.Tensor, p, q, stream=None) -> None:
+        n = pts.shape[0]
+        pp = (C.c_float * 3)(*[float(x) for x in p])
+        qq = (C.c_float * 4)(*[float(x) for x in q])
+        _check(_lib.aero_accum_push(self._h, _dev(pts, torch.float32, "pts") if n else None, n, pp, qq,
+                                    _stream_ptr(stream)), "aero_accum_push")
+
+    def view(self) -> tuple[RawCloud, int]:
+        """The ring as a cloud (frames x points_per_frame points) and the number
+        of real (non-padding) points in it."""
+        ptr, n, v = _vp(), C.c_int64(), C.c_int64()
+        _check(_lib.aero_accum_view(self._h, C.byref(ptr), C.byref(n), C.byref(v)), "aero_accum_view")
+        return RawCloud(ptr.value, n.value, self), v.value
+
+    def gather(self, dst: torch.Tensor, p0=None, q0=None, stream=None) -> int:
+        """Live frames, oldest first, compacted into dst (world, or the body
+        frame of (p0, q0)); returns the number of points written."""
+        n = C.c_int64()
+        pp = (C.c_float * 3)(*[float(x) for x in p0]) if p0 is not None else None
+        qq = (C.c_float * 4)(*[float(x) for x in q0]) if q0 is not None else None
+        _check(_lib.aero_accum_gather(self._h, pp, qq, _dev(dst, torch.float32, "dst"), dst.shape[0],
+                                      C.byref(n), _stream_ptr(stream)), "aero_accum_gather")
+        return n.value
+
+    def reset(self, stream=None) -> None:
+        _check(_lib.aero_accum_reset(self._h, _stream_ptr(stream)), "aero_accum_reset")
 
 
 class RolloutCost(torch.autograd.Function):

@@ -18,8 +18,8 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libaero_mppi.so")
-SOURCES = ["aero_mppi.cu", "partition.cu", "rollout.cu"]
-HEADERS = ["internal.h", "device.cuh"]
+SOURCES = ["aero_mppi.cu", "partition.cu", "rollout.cu", "accum.cu"]
+HEADERS = ["internal.h", "device.cuh", "adjoint.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -163,6 +163,32 @@ def _hit_spheres(o, d, spheres, t_best):
         np.minimum(t_best, np.where(ok, t, np.inf), out=t_best)
 
 
+def scene_distance(scene: Scene, p) -> np.ndarray:
+    """Exact distance from points p (M x 3) to the scene's solid primitives
+    (cylinders, boxes, spheres, the ground half-space z <= 0) and surfaces
+    (rectangles); zero inside a solid.  Clearance of a simulated flight."""
+    p = np.atleast_2d(np.asarray(p, np.float64))
+    d = np.full(len(p), np.inf)
+    for (cx, cy, r, z0, z1) in scene.cylinders:
+        dr = np.maximum(np.hypot(p[:, 0] - cx, p[:, 1] - cy) - r, 0.0)
+        dz = np.maximum(np.maximum(z0 - p[:, 2], p[:, 2] - z1), 0.0)
+        np.minimum(d, np.hypot(dr, dz), out=d)
+    if scene.ground:
+        np.minimum(d, np.maximum(p[:, 2], 0.0), out=d)
+    for lo, hi in scene.boxes:
+        e = np.maximum(np.maximum(np.asarray(lo) - p, p - np.asarray(hi)), 0.0)
+        np.minimum(d, np.linalg.norm(e, axis=1), out=d)
+    for (c, a1, a2, s1, s2) in scene.rects:
+        c, a1, a2 = (np.asarray(v, dtype=np.float64) for v in (c, a1, a2))
+        h = p - c
+        u, v, w = h @ a1, h @ a2, h @ np.cross(a1, a2)
+        du, dv = u - np.clip(u, -s1, s1), v - np.clip(v, -s2, s2)
+        np.minimum(d, np.sqrt(du * du + dv * dv + w * w), out=d)
+    for c, r in scene.spheres:
+        np.minimum(d, np.maximum(np.linalg.norm(p - np.asarray(c), axis=1) - r, 0.0), out=d)
+    return d
+
+
 def lidar_sweep(scene: Scene, origin, n_az: int, n_el: int, el_min_deg: float,
                 el_max_deg: float, max_range: float, range_sigma: float,
                 rng: np.random.Generator, chunk: int = 8192) -> np.ndarray:
