@@ -10,6 +10,17 @@
 namespace aero {
 
 // ---------------------------------------------------------------------------
+// Programmatic dependent launch (sm_90 and later).  pdl_start lets the next
+// kernel of the stream be scheduled now, then waits until this kernel's
+// predecessor has completed and its writes are visible.  Both instructions are
+// no-ops for a kernel launched without programmatic stream serialization.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void pdl_start() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+
+// ---------------------------------------------------------------------------
 // Philox4x32-10 (Salmon et al., SC'11): ten rounds of two 32x32 multiplies;
 // the key is bumped by the Weyl constants before every round but the first.
 // ---------------------------------------------------------------------------

@@ -101,6 +101,7 @@ __device__ __forceinline__ void partition_point(const PartitionArgs& a, const Sm
 }
 
 __global__ void __launch_bounds__(256) k_partition(PartitionArgs a, PartTables t) {
+  pdl_start();
   __shared__ SmemTables st;
   load_tables(t, a.A, a.El, st);
   __syncthreads();
@@ -291,6 +292,7 @@ __device__ bool scan_tile(int* count, int* fill, int* local, int* tile_sum, int*
 __global__ void __launch_bounds__(kScanThreads) k_grid_scan(int* count, int* fill, int* local,
                                                             int* tile_sum, int* tile_off, int ncells,
                                                             int ntiles, unsigned int* counter) {
+  pdl_start();
   scan_tile(count, fill, local, tile_sum, tile_off, ncells, ntiles, blockIdx.x, counter);
 }
 
@@ -427,6 +429,7 @@ __device__ void coarse_guides_block(const GuideArgs& a, const PartTables& t, int
 // the coarse argmax, goal cone, anchors and guides (they need only the keys).
 __global__ void __launch_bounds__(256) k_grid_count(CandArgs ca, GuideArgs ga, PartTables t,
                                                     int count_blocks) {
+  pdl_start();
   if ((int)blockIdx.x < count_blocks)
     cand_pass<false>(ca, blockIdx.x, count_blocks);
   else
@@ -445,6 +448,7 @@ __device__ __forceinline__ void range_cell(const int* local, const int* tile_off
 // every cell (which needs only the scan).
 __global__ void __launch_bounds__(256) k_grid_scatter(CandArgs ca, int scatter_blocks,
                                                       int2* __restrict__ range, int ncells) {
+  pdl_start();
   if ((int)blockIdx.x < scatter_blocks) {
     cand_pass<true>(ca, blockIdx.x, scatter_blocks);
     return;
@@ -474,6 +478,7 @@ __device__ __forceinline__ void share_of(long long total, long long w, long long
 }
 
 __global__ void __launch_bounds__(256) k_b_partition(BatchView v) {
+  pdl_start();
   __shared__ long long s_pre[kBatchMax + 1];
   __shared__ SmemTables st;
   __shared__ PartitionArgs s_pa;
@@ -526,6 +531,7 @@ __device__ __forceinline__ void cand_tasks(const BatchView& v, const long long* 
 
 // Count tasks, then the coarse cells (one warp each).
 __global__ void __launch_bounds__(256) k_b_count(BatchView v) {
+  pdl_start();
   __shared__ long long s_pi[kBatchMax + 1], s_pc[kBatchMax + 1];
   const int n = v.n;
   load_prefix(s_pi, v.pre + kPreItems * (n + 1), n);
@@ -543,6 +549,7 @@ __global__ void __launch_bounds__(256) k_b_count(BatchView v) {
 
 // Units [0, n): goal cone, anchors and guides of planner u; then the scan tiles.
 __global__ void __launch_bounds__(kScanThreads) k_b_scan(BatchView v) {
+  pdl_start();
   __shared__ long long s_pre[kBatchMax + 1];
   __shared__ SmemTables st;
   __shared__ GuideArgs s_ga;
@@ -572,6 +579,7 @@ __global__ void __launch_bounds__(kScanThreads) k_b_scan(BatchView v) {
 // keys of planners whose collision set is every kept point (read only by the
 // coarse pass, so emptied here).
 __global__ void __launch_bounds__(256) k_b_scatter(BatchView v) {
+  pdl_start();
   __shared__ long long s_pi[kBatchMax + 1], s_pc[kBatchMax + 1];
   const int n = v.n;
   load_prefix(s_pi, v.pre + kPreItems * (n + 1), n);
@@ -613,22 +621,21 @@ cudaError_t launch_grid_count(const CandArgs& ca, const GuideArgs& ga, const Par
                               cudaStream_t s) {
   const int count_blocks = ca.n_items > 0 ? blocks_for(ca.n_items * 32, 256, 152 * 32) : 0;
   const int coarse_blocks = (ga.Ac * ga.Ec + 7) / 8;  // 8 warps per block
-  k_grid_count<<<count_blocks + coarse_blocks, 256, 0, s>>>(ca, ga, t, count_blocks);
-  return cudaGetLastError();
+  return launch_k(k_grid_count, dim3(count_blocks + coarse_blocks), dim3(256), s, true, ca, ga, t,
+                  count_blocks);
 }
 
 cudaError_t launch_grid_scan(int* count, int* fill, int* local, int* tile_sum, int* tile_off,
                              int ncells, int ntiles, unsigned int* counter, cudaStream_t s) {
-  k_grid_scan<<<ntiles, kScanThreads, 0, s>>>(count, fill, local, tile_sum, tile_off, ncells, ntiles,
-                                               counter);
-  return cudaGetLastError();
+  return launch_k(k_grid_scan, dim3(ntiles), dim3(kScanThreads), s, true, count, fill, local, tile_sum,
+                  tile_off, ncells, ntiles, counter);
 }
 
 cudaError_t launch_grid_scatter(const CandArgs& ca, int2* range, int ncells, cudaStream_t s) {
   const int scatter_blocks = ca.n_items > 0 ? blocks_for(ca.n_items * 32, 256, 152 * 32) : 0;
   const int range_blocks = (ncells + 255) / 256;
-  k_grid_scatter<<<scatter_blocks + range_blocks, 256, 0, s>>>(ca, scatter_blocks, range, ncells);
-  return cudaGetLastError();
+  return launch_k(k_grid_scatter, dim3(scatter_blocks + range_blocks), dim3(256), s, true, ca,
+                  scatter_blocks, range, ncells);
 }
 
 cudaError_t batch_grid_occupancy(int out[4]) {
@@ -648,18 +655,15 @@ cudaError_t launch_batch_partition(const BatchView& v, int blocks, cudaStream_t 
 }
 
 cudaError_t launch_batch_count(const BatchView& v, int blocks, cudaStream_t s) {
-  k_b_count<<<blocks, 256, 0, s>>>(v);
-  return cudaGetLastError();
+  return launch_k(k_b_count, dim3(blocks), dim3(256), s, true, v);
 }
 
 cudaError_t launch_batch_scan(const BatchView& v, int blocks, cudaStream_t s) {
-  k_b_scan<<<blocks, kScanThreads, 0, s>>>(v);
-  return cudaGetLastError();
+  return launch_k(k_b_scan, dim3(blocks), dim3(kScanThreads), s, true, v);
 }
 
 cudaError_t launch_batch_scatter(const BatchView& v, int blocks, cudaStream_t s) {
-  k_b_scatter<<<blocks, 256, 0, s>>>(v);
-  return cudaGetLastError();
+  return launch_k(k_b_scatter, dim3(blocks), dim3(256), s, true, v);
 }
 
 cudaError_t launch_philox(uint32_t k0, uint32_t k1, uint32_t c1, uint32_t c2, uint32_t c3,

@@ -563,10 +563,12 @@ __device__ __forceinline__ void update_unit(const UpdateArgs& a, int e, bool fin
 }
 
 __global__ void __launch_bounds__(NT) k_rollout(RolloutArgs a) {
+  pdl_start();
   rollout_unit(a, blockIdx.y, blockIdx.x, a.ctr3);
 }
 
 __global__ void __launch_bounds__(NT) k_rollout_quad(RolloutArgs a) {
+  pdl_start();
   rollout_quad_unit(a, blockIdx.y, blockIdx.x, a.ctr3);
 }
 
@@ -575,6 +577,7 @@ __global__ void __launch_bounds__(NT) k_rollout_quad(RolloutArgs a) {
 // then agree bit for bit; from kernel parameters the compiler contracts some
 // products differently).
 __global__ void __launch_bounds__(UT) k_update(UpdateArgs a) {
+  pdl_start();
   __shared__ UpdateArgs s_a;
   block_copy_param(&s_a, &a);
   __syncthreads();
@@ -590,6 +593,7 @@ __global__ void __launch_bounds__(UT) k_update(UpdateArgs a) {
 // ---------------------------------------------------------------------------
 template <int kLanes, int kMinCtas>
 __global__ void __launch_bounds__(NT, kMinCtas) k_b_rollout(BatchView v, int it, int dynamic) {
+  pdl_start();
   __shared__ long long s_pre[kBatchMax + 1];
   __shared__ int s_order[kBatchMax];
   __shared__ RolloutArgs s_a;
@@ -642,6 +646,7 @@ __global__ void __launch_bounds__(NT, kMinCtas) k_b_rollout(BatchView v, int it,
 // Batched merge and update: units (planner, instance); the last iteration of a
 // planner runs its Stage II and selection.
 __global__ void __launch_bounds__(UT) k_b_update(BatchView v, int it) {
+  pdl_start();
   __shared__ long long s_pre[kBatchMax + 1];
   __shared__ UpdateArgs s_a;
   __shared__ int s_iters;
@@ -712,32 +717,23 @@ cudaError_t batch_rollout_occupancy(int out[4]) {
 
 cudaError_t launch_batch_rollout(const BatchView& v, int lanes, int it, int blocks, int dynamic,
                                  int six, cudaStream_t s) {
-  if (lanes == 4)
-    k_b_rollout<4, 4><<<blocks, NT, 0, s>>>(v, it, dynamic);
-  else if (six)
-    k_b_rollout<1, 6><<<blocks, NT, 0, s>>>(v, it, dynamic);
-  else
-    k_b_rollout<1, 5><<<blocks, NT, 0, s>>>(v, it, dynamic);
-  return cudaGetLastError();
+  if (lanes == 4) return launch_k(k_b_rollout<4, 4>, dim3(blocks), dim3(NT), s, true, v, it, dynamic);
+  if (six) return launch_k(k_b_rollout<1, 6>, dim3(blocks), dim3(NT), s, true, v, it, dynamic);
+  return launch_k(k_b_rollout<1, 5>, dim3(blocks), dim3(NT), s, true, v, it, dynamic);
 }
 
 cudaError_t launch_batch_update(const BatchView& v, int it, int blocks, cudaStream_t s) {
-  k_b_update<<<blocks, UT, 0, s>>>(v, it);
-  return cudaGetLastError();
+  return launch_k(k_b_update, dim3(blocks), dim3(UT), s, true, v, it);
 }
 
 cudaError_t launch_rollout(const RolloutArgs& a, cudaStream_t s) {
   dim3 grid(a.nb, a.E);
-  if (a.lanes_per_sample == 4)
-    k_rollout_quad<<<grid, NT, 0, s>>>(a);
-  else
-    k_rollout<<<grid, NT, 0, s>>>(a);
-  return cudaGetLastError();
+  if (a.lanes_per_sample == 4) return launch_k(k_rollout_quad, grid, dim3(NT), s, true, a);
+  return launch_k(k_rollout, grid, dim3(NT), s, true, a);
 }
 
 cudaError_t launch_update(const UpdateArgs& a, cudaStream_t s) {
-  k_update<<<a.E, UT, 0, s>>>(a);
-  return cudaGetLastError();
+  return launch_k(k_update, dim3(a.E), dim3(UT), s, true, a);
 }
 
 }  // namespace aero
