@@ -858,7 +858,7 @@ const char* aero_status_str(int status) {
 // so such callers use aero_plan_step_noalloc instead: its workspace is carved
 // from g_noalloc_scratch, a file-scope device array that the CUDA loader sets
 // up with the module and that every GPU loading this library keeps until the
-// process exits.  Its size is fixed by the kNa* limits below (about 5.3 MB).
+// process exits.  Its size is fixed by the kNa* limits below (about 6.5 MB).
 // ---------------------------------------------------------------------------
 namespace {
 
