@@ -48,13 +48,31 @@ __device__ __forceinline__ float uniform01(uint32_t w) {
 __device__ __forceinline__ float fast_sqrt(float x) { return x > 0.0f ? x * rsqrtf(x) : 0.0f; }
 
 // Four standard normals from one Philox block (Box-Muller on (u0,u1), (u2,u3)).
+// ln u for u in (0, 1): CUDA's hardware base-2 logarithm (absolute error
+// about 2^-22 on [0.5, 2]) times ln 2; near 1, where that absolute error would
+// dominate the small Box-Muller radius, the series -(v + v^2/2 + v^3/3 + v^4/4)
+// of ln(1 - v) with v = 1 - u exact (remainder below v^5/5 < 2e-13).
+__device__ __forceinline__ float log_unit(float u) {
+  const float v = 1.0f - u;
+  if (v < 4e-3f) return -v * fmaf(v, fmaf(v, fmaf(v, 0.25f, 1.0f / 3.0f), 0.5f), 1.0f);
+  return __log2f(u) * 0.693147180559945309f;
+}
+
+// Box-Muller on two uniforms: r (cos 2 pi u2, sin 2 pi u2), r = sqrt(-2 ln u1).
+// The angle is taken as 2 pi (u2 - 1/2) in [-pi, pi], where CUDA's hardware
+// sine and cosine have an absolute error of about 2^-21.4; with |r| <= 5.8 and
+// the radius error of log_unit the normals are within 5e-6 of their
+// correctly rounded values.
+__device__ __forceinline__ float2 box_muller(uint32_t w1, uint32_t w2) {
+  const float r = fast_sqrt(-2.0f * log_unit(uniform01(w1)));
+  float s, c;
+  __sincosf((uniform01(w2) - 0.5f) * 6.28318530717958648f, &s, &c);
+  return make_float2(-r * c, -r * s);  // cos(t + pi) = -cos t, sin(t + pi) = -sin t
+}
+
 __device__ __forceinline__ float4 normals4(uint4 w) {
-  const float ra = fast_sqrt(-2.0f * logf(uniform01(w.x)));
-  const float rb = fast_sqrt(-2.0f * logf(uniform01(w.z)));
-  float sa, ca, sb, cb;
-  sincospif(2.0f * uniform01(w.y), &sa, &ca);
-  sincospif(2.0f * uniform01(w.w), &sb, &cb);
-  return make_float4(ra * ca, ra * sa, rb * cb, rb * sb);
+  const float2 a = box_muller(w.x, w.y), b = box_muller(w.z, w.w);
+  return make_float4(a.x, a.y, b.x, b.y);
 }
 
 // Perturbation delta for sample k, step j, instance e (Sec. III-B).
