@@ -58,7 +58,9 @@ extern "C" {
 /* ---- debug buffers (aero_get_debug) ------------------------------------
  * Positions in debug buffers are relative to the start position p0 of the
  * last step (world axes), as the kernels keep them. */
-#define AERO_DBG_FINE_KEYS 0     /* uint64 [fine_el][fine_az]: (bits(r^2 f32) << 32) | point index;
+#define AERO_DBG_FINE_KEYS 0     /* uint64 [fine_el][fine_az]: (bits(r^2 f32) << 32) | point index
+                                    (kept by planners created with debug_samples_max > 0: the
+                                    others empty their keys during the step, saving a fill);
                                     0xFFFFFFFFFFFFFFFF = empty cone */
 #define AERO_DBG_COARSE_WIN 1    /* int32 [E_c][A_c]: winning fine cell j*fine_az+i of each coarse cell */
 #define AERO_DBG_GOAL_CELL 2     /* int32 [1]: fine cell of the goal direction */

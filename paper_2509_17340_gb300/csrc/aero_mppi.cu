@@ -463,9 +463,17 @@ int enqueue_step(aero_planner* pl, const aero_state_t* x0, const float* cloud, i
     }
   };
   mark(AERO_STAGE_PARTITION, 0);
-  if ((e = cudaMemsetAsync(pl->keys, 0xFF, sizeof(unsigned long long) * a.ncell, s)) != cudaSuccess)
-    return cuda_fail(e);
+  // A planner without debug buffers keeps its keys empty between steps (the
+  // scatter pass empties each key it reads), so a step needs no fill; one with
+  // debug buffers fills before the step and keeps the keys for aero_get_debug.
+  const bool reset = pl->lim.debug_samples_max == 0 && !a.raw;
+  if (!(reset && pl->keys_empty)) {
+    const size_t nk = reset ? (size_t)pl->lim.fine_cells_max : (size_t)a.ncell;
+    if ((e = cudaMemsetAsync(pl->keys, 0xFF, sizeof(unsigned long long) * nk, s)) != cudaSuccess)
+      return cuda_fail(e);
+  }
   pl->keys_empty = false;
+  if (reset) a.ca.reset_keys = pl->keys;
   if (pl->grid_dirty) {
     // the scan leaves the counts at zero; clear them only when a step may have
     // stopped between the count pass and the scan
@@ -505,6 +513,7 @@ int enqueue_step(aero_planner* pl, const aero_state_t* x0, const float* cloud, i
     mark(AERO_STAGE_UPDATE, 7 + 4 * it);
   }
   note_step(pl, p, a);
+  pl->keys_empty = reset;
   return AERO_OK;
 }
 
@@ -695,7 +704,8 @@ size_t aero_debug_size(aero_planner_t* pl, int32_t what) {
   const size_t D = p.debug_samples < p.K ? p.debug_samples : p.K;
   const size_t G = pl->last_grid.G;
   switch (what) {
-    case AERO_DBG_FINE_KEYS: return 8 * (size_t)p.fine_az * p.fine_el;
+    case AERO_DBG_FINE_KEYS:  // kept by planners with debug buffers only
+      return pl->lim.debug_samples_max > 0 ? 8 * (size_t)p.fine_az * p.fine_el : 0;
     case AERO_DBG_COARSE_WIN: return 4 * (size_t)(p.fine_az / p.pool_az) * (p.fine_el / p.pool_el);
     case AERO_DBG_GOAL_CELL: return 4;
     case AERO_DBG_ANCHOR_CELLS: return 4 * E;
@@ -716,6 +726,7 @@ size_t aero_debug_size(aero_planner_t* pl, int32_t what) {
 
 int aero_get_debug(aero_planner_t* pl, int32_t what, void* dst, size_t bytes, void* stream) {
   if (!pl || !dst || !pl->have_step || what < 0 || what >= AERO_DBG_COUNT) return AERO_ERR_INVALID_ARG;
+  if (what == AERO_DBG_FINE_KEYS && pl->lim.debug_samples_max == 0) return AERO_ERR_INVALID_ARG;
   cudaStream_t s = (cudaStream_t)stream;
   const aero_params_t& p = pl->last;
   if (what == AERO_DBG_GRID_META || what == AERO_DBG_GRID_POINTS || what == AERO_DBG_GRID_START) {

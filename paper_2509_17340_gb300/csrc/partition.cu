@@ -613,8 +613,7 @@ int blocks_for(int64_t n, int threads, int cap) {
 
 cudaError_t launch_partition(const PartitionArgs& a, const PartTables& t, cudaStream_t s) {
   if (a.n == 0) return cudaSuccess;
-  k_partition<<<blocks_for(a.n, 256, 152 * 16), 256, 0, s>>>(a, t);
-  return cudaGetLastError();
+  return launch_k(k_partition, dim3(blocks_for(a.n, 256, 152 * 16)), dim3(256), s, true, a, t);
 }
 
 cudaError_t launch_grid_count(const CandArgs& ca, const GuideArgs& ga, const PartTables& t,
