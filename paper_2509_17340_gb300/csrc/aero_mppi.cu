@@ -401,7 +401,9 @@ void make_step_args(aero_planner* pl, const aero_state_t* x0, const float* cloud
   ra.grid = gv;
   ra.partials = pl->partials;
   ra.sample_costs = pl->sample_costs;
-  ra.dU = pl->dU;
+  // four lanes per sample (small problems): the update pass regenerates the
+  // perturbations; one lane: they are stored, which measured faster there
+  ra.dU = lanes == 4 ? nullptr : pl->dU;
   ra.dbg_D = p.debug_samples < p.K ? p.debug_samples : p.K;
   ra.dbg_u = pl->dbg_u;
   ra.dbg_x = pl->dbg_x;

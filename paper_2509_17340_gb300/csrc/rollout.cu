@@ -25,15 +25,12 @@ __device__ __forceinline__ float4 clamp4(float4 u, float4 lo, float4 hi) {
                      fminf(fmaxf(u.z, lo.z), hi.z), fminf(fmaxf(u.w, lo.w), hi.w));
 }
 
-// Kahan-compensated accumulation of the per-step costs.
-struct KahanSum {
-  float s = 0.0f, c = 0.0f;
-  __device__ __forceinline__ void add(float v) {
-    const float y = v - c;
-    const float t = s + y;
-    c = (t - s) - y;
-    s = t;
-  }
+// Plain binary32 accumulation of the per-step costs: T <= 128 positive
+// terms, relative error below T * 2^-24 (under 1e-5, a tenth of the cost
+// tolerance), with one dependent addition per step instead of four.
+struct CostSum {
+  float s = 0.0f;
+  __device__ __forceinline__ void add(float v) { s += v; }
 };
 
 // Samples [b * NT, (b + 1) * NT) of instance e; ctr3: the noise counter's
@@ -73,7 +70,7 @@ __device__ __forceinline__ void rollout_unit(const RolloutArgs& a, int e, int b,
     for (int i = 0; i < 10; ++i) X[i] = a.x0[i];
   }
 
-  KahanSum S;
+  CostSum S;
   // step j's control: prefetched noise, clamp, the stored perturbation, J_ctrl's
   // terms Q_c |u_j|^2 (j <= T-2) and Q_cd |u_j - u_{j-1}|^2 (1 <= j <= T-2)
   float4 d_next = noise_delta(k, 0, e, ctr3, a.key0, a.key1, sigma);
@@ -240,7 +237,7 @@ __device__ __forceinline__ void rollout_quad_unit(const RolloutArgs& a, int e, i
   // lane-specific cost weights
   const float w_norm = q == 0 ? cp.Q_track : q == 1 ? cp.Q_p : q == 2 ? cp.Q_v : cp.Q_q;
 
-  KahanSum S;
+  CostSum S;
   float4 d_cur = make_float4(0.f, 0.f, 0.f, 0.f);
   float4 d_nxt = q < T ? noise_delta(k, q, e, ctr3, a.key0, a.key1, sigma) : d_cur;
   float4 u_prev = make_float4(0.f, 0.f, 0.f, 0.f);
