@@ -352,6 +352,19 @@ int aero_accum_destroy(aero_accum_t* acc);
 int aero_shift_nominal(float* u_nom, int32_t E, int32_t T, int32_t shift, float* scratch,
                        void* stream);
 
+/* ---- test hooks ----------------------------------------------------------
+ * Every device and pinned host allocation of the library (aero_create,
+ * aero_batch_create, aero_accum_create) is counted.  aero_test_fail_alloc(n)
+ * makes the n-th next allocation (0 = the next one) return
+ * cudaErrorMemoryAllocation once, so that a test can drive each error path of
+ * the create functions (they return AERO_ERR_ALLOC and free what they had
+ * allocated); n < 0 cancels a pending failure.  aero_test_alloc_stats returns
+ * the number of allocations made since the library was loaded and stores the
+ * number not yet freed in *live (when live is not null).  Process-wide; not
+ * meant for production callers. */
+int aero_test_fail_alloc(int64_t n);
+int64_t aero_test_alloc_stats(int64_t* live);
+
 /* Copy debug buffer `what` of the last step into dst (host or device), at most
  * `bytes` bytes, ordered on `stream` (asynchronous for device dst and pinned
  * host dst).  Errors: INVALID_ARG (unknown id, no step yet, bytes too small). */

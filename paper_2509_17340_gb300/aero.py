@@ -117,6 +117,9 @@ _lib.aero_accum_gather.argtypes = [_vp, C.POINTER(C.c_float), C.POINTER(C.c_floa
 _lib.aero_accum_reset.argtypes = [_vp, _vp]
 _lib.aero_accum_destroy.argtypes = [_vp]
 _lib.aero_shift_nominal.argtypes = [_vp, C.c_int32, C.c_int32, C.c_int32, _vp, _vp]
+_lib.aero_test_fail_alloc.argtypes = [C.c_int64]
+_lib.aero_test_alloc_stats.argtypes = [C.POINTER(C.c_int64)]
+_lib.aero_test_alloc_stats.restype = C.c_int64
 _lib.aero_status_str.argtypes = [C.c_int]
 _lib.aero_status_str.restype = C.c_char_p
 
@@ -138,6 +141,19 @@ def _check(code: int, what: str):
 
 def lib() -> C.CDLL:
     return _lib
+
+
+def inject_alloc_failure(n: int) -> None:
+    """Make the n-th next library allocation fail once (``aero_test_fail_alloc``);
+    n < 0 cancels a pending failure."""
+    _lib.aero_test_fail_alloc(int(n))
+
+
+def alloc_stats() -> tuple[int, int]:
+    """(allocations made, allocations not yet freed) by the library."""
+    live = C.c_int64(0)
+    total = _lib.aero_test_alloc_stats(C.byref(live))
+    return int(total), int(live.value)
 
 
 def default_params_struct() -> Params:

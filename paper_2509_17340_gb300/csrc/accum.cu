@@ -14,6 +14,10 @@
 #include <vector>
 
 #include "../../include/aero_mppi.h"
+#include "internal.h"
+
+using aero::dev_free;
+using aero::dev_malloc;
 
 struct aero_accum {
   int F = 0;                  // frame slots
@@ -158,11 +162,11 @@ int aero_accum_create(int32_t frames, int64_t points_per_frame, aero_accum_t** o
   a->N = points_per_frame;
   a->count.assign(frames, 0);
   const size_t bytes = sizeof(float) * 3 * (size_t)frames * (size_t)points_per_frame;
-  cudaError_t e = cudaMalloc((void**)&a->ring, bytes);
+  cudaError_t e = dev_malloc((void**)&a->ring, bytes);
   if (e == cudaSuccess) e = cudaMemset(a->ring, 0xFF, bytes);  // all-ones words are NaN
   if (e != cudaSuccess) {
     cudaGetLastError();
-    if (a->ring) cudaFree(a->ring);
+    dev_free(a->ring);
     delete a;
     return e == cudaErrorMemoryAllocation ? AERO_ERR_ALLOC : AERO_ERR_CUDA;
   }
@@ -254,7 +258,7 @@ int aero_shift_nominal(float* u_nom, int32_t E, int32_t T, int32_t shift, float*
 int aero_accum_destroy(aero_accum_t* a) {
   if (!a) return AERO_OK;
   cudaDeviceSynchronize();
-  if (a->ring) cudaFree(a->ring);
+  dev_free(a->ring);
   delete a;
   return AERO_OK;
 }

@@ -7,6 +7,7 @@
 #include <cstdint>
 #include <cstdio>
 #include <algorithm>
+#include <atomic>
 #include <cstring>
 #include <mutex>
 #include <new>
@@ -16,6 +17,63 @@
 #include "internal.h"
 
 using namespace aero;
+
+namespace aero {
+
+namespace {
+std::atomic<int64_t> g_alloc_total{0};       // allocations made
+std::atomic<int64_t> g_alloc_live{0};        // allocations not yet freed
+std::atomic<int64_t> g_alloc_fail_after{-1}; // allocations left before the injected failure
+
+// True for the allocation aero_test_fail_alloc picked; the countdown then
+// stays at -1 (off).
+bool injected_failure() {
+  int64_t c = g_alloc_fail_after.load();
+  while (c >= 0)
+    if (g_alloc_fail_after.compare_exchange_weak(c, c - 1)) return c == 0;
+  return false;
+}
+
+cudaError_t counted(cudaError_t e, void** p) {
+  if (e == cudaSuccess) {
+    g_alloc_total.fetch_add(1);
+    g_alloc_live.fetch_add(1);
+  } else {
+    *p = nullptr;
+  }
+  return e;
+}
+}  // namespace
+
+cudaError_t dev_malloc(void** p, size_t bytes) {
+  if (injected_failure()) {
+    *p = nullptr;
+    return cudaErrorMemoryAllocation;
+  }
+  return counted(cudaMalloc(p, bytes), p);
+}
+
+cudaError_t host_malloc(void** p, size_t bytes) {
+  if (injected_failure()) {
+    *p = nullptr;
+    return cudaErrorMemoryAllocation;
+  }
+  return counted(cudaMallocHost(p, bytes), p);
+}
+
+void dev_free(void* p) {
+  if (!p) return;
+  cudaFree(p);
+  g_alloc_live.fetch_sub(1);
+}
+
+void host_free(void* p) {
+  if (!p) return;
+  cudaFreeHost(p);
+  g_alloc_live.fetch_sub(1);
+}
+
+}  // namespace aero
 
 struct aero_planner {
   aero_limits_t lim{};
@@ -192,7 +250,7 @@ int validate(const aero_planner* pl, const aero_params_t* p, int64_t n_points) {
 
 template <typename T>
 cudaError_t alloc(T** p, size_t count) {
-  return cudaMalloc((void**)p, sizeof(T) * (count > 0 ? count : 1));
+  return dev_malloc((void**)p, sizeof(T) * (count > 0 ? count : 1));
 }
 
 void free_all(aero_planner* pl) {
@@ -203,8 +261,7 @@ void free_all(aero_planner* pl) {
                   pl->sample_costs, pl->dU,      pl->stage2_x, pl->counter,   pl->status,   pl->dbg_u,
                   pl->dbg_x,    pl->dbg_d,      pl->stage_cloud,      pl->stage_unom,   pl->stage_ubest,
                   pl->stage_cand,   pl->stage_best,   pl->dbg_pre};
-  for (void* q : ptrs)
-    if (q) cudaFree(q);
+  for (void* q : ptrs) dev_free(q);
 }
 
 constexpr size_t kProfSlots = 512;
@@ -642,6 +699,16 @@ int aero_create(const aero_limits_t* limits, aero_planner_t** out) {
   return AERO_OK;
 }
 
+int aero_test_fail_alloc(int64_t n) {
+  g_alloc_fail_after.store(n < 0 ? -1 : n);
+  return AERO_OK;
+}
+
+int64_t aero_test_alloc_stats(int64_t* live) {
+  if (live) *live = g_alloc_live.load();
+  return g_alloc_total.load();
+}
+
 int aero_destroy(aero_planner_t* pl) {
   if (!pl) return AERO_OK;
   cudaDeviceSynchronize();
@@ -1062,15 +1129,15 @@ BatchView view_of(aero_batch* b, int n) {
 void batch_free(aero_batch* b) {
   for (aero_planner* pl : b->planners) aero_destroy(pl);
   for (auto& g : b->graphs) cudaGraphExecDestroy(g.exec);
-  if (b->d_args) cudaFree(b->d_args);
-  if (b->d_tabs) cudaFree(b->d_tabs);
-  if (b->d_queue) cudaFree(b->d_queue);
-  if (b->scratch) cudaFree(b->scratch);
+  dev_free(b->d_args);
+  dev_free(b->d_tabs);
+  dev_free(b->d_queue);
+  dev_free(b->scratch);
   for (int r = 0; r < aero_batch::kRing; ++r) {
-    if (b->h_args[r]) cudaFreeHost(b->h_args[r]);
+    host_free(b->h_args[r]);
     if (b->h_done[r]) cudaEventDestroy(b->h_done[r]);
   }
-  if (b->h_tabs) cudaFreeHost(b->h_tabs);
+  host_free(b->h_tabs);
   if (b->tabs_done) cudaEventDestroy(b->tabs_done);
   if (b->cap) cudaStreamDestroy(b->cap);
   if (b->cap2) cudaStreamDestroy(b->cap2);
@@ -1339,19 +1406,19 @@ int aero_batch_create(const aero_limits_t* limits, int32_t n_max, aero_batch_t**
   if (e == cudaSuccess) e = batch_grid_occupancy(b->occ_grid);
   if (e == cudaSuccess) e = batch_rollout_occupancy(b->occ_roll);
   const size_t bytes = layout_for(n_max).bytes;
-  if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_args, bytes);
-  if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_tabs, sizeof(PartTables) * n_max);
-  if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_queue, 4 * sizeof(unsigned int));
+  if (e == cudaSuccess) e = dev_malloc((void**)&b->d_args, bytes);
+  if (e == cudaSuccess) e = dev_malloc((void**)&b->d_tabs, sizeof(PartTables) * n_max);
+  if (e == cudaSuccess) e = dev_malloc((void**)&b->d_queue, 4 * sizeof(unsigned int));
   if (e == cudaSuccess) e = cudaMemset(b->d_queue, 0, 4 * sizeof(unsigned int));
   b->scratch_stride = align16(sizeof(float) * ((size_t)b->lim.E_max * b->lim.T_max * 4 +
                                                (size_t)b->lim.T_max * 4 + b->lim.E_max + 1)) /
                       sizeof(float);
-  if (e == cudaSuccess) e = cudaMalloc((void**)&b->scratch, sizeof(float) * b->scratch_stride * n_max);
+  if (e == cudaSuccess) e = dev_malloc((void**)&b->scratch, sizeof(float) * b->scratch_stride * n_max);
   for (int r = 0; r < aero_batch::kRing && e == cudaSuccess; ++r) {
-    e = cudaMallocHost((void**)&b->h_args[r], bytes);
+    e = host_malloc((void**)&b->h_args[r], bytes);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->h_done[r], cudaEventDisableTiming);
   }
-  if (e == cudaSuccess) e = cudaMallocHost((void**)&b->h_tabs, sizeof(PartTables) * n_max);
+  if (e == cudaSuccess) e = host_malloc((void**)&b->h_tabs, sizeof(PartTables) * n_max);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->tabs_done, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->cap2, cudaStreamNonBlocking);

@@ -265,4 +265,13 @@ cudaError_t launch_k(void (*kernel)(KArgs...), dim3 grid, dim3 block, cudaStream
   return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
 }
 
+// Every device and pinned host allocation of the library goes through these
+// four calls.  They count live allocations and let a test make the n-th next
+// allocation fail (aero_test_fail_alloc), so that each error path of the
+// create functions can be driven without exhausting the device.
+cudaError_t dev_malloc(void** p, size_t bytes);
+cudaError_t host_malloc(void** p, size_t bytes);
+void dev_free(void* p);
+void host_free(void* p);
+
 }  // namespace aero

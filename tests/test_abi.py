@@ -87,3 +87,15 @@ def test_binding_struct_sizes_match_header():
     assert C.sizeof(aero.Params) == 232
     assert C.sizeof(aero.BatchItem) == 336
     assert C.sizeof(aero.BatchConfig) == 16
+
+
+def test_allocation_test_hooks_without_cuda(so):
+    # the counters and the injection countdown are host state: readable and
+    # settable without a device
+    so.aero_test_alloc_stats.restype = C.c_int64
+    live = C.c_int64(-1)
+    total = so.aero_test_alloc_stats(C.byref(live))
+    assert total >= 0 and 0 <= live.value <= total
+    assert so.aero_test_alloc_stats(None) == total
+    assert so.aero_test_fail_alloc(C.c_int64(3)) == 0
+    assert so.aero_test_fail_alloc(C.c_int64(-1)) == 0
