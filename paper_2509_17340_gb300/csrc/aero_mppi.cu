@@ -458,9 +458,9 @@ void make_step_args(aero_planner* pl, const aero_state_t* x0, const float* cloud
   ra.grid = gv;
   ra.partials = pl->partials;
   ra.sample_costs = pl->sample_costs;
-  // four lanes per sample (small problems): the update pass regenerates the
-  // perturbations; one lane: they are stored, which measured faster there
-  ra.dU = lanes == 4 ? nullptr : pl->dU;
+  // the sampled perturbations are stored when the workspace holds them, else
+  // the weighted sums regenerate them
+  ra.dU = pl->dU;
   ra.dbg_D = p.debug_samples < p.K ? p.debug_samples : p.K;
   ra.dbg_u = pl->dbg_u;
   ra.dbg_x = pl->dbg_x;
@@ -1122,6 +1122,7 @@ BatchView view_of(aero_batch* b, int n) {
   v.order1 = reinterpret_cast<const int*>(b->d_args + L.order1);
   v.order4 = reinterpret_cast<const int*>(b->d_args + L.order4);
   v.n = n;
+  v.T_max = b->lim.T_max;
   v.queue = b->d_queue;
   return v;
 }
@@ -1404,7 +1405,7 @@ int aero_batch_create(const aero_limits_t* limits, int32_t n_max, aero_batch_t**
   cudaError_t e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, dev);
   if (e == cudaSuccess) e = batch_grid_occupancy(b->occ_grid);
-  if (e == cudaSuccess) e = batch_rollout_occupancy(b->occ_roll);
+  if (e == cudaSuccess) e = batch_rollout_occupancy(b->occ_roll, b->lim.T_max);
   const size_t bytes = layout_for(n_max).bytes;
   if (e == cudaSuccess) e = dev_malloc((void**)&b->d_args, bytes);
   if (e == cudaSuccess) e = dev_malloc((void**)&b->d_tabs, sizeof(PartTables) * n_max);

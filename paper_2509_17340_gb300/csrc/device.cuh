@@ -172,13 +172,30 @@ __device__ __forceinline__ float dist2_to(const float4 q, float px, float py, fl
   return ax * ax + ay * ay + az * az;
 }
 
+// min(best, squared distances to the n entries at P), kW entries per round
+// so that kW loads are in flight; the last round repeats its first entry in
+// place of the missing ones (the minimum is exact in any order).
+template <int kW = 4>
+__device__ __forceinline__ float scan_min(const float4* P, int n, float px, float py, float pz,
+                                          float best) {
+  for (int t = 0; t < n; t += kW) {
+    float4 c[kW];
+    c[0] = __ldg(P + t);
+#pragma unroll
+    for (int i = 1; i < kW; ++i) c[i] = t + i < n ? __ldg(P + t + i) : c[0];
+    float m = dist2_to(c[0], px, py, pz);
+#pragma unroll
+    for (int i = 1; i < kW; ++i) m = fminf(m, dist2_to(c[i], px, py, pz));
+    best = fminf(best, m);
+  }
+  return best;
+}
+
 // One thread, one query.
 __device__ __forceinline__ float nn_dist2(float px, float py, float pz, const GridView& g,
                                           float dmax2) {
   const int2 r = cell_range(px, py, pz, g);
-  float best = dmax2;
-  for (int i = 0; i < r.y; ++i) best = fminf(best, dist2_to(__ldg(g.pts + r.x + i), px, py, pz));
-  return best;
+  return scan_min(g.pts + r.x, r.y, px, py, pz, dmax2);
 }
 
 // Asynchronous 16-byte global -> shared copy (cp.async, cached in L1).

@@ -16,7 +16,6 @@ constexpr int kGridMax = 96;         // collision-grid cells per axis, at most
 constexpr int kScanTile = 4096;      // cells per scan tile (1024 threads x 4)
 constexpr int kScanTileShift = 12;
 constexpr int kRolloutThreads = 128; // samples per rollout CTA (one warp-group)
-constexpr int kWarpStage = 256;     // candidate entries a warp stages in shared memory per step
 constexpr int kQuadMaxSamples = 32768;  // E*K up to which four lanes carry one sample
 
 // Binary32 edge tables of the partition, passed by value to the kernels.
@@ -113,7 +112,7 @@ struct DynParams {
 
 struct RolloutArgs {
   int E, K, T, nb;         // nb = CTAs per instance
-  int lanes_per_sample;    // 1, or 4 (k_rollout_quad) for small E*K
+  int lanes_per_sample;    // 1, or 4 (k_rollout_split) for small E*K
   float inv_lambda;
   float sigma[4], umin[4], umax[4];
   float x0[10];            // p = 0 (relative), q0, v0
@@ -204,6 +203,7 @@ struct BatchView {
   const int* order1;         // rollout position -> planner (one lane per sample)
   const int* order4;         // (four lanes per sample)
   int n;
+  int T_max;                 // longest horizon a planner of the batch may use
   unsigned int* queue;       // per rollout kernel: {next unit, exit ticket}, zero between launches
 };
 
@@ -221,7 +221,7 @@ cudaError_t launch_batch_update(const BatchView& v, int it, int blocks, cudaStre
 // Resident CTAs per SM: {partition, count, scan, scatter} and {rollout with one
 // lane per sample, with four, update, rollout with one lane compiled for six}.
 cudaError_t batch_grid_occupancy(int out[4]);
-cudaError_t batch_rollout_occupancy(int out[4]);
+cudaError_t batch_rollout_occupancy(int out[4], int T_max);
 
 cudaError_t launch_partition(const PartitionArgs& a, const PartTables& t, cudaStream_t s);
 cudaError_t launch_grid_count(const CandArgs& ca, const GuideArgs& ga, const PartTables& t,
@@ -250,12 +250,12 @@ cudaError_t launch_philox(uint32_t k0, uint32_t k1, uint32_t c1, uint32_t c2, ui
 // waits for it in griddepcontrol.wait (see pdl_wait), which hides the launch
 // latency of a chain of dependent kernels.
 template <typename... KArgs, typename... Args>
-cudaError_t launch_k(void (*kernel)(KArgs...), dim3 grid, dim3 block, cudaStream_t s, bool pdl,
-                     Args&&... args) {
+cudaError_t launch_ks(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                      bool pdl, Args&&... args) {
   cudaLaunchConfig_t cfg{};
   cfg.gridDim = grid;
   cfg.blockDim = block;
-  cfg.dynamicSmemBytes = 0;
+  cfg.dynamicSmemBytes = smem;
   cfg.stream = s;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
@@ -263,6 +263,12 @@ cudaError_t launch_k(void (*kernel)(KArgs...), dim3 grid, dim3 block, cudaStream
   cfg.attrs = pdl ? attr : nullptr;
   cfg.numAttrs = pdl ? 1 : 0;
   return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
+
+template <typename... KArgs, typename... Args>
+cudaError_t launch_k(void (*kernel)(KArgs...), dim3 grid, dim3 block, cudaStream_t s, bool pdl,
+                     Args&&... args) {
+  return launch_ks(kernel, grid, block, 0, s, pdl, std::forward<Args>(args)...);
 }
 
 // Every device and pinned host allocation of the library goes through these

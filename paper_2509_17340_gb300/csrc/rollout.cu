@@ -185,42 +185,134 @@ __device__ __forceinline__ void rollout_unit(const RolloutArgs& a, int e, int b,
 }
 
 // ---------------------------------------------------------------------------
-// The same Stage I pass with four lanes per sample (a quad), for problems too
-// small to fill the GPU with one lane per sample.  The quad's lanes hold the
-// same state (RK4 and the clamp run on all four, with identical results) and
-// split the rest: lane q draws the perturbation of step 4m + q of every block of
-// four steps (one block ahead) and the quad shares it by shuffles; the lanes
-// scan every fourth candidate; each lane evaluates one group of cost terms
-// (q = 0: guide tracking, velocity norm, control; 1: goal position; 2: goal
-// velocity; 3: attitude and collision) and a butterfly sum, bitwise the same on
-// the four lanes, adds them; for the update lane q handles component q.
+// The Stage I pass for problems too small to fill the GPU with one lane per
+// sample, split into phases so that only the dynamics stays sequential: 32
+// samples per CTA (four threads per sample, one in each warp); the horizon
+// in chunks of at most kChunk steps.
+//   noise    the perturbations of every step, drawn one chunk ahead (the
+//            first chunk by all warps, the next ones by warps 1-3 while warp
+//            0 integrates); the clamped controls stay in shared memory for
+//            the whole horizon;
+//   dynamics warp 0, one lane per sample, applies the chunk's controls with
+//            RK4 and adds the control and state cost terms; the positions go
+//            to shared memory;
+//   queries  every (sample, step) of the chunk looks up its cell; the
+//            non-empty candidate lists are cut into items of kItem entries
+//            and the CTA's threads take the items in turn, each folding its
+//            squared distances into the query's minimum with a shared-memory
+//            atomic minimum (exact in any order).  A warp therefore scans
+//            items, not its longest lane's list: the lists of one step's
+//            samples are mostly empty, with a few of up to a hundred entries.
+// Then the per-CTA minimum, weights and weighted perturbation sums as in the
+// one-lane pass: every warp holds the 32 samples' costs and reduces them
+// itself.
 // ---------------------------------------------------------------------------
-constexpr int QS = NT / 4;  // samples per CTA
+constexpr int QS = NT / 4;       // samples per CTA
+constexpr int kChunk = 32;       // steps per chunk
+constexpr int kQ = kChunk / NW;  // queries per thread and chunk, at most
+constexpr int kItem = 8;         // candidate entries per scan item
+constexpr int kChunkQ = kChunk * QS;
 
-__device__ __forceinline__ void rollout_quad_unit(const RolloutArgs& a, int e, int b,
-                                                  uint32_t ctr3) {
-  __shared__ float4 s_un[kMaxT];
-  __shared__ float s_gd[kMaxT * 3];
-  __shared__ float s_red[NW];
-  __shared__ float4 s_w[NW][kMaxT];
-  __shared__ float4 s_cand[NW][kWarpStage];
+// Dynamic shared memory of the split pass (bytes), for horizons up to T.
+__host__ __device__ constexpr size_t split_smem_bytes(int T) {
+  return 16 * (size_t)T * QS       // u: clamped controls [T][QS]
+         + 16 * (size_t)T          // un: nominal [T]
+         + 8 * (size_t)kChunkQ     // qrange: candidate range of each listed query
+         + 4 * (size_t)kChunkQ * 3 // pc: positions [kChunk][3][QS]
+         + 4 * (size_t)kChunkQ     // d2: squared distance bits [kChunk][QS]
+         + 4 * (size_t)NW * QS     // cost: partial sums [NW][QS]
+         + 4 * (size_t)(kChunkQ + 2)  // qitem: first item of each listed query (+ pad)
+         + 4 * (size_t)NW * 2      // scan: warp totals
+         + 12 * (size_t)T          // gd: guides [T][3]
+         + 2 * (size_t)kChunkQ;    // qslot: (step, sample) slot of each listed query
+}
 
-  const int tid = threadIdx.x;
-  const int lane = tid & 31, wid = tid >> 5, q = lane & 3, qbase = lane & ~3;
-  const int T = a.T;
-  for (int i = tid; i < T; i += NT) s_un[i] = reinterpret_cast<const float4*>(a.u_nom)[e * T + i];
-  for (int i = tid; i < 3 * T; i += NT) s_gd[i] = a.guides[e * T * 3 + i];
+struct SplitSmem {
+  float4* u;
+  float4* un;
+  int2* qrange;
+  float* pc;
+  int* d2;
+  float* cost;
+  int* qitem;
+  int2* scan;
+  float* gd;
+  unsigned short* qslot;
+};
+
+__device__ __forceinline__ SplitSmem split_layout(unsigned char* base, int T) {
+  SplitSmem m;
+  m.u = reinterpret_cast<float4*>(base);
+  m.un = m.u + (size_t)T * QS;
+  m.qrange = reinterpret_cast<int2*>(m.un + T);
+  m.pc = reinterpret_cast<float*>(m.qrange + kChunkQ);
+  m.d2 = reinterpret_cast<int*>(m.pc + 3 * kChunkQ);
+  m.cost = reinterpret_cast<float*>(m.d2 + kChunkQ);
+  m.qitem = reinterpret_cast<int*>(m.cost + NW * QS);
+  m.scan = reinterpret_cast<int2*>(m.qitem + kChunkQ + 1 + 1);  // +1 word keeps int2 aligned
+  m.gd = reinterpret_cast<float*>(m.scan + NW);
+  m.qslot = reinterpret_cast<unsigned short*>(m.gd + 3 * T);
+  return m;
+}
+
+// Exclusive prefix sums of (x, y) over the CTA; `total` receives the sums.
+__device__ __forceinline__ int2 block_scan2(int2 v, int2* warp_tot, int2& total) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  int2 inc = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int x = __shfl_up_sync(0xffffffffu, inc.x, o), y = __shfl_up_sync(0xffffffffu, inc.y, o);
+    if (lane >= o) {
+      inc.x += x;
+      inc.y += y;
+    }
+  }
+  if (lane == 31) warp_tot[wid] = inc;
   __syncthreads();
+  int2 before = make_int2(0, 0);
+  total = make_int2(0, 0);
+#pragma unroll
+  for (int w = 0; w < NW; ++w) {
+    const int2 t = warp_tot[w];
+    if (w < wid) {
+      before.x += t.x;
+      before.y += t.y;
+    }
+    total.x += t.x;
+    total.y += t.y;
+  }
+  return make_int2(before.x + inc.x - v.x, before.y + inc.y - v.y);
+}
 
-  const int k = b * QS + (tid >> 2);
+__device__ __forceinline__ void rollout_split_unit(const RolloutArgs& a, int e, int b,
+                                                   uint32_t ctr3) {
+  extern __shared__ __align__(16) unsigned char split_smem[];
+  const int T = a.T;
+  const SplitSmem m = split_layout(split_smem, T);
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  for (int i = tid; i < T; i += NT) m.un[i] = reinterpret_cast<const float4*>(a.u_nom)[e * T + i];
+  for (int i = tid; i < 3 * T; i += NT) m.gd[i] = a.guides[e * T * 3 + i];
+
+  const int k = b * QS + lane;  // this thread's sample in every phase
   const bool active = k < a.K;
   const CostParams& cp = a.cost;
   const float dmax2 = cp.d_max * cp.d_max;
-  const int dbg = (active && q == 0 && k < a.dbg_D) ? (e * a.dbg_D + k) : -1;
+  const int dbg = (active && k < a.dbg_D) ? (e * a.dbg_D + k) : -1;
   const float4 sigma = make_float4(a.sigma[0], a.sigma[1], a.sigma[2], a.sigma[3]);
   const float4 umin = make_float4(a.umin[0], a.umin[1], a.umin[2], a.umin[3]);
   const float4 umax = make_float4(a.umax[0], a.umax[1], a.umax[2], a.umax[3]);
-  float* dUf = a.dU ? reinterpret_cast<float*>(a.dU + (size_t)e * T * a.K + k) + q : nullptr;
+  const int nch = (T + kChunk - 1) / kChunk;
+  const int tcb = (T + nch - 1) / nch;  // steps per chunk (the last may be shorter)
+
+  // u_j for the steps j = first (mod stride) of [j0, j0 + tc)
+  auto noise = [&](int j0, int tc, int first, int stride) {
+    for (int j = j0 + first; j < j0 + tc; j += stride) {
+      const float4 un = m.un[j];
+      const float4 d = noise_delta(k, j, e, ctr3, a.key0, a.key1, sigma);
+      m.u[j * QS + lane] =
+          clamp4(make_float4(un.x + d.x, un.y + d.y, un.z + d.z, un.w + d.w), umin, umax);
+    }
+  };
 
   State x;
 #pragma unroll
@@ -229,164 +321,138 @@ __device__ __forceinline__ void rollout_quad_unit(const RolloutArgs& a, int e, i
   for (int i = 0; i < 4; ++i) x.q[i] = a.x0[3 + i];
 #pragma unroll
   for (int i = 0; i < 3; ++i) x.v[i] = a.x0[7 + i];
-  if (dbg >= 0) {
+  if (dbg >= 0 && wid == 0) {
     float* X = a.dbg_x + (size_t)dbg * (T + 1) * 10;
     for (int i = 0; i < 10; ++i) X[i] = a.x0[i];
   }
-
-  // lane-specific cost weights
-  const float w_norm = q == 0 ? cp.Q_track : q == 1 ? cp.Q_p : q == 2 ? cp.Q_v : cp.Q_q;
-
-  CostSum S;
-  float4 d_cur = make_float4(0.f, 0.f, 0.f, 0.f);
-  float4 d_nxt = q < T ? noise_delta(k, q, e, ctr3, a.key0, a.key1, sigma) : d_cur;
   float4 u_prev = make_float4(0.f, 0.f, 0.f, 0.f);
-  auto control = [&](int j, float& c_ctrl) -> float4 {
-    if ((j & 3) == 0) {
-      d_cur = d_nxt;
-      if (j + 4 + q < T) d_nxt = noise_delta(k, j + 4 + q, e, ctr3, a.key0, a.key1, sigma);
+  float S = 0.0f;  // warp 0: control and state terms; every warp: its queries' collision terms
+
+  __syncthreads();  // un, gd
+  noise(0, tcb < T ? tcb : T, wid, NW);
+  __syncthreads();
+  for (int j0 = 0; j0 < T; j0 += tcb) {
+    const int tc = tcb < T - j0 ? tcb : T - j0;
+    if (wid == 0) {
+      for (int jj = 0; jj < tc; ++jj) {
+        const int j = j0 + jj;
+        const float4 u = m.u[j * QS + lane];
+        // J_ctrl: Q_c |u_j|^2 (j <= T-2) and Q_cd |u_j - u_{j-1}|^2 (1 <= j <= T-2)
+        float c = 0.0f;
+        if (j <= T - 2) {
+          c = cp.Q_c * (u.x * u.x + u.y * u.y + u.z * u.z + u.w * u.w);
+          if (j >= 1) {
+            const float ax = u.x - u_prev.x, ay = u.y - u_prev.y, az = u.z - u_prev.z,
+                        aw = u.w - u_prev.w;
+            c += cp.Q_cd * (ax * ax + ay * ay + az * az + aw * aw);
+          }
+        }
+        u_prev = u;
+        rk4_step(x, u, a.dyn);
+        // state terms at x_{j+1} against the guide at t = (j + 1) dt
+        const float gx = m.gd[3 * j], gy = m.gd[3 * j + 1], gz = m.gd[3 * j + 2];
+        c += cp.Q_track * norm3f(x.p[0] - gx, x.p[1] - gy, x.p[2] - gz);
+        c += cp.Q_vnorm * (x.v[0] * x.v[0] + x.v[1] * x.v[1] + x.v[2] * x.v[2]);
+        c += goal_term(x, cp);
+        S += c;
+        m.pc[(jj * 3 + 0) * QS + lane] = x.p[0];
+        m.pc[(jj * 3 + 1) * QS + lane] = x.p[1];
+        m.pc[(jj * 3 + 2) * QS + lane] = x.p[2];
+        if (dbg >= 0) {
+          reinterpret_cast<float4*>(a.dbg_u)[(size_t)dbg * T + j] = u;
+          float* X = a.dbg_x + ((size_t)dbg * (T + 1) + j + 1) * 10;
+          for (int i = 0; i < 3; ++i) X[i] = x.p[i];
+          for (int i = 0; i < 4; ++i) X[3 + i] = x.q[i];
+          for (int i = 0; i < 3; ++i) X[7 + i] = x.v[i];
+        }
+      }
+    } else if (j0 + tc < T) {
+      noise(j0 + tc, tcb < T - j0 - tc ? tcb : T - j0 - tc, wid - 1, NW - 1);
     }
-    const int src = qbase + (j & 3);
-    const float4 d = make_float4(__shfl_sync(0xffffffffu, d_cur.x, src),
-                                 __shfl_sync(0xffffffffu, d_cur.y, src),
-                                 __shfl_sync(0xffffffffu, d_cur.z, src),
-                                 __shfl_sync(0xffffffffu, d_cur.w, src));
-    const float4 un = s_un[j];
-    const float4 u = clamp4(make_float4(un.x + d.x, un.y + d.y, un.z + d.z, un.w + d.w), umin, umax);
-    if (dUf && active) {
-      const float du = q == 0 ? u.x - un.x : q == 1 ? u.y - un.y : q == 2 ? u.z - un.z : u.w - un.w;
-      __stcs(dUf + (size_t)j * a.K * 4, du);
-    }
-    c_ctrl = 0.0f;
-    if (j <= T - 2) {
-      c_ctrl = cp.Q_c * (u.x * u.x + u.y * u.y + u.z * u.z + u.w * u.w);
-      if (j >= 1) {
-        const float ax = u.x - u_prev.x, ay = u.y - u_prev.y, az = u.z - u_prev.z, aw = u.w - u_prev.w;
-        c_ctrl += cp.Q_cd * (ax * ax + ay * ay + az * az + aw * aw);
+    __syncthreads();  // pc filled; the next chunk's controls drawn
+
+    // this thread's queries: steps jj = wid + 4 i of the chunk, sample `lane`
+    int2 rg[kQ];
+    int2 cnt = make_int2(0, 0);  // (listed queries, items)
+#pragma unroll
+    for (int i = 0; i < kQ; ++i) {
+      const int jj = wid + NW * i;
+      rg[i] = make_int2(0, 0);
+      if (jj < tc) {
+        m.d2[jj * QS + lane] = __float_as_int(dmax2);
+        if (active)
+          rg[i] = cell_range(m.pc[(jj * 3) * QS + lane], m.pc[(jj * 3 + 1) * QS + lane],
+                             m.pc[(jj * 3 + 2) * QS + lane], a.grid);
+      }
+      if (rg[i].y > 0) {
+        cnt.x += 1;
+        cnt.y += (rg[i].y + kItem - 1) / kItem;
       }
     }
-    u_prev = u;
-    return u;
-  };
-
-  float c_ctrl;
-  float4 u_j = control(0, c_ctrl);
-  rk4_step(x, u_j, a.dyn);
-  int2 range = cell_range(x.p[0], x.p[1], x.p[2], a.grid);
-  float4* buf = s_cand[wid];
-  for (int j = 1; j <= T; ++j) {
-    // stage x_j's candidates: quads laid end to end, lane q copies every fourth
-    const int n = range.y;
-    int incl = n;
+    int2 total;
+    int2 off = block_scan2(cnt, m.scan, total);
 #pragma unroll
-    for (int o = 4; o < 32; o <<= 1) {
-      const int y = __shfl_up_sync(0xffffffffu, incl, o);
-      if (lane >= o) incl += y;
+    for (int i = 0; i < kQ; ++i) {
+      if (rg[i].y > 0) {
+        m.qitem[off.x] = off.y;
+        m.qrange[off.x] = rg[i];
+        m.qslot[off.x] = (unsigned short)((wid + NW * i) * QS + lane);
+        off.x += 1;
+        off.y += (rg[i].y + kItem - 1) / kItem;
+      }
     }
-    const int total = __shfl_sync(0xffffffffu, incl, 31);
-    const int excl = incl - n;
-    const bool staged = total <= kWarpStage;
-    __syncwarp();
-    if (staged) {
-      for (int i = q; i < n; i += 4) cp_async16(buf + excl + i, a.grid.pts + range.x + i);
-      cp_async_commit();
+    if (tid == 0) m.qitem[total.x] = total.y;
+    __syncthreads();  // query list complete
+    for (int it = tid; it < total.y; it += NT) {
+      // the listed query holding item `it`: largest q with qitem[q] <= it
+      int lo = 0, hi = total.x - 1;
+      while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (m.qitem[mid] <= it) lo = mid; else hi = mid - 1;
+      }
+      const int2 r = m.qrange[lo];
+      const int slot = m.qslot[lo];
+      const int jj = slot / QS, sl = slot % QS;
+      const int first = (it - m.qitem[lo]) * kItem;
+      const int n = r.y - first < kItem ? r.y - first : kItem;
+      const float d2 = scan_min<kItem>(a.grid.pts + r.x + first, n, m.pc[(jj * 3) * QS + sl],
+                                       m.pc[(jj * 3 + 1) * QS + sl], m.pc[(jj * 3 + 2) * QS + sl],
+                                       dmax2);
+      if (d2 < dmax2) atomicMin(m.d2 + slot, __float_as_int(d2));  // non-negative: int order
     }
-    const int2 range_j = range;
-    State xn = x;
-    float c_next = 0.0f;
-    float4 u_next = u_j;
-    if (j < T) {
-      u_next = control(j, c_next);
-      rk4_step(xn, u_next, a.dyn);
-      range = cell_range(xn.p[0], xn.p[1], xn.p[2], a.grid);
+    __syncthreads();  // minima complete; pc free for the next chunk
+#pragma unroll
+    for (int i = 0; i < kQ; ++i) {
+      const int jj = wid + NW * i;
+      if (jj < tc && active) {
+        const float d2 = __int_as_float(m.d2[jj * QS + lane]);
+        S += jcol_from_d2(d2, cp, dmax2);
+        if (dbg >= 0) a.dbg_d[(size_t)dbg * T + j0 + jj] = d2 < dmax2 ? sqrtf(d2) : INFINITY;
+      }
     }
-    float best = dmax2;
-    if (staged) {
-      cp_async_wait_all();
-      for (int i = q; i < n; i += 4) best = fminf(best, dist2_to(buf[excl + i], x.p[0], x.p[1], x.p[2]));
-    } else {
-      for (int i = q; i < n; i += 4)
-        best = fminf(best, dist2_to(__ldg(a.grid.pts + range_j.x + i), x.p[0], x.p[1], x.p[2]));
-    }
-    best = fminf(best, __shfl_xor_sync(0xffffffffu, best, 1));
-    const float d2 = fminf(best, __shfl_xor_sync(0xffffffffu, best, 2));
-    // this lane's cost terms at x_j (guide at t = j dt)
-    const float gx = s_gd[3 * (j - 1)], gy = s_gd[3 * (j - 1) + 1], gz = s_gd[3 * (j - 1) + 2];
-    const float* qg = cp.q_goal;
-    const float r1 = -x.q[0] * qg[1] + x.q[1] * qg[0] - x.q[2] * qg[3] + x.q[3] * qg[2];
-    const float r2 = -x.q[0] * qg[2] + x.q[1] * qg[3] + x.q[2] * qg[0] - x.q[3] * qg[1];
-    const float r3 = -x.q[0] * qg[3] - x.q[1] * qg[2] + x.q[2] * qg[1] + x.q[3] * qg[0];
-    float vx, vy, vz;
-    if (q == 0) { vx = x.p[0] - gx; vy = x.p[1] - gy; vz = x.p[2] - gz; }
-    else if (q == 1) { vx = x.p[0] - cp.goal_rel[0]; vy = x.p[1] - cp.goal_rel[1]; vz = x.p[2] - cp.goal_rel[2]; }
-    else if (q == 2) { vx = x.v[0] - cp.v_goal[0]; vy = x.v[1] - cp.v_goal[1]; vz = x.v[2] - cp.v_goal[2]; }
-    else { vx = r1; vy = r2; vz = r3; }
-    float c = w_norm * norm3f(vx, vy, vz);
-    if (q == 3) c = w_norm * 2.8284271247461903f * fast_sqrt(vx * vx + vy * vy + vz * vz) +
-                    jcol_from_d2(d2, cp, dmax2);
-    if (q == 0) c += cp.Q_vnorm * (x.v[0] * x.v[0] + x.v[1] * x.v[1] + x.v[2] * x.v[2]) + c_ctrl;
-    c += __shfl_xor_sync(0xffffffffu, c, 1);
-    c += __shfl_xor_sync(0xffffffffu, c, 2);
-    S.add(c);
-    if (dbg >= 0) {
-      reinterpret_cast<float4*>(a.dbg_u)[(size_t)dbg * T + j - 1] = u_j;
-      float* X = a.dbg_x + ((size_t)dbg * (T + 1) + j) * 10;
-      for (int i = 0; i < 3; ++i) X[i] = x.p[i];
-      for (int i = 0; i < 4; ++i) X[3 + i] = x.q[i];
-      for (int i = 0; i < 3; ++i) X[7 + i] = x.v[i];
-      a.dbg_d[(size_t)dbg * T + j - 1] = d2 < dmax2 ? sqrtf(d2) : INFINITY;
-    }
-    x = xn;
-    u_j = u_next;
-    c_ctrl = c_next;
   }
-  const float Sk = S.s;
-  if (active && q == 0) a.sample_costs[(size_t)e * a.K + k] = Sk;
-
-  float m = warp_min(active ? Sk : INFINITY);
-  if (lane == 0) s_red[wid] = m;
+  m.cost[wid * QS + lane] = S;
   __syncthreads();
-  float rho = s_red[0];
-#pragma unroll
-  for (int w = 1; w < NW; ++w) rho = fminf(rho, s_red[w]);
-  __syncthreads();
+  const float Sk = ((m.cost[lane] + m.cost[QS + lane]) + m.cost[2 * QS + lane]) + m.cost[3 * QS + lane];
+  if (active && wid == 0) a.sample_costs[(size_t)e * a.K + k] = Sk;
+  // every warp: rho_b = min S, w_k = exp(-(S_k - rho_b)/lambda), eta_b = sum w_k
+  const float rho = warp_min(active ? Sk : INFINITY);
   const float wk = active ? expf((rho - Sk) * a.inv_lambda) : 0.0f;
-  const float ws = warp_sum(q == 0 ? wk : 0.0f);
-  if (lane == 0) s_red[wid] = ws;
-
-  // W_b[j][q] = sum over the CTA's samples of w_k du_k[j][q]
-  for (int j = 0; j < T; ++j) {
-    float du;
-    if (dUf) {
-      du = active ? __ldcs(dUf + (size_t)j * a.K * 4) : 0.0f;
-    } else {
-      const float4 un = s_un[j];
-      const float4 d = noise_delta(k, j, e, ctr3, a.key0, a.key1, sigma);
-      const float4 u = clamp4(make_float4(un.x + d.x, un.y + d.y, un.z + d.z, un.w + d.w), umin, umax);
-      du = active ? (q == 0 ? u.x - un.x : q == 1 ? u.y - un.y : q == 2 ? u.z - un.z : u.w - un.w) : 0.0f;
-    }
-    float v = wk * du;
-    v += __shfl_xor_sync(0xffffffffu, v, 4);
-    v += __shfl_xor_sync(0xffffffffu, v, 8);
-    v += __shfl_xor_sync(0xffffffffu, v, 16);
-    if (lane < 4) reinterpret_cast<float*>(&s_w[wid][j])[lane] = v;
-  }
-  __syncthreads();
+  const float eta = warp_sum(wk);
   float* out = a.partials + ((size_t)e * a.nb + b) * (4 + 4 * T);
   if (tid == 0) {
-    float eta = 0.0f;
-#pragma unroll
-    for (int w = 0; w < NW; ++w) eta += s_red[w];
     out[0] = rho;
     out[1] = eta;
   }
-  for (int i = tid; i < 4 * T; i += NT) {
-    const int j = i >> 2, cc = i & 3;
-    float sum = 0.0f;
-#pragma unroll
-    for (int w = 0; w < NW; ++w) sum += reinterpret_cast<const float*>(&s_w[w][j])[cc];
-    out[4 + i] = sum;
+  // W_b[j] = sum_k w_k du_k[j], warp w the steps j = w (mod 4)
+  for (int j = wid; j < T; j += NW) {
+    const float4 u = m.u[j * QS + lane], un = m.un[j];
+    const float4 du = active ? make_float4(u.x - un.x, u.y - un.y, u.z - un.z, u.w - un.w)
+                             : make_float4(0.f, 0.f, 0.f, 0.f);
+    const float r = warp_sum4(wk * du.x, wk * du.y, wk * du.z, wk * du.w, lane);
+    if ((lane & 7) == 0) out[4 + 4 * j + (lane >> 3)] = r;
   }
+  __syncthreads();  // shared memory free for the next unit
 }
 
 // ---------------------------------------------------------------------------
@@ -564,9 +630,9 @@ __global__ void __launch_bounds__(NT) k_rollout(RolloutArgs a) {
   rollout_unit(a, blockIdx.y, blockIdx.x, a.ctr3);
 }
 
-__global__ void __launch_bounds__(NT) k_rollout_quad(RolloutArgs a) {
+__global__ void __launch_bounds__(NT) k_rollout_split(RolloutArgs a) {
   pdl_start();
-  rollout_quad_unit(a, blockIdx.y, blockIdx.x, a.ctr3);
+  rollout_split_unit(a, blockIdx.y, blockIdx.x, a.ctr3);
 }
 
 // The single-planner update reads its arguments from shared memory, as the
@@ -626,7 +692,7 @@ __global__ void __launch_bounds__(NT, kMinCtas) k_b_rollout(BatchView v, int it,
       if (kLanes == 1)
         rollout_unit(s_a, e, b, s_a.ctr3 | (uint32_t)it);
       else
-        rollout_quad_unit(s_a, e, b, s_a.ctr3 | (uint32_t)it);
+        rollout_split_unit(s_a, e, b, s_a.ctr3 | (uint32_t)it);
     }
     if (!dynamic) u += gridDim.x;
     __syncthreads();  // the unit's shared memory is free again
@@ -702,9 +768,29 @@ cudaError_t launch_cost_grad(const CostGradArgs& a, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-cudaError_t batch_rollout_occupancy(int out[4]) {
-  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(out + 0, k_b_rollout<1, 5>, NT, 0);
-  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(out + 1, k_b_rollout<4, 4>, NT, 0);
+// The split pass reads its shared memory as one dynamic block sized for the
+// horizon; allow the largest (once per process).
+cudaError_t split_attributes() {
+  static const cudaError_t e = [] {
+    const int most = (int)split_smem_bytes(kMaxT);
+    cudaError_t r = cudaFuncSetAttribute(k_rollout_split, cudaFuncAttributeMaxDynamicSharedMemorySize, most);
+    // few CTAs per SM run the single-planner pass and its candidate scans
+    // live on L1 hits: ask for the smaller shared-memory carveout
+    if (r == cudaSuccess)
+      r = cudaFuncSetAttribute(k_rollout_split, cudaFuncAttributePreferredSharedMemoryCarveout, 50);
+    if (r == cudaSuccess)
+      r = cudaFuncSetAttribute(k_b_rollout<4, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, most);
+    return r;
+  }();
+  return e;
+}
+
+cudaError_t batch_rollout_occupancy(int out[4], int T_max) {
+  cudaError_t e = split_attributes();
+  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(out + 0, k_b_rollout<1, 5>, NT, 0);
+  if (e == cudaSuccess)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(out + 1, k_b_rollout<4, 4>, NT,
+                                                      split_smem_bytes(T_max));
   if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(out + 2, k_b_update, UT, 0);
   if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(out + 3, k_b_rollout<1, 6>, NT, 0);
   for (int i = 0; i < 4; ++i)
@@ -714,7 +800,9 @@ cudaError_t batch_rollout_occupancy(int out[4]) {
 
 cudaError_t launch_batch_rollout(const BatchView& v, int lanes, int it, int blocks, int dynamic,
                                  int six, cudaStream_t s) {
-  if (lanes == 4) return launch_k(k_b_rollout<4, 4>, dim3(blocks), dim3(NT), s, true, v, it, dynamic);
+  if (lanes == 4)
+    return launch_ks(k_b_rollout<4, 4>, dim3(blocks), dim3(NT), split_smem_bytes(v.T_max), s, true, v,
+                     it, dynamic);
   if (six) return launch_k(k_b_rollout<1, 6>, dim3(blocks), dim3(NT), s, true, v, it, dynamic);
   return launch_k(k_b_rollout<1, 5>, dim3(blocks), dim3(NT), s, true, v, it, dynamic);
 }
@@ -725,7 +813,11 @@ cudaError_t launch_batch_update(const BatchView& v, int it, int blocks, cudaStre
 
 cudaError_t launch_rollout(const RolloutArgs& a, cudaStream_t s) {
   dim3 grid(a.nb, a.E);
-  if (a.lanes_per_sample == 4) return launch_k(k_rollout_quad, grid, dim3(NT), s, true, a);
+  if (a.lanes_per_sample == 4) {
+    const cudaError_t e = split_attributes();
+    if (e != cudaSuccess) return e;
+    return launch_ks(k_rollout_split, grid, dim3(NT), split_smem_bytes(a.T), s, true, a);
+  }
   return launch_k(k_rollout, grid, dim3(NT), s, true, a);
 }
 
