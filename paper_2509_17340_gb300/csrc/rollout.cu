@@ -7,6 +7,7 @@
 // merges the per-CTA partials (log-sum-exp rescaling by the global minimum),
 // updates the nominal (Eq. mppi_update_simplified), and on the last iteration
 // runs Stage II and the selection.
+#include <atomic>
 #include <cfloat>
 #include <cstdint>
 
@@ -187,29 +188,32 @@ __device__ __forceinline__ void rollout_unit(const RolloutArgs& a, int e, int b,
 // ---------------------------------------------------------------------------
 // The Stage I pass for problems too small to fill the GPU with one lane per
 // sample, split into phases so that only the dynamics stays sequential: 32
-// samples per CTA (four threads per sample, one in each warp); the horizon
-// in chunks of at most kChunk steps.
+// samples per CTA (eight threads per sample, one in each of its eight warps);
+// the horizon in chunks of at most kChunk steps.
 //   noise    the perturbations of every step, drawn one chunk ahead (the
-//            first chunk by all warps, the next ones by warps 1-3 while warp
-//            0 integrates); the clamped controls stay in shared memory for
-//            the whole horizon;
-//   dynamics warp 0, one lane per sample, applies the chunk's controls with
-//            RK4 and adds the control and state cost terms; the positions go
-//            to shared memory;
+//            first chunk by all warps, the next ones by the seven warps that
+//            do not integrate); the clamped controls stay in shared memory
+//            for the whole horizon;
+//   dynamics one warp, one lane per sample, applies the chunk's controls with
+//            RK4; the states go to shared memory (this is the only serial
+//            chain, so nothing else runs in it);
 //   queries  every (sample, step) of the chunk looks up its cell; the
 //            non-empty candidate lists are cut into items of kItem entries
 //            and the CTA's threads take the items in turn, each folding its
 //            squared distances into the query's minimum with a shared-memory
 //            atomic minimum (exact in any order).  A warp therefore scans
 //            items, not its longest lane's list: the lists of one step's
-//            samples are mostly empty, with a few of up to a hundred entries.
+//            samples are mostly empty, with a few of up to a hundred entries;
+//   costs    every (sample, step) pair's control, state and collision terms.
 // Then the per-CTA minimum, weights and weighted perturbation sums as in the
 // one-lane pass: every warp holds the 32 samples' costs and reduces them
 // itself.
 // ---------------------------------------------------------------------------
-constexpr int QS = NT / 4;       // samples per CTA
-constexpr int kChunk = 32;       // steps per chunk
-constexpr int kQ = kChunk / NW;  // queries per thread and chunk, at most
+constexpr int ST = 256;          // threads per CTA (eight per sample)
+constexpr int SW = ST / 32;      // warps per CTA
+constexpr int QS = 32;           // samples per CTA
+constexpr int kChunk = 20;       // steps per chunk
+constexpr int kQ = (kChunk + SW - 1) / SW;  // queries per thread and chunk, at most
 constexpr int kItem = 8;         // candidate entries per scan item
 constexpr int kChunkQ = kChunk * QS;
 
@@ -218,11 +222,11 @@ __host__ __device__ constexpr size_t split_smem_bytes(int T) {
   return 16 * (size_t)T * QS       // u: clamped controls [T][QS]
          + 16 * (size_t)T          // un: nominal [T]
          + 8 * (size_t)kChunkQ     // qrange: candidate range of each listed query
-         + 4 * (size_t)kChunkQ * 3 // pc: positions [kChunk][3][QS]
+         + 4 * (size_t)kChunkQ * 10  // xs: states x_{j+1} [kChunk][10][QS]
          + 4 * (size_t)kChunkQ     // d2: squared distance bits [kChunk][QS]
-         + 4 * (size_t)NW * QS     // cost: partial sums [NW][QS]
+         + 4 * (size_t)SW * QS     // cost: partial sums [SW][QS]
          + 4 * (size_t)(kChunkQ + 2)  // qitem: first item of each listed query (+ pad)
-         + 4 * (size_t)NW * 2      // scan: warp totals
+         + 4 * (size_t)SW * 2      // scan: warp totals
          + 12 * (size_t)T          // gd: guides [T][3]
          + 2 * (size_t)kChunkQ;    // qslot: (step, sample) slot of each listed query
 }
@@ -231,7 +235,7 @@ struct SplitSmem {
   float4* u;
   float4* un;
   int2* qrange;
-  float* pc;
+  float* xs;
   int* d2;
   float* cost;
   int* qitem;
@@ -245,12 +249,12 @@ __device__ __forceinline__ SplitSmem split_layout(unsigned char* base, int T) {
   m.u = reinterpret_cast<float4*>(base);
   m.un = m.u + (size_t)T * QS;
   m.qrange = reinterpret_cast<int2*>(m.un + T);
-  m.pc = reinterpret_cast<float*>(m.qrange + kChunkQ);
-  m.d2 = reinterpret_cast<int*>(m.pc + 3 * kChunkQ);
+  m.xs = reinterpret_cast<float*>(m.qrange + kChunkQ);
+  m.d2 = reinterpret_cast<int*>(m.xs + 10 * kChunkQ);
   m.cost = reinterpret_cast<float*>(m.d2 + kChunkQ);
-  m.qitem = reinterpret_cast<int*>(m.cost + NW * QS);
+  m.qitem = reinterpret_cast<int*>(m.cost + SW * QS);
   m.scan = reinterpret_cast<int2*>(m.qitem + kChunkQ + 1 + 1);  // +1 word keeps int2 aligned
-  m.gd = reinterpret_cast<float*>(m.scan + NW);
+  m.gd = reinterpret_cast<float*>(m.scan + SW);
   m.qslot = reinterpret_cast<unsigned short*>(m.gd + 3 * T);
   return m;
 }
@@ -272,7 +276,7 @@ __device__ __forceinline__ int2 block_scan2(int2 v, int2* warp_tot, int2& total)
   int2 before = make_int2(0, 0);
   total = make_int2(0, 0);
 #pragma unroll
-  for (int w = 0; w < NW; ++w) {
+  for (int w = 0; w < SW; ++w) {
     const int2 t = warp_tot[w];
     if (w < wid) {
       before.x += t.x;
@@ -290,8 +294,8 @@ __device__ __forceinline__ void rollout_split_unit(const RolloutArgs& a, int e, 
   const int T = a.T;
   const SplitSmem m = split_layout(split_smem, T);
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-  for (int i = tid; i < T; i += NT) m.un[i] = reinterpret_cast<const float4*>(a.u_nom)[e * T + i];
-  for (int i = tid; i < 3 * T; i += NT) m.gd[i] = a.guides[e * T * 3 + i];
+  for (int i = tid; i < T; i += ST) m.un[i] = reinterpret_cast<const float4*>(a.u_nom)[e * T + i];
+  for (int i = tid; i < 3 * T; i += ST) m.gd[i] = a.guides[e * T * 3 + i];
 
   const int k = b * QS + lane;  // this thread's sample in every phase
   const bool active = k < a.K;
@@ -321,43 +325,34 @@ __device__ __forceinline__ void rollout_split_unit(const RolloutArgs& a, int e, 
   for (int i = 0; i < 4; ++i) x.q[i] = a.x0[3 + i];
 #pragma unroll
   for (int i = 0; i < 3; ++i) x.v[i] = a.x0[7 + i];
-  if (dbg >= 0 && wid == 0) {
+  // the integrating warp rotates with the block index, so that the
+  // integrators of the CTAs sharing an SM sit on different schedulers
+  const int wint = b & (SW - 1);
+  if (dbg >= 0 && wid == wint) {
     float* X = a.dbg_x + (size_t)dbg * (T + 1) * 10;
     for (int i = 0; i < 10; ++i) X[i] = a.x0[i];
   }
-  float4 u_prev = make_float4(0.f, 0.f, 0.f, 0.f);
-  float S = 0.0f;  // warp 0: control and state terms; every warp: its queries' collision terms
+  float S = 0.0f;  // every thread: the cost terms of its (sample, step) pairs
 
   __syncthreads();  // un, gd
-  noise(0, tcb < T ? tcb : T, wid, NW);
+  noise(0, tcb < T ? tcb : T, wid, SW);
   __syncthreads();
   for (int j0 = 0; j0 < T; j0 += tcb) {
     const int tc = tcb < T - j0 ? tcb : T - j0;
-    if (wid == 0) {
+    if (wid == wint) {
+      float4 u_nx = m.u[j0 * QS + lane];
       for (int jj = 0; jj < tc; ++jj) {
         const int j = j0 + jj;
-        const float4 u = m.u[j * QS + lane];
-        // J_ctrl: Q_c |u_j|^2 (j <= T-2) and Q_cd |u_j - u_{j-1}|^2 (1 <= j <= T-2)
-        float c = 0.0f;
-        if (j <= T - 2) {
-          c = cp.Q_c * (u.x * u.x + u.y * u.y + u.z * u.z + u.w * u.w);
-          if (j >= 1) {
-            const float ax = u.x - u_prev.x, ay = u.y - u_prev.y, az = u.z - u_prev.z,
-                        aw = u.w - u_prev.w;
-            c += cp.Q_cd * (ax * ax + ay * ay + az * az + aw * aw);
-          }
-        }
-        u_prev = u;
+        const float4 u = u_nx;
+        if (jj + 1 < tc) u_nx = m.u[(j + 1) * QS + lane];  // one step ahead
         rk4_step(x, u, a.dyn);
-        // state terms at x_{j+1} against the guide at t = (j + 1) dt
-        const float gx = m.gd[3 * j], gy = m.gd[3 * j + 1], gz = m.gd[3 * j + 2];
-        c += cp.Q_track * norm3f(x.p[0] - gx, x.p[1] - gy, x.p[2] - gz);
-        c += cp.Q_vnorm * (x.v[0] * x.v[0] + x.v[1] * x.v[1] + x.v[2] * x.v[2]);
-        c += goal_term(x, cp);
-        S += c;
-        m.pc[(jj * 3 + 0) * QS + lane] = x.p[0];
-        m.pc[(jj * 3 + 1) * QS + lane] = x.p[1];
-        m.pc[(jj * 3 + 2) * QS + lane] = x.p[2];
+        float* X = m.xs + jj * 10 * QS + lane;
+#pragma unroll
+        for (int i = 0; i < 3; ++i) X[i * QS] = x.p[i];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) X[(3 + i) * QS] = x.q[i];
+#pragma unroll
+        for (int i = 0; i < 3; ++i) X[(7 + i) * QS] = x.v[i];
         if (dbg >= 0) {
           reinterpret_cast<float4*>(a.dbg_u)[(size_t)dbg * T + j] = u;
           float* X = a.dbg_x + ((size_t)dbg * (T + 1) + j + 1) * 10;
@@ -367,22 +362,22 @@ __device__ __forceinline__ void rollout_split_unit(const RolloutArgs& a, int e, 
         }
       }
     } else if (j0 + tc < T) {
-      noise(j0 + tc, tcb < T - j0 - tc ? tcb : T - j0 - tc, wid - 1, NW - 1);
+      noise(j0 + tc, tcb < T - j0 - tc ? tcb : T - j0 - tc, ((wid - wint) & (SW - 1)) - 1, SW - 1);
     }
-    __syncthreads();  // pc filled; the next chunk's controls drawn
+    __syncthreads();  // xs filled; the next chunk's controls drawn
 
-    // this thread's queries: steps jj = wid + 4 i of the chunk, sample `lane`
+    // this thread's queries: steps jj = wid + 8 i of the chunk, sample `lane`
     int2 rg[kQ];
     int2 cnt = make_int2(0, 0);  // (listed queries, items)
 #pragma unroll
     for (int i = 0; i < kQ; ++i) {
-      const int jj = wid + NW * i;
+      const int jj = wid + SW * i;
       rg[i] = make_int2(0, 0);
       if (jj < tc) {
         m.d2[jj * QS + lane] = __float_as_int(dmax2);
         if (active)
-          rg[i] = cell_range(m.pc[(jj * 3) * QS + lane], m.pc[(jj * 3 + 1) * QS + lane],
-                             m.pc[(jj * 3 + 2) * QS + lane], a.grid);
+          rg[i] = cell_range(m.xs[(jj * 10) * QS + lane], m.xs[(jj * 10 + 1) * QS + lane],
+                             m.xs[(jj * 10 + 2) * QS + lane], a.grid);
       }
       if (rg[i].y > 0) {
         cnt.x += 1;
@@ -396,14 +391,14 @@ __device__ __forceinline__ void rollout_split_unit(const RolloutArgs& a, int e, 
       if (rg[i].y > 0) {
         m.qitem[off.x] = off.y;
         m.qrange[off.x] = rg[i];
-        m.qslot[off.x] = (unsigned short)((wid + NW * i) * QS + lane);
+        m.qslot[off.x] = (unsigned short)((wid + SW * i) * QS + lane);
         off.x += 1;
         off.y += (rg[i].y + kItem - 1) / kItem;
       }
     }
     if (tid == 0) m.qitem[total.x] = total.y;
     __syncthreads();  // query list complete
-    for (int it = tid; it < total.y; it += NT) {
+    for (int it = tid; it < total.y; it += ST) {
       // the listed query holding item `it`: largest q with qitem[q] <= it
       int lo = 0, hi = total.x - 1;
       while (lo < hi) {
@@ -415,25 +410,54 @@ __device__ __forceinline__ void rollout_split_unit(const RolloutArgs& a, int e, 
       const int jj = slot / QS, sl = slot % QS;
       const int first = (it - m.qitem[lo]) * kItem;
       const int n = r.y - first < kItem ? r.y - first : kItem;
-      const float d2 = scan_min<kItem>(a.grid.pts + r.x + first, n, m.pc[(jj * 3) * QS + sl],
-                                       m.pc[(jj * 3 + 1) * QS + sl], m.pc[(jj * 3 + 2) * QS + sl],
+      const float d2 = scan_min<kItem>(a.grid.pts + r.x + first, n, m.xs[(jj * 10) * QS + sl],
+                                       m.xs[(jj * 10 + 1) * QS + sl], m.xs[(jj * 10 + 2) * QS + sl],
                                        dmax2);
       if (d2 < dmax2) atomicMin(m.d2 + slot, __float_as_int(d2));  // non-negative: int order
     }
-    __syncthreads();  // minima complete; pc free for the next chunk
+    __syncthreads();  // minima complete
+    // the cost of every (sample, step) pair of this thread: J_ctrl's terms
+    // Q_c |u_j|^2 (j <= T-2) and Q_cd |u_j - u_{j-1}|^2 (1 <= j <= T-2), the
+    // state terms at x_{j+1} against the guide at t = (j + 1) dt, J_col
 #pragma unroll
     for (int i = 0; i < kQ; ++i) {
-      const int jj = wid + NW * i;
+      const int jj = wid + SW * i, j = j0 + jj;
       if (jj < tc && active) {
+        const float4 u = m.u[j * QS + lane];
+        float c = 0.0f;
+        if (j <= T - 2) {
+          c = cp.Q_c * (u.x * u.x + u.y * u.y + u.z * u.z + u.w * u.w);
+          if (j >= 1) {
+            const float4 up = m.u[(j - 1) * QS + lane];
+            const float ax = u.x - up.x, ay = u.y - up.y, az = u.z - up.z, aw = u.w - up.w;
+            c += cp.Q_cd * (ax * ax + ay * ay + az * az + aw * aw);
+          }
+        }
+        State y;
+        const float* X = m.xs + jj * 10 * QS + lane;
+#pragma unroll
+        for (int t = 0; t < 3; ++t) y.p[t] = X[t * QS];
+#pragma unroll
+        for (int t = 0; t < 4; ++t) y.q[t] = X[(3 + t) * QS];
+#pragma unroll
+        for (int t = 0; t < 3; ++t) y.v[t] = X[(7 + t) * QS];
+        const float gx = m.gd[3 * j], gy = m.gd[3 * j + 1], gz = m.gd[3 * j + 2];
+        c += cp.Q_track * norm3f(y.p[0] - gx, y.p[1] - gy, y.p[2] - gz);
+        c += cp.Q_vnorm * (y.v[0] * y.v[0] + y.v[1] * y.v[1] + y.v[2] * y.v[2]);
+        c += goal_term(y, cp);
         const float d2 = __int_as_float(m.d2[jj * QS + lane]);
-        S += jcol_from_d2(d2, cp, dmax2);
-        if (dbg >= 0) a.dbg_d[(size_t)dbg * T + j0 + jj] = d2 < dmax2 ? sqrtf(d2) : INFINITY;
+        c += jcol_from_d2(d2, cp, dmax2);
+        S += c;
+        if (dbg >= 0) a.dbg_d[(size_t)dbg * T + j] = d2 < dmax2 ? sqrtf(d2) : INFINITY;
       }
     }
+    __syncthreads();  // xs free for the next chunk
   }
   m.cost[wid * QS + lane] = S;
   __syncthreads();
-  const float Sk = ((m.cost[lane] + m.cost[QS + lane]) + m.cost[2 * QS + lane]) + m.cost[3 * QS + lane];
+  float Sk = 0.0f;  // the warps' partial sums in a fixed order
+#pragma unroll
+  for (int w = 0; w < SW; ++w) Sk += m.cost[w * QS + lane];
   if (active && wid == 0) a.sample_costs[(size_t)e * a.K + k] = Sk;
   // every warp: rho_b = min S, w_k = exp(-(S_k - rho_b)/lambda), eta_b = sum w_k
   const float rho = warp_min(active ? Sk : INFINITY);
@@ -444,8 +468,8 @@ __device__ __forceinline__ void rollout_split_unit(const RolloutArgs& a, int e, 
     out[0] = rho;
     out[1] = eta;
   }
-  // W_b[j] = sum_k w_k du_k[j], warp w the steps j = w (mod 4)
-  for (int j = wid; j < T; j += NW) {
+  // W_b[j] = sum_k w_k du_k[j], warp w the steps j = w (mod 8)
+  for (int j = wid; j < T; j += SW) {
     const float4 u = m.u[j * QS + lane], un = m.un[j];
     const float4 du = active ? make_float4(u.x - un.x, u.y - un.y, u.z - un.z, u.w - un.w)
                              : make_float4(0.f, 0.f, 0.f, 0.f);
@@ -630,7 +654,7 @@ __global__ void __launch_bounds__(NT) k_rollout(RolloutArgs a) {
   rollout_unit(a, blockIdx.y, blockIdx.x, a.ctr3);
 }
 
-__global__ void __launch_bounds__(NT) k_rollout_split(RolloutArgs a) {
+__global__ void __launch_bounds__(ST) k_rollout_split(RolloutArgs a) {
   pdl_start();
   rollout_split_unit(a, blockIdx.y, blockIdx.x, a.ctr3);
 }
@@ -655,7 +679,8 @@ __global__ void __launch_bounds__(UT) k_update(UpdateArgs a) {
 // count is at most `it` skip their units.
 // ---------------------------------------------------------------------------
 template <int kLanes, int kMinCtas>
-__global__ void __launch_bounds__(NT, kMinCtas) k_b_rollout(BatchView v, int it, int dynamic) {
+__global__ void __launch_bounds__(kLanes == 4 ? ST : NT, kMinCtas)
+    k_b_rollout(BatchView v, int it, int dynamic) {
   pdl_start();
   __shared__ long long s_pre[kBatchMax + 1];
   __shared__ int s_order[kBatchMax];
@@ -665,7 +690,7 @@ __global__ void __launch_bounds__(NT, kMinCtas) k_b_rollout(BatchView v, int it,
   const int n = v.n;
   load_prefix(s_pre, v.pre + (kLanes == 1 ? kPreRoll1 : kPreRoll4) * (n + 1), n);
   const int* order = kLanes == 1 ? v.order1 : v.order4;
-  for (int i = threadIdx.x; i < n; i += NT) s_order[i] = __ldg(order + i);
+  for (int i = threadIdx.x; i < n; i += blockDim.x) s_order[i] = __ldg(order + i);
   unsigned int* queue = v.queue + (kLanes == 1 ? 0 : 2);
   __syncthreads();
   const long long total = s_pre[n];
@@ -689,7 +714,7 @@ __global__ void __launch_bounds__(NT, kMinCtas) k_b_rollout(BatchView v, int it,
     if (it < s_iters) {
       const long long l = u - s_pre[pos];
       const int e = (int)(l / s_a.nb), b = (int)(l % s_a.nb);
-      if (kLanes == 1)
+      if constexpr (kLanes == 1)
         rollout_unit(s_a, e, b, s_a.ctr3 | (uint32_t)it);
       else
         rollout_split_unit(s_a, e, b, s_a.ctr3 | (uint32_t)it);
@@ -774,14 +799,25 @@ cudaError_t split_attributes() {
   static const cudaError_t e = [] {
     const int most = (int)split_smem_bytes(kMaxT);
     cudaError_t r = cudaFuncSetAttribute(k_rollout_split, cudaFuncAttributeMaxDynamicSharedMemorySize, most);
-    // few CTAs per SM run the single-planner pass and its candidate scans
-    // live on L1 hits: ask for the smaller shared-memory carveout
     if (r == cudaSuccess)
-      r = cudaFuncSetAttribute(k_rollout_split, cudaFuncAttributePreferredSharedMemoryCarveout, 50);
-    if (r == cudaSuccess)
-      r = cudaFuncSetAttribute(k_b_rollout<4, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, most);
+      r = cudaFuncSetAttribute(k_b_rollout<4, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, most);
     return r;
   }();
+  return e;
+}
+
+// Few CTAs per SM run the single-planner split pass and its candidate scans
+// live on L1 hits: the carveout asked for is the smallest that still holds
+// two of its CTAs (as a percentage of the 228 KB an SM can give).
+cudaError_t split_carveout(int T) {
+  static std::atomic<int> current{-1};
+  const size_t need = 2 * (split_smem_bytes(T) + 1024);
+  int pct = (int)((need * 100 + 228 * 1024 - 1) / (228 * 1024));
+  if (pct > 100) pct = 100;
+  if (current.load() == pct) return cudaSuccess;
+  const cudaError_t e =
+      cudaFuncSetAttribute(k_rollout_split, cudaFuncAttributePreferredSharedMemoryCarveout, pct);
+  if (e == cudaSuccess) current.store(pct);
   return e;
 }
 
@@ -789,7 +825,7 @@ cudaError_t batch_rollout_occupancy(int out[4], int T_max) {
   cudaError_t e = split_attributes();
   if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(out + 0, k_b_rollout<1, 5>, NT, 0);
   if (e == cudaSuccess)
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(out + 1, k_b_rollout<4, 4>, NT,
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(out + 1, k_b_rollout<4, 2>, ST,
                                                       split_smem_bytes(T_max));
   if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(out + 2, k_b_update, UT, 0);
   if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(out + 3, k_b_rollout<1, 6>, NT, 0);
@@ -801,7 +837,7 @@ cudaError_t batch_rollout_occupancy(int out[4], int T_max) {
 cudaError_t launch_batch_rollout(const BatchView& v, int lanes, int it, int blocks, int dynamic,
                                  int six, cudaStream_t s) {
   if (lanes == 4)
-    return launch_ks(k_b_rollout<4, 4>, dim3(blocks), dim3(NT), split_smem_bytes(v.T_max), s, true, v,
+    return launch_ks(k_b_rollout<4, 2>, dim3(blocks), dim3(ST), split_smem_bytes(v.T_max), s, true, v,
                      it, dynamic);
   if (six) return launch_k(k_b_rollout<1, 6>, dim3(blocks), dim3(NT), s, true, v, it, dynamic);
   return launch_k(k_b_rollout<1, 5>, dim3(blocks), dim3(NT), s, true, v, it, dynamic);
@@ -814,9 +850,10 @@ cudaError_t launch_batch_update(const BatchView& v, int it, int blocks, cudaStre
 cudaError_t launch_rollout(const RolloutArgs& a, cudaStream_t s) {
   dim3 grid(a.nb, a.E);
   if (a.lanes_per_sample == 4) {
-    const cudaError_t e = split_attributes();
+    cudaError_t e = split_attributes();
+    if (e == cudaSuccess) e = split_carveout(a.T);
     if (e != cudaSuccess) return e;
-    return launch_ks(k_rollout_split, grid, dim3(NT), split_smem_bytes(a.T), s, true, a);
+    return launch_ks(k_rollout_split, grid, dim3(ST), split_smem_bytes(a.T), s, true, a);
   }
   return launch_k(k_rollout, grid, dim3(NT), s, true, a);
 }
