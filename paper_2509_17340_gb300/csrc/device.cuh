@@ -198,19 +198,20 @@ __device__ __forceinline__ float nn_dist2(float px, float py, float pz, const Gr
   return scan_min(g.pts + r.x, r.y, px, py, pz, dmax2);
 }
 
-// Asynchronous 16-byte global -> shared copy (cp.async, cached in L1).
-__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
-  const unsigned dst = static_cast<unsigned>(__cvta_generic_to_shared(smem));
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 16;\n" ::"r"(dst), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
 // Piecewise collision penalty from a squared distance (d >= d_max -> 0).
 __device__ __forceinline__ float jcol_from_d2(float d2, const CostParams& c, float dmax2) {
   if (!(d2 < dmax2)) return 0.0f;
   const float d = sqrtf(d2);
   return d < c.d_min ? c.C_col : c.C_col * expf(-c.a_col * (d - c.d_min));
+}
+
+// The same value computed without branches (both outcomes evaluated), for
+// code that interleaves several independent evaluations.
+__device__ __forceinline__ float jcol_select(float d2, const CostParams& c, float dmax2) {
+  const float d = sqrtf(d2);
+  const float ex = c.C_col * expf(-c.a_col * (d - c.d_min));
+  return d2 < dmax2 ? (d < c.d_min ? c.C_col : ex) : 0.0f;
 }
 
 // ||R(q) R(q_g)^T - I||_F = 2 sqrt(2) |vec(q (x) conj(q_g))| for unit quaternions.

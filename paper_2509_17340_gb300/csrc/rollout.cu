@@ -222,7 +222,7 @@ __host__ __device__ constexpr size_t split_smem_bytes(int T) {
   return 16 * (size_t)T * QS       // u: clamped controls [T][QS]
          + 16 * (size_t)T          // un: nominal [T]
          + 8 * (size_t)kChunkQ     // qrange: candidate range of each listed query
-         + 4 * (size_t)kChunkQ * 10  // xs: states x_{j+1} [kChunk][10][QS]
+         + 40 * (size_t)kChunkQ    // xa, xb, xc: states x_{j+1} [kChunk][QS]
          + 4 * (size_t)kChunkQ     // d2: squared distance bits [kChunk][QS]
          + 4 * (size_t)SW * QS     // cost: partial sums [SW][QS]
          + 4 * (size_t)(kChunkQ + 2)  // qitem: first item of each listed query (+ pad)
@@ -235,7 +235,9 @@ struct SplitSmem {
   float4* u;
   float4* un;
   int2* qrange;
-  float* xs;
+  float4* xa;  // p, q0
+  float4* xb;  // q1, q2, q3, v0
+  float2* xc;  // v1, v2
   int* d2;
   float* cost;
   int* qitem;
@@ -249,8 +251,10 @@ __device__ __forceinline__ SplitSmem split_layout(unsigned char* base, int T) {
   m.u = reinterpret_cast<float4*>(base);
   m.un = m.u + (size_t)T * QS;
   m.qrange = reinterpret_cast<int2*>(m.un + T);
-  m.xs = reinterpret_cast<float*>(m.qrange + kChunkQ);
-  m.d2 = reinterpret_cast<int*>(m.xs + 10 * kChunkQ);
+  m.xa = reinterpret_cast<float4*>(m.qrange + kChunkQ);
+  m.xb = m.xa + kChunkQ;
+  m.xc = reinterpret_cast<float2*>(m.xb + kChunkQ);
+  m.d2 = reinterpret_cast<int*>(m.xc + kChunkQ);
   m.cost = reinterpret_cast<float*>(m.d2 + kChunkQ);
   m.qitem = reinterpret_cast<int*>(m.cost + SW * QS);
   m.scan = reinterpret_cast<int2*>(m.qitem + kChunkQ + 1 + 1);  // +1 word keeps int2 aligned
@@ -346,13 +350,9 @@ __device__ __forceinline__ void rollout_split_unit(const RolloutArgs& a, int e, 
         const float4 u = u_nx;
         if (jj + 1 < tc) u_nx = m.u[(j + 1) * QS + lane];  // one step ahead
         rk4_step(x, u, a.dyn);
-        float* X = m.xs + jj * 10 * QS + lane;
-#pragma unroll
-        for (int i = 0; i < 3; ++i) X[i * QS] = x.p[i];
-#pragma unroll
-        for (int i = 0; i < 4; ++i) X[(3 + i) * QS] = x.q[i];
-#pragma unroll
-        for (int i = 0; i < 3; ++i) X[(7 + i) * QS] = x.v[i];
+        m.xa[jj * QS + lane] = make_float4(x.p[0], x.p[1], x.p[2], x.q[0]);
+        m.xb[jj * QS + lane] = make_float4(x.q[1], x.q[2], x.q[3], x.v[0]);
+        m.xc[jj * QS + lane] = make_float2(x.v[1], x.v[2]);
         if (dbg >= 0) {
           reinterpret_cast<float4*>(a.dbg_u)[(size_t)dbg * T + j] = u;
           float* X = a.dbg_x + ((size_t)dbg * (T + 1) + j + 1) * 10;
@@ -364,7 +364,7 @@ __device__ __forceinline__ void rollout_split_unit(const RolloutArgs& a, int e, 
     } else if (j0 + tc < T) {
       noise(j0 + tc, tcb < T - j0 - tc ? tcb : T - j0 - tc, ((wid - wint) & (SW - 1)) - 1, SW - 1);
     }
-    __syncthreads();  // xs filled; the next chunk's controls drawn
+    __syncthreads();  // states filled; the next chunk's controls drawn
 
     // this thread's queries: steps jj = wid + 8 i of the chunk, sample `lane`
     int2 rg[kQ];
@@ -375,9 +375,10 @@ __device__ __forceinline__ void rollout_split_unit(const RolloutArgs& a, int e, 
       rg[i] = make_int2(0, 0);
       if (jj < tc) {
         m.d2[jj * QS + lane] = __float_as_int(dmax2);
-        if (active)
-          rg[i] = cell_range(m.xs[(jj * 10) * QS + lane], m.xs[(jj * 10 + 1) * QS + lane],
-                             m.xs[(jj * 10 + 2) * QS + lane], a.grid);
+        if (active) {
+          const float4 xa = m.xa[jj * QS + lane];
+          rg[i] = cell_range(xa.x, xa.y, xa.z, a.grid);
+        }
       }
       if (rg[i].y > 0) {
         cnt.x += 1;
@@ -407,51 +408,47 @@ __device__ __forceinline__ void rollout_split_unit(const RolloutArgs& a, int e, 
       }
       const int2 r = m.qrange[lo];
       const int slot = m.qslot[lo];
-      const int jj = slot / QS, sl = slot % QS;
       const int first = (it - m.qitem[lo]) * kItem;
       const int n = r.y - first < kItem ? r.y - first : kItem;
-      const float d2 = scan_min<kItem>(a.grid.pts + r.x + first, n, m.xs[(jj * 10) * QS + sl],
-                                       m.xs[(jj * 10 + 1) * QS + sl], m.xs[(jj * 10 + 2) * QS + sl],
-                                       dmax2);
+      const float4 xa = m.xa[slot];
+      const float d2 = scan_min<kItem>(a.grid.pts + r.x + first, n, xa.x, xa.y, xa.z, dmax2);
       if (d2 < dmax2) atomicMin(m.d2 + slot, __float_as_int(d2));  // non-negative: int order
     }
     __syncthreads();  // minima complete
     // the cost of every (sample, step) pair of this thread: J_ctrl's terms
     // Q_c |u_j|^2 (j <= T-2) and Q_cd |u_j - u_{j-1}|^2 (1 <= j <= T-2), the
-    // state terms at x_{j+1} against the guide at t = (j + 1) dt, J_col
+    // state terms at x_{j+1} against the guide at t = (j + 1) dt, J_col.  The
+    // pairs are evaluated without branches (a missing pair repeats the last
+    // step and is masked) so that their latencies overlap.
+    float cs[kQ];
 #pragma unroll
     for (int i = 0; i < kQ; ++i) {
-      const int jj = wid + SW * i, j = j0 + jj;
-      if (jj < tc && active) {
-        const float4 u = m.u[j * QS + lane];
-        float c = 0.0f;
-        if (j <= T - 2) {
-          c = cp.Q_c * (u.x * u.x + u.y * u.y + u.z * u.z + u.w * u.w);
-          if (j >= 1) {
-            const float4 up = m.u[(j - 1) * QS + lane];
-            const float ax = u.x - up.x, ay = u.y - up.y, az = u.z - up.z, aw = u.w - up.w;
-            c += cp.Q_cd * (ax * ax + ay * ay + az * az + aw * aw);
-          }
-        }
-        State y;
-        const float* X = m.xs + jj * 10 * QS + lane;
-#pragma unroll
-        for (int t = 0; t < 3; ++t) y.p[t] = X[t * QS];
-#pragma unroll
-        for (int t = 0; t < 4; ++t) y.q[t] = X[(3 + t) * QS];
-#pragma unroll
-        for (int t = 0; t < 3; ++t) y.v[t] = X[(7 + t) * QS];
-        const float gx = m.gd[3 * j], gy = m.gd[3 * j + 1], gz = m.gd[3 * j + 2];
-        c += cp.Q_track * norm3f(y.p[0] - gx, y.p[1] - gy, y.p[2] - gz);
-        c += cp.Q_vnorm * (y.v[0] * y.v[0] + y.v[1] * y.v[1] + y.v[2] * y.v[2]);
-        c += goal_term(y, cp);
-        const float d2 = __int_as_float(m.d2[jj * QS + lane]);
-        c += jcol_from_d2(d2, cp, dmax2);
-        S += c;
-        if (dbg >= 0) a.dbg_d[(size_t)dbg * T + j] = d2 < dmax2 ? sqrtf(d2) : INFINITY;
-      }
+      const int jq = wid + SW * i;
+      const int jj = jq < tc ? jq : tc - 1, j = j0 + jj;
+      const float4 u = m.u[j * QS + lane];
+      const float4 up = m.u[(j >= 1 ? j - 1 : 0) * QS + lane];
+      const float ax = u.x - up.x, ay = u.y - up.y, az = u.z - up.z, aw = u.w - up.w;
+      const float c_u = cp.Q_c * (u.x * u.x + u.y * u.y + u.z * u.z + u.w * u.w);
+      const float c_du = cp.Q_cd * (ax * ax + ay * ay + az * az + aw * aw);
+      float c = j <= T - 2 ? (j >= 1 ? c_u + c_du : c_u) : 0.0f;
+      const float4 xa = m.xa[jj * QS + lane], xb = m.xb[jj * QS + lane];
+      const float2 xc = m.xc[jj * QS + lane];
+      State y;
+      y.p[0] = xa.x; y.p[1] = xa.y; y.p[2] = xa.z;
+      y.q[0] = xa.w; y.q[1] = xb.x; y.q[2] = xb.y; y.q[3] = xb.z;
+      y.v[0] = xb.w; y.v[1] = xc.x; y.v[2] = xc.y;
+      const float gx = m.gd[3 * j], gy = m.gd[3 * j + 1], gz = m.gd[3 * j + 2];
+      c += cp.Q_track * norm3f(y.p[0] - gx, y.p[1] - gy, y.p[2] - gz);
+      c += cp.Q_vnorm * (y.v[0] * y.v[0] + y.v[1] * y.v[1] + y.v[2] * y.v[2]);
+      c += goal_term(y, cp);
+      const float d2 = __int_as_float(m.d2[jj * QS + lane]);
+      c += jcol_select(d2, cp, dmax2);
+      cs[i] = jq < tc && active ? c : 0.0f;
+      if (jq < tc && dbg >= 0) a.dbg_d[(size_t)dbg * T + j] = d2 < dmax2 ? sqrtf(d2) : INFINITY;
     }
-    __syncthreads();  // xs free for the next chunk
+#pragma unroll
+    for (int i = 0; i < kQ; ++i) S += cs[i];
+    __syncthreads();  // state buffers free for the next chunk
   }
   m.cost[wid * QS + lane] = S;
   __syncthreads();
