@@ -490,6 +490,7 @@ void make_step_args(aero_planner* pl, const aero_state_t* x0, const float* cloud
   ua.best_idx = best_idx;
   ua.u_best = u_best;
   ua.counter = pl->counter;
+  ua.inst_counter = pl->counter + 3;
   ua.status = pl->status;
 }
 
@@ -549,7 +550,7 @@ int enqueue_step(aero_planner* pl, const aero_state_t* x0, const float* cloud, i
     prof->launches[AERO_STAGE_PARTITION] = n > 0 ? 1 : 0;
     prof->launches[AERO_STAGE_GRID] = 3;
     prof->launches[AERO_STAGE_ROLLOUT] = p.iters;
-    prof->launches[AERO_STAGE_UPDATE] = p.iters;
+    prof->launches[AERO_STAGE_UPDATE] = rollout_runs_update(a.ra) ? 0 : p.iters;
   }
   // count pass + coarse argmax/anchors/guides, scan, scatter + cell ranges
   if ((e = launch_grid_count(a.ca, a.ga, a.tab, s)) != cudaSuccess) return cuda_fail(e);
@@ -563,12 +564,12 @@ int enqueue_step(aero_planner* pl, const aero_state_t* x0, const float* cloud, i
   const uint32_t ctr_base = a.ra.ctr3;
   for (int it = 0; it < p.iters; ++it) {
     a.ra.ctr3 = ctr_base | (uint32_t)it;
-    mark(AERO_STAGE_ROLLOUT, 4 + 4 * it);
-    if ((e = launch_rollout(a.ra, s)) != cudaSuccess) return cuda_fail(e);
-    mark(AERO_STAGE_ROLLOUT, 5 + 4 * it);
     a.ua.final_stage = it == p.iters - 1;
+    mark(AERO_STAGE_ROLLOUT, 4 + 4 * it);
+    if ((e = launch_rollout(a.ra, a.ua, s)) != cudaSuccess) return cuda_fail(e);
+    mark(AERO_STAGE_ROLLOUT, 5 + 4 * it);
     mark(AERO_STAGE_UPDATE, 6 + 4 * it);
-    if ((e = launch_update(a.ua, s)) != cudaSuccess) return cuda_fail(e);
+    if (!rollout_runs_update(a.ra) && (e = launch_update(a.ua, s)) != cudaSuccess) return cuda_fail(e);
     mark(AERO_STAGE_UPDATE, 7 + 4 * it);
   }
   note_step(pl, p, a);
@@ -675,7 +676,7 @@ int aero_create(const aero_limits_t* limits, aero_planner_t** out) {
   const size_t du_bytes = sizeof(float4) * (size_t)L.E_max * L.K_max * L.T_max;
   if (du_bytes <= kMaxStoredPerturbationBytes) chk(alloc(&pl->dU, (size_t)L.E_max * L.K_max * L.T_max));
   chk(alloc(&pl->stage2_x, (size_t)L.E_max * (L.T_max + 1) * 10));
-  chk(alloc(&pl->counter, 3));
+  chk(alloc(&pl->counter, kCounterWords));
   chk(alloc(&pl->status, 1));
   chk(alloc(&pl->dbg_u, (size_t)L.E_max * D * L.T_max * 4));
   chk(alloc(&pl->dbg_x, (size_t)L.E_max * D * (L.T_max + 1) * 10));
@@ -686,7 +687,7 @@ int aero_create(const aero_limits_t* limits, aero_planner_t** out) {
   chk(alloc(&pl->stage_ubest, (size_t)L.T_max * 4));
   chk(alloc(&pl->stage_cand, L.E_max));
   chk(alloc(&pl->stage_best, 1));
-  if (e == cudaSuccess) e = cudaMemset(pl->counter, 0, 3 * sizeof(unsigned int));
+  if (e == cudaSuccess) e = cudaMemset(pl->counter, 0, kCounterWords * sizeof(unsigned int));
   if (e == cudaSuccess) e = cudaMemset(pl->status, 0, sizeof(int));
   if (e == cudaSuccess) e = cudaDeviceSynchronize();
   if (e != cudaSuccess) {
@@ -957,7 +958,7 @@ constexpr size_t kNaBytes =
     align256(4 * ((size_t)kNaTiles + 1)) + align256(16 * (size_t)kNaCand) +
     align256(8 * (size_t)kNaGridCells) +
     align256(4 * (size_t)kNaE * kNaNb * (4 + 4 * kNaT)) + align256(4 * (size_t)kNaE * kNaK) +
-    align256(4 * (size_t)kNaE * (kNaT + 1) * 10) + align256(4) + align256(4);
+    align256(4 * (size_t)kNaE * (kNaT + 1) * 10) + align256(4 * kCounterWords) + align256(4);
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNaBytes];
 
@@ -1015,7 +1016,7 @@ void noalloc_carve(unsigned char* base, aero_planner& pl) {
   pl.partials = reinterpret_cast<float*>(take(4 * (size_t)kNaE * kNaNb * (4 + 4 * kNaT)));
   pl.sample_costs = reinterpret_cast<float*>(take(4 * (size_t)kNaE * kNaK));
   pl.stage2_x = reinterpret_cast<float*>(take(4 * (size_t)kNaE * (kNaT + 1) * 10));
-  pl.counter = reinterpret_cast<unsigned int*>(take(12));
+  pl.counter = reinterpret_cast<unsigned int*>(take(4 * kCounterWords));
   pl.status = reinterpret_cast<int*>(take(4));
 }
 
@@ -1045,8 +1046,8 @@ int aero_plan_step_noalloc(const aero_state_t* x0, const float* cloud, int64_t n
   if (rc != AERO_OK) return rc;
   noalloc_carve(base, pl);
   cudaStream_t s = (cudaStream_t)stream;
-  // the three last-block tickets and the status word must start at zero
-  cudaError_t e = cudaMemsetAsync(pl.counter, 0, 3 * sizeof(unsigned int), s);
+  // the last-block tickets and the status word must start at zero
+  cudaError_t e = cudaMemsetAsync(pl.counter, 0, kCounterWords * sizeof(unsigned int), s);
   if (e == cudaSuccess) e = cudaMemsetAsync(pl.status, 0, sizeof(int), s);
   if (e != cudaSuccess) return AERO_ERR_CUDA;
   return enqueue_step(&pl, x0, cloud, n, goal, *params, u_nom, u_best, cand, best_idx, s);

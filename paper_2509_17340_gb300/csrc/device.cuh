@@ -191,12 +191,6 @@ __device__ __forceinline__ float scan_min(const float4* P, int n, float px, floa
   return best;
 }
 
-// One thread, one query.
-__device__ __forceinline__ float nn_dist2(float px, float py, float pz, const GridView& g,
-                                          float dmax2) {
-  const int2 r = cell_range(px, py, pz, g);
-  return scan_min(g.pts + r.x, r.y, px, py, pz, dmax2);
-}
 
 
 // Piecewise collision penalty from a squared distance (d >= d_max -> 0).

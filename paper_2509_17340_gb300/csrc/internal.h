@@ -11,6 +11,10 @@ namespace aero {
 constexpr int kMaxAz = 512;
 constexpr int kMaxEl = 256;
 constexpr int kMaxE = 64;
+// Tickets of last-CTA patterns, zero between launches: [0] the update's
+// selection, [1] the coarse blocks, [2] the grid scan, [3 + e] the Stage I
+// CTAs of instance e in the split pass that also runs the update.
+constexpr int kCounterWords = 3 + kMaxE;
 constexpr int kMaxT = 128;
 constexpr int kGridMax = 96;         // collision-grid cells per axis, at most
 constexpr int kScanTile = 4096;      // cells per scan tile (1024 threads x 4)
@@ -151,6 +155,7 @@ struct UpdateArgs {
   int* best_idx;
   float* u_best;           // T x 4
   unsigned int* counter;   // last-CTA ticket, 0 between launches
+  unsigned int* inst_counter;  // E tickets of the split Stage I pass, 0 between launches
   int* status;             // bit 0: a normaliser eta was not a positive finite number
 };
 
@@ -239,7 +244,10 @@ struct CostGradArgs {
   float4* G;               // n x T, or null
 };
 
-cudaError_t launch_rollout(const RolloutArgs& a, cudaStream_t s);
+// Stage I; the split pass (lanes_per_sample 4) also runs the update `ua` in
+// the last CTA of every instance, the others leave it to launch_update.
+cudaError_t launch_rollout(const RolloutArgs& a, const UpdateArgs& ua, cudaStream_t s);
+bool rollout_runs_update(const RolloutArgs& a);
 cudaError_t launch_cost_grad(const CostGradArgs& a, cudaStream_t s);
 cudaError_t launch_update(const UpdateArgs& a, cudaStream_t s);
 cudaError_t launch_philox(uint32_t k0, uint32_t k1, uint32_t c1, uint32_t c2, uint32_t c3,

@@ -190,10 +190,10 @@ __device__ __forceinline__ void rollout_unit(const RolloutArgs& a, int e, int b,
 // sample, split into phases so that only the dynamics stays sequential: 32
 // samples per CTA (eight threads per sample, one in each of its eight warps);
 // the horizon in chunks of at most kChunk steps.
-//   noise    the perturbations of every step, drawn one chunk ahead (the
-//            first chunk by all warps, the next ones by the seven warps that
-//            do not integrate); the clamped controls stay in shared memory
-//            for the whole horizon;
+//   noise    the perturbations of every step, drawn by all warps before
+//            the first chunk (the integrating warp then has its scheduler
+//            to itself); the clamped controls stay in shared memory for the
+//            whole horizon;
 //   dynamics one warp, one lane per sample, applies the chunk's controls with
 //            RK4; the states go to shared memory (this is the only serial
 //            chain, so nothing else runs in it);
@@ -263,7 +263,9 @@ __device__ __forceinline__ SplitSmem split_layout(unsigned char* base, int T) {
   return m;
 }
 
-// Exclusive prefix sums of (x, y) over the CTA; `total` receives the sums.
+// Exclusive prefix sums of (x, y) over a CTA of kWarps warps; `total`
+// receives the sums.  warp_tot: kWarps entries of shared memory.
+template <int kWarps>
 __device__ __forceinline__ int2 block_scan2(int2 v, int2* warp_tot, int2& total) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   int2 inc = v;
@@ -280,7 +282,7 @@ __device__ __forceinline__ int2 block_scan2(int2 v, int2* warp_tot, int2& total)
   int2 before = make_int2(0, 0);
   total = make_int2(0, 0);
 #pragma unroll
-  for (int w = 0; w < SW; ++w) {
+  for (int w = 0; w < kWarps; ++w) {
     const int2 t = warp_tot[w];
     if (w < wid) {
       before.x += t.x;
@@ -339,7 +341,7 @@ __device__ __forceinline__ void rollout_split_unit(const RolloutArgs& a, int e, 
   float S = 0.0f;  // every thread: the cost terms of its (sample, step) pairs
 
   __syncthreads();  // un, gd
-  noise(0, tcb < T ? tcb : T, wid, SW);
+  noise(0, T, wid, SW);
   __syncthreads();
   for (int j0 = 0; j0 < T; j0 += tcb) {
     const int tc = tcb < T - j0 ? tcb : T - j0;
@@ -361,10 +363,8 @@ __device__ __forceinline__ void rollout_split_unit(const RolloutArgs& a, int e, 
           for (int i = 0; i < 3; ++i) X[7 + i] = x.v[i];
         }
       }
-    } else if (j0 + tc < T) {
-      noise(j0 + tc, tcb < T - j0 - tc ? tcb : T - j0 - tc, ((wid - wint) & (SW - 1)) - 1, SW - 1);
     }
-    __syncthreads();  // states filled; the next chunk's controls drawn
+    __syncthreads();  // states filled
 
     // this thread's queries: steps jj = wid + 8 i of the chunk, sample `lane`
     int2 rg[kQ];
@@ -386,7 +386,7 @@ __device__ __forceinline__ void rollout_split_unit(const RolloutArgs& a, int e, 
       }
     }
     int2 total;
-    int2 off = block_scan2(cnt, m.scan, total);
+    int2 off = block_scan2<SW>(cnt, m.scan, total);
 #pragma unroll
     for (int i = 0; i < kQ; ++i) {
       if (rg[i].y > 0) {
@@ -481,9 +481,14 @@ __device__ __forceinline__ void rollout_split_unit(const RolloutArgs& a, int e, 
 // final iteration roll out the updated nominal (Stage II), score S(2), and let
 // the last CTA to finish pick the argmin.
 // ---------------------------------------------------------------------------
-constexpr int UT = 128;
+constexpr int UT = 128;  // threads of the update kernels
 
+// kThreads: the CTA's threads (128 in the update kernels, 256 in the split
+// Stage I pass).  The partials are read through L2 (ld.cg): in the split pass
+// other CTAs of the same launch wrote them.
+template <int kThreads>
 __device__ __forceinline__ void update_unit(const UpdateArgs& a, int e, bool final_stage) {
+  constexpr int UT = kThreads;
   __shared__ float s_scale[1024];
   __shared__ float s_red[UT / 32];
   __shared__ __align__(16) float s_x[(kMaxT + 1) * 10];  // also the refinement's AdjScratch
@@ -492,13 +497,19 @@ __device__ __forceinline__ void update_unit(const UpdateArgs& a, int e, bool fin
   __shared__ float s_c[kMaxT];
   __shared__ float4 s_acc[UT / 32][kMaxT];
   __shared__ bool s_last;
+  // Stage II's nearest-point queries (one per step, cut into items)
+  __shared__ int s_qitem[kMaxT + 1];
+  __shared__ int2 s_qrange[kMaxT];
+  __shared__ int s_qslot[kMaxT];
+  __shared__ int s_d2[kMaxT];
+  __shared__ int2 s_scan[UT / 32];
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const int T = a.T, stride = 4 + 4 * T;
   const float* P = a.partials + (size_t)e * a.nb * stride;
 
   // rho = min rho_b
   float m = INFINITY;
-  for (int b = tid; b < a.nb; b += UT) m = fminf(m, P[(size_t)b * stride]);
+  for (int b = tid; b < a.nb; b += UT) m = fminf(m, __ldcg(P + (size_t)b * stride));
   m = warp_min(m);
   if (lane == 0) s_red[wid] = m;
   __syncthreads();
@@ -508,9 +519,9 @@ __device__ __forceinline__ void update_unit(const UpdateArgs& a, int e, bool fin
   // eta = sum eta_b exp(-(rho_b - rho)/lambda)
   float eta = 0.0f;
   for (int b = tid; b < a.nb; b += UT) {
-    const float sc = expf((rho - P[(size_t)b * stride]) * a.inv_lambda);
+    const float sc = expf((rho - __ldcg(P + (size_t)b * stride)) * a.inv_lambda);
     if (b < 1024) s_scale[b] = sc;
-    eta += sc * P[(size_t)b * stride + 1];
+    eta += sc * __ldcg(P + (size_t)b * stride + 1);
   }
   eta = warp_sum(eta);
   if (lane == 0) s_red[wid] = eta;
@@ -522,7 +533,7 @@ __device__ __forceinline__ void update_unit(const UpdateArgs& a, int e, bool fin
   }
   const float inv_eta = 1.0f / eta;
   auto scale = [&](int b) {
-    return b < 1024 ? s_scale[b] : expf((rho - P[(size_t)b * stride]) * a.inv_lambda);
+    return b < 1024 ? s_scale[b] : expf((rho - __ldcg(P + (size_t)b * stride)) * a.inv_lambda);
   };
   __syncthreads();  // s_scale complete
   // sum_b scale_b W_b: warp w takes the rows b = w (mod 4), lane the float4
@@ -539,7 +550,7 @@ __device__ __forceinline__ void update_unit(const UpdateArgs& a, int e, bool fin
     for (int q = 0; q < kCol; ++q) {
       const int c4 = lane + 32 * q;
       if (c4 < T) {
-        const float4 w4 = row[c4];
+        const float4 w4 = __ldcg(row + c4);
         acc[q].x += sc * w4.x;
         acc[q].y += sc * w4.y;
         acc[q].z += sc * w4.z;
@@ -594,15 +605,47 @@ __device__ __forceinline__ void update_unit(const UpdateArgs& a, int e, bool fin
     }
   }
   __syncthreads();
+  // the nearest point of every state x_{j+1} (thread j): the non-empty
+  // candidate lists cut into items of kItem entries, taken by all threads
+  static_assert(kMaxT <= UT, "one Stage II query per thread");
   const float dmax2 = a.cost.d_max * a.cost.d_max;
-  for (int j = tid; j < T; j += UT) {
+  int2 rg = make_int2(0, 0);
+  if (tid < T) {
+    const float* X = s_x + (tid + 1) * 10;
+    rg = cell_range(X[0], X[1], X[2], a.grid);
+    s_d2[tid] = __float_as_int(dmax2);
+  }
+  int2 total;
+  const int2 off = block_scan2<UT / 32>(
+      rg.y > 0 ? make_int2(1, (rg.y + kItem - 1) / kItem) : make_int2(0, 0), s_scan, total);
+  if (rg.y > 0) {
+    s_qitem[off.x] = off.y;
+    s_qrange[off.x] = rg;
+    s_qslot[off.x] = tid;
+  }
+  __syncthreads();
+  for (int it = tid; it < total.y; it += UT) {
+    int lo = 0, hi = total.x - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (s_qitem[mid] <= it) lo = mid; else hi = mid - 1;
+    }
+    const int2 r = s_qrange[lo];
+    const int j = s_qslot[lo];
+    const int first = (it - s_qitem[lo]) * kItem;
+    const int n = r.y - first < kItem ? r.y - first : kItem;
     const float* X = s_x + (j + 1) * 10;
+    const float d2 = scan_min<kItem>(a.grid.pts + r.x + first, n, X[0], X[1], X[2], dmax2);
+    if (d2 < dmax2) atomicMin(s_d2 + j, __float_as_int(d2));  // non-negative: int order
+  }
+  __syncthreads();
+  if (tid < T) {
+    const float* X = s_x + (tid + 1) * 10;
     State x;
     for (int i = 0; i < 3; ++i) x.p[i] = X[i];
     for (int i = 0; i < 4; ++i) x.q[i] = X[3 + i];
     for (int i = 0; i < 3; ++i) x.v[i] = X[7 + i];
-    const float d2 = nn_dist2(x.p[0], x.p[1], x.p[2], a.grid, dmax2);
-    s_c[j] = goal_term(x, a.cost) + jcol_from_d2(d2, a.cost, dmax2);
+    s_c[tid] = goal_term(x, a.cost) + jcol_from_d2(__int_as_float(s_d2[tid]), a.cost, dmax2);
   }
   for (int i = tid; i < (T + 1) * 10; i += UT) a.stage2_x[(size_t)e * (T + 1) * 10 + i] = s_x[i];
   __syncthreads();
@@ -651,9 +694,24 @@ __global__ void __launch_bounds__(NT) k_rollout(RolloutArgs a) {
   rollout_unit(a, blockIdx.y, blockIdx.x, a.ctr3);
 }
 
-__global__ void __launch_bounds__(ST) k_rollout_split(RolloutArgs a) {
+// The split pass with the update of every instance run by the last of its
+// CTAs to finish (a ticket per instance, reset by that CTA): no update launch.
+__global__ void __launch_bounds__(ST) k_rollout_split(RolloutArgs a, UpdateArgs ua) {
   pdl_start();
-  rollout_split_unit(a, blockIdx.y, blockIdx.x, a.ctr3);
+  const int e = blockIdx.y;
+  rollout_split_unit(a, e, blockIdx.x, a.ctr3);
+  __shared__ bool s_last_b;
+  __shared__ UpdateArgs s_ua;
+  __threadfence();  // this CTA's partials are visible before its ticket
+  __syncthreads();
+  if (threadIdx.x == 0) s_last_b = atomicAdd(ua.inst_counter + e, 1u) == (unsigned)(a.nb - 1);
+  __syncthreads();
+  if (!s_last_b) return;
+  __threadfence();
+  if (threadIdx.x == 0) ua.inst_counter[e] = 0u;
+  block_copy_param(&s_ua, &ua);
+  __syncthreads();
+  update_unit<ST>(s_ua, e, s_ua.final_stage != 0);
 }
 
 // The single-planner update reads its arguments from shared memory, as the
@@ -665,7 +723,7 @@ __global__ void __launch_bounds__(UT) k_update(UpdateArgs a) {
   __shared__ UpdateArgs s_a;
   block_copy_param(&s_a, &a);
   __syncthreads();
-  update_unit(s_a, blockIdx.x, s_a.final_stage != 0);
+  update_unit<UT>(s_a, blockIdx.x, s_a.final_stage != 0);
 }
 
 // ---------------------------------------------------------------------------
@@ -748,7 +806,7 @@ __global__ void __launch_bounds__(UT) k_b_update(BatchView v, int it) {
       __syncthreads();
       cur = item;
     }
-    if (it < s_iters) update_unit(s_a, (int)(u - s_pre[item]), it == s_iters - 1);
+    if (it < s_iters) update_unit<UT>(s_a, (int)(u - s_pre[item]), it == s_iters - 1);
     __syncthreads();
   }
 }
@@ -808,7 +866,11 @@ cudaError_t split_attributes() {
 // two of its CTAs (as a percentage of the 228 KB an SM can give).
 cudaError_t split_carveout(int T) {
   static std::atomic<int> current{-1};
-  const size_t need = 2 * (split_smem_bytes(T) + 1024);
+  static const size_t static_bytes = [] {
+    cudaFuncAttributes fa{};
+    return cudaFuncGetAttributes(&fa, k_rollout_split) == cudaSuccess ? fa.sharedSizeBytes : 0;
+  }();
+  const size_t need = 2 * (split_smem_bytes(T) + static_bytes + 1024);
   int pct = (int)((need * 100 + 228 * 1024 - 1) / (228 * 1024));
   if (pct > 100) pct = 100;
   if (current.load() == pct) return cudaSuccess;
@@ -844,13 +906,15 @@ cudaError_t launch_batch_update(const BatchView& v, int it, int blocks, cudaStre
   return launch_k(k_b_update, dim3(blocks), dim3(UT), s, true, v, it);
 }
 
-cudaError_t launch_rollout(const RolloutArgs& a, cudaStream_t s) {
+bool rollout_runs_update(const RolloutArgs& a) { return a.lanes_per_sample == 4; }
+
+cudaError_t launch_rollout(const RolloutArgs& a, const UpdateArgs& ua, cudaStream_t s) {
   dim3 grid(a.nb, a.E);
   if (a.lanes_per_sample == 4) {
     cudaError_t e = split_attributes();
     if (e == cudaSuccess) e = split_carveout(a.T);
     if (e != cudaSuccess) return e;
-    return launch_ks(k_rollout_split, grid, dim3(ST), split_smem_bytes(a.T), s, true, a);
+    return launch_ks(k_rollout_split, grid, dim3(ST), split_smem_bytes(a.T), s, true, a, ua);
   }
   return launch_k(k_rollout, grid, dim3(NT), s, true, a);
 }
