@@ -162,6 +162,19 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+# E*K at or below which a planning step runs the split Stage I pass (four or
+# more threads per sample, the update fused into its last CTAs)
+SPLIT_MAX_SAMPLES = 32768
+
+
+def rollout_kernel_name(P: dict) -> str:
+    lanes = P.get("lanes_per_sample", 0) or (4 if P["E"] * P["K"] <= SPLIT_MAX_SAMPLES else 1)
+    if lanes == 4:
+        return ("k_rollout_split (noise, RK4, S(1), per-CTA partials; the last CTA of each "
+                "instance merges them, updates the nominal and runs Stage II)")
+    return "k_rollout (fused noise + RK4 + S(1) + update partials)"
+
+
 def rollout_traffic(workload: str):
     """DRAM bytes per k_rollout launch from the committed ncu summary, or None
     when the kernel's source changed since those counters were taken."""
@@ -692,10 +705,12 @@ def main():
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": config_of(P, w),
         "stage_ms_per_step": {k: v[0] / n_diag for k, v in breakdown.items()},
-        "roofline": {"kernel": "k_rollout (fused noise + RK4 + S(1) + update partials)",
+        "roofline": {"kernel": rollout_kernel_name(P),
                      "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak, "traffic": rollout_traffic(WORKLOAD),
                      "flops_per_launch": flops, "avg_launch_ms": r_avg_ms,
+                     "flops_note": "Stage I only (noise, RK4, S(1)); the launch time also "
+                                   "covers what the kernel fuses",
                      "peak_note": "FP32 FMA pipes: 152 SMs x 128 lanes x 2 x 2070 MHz (max SM clock)"},
         "clocks": clocks,
         "e2e": e2e,

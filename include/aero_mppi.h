@@ -126,8 +126,11 @@ typedef struct {
   float v_goal[3];        /* goal velocity */
   float q_goal[4];        /* goal attitude (w, x, y, z) */
   int32_t debug_samples;  /* D: record rollouts of samples k < D (0 = off) */
-  int32_t lanes_per_sample; /* threads per sample in the rollout kernel: 0 = automatic
-                             (4 when E*K <= 32768, else 1), or 1 or 4 */
+  int32_t lanes_per_sample; /* Stage I kernel: 1 = one thread per sample; 4 = the split
+                             pass for small problems (noise, dynamics, nearest-point
+                             queries and costs in separate phases over eight threads per
+                             sample, the update run by each instance's last CTA);
+                             0 = automatic (4 when E*K <= 32768, else 1) */
   uint64_t seed;          /* Philox key */
   uint64_t step_id;       /* enters the Philox counter: (k, j, e, (step_id << 8) | iter) */
   int32_t refine_steps;   /* gradient refinement of every updated nominal before Stage II:
@@ -222,8 +225,11 @@ int aero_plan_step_noalloc(const aero_state_t* x0, const float* cloud_xyz, int64
  * batch shape (item count, largest iteration count, configuration) and then
  * replayed; a call uploads the items' arguments in one host-to-device copy and
  * launches the graph on `stream`.
- * Every item's results are bitwise those of aero_plan_step with the same
- * lanes_per_sample (the per-unit arithmetic is the same code). */
+ * Every item computes what aero_plan_step computes with the same
+ * lanes_per_sample: the partition and grid decisions are identical and the
+ * floating-point results agree to rounding (the unit code is compiled in other
+ * contexts, and the batched update merges the partials with other thread
+ * counts). */
 typedef struct {
   aero_state_t x0;            /* current state */
   const float* cloud_xyz;     /* device, n_points x 3 float (may be NULL if n_points == 0) */
@@ -240,8 +246,8 @@ typedef struct aero_batch aero_batch_t;
 
 /* Launch configuration of a batch (the autotuner's search space). */
 typedef struct {
-  int32_t quad_max_samples;    /* items with lanes_per_sample == 0 use four lanes per sample
-                                  when E*K <= this, else one */
+  int32_t quad_max_samples;    /* items with lanes_per_sample == 0 use the split pass (4)
+                                  when E*K <= this, else one thread per sample */
   int32_t rollout_ctas_per_sm; /* persistent Stage I CTAs per SM; 0 = as many as fit; 6 or more
                                   also selects the one-lane kernel built for six per SM
                                   (fewer registers) */

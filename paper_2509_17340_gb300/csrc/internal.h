@@ -20,7 +20,7 @@ constexpr int kGridMax = 96;         // collision-grid cells per axis, at most
 constexpr int kScanTile = 4096;      // cells per scan tile (1024 threads x 4)
 constexpr int kScanTileShift = 12;
 constexpr int kRolloutThreads = 128; // samples per rollout CTA (one warp-group)
-constexpr int kQuadMaxSamples = 32768;  // E*K up to which four lanes carry one sample
+constexpr int kQuadMaxSamples = 32768;  // E*K up to which the split Stage I pass runs
 
 // Binary32 edge tables of the partition, passed by value to the kernels.
 // Azimuth edge k: theta_k = pi (2k - A) / A; elevation edge k: phi_k = lo +
