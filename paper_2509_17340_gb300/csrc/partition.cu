@@ -425,15 +425,18 @@ __device__ void coarse_guides_block(const GuideArgs& a, const PartTables& t, int
   guides_block(a, st);
 }
 
-// K2a + K3: the count pass of the candidate lists and, in the remaining blocks,
-// the coarse argmax, goal cone, anchors and guides (they need only the keys).
+// K2a + K3: the coarse argmax, goal cone, anchors and guides (they need only
+// the keys) in the first blocks, which are dispatched first because the last of
+// them continues with the anchors and guides; the count pass of the candidate
+// lists in the remaining blocks.
 __global__ void __launch_bounds__(256) k_grid_count(CandArgs ca, GuideArgs ga, PartTables t,
                                                     int count_blocks) {
   pdl_start();
-  if ((int)blockIdx.x < count_blocks)
-    cand_pass<false>(ca, blockIdx.x, count_blocks);
+  const int ncb = (int)gridDim.x - count_blocks;
+  if ((int)blockIdx.x < ncb)
+    coarse_guides_block(ga, t, blockIdx.x, ncb);
   else
-    coarse_guides_block(ga, t, blockIdx.x - count_blocks, gridDim.x - count_blocks);
+    cand_pass<false>(ca, blockIdx.x - ncb, count_blocks);
 }
 
 // {first entry, count} of cell c from the scanned counts.
@@ -453,8 +456,10 @@ __global__ void __launch_bounds__(256) k_grid_scatter(CandArgs ca, int scatter_b
     cand_pass<true>(ca, blockIdx.x, scatter_blocks);
     return;
   }
-  const int c = (blockIdx.x - scatter_blocks) * blockDim.x + threadIdx.x;
-  if (c < ncells) range_cell(ca.local, ca.tile_off, ca.grid.cap, range, c);
+  const int nrb = (int)gridDim.x - scatter_blocks;
+  for (int c = (blockIdx.x - scatter_blocks) * blockDim.x + threadIdx.x; c < ncells;
+       c += nrb * blockDim.x)
+    range_cell(ca.local, ca.tile_off, ca.grid.cap, range, c);
 }
 
 __global__ void k_philox(uint32_t k0, uint32_t k1, uint32_t c1, uint32_t c2, uint32_t c3,
@@ -618,7 +623,8 @@ cudaError_t launch_partition(const PartitionArgs& a, const PartTables& t, cudaSt
 
 cudaError_t launch_grid_count(const CandArgs& ca, const GuideArgs& ga, const PartTables& t,
                               cudaStream_t s) {
-  const int count_blocks = ca.n_items > 0 ? blocks_for(ca.n_items * 32, 256, 152 * 32) : 0;
+  // one warp per collision item up to four blocks per SM, then items per warp
+  const int count_blocks = ca.n_items > 0 ? blocks_for(ca.n_items * 32, 256, 152 * 4) : 0;
   const int coarse_blocks = (ga.Ac * ga.Ec + 7) / 8;  // 8 warps per block
   return launch_k(k_grid_count, dim3(count_blocks + coarse_blocks), dim3(256), s, true, ca, ga, t,
                   count_blocks);
@@ -631,8 +637,8 @@ cudaError_t launch_grid_scan(int* count, int* fill, int* local, int* tile_sum, i
 }
 
 cudaError_t launch_grid_scatter(const CandArgs& ca, int2* range, int ncells, cudaStream_t s) {
-  const int scatter_blocks = ca.n_items > 0 ? blocks_for(ca.n_items * 32, 256, 152 * 32) : 0;
-  const int range_blocks = (ncells + 255) / 256;
+  const int scatter_blocks = ca.n_items > 0 ? blocks_for(ca.n_items * 32, 256, 152 * 4) : 0;
+  const int range_blocks = blocks_for(ncells, 256, 152 * 2);
   return launch_k(k_grid_scatter, dim3(scatter_blocks + range_blocks), dim3(256), s, true, ca,
                   scatter_blocks, range, ncells);
 }
