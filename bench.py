@@ -167,6 +167,15 @@ class ClockSampler:
 SPLIT_MAX_SAMPLES = 32768
 
 
+def step_percentiles(step_ms: list) -> dict:
+    """p10 / p90 of the per-step device times (nearest rank)."""
+    xs = sorted(step_ms)
+    if not xs:
+        return {}
+    pick = lambda q: xs[min(len(xs) - 1, max(0, int(math.ceil(q * len(xs))) - 1))]
+    return {"ms_per_step_p10": pick(0.10), "ms_per_step_p90": pick(0.90)}
+
+
 def rollout_kernel_name(P: dict) -> str:
     lanes = P.get("lanes_per_sample", 0) or (4 if P["E"] * P["K"] <= SPLIT_MAX_SAMPLES else 1)
     if lanes == 4:
@@ -379,7 +388,7 @@ def run_accumulate(args, rank: int, world: int, local: int):
     line = {
         "metric": METRIC, "value": world * units * args.steps / (total_ms / 1e3), "unit": "points/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": total_ms / args.steps, "ms_per_step_median": statistics.median(step_ms),
+        "ms_per_step": total_ms / args.steps, "ms_per_step_median": statistics.median(step_ms), **step_percentiles(step_ms),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic",
         "config": {"workload": f"accumulate: {F} frames x {N} points, push one frame + gather all",
@@ -511,7 +520,7 @@ def run_batched(args, rank: int, world: int, local: int):
     line = {
         "metric": METRIC, "value": world * units * args.steps / (total_ms / 1e3), "unit": UNIT,
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": total_ms / args.steps, "ms_per_step_median": statistics.median(step_ms),
+        "ms_per_step": total_ms / args.steps, "ms_per_step_median": statistics.median(step_ms), **step_percentiles(step_ms),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic",
         "config": {"workload": f"batched: {len(ws)} planners, E in {{4,8,16}}, K in {{256,1024,4096}}, "
@@ -701,7 +710,7 @@ def main():
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
-        "ms_per_step_median": statistics.median(step_ms), "higher_is_better": True,
+        "ms_per_step_median": statistics.median(step_ms), **step_percentiles(step_ms), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": config_of(P, w),
         "stage_ms_per_step": {k: v[0] / n_diag for k, v in breakdown.items()},

@@ -81,7 +81,10 @@ extern "C" {
                                     +inf where none is closer than d_max */
 #define AERO_DBG_PRE_REFINE 14   /* float [E][T][4]: nominals after the last update, before the
                                     gradient refinement (written when refine_steps > 0) */
-#define AERO_DBG_COUNT 15
+#define AERO_DBG_POINT_COUNTS 15 /* int64 [3]: points given, points skipped as non-finite,
+                                    points kept by the partition (within r_max and the
+                                    elevation span) */
+#define AERO_DBG_COUNT 16
 
 /* ---- inputs ----------------------------------------------------------- */
 

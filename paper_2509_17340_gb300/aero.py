@@ -28,7 +28,11 @@ ERR_INVALID_ARG, ERR_EXCEEDS_LIMITS, ERR_CUDA, ERR_ALLOC, ERR_DEVICE_CHECK, ERR_
 
 DBG = dict(FINE_KEYS=0, COARSE_WIN=1, GOAL_CELL=2, ANCHOR_CELLS=3, ANCHORS=4, GUIDES=5,
            GRID_META=6, GRID_START=7, GRID_POINTS=8, SAMPLE_COSTS=9, STAGE2_STATES=10,
-           SAMPLE_U=11, SAMPLE_X=12, SAMPLE_DIST=13, PRE_REFINE=14)
+           SAMPLE_U=11, SAMPLE_X=12, SAMPLE_DIST=13, PRE_REFINE=14, POINT_COUNTS=15)
+
+# element type of each debug buffer (float32 when not listed)
+_DBG_DTYPE = {"FINE_KEYS": np.uint64, "COARSE_WIN": np.int32, "GOAL_CELL": np.int32,
+              "ANCHOR_CELLS": np.int32, "GRID_START": np.int32, "POINT_COUNTS": np.int64}
 
 STAGES = ["partition", "grid", "rollout", "update"]
 
@@ -290,8 +294,7 @@ class Planner:
             torch.cuda.synchronize()
             return buf
         nbytes = _lib.aero_debug_size(self._h, wid)
-        dtype = {"FINE_KEYS": np.uint64, "COARSE_WIN": np.int32, "GOAL_CELL": np.int32,
-                 "ANCHOR_CELLS": np.int32, "GRID_START": np.int32}.get(what, np.float32)
+        dtype = _DBG_DTYPE.get(what, np.float32)
         buf = np.zeros(nbytes // np.dtype(dtype).itemsize, dtype)
         _check(_lib.aero_get_debug(self._h, wid, buf.ctypes.data, nbytes, stream_p), "aero_get_debug")
         torch.cuda.synchronize()
@@ -447,8 +450,7 @@ class Batch:
             buf = np.zeros((int(meta[1]), 4), np.float32)
         else:
             nbytes = _lib.aero_batch_debug_size(self._h, slot, wid)
-            dtype = {"FINE_KEYS": np.uint64, "COARSE_WIN": np.int32, "GOAL_CELL": np.int32,
-                     "ANCHOR_CELLS": np.int32, "GRID_START": np.int32}.get(what, np.float32)
+            dtype = _DBG_DTYPE.get(what, np.float32)
             buf = np.zeros(nbytes // np.dtype(dtype).itemsize, dtype)
         _check(_lib.aero_batch_get_debug(self._h, slot, wid, buf.ctypes.data, buf.nbytes, stream_p),
                "aero_batch_get_debug")

@@ -107,6 +107,8 @@ struct aero_planner {
   float* dbg_x = nullptr;
   float* dbg_d = nullptr;
   float* dbg_pre = nullptr;   // nominals before the gradient refinement
+  int2* part_counts = nullptr;  // per partition block or chunk: {non-finite, kept} points
+  int part_slots = 0;         // entries of part_counts
   // staging for aero_plan_step_host
   float* stage_cloud = nullptr;
   float* stage_unom = nullptr;
@@ -120,6 +122,8 @@ struct aero_planner {
   UpdateArgs last_ctx{};  // state, dynamics, costs, grid and guides of the last step
   int last_ntiles = 0;
   int last_nb = 0;
+  int last_part_slots = 0;    // part_counts entries written by the last step
+  int64_t last_n_points = 0;
   // stage timing (aero_profile_enable / aero_profile_read)
   struct ProfSlot {
     // start/end of: partition, grid, then rollout and update of every iteration
@@ -260,7 +264,7 @@ void free_all(aero_planner* pl) {
                   pl->cand,     pl->grid_range, pl->partials,
                   pl->sample_costs, pl->dU,      pl->stage2_x, pl->counter,   pl->status,   pl->dbg_u,
                   pl->dbg_x,    pl->dbg_d,      pl->stage_cloud,      pl->stage_unom,   pl->stage_ubest,
-                  pl->stage_cand,   pl->stage_best,   pl->dbg_pre};
+                  pl->stage_cand,   pl->stage_best,   pl->dbg_pre,      pl->part_counts};
   for (void* q : ptrs) dev_free(q);
 }
 
@@ -368,6 +372,7 @@ void make_step_args(aero_planner* pl, const aero_state_t* x0, const float* cloud
   pa.check_hi = a.check_hi;
   pa.keys = pl->keys;
   pa.item_flag = a.raw ? pl->item_flag : nullptr;
+  pa.counts = pl->part_counts;
 
   CandArgs& ca = a.ca;
   ca.cloud = cloud;
@@ -503,6 +508,8 @@ void note_step(aero_planner* pl, const aero_params_t& p, const StepArgs& a) {
   pl->last_grid = a.grid;
   pl->last_ntiles = a.ntiles;
   pl->last_nb = a.nb;
+  pl->last_part_slots = partition_blocks(a.pa.n);
+  pl->last_n_points = a.pa.n;
 }
 
 // Enqueue one step; all pointers already validated.
@@ -682,6 +689,9 @@ int aero_create(const aero_limits_t* limits, aero_planner_t** out) {
   chk(alloc(&pl->dbg_x, (size_t)L.E_max * D * (L.T_max + 1) * 10));
   chk(alloc(&pl->dbg_d, (size_t)L.E_max * D * L.T_max));
   chk(alloc(&pl->dbg_pre, (size_t)L.E_max * L.T_max * 4));
+  // one count pair per partition block (single step) or chunk of points (batched)
+  pl->part_slots = (int)std::max<int64_t>(kPartBlocksMax, (L.n_points_max + kPartChunk - 1) / kPartChunk);
+  chk(alloc(&pl->part_counts, pl->part_slots));
   chk(alloc(&pl->stage_cloud, (size_t)L.n_points_max * 3));
   chk(alloc(&pl->stage_unom, (size_t)L.E_max * L.T_max * 4));
   chk(alloc(&pl->stage_ubest, (size_t)L.T_max * 4));
@@ -790,6 +800,7 @@ size_t aero_debug_size(aero_planner_t* pl, int32_t what) {
     case AERO_DBG_SAMPLE_X: return 4 * E * D * (T + 1) * 10;
     case AERO_DBG_SAMPLE_DIST: return 4 * E * D * T;
     case AERO_DBG_PRE_REFINE: return p.refine_steps > 0 ? 4 * E * T * 4 : 0;
+    case AERO_DBG_POINT_COUNTS: return 3 * sizeof(int64_t);
     default: return 0;
   }
 }
@@ -830,6 +841,22 @@ int aero_get_debug(aero_planner_t* pl, int32_t what, void* dst, size_t bytes, vo
     if (e != cudaSuccess) return cuda_fail(e);
     for (size_t c = 0; c <= (size_t)gcells; ++c) local[c] += off[c >> kScanTileShift];
     return cuda_fail(cudaMemcpy(dst, local.data(), need, cudaMemcpyDefault));
+  }
+  if (what == AERO_DBG_POINT_COUNTS) {
+    // synchronous: the per-block counts are summed on the host
+    if (bytes < 3 * sizeof(int64_t)) return AERO_ERR_INVALID_ARG;
+    std::vector<int2> c((size_t)pl->last_part_slots);
+    cudaError_t e = cudaSuccess;
+    if (!c.empty())
+      e = cudaMemcpyAsync(c.data(), pl->part_counts, sizeof(int2) * c.size(), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e);
+    int64_t out[3] = {pl->last_n_points, 0, 0};
+    for (const int2& v : c) {
+      out[1] += v.x;
+      out[2] += v.y;
+    }
+    return cuda_fail(cudaMemcpy(dst, out, sizeof(out), cudaMemcpyDefault));
   }
   const size_t need = aero_debug_size(pl, what);
   if (bytes < need) return AERO_ERR_INVALID_ARG;
@@ -958,7 +985,8 @@ constexpr size_t kNaBytes =
     align256(4 * ((size_t)kNaTiles + 1)) + align256(16 * (size_t)kNaCand) +
     align256(8 * (size_t)kNaGridCells) +
     align256(4 * (size_t)kNaE * kNaNb * (4 + 4 * kNaT)) + align256(4 * (size_t)kNaE * kNaK) +
-    align256(4 * (size_t)kNaE * (kNaT + 1) * 10) + align256(4 * kCounterWords) + align256(4);
+    align256(4 * (size_t)kNaE * (kNaT + 1) * 10) + align256(4 * kCounterWords) +
+    align256(8 * (size_t)kPartBlocksMax) + align256(4);
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNaBytes];
 
@@ -1017,6 +1045,8 @@ void noalloc_carve(unsigned char* base, aero_planner& pl) {
   pl.sample_costs = reinterpret_cast<float*>(take(4 * (size_t)kNaE * kNaK));
   pl.stage2_x = reinterpret_cast<float*>(take(4 * (size_t)kNaE * (kNaT + 1) * 10));
   pl.counter = reinterpret_cast<unsigned int*>(take(4 * kCounterWords));
+  pl.part_counts = reinterpret_cast<int2*>(take(8 * (size_t)kPartBlocksMax));
+  pl.part_slots = kPartBlocksMax;
   pl.status = reinterpret_cast<int*>(take(4));
 }
 
@@ -1369,6 +1399,8 @@ int batch_enqueue(aero_batch* b, const aero_batch_item_t* items, int n, cudaStre
     pl->last = items[i].params;
     pl->last_grid = meta[i].grid;
     pl->last_ntiles = meta[i].ntiles;
+    pl->last_part_slots = (int)((items[i].n_points + kPartChunk - 1) / kPartChunk);
+    pl->last_n_points = items[i].n_points;
     pl->last_nb = meta[i].nb;
   }
   b->last_n = n;

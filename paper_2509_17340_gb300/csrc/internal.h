@@ -55,6 +55,7 @@ struct PartitionArgs {
   int check_lo, check_hi;
   unsigned long long* keys;
   int* item_flag;  // collision set = every kept point: 1 where the point is kept, else 0
+  int2* counts;    // per block (batched: per chunk of points): {non-finite points, kept points}
 };
 
 // Count and scatter passes of the candidate lists.
@@ -229,6 +230,8 @@ cudaError_t batch_grid_occupancy(int out[4]);
 cudaError_t batch_rollout_occupancy(int out[4], int T_max);
 
 cudaError_t launch_partition(const PartitionArgs& a, const PartTables& t, cudaStream_t s);
+int partition_blocks(int64_t n);  // CTAs of launch_partition for n points (0 when n == 0)
+constexpr int kPartBlocksMax = 152 * 16;
 cudaError_t launch_grid_count(const CandArgs& ca, const GuideArgs& ga, const PartTables& t,
                               cudaStream_t s);
 cudaError_t launch_grid_scan(int* count, int* fill, int* local, int* tile_sum, int* tile_off,

@@ -70,12 +70,15 @@ __device__ __forceinline__ void load_tables(const PartTables& t, int A, int El, 
   }
 }
 
-__device__ __forceinline__ void partition_point(const PartitionArgs& a, const SmemTables& st,
-                                                int64_t i) {
+// Returns 0 for a non-finite point, 1 for a point outside the partition's
+// range or elevation span, 2 for a kept point.
+__device__ __forceinline__ int partition_point(const PartitionArgs& a, const SmemTables& st,
+                                               int64_t i) {
   const float px = __ldg(a.cloud + 3 * i), py = __ldg(a.cloud + 3 * i + 1),
               pz = __ldg(a.cloud + 3 * i + 2);
   int cell = -1;
-  if (isfinite(px) && isfinite(py) && isfinite(pz)) {
+  const bool finite = isfinite(px) && isfinite(py) && isfinite(pz);
+  if (finite) {
     const float dx = sub(px, a.p0[0]), dy = sub(py, a.p0[1]), dz = sub(pz, a.p0[2]);
     float b[3];
     to_body(a.R, dx, dy, dz, b);
@@ -98,6 +101,25 @@ __device__ __forceinline__ void partition_point(const PartitionArgs& a, const Sm
     }
   }
   if (a.item_flag) a.item_flag[i] = cell >= 0 ? 1 : 0;
+  return !finite ? 0 : cell >= 0 ? 2 : 1;
+}
+
+// The block's totals of (non-finite, kept) points, stored by thread 0 at *out.
+__device__ __forceinline__ void block_count2(int nf, int kept, int2* out) {
+  __shared__ int s_nf, s_kept;
+  if (threadIdx.x == 0) {
+    s_nf = 0;
+    s_kept = 0;
+  }
+  __syncthreads();
+  nf = __reduce_add_sync(0xffffffffu, nf);
+  kept = __reduce_add_sync(0xffffffffu, kept);
+  if ((threadIdx.x & 31) == 0 && (nf | kept)) {
+    atomicAdd(&s_nf, nf);
+    atomicAdd(&s_kept, kept);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) *out = make_int2(s_nf, s_kept);
 }
 
 __global__ void __launch_bounds__(256) k_partition(PartitionArgs a, PartTables t) {
@@ -106,8 +128,13 @@ __global__ void __launch_bounds__(256) k_partition(PartitionArgs a, PartTables t
   load_tables(t, a.A, a.El, st);
   __syncthreads();
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += stride)
-    partition_point(a, st, i);
+  int nf = 0, kept = 0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += stride) {
+    const int r = partition_point(a, st, i);
+    nf += r == 0;
+    kept += r == 2;
+  }
+  if (a.counts) block_count2(nf, kept, a.counts + blockIdx.x);
 }
 
 // ---------------------------------------------------------------------------
@@ -503,9 +530,15 @@ __global__ void __launch_bounds__(256) k_b_partition(BatchView v) {
       __syncthreads();
       cur = it;
     }
-    const int64_t base = (u - s_pre[it]) * kPartChunk;
+    const int64_t chunk = u - s_pre[it], base = chunk * kPartChunk;
+    int nf = 0, kept = 0;
     for (int r = threadIdx.x; r < kPartChunk; r += blockDim.x)
-      if (base + r < s_pa.n) partition_point(s_pa, st, base + r);
+      if (base + r < s_pa.n) {
+        const int c = partition_point(s_pa, st, base + r);
+        nf += c == 0;
+        kept += c == 2;
+      }
+    if (s_pa.counts) block_count2(nf, kept, s_pa.counts + chunk);
   }
 }
 
@@ -616,9 +649,11 @@ int blocks_for(int64_t n, int threads, int cap) {
 
 }  // namespace
 
+int partition_blocks(int64_t n) { return n > 0 ? blocks_for(n, 256, kPartBlocksMax) : 0; }
+
 cudaError_t launch_partition(const PartitionArgs& a, const PartTables& t, cudaStream_t s) {
   if (a.n == 0) return cudaSuccess;
-  return launch_k(k_partition, dim3(blocks_for(a.n, 256, 152 * 16)), dim3(256), s, true, a, t);
+  return launch_k(k_partition, dim3(partition_blocks(a.n)), dim3(256), s, true, a, t);
 }
 
 cudaError_t launch_grid_count(const CandArgs& ca, const GuideArgs& ga, const PartTables& t,

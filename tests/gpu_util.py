@@ -36,6 +36,7 @@ def run_gpu(aero, planner, w, P: dict, u0: np.ndarray, cloud=None, debug=True) -
         E, K, T = P["E"], P["K"], P["T"]
         D = min(P.get("debug_samples", 0), K)
         out["keys"] = planner.debug("FINE_KEYS")
+        out["point_counts"] = planner.debug("POINT_COUNTS")
         out["coarse"] = planner.debug("COARSE_WIN")
         out["goal_cell"] = int(planner.debug("GOAL_CELL")[0])
         out["anchor_cells"] = planner.debug("ANCHOR_CELLS")

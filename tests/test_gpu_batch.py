@@ -68,7 +68,7 @@ def _check_slot(aero, orc, batch, pl, slot, w, b, u_in, dev, oracle_budget=1_000
     import torch
     P = w.params
     un, ub, cand, best = _planner_step(aero, pl, w, u_in, dev)
-    for what in ("GOAL_CELL", "ANCHOR_CELLS", "COARSE_WIN"):
+    for what in ("GOAL_CELL", "ANCHOR_CELLS", "COARSE_WIN", "POINT_COUNTS"):
         assert np.array_equal(batch.debug(slot, what), pl.debug(what)), (slot, what)
     for what in ("ANCHORS", "GUIDES"):
         np.testing.assert_allclose(batch.debug(slot, what), pl.debug(what), rtol=1e-6, atol=1e-5)

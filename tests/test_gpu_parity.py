@@ -145,6 +145,18 @@ def test_partition_keys_bit_exact(results, orc, name):
 
 
 @pytest.mark.parametrize("name", CASES)
+def test_point_counts(results, orc, name):
+    """Points given, skipped as non-finite, kept by the partition: exact."""
+    w, u0, g, o = results(name)
+    cloud = np.asarray(w.cloud, np.float32).reshape(-1, 3)
+    nonfinite = int((~np.isfinite(cloud).all(axis=1)).sum())
+    _, kept = orc.partition(cloud, w.p0, w.q0, w.params)
+    assert list(g["point_counts"]) == [len(cloud), nonfinite, kept]
+    if name == "degenerate":
+        assert nonfinite == 2
+
+
+@pytest.mark.parametrize("name", CASES)
 def test_coarse_goal_and_anchor_cells_bit_exact(results, orc, name):
     w, u0, g, o = results(name)
     P = w.params
