@@ -290,8 +290,9 @@ int aero_batch_tune(aero_batch_t* batch, const aero_batch_item_t* items, int32_t
                     void* stream, aero_batch_config_t* best, float* best_ms);
 
 /* OR of the status words of the batch's slots (bit 0: an update's normaliser
- * was not a positive finite number; bit 1: a candidate list overflowed), which
- * are then cleared.  Synchronous. */
+ * was not a positive finite number; bit 1: a candidate list overflowed) and, in
+ * the checked build, of the index-check bits (1 << 8 and up, see
+ * aero_sync_status), which are then cleared.  Synchronous. */
 int aero_batch_sync_status(aero_batch_t* batch, int32_t* status);
 
 /* Debug copies of slot `slot`'s last step, as aero_debug_size / aero_get_debug
@@ -373,6 +374,10 @@ int aero_shift_nominal(float* u_nom, int32_t E, int32_t T, int32_t shift, float*
  * meant for production callers. */
 int aero_test_fail_alloc(int64_t n);
 int64_t aero_test_alloc_stats(int64_t* live);
+/* Checked build only: record `bits` (> 0) as if an index check had failed, so
+ * that a test can see aero_sync_status report it; the product build returns
+ * AERO_ERR_INVALID_ARG. */
+int aero_test_raise_check(int32_t bits);
 
 /* Copy debug buffer `what` of the last step into dst (host or device), at most
  * `bytes` bytes, ordered on `stream` (asynchronous for device dst and pinned
@@ -381,7 +386,12 @@ int aero_get_debug(aero_planner_t* planner, int32_t what, void* dst, size_t byte
 
 /* Synchronise `stream`, then report the kernels' status word: AERO_OK, or
  * DEVICE_CHECK when a kernel recorded an internal inconsistency, or CUDA when
- * the stream holds an error.  Clears the status word. */
+ * the stream holds an error.  Clears the status word.
+ * The checked build of the library (libaero_mppi_checked.so, compiled with
+ * AERO_CHECKED) also guards the indices the kernels rely on (fine cell, grid
+ * cell, candidate range, query slot and item, partial row, accumulation slot):
+ * a failed check skips the access and is reported here as DEVICE_CHECK (it then
+ * synchronises the device).  The product build has no such checks. */
 int aero_sync_status(aero_planner_t* planner, void* stream);
 
 /* ---- stage timing --------------------------------------------------------

@@ -13,12 +13,15 @@ import os
 import numpy as np
 import torch
 
+from . import library_name
+
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libaero_mppi.so")
+LIB_PATH = os.path.join(_HERE, library_name())
 
 if not os.path.exists(LIB_PATH):
     raise ImportError(f"{LIB_PATH} is missing: build it with "
-                      "`python -m paper_2509_17340_gb300.build` (needs nvcc); there is no CPU fallback")
+                      "`python -m paper_2509_17340_gb300.build` (`--checked` for the checked "
+                      "build; needs nvcc); there is no CPU fallback")
 
 _lib = C.CDLL(LIB_PATH)
 
@@ -124,6 +127,7 @@ _lib.aero_shift_nominal.argtypes = [_vp, C.c_int32, C.c_int32, C.c_int32, _vp, _
 _lib.aero_test_fail_alloc.argtypes = [C.c_int64]
 _lib.aero_test_alloc_stats.argtypes = [C.POINTER(C.c_int64)]
 _lib.aero_test_alloc_stats.restype = C.c_int64
+_lib.aero_test_raise_check.argtypes = [C.c_int32]
 _lib.aero_status_str.argtypes = [C.c_int]
 _lib.aero_status_str.restype = C.c_char_p
 
@@ -151,6 +155,12 @@ def inject_alloc_failure(n: int) -> None:
     """Make the n-th next library allocation fail once (``aero_test_fail_alloc``);
     n < 0 cancels a pending failure."""
     _lib.aero_test_fail_alloc(int(n))
+
+
+def raise_check(bits: int) -> int:
+    """Checked build: record `bits` as a failed index check (tests); returns the
+    status code (AERO_ERR_INVALID_ARG from the product build)."""
+    return int(_lib.aero_test_raise_check(int(bits)))
 
 
 def alloc_stats() -> tuple[int, int]:

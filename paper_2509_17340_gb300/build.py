@@ -18,6 +18,9 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libaero_mppi.so")
+# the same sources with AERO_CHECKED: every index the kernels rely on is
+# checked on the device and a failed check is reported by aero_sync_status
+CHECKED_LIB = os.path.join(PKG, "libaero_mppi_checked.so")
 SOURCES = ["aero_mppi.cu", "partition.cu", "rollout.cu", "accum.cu"]
 HEADERS = ["internal.h", "device.cuh", "adjoint.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
@@ -30,32 +33,37 @@ def nvcc() -> str:
     raise RuntimeError("nvcc not found: the CUDA toolkit is required to build libaero_mppi.so")
 
 
-def _flags(verbose_ptxas: bool) -> list[str]:
+def _flags(verbose_ptxas: bool, checked: bool = False) -> list[str]:
     f = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-ffp-contract=off",
                 "-I", os.path.join(ROOT, "include")]
+    if checked:
+        f += ["-DAERO_CHECKED"]
     if verbose_ptxas:
         f += ["-Xptxas", "-v"]
     return f
 
 
-def _stale() -> bool:
-    if not os.path.exists(LIB):
+def _stale(lib: str = LIB) -> bool:
+    if not os.path.exists(lib):
         return True
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     deps = [os.path.join(CSRC, s) for s in SOURCES + HEADERS] + [os.path.join(ROOT, "include", "aero_mppi.h")]
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(force: bool = False, verbose_ptxas: bool = False) -> str:
-    """Compile and link; returns the library path.  Skips work when up to date."""
-    if not force and not _stale():
-        return LIB
-    os.makedirs(BUILD, exist_ok=True)
+def build(force: bool = False, verbose_ptxas: bool = False, checked: bool = False) -> str:
+    """Compile and link; returns the library path.  Skips work when up to date.
+    checked: the checked build (CHECKED_LIB) instead of the product library."""
+    lib = CHECKED_LIB if checked else LIB
+    if not force and not _stale(lib):
+        return lib
+    bdir = os.path.join(BUILD, "checked") if checked else BUILD
+    os.makedirs(bdir, exist_ok=True)
     cc = nvcc()
-    flags = _flags(verbose_ptxas)
+    flags = _flags(verbose_ptxas, checked)
 
     def compile_one(src: str) -> str:
-        obj = os.path.join(BUILD, src.replace(".cu", ".o"))
+        obj = os.path.join(bdir, src.replace(".cu", ".o"))
         cmd = [cc, *flags, "-c", os.path.join(CSRC, src), "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
@@ -66,13 +74,14 @@ def build(force: bool = False, verbose_ptxas: bool = False) -> str:
 
     with ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
         objs = list(ex.map(compile_one, SOURCES))
-    tmp = LIB + f".tmp{os.getpid()}"
+    tmp = lib + f".tmp{os.getpid()}"
     r = subprocess.run([cc, *ARCH, "-shared", "-o", tmp, *objs], capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":
-    print(build(force="--force" in sys.argv, verbose_ptxas="-v" in sys.argv))
+    print(build(force="--force" in sys.argv, verbose_ptxas="-v" in sys.argv,
+                checked="--checked" in sys.argv))

@@ -107,6 +107,7 @@ __global__ void __launch_bounds__(kThreads) k_accum_gather(const float* __restri
       const int mid = (lo + hi + 1) >> 1;
       if (a.pre[mid] <= i) lo = mid; else hi = mid - 1;
     }
+    if (!AERO_CHECK(a.slot[lo] >= 0 && i - a.pre[lo] < N, ::aero::kChkAccum)) continue;
     const int64_t src = (int64_t)a.slot[lo] * N + (i - a.pre[lo]);
     float x = __ldg(ring + 3 * src), y = __ldg(ring + 3 * src + 1), z = __ldg(ring + 3 * src + 2);
     if (a.body) {
@@ -148,6 +149,21 @@ int blocks_for(int64_t n) {
 int fail(cudaError_t e) { return e == cudaSuccess ? AERO_OK : AERO_ERR_CUDA; }
 
 }  // namespace
+
+namespace aero {
+cudaError_t check_word_accum(int* out, bool clear) {
+#ifdef AERO_CHECKED
+  cudaError_t e = cudaMemcpyFromSymbol(out, g_check_word, sizeof(int));
+  const int zero = 0;
+  if (e == cudaSuccess && clear) e = cudaMemcpyToSymbol(g_check_word, &zero, sizeof(int));
+  return e;
+#else
+  (void)clear;
+  *out = 0;
+  return cudaSuccess;
+#endif
+}
+}  // namespace aero
 
 extern "C" {
 

@@ -61,6 +61,24 @@ cudaError_t host_malloc(void** p, size_t bytes) {
   return counted(cudaMallocHost(p, bytes), p);
 }
 
+cudaError_t read_check_words(int* out, bool clear) {
+  *out = 0;
+#ifdef AERO_CHECKED
+  cudaError_t e = cudaDeviceSynchronize();
+  int w = 0;
+  if (e == cudaSuccess) e = check_word_partition(&w, clear);
+  *out |= w;
+  if (e == cudaSuccess) e = check_word_rollout(&w, clear);
+  *out |= w;
+  if (e == cudaSuccess) e = check_word_accum(&w, clear);
+  *out |= w;
+  return e;
+#else
+  (void)clear;
+  return cudaSuccess;
+#endif
+}
+
 void dev_free(void* p) {
   if (!p) return;
   cudaFree(p);
@@ -715,6 +733,13 @@ int aero_test_fail_alloc(int64_t n) {
   return AERO_OK;
 }
 
+int aero_test_raise_check(int32_t bits) {
+  if (bits <= 0) return AERO_ERR_INVALID_ARG;
+  const cudaError_t e = raise_check_partition(bits);
+  if (e == cudaErrorNotSupported) return AERO_ERR_INVALID_ARG;
+  return e == cudaSuccess ? AERO_OK : AERO_ERR_CUDA;
+}
+
 int64_t aero_test_alloc_stats(int64_t* live) {
   if (live) *live = g_alloc_live.load();
   return g_alloc_total.load();
@@ -888,7 +913,9 @@ int aero_sync_status(aero_planner_t* pl, void* stream) {
   cudaError_t e = cudaMemcpyAsync(&st, pl->status, sizeof(int), cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return AERO_ERR_CUDA;
-  if (st != 0) {
+  int cw = 0;
+  if (read_check_words(&cw, true) != cudaSuccess) return AERO_ERR_CUDA;
+  if (st != 0 || cw != 0) {
     cudaMemsetAsync(pl->status, 0, sizeof(int), s);
     cudaStreamSynchronize(s);
     return AERO_ERR_DEVICE_CHECK;
@@ -1554,7 +1581,9 @@ int aero_batch_sync_status(aero_batch_t* b, int32_t* status) {
     if (st != 0 && cudaMemset(pl->status, 0, sizeof(int)) != cudaSuccess) return AERO_ERR_CUDA;
     acc |= st;
   }
-  *status = acc;
+  int cw = 0;
+  if (read_check_words(&cw, true) != cudaSuccess) return AERO_ERR_CUDA;
+  *status = acc | cw;
   return AERO_OK;
 }
 

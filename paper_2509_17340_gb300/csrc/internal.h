@@ -282,6 +282,39 @@ cudaError_t launch_k(void (*kernel)(KArgs...), dim3 grid, dim3 block, cudaStream
   return launch_ks(kernel, grid, block, 0, s, pdl, std::forward<Args>(args)...);
 }
 
+// ---------------------------------------------------------------------------
+// Checked builds (-DAERO_CHECKED, libaero_mppi_checked.so).  AERO_CHECK(cond,
+// bit) guards an index the kernels rely on: in a checked build a failed
+// condition records `bit` in the translation unit's check word and the guarded
+// access is skipped (no trap, no assert); aero_sync_status then reports
+// AERO_ERR_DEVICE_CHECK.  In the product build it is the constant true.
+// ---------------------------------------------------------------------------
+enum CheckBit : int {
+  kChkFineCell = 1 << 8,     // partition: fine cell outside the partition
+  kChkGridCell = 1 << 9,     // candidate grid: cell outside the grid
+  kChkRange = 1 << 10,       // candidate range beyond the entries written
+  kChkQuery = 1 << 11,       // split pass / Stage II: query slot or item outside its list
+  kChkPartial = 1 << 12,     // partial row or sample outside the instance's block
+  kChkAccum = 1 << 13,       // accumulation ring slot
+};
+#ifdef AERO_CHECKED
+static __device__ int g_check_word;
+__device__ __forceinline__ bool check_fail(int bit) {
+  atomicOr(&g_check_word, bit);
+  return false;
+}
+#define AERO_CHECK(cond, bit) ((cond) ? true : ::aero::check_fail(bit))
+#else
+#define AERO_CHECK(cond, bit) true
+#endif
+// The check words of the library's translation units, or'ed (0 in the product
+// build); `clear` resets them.  Synchronises the device.
+cudaError_t read_check_words(int* out, bool clear);
+cudaError_t check_word_partition(int* out, bool clear);
+cudaError_t check_word_rollout(int* out, bool clear);
+cudaError_t check_word_accum(int* out, bool clear);
+cudaError_t raise_check_partition(int bits);  // checked build: record `bits` (tests)
+
 // Every device and pinned host allocation of the library goes through these
 // four calls.  They count live allocations and let a test make the n-th next
 // allocation fail (aero_test_fail_alloc), so that each error path of the

@@ -95,8 +95,10 @@ __device__ __forceinline__ int partition_point(const PartitionArgs& a, const Sme
         const int c = je * a.A + ia;
         const unsigned long long key =
             ((unsigned long long)__float_as_uint(r2) << 32) | (unsigned long long)(uint32_t)i;
-        atomicMin(a.keys + c, key);
-        cell = c;
+        if (AERO_CHECK(c >= 0 && c < a.A * a.El, kChkFineCell)) {
+          atomicMin(a.keys + c, key);
+          cell = c;
+        }
       }
     }
   }
@@ -193,6 +195,7 @@ __device__ __forceinline__ void cand_task(const CandArgs& a, int64_t it, int lan
                      gap2(pz, g.origin + z * g.h, g.h);
     if (d2 >= r2) continue;
     const int c = (z * g.G + y) * g.G + x;
+    if (!AERO_CHECK(c >= 0 && c < g.G * g.G * g.G, kChkGridCell)) continue;
     if (!kScatter) {
       atomicAdd(a.count + c, 1);
     } else {
@@ -471,7 +474,7 @@ __device__ __forceinline__ void range_cell(const int* local, const int* tile_off
                                            int2* range, int c) {
   const int s = min(local[c] + tile_off[c >> kScanTileShift], cap);
   const int e = min(local[c + 1] + tile_off[(c + 1) >> kScanTileShift], cap);
-  range[c] = make_int2(s, e - s);
+  range[c] = AERO_CHECK(s >= 0 && e >= s, kChkRange) ? make_int2(s, e - s) : make_int2(0, 0);
 }
 
 // K2c: the scatter pass and, in the remaining blocks, the {start, count} of
@@ -714,4 +717,31 @@ cudaError_t launch_philox(uint32_t k0, uint32_t k1, uint32_t c1, uint32_t c2, ui
   return cudaGetLastError();
 }
 
+cudaError_t raise_check_partition(int bits) {
+#ifdef AERO_CHECKED
+  int w = 0;
+  cudaError_t e = cudaMemcpyFromSymbol(&w, g_check_word, sizeof(int));
+  w |= bits;
+  if (e == cudaSuccess) e = cudaMemcpyToSymbol(g_check_word, &w, sizeof(int));
+  return e;
+#else
+  (void)bits;
+  return cudaErrorNotSupported;
+#endif
+}
+
+cudaError_t check_word_partition(int* out, bool clear) {
+#ifdef AERO_CHECKED
+  cudaError_t e = cudaMemcpyFromSymbol(out, g_check_word, sizeof(int));
+  const int zero = 0;
+  if (e == cudaSuccess && clear) e = cudaMemcpyToSymbol(g_check_word, &zero, sizeof(int));
+  return e;
+#else
+  (void)clear;
+  *out = 0;
+  return cudaSuccess;
+#endif
+}
+
 }  // namespace aero
+

@@ -169,6 +169,7 @@ __device__ __forceinline__ void rollout_unit(const RolloutArgs& a, int e, int b,
   }
   __syncthreads();
   float* out = a.partials + ((size_t)e * a.nb + b) * (4 + 4 * T);
+  if (!AERO_CHECK(b < a.nb && e < a.E, kChkPartial)) return;
   if (tid == 0) {
     float eta = 0.0f;
 #pragma unroll
@@ -410,6 +411,7 @@ __device__ __forceinline__ void rollout_split_unit(const RolloutArgs& a, int e, 
       const int slot = m.qslot[lo];
       const int first = (it - m.qitem[lo]) * kItem;
       const int n = r.y - first < kItem ? r.y - first : kItem;
+      if (!AERO_CHECK(slot < kChunkQ && first >= 0 && n > 0 && r.x >= 0, kChkQuery)) continue;
       const float4 xa = m.xa[slot];
       const float d2 = scan_min<kItem>(a.grid.pts + r.x + first, n, xa.x, xa.y, xa.z, dmax2);
       if (d2 < dmax2) atomicMin(m.d2 + slot, __float_as_int(d2));  // non-negative: int order
@@ -461,7 +463,8 @@ __device__ __forceinline__ void rollout_split_unit(const RolloutArgs& a, int e, 
   const float wk = active ? expf((rho - Sk) * a.inv_lambda) : 0.0f;
   const float eta = warp_sum(wk);
   float* out = a.partials + ((size_t)e * a.nb + b) * (4 + 4 * T);
-  if (tid == 0) {
+  const bool row_ok = AERO_CHECK(b < a.nb && e < a.E, kChkPartial);
+  if (tid == 0 && row_ok) {
     out[0] = rho;
     out[1] = eta;
   }
@@ -471,7 +474,7 @@ __device__ __forceinline__ void rollout_split_unit(const RolloutArgs& a, int e, 
     const float4 du = active ? make_float4(u.x - un.x, u.y - un.y, u.z - un.z, u.w - un.w)
                              : make_float4(0.f, 0.f, 0.f, 0.f);
     const float r = warp_sum4(wk * du.x, wk * du.y, wk * du.z, wk * du.w, lane);
-    if ((lane & 7) == 0) out[4 + 4 * j + (lane >> 3)] = r;
+    if ((lane & 7) == 0 && row_ok) out[4 + 4 * j + (lane >> 3)] = r;
   }
   __syncthreads();  // shared memory free for the next unit
 }
@@ -634,6 +637,7 @@ __device__ __forceinline__ void update_unit(const UpdateArgs& a, int e, bool fin
     const int j = s_qslot[lo];
     const int first = (it - s_qitem[lo]) * kItem;
     const int n = r.y - first < kItem ? r.y - first : kItem;
+    if (!AERO_CHECK(j < T && first >= 0 && n > 0 && r.x >= 0, kChkQuery)) continue;
     const float* X = s_x + (j + 1) * 10;
     const float d2 = scan_min<kItem>(a.grid.pts + r.x + first, n, X[0], X[1], X[2], dmax2);
     if (d2 < dmax2) atomicMin(s_d2 + j, __float_as_int(d2));  // non-negative: int order
@@ -923,4 +927,18 @@ cudaError_t launch_update(const UpdateArgs& a, cudaStream_t s) {
   return launch_k(k_update, dim3(a.E), dim3(UT), s, true, a);
 }
 
+cudaError_t check_word_rollout(int* out, bool clear) {
+#ifdef AERO_CHECKED
+  cudaError_t e = cudaMemcpyFromSymbol(out, g_check_word, sizeof(int));
+  const int zero = 0;
+  if (e == cudaSuccess && clear) e = cudaMemcpyToSymbol(g_check_word, &zero, sizeof(int));
+  return e;
+#else
+  (void)clear;
+  *out = 0;
+  return cudaSuccess;
+#endif
+}
+
 }  // namespace aero
+

@@ -99,3 +99,11 @@ def test_allocation_test_hooks_without_cuda(so):
     assert so.aero_test_alloc_stats(None) == total
     assert so.aero_test_fail_alloc(C.c_int64(3)) == 0
     assert so.aero_test_fail_alloc(C.c_int64(-1)) == 0
+
+
+def test_checked_build_exports_every_declared_symbol():
+    # the checked build compiles the same sources with AERO_CHECKED
+    from paper_2509_17340_gb300 import build
+    lib = C.CDLL(build.build(checked=True))
+    for name in declared_functions():
+        assert hasattr(lib, name), name
