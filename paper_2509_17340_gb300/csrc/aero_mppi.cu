@@ -430,7 +430,6 @@ void make_step_args(aero_planner* pl, const aero_state_t* x0, const float* cloud
   ga.v_end = p.v_end;
   for (int i = 0; i < 3; ++i) ga.v0[i] = x0->v[i];
   ga.coarse_win = pl->coarse_win;
-  ga.counter = pl->counter + 1;
   ga.cells = pl->cells;
   ga.anchors = pl->anchors;
   ga.guides = pl->guides;
@@ -577,10 +576,11 @@ int enqueue_step(aero_planner* pl, const aero_state_t* x0, const float* cloud, i
     prof->launches[AERO_STAGE_ROLLOUT] = p.iters;
     prof->launches[AERO_STAGE_UPDATE] = rollout_runs_update(a.ra) ? 0 : p.iters;
   }
-  // count pass + coarse argmax/anchors/guides, scan, scatter + cell ranges
-  if ((e = launch_grid_count(a.ca, a.ga, a.tab, s)) != cudaSuccess) return cuda_fail(e);
+  // count pass + coarse argmax, scan + goal cone/anchors/guides, scatter + cell ranges
+  if ((e = launch_grid_count(a.ca, a.ga, s)) != cudaSuccess) return cuda_fail(e);
   if ((e = launch_grid_scan(pl->grid_count, pl->grid_fill, pl->grid_local, pl->tile_sum,
-                            pl->tile_off, a.gcells + 1, a.ntiles, pl->counter + 2, s)) != cudaSuccess)
+                            pl->tile_off, a.gcells + 1, a.ntiles, pl->counter + 2, a.ga, a.tab,
+                            s)) != cudaSuccess)
     return cuda_fail(e);
   if ((e = launch_grid_scatter(a.ca, pl->grid_range, a.gcells, s)) != cudaSuccess)
     return cuda_fail(e);

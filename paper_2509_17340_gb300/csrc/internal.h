@@ -12,8 +12,8 @@ constexpr int kMaxAz = 512;
 constexpr int kMaxEl = 256;
 constexpr int kMaxE = 64;
 // Tickets of last-CTA patterns, zero between launches: [0] the update's
-// selection, [1] the coarse blocks, [2] the grid scan, [3 + e] the Stage I
-// CTAs of instance e in the split pass that also runs the update.
+// selection, [1] unused, [2] the grid scan, [3 + e] the Stage I CTAs of
+// instance e in the split pass that also runs the update.
 constexpr int kCounterWords = 3 + kMaxE;
 constexpr int kMaxT = 128;
 constexpr int kGridMax = 96;         // collision-grid cells per axis, at most
@@ -92,7 +92,6 @@ struct GuideArgs {
   float v0[3];
   // outputs
   int* coarse_win;     // Ac * Ec
-  unsigned int* counter; // last-block ticket of the coarse blocks, 0 between launches
   int* cells;          // [0] goal fine cell, [1 + e] anchor coarse cell
   float* anchors;      // E x 3 (relative to p0)
   float* guides;       // E x T x 3 (relative to p0)
@@ -232,10 +231,11 @@ cudaError_t batch_rollout_occupancy(int out[4], int T_max);
 cudaError_t launch_partition(const PartitionArgs& a, const PartTables& t, cudaStream_t s);
 int partition_blocks(int64_t n);  // CTAs of launch_partition for n points (0 when n == 0)
 constexpr int kPartBlocksMax = 152 * 16;
-cudaError_t launch_grid_count(const CandArgs& ca, const GuideArgs& ga, const PartTables& t,
-                              cudaStream_t s);
+// count pass + coarse argmax; then the tile scans + goal cone, anchors, guides
+cudaError_t launch_grid_count(const CandArgs& ca, const GuideArgs& ga, cudaStream_t s);
 cudaError_t launch_grid_scan(int* count, int* fill, int* local, int* tile_sum, int* tile_off,
-                             int ncells, int ntiles, unsigned int* counter, cudaStream_t s);
+                             int ncells, int ntiles, unsigned int* counter, const GuideArgs& ga,
+                             const PartTables& t, cudaStream_t s);
 cudaError_t launch_grid_scatter(const CandArgs& ca, int2* range, int ncells, cudaStream_t s);
 // S(1) of n noise-free rollouts of instance `instance` and their gradients.
 struct CostGradArgs {

@@ -319,12 +319,7 @@ __device__ bool scan_tile(int* count, int* fill, int* local, int* tile_sum, int*
   return true;
 }
 
-__global__ void __launch_bounds__(kScanThreads) k_grid_scan(int* count, int* fill, int* local,
-                                                            int* tile_sum, int* tile_off, int ncells,
-                                                            int ntiles, unsigned int* counter) {
-  pdl_start();
-  scan_tile(count, fill, local, tile_sum, tile_off, ncells, ntiles, blockIdx.x, counter);
-}
+
 
 // Coarse argmax of one coarse cell (Eq. safe-vector) by one warp: larger r,
 // then nearer the coarse centre, then lower fine index; empty cones count as
@@ -434,39 +429,39 @@ __device__ void guides_block(const GuideArgs& a, const SmemTables& st) {
   }
 }
 
-// `ncb` blocks, one warp per coarse cell; the last of them to finish continues
-// with the goal cone, anchors and guides.
-__device__ void coarse_guides_block(const GuideArgs& a, const PartTables& t, int cb, int ncb) {
-  __shared__ SmemTables st;
-  __shared__ bool s_last;
-  const int ncoarse = a.Ac * a.Ec;
-  const int lane = threadIdx.x & 31, nwarp = ncb * (blockDim.x >> 5);
-  for (int cc = cb * (blockDim.x >> 5) + (threadIdx.x >> 5); cc < ncoarse; cc += nwarp)
-    coarse_cell(a, cc, lane);
-  if (lane == 0) __threadfence();  // the winners' writers publish them
-  __syncthreads();
-  if (threadIdx.x == 0) s_last = atomicAdd(a.counter, 1u) == (unsigned)(ncb - 1);
-  __syncthreads();
-  if (!s_last) return;
-  __threadfence();
-  load_tables(t, a.A, a.El, st);
-  if (threadIdx.x == 0) *a.counter = 0u;
-  __syncthreads();
-  guides_block(a, st);
-}
-
-// K2a + K3: the coarse argmax, goal cone, anchors and guides (they need only
-// the keys) in the first blocks, which are dispatched first because the last of
-// them continues with the anchors and guides; the count pass of the candidate
-// lists in the remaining blocks.
-__global__ void __launch_bounds__(256) k_grid_count(CandArgs ca, GuideArgs ga, PartTables t,
-                                                    int count_blocks) {
+// K2a + K3a: the coarse argmax (one warp per coarse cell; it needs only the
+// keys) in the first blocks, dispatched first; the count pass of the candidate
+// lists in the remaining blocks.  The goal cone, anchors and guides follow in
+// the scan launch, once every coarse winner is written.
+__global__ void __launch_bounds__(256) k_grid_count(CandArgs ca, GuideArgs ga, int count_blocks) {
   pdl_start();
   const int ncb = (int)gridDim.x - count_blocks;
-  if ((int)blockIdx.x < ncb)
-    coarse_guides_block(ga, t, blockIdx.x, ncb);
-  else
+  if ((int)blockIdx.x < ncb) {
+    const int ncoarse = ga.Ac * ga.Ec;
+    const int lane = threadIdx.x & 31, nwarp = ncb * (blockDim.x >> 5);
+    for (int cc = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); cc < ncoarse; cc += nwarp)
+      coarse_cell(ga, cc, lane);
+  } else {
     cand_pass<false>(ca, blockIdx.x - ncb, count_blocks);
+  }
+}
+
+// K2b + K3b: the tile scans in blocks [0, ntiles); block ntiles computes the
+// goal cone, anchors and guides (Sec. IV-B) from the coarse winners of the
+// count launch.
+__global__ void __launch_bounds__(kScanThreads) k_grid_scan(int* count, int* fill, int* local,
+                                                            int* tile_sum, int* tile_off, int ncells,
+                                                            int ntiles, unsigned int* counter,
+                                                            GuideArgs ga, PartTables t) {
+  pdl_start();
+  if ((int)blockIdx.x < ntiles) {
+    scan_tile(count, fill, local, tile_sum, tile_off, ncells, ntiles, blockIdx.x, counter);
+    return;
+  }
+  __shared__ SmemTables st;
+  load_tables(t, ga.A, ga.El, st);
+  __syncthreads();
+  guides_block(ga, st);
 }
 
 // {first entry, count} of cell c from the scanned counts.
@@ -659,19 +654,19 @@ cudaError_t launch_partition(const PartitionArgs& a, const PartTables& t, cudaSt
   return launch_k(k_partition, dim3(partition_blocks(a.n)), dim3(256), s, true, a, t);
 }
 
-cudaError_t launch_grid_count(const CandArgs& ca, const GuideArgs& ga, const PartTables& t,
-                              cudaStream_t s) {
+cudaError_t launch_grid_count(const CandArgs& ca, const GuideArgs& ga, cudaStream_t s) {
   // one warp per collision item up to four blocks per SM, then items per warp
   const int count_blocks = ca.n_items > 0 ? blocks_for(ca.n_items * 32, 256, 152 * 4) : 0;
   const int coarse_blocks = (ga.Ac * ga.Ec + 7) / 8;  // 8 warps per block
-  return launch_k(k_grid_count, dim3(count_blocks + coarse_blocks), dim3(256), s, true, ca, ga, t,
+  return launch_k(k_grid_count, dim3(count_blocks + coarse_blocks), dim3(256), s, true, ca, ga,
                   count_blocks);
 }
 
 cudaError_t launch_grid_scan(int* count, int* fill, int* local, int* tile_sum, int* tile_off,
-                             int ncells, int ntiles, unsigned int* counter, cudaStream_t s) {
-  return launch_k(k_grid_scan, dim3(ntiles), dim3(kScanThreads), s, true, count, fill, local, tile_sum,
-                  tile_off, ncells, ntiles, counter);
+                             int ncells, int ntiles, unsigned int* counter, const GuideArgs& ga,
+                             const PartTables& t, cudaStream_t s) {
+  return launch_k(k_grid_scan, dim3(ntiles + 1), dim3(kScanThreads), s, true, count, fill, local,
+                  tile_sum, tile_off, ncells, ntiles, counter, ga, t);
 }
 
 cudaError_t launch_grid_scatter(const CandArgs& ca, int2* range, int ncells, cudaStream_t s) {
