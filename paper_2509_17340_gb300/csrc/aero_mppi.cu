@@ -160,8 +160,6 @@ struct aero_planner {
 
 namespace {
 
-constexpr int kGridCellsMax = kGridMax * kGridMax * kGridMax;
-constexpr int kMaxTiles = (kGridCellsMax + 1 + kScanTile - 1) / kScanTile;
 // A point joins the lists of the cells within `reach` (just above d_max) of it:
 // at most 6^3 cells of edge d_max / 2, at most 3^3 of edge d_max (1 + 1/16).
 constexpr int kFineDup = 216, kCoarseDup = 27;
@@ -579,10 +577,11 @@ int enqueue_step(aero_planner* pl, const aero_state_t* x0, const float* cloud, i
   // count pass + coarse argmax, scan + goal cone/anchors/guides, scatter + cell ranges
   if ((e = launch_grid_count(a.ca, a.ga, s)) != cudaSuccess) return cuda_fail(e);
   if ((e = launch_grid_scan(pl->grid_count, pl->grid_fill, pl->grid_local, pl->tile_sum,
-                            pl->tile_off, a.gcells + 1, a.ntiles, pl->counter + 2, a.ga, a.tab,
-                            s)) != cudaSuccess)
+                            pl->tile_off, a.gcells + 1, a.ntiles, nullptr, a.ga, a.tab, s)) !=
+      cudaSuccess)
     return cuda_fail(e);
-  if ((e = launch_grid_scatter(a.ca, pl->grid_range, a.gcells, s)) != cudaSuccess)
+  if ((e = launch_grid_scatter(a.ca, pl->grid_range, a.gcells, pl->tile_sum, pl->tile_off,
+                               a.ntiles, s)) != cudaSuccess)
     return cuda_fail(e);
   mark(AERO_STAGE_GRID, 3);
 

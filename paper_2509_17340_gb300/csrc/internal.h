@@ -12,13 +12,15 @@ constexpr int kMaxAz = 512;
 constexpr int kMaxEl = 256;
 constexpr int kMaxE = 64;
 // Tickets of last-CTA patterns, zero between launches: [0] the update's
-// selection, [1] unused, [2] the grid scan, [3 + e] the Stage I CTAs of
+// selection, [1] unused, [2] the batched grid scan, [3 + e] the Stage I CTAs of
 // instance e in the split pass that also runs the update.
 constexpr int kCounterWords = 3 + kMaxE;
 constexpr int kMaxT = 128;
 constexpr int kGridMax = 96;         // collision-grid cells per axis, at most
+constexpr int kGridCellsMax = kGridMax * kGridMax * kGridMax;
 constexpr int kScanTile = 4096;      // cells per scan tile (1024 threads x 4)
 constexpr int kScanTileShift = 12;
+constexpr int kMaxTiles = (kGridCellsMax + 1 + kScanTile - 1) / kScanTile;
 constexpr int kRolloutThreads = 128; // samples per rollout CTA (one warp-group)
 constexpr int kQuadMaxSamples = 32768;  // E*K up to which the split Stage I pass runs
 
@@ -236,7 +238,10 @@ cudaError_t launch_grid_count(const CandArgs& ca, const GuideArgs& ga, cudaStrea
 cudaError_t launch_grid_scan(int* count, int* fill, int* local, int* tile_sum, int* tile_off,
                              int ncells, int ntiles, unsigned int* counter, const GuideArgs& ga,
                              const PartTables& t, cudaStream_t s);
-cudaError_t launch_grid_scatter(const CandArgs& ca, int2* range, int ncells, cudaStream_t s);
+// scatter + cell ranges; the tile offsets are computed here from the tile
+// totals of the scan launch (and written to tile_off)
+cudaError_t launch_grid_scatter(const CandArgs& ca, int2* range, int ncells, const int* tile_sum,
+                                int* tile_off, int ntiles, cudaStream_t s);
 // S(1) of n noise-free rollouts of instance `instance` and their gradients.
 struct CostGradArgs {
   UpdateArgs ctx;          // x0, dynamics, costs, grid, guides, T of the last step

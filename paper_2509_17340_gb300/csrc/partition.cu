@@ -305,11 +305,16 @@ __device__ bool scan_tile(int* count, int* fill, int* local, int* tile_sum, int*
         fill[i0 + u] = 0;
       }
   }
-  // the last block reads only the tile totals: only their writer fences
+  // the last block reads only the tile totals: only their writer fences.
+  // Without a ticket the tile offsets are left to the next launch.
   if (threadIdx.x == 0) {
     tile_sum[tile] = total;
-    __threadfence();
-    s_last = atomicAdd(counter, 1u) == (unsigned)(ntiles - 1);
+    if (counter) {
+      __threadfence();
+      s_last = atomicAdd(counter, 1u) == (unsigned)(ntiles - 1);
+    } else {
+      s_last = false;
+    }
   }
   __syncthreads();
   if (!s_last) return false;
@@ -473,18 +478,43 @@ __device__ __forceinline__ void range_cell(const int* local, const int* tile_off
 }
 
 // K2c: the scatter pass and, in the remaining blocks, the {start, count} of
-// every cell (which needs only the scan).
+// every cell (which needs only the scan).  Every block first turns the scan's
+// tile totals into tile offsets in shared memory (at most kMaxTiles of them);
+// block 0 also stores them.
 __global__ void __launch_bounds__(256) k_grid_scatter(CandArgs ca, int scatter_blocks,
-                                                      int2* __restrict__ range, int ncells) {
+                                                      int2* __restrict__ range, int ncells,
+                                                      const int* tile_sum, int* tile_off,
+                                                      int ntiles) {
   pdl_start();
+  __shared__ int s_off[kMaxTiles + 1];
+  __shared__ int s_warp[32];
+  __shared__ int s_carry;
+  if (threadIdx.x == 0) s_carry = 0;
+  __syncthreads();
+  for (int base = 0; base < ntiles; base += blockDim.x) {
+    const int i = base + threadIdx.x;
+    const int v = i < ntiles ? __ldg(tile_sum + i) : 0;
+    int total;
+    const int r = block_exclusive_scan(v, s_warp, total);
+    if (i < ntiles) s_off[i] = s_carry + r;
+    __syncthreads();
+    if (threadIdx.x == 0) s_carry += total;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) s_off[ntiles] = s_carry;
+  __syncthreads();
+  if (blockIdx.x == 0)
+    for (int i = threadIdx.x; i <= ntiles; i += blockDim.x) tile_off[i] = s_off[i];
   if ((int)blockIdx.x < scatter_blocks) {
-    cand_pass<true>(ca, blockIdx.x, scatter_blocks);
+    CandArgs a = ca;
+    a.tile_off = s_off;
+    cand_pass<true>(a, blockIdx.x, scatter_blocks);
     return;
   }
   const int nrb = (int)gridDim.x - scatter_blocks;
   for (int c = (blockIdx.x - scatter_blocks) * blockDim.x + threadIdx.x; c < ncells;
        c += nrb * blockDim.x)
-    range_cell(ca.local, ca.tile_off, ca.grid.cap, range, c);
+    range_cell(ca.local, s_off, ca.grid.cap, range, c);
 }
 
 __global__ void k_philox(uint32_t k0, uint32_t k1, uint32_t c1, uint32_t c2, uint32_t c3,
@@ -669,11 +699,12 @@ cudaError_t launch_grid_scan(int* count, int* fill, int* local, int* tile_sum, i
                   tile_sum, tile_off, ncells, ntiles, counter, ga, t);
 }
 
-cudaError_t launch_grid_scatter(const CandArgs& ca, int2* range, int ncells, cudaStream_t s) {
+cudaError_t launch_grid_scatter(const CandArgs& ca, int2* range, int ncells, const int* tile_sum,
+                                int* tile_off, int ntiles, cudaStream_t s) {
   const int scatter_blocks = ca.n_items > 0 ? blocks_for(ca.n_items * 32, 256, 152 * 4) : 0;
   const int range_blocks = blocks_for(ncells, 256, 152 * 2);
   return launch_k(k_grid_scatter, dim3(scatter_blocks + range_blocks), dim3(256), s, true, ca,
-                  scatter_blocks, range, ncells);
+                  scatter_blocks, range, ncells, tile_sum, tile_off, ntiles);
 }
 
 cudaError_t batch_grid_occupancy(int out[4]) {
