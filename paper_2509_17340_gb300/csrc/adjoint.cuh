@@ -183,12 +183,13 @@ __device__ __forceinline__ void dyn_vjp(const float* x, float4 u, const DynParam
   gx[6] += s * (2.0f * qx * V0 + 2.0f * qy * V1);
 }
 
-// Reverse of one RK4 step from x with control u: lam holds dS/dx_{j+1} on
-// entry and dS/dx_j on return; gu gets dS/du_j from the dynamics.
-__device__ __forceinline__ void rk4_vjp(const float* x, float4 u, const DynParams& dp, float* lam,
-                                        float* gu) {
+// The stage states of one RK4 step from x with control u (Eq. dynamics):
+// t2 = x + h/2 k1, t3 = x + h/2 k2, t4 = x + h k3, and the quaternion before
+// renormalisation y = q + h/6 (k1 + 2 k2 + 2 k3 + k4) (quaternion part).
+__device__ __forceinline__ void rk4_stages(const float* x, float4 u, const DynParams& dp, float* t2,
+                                           float* t3, float* t4, float* y) {
   const float h = dp.dt;
-  float k1[10], k2[10], k3[10], k4[10], t2[10], t3[10], t4[10];
+  float k1[10], k2[10], k3[10], k4[10];
   dyn_f(x, u, dp, k1);
 #pragma unroll
   for (int i = 0; i < 10; ++i) t2[i] = x[i] + 0.5f * h * k1[i];
@@ -199,11 +200,19 @@ __device__ __forceinline__ void rk4_vjp(const float* x, float4 u, const DynParam
 #pragma unroll
   for (int i = 0; i < 10; ++i) t4[i] = x[i] + h * k3[i];
   dyn_f(t4, u, dp, k4);
-  // the quaternion before renormalisation, and the projection (I - q q^T)/|y|
-  float y[4];
 #pragma unroll
   for (int i = 0; i < 4; ++i)
     y[i] = x[3 + i] + h * (1.0f / 6.0f) * (k1[3 + i] + 2.0f * k2[3 + i] + 2.0f * k3[3 + i] + k4[3 + i]);
+}
+
+// Reverse of one RK4 step given its stage states: lam holds dS/dx_{j+1} on
+// entry and dS/dx_j on return; gu gets dS/du_j from the dynamics.  Through the
+// renormalisation q+ = y/|y| (projection (I - q+ q+^T)/|y|), then the four
+// stages in reverse.
+__device__ __forceinline__ void rk4_vjp_stages(const float* x, const float* t2, const float* t3,
+                                               const float* t4, const float* y, float4 u,
+                                               const DynParams& dp, float* lam, float* gu) {
+  const float h = dp.dt;
   const float inv = rsqrtf(y[0] * y[0] + y[1] * y[1] + y[2] * y[2] + y[3] * y[3]);
   const float dot = (y[0] * lam[3] + y[1] * lam[4] + y[2] * lam[5] + y[3] * lam[6]) * inv;
   float ly[10];
@@ -232,6 +241,14 @@ __device__ __forceinline__ void rk4_vjp(const float* x, float4 u, const DynParam
 #pragma unroll
   for (int i = 0; i < 10; ++i) { lam[i] += lt[i]; l1[i] += 0.5f * h * lt[i]; }
   dyn_vjp(x, u, dp, l1, lam, gu);
+}
+
+// Reverse of one RK4 step from x with control u (stage states recomputed).
+__device__ __forceinline__ void rk4_vjp(const float* x, float4 u, const DynParams& dp, float* lam,
+                                        float* gu) {
+  float t2[10], t3[10], t4[10], y[4];
+  rk4_stages(x, u, dp, t2, t3, t4, y);
+  rk4_vjp_stages(x, t2, t3, t4, y, u, dp, lam, gu);
 }
 
 // S(1) of the noise-free rollout of u (shared, T entries) from x0 and, with
@@ -344,24 +361,203 @@ __device__ float warp_cost_grad(const float4* u, float4* g, const float* guide, 
   return S;
 }
 
-// refine_steps clamped gradient steps u <- clamp(u - refine_step dS/du) on
-// the shared nominal u, by one warp (g: shared scratch of T entries).
-__device__ __forceinline__ void warp_refine(float4* u, float4* g, const float* guide, int T,
-                                            const float* x0, const DynParams& dp,
-                                            const CostParams& cp, const GridView& grid,
-                                            const float* umin, const float* umax, int steps,
-                                            float alpha, AdjScratch& sc, int lane) {
-  for (int r = 0; r < steps; ++r) {
-    warp_cost_grad<true>(u, g, guide, T, x0, dp, cp, grid, sc, lane);
-    for (int t = lane; t < T; t += 32) {
-      const float4 a = u[t], d = g[t];
-      u[t] = make_float4(fminf(fmaxf(a.x - alpha * d.x, umin[0]), umax[0]),
-                         fminf(fmaxf(a.y - alpha * d.y, umin[1]), umax[1]),
-                         fminf(fmaxf(a.z - alpha * d.z, umin[2]), umax[2]),
-                         fminf(fmaxf(a.w - alpha * d.w, umin[3]), umax[3]));
+// ---------------------------------------------------------------------------
+// Gradient refinement by a whole CTA (the update kernels): the two serial
+// chains run on thread 0 (the forward RK4 steps; the backward vector-Jacobian
+// products, from stage states stored by the forward pass), everything else
+// over the CTA: the stage states of every step, the nearest point of every
+// state (candidate lists cut into items of kRefItem entries; a 64-bit atomic
+// minimum of (squared distance bits, entry) keeps the lowest entry among
+// ties), the state terms and their gradients, the control terms and the
+// clamped step.  The same arithmetic as warp_cost_grad<true> followed by the
+// clamped step.
+// ---------------------------------------------------------------------------
+constexpr int kRefItem = 8;
+
+struct RefineScratch {
+  float4* g;                 // T: dS/du
+  unsigned long long* key;   // T: (bits(d2) << 32) | entry of the nearest point of x_{j+1}
+  int2* qrange;              // T: candidate range of each listed query
+  int2* scan;                // warps: block-scan totals
+  float* xs;                 // (T + 1) x 10: states x_0 .. x_T
+  float* st;                 // T x 34: stage states t2, t3, t4 and y of step j
+  float* gs;                 // T x 10: state-term gradients at x_{j+1}
+  int* qitem;                // T + 1: first item of each listed query
+  int* qslot;                // T: step of each listed query
+};
+
+__host__ __device__ constexpr size_t refine_smem_bytes(int T, int warps) {
+  return 16 * (size_t)T + 8 * (size_t)T + 8 * (size_t)T + 8 * (size_t)warps +
+         4 * (size_t)(T + 1) * 10 + 4 * (size_t)T * 34 + 4 * (size_t)T * 10 + 4 * (size_t)(T + 1) +
+         4 * (size_t)T;
+}
+
+__device__ __forceinline__ RefineScratch refine_layout(unsigned char* base, int T, int warps) {
+  RefineScratch r;
+  r.g = reinterpret_cast<float4*>(base);
+  r.key = reinterpret_cast<unsigned long long*>(r.g + T);
+  r.qrange = reinterpret_cast<int2*>(r.key + T);
+  r.scan = r.qrange + T;
+  r.xs = reinterpret_cast<float*>(r.scan + warps);
+  r.st = r.xs + (size_t)(T + 1) * 10;
+  r.gs = r.st + (size_t)T * 34;
+  r.qitem = reinterpret_cast<int*>(r.gs + (size_t)T * 10);
+  r.qslot = r.qitem + T + 1;
+  return r;
+}
+
+// Exclusive prefix sums of (x, y) over a CTA of kWarps warps (totals in `total`).
+template <int kWarps>
+__device__ __forceinline__ int2 refine_scan2(int2 v, int2* warp_tot, int2& total) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  int2 inc = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int x = __shfl_up_sync(0xffffffffu, inc.x, o), y = __shfl_up_sync(0xffffffffu, inc.y, o);
+    if (lane >= o) {
+      inc.x += x;
+      inc.y += y;
     }
-    __syncwarp();
+  }
+  if (lane == 31) warp_tot[wid] = inc;
+  __syncthreads();
+  int2 before = make_int2(0, 0);
+  total = make_int2(0, 0);
+#pragma unroll
+  for (int w = 0; w < kWarps; ++w) {
+    const int2 t = warp_tot[w];
+    if (w < wid) {
+      before.x += t.x;
+      before.y += t.y;
+    }
+    total.x += t.x;
+    total.y += t.y;
+  }
+  return make_int2(before.x + inc.x - v.x, before.y + inc.y - v.y);
+}
+
+// `steps` clamped gradient steps u <- clamp(u - alpha dS/du) on the nominal u
+// (shared, T <= kThreads entries), by all kThreads threads of the CTA.
+template <int kThreads>
+__device__ void block_refine(float4* u, const float* guide, int T, const float* x0,
+                             const DynParams& dp, const CostParams& cp, const GridView& grid,
+                             const float* umin, const float* umax, int steps, float alpha,
+                             const RefineScratch& rs) {
+  const int tid = threadIdx.x;
+  const float dmax2 = cp.d_max * cp.d_max;
+  const unsigned long long none =
+      ((unsigned long long)__float_as_uint(dmax2) << 32) | 0xffffffffull;
+  for (int r = 0; r < steps; ++r) {
+    // forward: the states x_0 .. x_T
+    if (tid == 0) {
+      State x = state_load(x0);
+      state_store(rs.xs, x);
+      for (int j = 0; j < T; ++j) {
+        rk4_step(x, u[j], dp);
+        state_store(rs.xs + (j + 1) * 10, x);
+      }
+    }
+    __syncthreads();
+    // step tid: its stage states and the candidate range of x_{tid+1}
+    int2 rg = make_int2(0, 0);
+    if (tid < T) {
+      float* stj = rs.st + (size_t)tid * 34;
+      rk4_stages(rs.xs + tid * 10, u[tid], dp, stj, stj + 10, stj + 20, stj + 30);
+      rs.key[tid] = none;
+      const float* x1 = rs.xs + (tid + 1) * 10;
+      rg = cell_range(x1[0], x1[1], x1[2], grid);
+    }
+    int2 total;
+    const int2 off = refine_scan2<kThreads / 32>(
+        rg.y > 0 ? make_int2(1, (rg.y + kRefItem - 1) / kRefItem) : make_int2(0, 0), rs.scan, total);
+    if (rg.y > 0) {
+      rs.qitem[off.x] = off.y;
+      rs.qrange[off.x] = rg;
+      rs.qslot[off.x] = tid;
+    }
+    __syncthreads();
+    for (int it = tid; it < total.y; it += kThreads) {
+      int lo = 0, hi = total.x - 1;
+      while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (rs.qitem[mid] <= it) lo = mid; else hi = mid - 1;
+      }
+      const int2 q = rs.qrange[lo];
+      const int j = rs.qslot[lo];
+      const int first = (it - rs.qitem[lo]) * kRefItem;
+      const int n = q.y - first < kRefItem ? q.y - first : kRefItem;
+      if (!AERO_CHECK(j < T && first >= 0 && n > 0 && q.x >= 0, kChkQuery)) continue;
+      const float* x1 = rs.xs + (j + 1) * 10;
+      float best = dmax2;
+      int bi = -1;
+      for (int c = 0; c < n; ++c) {  // in entry order: the first of equal distances stays
+        const float d2 = dist2_to(__ldg(grid.pts + q.x + first + c), x1[0], x1[1], x1[2]);
+        if (d2 < best) {
+          best = d2;
+          bi = q.x + first + c;
+        }
+      }
+      if (bi >= 0)
+        atomicMin(rs.key + j, ((unsigned long long)__float_as_uint(best) << 32) | (unsigned)bi);
+    }
+    __syncthreads();
+    // state-term gradients at x_{tid+1}
+    if (tid < T) {
+      const unsigned long long kk = rs.key[tid];
+      const float d2 = __uint_as_float((unsigned)(kk >> 32));
+      const unsigned bi = (unsigned)kk;
+      const float4 nearest = bi != 0xffffffffu ? __ldg(grid.pts + bi) : make_float4(0.f, 0.f, 0.f, 0.f);
+      state_terms<true>(state_load(rs.xs + (tid + 1) * 10), guide[3 * tid], guide[3 * tid + 1],
+                        guide[3 * tid + 2], d2, nearest, cp, dmax2, rs.gs + tid * 10);
+    }
+    __syncthreads();
+    // backward: the serial vector-Jacobian products
+    if (tid == 0) {
+      float lam[10];
+#pragma unroll
+      for (int i = 0; i < 10; ++i) lam[i] = 0.0f;
+      for (int k = T - 1; k >= 0; --k) {
+#pragma unroll
+        for (int i = 0; i < 10; ++i) lam[i] += rs.gs[k * 10 + i];
+        float gu[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+        const float* stk = rs.st + (size_t)k * 34;
+        rk4_vjp_stages(rs.xs + k * 10, stk, stk + 10, stk + 20, stk + 30, u[k], dp, lam, gu);
+        rs.g[k] = make_float4(gu[0], gu[1], gu[2], gu[3]);
+      }
+    }
+    __syncthreads();
+    // control terms, then the clamped step
+    if (tid < T) {
+      const int t = tid;
+      float4 a = rs.g[t];
+      const float4 ut = u[t];
+      if (t <= T - 2) {
+        a.x += 2.0f * cp.Q_c * ut.x; a.y += 2.0f * cp.Q_c * ut.y;
+        a.z += 2.0f * cp.Q_c * ut.z; a.w += 2.0f * cp.Q_c * ut.w;
+      }
+      if (t >= 1 && t <= T - 2) {
+        const float4 b = u[t - 1];
+        a.x += 2.0f * cp.Q_cd * (ut.x - b.x); a.y += 2.0f * cp.Q_cd * (ut.y - b.y);
+        a.z += 2.0f * cp.Q_cd * (ut.z - b.z); a.w += 2.0f * cp.Q_cd * (ut.w - b.w);
+      }
+      if (t + 1 >= 1 && t + 1 <= T - 2) {
+        const float4 c = u[t + 1];
+        a.x -= 2.0f * cp.Q_cd * (c.x - ut.x); a.y -= 2.0f * cp.Q_cd * (c.y - ut.y);
+        a.z -= 2.0f * cp.Q_cd * (c.z - ut.z); a.w -= 2.0f * cp.Q_cd * (c.w - ut.w);
+      }
+      rs.g[t] = a;
+    }
+    __syncthreads();
+    if (tid < T) {
+      const float4 a = u[tid], d = rs.g[tid];
+      u[tid] = make_float4(fminf(fmaxf(a.x - alpha * d.x, umin[0]), umax[0]),
+                           fminf(fmaxf(a.y - alpha * d.y, umin[1]), umax[1]),
+                           fminf(fmaxf(a.z - alpha * d.z, umin[2]), umax[2]),
+                           fminf(fmaxf(a.w - alpha * d.w, umin[3]), umax[3]));
+    }
+    __syncthreads();
   }
 }
 
 }  // namespace aero
+

@@ -490,11 +490,12 @@ constexpr int UT = 128;  // threads of the update kernels
 // Stage I pass).  The partials are read through L2 (ld.cg): in the split pass
 // other CTAs of the same launch wrote them.
 template <int kThreads>
-__device__ __forceinline__ void update_unit(const UpdateArgs& a, int e, bool final_stage) {
+__device__ __forceinline__ void update_unit(const UpdateArgs& a, int e, bool final_stage,
+                                            unsigned char* rscratch) {
   constexpr int UT = kThreads;
   __shared__ float s_scale[1024];
   __shared__ float s_red[UT / 32];
-  __shared__ __align__(16) float s_x[(kMaxT + 1) * 10];  // also the refinement's AdjScratch
+  __shared__ __align__(16) float s_x[(kMaxT + 1) * 10];  // Stage II states
   __shared__ float4 s_u4[kMaxT];
   float* s_u = reinterpret_cast<float*>(s_u4);
   __shared__ float s_c[kMaxT];
@@ -578,16 +579,13 @@ __device__ __forceinline__ void update_unit(const UpdateArgs& a, int e, bool fin
   if (!final_stage) return;
   __syncthreads();
 
-  // gradient refinement of the updated nominal (warp 0; s_x and s_acc serve
-  // as its scratch before Stage II fills s_x)
+  // gradient refinement of the updated nominal by the whole CTA (rscratch:
+  // refine_smem_bytes(T, warps) of shared memory)
   if (a.refine_steps > 0) {
     if (a.dbg_pre)
       for (int i = tid; i < 4 * T; i += UT) a.dbg_pre[(size_t)e * T * 4 + i] = s_u[i];
-    if (wid == 0)
-      warp_refine(s_u4, s_acc[0], a.guides + (size_t)e * T * 3, T, a.x0, a.dyn, a.cost, a.grid,
-                  a.umin, a.umax, a.refine_steps, a.refine_step,
-                  *reinterpret_cast<AdjScratch*>(s_x), lane);
-    __syncthreads();
+    block_refine<UT>(s_u4, a.guides + (size_t)e * T * 3, T, a.x0, a.dyn, a.cost, a.grid, a.umin,
+                     a.umax, a.refine_steps, a.refine_step, refine_layout(rscratch, T, UT / 32));
     for (int i = tid; i < 4 * T; i += UT) un[i] = s_u[i];
     __syncthreads();
   }
@@ -715,7 +713,8 @@ __global__ void __launch_bounds__(ST) k_rollout_split(RolloutArgs a, UpdateArgs 
   if (threadIdx.x == 0) ua.inst_counter[e] = 0u;
   block_copy_param(&s_ua, &ua);
   __syncthreads();
-  update_unit<ST>(s_ua, e, s_ua.final_stage != 0);
+  extern __shared__ __align__(16) unsigned char fused_smem[];  // the split pass's, free again
+  update_unit<ST>(s_ua, e, s_ua.final_stage != 0, fused_smem);
 }
 
 // The single-planner update reads its arguments from shared memory, as the
@@ -727,7 +726,8 @@ __global__ void __launch_bounds__(UT) k_update(UpdateArgs a) {
   __shared__ UpdateArgs s_a;
   block_copy_param(&s_a, &a);
   __syncthreads();
-  update_unit<UT>(s_a, blockIdx.x, s_a.final_stage != 0);
+  extern __shared__ __align__(16) unsigned char upd_smem[];  // the refinement's scratch
+  update_unit<UT>(s_a, blockIdx.x, s_a.final_stage != 0, upd_smem);
 }
 
 // ---------------------------------------------------------------------------
@@ -794,6 +794,7 @@ __global__ void __launch_bounds__(kLanes == 4 ? ST : NT, kMinCtas)
 // planner runs its Stage II and selection.
 __global__ void __launch_bounds__(UT) k_b_update(BatchView v, int it) {
   pdl_start();
+  extern __shared__ __align__(16) unsigned char upd_smem[];  // the refinement's scratch
   __shared__ long long s_pre[kBatchMax + 1];
   __shared__ UpdateArgs s_a;
   __shared__ int s_iters;
@@ -810,13 +811,14 @@ __global__ void __launch_bounds__(UT) k_b_update(BatchView v, int it) {
       __syncthreads();
       cur = item;
     }
-    if (it < s_iters) update_unit<UT>(s_a, (int)(u - s_pre[item]), it == s_iters - 1);
+    if (it < s_iters) update_unit<UT>(s_a, (int)(u - s_pre[item]), it == s_iters - 1, upd_smem);
     __syncthreads();
   }
 }
 
-static_assert(sizeof(AdjScratch) <= sizeof(float) * (kMaxT + 1) * 10,
-              "the update kernel's Stage II state array holds the refinement scratch");
+static_assert(refine_smem_bytes(kMaxT, ST / 32) <= split_smem_bytes(kMaxT) &&
+                  refine_smem_bytes(1, ST / 32) <= split_smem_bytes(1),
+              "the split pass's shared memory holds the fused update's refinement scratch");
 
 // One warp per control sequence: S(1) of its noise-free rollout and dS/dU.
 constexpr int kCgWarps = 4;
@@ -860,6 +862,11 @@ cudaError_t split_attributes() {
     cudaError_t r = cudaFuncSetAttribute(k_rollout_split, cudaFuncAttributeMaxDynamicSharedMemorySize, most);
     if (r == cudaSuccess)
       r = cudaFuncSetAttribute(k_b_rollout<4, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, most);
+    const int refine = (int)refine_smem_bytes(kMaxT, UT / 32);
+    if (r == cudaSuccess)
+      r = cudaFuncSetAttribute(k_update, cudaFuncAttributeMaxDynamicSharedMemorySize, refine);
+    if (r == cudaSuccess)
+      r = cudaFuncSetAttribute(k_b_update, cudaFuncAttributeMaxDynamicSharedMemorySize, refine);
     return r;
   }();
   return e;
@@ -890,7 +897,9 @@ cudaError_t batch_rollout_occupancy(int out[4], int T_max) {
   if (e == cudaSuccess)
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(out + 1, k_b_rollout<4, 2>, ST,
                                                       split_smem_bytes(T_max));
-  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(out + 2, k_b_update, UT, 0);
+  if (e == cudaSuccess)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(out + 2, k_b_update, UT,
+                                                      refine_smem_bytes(T_max, UT / 32));
   if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(out + 3, k_b_rollout<1, 6>, NT, 0);
   for (int i = 0; i < 4; ++i)
     if (out[i] < 1) out[i] = 1;
@@ -907,7 +916,8 @@ cudaError_t launch_batch_rollout(const BatchView& v, int lanes, int it, int bloc
 }
 
 cudaError_t launch_batch_update(const BatchView& v, int it, int blocks, cudaStream_t s) {
-  return launch_k(k_b_update, dim3(blocks), dim3(UT), s, true, v, it);
+  return launch_ks(k_b_update, dim3(blocks), dim3(UT), refine_smem_bytes(v.T_max, UT / 32), s, true,
+                   v, it);
 }
 
 bool rollout_runs_update(const RolloutArgs& a) { return a.lanes_per_sample == 4; }
@@ -924,7 +934,10 @@ cudaError_t launch_rollout(const RolloutArgs& a, const UpdateArgs& ua, cudaStrea
 }
 
 cudaError_t launch_update(const UpdateArgs& a, cudaStream_t s) {
-  return launch_k(k_update, dim3(a.E), dim3(UT), s, true, a);
+  const cudaError_t e = split_attributes();  // also the update kernels' scratch limit
+  if (e != cudaSuccess) return e;
+  const size_t smem = a.refine_steps > 0 ? refine_smem_bytes(a.T, UT / 32) : 0;
+  return launch_ks(k_update, dim3(a.E), dim3(UT), smem, s, true, a);
 }
 
 cudaError_t check_word_rollout(int* out, bool clear) {
