@@ -666,6 +666,33 @@ def main():
     breakdown = pl.profile_read()
     total_ms = max_over_ranks(sum(step_ms), dist, dev)
 
+    # diagnostic: the same step captured once in a CUDA graph and replayed (no
+    # host launch cost, no events between the kernels; L2 flushed before each)
+    graph_ms = []
+    with torch.cuda.stream(stream):
+        P["step_id"] = 30_000
+        ps = aero.params_struct(P)
+        u_nom.copy_(u0)
+        pl.plan_step(state, cloud, w.goal, ps, u_nom, u_best, cand, best, stream)
+        graph = torch.cuda.CUDAGraph()
+        stream.synchronize()
+        graph.capture_begin()
+        pl.plan_step(state, cloud, w.goal, ps, u_nom, u_best, cand, best, stream)
+        graph.capture_end()
+        gev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(min(args.steps, 200))]
+        for i in range(args.warmup + len(gev)):
+            flush.fill_(float(i))
+            u_nom.copy_(u0)
+            if i >= args.warmup:
+                gev[i - args.warmup][0].record(stream)
+            graph.replay()
+            if i >= args.warmup:
+                gev[i - args.warmup][1].record(stream)
+        torch.cuda.synchronize()
+        graph_ms = [a.elapsed_time(b) for a, b in gev]
+        del graph
+
     # end-to-end through the host-memory entry point (pinned buffers)
     e2e = None
     if True:
@@ -714,6 +741,10 @@ def main():
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": config_of(P, w),
         "stage_ms_per_step": {k: v[0] / n_diag for k, v in breakdown.items()},
+        "graph_replay": {"ms_per_step_median": statistics.median(graph_ms) if graph_ms else None,
+                         "steps": len(graph_ms),
+                         "note": "diagnostic: one step captured in a CUDA graph and replayed, "
+                                 "L2 flushed before each replay; not the headline value"},
         "roofline": {"kernel": rollout_kernel_name(P),
                      "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak, "traffic": rollout_traffic(WORKLOAD),

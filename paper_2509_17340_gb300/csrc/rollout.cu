@@ -511,9 +511,11 @@ __device__ __forceinline__ void update_unit(const UpdateArgs& a, int e, bool fin
   const int T = a.T, stride = 4 + 4 * T;
   const float* P = a.partials + (size_t)e * a.nb * stride;
 
-  // rho = min rho_b
+  // rho = min rho_b (a thread's first row keeps its rho_b and eta_b for the sum)
   float m = INFINITY;
-  for (int b = tid; b < a.nb; b += UT) m = fminf(m, __ldcg(P + (size_t)b * stride));
+  const float2 first_row = tid < a.nb ? __ldcg(reinterpret_cast<const float2*>(P + (size_t)tid * stride))
+                                      : make_float2(INFINITY, 0.0f);
+  for (int b = tid; b < a.nb; b += UT) m = fminf(m, b == tid ? first_row.x : __ldcg(P + (size_t)b * stride));
   m = warp_min(m);
   if (lane == 0) s_red[wid] = m;
   __syncthreads();
@@ -523,9 +525,9 @@ __device__ __forceinline__ void update_unit(const UpdateArgs& a, int e, bool fin
   // eta = sum eta_b exp(-(rho_b - rho)/lambda)
   float eta = 0.0f;
   for (int b = tid; b < a.nb; b += UT) {
-    const float sc = expf((rho - __ldcg(P + (size_t)b * stride)) * a.inv_lambda);
+    const float sc = expf((rho - (b == tid ? first_row.x : __ldcg(P + (size_t)b * stride))) * a.inv_lambda);
     if (b < 1024) s_scale[b] = sc;
-    eta += sc * __ldcg(P + (size_t)b * stride + 1);
+    eta += sc * (b == tid ? first_row.y : __ldcg(P + (size_t)b * stride + 1));
   }
   eta = warp_sum(eta);
   if (lane == 0) s_red[wid] = eta;
