@@ -183,10 +183,11 @@ int aero_plan_step(aero_planner_t* planner, const aero_state_t* x0, const float*
                    int32_t* best_idx_out, void* stream);
 
 /* The same step for callers whose data lives in host memory: every array
- * argument is a host pointer (pinned memory gives the fastest copies).  The
- * cloud and the warm start are copied into the planner's device buffers on
- * `stream`, the step runs, the outputs are copied back, and the call returns
- * after synchronising the stream. */
+ * argument is a host pointer (a pinned cloud and warm start give the fastest
+ * copies).  The cloud and the warm start are copied into the planner's device
+ * buffers on `stream`, the step runs, its outputs come back in one copy into
+ * the planner's pinned staging buffer, and the call returns after
+ * synchronising the stream and copying them into the caller's buffers. */
 int aero_plan_step_host(aero_planner_t* planner, const aero_state_t* x0, const float* cloud_xyz,
                         int64_t n_points, const float goal[3], const aero_params_t* params,
                         float* u_nom_inout, float* u_best_out, float* cand_costs_out,

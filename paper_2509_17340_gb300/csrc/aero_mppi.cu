@@ -129,10 +129,10 @@ struct aero_planner {
   int part_slots = 0;         // entries of part_counts
   // staging for aero_plan_step_host
   float* stage_cloud = nullptr;
-  float* stage_unom = nullptr;
-  float* stage_ubest = nullptr;
-  float* stage_cand = nullptr;
-  int* stage_best = nullptr;
+  // the step's outputs, contiguous (nominals, best sequence, candidate costs,
+  // best index) so that one copy brings them back; h_out is its pinned twin
+  float* stage_out = nullptr;
+  float* h_out = nullptr;
   // metadata of the last step (debug copies)
   bool have_step = false;
   aero_params_t last{};
@@ -141,6 +141,12 @@ struct aero_planner {
   int last_ntiles = 0;
   int last_nb = 0;
   int last_part_slots = 0;    // part_counts entries written by the last step
+  // the partition's edge tables of the last geometry (fine_az, fine_el, el_lo, el_hi)
+  bool tab_valid = false;
+  int tab_A = 0, tab_El = 0;
+  float tab_lo = 0.0f, tab_hi = 0.0f;
+  int tab_check_lo = 0, tab_check_hi = 0;
+  PartTables tab{};
   int64_t last_n_points = 0;
   // stage timing (aero_profile_enable / aero_profile_read)
   struct ProfSlot {
@@ -279,9 +285,10 @@ void free_all(aero_planner* pl) {
                   pl->tile_off,
                   pl->cand,     pl->grid_range, pl->partials,
                   pl->sample_costs, pl->dU,      pl->stage2_x, pl->counter,   pl->status,   pl->dbg_u,
-                  pl->dbg_x,    pl->dbg_d,      pl->stage_cloud,      pl->stage_unom,   pl->stage_ubest,
-                  pl->stage_cand,   pl->stage_best,   pl->dbg_pre,      pl->part_counts};
+                  pl->dbg_x,    pl->dbg_d,      pl->stage_cloud,      pl->stage_out,
+                  pl->dbg_pre,      pl->part_counts};
   for (void* q : ptrs) dev_free(q);
+  host_free(pl->h_out);
 }
 
 constexpr size_t kProfSlots = 512;
@@ -365,7 +372,19 @@ void make_step_args(aero_planner* pl, const aero_state_t* x0, const float* cloud
                     const float* goal, const aero_params_t& p, float* u_nom, float* u_best,
                     float* cand, int32_t* best_idx, int lanes, bool coarse, StepArgs& a) {
   a.ncell = p.fine_az * p.fine_el;
-  make_tables(p, a.tab, a.check_lo, a.check_hi);
+  // the edge tables depend only on the partition geometry: recomputed when it changes
+  if (!pl->tab_valid || pl->tab_A != p.fine_az || pl->tab_El != p.fine_el || pl->tab_lo != p.el_lo ||
+      pl->tab_hi != p.el_hi) {
+    make_tables(p, pl->tab, pl->tab_check_lo, pl->tab_check_hi);
+    pl->tab_valid = true;
+    pl->tab_A = p.fine_az;
+    pl->tab_El = p.fine_el;
+    pl->tab_lo = p.el_lo;
+    pl->tab_hi = p.el_hi;
+  }
+  a.tab = pl->tab;
+  a.check_lo = pl->tab_check_lo;
+  a.check_hi = pl->tab_check_hi;
   float R[9];
   rot_f32(x0->q, R);
   const float rm = p.r_max;
@@ -710,10 +729,9 @@ int aero_create(const aero_limits_t* limits, aero_planner_t** out) {
   pl->part_slots = (int)std::max<int64_t>(kPartBlocksMax, (L.n_points_max + kPartChunk - 1) / kPartChunk);
   chk(alloc(&pl->part_counts, pl->part_slots));
   chk(alloc(&pl->stage_cloud, (size_t)L.n_points_max * 3));
-  chk(alloc(&pl->stage_unom, (size_t)L.E_max * L.T_max * 4));
-  chk(alloc(&pl->stage_ubest, (size_t)L.T_max * 4));
-  chk(alloc(&pl->stage_cand, L.E_max));
-  chk(alloc(&pl->stage_best, 1));
+  const size_t out_words = (size_t)L.E_max * L.T_max * 4 + (size_t)L.T_max * 4 + L.E_max + 1;
+  chk(alloc(&pl->stage_out, out_words));
+  chk(host_malloc((void**)&pl->h_out, sizeof(float) * out_words));
   if (e == cudaSuccess) e = cudaMemset(pl->counter, 0, kCounterWords * sizeof(unsigned int));
   if (e == cudaSuccess) e = cudaMemset(pl->status, 0, sizeof(int));
   if (e == cudaSuccess) e = cudaDeviceSynchronize();
@@ -783,22 +801,26 @@ int aero_plan_step_host(aero_planner_t* pl, const aero_state_t* x0, const float*
   if (n > 0 && (e = cudaMemcpyAsync(pl->stage_cloud, cloud, sizeof(float) * 3 * n,
                                     cudaMemcpyHostToDevice, s)) != cudaSuccess)
     return cuda_fail(e);
-  if ((e = cudaMemcpyAsync(pl->stage_unom, u_nom, sizeof(float) * nu, cudaMemcpyHostToDevice, s)) !=
-      cudaSuccess)
+  // outputs laid out back to back (each part stays 16-byte aligned)
+  const size_t nb = (size_t)params->T * 4, ne = (size_t)params->E;
+  float* d_unom = pl->stage_out;
+  float* d_ubest = d_unom + nu;
+  float* d_cand = d_ubest + nb;
+  int32_t* d_best = reinterpret_cast<int32_t*>(d_cand + ne);
+  if ((e = cudaMemcpyAsync(d_unom, u_nom, sizeof(float) * nu, cudaMemcpyHostToDevice, s)) != cudaSuccess)
     return cuda_fail(e);
-  rc = enqueue_step(pl, x0, pl->stage_cloud, n, goal, *params, pl->stage_unom, pl->stage_ubest, pl->stage_cand,
-                    pl->stage_best, s);
+  rc = enqueue_step(pl, x0, pl->stage_cloud, n, goal, *params, d_unom, d_ubest, d_cand, d_best, s);
   if (rc != AERO_OK) return rc;
-  if ((e = cudaMemcpyAsync(u_nom, pl->stage_unom, sizeof(float) * nu, cudaMemcpyDeviceToHost, s)) !=
-          cudaSuccess ||
-      (e = cudaMemcpyAsync(u_best, pl->stage_ubest, sizeof(float) * params->T * 4,
-                           cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
-      (e = cudaMemcpyAsync(cand, pl->stage_cand, sizeof(float) * params->E, cudaMemcpyDeviceToHost,
+  const size_t words = nu + nb + ne + 1;
+  if ((e = cudaMemcpyAsync(pl->h_out, pl->stage_out, sizeof(float) * words, cudaMemcpyDeviceToHost,
                            s)) != cudaSuccess ||
-      (e = cudaMemcpyAsync(best_idx, pl->stage_best, sizeof(int32_t), cudaMemcpyDeviceToHost, s)) !=
-          cudaSuccess)
+      (e = cudaStreamSynchronize(s)) != cudaSuccess)
     return cuda_fail(e);
-  return cuda_fail(cudaStreamSynchronize(s));
+  std::memcpy(u_nom, pl->h_out, sizeof(float) * nu);
+  std::memcpy(u_best, pl->h_out + nu, sizeof(float) * nb);
+  std::memcpy(cand, pl->h_out + nu + nb, sizeof(float) * ne);
+  std::memcpy(best_idx, pl->h_out + nu + nb + ne, sizeof(int32_t));
+  return AERO_OK;
 }
 
 size_t aero_debug_size(aero_planner_t* pl, int32_t what) {
