@@ -147,6 +147,8 @@ struct aero_planner {
   float tab_lo = 0.0f, tab_hi = 0.0f;
   int tab_check_lo = 0, tab_check_hi = 0;
   PartTables tab{};
+  PartTables* d_tab = nullptr;  // device copy, read by the partition and the guides
+  bool tab_upload = true;       // d_tab behind tab
   int64_t last_n_points = 0;
   // stage timing (aero_profile_enable / aero_profile_read)
   struct ProfSlot {
@@ -286,7 +288,7 @@ void free_all(aero_planner* pl) {
                   pl->cand,     pl->grid_range, pl->partials,
                   pl->sample_costs, pl->dU,      pl->stage2_x, pl->counter,   pl->status,   pl->dbg_u,
                   pl->dbg_x,    pl->dbg_d,      pl->stage_cloud,      pl->stage_out,
-                  pl->dbg_pre,      pl->part_counts};
+                  pl->dbg_pre,      pl->part_counts,  pl->d_tab};
   for (void* q : ptrs) dev_free(q);
   host_free(pl->h_out);
 }
@@ -377,6 +379,7 @@ void make_step_args(aero_planner* pl, const aero_state_t* x0, const float* cloud
       pl->tab_hi != p.el_hi) {
     make_tables(p, pl->tab, pl->tab_check_lo, pl->tab_check_hi);
     pl->tab_valid = true;
+    pl->tab_upload = true;
     pl->tab_A = p.fine_az;
     pl->tab_El = p.fine_el;
     pl->tab_lo = p.el_lo;
@@ -584,7 +587,13 @@ int enqueue_step(aero_planner* pl, const aero_state_t* x0, const float* cloud, i
   }
   pl->grid_dirty = true;
 
-  if ((e = launch_partition(a.pa, a.tab, s)) != cudaSuccess) return cuda_fail(e);
+  if (pl->tab_upload) {
+    if ((e = cudaMemcpyAsync(pl->d_tab, &pl->tab, sizeof(PartTables), cudaMemcpyHostToDevice, s)) !=
+        cudaSuccess)
+      return cuda_fail(e);
+    pl->tab_upload = false;
+  }
+  if ((e = launch_partition(a.pa, pl->d_tab, s)) != cudaSuccess) return cuda_fail(e);
   mark(AERO_STAGE_PARTITION, 1);
   mark(AERO_STAGE_GRID, 2);
   if (prof) {
@@ -596,7 +605,7 @@ int enqueue_step(aero_planner* pl, const aero_state_t* x0, const float* cloud, i
   // count pass + coarse argmax, scan + goal cone/anchors/guides, scatter + cell ranges
   if ((e = launch_grid_count(a.ca, a.ga, s)) != cudaSuccess) return cuda_fail(e);
   if ((e = launch_grid_scan(pl->grid_count, pl->grid_fill, pl->grid_local, pl->tile_sum,
-                            pl->tile_off, a.gcells + 1, a.ntiles, nullptr, a.ga, a.tab, s)) !=
+                            pl->tile_off, a.gcells + 1, a.ntiles, nullptr, a.ga, pl->d_tab, s)) !=
       cudaSuccess)
     return cuda_fail(e);
   if ((e = launch_grid_scatter(a.ca, pl->grid_range, a.gcells, pl->tile_sum, pl->tile_off,
@@ -731,6 +740,7 @@ int aero_create(const aero_limits_t* limits, aero_planner_t** out) {
   chk(alloc(&pl->stage_cloud, (size_t)L.n_points_max * 3));
   const size_t out_words = (size_t)L.E_max * L.T_max * 4 + (size_t)L.T_max * 4 + L.E_max + 1;
   chk(alloc(&pl->stage_out, out_words));
+  chk(alloc(&pl->d_tab, 1));
   chk(host_malloc((void**)&pl->h_out, sizeof(float) * out_words));
   if (e == cudaSuccess) e = cudaMemset(pl->counter, 0, kCounterWords * sizeof(unsigned int));
   if (e == cudaSuccess) e = cudaMemset(pl->status, 0, sizeof(int));
@@ -1034,7 +1044,7 @@ constexpr size_t kNaBytes =
     align256(8 * (size_t)kNaGridCells) +
     align256(4 * (size_t)kNaE * kNaNb * (4 + 4 * kNaT)) + align256(4 * (size_t)kNaE * kNaK) +
     align256(4 * (size_t)kNaE * (kNaT + 1) * 10) + align256(4 * kCounterWords) +
-    align256(8 * (size_t)kPartBlocksMax) + align256(4);
+    align256(8 * (size_t)kPartBlocksMax) + align256(sizeof(PartTables)) + align256(4);
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNaBytes];
 
@@ -1094,6 +1104,7 @@ void noalloc_carve(unsigned char* base, aero_planner& pl) {
   pl.stage2_x = reinterpret_cast<float*>(take(4 * (size_t)kNaE * (kNaT + 1) * 10));
   pl.counter = reinterpret_cast<unsigned int*>(take(4 * kCounterWords));
   pl.part_counts = reinterpret_cast<int2*>(take(8 * (size_t)kPartBlocksMax));
+  pl.d_tab = reinterpret_cast<PartTables*>(take(sizeof(PartTables)));
   pl.part_slots = kPartBlocksMax;
   pl.status = reinterpret_cast<int*>(take(4));
 }

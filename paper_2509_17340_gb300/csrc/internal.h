@@ -230,14 +230,15 @@ cudaError_t launch_batch_update(const BatchView& v, int it, int blocks, cudaStre
 cudaError_t batch_grid_occupancy(int out[4]);
 cudaError_t batch_rollout_occupancy(int out[4], int T_max);
 
-cudaError_t launch_partition(const PartitionArgs& a, const PartTables& t, cudaStream_t s);
+// t: the edge tables in device memory
+cudaError_t launch_partition(const PartitionArgs& a, const PartTables* t, cudaStream_t s);
 int partition_blocks(int64_t n);  // CTAs of launch_partition for n points (0 when n == 0)
 constexpr int kPartBlocksMax = 152 * 16;
 // count pass + coarse argmax; then the tile scans + goal cone, anchors, guides
 cudaError_t launch_grid_count(const CandArgs& ca, const GuideArgs& ga, cudaStream_t s);
 cudaError_t launch_grid_scan(int* count, int* fill, int* local, int* tile_sum, int* tile_off,
                              int ncells, int ntiles, unsigned int* counter, const GuideArgs& ga,
-                             const PartTables& t, cudaStream_t s);
+                             const PartTables* t, cudaStream_t s);
 // scatter + cell ranges; the tile offsets are computed here from the tile
 // totals of the scan launch (and written to tile_off)
 cudaError_t launch_grid_scatter(const CandArgs& ca, int2* range, int ncells, const int* tile_sum,

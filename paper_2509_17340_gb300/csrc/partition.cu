@@ -124,10 +124,10 @@ __device__ __forceinline__ void block_count2(int nf, int kept, int2* out) {
   if (threadIdx.x == 0) *out = make_int2(s_nf, s_kept);
 }
 
-__global__ void __launch_bounds__(256) k_partition(PartitionArgs a, PartTables t) {
+__global__ void __launch_bounds__(256) k_partition(PartitionArgs a, const PartTables* __restrict__ t) {
   pdl_start();
   __shared__ SmemTables st;
-  load_tables(t, a.A, a.El, st);
+  load_tables(*t, a.A, a.El, st);
   __syncthreads();
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   int nf = 0, kept = 0;
@@ -457,14 +457,15 @@ __global__ void __launch_bounds__(256) k_grid_count(CandArgs ca, GuideArgs ga, i
 __global__ void __launch_bounds__(kScanThreads) k_grid_scan(int* count, int* fill, int* local,
                                                             int* tile_sum, int* tile_off, int ncells,
                                                             int ntiles, unsigned int* counter,
-                                                            GuideArgs ga, PartTables t) {
+                                                            GuideArgs ga,
+                                                            const PartTables* __restrict__ t) {
   pdl_start();
   if ((int)blockIdx.x < ntiles) {
     scan_tile(count, fill, local, tile_sum, tile_off, ncells, ntiles, blockIdx.x, counter);
     return;
   }
   __shared__ SmemTables st;
-  load_tables(t, ga.A, ga.El, st);
+  load_tables(*t, ga.A, ga.El, st);
   __syncthreads();
   guides_block(ga, st);
 }
@@ -679,7 +680,7 @@ int blocks_for(int64_t n, int threads, int cap) {
 
 int partition_blocks(int64_t n) { return n > 0 ? blocks_for(n, 256, kPartBlocksMax) : 0; }
 
-cudaError_t launch_partition(const PartitionArgs& a, const PartTables& t, cudaStream_t s) {
+cudaError_t launch_partition(const PartitionArgs& a, const PartTables* t, cudaStream_t s) {
   if (a.n == 0) return cudaSuccess;
   return launch_k(k_partition, dim3(partition_blocks(a.n)), dim3(256), s, true, a, t);
 }
@@ -694,7 +695,7 @@ cudaError_t launch_grid_count(const CandArgs& ca, const GuideArgs& ga, cudaStrea
 
 cudaError_t launch_grid_scan(int* count, int* fill, int* local, int* tile_sum, int* tile_off,
                              int ncells, int ntiles, unsigned int* counter, const GuideArgs& ga,
-                             const PartTables& t, cudaStream_t s) {
+                             const PartTables* t, cudaStream_t s) {
   return launch_k(k_grid_scan, dim3(ntiles + 1), dim3(kScanThreads), s, true, count, fill, local,
                   tile_sum, tile_off, ncells, ntiles, counter, ga, t);
 }
