@@ -315,15 +315,6 @@ __device__ __forceinline__ void rollout_split_unit(const RolloutArgs& a, int e, 
   const int nch = (T + kChunk - 1) / kChunk;
   const int tcb = (T + nch - 1) / nch;  // steps per chunk (the last may be shorter)
 
-  // u_j for the steps j = first (mod stride) of [j0, j0 + tc)
-  auto noise = [&](int j0, int tc, int first, int stride) {
-    for (int j = j0 + first; j < j0 + tc; j += stride) {
-      const float4 un = m.un[j];
-      const float4 d = noise_delta(k, j, e, ctr3, a.key0, a.key1, sigma);
-      m.u[j * QS + lane] =
-          clamp4(make_float4(un.x + d.x, un.y + d.y, un.z + d.z, un.w + d.w), umin, umax);
-    }
-  };
 
   State x;
 #pragma unroll
@@ -341,8 +332,15 @@ __device__ __forceinline__ void rollout_split_unit(const RolloutArgs& a, int e, 
   }
   float S = 0.0f;  // every thread: the cost terms of its (sample, step) pairs
 
+  // the perturbations (independent of the nominal) while the nominal loads,
+  // then the clamped controls: each thread rereads only what it wrote
+  for (int j = wid; j < T; j += SW)
+    m.u[j * QS + lane] = noise_delta(k, j, e, ctr3, a.key0, a.key1, sigma);
   __syncthreads();  // un, gd
-  noise(0, T, wid, SW);
+  for (int j = wid; j < T; j += SW) {
+    const float4 un = m.un[j], d = m.u[j * QS + lane];
+    m.u[j * QS + lane] = clamp4(make_float4(un.x + d.x, un.y + d.y, un.z + d.z, un.w + d.w), umin, umax);
+  }
   __syncthreads();
   for (int j0 = 0; j0 < T; j0 += tcb) {
     const int tc = tcb < T - j0 ? tcb : T - j0;
