@@ -175,6 +175,9 @@ int aero_destroy(aero_planner_t* planner);
  *   cand_costs_out device, E float: Stage II cost S(2) of each instance.
  *   best_idx_out device, 1 int32: index of the selected instance (lowest
  *               S(2), ties to the lower index).
+ * The call only enqueues work on `stream` (it neither allocates nor
+ * synchronises), so it can be captured into a CUDA graph and replayed; the
+ * graph replays the captured arguments (state, goal, step_id, buffers).
  * Errors (nothing is enqueued): INVALID_ARG, EXCEEDS_LIMITS, NOT_DEVICE_PTR;
  * CUDA if a launch fails. */
 int aero_plan_step(aero_planner_t* planner, const aero_state_t* x0, const float* cloud_xyz,

@@ -742,6 +742,7 @@ int aero_create(const aero_limits_t* limits, aero_planner_t** out) {
   chk(alloc(&pl->stage_out, out_words));
   chk(alloc(&pl->d_tab, 1));
   chk(host_malloc((void**)&pl->h_out, sizeof(float) * out_words));
+  if (e == cudaSuccess) e = split_attributes();
   if (e == cudaSuccess) e = cudaMemset(pl->counter, 0, kCounterWords * sizeof(unsigned int));
   if (e == cudaSuccess) e = cudaMemset(pl->status, 0, sizeof(int));
   if (e == cudaSuccess) e = cudaDeviceSynchronize();

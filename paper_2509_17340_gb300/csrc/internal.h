@@ -257,6 +257,8 @@ struct CostGradArgs {
 // the last CTA of every instance, the others leave it to launch_update.
 cudaError_t launch_rollout(const RolloutArgs& a, const UpdateArgs& ua, cudaStream_t s);
 bool rollout_runs_update(const RolloutArgs& a);
+// Sets the kernels' shared-memory limits (once per process).
+cudaError_t split_attributes();
 cudaError_t launch_cost_grad(const CostGradArgs& a, cudaStream_t s);
 cudaError_t launch_update(const UpdateArgs& a, cudaStream_t s);
 cudaError_t launch_philox(uint32_t k0, uint32_t k1, uint32_t c1, uint32_t c2, uint32_t c3,

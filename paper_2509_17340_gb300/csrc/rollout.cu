@@ -855,7 +855,8 @@ cudaError_t launch_cost_grad(const CostGradArgs& a, cudaStream_t s) {
 }
 
 // The split pass reads its shared memory as one dynamic block sized for the
-// horizon; allow the largest (once per process).
+// horizon; allow the largest (once per process; the create functions call it
+// first, so that no launch captured into a graph is the first).
 cudaError_t split_attributes() {
   static const cudaError_t e = [] {
     const int most = (int)split_smem_bytes(kMaxT);
@@ -926,7 +927,11 @@ cudaError_t launch_rollout(const RolloutArgs& a, const UpdateArgs& ua, cudaStrea
   dim3 grid(a.nb, a.E);
   if (a.lanes_per_sample == 4) {
     cudaError_t e = split_attributes();
-    if (e == cudaSuccess) e = split_carveout(a.T);
+    // the carveout is a hint: a launch being captured into a graph keeps the
+    // one set by earlier launches
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (e == cudaSuccess) e = cudaStreamIsCapturing(s, &cs);
+    if (e == cudaSuccess && cs == cudaStreamCaptureStatusNone) e = split_carveout(a.T);
     if (e != cudaSuccess) return e;
     return launch_ks(k_rollout_split, grid, dim3(ST), split_smem_bytes(a.T), s, true, a, ua);
   }
