@@ -65,4 +65,22 @@ def test_graph_replay_equals_direct_steps(aero, variant):
         for a, b in zip((g_un, g_ub, g_cand, g_best), r):
             assert torch.equal(a, b), variant
     assert pl.sync_status() == 0
+    # a fresh planner's very first call captured (its workspace clears included)
+    pl2 = aero.Planner(E_max=P["E"], K_max=P["K"], T_max=P["T"],
+                       fine_cells_max=P["fine_az"] * P["fine_el"], n_points_max=len(w.cloud))
+    f_un, f_ub, f_cand, f_best = buffers()
+    graph2 = torch.cuda.CUDAGraph()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        graph2.capture_begin()
+        pl2.plan_step(state, cloud, w.goal, ps, f_un, f_ub, f_cand, f_best, stream=side)
+        graph2.capture_end()
+    torch.cuda.current_stream().wait_stream(side)
+    for r in ref:
+        graph2.replay()
+        torch.cuda.synchronize()
+        for a, b in zip((f_un, f_ub, f_cand, f_best), r):
+            assert torch.equal(a, b), variant
+    assert pl2.sync_status() == 0
+    pl2.close()
     pl.close()
