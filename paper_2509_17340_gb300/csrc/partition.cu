@@ -70,12 +70,15 @@ __device__ __forceinline__ void load_tables(const PartTables& t, int A, int El, 
   }
 }
 
-// Returns 0 for a non-finite point, 1 for a point outside the partition's
-// range or elevation span, 2 for a kept point.
+__device__ __forceinline__ float3 cloud_point(const PartitionArgs& a, int64_t i) {
+  return make_float3(__ldg(a.cloud + 3 * i), __ldg(a.cloud + 3 * i + 1), __ldg(a.cloud + 3 * i + 2));
+}
+
+// Point i at (px, py, pz).  Returns 0 for a non-finite point, 1 for a point
+// outside the partition's range or elevation span, 2 for a kept point.
 __device__ __forceinline__ int partition_point(const PartitionArgs& a, const SmemTables& st,
-                                               int64_t i) {
-  const float px = __ldg(a.cloud + 3 * i), py = __ldg(a.cloud + 3 * i + 1),
-              pz = __ldg(a.cloud + 3 * i + 2);
+                                               int64_t i, float3 pt) {
+  const float px = pt.x, py = pt.y, pz = pt.z;
   int cell = -1;
   const bool finite = isfinite(px) && isfinite(py) && isfinite(pz);
   if (finite) {
@@ -127,14 +130,18 @@ __device__ __forceinline__ void block_count2(int nf, int kept, int2* out) {
 __global__ void __launch_bounds__(256) k_partition(PartitionArgs a, const PartTables* __restrict__ t) {
   pdl_start();
   __shared__ SmemTables st;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  // the first point is fetched while the edge tables load
+  float3 pt = i < a.n ? cloud_point(a, i) : make_float3(0.f, 0.f, 0.f);
   load_tables(*t, a.A, a.El, st);
   __syncthreads();
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   int nf = 0, kept = 0;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += stride) {
-    const int r = partition_point(a, st, i);
+  for (; i < a.n; i += stride) {
+    const int r = partition_point(a, st, i, pt);
     nf += r == 0;
     kept += r == 2;
+    if (i + stride < a.n) pt = cloud_point(a, i + stride);
   }
   if (a.counts) block_count2(nf, kept, a.counts + blockIdx.x);
 }
@@ -563,7 +570,7 @@ __global__ void __launch_bounds__(256) k_b_partition(BatchView v) {
     int nf = 0, kept = 0;
     for (int r = threadIdx.x; r < kPartChunk; r += blockDim.x)
       if (base + r < s_pa.n) {
-        const int c = partition_point(s_pa, st, base + r);
+        const int c = partition_point(s_pa, st, base + r, cloud_point(s_pa, base + r));
         nf += c == 0;
         kept += c == 2;
       }
