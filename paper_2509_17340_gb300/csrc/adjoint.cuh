@@ -406,35 +406,6 @@ __device__ __forceinline__ RefineScratch refine_layout(unsigned char* base, int 
   return r;
 }
 
-// Exclusive prefix sums of (x, y) over a CTA of kWarps warps (totals in `total`).
-template <int kWarps>
-__device__ __forceinline__ int2 refine_scan2(int2 v, int2* warp_tot, int2& total) {
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  int2 inc = v;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const int x = __shfl_up_sync(0xffffffffu, inc.x, o), y = __shfl_up_sync(0xffffffffu, inc.y, o);
-    if (lane >= o) {
-      inc.x += x;
-      inc.y += y;
-    }
-  }
-  if (lane == 31) warp_tot[wid] = inc;
-  __syncthreads();
-  int2 before = make_int2(0, 0);
-  total = make_int2(0, 0);
-#pragma unroll
-  for (int w = 0; w < kWarps; ++w) {
-    const int2 t = warp_tot[w];
-    if (w < wid) {
-      before.x += t.x;
-      before.y += t.y;
-    }
-    total.x += t.x;
-    total.y += t.y;
-  }
-  return make_int2(before.x + inc.x - v.x, before.y + inc.y - v.y);
-}
 
 // `steps` clamped gradient steps u <- clamp(u - alpha dS/du) on the nominal u
 // (shared, T <= kThreads entries), by all kThreads threads of the CTA.
@@ -468,7 +439,7 @@ __device__ void block_refine(float4* u, const float* guide, int T, const float* 
       rg = cell_range(x1[0], x1[1], x1[2], grid);
     }
     int2 total;
-    const int2 off = refine_scan2<kThreads / 32>(
+    const int2 off = block_scan2<kThreads / 32>(
         rg.y > 0 ? make_int2(1, (rg.y + kRefItem - 1) / kRefItem) : make_int2(0, 0), rs.scan, total);
     if (rg.y > 0) {
       rs.qitem[off.x] = off.y;
@@ -477,11 +448,7 @@ __device__ void block_refine(float4* u, const float* guide, int T, const float* 
     }
     __syncthreads();
     for (int it = tid; it < total.y; it += kThreads) {
-      int lo = 0, hi = total.x - 1;
-      while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (rs.qitem[mid] <= it) lo = mid; else hi = mid - 1;
-      }
+      const int lo = item_owner(rs.qitem, total.x, it);
       const int2 q = rs.qrange[lo];
       const int j = rs.qslot[lo];
       const int first = (it - rs.qitem[lo]) * kRefItem;

@@ -261,6 +261,48 @@ __device__ __forceinline__ float warp_sum4(float a0, float a1, float a2, float a
   return c;
 }
 
+// Exclusive prefix sums of (x, y) over a CTA of kWarps warps; `total`
+// receives the sums.  warp_tot: kWarps entries of shared memory.
+template <int kWarps>
+__device__ __forceinline__ int2 block_scan2(int2 v, int2* warp_tot, int2& total) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  int2 inc = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int x = __shfl_up_sync(0xffffffffu, inc.x, o), y = __shfl_up_sync(0xffffffffu, inc.y, o);
+    if (lane >= o) {
+      inc.x += x;
+      inc.y += y;
+    }
+  }
+  if (lane == 31) warp_tot[wid] = inc;
+  __syncthreads();
+  int2 before = make_int2(0, 0);
+  total = make_int2(0, 0);
+#pragma unroll
+  for (int w = 0; w < kWarps; ++w) {
+    const int2 t = warp_tot[w];
+    if (w < wid) {
+      before.x += t.x;
+      before.y += t.y;
+    }
+    total.x += t.x;
+    total.y += t.y;
+  }
+  return make_int2(before.x + inc.x - v.x, before.y + inc.y - v.y);
+}
+
+// The listed query holding work item `it`: the largest q < nq with
+// first_item[q] <= it (first_item ascending from first_item[0] = 0).
+__device__ __forceinline__ int item_owner(const int* first_item, int nq, int it) {
+  int lo = 0, hi = nq - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (first_item[mid] <= it) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
 // ---------------------------------------------------------------------------
 // Batched launches: unit -> planner lookup and block-wide copies of arguments.
 // ---------------------------------------------------------------------------

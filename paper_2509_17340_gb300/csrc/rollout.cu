@@ -264,36 +264,6 @@ __device__ __forceinline__ SplitSmem split_layout(unsigned char* base, int T) {
   return m;
 }
 
-// Exclusive prefix sums of (x, y) over a CTA of kWarps warps; `total`
-// receives the sums.  warp_tot: kWarps entries of shared memory.
-template <int kWarps>
-__device__ __forceinline__ int2 block_scan2(int2 v, int2* warp_tot, int2& total) {
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  int2 inc = v;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const int x = __shfl_up_sync(0xffffffffu, inc.x, o), y = __shfl_up_sync(0xffffffffu, inc.y, o);
-    if (lane >= o) {
-      inc.x += x;
-      inc.y += y;
-    }
-  }
-  if (lane == 31) warp_tot[wid] = inc;
-  __syncthreads();
-  int2 before = make_int2(0, 0);
-  total = make_int2(0, 0);
-#pragma unroll
-  for (int w = 0; w < kWarps; ++w) {
-    const int2 t = warp_tot[w];
-    if (w < wid) {
-      before.x += t.x;
-      before.y += t.y;
-    }
-    total.x += t.x;
-    total.y += t.y;
-  }
-  return make_int2(before.x + inc.x - v.x, before.y + inc.y - v.y);
-}
 
 __device__ __forceinline__ void rollout_split_unit(const RolloutArgs& a, int e, int b,
                                                    uint32_t ctr3) {
@@ -399,12 +369,7 @@ __device__ __forceinline__ void rollout_split_unit(const RolloutArgs& a, int e, 
     if (tid == 0) m.qitem[total.x] = total.y;
     __syncthreads();  // query list complete
     for (int it = tid; it < total.y; it += ST) {
-      // the listed query holding item `it`: largest q with qitem[q] <= it
-      int lo = 0, hi = total.x - 1;
-      while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (m.qitem[mid] <= it) lo = mid; else hi = mid - 1;
-      }
+      const int lo = item_owner(m.qitem, total.x, it);
       const int2 r = m.qrange[lo];
       const int slot = m.qslot[lo];
       const int first = (it - m.qitem[lo]) * kItem;
@@ -626,11 +591,7 @@ __device__ __forceinline__ void update_unit(const UpdateArgs& a, int e, bool fin
   }
   __syncthreads();
   for (int it = tid; it < total.y; it += UT) {
-    int lo = 0, hi = total.x - 1;
-    while (lo < hi) {
-      const int mid = (lo + hi + 1) >> 1;
-      if (s_qitem[mid] <= it) lo = mid; else hi = mid - 1;
-    }
+    const int lo = item_owner(s_qitem, total.x, it);
     const int2 r = s_qrange[lo];
     const int j = s_qslot[lo];
     const int first = (it - s_qitem[lo]) * kItem;
