@@ -261,11 +261,25 @@ __device__ __forceinline__ float warp_sum4(float a0, float a1, float a2, float a
   return c;
 }
 
-// Exclusive prefix sums of (x, y) over a CTA of kWarps warps; `total`
-// receives the sums.  warp_tot: kWarps entries of shared memory.
-template <int kWarps>
-__device__ __forceinline__ int2 block_scan2(int2 v, int2* warp_tot, int2& total) {
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+// Barrier among the kWarps warps that execute it: barrier 0 (the CTA's,
+// kWarps = all of them) or named barrier kBar among a subset of warps.
+template <int kWarps, int kBar>
+__device__ __forceinline__ void warps_sync() {
+  if constexpr (kBar == 0) {
+    __syncthreads();
+  } else {
+    asm volatile("bar.sync %0, %1;" ::"n"(kBar), "n"(kWarps * 32) : "memory");
+  }
+}
+
+// Exclusive prefix sums of (x, y) over kWarps warps (the CTA, or the warps
+// that meet at named barrier kBar, numbered wid = 0..kWarps-1 among
+// themselves); `total` receives the sums.  warp_tot: kWarps entries of
+// shared memory.
+template <int kWarps, int kBar = 0>
+__device__ __forceinline__ int2 block_scan2(int2 v, int2* warp_tot, int2& total,
+                                            int wid = threadIdx.x >> 5) {
+  const int lane = threadIdx.x & 31;
   int2 inc = v;
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
@@ -276,7 +290,7 @@ __device__ __forceinline__ int2 block_scan2(int2 v, int2* warp_tot, int2& total)
     }
   }
   if (lane == 31) warp_tot[wid] = inc;
-  __syncthreads();
+  warps_sync<kWarps, kBar>();
   int2 before = make_int2(0, 0);
   total = make_int2(0, 0);
 #pragma unroll

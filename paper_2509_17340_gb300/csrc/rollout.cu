@@ -192,29 +192,34 @@ __device__ __forceinline__ void rollout_unit(const RolloutArgs& a, int e, int b,
 // samples per CTA (eight threads per sample, one in each of its eight warps);
 // the horizon in chunks of at most kChunk steps.
 //   noise    the perturbations of every step, drawn by all warps before
-//            the first chunk (the integrating warp then has its scheduler
-//            to itself); the clamped controls stay in shared memory for the
-//            whole horizon;
-//   dynamics one warp, one lane per sample, applies the chunk's controls with
-//            RK4; the states go to shared memory (this is the only serial
-//            chain, so nothing else runs in it);
-//   queries  every (sample, step) of the chunk looks up its cell; the
-//            non-empty candidate lists are cut into items of kItem entries
-//            and the CTA's threads take the items in turn, each folding its
-//            squared distances into the query's minimum with a shared-memory
-//            atomic minimum (exact in any order).  A warp therefore scans
-//            items, not its longest lane's list: the lists of one step's
-//            samples are mostly empty, with a few of up to a hundred entries;
-//   costs    every (sample, step) pair's control, state and collision terms.
-// Then the per-CTA minimum, weights and weighted perturbation sums as in the
-// one-lane pass: every warp holds the 32 samples' costs and reduces them
-// itself.
+//            the first chunk; the clamped controls stay in shared memory for
+//            the whole horizon;
+//   dynamics one warp (the integrator), one lane per sample, applies a
+//            chunk's controls with RK4 and stores the states in one of two
+//            chunk buffers;
+//   queries  the seven other warps (the workers) look up the cell of every
+//            (sample, step) of the chunk integrated before; the non-empty
+//            candidate lists are cut into items of kItem entries and the
+//            workers take the items in turn, each folding its squared
+//            distances into the query's minimum with a shared-memory atomic
+//            minimum (exact in any order).  A warp therefore scans items, not
+//            its longest lane's list: the lists of one step's samples are
+//            mostly empty, with a few of up to a hundred entries;
+//   costs    the workers evaluate every (sample, step) pair's control, state
+//            and collision terms.
+// The integrator runs chunk c + 1 while the workers query and score chunk c
+// (they meet at a named barrier; the CTA's barrier closes each round), so the
+// serial chain overlaps the rest.  Then the per-CTA minimum, weights and
+// weighted perturbation sums as in the one-lane pass: every warp holds the 32
+// samples' costs and reduces them itself.
 // ---------------------------------------------------------------------------
 constexpr int ST = 256;          // threads per CTA (eight per sample)
 constexpr int SW = ST / 32;      // warps per CTA
+constexpr int SWK = SW - 1;      // worker warps (all but the integrator)
+constexpr int kWorkBar = 1;      // the workers' named barrier
 constexpr int QS = 32;           // samples per CTA
 constexpr int kChunk = 20;       // steps per chunk
-constexpr int kQ = (kChunk + SW - 1) / SW;  // queries per thread and chunk, at most
+constexpr int kQ = (kChunk + SWK - 1) / SWK;  // queries per worker thread and chunk, at most
 constexpr int kItem = 8;         // candidate entries per scan item
 constexpr int kChunkQ = kChunk * QS;
 
@@ -223,7 +228,7 @@ __host__ __device__ constexpr size_t split_smem_bytes(int T) {
   return 16 * (size_t)T * QS       // u: clamped controls [T][QS]
          + 16 * (size_t)T          // un: nominal [T]
          + 8 * (size_t)kChunkQ     // qrange: candidate range of each listed query
-         + 40 * (size_t)kChunkQ    // xa, xb, xc: states x_{j+1} [kChunk][QS]
+         + 80 * (size_t)kChunkQ    // xa, xb, xc: states x_{j+1} [2][kChunk][QS]
          + 4 * (size_t)kChunkQ     // d2: squared distance bits [kChunk][QS]
          + 4 * (size_t)SW * QS     // cost: partial sums [SW][QS]
          + 4 * (size_t)(kChunkQ + 2)  // qitem: first item of each listed query (+ pad)
@@ -236,7 +241,7 @@ struct SplitSmem {
   float4* u;
   float4* un;
   int2* qrange;
-  float4* xa;  // p, q0
+  float4* xa;  // p, q0        [2][kChunkQ]
   float4* xb;  // q1, q2, q3, v0
   float2* xc;  // v1, v2
   int* d2;
@@ -253,9 +258,9 @@ __device__ __forceinline__ SplitSmem split_layout(unsigned char* base, int T) {
   m.un = m.u + (size_t)T * QS;
   m.qrange = reinterpret_cast<int2*>(m.un + T);
   m.xa = reinterpret_cast<float4*>(m.qrange + kChunkQ);
-  m.xb = m.xa + kChunkQ;
-  m.xc = reinterpret_cast<float2*>(m.xb + kChunkQ);
-  m.d2 = reinterpret_cast<int*>(m.xc + kChunkQ);
+  m.xb = m.xa + 2 * kChunkQ;
+  m.xc = reinterpret_cast<float2*>(m.xb + 2 * kChunkQ);
+  m.d2 = reinterpret_cast<int*>(m.xc + 2 * kChunkQ);
   m.cost = reinterpret_cast<float*>(m.d2 + kChunkQ);
   m.qitem = reinterpret_cast<int*>(m.cost + SW * QS);
   m.scan = reinterpret_cast<int2*>(m.qitem + kChunkQ + 1 + 1);  // +1 word keeps int2 aligned
@@ -263,7 +268,6 @@ __device__ __forceinline__ SplitSmem split_layout(unsigned char* base, int T) {
   m.qslot = reinterpret_cast<unsigned short*>(m.gd + 3 * T);
   return m;
 }
-
 
 __device__ __forceinline__ void rollout_split_unit(const RolloutArgs& a, int e, int b,
                                                    uint32_t ctr3) {
@@ -285,7 +289,6 @@ __device__ __forceinline__ void rollout_split_unit(const RolloutArgs& a, int e, 
   const int nch = (T + kChunk - 1) / kChunk;
   const int tcb = (T + nch - 1) / nch;  // steps per chunk (the last may be shorter)
 
-
   State x;
 #pragma unroll
   for (int i = 0; i < 3; ++i) x.p[i] = a.x0[i];
@@ -293,14 +296,17 @@ __device__ __forceinline__ void rollout_split_unit(const RolloutArgs& a, int e, 
   for (int i = 0; i < 4; ++i) x.q[i] = a.x0[3 + i];
 #pragma unroll
   for (int i = 0; i < 3; ++i) x.v[i] = a.x0[7 + i];
-  // the integrating warp rotates with the block index, so that the
-  // integrators of the CTAs sharing an SM sit on different schedulers
+  // the integrator rotates with the block index, so that the integrators of
+  // the CTAs sharing an SM sit on different schedulers; the workers are
+  // numbered widx = 0..SWK-1 from the warp after it
   const int wint = b & (SW - 1);
-  if (dbg >= 0 && wid == wint) {
+  const bool integrator = wid == wint;
+  const int widx = (wid + SW - 1 - wint) & (SW - 1);
+  if (dbg >= 0 && integrator) {
     float* X = a.dbg_x + (size_t)dbg * (T + 1) * 10;
     for (int i = 0; i < 10; ++i) X[i] = a.x0[i];
   }
-  float S = 0.0f;  // every thread: the cost terms of its (sample, step) pairs
+  float S = 0.0f;  // every worker thread: the cost terms of its (sample, step) pairs
 
   // the perturbations (independent of the nominal) while the nominal loads,
   // then the clamped controls: each thread rereads only what it wrote
@@ -312,41 +318,50 @@ __device__ __forceinline__ void rollout_split_unit(const RolloutArgs& a, int e, 
     m.u[j * QS + lane] = clamp4(make_float4(un.x + d.x, un.y + d.y, un.z + d.z, un.w + d.w), umin, umax);
   }
   __syncthreads();
-  for (int j0 = 0; j0 < T; j0 += tcb) {
-    const int tc = tcb < T - j0 ? tcb : T - j0;
-    if (wid == wint) {
-      float4 u_nx = m.u[j0 * QS + lane];
-      for (int jj = 0; jj < tc; ++jj) {
-        const int j = j0 + jj;
-        const float4 u = u_nx;
-        if (jj + 1 < tc) u_nx = m.u[(j + 1) * QS + lane];  // one step ahead
-        rk4_step(x, u, a.dyn);
-        m.xa[jj * QS + lane] = make_float4(x.p[0], x.p[1], x.p[2], x.q[0]);
-        m.xb[jj * QS + lane] = make_float4(x.q[1], x.q[2], x.q[3], x.v[0]);
-        m.xc[jj * QS + lane] = make_float2(x.v[1], x.v[2]);
-        if (dbg >= 0) {
-          reinterpret_cast<float4*>(a.dbg_u)[(size_t)dbg * T + j] = u;
-          float* X = a.dbg_x + ((size_t)dbg * (T + 1) + j + 1) * 10;
-          for (int i = 0; i < 3; ++i) X[i] = x.p[i];
-          for (int i = 0; i < 4; ++i) X[3 + i] = x.q[i];
-          for (int i = 0; i < 3; ++i) X[7 + i] = x.v[i];
-        }
+
+  // the integrator: the states of chunk c into buffer c & 1
+  auto integrate = [&](int c) {
+    const int j0 = c * tcb, tc = tcb < T - j0 ? tcb : T - j0;
+    float4* xa = m.xa + (c & 1) * kChunkQ;
+    float4* xb = m.xb + (c & 1) * kChunkQ;
+    float2* xc = m.xc + (c & 1) * kChunkQ;
+    float4 u_nx = m.u[j0 * QS + lane];
+    for (int jj = 0; jj < tc; ++jj) {
+      const int j = j0 + jj;
+      const float4 u = u_nx;
+      if (jj + 1 < tc) u_nx = m.u[(j + 1) * QS + lane];  // one step ahead
+      rk4_step(x, u, a.dyn);
+      xa[jj * QS + lane] = make_float4(x.p[0], x.p[1], x.p[2], x.q[0]);
+      xb[jj * QS + lane] = make_float4(x.q[1], x.q[2], x.q[3], x.v[0]);
+      xc[jj * QS + lane] = make_float2(x.v[1], x.v[2]);
+      if (dbg >= 0) {
+        reinterpret_cast<float4*>(a.dbg_u)[(size_t)dbg * T + j] = u;
+        float* X = a.dbg_x + ((size_t)dbg * (T + 1) + j + 1) * 10;
+        for (int i = 0; i < 3; ++i) X[i] = x.p[i];
+        for (int i = 0; i < 4; ++i) X[3 + i] = x.q[i];
+        for (int i = 0; i < 3; ++i) X[7 + i] = x.v[i];
       }
     }
-    __syncthreads();  // states filled
+  };
 
-    // this thread's queries: steps jj = wid + 8 i of the chunk, sample `lane`
+  // the workers: queries and costs of chunk c
+  auto score_chunk = [&](int c) {
+    const int j0 = c * tcb, tc = tcb < T - j0 ? tcb : T - j0;
+    const float4* xa = m.xa + (c & 1) * kChunkQ;
+    const float4* xb = m.xb + (c & 1) * kChunkQ;
+    const float2* xc = m.xc + (c & 1) * kChunkQ;
+    // this thread's queries: steps jj = widx + SWK i of the chunk, sample `lane`
     int2 rg[kQ];
     int2 cnt = make_int2(0, 0);  // (listed queries, items)
 #pragma unroll
     for (int i = 0; i < kQ; ++i) {
-      const int jj = wid + SW * i;
+      const int jj = widx + SWK * i;
       rg[i] = make_int2(0, 0);
       if (jj < tc) {
         m.d2[jj * QS + lane] = __float_as_int(dmax2);
         if (active) {
-          const float4 xa = m.xa[jj * QS + lane];
-          rg[i] = cell_range(xa.x, xa.y, xa.z, a.grid);
+          const float4 p = xa[jj * QS + lane];
+          rg[i] = cell_range(p.x, p.y, p.z, a.grid);
         }
       }
       if (rg[i].y > 0) {
@@ -355,31 +370,31 @@ __device__ __forceinline__ void rollout_split_unit(const RolloutArgs& a, int e, 
       }
     }
     int2 total;
-    int2 off = block_scan2<SW>(cnt, m.scan, total);
+    int2 off = block_scan2<SWK, kWorkBar>(cnt, m.scan, total, widx);
 #pragma unroll
     for (int i = 0; i < kQ; ++i) {
       if (rg[i].y > 0) {
         m.qitem[off.x] = off.y;
         m.qrange[off.x] = rg[i];
-        m.qslot[off.x] = (unsigned short)((wid + SW * i) * QS + lane);
+        m.qslot[off.x] = (unsigned short)((widx + SWK * i) * QS + lane);
         off.x += 1;
         off.y += (rg[i].y + kItem - 1) / kItem;
       }
     }
-    if (tid == 0) m.qitem[total.x] = total.y;
-    __syncthreads();  // query list complete
-    for (int it = tid; it < total.y; it += ST) {
+    if (widx == 0 && lane == 0) m.qitem[total.x] = total.y;
+    warps_sync<SWK, kWorkBar>();  // query list complete
+    for (int it = widx * 32 + lane; it < total.y; it += SWK * 32) {
       const int lo = item_owner(m.qitem, total.x, it);
       const int2 r = m.qrange[lo];
       const int slot = m.qslot[lo];
       const int first = (it - m.qitem[lo]) * kItem;
       const int n = r.y - first < kItem ? r.y - first : kItem;
       if (!AERO_CHECK(slot < kChunkQ && first >= 0 && n > 0 && r.x >= 0, kChkQuery)) continue;
-      const float4 xa = m.xa[slot];
-      const float d2 = scan_min<kItem>(a.grid.pts + r.x + first, n, xa.x, xa.y, xa.z, dmax2);
+      const float4 p = xa[slot];
+      const float d2 = scan_min<kItem>(a.grid.pts + r.x + first, n, p.x, p.y, p.z, dmax2);
       if (d2 < dmax2) atomicMin(m.d2 + slot, __float_as_int(d2));  // non-negative: int order
     }
-    __syncthreads();  // minima complete
+    warps_sync<SWK, kWorkBar>();  // minima complete
     // the cost of every (sample, step) pair of this thread: J_ctrl's terms
     // Q_c |u_j|^2 (j <= T-2) and Q_cd |u_j - u_{j-1}|^2 (1 <= j <= T-2), the
     // state terms at x_{j+1} against the guide at t = (j + 1) dt, J_col.  The
@@ -388,32 +403,42 @@ __device__ __forceinline__ void rollout_split_unit(const RolloutArgs& a, int e, 
     float cs[kQ];
 #pragma unroll
     for (int i = 0; i < kQ; ++i) {
-      const int jq = wid + SW * i;
+      const int jq = widx + SWK * i;
       const int jj = jq < tc ? jq : tc - 1, j = j0 + jj;
       const float4 u = m.u[j * QS + lane];
       const float4 up = m.u[(j >= 1 ? j - 1 : 0) * QS + lane];
       const float ax = u.x - up.x, ay = u.y - up.y, az = u.z - up.z, aw = u.w - up.w;
       const float c_u = cp.Q_c * (u.x * u.x + u.y * u.y + u.z * u.z + u.w * u.w);
       const float c_du = cp.Q_cd * (ax * ax + ay * ay + az * az + aw * aw);
-      float c = j <= T - 2 ? (j >= 1 ? c_u + c_du : c_u) : 0.0f;
-      const float4 xa = m.xa[jj * QS + lane], xb = m.xb[jj * QS + lane];
-      const float2 xc = m.xc[jj * QS + lane];
+      float cj = j <= T - 2 ? (j >= 1 ? c_u + c_du : c_u) : 0.0f;
+      const float4 pa = xa[jj * QS + lane], pb = xb[jj * QS + lane];
+      const float2 pc = xc[jj * QS + lane];
       State y;
-      y.p[0] = xa.x; y.p[1] = xa.y; y.p[2] = xa.z;
-      y.q[0] = xa.w; y.q[1] = xb.x; y.q[2] = xb.y; y.q[3] = xb.z;
-      y.v[0] = xb.w; y.v[1] = xc.x; y.v[2] = xc.y;
+      y.p[0] = pa.x; y.p[1] = pa.y; y.p[2] = pa.z;
+      y.q[0] = pa.w; y.q[1] = pb.x; y.q[2] = pb.y; y.q[3] = pb.z;
+      y.v[0] = pb.w; y.v[1] = pc.x; y.v[2] = pc.y;
       const float gx = m.gd[3 * j], gy = m.gd[3 * j + 1], gz = m.gd[3 * j + 2];
-      c += cp.Q_track * norm3f(y.p[0] - gx, y.p[1] - gy, y.p[2] - gz);
-      c += cp.Q_vnorm * (y.v[0] * y.v[0] + y.v[1] * y.v[1] + y.v[2] * y.v[2]);
-      c += goal_term(y, cp);
+      cj += cp.Q_track * norm3f(y.p[0] - gx, y.p[1] - gy, y.p[2] - gz);
+      cj += cp.Q_vnorm * (y.v[0] * y.v[0] + y.v[1] * y.v[1] + y.v[2] * y.v[2]);
+      cj += goal_term(y, cp);
       const float d2 = __int_as_float(m.d2[jj * QS + lane]);
-      c += jcol_select(d2, cp, dmax2);
-      cs[i] = jq < tc && active ? c : 0.0f;
+      cj += jcol_select(d2, cp, dmax2);
+      cs[i] = jq < tc && active ? cj : 0.0f;
       if (jq < tc && dbg >= 0) a.dbg_d[(size_t)dbg * T + j] = d2 < dmax2 ? sqrtf(d2) : INFINITY;
     }
 #pragma unroll
     for (int i = 0; i < kQ; ++i) S += cs[i];
-    __syncthreads();  // state buffers free for the next chunk
+  };
+
+  if (integrator) integrate(0);
+  __syncthreads();  // chunk 0's states filled
+  for (int c = 0; c < nch; ++c) {
+    if (integrator) {
+      if (c + 1 < nch) integrate(c + 1);
+    } else {
+      score_chunk(c);
+    }
+    __syncthreads();  // chunk c + 1 filled; chunk c's buffer free
   }
   m.cost[wid * QS + lane] = S;
   __syncthreads();
@@ -449,29 +474,84 @@ __device__ __forceinline__ void rollout_split_unit(const RolloutArgs& a, int e, 
 // ---------------------------------------------------------------------------
 constexpr int UT = 128;  // threads of the update kernels
 
+__host__ __device__ constexpr size_t round16(size_t n) { return (n + 15) & ~(size_t)15; }
+
+// Shared memory of update_unit (bytes) for horizon T and `warps` warps: its
+// own arrays, then the refinement's scratch when `refine`.
+__host__ __device__ constexpr size_t update_smem_bytes(int T, int warps, bool refine) {
+  return 16 * (size_t)warps * T          // acc: weighted sums [warps][T]
+         + round16(40 * (size_t)(T + 1))  // x: Stage II states [T + 1][10]
+         + 16 * (size_t)T                 // u: the updated nominal [T]
+         + round16(8 * (size_t)T)         // qrange: candidate range of each listed query
+         + 4 * 1024                       // scale: exp(-(rho_b - rho)/lambda), b < 1024
+         + 4 * round16(4 * (size_t)(T + 1))  // c, qitem, qslot, d2
+         + round16(4 * (size_t)warps)     // red: warp reductions
+         + round16(8 * (size_t)warps)     // scan: warp totals
+         + (refine ? refine_smem_bytes(T, warps) : 0);
+}
+
+struct UpdSmem {
+  float4* acc;
+  float* x;
+  float4* u4;
+  int2* qrange;
+  float* scale;
+  float* c;
+  int* qitem;
+  int* qslot;
+  int* d2;
+  float* red;
+  int2* scan;
+  unsigned char* refine;
+};
+
+__device__ __forceinline__ UpdSmem update_layout(unsigned char* base, int T, int warps) {
+  UpdSmem m;
+  size_t o = 0;
+  auto take = [&](size_t n) {
+    unsigned char* p = base + o;
+    o += round16(n);
+    return p;
+  };
+  m.acc = reinterpret_cast<float4*>(take(16 * (size_t)warps * T));
+  m.x = reinterpret_cast<float*>(take(40 * (size_t)(T + 1)));
+  m.u4 = reinterpret_cast<float4*>(take(16 * (size_t)T));
+  m.qrange = reinterpret_cast<int2*>(take(8 * (size_t)T));
+  m.scale = reinterpret_cast<float*>(take(4 * 1024));
+  m.c = reinterpret_cast<float*>(take(4 * (size_t)(T + 1)));
+  m.qitem = reinterpret_cast<int*>(take(4 * (size_t)(T + 1)));
+  m.qslot = reinterpret_cast<int*>(take(4 * (size_t)(T + 1)));
+  m.d2 = reinterpret_cast<int*>(take(4 * (size_t)(T + 1)));
+  m.red = reinterpret_cast<float*>(take(4 * (size_t)warps));
+  m.scan = reinterpret_cast<int2*>(take(8 * (size_t)warps));
+  m.refine = base + o;
+  return m;
+}
+
 // kThreads: the CTA's threads (128 in the update kernels, 256 in the split
-// Stage I pass).  The partials are read through L2 (ld.cg): in the split pass
-// other CTAs of the same launch wrote them.
+// Stage I pass).  smem: update_smem_bytes(T, kThreads / 32, refine) bytes of
+// dynamic shared memory (16-byte aligned).  The partials are read through L2
+// (ld.cg): in the split pass other CTAs of the same launch wrote them.
 template <int kThreads>
 __device__ __forceinline__ void update_unit(const UpdateArgs& a, int e, bool final_stage,
-                                            unsigned char* rscratch) {
+                                            unsigned char* smem) {
   constexpr int UT = kThreads;
-  __shared__ float s_scale[1024];
-  __shared__ float s_red[UT / 32];
-  __shared__ __align__(16) float s_x[(kMaxT + 1) * 10];  // Stage II states
-  __shared__ float4 s_u4[kMaxT];
-  float* s_u = reinterpret_cast<float*>(s_u4);
-  __shared__ float s_c[kMaxT];
-  __shared__ float4 s_acc[UT / 32][kMaxT];
+  const int T = a.T, stride = 4 + 4 * T;
+  const UpdSmem sm = update_layout(smem, T, UT / 32);
+  float* const s_scale = sm.scale;
+  float* const s_red = sm.red;
+  float* const s_x = sm.x;  // Stage II states
+  float4* const s_u4 = sm.u4;
+  float* const s_u = reinterpret_cast<float*>(s_u4);
+  float* const s_c = sm.c;
   __shared__ bool s_last;
   // Stage II's nearest-point queries (one per step, cut into items)
-  __shared__ int s_qitem[kMaxT + 1];
-  __shared__ int2 s_qrange[kMaxT];
-  __shared__ int s_qslot[kMaxT];
-  __shared__ int s_d2[kMaxT];
-  __shared__ int2 s_scan[UT / 32];
+  int* const s_qitem = sm.qitem;
+  int2* const s_qrange = sm.qrange;
+  int* const s_qslot = sm.qslot;
+  int* const s_d2 = sm.d2;
+  int2* const s_scan = sm.scan;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-  const int T = a.T, stride = 4 + 4 * T;
   const float* P = a.partials + (size_t)e * a.nb * stride;
 
   // rho = min rho_b (a thread's first row keeps its rho_b and eta_b for the sum)
@@ -529,14 +609,14 @@ __device__ __forceinline__ void update_unit(const UpdateArgs& a, int e, bool fin
   }
 #pragma unroll
   for (int q = 0; q < kCol; ++q)
-    if (lane + 32 * q < T) s_acc[wid][lane + 32 * q] = acc[q];
+    if (lane + 32 * q < T) sm.acc[wid * T + lane + 32 * q] = acc[q];
   __syncthreads();
   float* un = a.u_nom + (size_t)e * T * 4;
   for (int i = tid; i < 4 * T; i += UT) {
     const int j = i >> 2, c = i & 3;
     float sum = 0.0f;
 #pragma unroll
-    for (int w = 0; w < UT / 32; ++w) sum += reinterpret_cast<const float*>(&s_acc[w][j])[c];
+    for (int w = 0; w < UT / 32; ++w) sum += reinterpret_cast<const float*>(&sm.acc[w * T + j])[c];
     const float v = un[i] + sum * inv_eta;
     un[i] = v;
     s_u[i] = v;
@@ -544,13 +624,13 @@ __device__ __forceinline__ void update_unit(const UpdateArgs& a, int e, bool fin
   if (!final_stage) return;
   __syncthreads();
 
-  // gradient refinement of the updated nominal by the whole CTA (rscratch:
-  // refine_smem_bytes(T, warps) of shared memory)
+  // gradient refinement of the updated nominal by the whole CTA (the scratch
+  // after the update's own arrays)
   if (a.refine_steps > 0) {
     if (a.dbg_pre)
       for (int i = tid; i < 4 * T; i += UT) a.dbg_pre[(size_t)e * T * 4 + i] = s_u[i];
     block_refine<UT>(s_u4, a.guides + (size_t)e * T * 3, T, a.x0, a.dyn, a.cost, a.grid, a.umin,
-                     a.umax, a.refine_steps, a.refine_step, refine_layout(rscratch, T, UT / 32));
+                     a.umax, a.refine_steps, a.refine_step, refine_layout(sm.refine, T, UT / 32));
     for (int i = tid; i < 4 * T; i += UT) un[i] = s_u[i];
     __syncthreads();
   }
@@ -659,7 +739,7 @@ __global__ void __launch_bounds__(NT) k_rollout(RolloutArgs a) {
 
 // The split pass with the update of every instance run by the last of its
 // CTAs to finish (a ticket per instance, reset by that CTA): no update launch.
-__global__ void __launch_bounds__(ST) k_rollout_split(RolloutArgs a, UpdateArgs ua) {
+__global__ void __launch_bounds__(ST, 2) k_rollout_split(RolloutArgs a, UpdateArgs ua) {
   pdl_start();
   const int e = blockIdx.y;
   rollout_split_unit(a, e, blockIdx.x, a.ctr3);
@@ -687,7 +767,7 @@ __global__ void __launch_bounds__(UT) k_update(UpdateArgs a) {
   __shared__ UpdateArgs s_a;
   block_copy_param(&s_a, &a);
   __syncthreads();
-  extern __shared__ __align__(16) unsigned char upd_smem[];  // the refinement's scratch
+  extern __shared__ __align__(16) unsigned char upd_smem[];  // update_smem_bytes(T, UT / 32, refine)
   update_unit<UT>(s_a, blockIdx.x, s_a.final_stage != 0, upd_smem);
 }
 
@@ -755,7 +835,7 @@ __global__ void __launch_bounds__(kLanes == 4 ? ST : NT, kMinCtas)
 // planner runs its Stage II and selection.
 __global__ void __launch_bounds__(UT) k_b_update(BatchView v, int it) {
   pdl_start();
-  extern __shared__ __align__(16) unsigned char upd_smem[];  // the refinement's scratch
+  extern __shared__ __align__(16) unsigned char upd_smem[];  // update_smem_bytes(T_max, UT / 32, true)
   __shared__ long long s_pre[kBatchMax + 1];
   __shared__ UpdateArgs s_a;
   __shared__ int s_iters;
@@ -777,9 +857,13 @@ __global__ void __launch_bounds__(UT) k_b_update(BatchView v, int it) {
   }
 }
 
-static_assert(refine_smem_bytes(kMaxT, ST / 32) <= split_smem_bytes(kMaxT) &&
-                  refine_smem_bytes(1, ST / 32) <= split_smem_bytes(1),
-              "the split pass's shared memory holds the fused update's refinement scratch");
+constexpr bool fused_update_fits() {
+  for (int T = 1; T <= kMaxT; ++T)
+    if (update_smem_bytes(T, ST / 32, true) > split_smem_bytes(T)) return false;
+  return true;
+}
+static_assert(fused_update_fits(),
+              "the split pass's shared memory holds the fused update and its refinement scratch");
 
 // One warp per control sequence: S(1) of its noise-free rollout and dS/dU.
 constexpr int kCgWarps = 4;
@@ -824,7 +908,7 @@ cudaError_t split_attributes() {
     cudaError_t r = cudaFuncSetAttribute(k_rollout_split, cudaFuncAttributeMaxDynamicSharedMemorySize, most);
     if (r == cudaSuccess)
       r = cudaFuncSetAttribute(k_b_rollout<4, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, most);
-    const int refine = (int)refine_smem_bytes(kMaxT, UT / 32);
+    const int refine = (int)update_smem_bytes(kMaxT, UT / 32, true);
     if (r == cudaSuccess)
       r = cudaFuncSetAttribute(k_update, cudaFuncAttributeMaxDynamicSharedMemorySize, refine);
     if (r == cudaSuccess)
@@ -861,7 +945,7 @@ cudaError_t batch_rollout_occupancy(int out[4], int T_max) {
                                                       split_smem_bytes(T_max));
   if (e == cudaSuccess)
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(out + 2, k_b_update, UT,
-                                                      refine_smem_bytes(T_max, UT / 32));
+                                                      update_smem_bytes(T_max, UT / 32, true));
   if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(out + 3, k_b_rollout<1, 6>, NT, 0);
   for (int i = 0; i < 4; ++i)
     if (out[i] < 1) out[i] = 1;
@@ -878,8 +962,8 @@ cudaError_t launch_batch_rollout(const BatchView& v, int lanes, int it, int bloc
 }
 
 cudaError_t launch_batch_update(const BatchView& v, int it, int blocks, cudaStream_t s) {
-  return launch_ks(k_b_update, dim3(blocks), dim3(UT), refine_smem_bytes(v.T_max, UT / 32), s, true,
-                   v, it);
+  return launch_ks(k_b_update, dim3(blocks), dim3(UT), update_smem_bytes(v.T_max, UT / 32, true), s,
+                   true, v, it);
 }
 
 bool rollout_runs_update(const RolloutArgs& a) { return a.lanes_per_sample == 4; }
@@ -902,7 +986,7 @@ cudaError_t launch_rollout(const RolloutArgs& a, const UpdateArgs& ua, cudaStrea
 cudaError_t launch_update(const UpdateArgs& a, cudaStream_t s) {
   const cudaError_t e = split_attributes();  // also the update kernels' scratch limit
   if (e != cudaSuccess) return e;
-  const size_t smem = a.refine_steps > 0 ? refine_smem_bytes(a.T, UT / 32) : 0;
+  const size_t smem = update_smem_bytes(a.T, UT / 32, a.refine_steps > 0);
   return launch_ks(k_update, dim3(a.E), dim3(UT), smem, s, true, a);
 }
 
