@@ -130,9 +130,11 @@ typedef struct {
   float q_goal[4];        /* goal attitude (w, x, y, z) */
   int32_t debug_samples;  /* D: record rollouts of samples k < D (0 = off) */
   int32_t lanes_per_sample; /* Stage I kernel: 1 = one thread per sample; 4 = the split
-                             pass for small problems (noise, dynamics, nearest-point
-                             queries and costs in separate phases over eight threads per
-                             sample, the update run by each instance's last CTA);
+                             pass for small problems (eight threads per sample: noise
+                             for the whole horizon, then one warp integrates the next
+                             chunk of steps while the others run the nearest-point
+                             queries and costs of the last; the update run by each
+                             instance's last CTA);
                              0 = automatic (4 when E*K <= 32768, else 1) */
   uint64_t seed;          /* Philox key */
   uint64_t step_id;       /* enters the Philox counter: (k, j, e, (step_id << 8) | iter) */
