@@ -204,7 +204,7 @@ int aero_plan_step_host(aero_planner_t* planner, const aero_state_t* x0, const f
  * the device and take an unbounded time, and some host programs own all device
  * memory through their own pool; aero_create allocates, so they call this
  * instead.  No planner is needed and nothing is allocated: the workspace is a
- * fixed file-scope device array of about 6.5 MB that every GPU loading this
+ * fixed file-scope device array of about 7.5 MB that every GPU loading this
  * library keeps until the process exits.
  *   Limits: E <= 16, K <= 2048, T <= 64, fine_az * fine_el <= 8192,
  *   n_points <= 65536, collision_set == 0 (P_f), debug_samples == 0; the

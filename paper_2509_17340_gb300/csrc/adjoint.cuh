@@ -60,7 +60,7 @@ __device__ __forceinline__ void warp_nn_segment(AdjScratch& sc, int n, const Gri
     const float* x = sc.seg + (k + 1) * 10;
     const int2 r = cell_range(x[0], x[1], x[2], g);
     for (int i = q; i < r.y; i += 4) {
-      const float d2 = dist2_to(__ldg(g.pts + r.x + i), x[0], x[1], x[2]);
+      const float d2 = dist2_to(grid_point(g, r.x + i), x[0], x[1], x[2]);
       if (d2 < best) {
         best = d2;
         bi = r.x + i;
@@ -78,7 +78,7 @@ __device__ __forceinline__ void warp_nn_segment(AdjScratch& sc, int n, const Gri
   }
   if (k < n && q == 0) {
     sc.d2[k] = best;
-    sc.nearest[k] = bi != 0x7fffffff ? __ldg(g.pts + bi) : make_float4(0.f, 0.f, 0.f, 0.f);
+    sc.nearest[k] = bi != 0x7fffffff ? grid_point(g, bi) : make_float4(0.f, 0.f, 0.f, 0.f);
   }
 }
 
@@ -458,7 +458,7 @@ __device__ void block_refine(float4* u, const float* guide, int T, const float* 
       float best = dmax2;
       int bi = -1;
       for (int c = 0; c < n; ++c) {  // in entry order: the first of equal distances stays
-        const float d2 = dist2_to(__ldg(grid.pts + q.x + first + c), x1[0], x1[1], x1[2]);
+        const float d2 = dist2_to(grid_point(grid, q.x + first + c), x1[0], x1[1], x1[2]);
         if (d2 < best) {
           best = d2;
           bi = q.x + first + c;
@@ -473,7 +473,7 @@ __device__ void block_refine(float4* u, const float* guide, int T, const float* 
       const unsigned long long kk = rs.key[tid];
       const float d2 = __uint_as_float((unsigned)(kk >> 32));
       const unsigned bi = (unsigned)kk;
-      const float4 nearest = bi != 0xffffffffu ? __ldg(grid.pts + bi) : make_float4(0.f, 0.f, 0.f, 0.f);
+      const float4 nearest = bi != 0xffffffffu ? grid_point(grid, (int)bi) : make_float4(0.f, 0.f, 0.f, 0.f);
       state_terms<true>(state_load(rs.xs + (tid + 1) * 10), guide[3 * tid], guide[3 * tid + 1],
                         guide[3 * tid + 2], d2, nearest, cp, dmax2, rs.gs + tid * 10);
     }

@@ -110,7 +110,9 @@ struct aero_planner {
   int* grid_local = nullptr;  // G^3 + 1 tile-local exclusive prefix
   int* tile_sum = nullptr;
   int* tile_off = nullptr;
-  float4* cand = nullptr;     // candidate entries
+  float4* cand = nullptr;     // candidate entries: points, or item indices (as uint32)
+  float4* cand_pts = nullptr; // collision point of every item, minus p0 (index entries)
+  bool last_idx_entries = false;  // the last step's entries were item indices
   int2* grid_range = nullptr; // G^3 {first entry, count}
   int cand_cap = 0;
   int grid_max = kGridMax;    // cells per axis the grid arrays can hold
@@ -285,7 +287,7 @@ void free_all(aero_planner* pl) {
   void* ptrs[] = {pl->keys,     pl->coarse_win, pl->cells,        pl->anchors,  pl->guides,
                   pl->item_flag, pl->grid_count, pl->grid_fill, pl->grid_local, pl->tile_sum,
                   pl->tile_off,
-                  pl->cand,     pl->grid_range, pl->partials,
+                  pl->cand,     pl->cand_pts,   pl->grid_range, pl->partials,
                   pl->sample_costs, pl->dU,      pl->stage2_x, pl->counter,   pl->status,   pl->dbg_u,
                   pl->dbg_x,    pl->dbg_d,      pl->stage_cloud,      pl->stage_out,
                   pl->dbg_pre,      pl->part_counts,  pl->d_tab};
@@ -372,7 +374,8 @@ int lanes_of(const aero_params_t& p, int64_t quad_max) {
 
 void make_step_args(aero_planner* pl, const aero_state_t* x0, const float* cloud, int64_t n,
                     const float* goal, const aero_params_t& p, float* u_nom, float* u_best,
-                    float* cand, int32_t* best_idx, int lanes, bool coarse, StepArgs& a) {
+                    float* cand, int32_t* best_idx, int lanes, bool coarse, bool idx_entries,
+                    StepArgs& a) {
   a.ncell = p.fine_az * p.fine_el;
   // the edge tables depend only on the partition geometry: recomputed when it changes
   if (!pl->tab_valid || pl->tab_A != p.fine_az || pl->tab_El != p.fine_el || pl->tab_lo != p.el_lo ||
@@ -424,7 +427,9 @@ void make_step_args(aero_planner* pl, const aero_state_t* x0, const float* cloud
   ca.fill = pl->grid_fill;
   ca.local = pl->grid_local;
   ca.tile_off = pl->tile_off;
-  ca.cand = pl->cand;
+  ca.cand = idx_entries ? reinterpret_cast<uint32_t*>(pl->cand) : nullptr;
+  ca.pts = idx_entries ? pl->cand_pts : nullptr;
+  ca.cand4 = idx_entries ? nullptr : pl->cand;
   ca.status = pl->status;
   ca.reset_keys = nullptr;
 
@@ -470,7 +475,8 @@ void make_step_args(aero_planner* pl, const aero_state_t* x0, const float* cloud
   for (int i = 0; i < 3; ++i) cp.v_goal[i] = p.v_goal[i];
   for (int i = 0; i < 4; ++i) cp.q_goal[i] = p.q_goal[i];
   DynParams dp{p.dt, 1.0f / p.mass, p.g};
-  GridView gv{pl->grid_range, pl->cand, a.grid.G, a.grid.origin, a.grid.inv_h};
+  GridView gv{pl->grid_range, ca.cand, idx_entries ? pl->cand_pts : pl->cand, a.grid.G, a.grid.origin,
+              a.grid.inv_h};
   const float x0v[10] = {0.0f, 0.0f, 0.0f, x0->q[0], x0->q[1], x0->q[2], x0->q[3],
                          x0->v[0], x0->v[1], x0->v[2]};
   a.lanes = lanes;
@@ -543,6 +549,7 @@ void note_step(aero_planner* pl, const aero_params_t& p, const StepArgs& a) {
   pl->have_step = true;
   pl->last = p;
   pl->last_grid = a.grid;
+  pl->last_idx_entries = a.ca.cand != nullptr;
   pl->last_ntiles = a.ntiles;
   pl->last_nb = a.nb;
   pl->last_part_slots = partition_blocks(a.pa.n);
@@ -555,7 +562,7 @@ int enqueue_step(aero_planner* pl, const aero_state_t* x0, const float* cloud, i
                  float* cand, int32_t* best_idx, cudaStream_t s) {
   StepArgs a;
   make_step_args(pl, x0, cloud, n, goal, p, u_nom, u_best, cand, best_idx,
-                 lanes_of(p, kQuadMaxSamples), false, a);
+                 lanes_of(p, kQuadMaxSamples), false, true, a);
 
   cudaError_t e;
   aero_planner::ProfSlot* prof = prof_slot(pl, p.iters);
@@ -720,6 +727,7 @@ int aero_create(const aero_limits_t* limits, aero_planner_t** out) {
   chk(alloc(&pl->tile_sum, kMaxTiles));
   chk(alloc(&pl->tile_off, kMaxTiles + 1));
   chk(alloc(&pl->cand, cap));
+  chk(alloc(&pl->cand_pts, std::max<int64_t>(L.fine_cells_max, L.n_points_max)));
   chk(alloc(&pl->grid_range, kGridCellsMax));
   chk(alloc(&pl->partials, (size_t)L.E_max * nbmax * (4 + 4 * L.T_max)));
   chk(alloc(&pl->sample_costs, (size_t)L.E_max * L.K_max));
@@ -885,9 +893,22 @@ int aero_get_debug(aero_planner_t* pl, int32_t what, void* dst, size_t bytes, vo
       return cuda_fail(cudaMemcpy(dst, meta, 32, cudaMemcpyDefault));
     }
     if (what == AERO_DBG_GRID_POINTS) {
-      const size_t need = sizeof(float4) * (size_t)(n_entries < g.cap ? n_entries : g.cap);
+      // the entries' points, gathered on the host
+      const size_t ne = (size_t)(n_entries < g.cap ? n_entries : g.cap);
+      const size_t need = sizeof(float4) * ne;
       if (bytes < need) return AERO_ERR_INVALID_ARG;
-      return cuda_fail(cudaMemcpy(dst, pl->cand, need, cudaMemcpyDefault));
+      if (!pl->last_idx_entries) return cuda_fail(cudaMemcpy(dst, pl->cand, need, cudaMemcpyDefault));
+      const size_t n_items = (size_t)std::max<int64_t>(pl->lim.fine_cells_max, pl->lim.n_points_max);
+      std::vector<uint32_t> idx(ne);
+      std::vector<float4> pts(n_items), out(ne);
+      e = cudaMemcpy(idx.data(), pl->cand, 4 * ne, cudaMemcpyDeviceToHost);
+      if (e == cudaSuccess) e = cudaMemcpy(pts.data(), pl->cand_pts, sizeof(float4) * n_items, cudaMemcpyDeviceToHost);
+      if (e != cudaSuccess) return cuda_fail(e);
+      for (size_t i = 0; i < ne; ++i) {
+        if (idx[i] >= n_items) return AERO_ERR_DEVICE_CHECK;
+        out[i] = pts[idx[i]];
+      }
+      return cuda_fail(cudaMemcpy(dst, out.data(), need, cudaMemcpyDefault));
     }
     const size_t need = sizeof(int32_t) * ((size_t)gcells + 1);
     if (bytes < need) return AERO_ERR_INVALID_ARG;
@@ -1025,7 +1046,7 @@ const char* aero_status_str(int status) {
 // so such callers use aero_plan_step_noalloc instead: its workspace is carved
 // from g_noalloc_scratch, a file-scope device array that the CUDA loader sets
 // up with the module and that every GPU loading this library keeps until the
-// process exits.  Its size is fixed by the kNa* limits below (about 6.5 MB).
+// process exits.  Its size is fixed by the kNa* limits below (about 7.5 MB).
 // ---------------------------------------------------------------------------
 namespace {
 
@@ -1042,6 +1063,7 @@ constexpr size_t kNaBytes =
     align256(4 * 3 * kNaE) + align256(4 * 3 * (size_t)kNaE * kNaT) + align256(4 * (size_t)kNaPoints) +
     3 * align256(4 * ((size_t)kNaGridCells + 1)) + align256(4 * (size_t)kNaTiles) +
     align256(4 * ((size_t)kNaTiles + 1)) + align256(16 * (size_t)kNaCand) +
+    align256(16 * (size_t)std::max<int64_t>(kNaCells, kNaPoints)) +
     align256(8 * (size_t)kNaGridCells) +
     align256(4 * (size_t)kNaE * kNaNb * (4 + 4 * kNaT)) + align256(4 * (size_t)kNaE * kNaK) +
     align256(4 * (size_t)kNaE * (kNaT + 1) * 10) + align256(4 * kCounterWords) +
@@ -1096,6 +1118,7 @@ void noalloc_carve(unsigned char* base, aero_planner& pl) {
   pl.tile_sum = reinterpret_cast<int*>(take(4 * (size_t)kNaTiles));
   pl.tile_off = reinterpret_cast<int*>(take(4 * ((size_t)kNaTiles + 1)));
   pl.cand = reinterpret_cast<float4*>(take(16 * (size_t)kNaCand));
+  pl.cand_pts = reinterpret_cast<float4*>(take(16 * (size_t)std::max<int64_t>(kNaCells, kNaPoints)));
   pl.grid_range = reinterpret_cast<int2*>(take(8 * (size_t)kNaGridCells));
   pl.cand_cap = kNaCand;
   pl.grid_max = kNaGrid;
@@ -1365,7 +1388,7 @@ int batch_enqueue(aero_batch* b, const aero_batch_item_t* items, int n, cudaStre
     }
     StepArgs a;
     make_step_args(pl, &it.x0, it.cloud_xyz, it.n_points, it.goal, p, u_nom, u_best, cand, best,
-                   lanes_of(p, cfg.quad_max_samples), cfg.coarse_cells != 0, a);
+                   lanes_of(p, cfg.quad_max_samples), cfg.coarse_cells != 0, false, a);
     BatchItem& bi = hi[i];
     bi.pa = a.pa;
     bi.ca = a.ca;
@@ -1458,6 +1481,7 @@ int batch_enqueue(aero_batch* b, const aero_batch_item_t* items, int n, cudaStre
     pl->have_step = true;
     pl->last = items[i].params;
     pl->last_grid = meta[i].grid;
+    pl->last_idx_entries = false;
     pl->last_ntiles = meta[i].ntiles;
     pl->last_part_slots = (int)((items[i].n_points + kPartChunk - 1) / kPartChunk);
     pl->last_n_points = items[i].n_points;

@@ -172,17 +172,44 @@ __device__ __forceinline__ float dist2_to(const float4 q, float px, float py, fl
   return ax * ax + ay * ay + az * az;
 }
 
-// min(best, squared distances to the n entries at P), kW entries per round
-// so that kW loads are in flight; the last round repeats its first entry in
-// place of the missing ones (the minimum is exact in any order).
+// The collision point of candidate entry e of the grid (either form).
+__device__ __forceinline__ float4 grid_point(const GridView& g, int e) {
+  return g.cand ? __ldg(g.pts + __ldg(g.cand + e)) : __ldg(g.pts + e);
+}
+
+// The same for a grid whose entry form is known at compile time (kIdx: item
+// indices), for the per-entry loop of the one-thread pass.
+template <bool kIdx>
+__device__ __forceinline__ float4 grid_point_of(const GridView& g, int e) {
+  if constexpr (kIdx)
+    return __ldg(g.pts + __ldg(g.cand + e));
+  else
+    return __ldg(g.pts + e);
+}
+
+// min(best, squared distances to the points of the n candidate entries from
+// `first`), kW entries per round so that kW loads are in flight; the last
+// round repeats its first entry in place of the missing ones (the minimum is
+// exact in any order).
 template <int kW = 4>
-__device__ __forceinline__ float scan_min(const float4* P, int n, float px, float py, float pz,
-                                          float best) {
+__device__ __forceinline__ float scan_min(const GridView& g, int first, int n, float px, float py,
+                                          float pz, float best) {
+  const uint32_t* E = g.cand ? g.cand + first : nullptr;
+  const float4* P = g.cand ? g.pts : g.pts + first;
   for (int t = 0; t < n; t += kW) {
     float4 c[kW];
-    c[0] = __ldg(P + t);
+    if (E) {
+      uint32_t id[kW];
+      id[0] = __ldg(E + t);
 #pragma unroll
-    for (int i = 1; i < kW; ++i) c[i] = t + i < n ? __ldg(P + t + i) : c[0];
+      for (int i = 1; i < kW; ++i) id[i] = t + i < n ? __ldg(E + t + i) : id[0];
+#pragma unroll
+      for (int i = 0; i < kW; ++i) c[i] = __ldg(P + id[i]);
+    } else {
+      c[0] = __ldg(P + t);
+#pragma unroll
+      for (int i = 1; i < kW; ++i) c[i] = t + i < n ? __ldg(P + t + i) : c[0];
+    }
     float m = dist2_to(c[0], px, py, pz);
 #pragma unroll
     for (int i = 1; i < kW; ++i) m = fminf(m, dist2_to(c[i], px, py, pz));

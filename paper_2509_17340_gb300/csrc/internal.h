@@ -73,7 +73,12 @@ struct CandArgs {
   int* fill;           // G^3 + 1: fill cursors of the scatter pass; zeroed by the scan
   const int* local;    // tile-local exclusive prefix of the counts (scatter pass)
   const int* tile_off; // exclusive prefix of the tile totals (scatter pass)
-  float4* cand;        // candidate entries (scatter pass)
+  // candidate entries (scatter pass), in one of two forms: item indices into
+  // pts, whose points the count pass stores (cand non-null), or the points
+  // themselves (cand4)
+  uint32_t* cand;
+  float4* pts;         // n_items: collision point of each item, minus p0
+  float4* cand4;
   int* status;
   unsigned long long* reset_keys;  // non-null: the scatter pass empties each key it reads
 };
@@ -100,8 +105,9 @@ struct GuideArgs {
 };
 
 struct GridView {
-  const int2* range;   // G^3 cell ranges into pts
-  const float4* pts;   // candidate entries, grouped by cell
+  const int2* range;     // G^3 cell ranges into the candidate entries
+  const uint32_t* cand;  // entries as item indices into pts, grouped by cell; or null:
+  const float4* pts;     // the items' collision points (minus p0), or (cand null) the entries' own
   int G;
   float origin, inv_h;
 };

@@ -147,10 +147,13 @@ __global__ void __launch_bounds__(256) k_partition(PartitionArgs a, const PartTa
 }
 
 // ---------------------------------------------------------------------------
-// K2a / K2d: candidate lists.  For every collision point p, every cell whose
-// box is closer to p than `reach` gets p: the count pass adds to the cell's
-// counter, the scatter pass writes p at start(cell) + its fill ticket.  Order
-// within a cell depends on the atomics, but only the minimum distance is used.
+// K2a / K2d: candidate lists.  For every collision point p (item i), every
+// cell whose box is closer to p than `reach` gets p: the count pass adds to
+// the cell's counter, the scatter pass writes the entry at start(cell) + its
+// fill ticket.  An entry is either i (4 bytes; the count pass stores p at
+// pts[i], and the points, far fewer than the entries, stay in L1) or p itself
+// (16 bytes, one load fewer per entry read).  Order within a cell depends on
+// the atomics, but only the minimum distance is used.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ bool cand_item(const CandArgs& a, int64_t it, float& px, float& py,
                                           float& pz) {
@@ -187,6 +190,7 @@ __device__ __forceinline__ void cand_task(const CandArgs& a, int64_t it, int lan
     __syncwarp();
     if (lane == 0) a.reset_keys[it] = kEmpty;
   }
+  if (!kScatter && a.cand && lane == 0) a.pts[it] = make_float4(px, py, pz, 0.0f);
   const int x0 = max(__float2int_rd((px - g.reach - g.origin) * g.inv_h), 0);
   const int x1 = min(__float2int_rd((px + g.reach - g.origin) * g.inv_h), g.G - 1);
   const int y0 = max(__float2int_rd((py - g.reach - g.origin) * g.inv_h), 0);
@@ -207,9 +211,12 @@ __device__ __forceinline__ void cand_task(const CandArgs& a, int64_t it, int lan
       atomicAdd(a.count + c, 1);
     } else {
       const int pos = a.local[c] + a.tile_off[c >> kScanTileShift] + atomicAdd(a.fill + c, 1);
-      if (pos < g.cap)
-        a.cand[pos] = make_float4(px, py, pz, 0.0f);
-      else
+      if (pos < g.cap) {
+        if (a.cand)
+          a.cand[pos] = (uint32_t)it;
+        else
+          a.cand4[pos] = make_float4(px, py, pz, 0.0f);
+      } else
         atomicOr(a.status, 2);
     }
   }

@@ -35,7 +35,9 @@ struct CostSum {
 };
 
 // Samples [b * NT, (b + 1) * NT) of instance e; ctr3: the noise counter's
-// last word, (step_id << 8) | iteration.
+// last word, (step_id << 8) | iteration.  kIdx: the grid's candidate entries
+// are item indices (a single planner's step), else points (batched steps).
+template <bool kIdx>
 __device__ __forceinline__ void rollout_unit(const RolloutArgs& a, int e, int b, uint32_t ctr3) {
   __shared__ float4 s_un[kMaxT];
   __shared__ float s_gd[kMaxT * 3];
@@ -117,7 +119,7 @@ __device__ __forceinline__ void rollout_unit(const RolloutArgs& a, int e, int b,
     }
     float d2 = dmax2;
     for (int i = 0; i < range_j.y; ++i)
-      d2 = fminf(d2, dist2_to(__ldg(a.grid.pts + range_j.x + i), x.p[0], x.p[1], x.p[2]));
+      d2 = fminf(d2, dist2_to(grid_point_of<kIdx>(a.grid, range_j.x + i), x.p[0], x.p[1], x.p[2]));
     // state terms at x_j against the guide at t = j dt
     const float gx = s_gd[3 * (j - 1)], gy = s_gd[3 * (j - 1) + 1], gz = s_gd[3 * (j - 1) + 2];
     float c = c_ctrl;
@@ -391,7 +393,7 @@ __device__ __forceinline__ void rollout_split_unit(const RolloutArgs& a, int e, 
       const int n = r.y - first < kItem ? r.y - first : kItem;
       if (!AERO_CHECK(slot < kChunkQ && first >= 0 && n > 0 && r.x >= 0, kChkQuery)) continue;
       const float4 p = xa[slot];
-      const float d2 = scan_min<kItem>(a.grid.pts + r.x + first, n, p.x, p.y, p.z, dmax2);
+      const float d2 = scan_min<kItem>(a.grid, r.x + first, n, p.x, p.y, p.z, dmax2);
       if (d2 < dmax2) atomicMin(m.d2 + slot, __float_as_int(d2));  // non-negative: int order
     }
     warps_sync<SWK, kWorkBar>();  // minima complete
@@ -678,7 +680,7 @@ __device__ __forceinline__ void update_unit(const UpdateArgs& a, int e, bool fin
     const int n = r.y - first < kItem ? r.y - first : kItem;
     if (!AERO_CHECK(j < T && first >= 0 && n > 0 && r.x >= 0, kChkQuery)) continue;
     const float* X = s_x + (j + 1) * 10;
-    const float d2 = scan_min<kItem>(a.grid.pts + r.x + first, n, X[0], X[1], X[2], dmax2);
+    const float d2 = scan_min<kItem>(a.grid, r.x + first, n, X[0], X[1], X[2], dmax2);
     if (d2 < dmax2) atomicMin(s_d2 + j, __float_as_int(d2));  // non-negative: int order
   }
   __syncthreads();
@@ -732,9 +734,9 @@ __device__ __forceinline__ void update_unit(const UpdateArgs& a, int e, bool fin
   for (int i = tid; i < 4 * T; i += UT) a.u_best[i] = __ldcg(ub + i);
 }
 
-__global__ void __launch_bounds__(NT) k_rollout(RolloutArgs a) {
+__global__ void __launch_bounds__(NT, 6) k_rollout(RolloutArgs a) {
   pdl_start();
-  rollout_unit(a, blockIdx.y, blockIdx.x, a.ctr3);
+  rollout_unit<true>(a, blockIdx.y, blockIdx.x, a.ctr3);
 }
 
 // The split pass with the update of every instance run by the last of its
@@ -815,7 +817,7 @@ __global__ void __launch_bounds__(kLanes == 4 ? ST : NT, kMinCtas)
       const long long l = u - s_pre[pos];
       const int e = (int)(l / s_a.nb), b = (int)(l % s_a.nb);
       if constexpr (kLanes == 1)
-        rollout_unit(s_a, e, b, s_a.ctr3 | (uint32_t)it);
+        rollout_unit<false>(s_a, e, b, s_a.ctr3 | (uint32_t)it);
       else
         rollout_split_unit(s_a, e, b, s_a.ctr3 | (uint32_t)it);
     }
