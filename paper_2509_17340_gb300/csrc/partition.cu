@@ -179,7 +179,9 @@ __device__ __forceinline__ float gap2(float v, float lo, float h) {
 }
 
 // One warp per collision item; its lanes share the item's block of cells.
-template <bool kScatter>
+// kIdx: the entries are item indices (a single planner's step), else points
+// (batched steps); the form is fixed per launch, so it is a template argument.
+template <bool kScatter, bool kIdx>
 __device__ __forceinline__ void cand_task(const CandArgs& a, int64_t it, int lane) {
   const GridGeom& g = a.grid;
   const float r2 = g.reach * g.reach;
@@ -190,7 +192,9 @@ __device__ __forceinline__ void cand_task(const CandArgs& a, int64_t it, int lan
     __syncwarp();
     if (lane == 0) a.reset_keys[it] = kEmpty;
   }
-  if (!kScatter && a.cand && lane == 0) a.pts[it] = make_float4(px, py, pz, 0.0f);
+  if constexpr (!kScatter && kIdx) {
+    if (lane == 0) a.pts[it] = make_float4(px, py, pz, 0.0f);
+  }
   const int x0 = max(__float2int_rd((px - g.reach - g.origin) * g.inv_h), 0);
   const int x1 = min(__float2int_rd((px + g.reach - g.origin) * g.inv_h), g.G - 1);
   const int y0 = max(__float2int_rd((py - g.reach - g.origin) * g.inv_h), 0);
@@ -212,7 +216,7 @@ __device__ __forceinline__ void cand_task(const CandArgs& a, int64_t it, int lan
     } else {
       const int pos = a.local[c] + a.tile_off[c >> kScanTileShift] + atomicAdd(a.fill + c, 1);
       if (pos < g.cap) {
-        if (a.cand)
+        if constexpr (kIdx)
           a.cand[pos] = (uint32_t)it;
         else
           a.cand4[pos] = make_float4(px, py, pz, 0.0f);
@@ -228,7 +232,7 @@ __device__ void cand_pass(const CandArgs& a, int block, int nblocks) {
   const int lane = threadIdx.x & 31;
   const int64_t warps = (int64_t)nblocks * (blockDim.x >> 5);
   for (int64_t it = ((int64_t)block * blockDim.x + threadIdx.x) >> 5; it < a.n_items; it += warps)
-    cand_task<kScatter>(a, it, lane);
+    cand_task<kScatter, true>(a, it, lane);
 }
 
 // ---------------------------------------------------------------------------
@@ -605,7 +609,7 @@ __device__ __forceinline__ void cand_tasks(const BatchView& v, const long long* 
         while (t >= s_pi[it + 1]) ++it;
         a = v.items[it].ca;
       }
-      cand_task<kScatter>(a, t - s_pi[it], lane);
+      cand_task<kScatter, false>(a, t - s_pi[it], lane);
     }
   }
 }
