@@ -302,62 +302,62 @@ __device__ float warp_cost_grad(const float4* u, float4* g, const float* guide, 
     }
   }
   S += warp_sum(jc);
-  if (!kGrad) return S;
-
-  float lam[10];
+  if constexpr (kGrad) {
+    float lam[10];
 #pragma unroll
-  for (int i = 0; i < 10; ++i) lam[i] = 0.0f;
-  for (int s = nseg - 1; s >= 0; --s) {
-    const int j0 = s * kCkpt, n = min(T, j0 + kCkpt) - j0;
-    // recompute the segment's states from its checkpoint
-    State y = state_load(sc.ck + s * 10);
-    if (lane == 0) state_store(sc.seg, y);
-    for (int k = 0; k < n; ++k) {
-      rk4_step(y, u[j0 + k], dp);
-      if (lane == 0) state_store(sc.seg + (k + 1) * 10, y);
+    for (int i = 0; i < 10; ++i) lam[i] = 0.0f;
+    for (int s = nseg - 1; s >= 0; --s) {
+      const int j0 = s * kCkpt, n = min(T, j0 + kCkpt) - j0;
+      // recompute the segment's states from its checkpoint
+      State y = state_load(sc.ck + s * 10);
+      if (lane == 0) state_store(sc.seg, y);
+      for (int k = 0; k < n; ++k) {
+        rk4_step(y, u[j0 + k], dp);
+        if (lane == 0) state_store(sc.seg + (k + 1) * 10, y);
+      }
+      __syncwarp();
+      warp_nn_segment(sc, n, grid, dmax2, lane);
+      __syncwarp();
+      if (lane < n) {
+        const int j = j0 + lane;
+        float gs[10];
+        state_terms<true>(state_load(sc.seg + (lane + 1) * 10), guide[3 * j], guide[3 * j + 1],
+                          guide[3 * j + 2], sc.d2[lane], sc.nearest[lane], cp, dmax2, gs);
+#pragma unroll
+        for (int i = 0; i < 10; ++i) sc.gs[lane][i] = gs[i];
+      }
+      __syncwarp();
+      for (int k = n - 1; k >= 0; --k) {
+#pragma unroll
+        for (int i = 0; i < 10; ++i) lam[i] += sc.gs[k][i];
+        float gu[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+        rk4_vjp(sc.seg + k * 10, u[j0 + k], dp, lam, gu);
+        if (lane == 0) g[j0 + k] = make_float4(gu[0], gu[1], gu[2], gu[3]);
+      }
+      __syncwarp();
     }
-    __syncwarp();
-    warp_nn_segment(sc, n, grid, dmax2, lane);
-    __syncwarp();
-    if (lane < n) {
-      const int j = j0 + lane;
-      float gs[10];
-      state_terms<true>(state_load(sc.seg + (lane + 1) * 10), guide[3 * j], guide[3 * j + 1],
-                        guide[3 * j + 2], sc.d2[lane], sc.nearest[lane], cp, dmax2, gs);
-#pragma unroll
-      for (int i = 0; i < 10; ++i) sc.gs[lane][i] = gs[i];
-    }
-    __syncwarp();
-    for (int k = n - 1; k >= 0; --k) {
-#pragma unroll
-      for (int i = 0; i < 10; ++i) lam[i] += sc.gs[k][i];
-      float gu[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-      rk4_vjp(sc.seg + k * 10, u[j0 + k], dp, lam, gu);
-      if (lane == 0) g[j0 + k] = make_float4(gu[0], gu[1], gu[2], gu[3]);
+    // control terms
+    for (int t = lane; t < T; t += 32) {
+      float4 a = g[t];
+      const float4 ut = u[t];
+      if (t <= T - 2) {
+        a.x += 2.0f * cp.Q_c * ut.x; a.y += 2.0f * cp.Q_c * ut.y;
+        a.z += 2.0f * cp.Q_c * ut.z; a.w += 2.0f * cp.Q_c * ut.w;
+      }
+      if (t >= 1 && t <= T - 2) {
+        const float4 b = u[t - 1];
+        a.x += 2.0f * cp.Q_cd * (ut.x - b.x); a.y += 2.0f * cp.Q_cd * (ut.y - b.y);
+        a.z += 2.0f * cp.Q_cd * (ut.z - b.z); a.w += 2.0f * cp.Q_cd * (ut.w - b.w);
+      }
+      if (t + 1 >= 1 && t + 1 <= T - 2) {
+        const float4 c = u[t + 1];
+        a.x -= 2.0f * cp.Q_cd * (c.x - ut.x); a.y -= 2.0f * cp.Q_cd * (c.y - ut.y);
+        a.z -= 2.0f * cp.Q_cd * (c.z - ut.z); a.w -= 2.0f * cp.Q_cd * (c.w - ut.w);
+      }
+      g[t] = a;
     }
     __syncwarp();
   }
-  // control terms
-  for (int t = lane; t < T; t += 32) {
-    float4 a = g[t];
-    const float4 ut = u[t];
-    if (t <= T - 2) {
-      a.x += 2.0f * cp.Q_c * ut.x; a.y += 2.0f * cp.Q_c * ut.y;
-      a.z += 2.0f * cp.Q_c * ut.z; a.w += 2.0f * cp.Q_c * ut.w;
-    }
-    if (t >= 1 && t <= T - 2) {
-      const float4 b = u[t - 1];
-      a.x += 2.0f * cp.Q_cd * (ut.x - b.x); a.y += 2.0f * cp.Q_cd * (ut.y - b.y);
-      a.z += 2.0f * cp.Q_cd * (ut.z - b.z); a.w += 2.0f * cp.Q_cd * (ut.w - b.w);
-    }
-    if (t + 1 >= 1 && t + 1 <= T - 2) {
-      const float4 c = u[t + 1];
-      a.x -= 2.0f * cp.Q_cd * (c.x - ut.x); a.y -= 2.0f * cp.Q_cd * (c.y - ut.y);
-      a.z -= 2.0f * cp.Q_cd * (c.z - ut.z); a.w -= 2.0f * cp.Q_cd * (c.w - ut.w);
-    }
-    g[t] = a;
-  }
-  __syncwarp();
   return S;
 }
 
