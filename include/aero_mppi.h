@@ -103,7 +103,11 @@ typedef struct {
   int32_t fine_cells_max;   /* fine_az * fine_el, <= 512 * 256 */
   int64_t n_points_max;     /* cloud size, <= 2^31 - 1 */
   int32_t debug_samples_max; /* D: samples per instance whose rollouts can be recorded */
-  int32_t reserved_;
+  int32_t raw_points_max;   /* cloud size up to which the every-point collision set
+                               (collision_set = 1) can be used: 0 = n_points_max, -1 = never
+                               (its per-point arrays are then not allocated); otherwise
+                               1 .. n_points_max.  A step with collision_set = 1 and more
+                               points returns AERO_ERR_EXCEEDS_LIMITS */
 } aero_limits_t;
 
 /* Parameters of one planning step; aero_params_default() fills Table I. */
@@ -214,7 +218,11 @@ int aero_plan_step_host(aero_planner_t* planner, const aero_state_t* x0, const f
  *   there are no debug buffers.
  *   The first call on a device looks up the array's device address (once per
  *   device, with that device current); make that first call before any stream
- *   capture.  All calls share the array, which keeps the last call's contents:
+ *   capture: a first call on a stream that is being captured returns
+ *   AERO_ERR_INVALID_ARG.  The partition's edge tables are copied into the
+ *   array from a host copy that the library keeps per device, only when the
+ *   partition geometry (fine_az, fine_el, el_lo, el_hi) differs from the last
+ *   call's.  All calls share the array, which keeps the last call's contents:
  *   calls whose work overlaps on the GPU (other streams, other host threads)
  *   race on it, so order them on one stream. */
 int aero_plan_step_noalloc(const aero_state_t* x0, const float* cloud_xyz, int64_t n_points,

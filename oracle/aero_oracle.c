@@ -784,6 +784,21 @@ void orc_mppi_update(const double* S, const double* dU, int K, int T, double lam
  * One planning step
  * ====================================================================== */
 
+/* Threads of the per-sample loop of orc_plan_step (OpenMP builds; 1 = serial).
+ * Returns the count in use, which stays 1 when the library was built without
+ * OpenMP. */
+static int g_threads = 1;
+
+int orc_set_threads(int n) {
+#ifdef _OPENMP
+  g_threads = n > 0 ? n : 1;
+#else
+  (void)n;
+  g_threads = 1;
+#endif
+  return g_threads;
+}
+
 /* Collision set: P_f (the winning point of every non-empty cone, Sec. IV-C) or
  * every point kept by the partition.  Returns its size; pts gets 3 per point. */
 int64_t orc_collision_set(const float* cloud, int64_t n, const float p0[3], const float q0[4],
@@ -859,27 +874,42 @@ int orc_plan_step(const float* cloud, int64_t n, const float p0f[3], const float
   double* dU = malloc(sizeof(double) * (int64_t)K * T * 4);
   double* S = malloc(sizeof(double) * K);
   double* X = malloc(sizeof(double) * (T + 1) * 10);
-  double* Uk = malloc(sizeof(double) * T * 4);
   for (int it = 0; it < P->iters; ++it)
     for (int e = 0; e < E; ++e) {
       double* un = u_nom + (int64_t)e * T * 4;
-      for (int k = 0; k < K; ++k) {
-        for (int j = 0; j < T; ++j) {
-          double delta[4];
-          orc_noise(P, e, k, j, it, delta);
-          for (int c = 0; c < 4; ++c) {
-            double u = un[4 * j + c] + delta[c];
-            if (u < P->u_min[c]) u = P->u_min[c];
-            if (u > P->u_max[c]) u = P->u_max[c];
-            Uk[4 * j + c] = u;
-            dU[(int64_t)k * T * 4 + 4 * j + c] = u - un[4 * j + c];
+      /* the samples are independent: with OpenMP (orc_set_threads) they are
+       * shared among threads; each writes only its own S[k] and dU row, and
+       * the update below runs serially in sample order, so the result does
+       * not depend on the thread count */
+#ifdef _OPENMP
+#pragma omp parallel num_threads(g_threads)
+#endif
+      {
+        double* Uk = malloc(sizeof(double) * T * 4);
+        double* Xk = malloc(sizeof(double) * (T + 1) * 10);
+#ifdef _OPENMP
+#pragma omp for schedule(dynamic, 4)
+#endif
+        for (int k = 0; k < K; ++k) {
+          for (int j = 0; j < T; ++j) {
+            double delta[4];
+            orc_noise(P, e, k, j, it, delta);
+            for (int c = 0; c < 4; ++c) {
+              double u = un[4 * j + c] + delta[c];
+              if (u < P->u_min[c]) u = P->u_min[c];
+              if (u > P->u_max[c]) u = P->u_max[c];
+              Uk[4 * j + c] = u;
+              dU[(int64_t)k * T * 4 + 4 * j + c] = u - un[4 * j + c];
+            }
           }
+          orc_rollout(x0, Uk, T, P->dt, P->mass, P->g, Xk);
+          double terms[6];
+          orc_cost_terms(Xk, Uk, guides + (int64_t)e * T * 3, goal, pts, npts, P, 1, terms, NULL);
+          S[k] = terms[5];
+          if (S1_out) S1_out[(int64_t)e * K + k] = S[k];
         }
-        orc_rollout(x0, Uk, T, P->dt, P->mass, P->g, X);
-        double terms[6];
-        orc_cost_terms(X, Uk, guides + (int64_t)e * T * 3, goal, pts, npts, P, 1, terms, NULL);
-        S[k] = terms[5];
-        if (S1_out) S1_out[(int64_t)e * K + k] = S[k];
+        free(Uk);
+        free(Xk);
       }
       orc_mppi_update(S, dU, K, T, P->lam, un, NULL);
     }
@@ -904,6 +934,6 @@ int orc_plan_step(const float* cloud, int64_t n, const float p0f[3], const float
   if (keys_out) memcpy(keys_out, keys, sizeof(uint64_t) * ncell);
 
   free(keys); free(win); free(rwin); free(acell); free(guides); free(pts);
-  free(dU); free(S); free(X); free(Uk);
+  free(dU); free(S); free(X);
   return 0;
 }

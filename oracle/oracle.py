@@ -25,13 +25,23 @@ _lib = None
 
 
 def build(force: bool = False) -> str:
-    """Compile the oracle into ``oracle/liborc.so`` (gcc, plain C11)."""
+    """Compile the oracle into ``oracle/liborc.so`` (gcc, plain C11; with OpenMP
+    for the per-sample loop of a planning step when gcc offers it, else serial)."""
     if force or not os.path.exists(LIB) or os.path.getmtime(LIB) < os.path.getmtime(SRC):
         tmp = LIB + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-std=c11", "-O2", "-fPIC", "-shared", "-ffp-contract=off",
-                               "-fno-fast-math", "-o", tmp, SRC, "-lm"])
+        base = ["gcc", "-std=c11", "-O2", "-fPIC", "-shared", "-ffp-contract=off", "-fno-fast-math",
+                "-o", tmp, SRC, "-lm"]
+        r = subprocess.run(base[:1] + ["-fopenmp"] + base[1:], capture_output=True, text=True)
+        if r.returncode != 0:
+            subprocess.check_call(base)
         os.replace(tmp, LIB)
     return LIB
+
+
+def set_threads(n: int) -> int:
+    """Threads of the per-sample loop of ``plan_step`` (results do not depend on
+    it); returns the count in use (1 when built without OpenMP)."""
+    return int(lib().orc_set_threads(C.c_int(int(n))))
 
 
 class Params(C.Structure):

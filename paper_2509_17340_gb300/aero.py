@@ -47,7 +47,7 @@ class State(C.Structure):
 class Limits(C.Structure):
     _fields_ = [("E_max", C.c_int32), ("K_max", C.c_int32), ("T_max", C.c_int32),
                 ("fine_cells_max", C.c_int32), ("n_points_max", C.c_int64),
-                ("debug_samples_max", C.c_int32), ("reserved_", C.c_int32)]
+                ("debug_samples_max", C.c_int32), ("raw_points_max", C.c_int32)]
 
 
 class Params(C.Structure):
@@ -233,11 +233,12 @@ class Planner:
     """Owns an ``aero_planner_t`` (device workspace sized by the limits)."""
 
     def __init__(self, E_max=64, K_max=8192, T_max=64, fine_cells_max=512 * 64,
-                 n_points_max=1 << 18, debug_samples_max=0, device=None):
+                 n_points_max=1 << 18, debug_samples_max=0, device=None, raw_points_max=0):
         if device is not None:
             torch.cuda.set_device(device)
         torch.cuda.init()
-        lim = Limits(E_max, K_max, T_max, fine_cells_max, n_points_max, debug_samples_max, 0)
+        lim = Limits(E_max, K_max, T_max, fine_cells_max, n_points_max, debug_samples_max,
+                     raw_points_max)
         h = _vp()
         _check(_lib.aero_create(C.byref(lim), C.byref(h)), "aero_create")
         self._h = h

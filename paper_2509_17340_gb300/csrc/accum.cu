@@ -143,7 +143,8 @@ __global__ void __launch_bounds__(kThreads) k_shift(float* __restrict__ u, const
 int blocks_for(int64_t n) {
   int64_t b = (n + kThreads - 1) / kThreads;
   if (b < 1) b = 1;
-  return (int)(b < 152 * 16 ? b : 152 * 16);
+  const int cap = 16 * aero::device_sms();
+  return (int)(b < cap ? b : cap);
 }
 
 int fail(cudaError_t e) { return e == cudaSuccess ? AERO_OK : AERO_ERR_CUDA; }

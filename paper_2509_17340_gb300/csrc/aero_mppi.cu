@@ -79,6 +79,26 @@ cudaError_t read_check_words(int* out, bool clear) {
 #endif
 }
 
+int device_sms() {
+  static std::atomic<int> cache[64];
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    return 1;
+  }
+  if (dev >= 0 && dev < 64) {
+    const int v = cache[dev].load();
+    if (v > 0) return v;
+  }
+  int n = 0;
+  if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n < 1) {
+    cudaGetLastError();
+    return 1;
+  }
+  if (dev >= 0 && dev < 64) cache[dev].store(n);
+  return n;
+}
+
 void dev_free(void* p) {
   if (!p) return;
   cudaFree(p);
@@ -119,7 +139,6 @@ struct aero_planner {
   int grid_cells_cap = kGridMax * kGridMax * kGridMax;
   float* partials = nullptr;
   float* sample_costs = nullptr;
-  float4* dU = nullptr;       // sampled perturbations, when the planner is small enough
   float* stage2_x = nullptr;
   unsigned int* counter = nullptr;
   int* status = nullptr;
@@ -152,6 +171,7 @@ struct aero_planner {
   PartTables* d_tab = nullptr;  // device copy, read by the partition and the guides
   bool tab_upload = true;       // d_tab behind tab
   int64_t last_n_points = 0;
+  int64_t raw_max = 0;          // cloud size up to which the every-point set fits
   // stage timing (aero_profile_enable / aero_profile_read)
   struct ProfSlot {
     // start/end of: partition, grid, then rollout and update of every iteration
@@ -173,7 +193,6 @@ namespace {
 // A point joins the lists of the cells within `reach` (just above d_max) of it:
 // at most 6^3 cells of edge d_max / 2, at most 3^3 of edge d_max (1 + 1/16).
 constexpr int kFineDup = 216, kCoarseDup = 27;
-constexpr size_t kMaxStoredPerturbationBytes = size_t(2) << 30;
 
 int cuda_fail(cudaError_t e) {
   if (e == cudaSuccess) return AERO_OK;
@@ -273,7 +292,7 @@ int validate(const aero_planner* pl, const aero_params_t* p, int64_t n_points) {
     return AERO_ERR_INVALID_ARG;
   if (p->E > L.E_max || p->K > L.K_max || p->T > L.T_max ||
       (int64_t)p->fine_az * p->fine_el > L.fine_cells_max || n_points > L.n_points_max ||
-      p->debug_samples > L.debug_samples_max)
+      p->debug_samples > L.debug_samples_max || (p->collision_set == 1 && n_points > pl->raw_max))
     return AERO_ERR_EXCEEDS_LIMITS;
   return AERO_OK;
 }
@@ -288,7 +307,7 @@ void free_all(aero_planner* pl) {
                   pl->item_flag, pl->grid_count, pl->grid_fill, pl->grid_local, pl->tile_sum,
                   pl->tile_off,
                   pl->cand,     pl->cand_pts,   pl->grid_range, pl->partials,
-                  pl->sample_costs, pl->dU,      pl->stage2_x, pl->counter,   pl->status,   pl->dbg_u,
+                  pl->sample_costs, pl->stage2_x, pl->counter,   pl->status,   pl->dbg_u,
                   pl->dbg_x,    pl->dbg_d,      pl->stage_cloud,      pl->stage_out,
                   pl->dbg_pre,      pl->part_counts,  pl->d_tab};
   for (void* q : ptrs) dev_free(q);
@@ -506,9 +525,6 @@ void make_step_args(aero_planner* pl, const aero_state_t* x0, const float* cloud
   ra.grid = gv;
   ra.partials = pl->partials;
   ra.sample_costs = pl->sample_costs;
-  // the sampled perturbations are stored when the workspace holds them, else
-  // the weighted sums regenerate them
-  ra.dU = pl->dU;
   ra.dbg_D = p.debug_samples < p.K ? p.debug_samples : p.K;
   ra.dbg_u = pl->dbg_u;
   ra.dbg_x = pl->dbg_x;
@@ -697,16 +713,17 @@ int aero_create(const aero_limits_t* limits, aero_planner_t** out) {
   if (L.E_max < 1 || L.E_max > kMaxE || L.K_max < 1 || L.K_max > (1 << 20) || L.T_max < 1 ||
       L.T_max > kMaxT || L.fine_cells_max < 2 || L.fine_cells_max > kMaxAz * kMaxEl ||
       L.n_points_max < 0 || L.n_points_max > 0x7FFFFFFFLL || L.debug_samples_max < 0 ||
-      L.debug_samples_max > L.K_max)
+      L.debug_samples_max > L.K_max || L.raw_points_max < -1 || L.raw_points_max > L.n_points_max)
     return AERO_ERR_INVALID_ARG;
   aero_planner* pl = new (std::nothrow) aero_planner();
   if (!pl) return AERO_ERR_ALLOC;
   pl->lim = L;
+  pl->raw_max = L.raw_points_max == 0 ? L.n_points_max : (L.raw_points_max < 0 ? 0 : L.raw_points_max);
   cudaGetDevice(&pl->device);
   // partial rows: one per rollout CTA, whose smallest sample count is 128 / 4
   const int64_t nbmax = (L.K_max + kRolloutThreads / 4 - 1) / (kRolloutThreads / 4);
   const int64_t cap_fine = (int64_t)kFineDup * L.fine_cells_max;
-  const int64_t cap_raw = (int64_t)kCoarseDup * L.n_points_max;
+  const int64_t cap_raw = (int64_t)kCoarseDup * pl->raw_max;
   int64_t cap = cap_fine > cap_raw ? cap_fine : cap_raw;
   if (cap > 0x7FFFFFFFLL) cap = 0x7FFFFFFFLL;
   pl->cand_cap = (int)cap;
@@ -720,21 +737,17 @@ int aero_create(const aero_limits_t* limits, aero_planner_t** out) {
   chk(alloc(&pl->cells, L.E_max + 1));
   chk(alloc(&pl->anchors, L.E_max * 3));
   chk(alloc(&pl->guides, (size_t)L.E_max * L.T_max * 3));
-  chk(alloc(&pl->item_flag, L.n_points_max));
+  chk(alloc(&pl->item_flag, pl->raw_max));
   chk(alloc(&pl->grid_count, kGridCellsMax + 1));
   chk(alloc(&pl->grid_fill, kGridCellsMax + 1));
   chk(alloc(&pl->grid_local, kGridCellsMax + 1));
   chk(alloc(&pl->tile_sum, kMaxTiles));
   chk(alloc(&pl->tile_off, kMaxTiles + 1));
   chk(alloc(&pl->cand, cap));
-  chk(alloc(&pl->cand_pts, std::max<int64_t>(L.fine_cells_max, L.n_points_max)));
+  chk(alloc(&pl->cand_pts, std::max<int64_t>(L.fine_cells_max, pl->raw_max)));
   chk(alloc(&pl->grid_range, kGridCellsMax));
   chk(alloc(&pl->partials, (size_t)L.E_max * nbmax * (4 + 4 * L.T_max)));
   chk(alloc(&pl->sample_costs, (size_t)L.E_max * L.K_max));
-  // the sampled perturbations are kept for the update when they take at most
-  // kMaxStoredPerturbationBytes; larger planners regenerate them from Philox
-  const size_t du_bytes = sizeof(float4) * (size_t)L.E_max * L.K_max * L.T_max;
-  if (du_bytes <= kMaxStoredPerturbationBytes) chk(alloc(&pl->dU, (size_t)L.E_max * L.K_max * L.T_max));
   chk(alloc(&pl->stage2_x, (size_t)L.E_max * (L.T_max + 1) * 10));
   chk(alloc(&pl->counter, kCounterWords));
   chk(alloc(&pl->status, 1));
@@ -898,7 +911,7 @@ int aero_get_debug(aero_planner_t* pl, int32_t what, void* dst, size_t bytes, vo
       const size_t need = sizeof(float4) * ne;
       if (bytes < need) return AERO_ERR_INVALID_ARG;
       if (!pl->last_idx_entries) return cuda_fail(cudaMemcpy(dst, pl->cand, need, cudaMemcpyDefault));
-      const size_t n_items = (size_t)std::max<int64_t>(pl->lim.fine_cells_max, pl->lim.n_points_max);
+      const size_t n_items = (size_t)std::max<int64_t>(pl->lim.fine_cells_max, pl->raw_max);
       std::vector<uint32_t> idx(ne);
       std::vector<float4> pts(n_items), out(ne);
       e = cudaMemcpy(idx.data(), pl->cand, 4 * ne, cudaMemcpyDeviceToHost);
@@ -1074,18 +1087,34 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kNaBytes];
 struct NoAllocDevice {
   bool ready = false;
   unsigned char* base = nullptr;
+  // the partition's edge tables last uploaded into this device's array, and
+  // their geometry: a call uploads them only when the geometry changes, from
+  // this host copy, which lives as long as the process
+  bool tab_valid = false;
+  int tab_A = 0, tab_El = 0;
+  float tab_lo = 0.0f, tab_hi = 0.0f;
+  int tab_check_lo = 0, tab_check_hi = 0;
+  PartTables tab{};
 };
 NoAllocDevice g_na_dev[64];
 std::mutex g_na_mutex;
 
-// Device address of the scratch array on the current device, looked up once
-// per device (host code must not use the symbol itself as an address).
-int noalloc_base(unsigned char** out) {
+// The current device's scratch state, set up on the first call (the device
+// address of the array, looked up once per device with that device current:
+// host code must not use the symbol itself as an address).  A first call on a
+// stream that is being captured is refused: the look-up is not a stream
+// operation.
+int noalloc_device(cudaStream_t s, NoAllocDevice** out) {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return AERO_ERR_CUDA;
-  std::lock_guard<std::mutex> lock(g_na_mutex);
   NoAllocDevice& d = g_na_dev[dev];
   if (!d.ready) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cs) != cudaSuccess) {
+      cudaGetLastError();
+      return AERO_ERR_CUDA;
+    }
+    if (cs != cudaStreamCaptureStatusNone) return AERO_ERR_INVALID_ARG;
     void* p = nullptr;
     if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || p == nullptr) {
       cudaGetLastError();
@@ -1094,7 +1123,7 @@ int noalloc_base(unsigned char** out) {
     d.base = static_cast<unsigned char*>(p);
     d.ready = true;
   }
-  *out = d.base;
+  *out = &d;
   return AERO_OK;
 }
 
@@ -1147,6 +1176,7 @@ int aero_plan_step_noalloc(const aero_state_t* x0, const float* cloud, int64_t n
   pl.lim.fine_cells_max = kNaCells;
   pl.lim.n_points_max = kNaPoints;
   pl.lim.debug_samples_max = 0;
+  pl.raw_max = kNaPoints;
   int rc = validate(&pl, params, n);
   if (rc != AERO_OK) return rc;
   if (params->collision_set != 0) return AERO_ERR_EXCEEDS_LIMITS;
@@ -1154,11 +1184,45 @@ int aero_plan_step_noalloc(const aero_state_t* x0, const float* cloud, int64_t n
   if ((n > 0 && !is_device_ptr(cloud)) || !is_device_ptr(u_nom) || !is_device_ptr(u_best) ||
       !is_device_ptr(cand) || !is_device_ptr(best_idx))
     return AERO_ERR_NOT_DEVICE_PTR;
-  unsigned char* base = nullptr;
-  rc = noalloc_base(&base);
-  if (rc != AERO_OK) return rc;
-  noalloc_carve(base, pl);
   cudaStream_t s = (cudaStream_t)stream;
+  std::lock_guard<std::mutex> lock(g_na_mutex);
+  NoAllocDevice* d = nullptr;
+  rc = noalloc_device(s, &d);
+  if (rc != AERO_OK) return rc;
+  noalloc_carve(d->base, pl);
+  // the edge tables: the device's own host copy, uploaded only when the
+  // partition geometry differs from the last upload
+  pl.tab_valid = d->tab_valid;
+  pl.tab_A = d->tab_A;
+  pl.tab_El = d->tab_El;
+  pl.tab_lo = d->tab_lo;
+  pl.tab_hi = d->tab_hi;
+  pl.tab_check_lo = d->tab_check_lo;
+  pl.tab_check_hi = d->tab_check_hi;
+  const bool same = d->tab_valid && d->tab_A == params->fine_az && d->tab_El == params->fine_el &&
+                    d->tab_lo == params->el_lo && d->tab_hi == params->el_hi;
+  if (!same) {
+    make_tables(*params, d->tab, d->tab_check_lo, d->tab_check_hi);
+    d->tab_valid = true;
+    d->tab_A = params->fine_az;
+    d->tab_El = params->fine_el;
+    d->tab_lo = params->el_lo;
+    d->tab_hi = params->el_hi;
+    cudaError_t e = cudaMemcpyAsync(pl.d_tab, &d->tab, sizeof(PartTables), cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) {
+      d->tab_valid = false;
+      return AERO_ERR_CUDA;
+    }
+    pl.tab_valid = true;
+    pl.tab_A = d->tab_A;
+    pl.tab_El = d->tab_El;
+    pl.tab_lo = d->tab_lo;
+    pl.tab_hi = d->tab_hi;
+    pl.tab_check_lo = d->tab_check_lo;
+    pl.tab_check_hi = d->tab_check_hi;
+  }
+  pl.tab = d->tab;
+  pl.tab_upload = false;
   // the last-block tickets and the status word must start at zero
   cudaError_t e = cudaMemsetAsync(pl.counter, 0, kCounterWords * sizeof(unsigned int), s);
   if (e == cudaSuccess) e = cudaMemsetAsync(pl.status, 0, sizeof(int), s);

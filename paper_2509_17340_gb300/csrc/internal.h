@@ -136,7 +136,6 @@ struct RolloutArgs {
   GridView grid;
   float* partials;         // E x nb x (4 + 4T): rho, eta, 2 pad, W (16-byte aligned)
   float* sample_costs;     // E x K
-  float4* dU;              // E x T x K clamped perturbations, or null: regenerate them
   int dbg_D;
   float* dbg_u;            // E x D x T x 4
   float* dbg_x;            // E x D x (T+1) x 10
@@ -239,7 +238,10 @@ cudaError_t batch_rollout_occupancy(int out[4], int T_max);
 // t: the edge tables in device memory
 cudaError_t launch_partition(const PartitionArgs& a, const PartTables* t, cudaStream_t s);
 int partition_blocks(int64_t n);  // CTAs of launch_partition for n points (0 when n == 0)
-constexpr int kPartBlocksMax = 152 * 16;
+constexpr int kPartBlocksMax = 4096;  // CTAs of launch_partition, at most (16 per SM, capped)
+// Streaming multiprocessors of the current device, queried once per device
+// (1 if the query fails: the launches stay correct, only slower).
+int device_sms();
 // count pass + coarse argmax; then the tile scans + goal cone, anchors, guides
 cudaError_t launch_grid_count(const CandArgs& ca, const GuideArgs& ga, cudaStream_t s);
 cudaError_t launch_grid_scan(int* count, int* fill, int* local, int* tile_sum, int* tile_off,
@@ -263,7 +265,7 @@ struct CostGradArgs {
 // the last CTA of every instance, the others leave it to launch_update.
 cudaError_t launch_rollout(const RolloutArgs& a, const UpdateArgs& ua, cudaStream_t s);
 bool rollout_runs_update(const RolloutArgs& a);
-// Sets the kernels' shared-memory limits (once per process).
+// Sets the kernels' shared-memory limits (once per device).
 cudaError_t split_attributes();
 cudaError_t launch_cost_grad(const CostGradArgs& a, cudaStream_t s);
 cudaError_t launch_update(const UpdateArgs& a, cudaStream_t s);

@@ -696,7 +696,10 @@ int blocks_for(int64_t n, int threads, int cap) {
 
 }  // namespace
 
-int partition_blocks(int64_t n) { return n > 0 ? blocks_for(n, 256, kPartBlocksMax) : 0; }
+int partition_blocks(int64_t n) {
+  const int cap = 16 * device_sms();
+  return n > 0 ? blocks_for(n, 256, cap < kPartBlocksMax ? cap : kPartBlocksMax) : 0;
+}
 
 cudaError_t launch_partition(const PartitionArgs& a, const PartTables* t, cudaStream_t s) {
   if (a.n == 0) return cudaSuccess;
@@ -705,7 +708,7 @@ cudaError_t launch_partition(const PartitionArgs& a, const PartTables* t, cudaSt
 
 cudaError_t launch_grid_count(const CandArgs& ca, const GuideArgs& ga, cudaStream_t s) {
   // one warp per collision item up to four blocks per SM, then items per warp
-  const int count_blocks = ca.n_items > 0 ? blocks_for(ca.n_items * 32, 256, 152 * 4) : 0;
+  const int count_blocks = ca.n_items > 0 ? blocks_for(ca.n_items * 32, 256, 4 * device_sms()) : 0;
   const int coarse_blocks = (ga.Ac * ga.Ec + 7) / 8;  // 8 warps per block
   return launch_k(k_grid_count, dim3(count_blocks + coarse_blocks), dim3(256), s, true, ca, ga,
                   count_blocks);
@@ -720,8 +723,9 @@ cudaError_t launch_grid_scan(int* count, int* fill, int* local, int* tile_sum, i
 
 cudaError_t launch_grid_scatter(const CandArgs& ca, int2* range, int ncells, const int* tile_sum,
                                 int* tile_off, int ntiles, cudaStream_t s) {
-  const int scatter_blocks = ca.n_items > 0 ? blocks_for(ca.n_items * 32, 256, 152 * 4) : 0;
-  const int range_blocks = blocks_for(ncells, 256, 152 * 2);
+  const int sms = device_sms();
+  const int scatter_blocks = ca.n_items > 0 ? blocks_for(ca.n_items * 32, 256, 4 * sms) : 0;
+  const int range_blocks = blocks_for(ncells, 256, 2 * sms);
   return launch_k(k_grid_scatter, dim3(scatter_blocks + range_blocks), dim3(256), s, true, ca,
                   scatter_blocks, range, ncells, tile_sum, tile_off, ntiles);
 }
@@ -757,7 +761,7 @@ cudaError_t launch_batch_scatter(const BatchView& v, int blocks, cudaStream_t s)
 cudaError_t launch_philox(uint32_t k0, uint32_t k1, uint32_t c1, uint32_t c2, uint32_t c3,
                           int64_t n, uint32_t* out, cudaStream_t s) {
   if (n == 0) return cudaSuccess;
-  k_philox<<<blocks_for(n, 256, 152 * 16), 256, 0, s>>>(k0, k1, c1, c2, c3, n,
+  k_philox<<<blocks_for(n, 256, 16 * device_sms()), 256, 0, s>>>(k0, k1, c1, c2, c3, n,
                                                           reinterpret_cast<uint4*>(out));
   return cudaGetLastError();
 }

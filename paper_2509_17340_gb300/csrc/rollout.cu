@@ -2,11 +2,13 @@
 // (one warp-group) rolls out 128 samples of one instance.  Per sample and
 // step: Philox noise in registers, clamp, RK4, the S(1) cost terms with the
 // nearest-point distance from the collision grid.  Then per CTA: the minimum
-// cost rho_b, eta_b = sum exp(-(S - rho_b)/lambda) and, by regenerating the
-// noise, W_b[j][c] = sum exp(-(S - rho_b)/lambda) du[j][c].  The update kernel
-// merges the per-CTA partials (log-sum-exp rescaling by the global minimum),
-// updates the nominal (Eq. mppi_update_simplified), and on the last iteration
-// runs Stage II and the selection.
+// cost rho_b, eta_b = sum exp(-(S - rho_b)/lambda) and W_b[j][c] = sum
+// exp(-(S - rho_b)/lambda) du[j][c], the perturbations regenerated from the
+// counter-based generator for the samples whose weight is not zero (nothing
+// is stored per sample and step).  The update kernel merges the per-CTA
+// partials (log-sum-exp rescaling by the global minimum), updates the nominal
+// (Eq. mppi_update_simplified), and on the last iteration runs Stage II and
+// the selection.
 #include <atomic>
 #include <cfloat>
 #include <cstdint>
@@ -20,6 +22,7 @@ namespace {
 
 constexpr int NT = kRolloutThreads;
 constexpr int NW = NT / 32;
+static_assert(kMaxT <= NT, "every step of the horizon has a thread in the weighted-sum pass");
 
 __device__ __forceinline__ float4 clamp4(float4 u, float4 lo, float4 hi) {
   return make_float4(fminf(fmaxf(u.x, lo.x), hi.x), fminf(fmaxf(u.y, lo.y), hi.y),
@@ -42,7 +45,10 @@ __device__ __forceinline__ void rollout_unit(const RolloutArgs& a, int e, int b,
   __shared__ float4 s_un[kMaxT];
   __shared__ float s_gd[kMaxT * 3];
   __shared__ float s_red[NW];
-  __shared__ float4 s_w[NW][kMaxT];
+  __shared__ int s_nz[NW];       // weighted samples per warp
+  __shared__ int s_lk[NT];       // the CTA's samples of non-zero weight, in sample order
+  __shared__ float s_lw[NT];     // and their weights
+  __shared__ float4 s_w[NT];     // W_b partial sums [replica][step], NT >= replicas x T
 
   const int tid = threadIdx.x;
   const int lane = tid & 31, wid = tid >> 5;
@@ -59,7 +65,6 @@ __device__ __forceinline__ void rollout_unit(const RolloutArgs& a, int e, int b,
   const float4 sigma = make_float4(a.sigma[0], a.sigma[1], a.sigma[2], a.sigma[3]);
   const float4 umin = make_float4(a.umin[0], a.umin[1], a.umin[2], a.umin[3]);
   const float4 umax = make_float4(a.umax[0], a.umax[1], a.umax[2], a.umax[3]);
-  float4* dU = a.dU ? a.dU + (size_t)e * T * a.K + k : nullptr;  // [e][j][k]
 
   State x;
 #pragma unroll
@@ -74,7 +79,7 @@ __device__ __forceinline__ void rollout_unit(const RolloutArgs& a, int e, int b,
   }
 
   CostSum S;
-  // step j's control: prefetched noise, clamp, the stored perturbation, J_ctrl's
+  // step j's control: prefetched noise, clamp, J_ctrl's
   // terms Q_c |u_j|^2 (j <= T-2) and Q_cd |u_j - u_{j-1}|^2 (1 <= j <= T-2)
   float4 d_next = noise_delta(k, 0, e, ctr3, a.key0, a.key1, sigma);
   float4 un_next = s_un[0];
@@ -86,8 +91,6 @@ __device__ __forceinline__ void rollout_unit(const RolloutArgs& a, int e, int b,
       un_next = s_un[j + 1];
     }
     const float4 u = clamp4(make_float4(un.x + d.x, un.y + d.y, un.z + d.z, un.w + d.w), umin, umax);
-    if (dU && active)  // streaming store: read once, by this thread, after the rollout
-      __stcs(dU + (size_t)j * a.K, make_float4(u.x - un.x, u.y - un.y, u.z - un.z, u.w - un.w));
     c_ctrl = 0.0f;
     if (j <= T - 2) {
       c_ctrl = cp.Q_c * (u.x * u.x + u.y * u.y + u.z * u.z + u.w * u.w);
@@ -153,21 +156,46 @@ __device__ __forceinline__ void rollout_unit(const RolloutArgs& a, int e, int b,
   __syncthreads();
   const float wk = active ? expf((rho - Sk) * a.inv_lambda) : 0.0f;
   const float ws = warp_sum(wk);
-  if (lane == 0) s_red[wid] = ws;
-
-  // W_b[j] = sum_k w_k du_k[j]: the stored perturbations, or the noise regenerated
-  for (int j = 0; j < T; ++j) {
-    float4 du;
-    if (dU) {
-      du = active ? __ldcs(dU + (size_t)j * a.K) : make_float4(0.f, 0.f, 0.f, 0.f);
-    } else {
-      const float4 un = s_un[j];
-      const float4 d = noise_delta(k, j, e, ctr3, a.key0, a.key1, sigma);
+  // the samples of non-zero weight, listed in sample order: a sample whose
+  // weight underflows to zero adds exactly nothing to W_b, so only the listed
+  // ones regenerate their perturbations (with lambda = 1, a sample whose cost
+  // exceeds the CTA's best by more than about 104 is not listed)
+  const unsigned nzb = __ballot_sync(0xffffffffu, wk > 0.0f);
+  if (lane == 0) {
+    s_red[wid] = ws;
+    s_nz[wid] = __popc(nzb);
+  }
+  __syncthreads();
+  int nz = 0, before = 0;
+#pragma unroll
+  for (int w = 0; w < NW; ++w) {
+    before += w < wid ? s_nz[w] : 0;
+    nz += s_nz[w];
+  }
+  if (wk > 0.0f) {
+    const int pos = before + __popc(nzb & ((1u << lane) - 1u));
+    s_lk[pos] = k;
+    s_lw[pos] = wk;
+  }
+  __syncthreads();
+  // W_b[j] = sum over the listed samples of w_k du_k[j]: thread t takes step
+  // j = t mod T and the listed samples i = r, r + R, ... of replica r = t / T
+  // (R = NT / T replicas; a fixed order, so the sums are reproducible)
+  const int R = T <= NT ? NT / T : 1;
+  if (tid < R * T) {
+    const int j = tid % T, r = tid / T;
+    const float4 un = s_un[j];
+    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int i = r; i < nz; i += R) {
+      const float w = s_lw[i];
+      const float4 d = noise_delta(s_lk[i], j, e, ctr3, a.key0, a.key1, sigma);
       const float4 u = clamp4(make_float4(un.x + d.x, un.y + d.y, un.z + d.z, un.w + d.w), umin, umax);
-      du = make_float4(u.x - un.x, u.y - un.y, u.z - un.z, u.w - un.w);
+      acc.x += w * (u.x - un.x);
+      acc.y += w * (u.y - un.y);
+      acc.z += w * (u.z - un.z);
+      acc.w += w * (u.w - un.w);
     }
-    const float r = warp_sum4(wk * du.x, wk * du.y, wk * du.z, wk * du.w, lane);
-    if ((lane & 7) == 0) reinterpret_cast<float*>(&s_w[wid][j])[lane >> 3] = r;
+    s_w[tid] = acc;
   }
   __syncthreads();
   float* out = a.partials + ((size_t)e * a.nb + b) * (4 + 4 * T);
@@ -182,8 +210,7 @@ __device__ __forceinline__ void rollout_unit(const RolloutArgs& a, int e, int b,
   for (int i = tid; i < 4 * T; i += NT) {
     const int j = i >> 2, cc = i & 3;
     float s = 0.0f;
-#pragma unroll
-    for (int w = 0; w < NW; ++w) s += reinterpret_cast<const float*>(&s_w[w][j])[cc];
+    for (int r = 0; r < R; ++r) s += reinterpret_cast<const float*>(&s_w[r * T + j])[cc];
     out[4 + i] = s;
   }
 }
@@ -902,29 +929,39 @@ cudaError_t launch_cost_grad(const CostGradArgs& a, cudaStream_t s) {
 }
 
 // The split pass reads its shared memory as one dynamic block sized for the
-// horizon; allow the largest (once per process; the create functions call it
-// first, so that no launch captured into a graph is the first).
+// horizon; allow the largest.  The attribute belongs to the device, so it is
+// set once per device (the create functions call this first, so that no
+// launch captured into a graph is the first on its device).
 cudaError_t split_attributes() {
-  static const cudaError_t e = [] {
-    const int most = (int)split_smem_bytes(kMaxT);
-    cudaError_t r = cudaFuncSetAttribute(k_rollout_split, cudaFuncAttributeMaxDynamicSharedMemorySize, most);
-    if (r == cudaSuccess)
-      r = cudaFuncSetAttribute(k_b_rollout<4, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, most);
-    const int refine = (int)update_smem_bytes(kMaxT, UT / 32, true);
-    if (r == cudaSuccess)
-      r = cudaFuncSetAttribute(k_update, cudaFuncAttributeMaxDynamicSharedMemorySize, refine);
-    if (r == cudaSuccess)
-      r = cudaFuncSetAttribute(k_b_update, cudaFuncAttributeMaxDynamicSharedMemorySize, refine);
-    return r;
-  }();
-  return e;
+  static std::atomic<int> done[64];  // 0: not yet, 1: set, else the error + 2
+  int dev = 0;
+  cudaError_t r = cudaGetDevice(&dev);
+  if (r != cudaSuccess) return r;
+  const bool cached = dev >= 0 && dev < 64;
+  if (cached) {
+    const int d = done[dev].load();
+    if (d == 1) return cudaSuccess;
+    if (d > 1) return (cudaError_t)(d - 2);
+  }
+  const int most = (int)split_smem_bytes(kMaxT);
+  r = cudaFuncSetAttribute(k_rollout_split, cudaFuncAttributeMaxDynamicSharedMemorySize, most);
+  if (r == cudaSuccess)
+    r = cudaFuncSetAttribute(k_b_rollout<4, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, most);
+  const int refine = (int)update_smem_bytes(kMaxT, UT / 32, true);
+  if (r == cudaSuccess)
+    r = cudaFuncSetAttribute(k_update, cudaFuncAttributeMaxDynamicSharedMemorySize, refine);
+  if (r == cudaSuccess)
+    r = cudaFuncSetAttribute(k_b_update, cudaFuncAttributeMaxDynamicSharedMemorySize, refine);
+  if (cached) done[dev].store(r == cudaSuccess ? 1 : (int)r + 2);
+  return r;
 }
 
 // Few CTAs per SM run the single-planner split pass and its candidate scans
 // live on L1 hits: the carveout asked for is the smallest that still holds
-// two of its CTAs (as a percentage of the 228 KB an SM can give).
+// two of its CTAs (as a percentage of the 228 KB an SM can give).  Like the
+// size limit, the carveout is an attribute per device.
 cudaError_t split_carveout(int T) {
-  static std::atomic<int> current{-1};
+  static std::atomic<int> current[64];  // the percentage set on each device, plus one
   static const size_t static_bytes = [] {
     cudaFuncAttributes fa{};
     return cudaFuncGetAttributes(&fa, k_rollout_split) == cudaSuccess ? fa.sharedSizeBytes : 0;
@@ -932,10 +969,13 @@ cudaError_t split_carveout(int T) {
   const size_t need = 2 * (split_smem_bytes(T) + static_bytes + 1024);
   int pct = (int)((need * 100 + 228 * 1024 - 1) / (228 * 1024));
   if (pct > 100) pct = 100;
-  if (current.load() == pct) return cudaSuccess;
-  const cudaError_t e =
-      cudaFuncSetAttribute(k_rollout_split, cudaFuncAttributePreferredSharedMemoryCarveout, pct);
-  if (e == cudaSuccess) current.store(pct);
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  const bool cached = dev >= 0 && dev < 64;
+  if (cached && current[dev].load() == pct + 1) return cudaSuccess;
+  e = cudaFuncSetAttribute(k_rollout_split, cudaFuncAttributePreferredSharedMemoryCarveout, pct);
+  if (e == cudaSuccess && cached) current[dev].store(pct + 1);
   return e;
 }
 

@@ -47,4 +47,32 @@ def test_traffic_is_null_without_a_record(tmp_path, monkeypatch):
 
 
 def test_fp32_peak_is_the_unit_count_times_the_clock():
-    assert bench.fp32_peak_tflops(2070.0) == pytest.approx(152 * 128 * 2 * 2070e6 / 1e12)
+    assert bench.fp32_peak_tflops(2070.0, 152) == pytest.approx(152 * 128 * 2 * 2070e6 / 1e12)
+    assert bench.fp32_peak_tflops(1000.0, 10) == pytest.approx(10 * 128 * 2 * 1e9 / 1e12)
+
+
+def _smi(sm, util, reasons=("Not Active",) * 4, mx=2070, power=500.0):
+    return ", ".join(["0", str(sm), str(mx), str(power), str(util), "0x0", *reasons])
+
+
+def test_clock_summary_takes_the_median_under_load_and_every_reason():
+    lines = [_smi(2070, 0), _smi(1900, 95), _smi(1800, 99), _smi(1700, 97),
+             _smi(2070, 80, ("Not Active", "Not Active", "Not Active", "Active")),
+             "garbage line", ""]
+    c = bench.clock_summary(lines)
+    assert c["samples"] == 5 and c["samples_under_load"] == 4
+    assert c["sm_mhz"] == pytest.approx((1800 + 1900) / 2)
+    assert c["sm_max_mhz"] == 2070.0
+    assert c["reasons"] == ["sw_power_cap"]
+
+
+def test_clock_summary_without_load_uses_every_sample():
+    c = bench.clock_summary([_smi(2070, 0), _smi(2000, 10)])
+    assert c["samples_under_load"] == 0 and c["sm_mhz"] == pytest.approx(2035.0)
+    assert bench.clock_summary([])["sm_mhz"] is None
+
+
+def test_flop_count_is_the_sum_of_its_terms():
+    assert bench.rollout_flops_per_step() == 16 + 12 + 226 + 13 + 69 + 1 + 8
+    P = dict(E=2, K=3, T=5, iters=2)
+    assert bench.rollout_steps(P) == 2 * 3 * 5 * 2 + 2 * 5

@@ -57,7 +57,8 @@ def test_two_ranks_weak_scaling_and_max_time():
 
 def test_reference_arm_runs_the_oracle_on_cpu():
     r = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--steps", "1",
-                        "--warmup", "0"], cwd=ROOT, capture_output=True, text=True, timeout=600)
+                        "--warmup", "0", "--reference-budget", "3"], cwd=ROOT, capture_output=True,
+                       text=True, timeout=600)
     assert r.returncode == 0, r.stderr
     line = json.loads([l for l in r.stdout.splitlines() if l.startswith("{")][-1])
     assert line["impl"] == "reference" and line["value"] > 0 and line["unit"] == "rollout-steps/s"
