@@ -781,7 +781,8 @@ def run_partition_sweep(args, rank: int, world: int, local: int):
     dev = torch.device("cuda", local)
     stream = torch.cuda.Stream(device=dev)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
-    sizes = [n for n in SWEEP_SIZES if n <= args.sweep_max]
+    sizes = ([int(x) for x in args.sweep_sizes.split(",")] if args.sweep_sizes else
+             [n for n in SWEEP_SIZES if n <= args.sweep_max])
     clk = ClockSampler(local).start()
     rows = partition_sweep(aero, dev, stream, flush, sizes, args.steps, args.warmup, rank_seed(rank))
     clk.stop()
@@ -1009,6 +1010,8 @@ def main():
                     help="reference arm: wall seconds its whole run aims at")
     ap.add_argument("--sweep-max", type=int, default=10**8,
                     help="partition_sweep: largest cloud size")
+    ap.add_argument("--sweep-sizes", default="",
+                    help="partition_sweep: cloud sizes (comma list) instead of 1e5 .. --sweep-max")
     ap.add_argument("--no-stage-timing", action="store_true",
                     help="diagnostic: no per-stage events in the timed steps (no roofline)")
     args = ap.parse_args()

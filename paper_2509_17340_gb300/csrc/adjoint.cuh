@@ -50,35 +50,45 @@ __device__ __forceinline__ State state_load(const float* d) {
 
 // Nearest collision points of the n <= 8 states seg[1..n] by the warp, four
 // lanes per state: squared distances (d_max^2 when none is closer) and the
-// nearest points (lowest entry among ties) into sc.d2 / sc.nearest.
+// nearest points into sc.d2 / sc.nearest.  Among equidistant points the one of
+// lowest item index wins (the collision set's order, as the oracle breaks
+// ties), whatever the order of the entries in the cell's list.
 __device__ __forceinline__ void warp_nn_segment(AdjScratch& sc, int n, const GridView& g,
                                                 float dmax2, int lane) {
   const int k = lane >> 2, q = lane & 3;
   float best = dmax2;
-  int bi = 0x7fffffff;
+  int bitem = 0x7fffffff;
+  float4 bp = make_float4(0.f, 0.f, 0.f, 0.f);
   if (k < n) {
     const float* x = sc.seg + (k + 1) * 10;
     const int2 r = cell_range(x[0], x[1], x[2], g);
     for (int i = q; i < r.y; i += 4) {
-      const float d2 = dist2_to(grid_point(g, r.x + i), x[0], x[1], x[2]);
-      if (d2 < best) {
+      const float4 p = grid_point(g, r.x + i);
+      const float d2 = dist2_to(p, x[0], x[1], x[2]);
+      const int item = point_item(p);
+      if (d2 < best || (d2 == best && d2 < dmax2 && item < bitem)) {
         best = d2;
-        bi = r.x + i;
+        bitem = item;
+        bp = p;
       }
     }
   }
 #pragma unroll
   for (int o = 1; o < 4; o <<= 1) {
     const float ob = __shfl_xor_sync(0xffffffffu, best, o);
-    const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-    if (ob < best || (ob == best && oi < bi)) {
+    const int oi = __shfl_xor_sync(0xffffffffu, bitem, o);
+    const float ox = __shfl_xor_sync(0xffffffffu, bp.x, o);
+    const float oy = __shfl_xor_sync(0xffffffffu, bp.y, o);
+    const float oz = __shfl_xor_sync(0xffffffffu, bp.z, o);
+    if (ob < best || (ob == best && oi < bitem)) {
       best = ob;
-      bi = oi;
+      bitem = oi;
+      bp = make_float4(ox, oy, oz, bp.w);
     }
   }
   if (k < n && q == 0) {
     sc.d2[k] = best;
-    sc.nearest[k] = bi != 0x7fffffff ? grid_point(g, bi) : make_float4(0.f, 0.f, 0.f, 0.f);
+    sc.nearest[k] = bitem != 0x7fffffff ? bp : make_float4(0.f, 0.f, 0.f, 0.f);
   }
 }
 
@@ -367,16 +377,17 @@ __device__ float warp_cost_grad(const float4* u, float4* g, const float* guide, 
 // products, from stage states stored by the forward pass), everything else
 // over the CTA: the stage states of every step, the nearest point of every
 // state (candidate lists cut into items of kRefItem entries; a 64-bit atomic
-// minimum of (squared distance bits, entry) keeps the lowest entry among
-// ties), the state terms and their gradients, the control terms and the
-// clamped step.  The same arithmetic as warp_cost_grad<true> followed by the
-// clamped step.
+// minimum of (squared distance bits, item index) keeps the lowest item among
+// equidistant points, the collision set's order), the state terms and their
+// gradients, the control terms and the clamped step.  The same arithmetic as
+// warp_cost_grad<true> followed by the clamped step.
 // ---------------------------------------------------------------------------
 constexpr int kRefItem = 8;
 
 struct RefineScratch {
   float4* g;                 // T: dS/du
-  unsigned long long* key;   // T: (bits(d2) << 32) | entry of the nearest point of x_{j+1}
+  unsigned long long* key;   // T: (bits(d2) << 32) | item of the nearest point of x_{j+1}
+  float4* near;              // T: that point (entries holding points: found by a second pass)
   int2* qrange;              // T: candidate range of each listed query
   int2* scan;                // warps: block-scan totals
   float* xs;                 // (T + 1) x 10: states x_0 .. x_T
@@ -387,7 +398,7 @@ struct RefineScratch {
 };
 
 __host__ __device__ constexpr size_t refine_smem_bytes(int T, int warps) {
-  return 16 * (size_t)T + 8 * (size_t)T + 8 * (size_t)T + 8 * (size_t)warps +
+  return 16 * (size_t)T + 8 * (size_t)T + 16 * (size_t)T + 8 * (size_t)T + 8 * (size_t)warps +
          4 * (size_t)(T + 1) * 10 + 4 * (size_t)T * 34 + 4 * (size_t)T * 10 + 4 * (size_t)(T + 1) +
          4 * (size_t)T;
 }
@@ -396,7 +407,8 @@ __device__ __forceinline__ RefineScratch refine_layout(unsigned char* base, int 
   RefineScratch r;
   r.g = reinterpret_cast<float4*>(base);
   r.key = reinterpret_cast<unsigned long long*>(r.g + T);
-  r.qrange = reinterpret_cast<int2*>(r.key + T);
+  r.near = reinterpret_cast<float4*>(r.key + T);
+  r.qrange = reinterpret_cast<int2*>(r.near + T);
   r.scan = r.qrange + T;
   r.xs = reinterpret_cast<float*>(r.scan + warps);
   r.st = r.xs + (size_t)(T + 1) * 10;
@@ -447,33 +459,61 @@ __device__ void block_refine(float4* u, const float* guide, int T, const float* 
       rs.qslot[off.x] = tid;
     }
     __syncthreads();
-    for (int it = tid; it < total.y; it += kThreads) {
+    // the nearest point of a listed query's item of entries: (squared
+    // distance, item index) of the point of lowest (distance, item), and the point
+    auto item_min = [&](int it, int& j, float& best, int& bitem, float4& bp) {
       const int lo = item_owner(rs.qitem, total.x, it);
       const int2 q = rs.qrange[lo];
-      const int j = rs.qslot[lo];
+      j = rs.qslot[lo];
       const int first = (it - rs.qitem[lo]) * kRefItem;
       const int n = q.y - first < kRefItem ? q.y - first : kRefItem;
-      if (!AERO_CHECK(j < T && first >= 0 && n > 0 && q.x >= 0, kChkQuery)) continue;
+      best = dmax2;
+      bitem = -1;
+      if (!AERO_CHECK(j < T && first >= 0 && n > 0 && q.x >= 0, kChkQuery)) return;
       const float* x1 = rs.xs + (j + 1) * 10;
-      float best = dmax2;
-      int bi = -1;
-      for (int c = 0; c < n; ++c) {  // in entry order: the first of equal distances stays
-        const float d2 = dist2_to(grid_point(grid, q.x + first + c), x1[0], x1[1], x1[2]);
-        if (d2 < best) {
+      for (int c = 0; c < n; ++c) {
+        const float4 p = grid_point(grid, q.x + first + c);
+        const float d2 = dist2_to(p, x1[0], x1[1], x1[2]);
+        const int item = point_item(p);
+        if (d2 < best || (d2 == best && bitem >= 0 && item < bitem)) {
           best = d2;
-          bi = q.x + first + c;
+          bitem = item;
+          bp = p;
         }
       }
-      if (bi >= 0)
-        atomicMin(rs.key + j, ((unsigned long long)__float_as_uint(best) << 32) | (unsigned)bi);
+    };
+    for (int it = tid; it < total.y; it += kThreads) {
+      int j, bitem;
+      float best;
+      float4 bp;
+      item_min(it, j, best, bitem, bp);
+      if (bitem >= 0)
+        atomicMin(rs.key + j, ((unsigned long long)__float_as_uint(best) << 32) | (unsigned)bitem);
     }
     __syncthreads();
+    if (!grid.cand) {
+      // entries holding the points: the winner's point from the item that
+      // holds the winning (distance, item) pair
+      for (int it = tid; it < total.y; it += kThreads) {
+        int j, bitem;
+        float best;
+        float4 bp;
+        item_min(it, j, best, bitem, bp);
+        if (bitem >= 0 &&
+            rs.key[j] == (((unsigned long long)__float_as_uint(best) << 32) | (unsigned)bitem))
+          rs.near[j] = bp;
+      }
+      __syncthreads();
+    }
     // state-term gradients at x_{tid+1}
     if (tid < T) {
       const unsigned long long kk = rs.key[tid];
       const float d2 = __uint_as_float((unsigned)(kk >> 32));
       const unsigned bi = (unsigned)kk;
-      const float4 nearest = bi != 0xffffffffu ? grid_point(grid, (int)bi) : make_float4(0.f, 0.f, 0.f, 0.f);
+      // entries holding item indices: the item's point directly
+      const float4 nearest = bi == 0xffffffffu ? make_float4(0.f, 0.f, 0.f, 0.f)
+                             : grid.cand       ? __ldg(grid.pts + bi)
+                                               : rs.near[tid];
       state_terms<true>(state_load(rs.xs + (tid + 1) * 10), guide[3 * tid], guide[3 * tid + 1],
                         guide[3 * tid + 2], d2, nearest, cp, dmax2, rs.gs + tid * 10);
     }

@@ -172,10 +172,14 @@ __device__ __forceinline__ float dist2_to(const float4 q, float px, float py, fl
   return ax * ax + ay * ay + az * az;
 }
 
-// The collision point of candidate entry e of the grid (either form).
+// The collision point of candidate entry e of the grid (either form); its w
+// holds the bits of the point's item index (the position of the point in the
+// collision set: the fine cone of a P_f point, the index of a kept point).
 __device__ __forceinline__ float4 grid_point(const GridView& g, int e) {
   return g.cand ? __ldg(g.pts + __ldg(g.cand + e)) : __ldg(g.pts + e);
 }
+
+__device__ __forceinline__ int point_item(float4 p) { return __float_as_int(p.w); }
 
 // The same for a grid whose entry form is known at compile time (kIdx: item
 // indices), for the per-entry loop of the one-thread pass.

@@ -77,8 +77,8 @@ struct CandArgs {
   // pts, whose points the count pass stores (cand non-null), or the points
   // themselves (cand4)
   uint32_t* cand;
-  float4* pts;         // n_items: collision point of each item, minus p0
-  float4* cand4;
+  float4* pts;         // n_items: collision point of each item, minus p0 (w: the item index's bits)
+  float4* cand4;       // entries holding the points (w: the item index's bits)
   int* status;
   unsigned long long* reset_keys;  // non-null: the scatter pass empties each key it reads
 };

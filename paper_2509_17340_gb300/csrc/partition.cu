@@ -152,8 +152,10 @@ __global__ void __launch_bounds__(256) k_partition(PartitionArgs a, const PartTa
 // the cell's counter, the scatter pass writes the entry at start(cell) + its
 // fill ticket.  An entry is either i (4 bytes; the count pass stores p at
 // pts[i], and the points, far fewer than the entries, stay in L1) or p itself
-// (16 bytes, one load fewer per entry read).  Order within a cell depends on
-// the atomics, but only the minimum distance is used.
+// (16 bytes, one load fewer per entry read).  Either way a point carries its
+// item index in w (bits of an int), so that ties between equidistant points
+// are broken by item, the collision set's order, whatever the order of the
+// entries within a cell, which depends on the atomics.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ bool cand_item(const CandArgs& a, int64_t it, float& px, float& py,
                                           float& pz) {
@@ -193,7 +195,7 @@ __device__ __forceinline__ void cand_task(const CandArgs& a, int64_t it, int lan
     if (lane == 0) a.reset_keys[it] = kEmpty;
   }
   if constexpr (!kScatter && kIdx) {
-    if (lane == 0) a.pts[it] = make_float4(px, py, pz, 0.0f);
+    if (lane == 0) a.pts[it] = make_float4(px, py, pz, __int_as_float((int)it));
   }
   const int x0 = max(__float2int_rd((px - g.reach - g.origin) * g.inv_h), 0);
   const int x1 = min(__float2int_rd((px + g.reach - g.origin) * g.inv_h), g.G - 1);
@@ -219,7 +221,7 @@ __device__ __forceinline__ void cand_task(const CandArgs& a, int64_t it, int lan
         if constexpr (kIdx)
           a.cand[pos] = (uint32_t)it;
         else
-          a.cand4[pos] = make_float4(px, py, pz, 0.0f);
+          a.cand4[pos] = make_float4(px, py, pz, __int_as_float((int)it));
       } else
         atomicOr(a.status, 2);
     }

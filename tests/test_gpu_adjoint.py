@@ -233,3 +233,109 @@ def test_invalid_refinement_and_cost_grad_arguments(aero):
                          w.goal, aero.params_struct(P), un, ub, c, bi)
         assert ei.value.code == aero.ERR_INVALID_ARG, upd
     pl.close()
+
+
+# ----------------------------------------------------------------- equidistant points
+
+def _tie_case(**upd):
+    """Two points mirrored across the plane y = 0 (at y = +-0.6 m, 1.07 m ahead)
+    and a start moving along +x with zero body rates and no rate noise: every
+    state of every rollout stays exactly on y = 0, so both points are at
+    exactly the same binary32 distance from it.  They fall in different fine
+    cones; the oracle takes the one of lower index in the collision set (the
+    lower cone, y = -0.6), and so must the GPU, whatever the order of the
+    entries in the cell's list.  The choice flips the sign of the collision
+    gradient's lateral part."""
+    w = I.make_workload("refined")
+    far = I.random_cloud(200, seed=5, centre=(0.0, 0.0, 1.5), spread=9.0)
+    far = far[np.linalg.norm(far - w.p0, axis=1) > 4.0]
+    pair = np.array([[1.07, 0.6, 1.5], [1.07, -0.6, 1.5]], np.float32)
+    w.cloud = np.ascontiguousarray(np.concatenate([pair, far]), np.float32)
+    w.v0 = np.array([3.0, 0.0, 0.0], np.float32)
+    w.params.update(K=64, T=20, sigma=[2.0, 0.0, 0.0, 0.0], refine_steps=0)
+    w.params.update(upd)
+    return w
+
+
+def test_tied_nearest_points_follow_the_collision_set_order(aero, orc):
+    """aero_cost_grad (one warp per sequence) at exact ties: the gradient is
+    the oracle's, which takes the lower-index point, and differs from the one
+    the other point would give."""
+    import torch
+    w = _tie_case()
+    P = w.params
+    pl, un, _, _ = _step(aero, w)
+    guides = pl.debug("GUIDES").reshape(P["E"], P["T"], 3).astype(np.float64) + w.p0
+    pts = _oracle_pts(orc, w)
+    lower = int(np.argmin([np.linalg.norm(p - [1.07, -0.6, 1.5]) for p in pts]))
+    upper = int(np.argmin([np.linalg.norm(p - [1.07, 0.6, 1.5]) for p in pts]))
+    assert lower < upper      # the y = -0.6 point comes first in the collision set
+    hover = np.zeros((P["T"], 4), np.float32)
+    hover[:, 0] = P["mass"] * P["g"]
+    U = torch.from_numpy(np.stack([hover])).cuda()
+    S = torch.empty(1, device="cuda")
+    G = torch.empty_like(U)
+    for e in range(P["E"]):
+        pl.cost_grad(e, U, S, G)
+        torch.cuda.synchronize()
+        ok, t = _clear(orc, w, hover.astype(np.float64), guides[e], pts)
+        assert ok and t["J_col"] > 0
+        S_o, G_o = orc.cost_grad(x0_of(w), hover.astype(np.float64), guides[e],
+                                 w.goal.astype(np.float64), pts, P)
+        swapped = pts.copy()
+        swapped[[lower, upper]] = swapped[[upper, lower]]
+        _, G_alt = orc.cost_grad(x0_of(w), hover.astype(np.float64), guides[e],
+                                 w.goal.astype(np.float64), swapped, P)
+        tol = TOL_GRAD * np.abs(G_o).max() + 1e-3
+        assert np.abs(G_alt - G_o).max() > 10 * tol      # the tie decides the gradient
+        g = G[0].cpu().numpy().astype(np.float64)
+        assert abs(float(S[0]) - S_o) <= TOL_COST_REL * abs(S_o)
+        assert np.abs(g - G_o).max() <= tol, e
+    pl.close()
+
+
+@pytest.mark.parametrize("batched", [False, True])
+def test_tied_nearest_points_in_the_refinement(aero, orc, batched):
+    """The refinement inside the update (the whole CTA; candidate entries as
+    item indices in a single planner's step, as the points themselves in a
+    batched step, where the winner's point is found by a second pass) at the
+    same exact ties: one tiny step equals the oracle's step from the GPU's
+    pre-refinement nominal."""
+    import torch
+    alpha = 1e-6
+    w = _tie_case(refine_steps=1, refine_step=alpha)
+    P = w.params
+    if batched:
+        dev = torch.device("cuda")
+        batch = aero.Batch(1, E_max=P["E"], K_max=P["K"], T_max=P["T"],
+                           fine_cells_max=P["fine_az"] * P["fine_el"], n_points_max=len(w.cloud))
+        un = torch.from_numpy(w.hover_nominal()).to(dev)
+        bufs = (torch.from_numpy(w.cloud).to(dev), torch.empty((P["T"], 4), device=dev),
+                torch.empty((P["E"],), device=dev), torch.empty((1,), dtype=torch.int32, device=dev))
+        batch.plan([aero.Batch.item(aero.state_struct(w.p0, w.q0, w.v0), bufs[0], w.goal,
+                                    aero.params_struct(P), un, bufs[1], bufs[2], bufs[3])])
+        torch.cuda.synchronize()
+        pre = batch.debug(0, "PRE_REFINE").reshape(P["E"], P["T"], 4).astype(np.float64)
+        guides = batch.debug(0, "GUIDES").reshape(P["E"], P["T"], 3).astype(np.float64) + w.p0
+    else:
+        pl, un, _, _ = _step(aero, w)
+        pre = pl.debug("PRE_REFINE").reshape(P["E"], P["T"], 4).astype(np.float64)
+        guides = pl.debug("GUIDES").reshape(P["E"], P["T"], 3).astype(np.float64) + w.p0
+    pts = _oracle_pts(orc, w)
+    u_gpu = un.cpu().numpy().astype(np.float64)
+    compared = 0
+    for e in range(P["E"]):
+        assert np.all(pre[e][:, 1:] == 0.0)      # no rate noise: the nominal stays in the plane
+        ok, t = _clear(orc, w, pre[e], guides[e], pts)
+        if not ok or t["J_col"] == 0:
+            continue
+        ref = orc.refine(x0_of(w), pre[e], guides[e], w.goal.astype(np.float64), pts, P)
+        _, G0 = orc.cost_grad(x0_of(w), pre[e], guides[e], w.goal.astype(np.float64), pts, P)
+        tol = alpha * (TOL_GRAD * np.abs(G0).max() + 1e-3) + 1e-6
+        assert np.abs(u_gpu[e] - ref).max() <= tol, e
+        compared += 1
+    assert compared >= P["E"] // 2
+    if batched:
+        batch.close()
+    else:
+        pl.close()

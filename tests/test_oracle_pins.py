@@ -575,3 +575,86 @@ def test_plan_step_empty_cloud(orc):
     out = orc.plan_step(np.zeros((0, 3), np.float32), w.p0, w.q0, w.v0, w.goal, P, u0)
     assert np.all(out["keys"] == orc.EMPTY)
     assert np.all(np.isfinite(out["cand"]))
+
+
+# ----------------------------------------------------------------- collision sets
+
+def _clean_cloud(rng, p0, R, P, n):
+    """n points around p0 none of which is within 1e-3 rad of a cone edge or of
+    the elevation span's ends, nor within 1e-3 m of r_max (so that binary32
+    and binary64 decisions agree), plus the degenerate points the partition
+    drops: p0 itself, non-finite coordinates, a point beyond r_max."""
+    out = []
+    while len(out) < n:
+        p = p0 + rng.uniform(-1.3, 1.3, 3) * P["r_max"]
+        b = R.T @ (p.astype(np.float32).astype(np.float64) - p0)
+        r = np.linalg.norm(b)
+        _, _, dedge = _exact_cell(b, P)
+        be = math.atan2(b[2], math.hypot(b[0], b[1]))
+        if dedge < 1e-3 or abs(r - P["r_max"]) < 1e-3:
+            continue
+        if min(abs(be - P["el_lo"]), abs(be - P["el_hi"])) < 1e-3:
+            continue
+        out.append(p)
+    out += [p0, [np.nan, 1, 1], [1, np.inf, 1], p0 + [0, 0, 3 * P["r_max"]]]
+    return np.array(out, np.float32)
+
+
+@pytest.mark.parametrize("span", [(-math.pi / 2, math.pi / 2), (-0.4, 0.9)])
+def test_collision_sets_by_enumeration(orc, span):
+    """Sec. IV-C's filtered cloud P_f: the nearest point of every non-empty
+    cone, in world coordinates, in cone order; and the every-point set: the
+    points the partition keeps (finite, 0 < r <= r_max, inside the elevation
+    span), in point order.  Both by enumeration with binary64 angles on a
+    rotated start, so a wrong frame, a wrong half of the packed key or a
+    filter that keeps points outside the span or range fails."""
+    P = I.default_params()
+    P.update(fine_az=24, fine_el=12, r_max=5.0, el_lo=span[0], el_hi=span[1])
+    rng = np.random.default_rng(17)
+    q0 = I.random_unit_quaternion(rng)
+    p0 = np.array([1.5, -2.0, 0.7], np.float32)
+    R = _scipy_R(q0.astype(np.float64))
+    p0d = p0.astype(np.float64)
+    cloud = _clean_cloud(rng, p0d, R, P, 400)
+    best, kept = {}, []
+    for idx, p in enumerate(cloud.astype(np.float64)):
+        if not np.all(np.isfinite(p)):
+            continue
+        b = R.T @ (p - p0d)
+        r = np.linalg.norm(b)
+        if r == 0.0 or r > P["r_max"]:
+            continue
+        be = math.atan2(b[2], math.hypot(b[0], b[1]))
+        if not (P["el_lo"] <= be <= P["el_hi"]):
+            continue
+        kept.append(idx)
+        i, j, _ = _exact_cell(b, P)
+        c = j * P["fine_az"] + i
+        if c not in best or r < best[c][0]:
+            best[c] = (r, idx)
+    keys, n_kept = orc.partition(cloud, p0, q0, P)
+    assert n_kept == len(kept)
+    pf = orc.collision_set(cloud, p0, q0, keys, dict(P, collision_set=0))
+    want = np.array([cloud[best[c][1]] for c in sorted(best)], np.float64).reshape(-1, 3)
+    assert pf.shape == want.shape and np.array_equal(pf, want)
+    raw = orc.collision_set(cloud, p0, q0, keys, dict(P, collision_set=1))
+    assert np.array_equal(raw, cloud[kept].astype(np.float64))
+    if span[1] - span[0] < math.pi:
+        # the narrow span drops points that the full sphere keeps
+        full = orc.collision_set(cloud, p0, q0, keys, dict(P, collision_set=1, el_lo=-math.pi / 2,
+                                                           el_hi=math.pi / 2))
+        assert len(full) > len(raw)
+
+
+def test_collision_set_of_empty_and_single_point_clouds(orc):
+    P = I.default_params()
+    p0 = np.array([0.0, 0.0, 1.0], np.float32)
+    q0 = np.array([1, 0, 0, 0], np.float32)
+    empty = np.zeros((0, 3), np.float32)
+    keys, _ = orc.partition(empty, p0, q0, P)
+    assert len(orc.collision_set(empty, p0, q0, keys, dict(P, collision_set=0))) == 0
+    one = np.array([[3.0, 0.5, 1.25]], np.float32)
+    keys, _ = orc.partition(one, p0, q0, P)
+    for mode in (0, 1):
+        s = orc.collision_set(one, p0, q0, keys, dict(P, collision_set=mode))
+        assert np.array_equal(s, one.astype(np.float64))
