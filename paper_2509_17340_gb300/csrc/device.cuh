@@ -150,6 +150,66 @@ __device__ __forceinline__ void rk4_step(State& x, float4 u, const DynParams& dp
   x.q[3] = n3 * inv;
 }
 
+// The same step split by dependence (Stage II's noise-free rollouts): the
+// attitude update does not depend on p or v, so a trajectory's quaternions can
+// be chained alone.  With b = ca / 2, the unnormalised q+ = cq q + ca A q is
+// the map M q, M = [[cq, -b wx, -b wy, -b wz], [b wx, cq, b wz, -b wy],
+// [b wy, -b wz, cq, b wx], [b wz, b wy, -b wx, cq]]; rk4_attitude_coefs gives
+// (cq, b wx, b wy, b wz) of a step and attitude_map applies M and renormalises.
+__device__ __forceinline__ float4 rk4_attitude_coefs(float4 u, const DynParams& dp) {
+  const float h = dp.dt;
+  const float s = 0.25f * (u.y * u.y + u.z * u.z + u.w * u.w);
+  const float hh = h * h * s;
+  const float cq = 1.0f - 0.5f * hh + hh * hh * (1.0f / 24.0f);
+  const float b = 0.5f * h * (1.0f - hh * (1.0f / 6.0f));
+  return make_float4(cq, b * u.y, b * u.z, b * u.w);
+}
+
+__device__ __forceinline__ void attitude_map(float4 m, float* q) {
+  const float n0 = m.x * q[0] - m.y * q[1] - m.z * q[2] - m.w * q[3];
+  const float n1 = m.y * q[0] + m.x * q[1] + m.w * q[2] - m.z * q[3];
+  const float n2 = m.z * q[0] - m.w * q[1] + m.x * q[2] + m.y * q[3];
+  const float n3 = m.w * q[0] + m.z * q[1] - m.y * q[2] + m.x * q[3];
+  const float inv = rsqrtf(n0 * n0 + n1 * n1 + n2 * n2 + n3 * n3);
+  q[0] = n0 * inv;
+  q[1] = n1 * inv;
+  q[2] = n2 * inv;
+  q[3] = n3 * inv;
+}
+
+// The position and velocity increments of one step from the step's start
+// attitude q and control u (the RK4 stage sums of rk4_step):
+// p+ = p + h v + inc[0..2], v+ = v + inc[3..5].
+__device__ __forceinline__ void rk4_translation_increments(const float* q, float4 u, const DynParams& dp,
+                                                           float* inc) {
+  const float h = dp.dt;
+  const float wx = u.y, wy = u.z, wz = u.w;
+  const float a0 = 0.5f * (-q[1] * wx - q[2] * wy - q[3] * wz);
+  const float a1 = 0.5f * (q[0] * wx + q[2] * wz - q[3] * wy);
+  const float a2 = 0.5f * (q[0] * wy - q[1] * wz + q[3] * wx);
+  const float a3 = 0.5f * (q[0] * wz + q[1] * wy - q[2] * wx);
+  const float s = 0.25f * (wx * wx + wy * wy + wz * wz);
+  const float hh = h * h * s;
+  const float c3 = 1.0f - 0.25f * hh, c4 = 1.0f - 0.5f * hh;
+  const float hb = 0.5f * h, h4 = h * c3;
+  float r1x, r1y, r1z, r2x, r2y, r2z, r3x, r3y, r3z, r4x, r4y, r4z;
+  r_e3(q[0], q[1], q[2], q[3], r1x, r1y, r1z);
+  r_e3(q[0] + hb * a0, q[1] + hb * a1, q[2] + hb * a2, q[3] + hb * a3, r2x, r2y, r2z);
+  r_e3(c3 * q[0] + hb * a0, c3 * q[1] + hb * a1, c3 * q[2] + hb * a2, c3 * q[3] + hb * a3, r3x,
+       r3y, r3z);
+  r_e3(c4 * q[0] + h4 * a0, c4 * q[1] + h4 * a1, c4 * q[2] + h4 * a2, c4 * q[3] + h4 * a3, r4x,
+       r4y, r4z);
+  const float f = u.x * dp.inv_mass;
+  const float fp = h * h * (1.0f / 6.0f) * f, fv = h * (1.0f / 6.0f) * f;
+  const float gp = 0.5f * h * h * dp.g, gv = h * dp.g;
+  inc[0] = fp * (r1x + r2x + r3x);
+  inc[1] = fp * (r1y + r2y + r3y);
+  inc[2] = fp * (r1z + r2z + r3z) - gp;
+  inc[3] = fv * (r1x + 2.0f * (r2x + r3x) + r4x);
+  inc[4] = fv * (r1y + 2.0f * (r2y + r3y) + r4y);
+  inc[5] = fv * (r1z + 2.0f * (r2z + r3z) + r4z) - gv;
+}
+
 // ---------------------------------------------------------------------------
 // Collision queries on the candidate lists.  The list of the query's cell holds
 // every collision point closer than d_max to that cell's box, so the nearest

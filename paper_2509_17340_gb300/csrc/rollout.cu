@@ -664,19 +664,45 @@ __device__ __forceinline__ void update_unit(const UpdateArgs& a, int e, bool fin
     __syncthreads();
   }
 
-  // Stage II: noise-free rollout of the (updated, refined) nominal
+  // Stage II: noise-free rollout of the (updated, refined) nominal, split by
+  // dependence (the attitude does not depend on p or v): the attitude maps of
+  // all steps in parallel, one thread chaining them; then every step's
+  // position and velocity increments in parallel; then one thread summing
+  // them in step order.  The merge's scratch (acc) is free again and holds
+  // the maps and the increments (40 T bytes of its 64 T or more).
+  static_assert(UT / 32 >= 3, "the merge's scratch holds Stage II's maps and increments");
+  float4* const s_att = sm.acc;                                  // [T]
+  float* const s_inc = reinterpret_cast<float*>(sm.acc + T);     // [T][6]
+  for (int j = tid; j < T; j += UT) s_att[j] = rk4_attitude_coefs(s_u4[j], a.dyn);
+  __syncthreads();
   if (tid == 0) {
-    State x;
-    for (int i = 0; i < 3; ++i) x.p[i] = a.x0[i];
-    for (int i = 0; i < 4; ++i) x.q[i] = a.x0[3 + i];
-    for (int i = 0; i < 3; ++i) x.v[i] = a.x0[7 + i];
+    float q[4] = {a.x0[3], a.x0[4], a.x0[5], a.x0[6]};
     for (int i = 0; i < 10; ++i) s_x[i] = a.x0[i];
     for (int j = 0; j < T; ++j) {
-      rk4_step(x, s_u4[j], a.dyn);
+      attitude_map(s_att[j], q);
+      float* X = s_x + (j + 1) * 10 + 3;
+      X[0] = q[0];
+      X[1] = q[1];
+      X[2] = q[2];
+      X[3] = q[3];
+    }
+  }
+  __syncthreads();
+  for (int j = tid; j < T; j += UT) rk4_translation_increments(s_x + j * 10 + 3, s_u4[j], a.dyn, s_inc + 6 * j);
+  __syncthreads();
+  if (tid == 0) {
+    const float h = a.dyn.dt;
+    float p[3] = {a.x0[0], a.x0[1], a.x0[2]}, v[3] = {a.x0[7], a.x0[8], a.x0[9]};
+    for (int j = 0; j < T; ++j) {
+      const float* inc = s_inc + 6 * j;
       float* X = s_x + (j + 1) * 10;
-      for (int i = 0; i < 3; ++i) X[i] = x.p[i];
-      for (int i = 0; i < 4; ++i) X[3 + i] = x.q[i];
-      for (int i = 0; i < 3; ++i) X[7 + i] = x.v[i];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        p[c] += h * v[c] + inc[c];
+        v[c] += inc[3 + c];
+        X[c] = p[c];
+        X[7 + c] = v[c];
+      }
     }
   }
   __syncthreads();
