@@ -193,6 +193,9 @@ namespace {
 // A point joins the lists of the cells within `reach` (just above d_max) of it:
 // at most 6^3 cells of edge d_max / 2, at most 3^3 of edge d_max (1 + 1/16).
 constexpr int kFineDup = 216, kCoarseDup = 27;
+// points per fine cone from which the partition reads a cone's key before its
+// atomic minimum: in dense clouds most points cannot lower their cone's key
+constexpr int64_t kPartFilterPointsPerCone = 32;
 
 int cuda_fail(cudaError_t e) {
   if (e == cudaSuccess) return AERO_OK;
@@ -430,6 +433,7 @@ void make_step_args(aero_planner* pl, const aero_state_t* x0, const float* cloud
   pa.El = p.fine_el;
   pa.check_lo = a.check_lo;
   pa.check_hi = a.check_hi;
+  pa.filter = n >= kPartFilterPointsPerCone * (int64_t)a.ncell;
   pa.keys = pl->keys;
   pa.item_flag = a.raw ? pl->item_flag : nullptr;
   pa.counts = pl->part_counts;
@@ -517,6 +521,10 @@ void make_step_args(aero_planner* pl, const aero_state_t* x0, const float* cloud
   for (int i = 0; i < 10; ++i) ra.x0[i] = x0v[i];
   ra.key0 = (uint32_t)p.seed;
   ra.key1 = (uint32_t)(p.seed >> 32);
+  for (int r = 0; r < 10; ++r) {  // Philox4x32-10's key schedule (32-bit wrap-around)
+    ra.rk[2 * r] = ra.key0 + (uint32_t)r * 0x9E3779B9u;
+    ra.rk[2 * r + 1] = ra.key1 + (uint32_t)r * 0xBB67AE85u;
+  }
   ra.ctr3 = (uint32_t)(p.step_id << 8);
   ra.dyn = dp;
   ra.cost = cp;

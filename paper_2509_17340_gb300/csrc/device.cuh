@@ -39,9 +39,25 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1
   return c;
 }
 
-// (2 (w >> 9) + 1) 2^-24: exact in binary32, in (0, 1).
+// The same rounds with the key schedule given: rk[2r], rk[2r + 1] are the
+// key words of round r (the key plus r times the Weyl constants).  Kernels
+// whose arguments live in the parameter space read them as constant operands.
+__device__ __forceinline__ uint4 philox4x32_10_rk(uint4 c, const uint32_t* rk) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint64_t p0 = (uint64_t)0xD2511F53u * c.x;
+    const uint64_t p1 = (uint64_t)0xCD9E8D57u * c.z;
+    c = make_uint4((uint32_t)(p1 >> 32) ^ c.y ^ rk[2 * r], (uint32_t)p1,
+                   (uint32_t)(p0 >> 32) ^ c.w ^ rk[2 * r + 1], (uint32_t)p0);
+  }
+  return c;
+}
+
+// (2 (w >> 9) + 1) 2^-24: exact in binary32, in (0, 1).  Built from the bits:
+// 1 + (w >> 9) 2^-23 has those mantissa bits, and subtracting 1 - 2^-24 is
+// exact (Sterbenz), leaving (w >> 9) 2^-23 + 2^-24 with no integer conversion.
 __device__ __forceinline__ float uniform01(uint32_t w) {
-  return static_cast<float>(2u * (w >> 9) + 1u) * 5.9604644775390625e-8f;
+  return __uint_as_float(0x3F800000u | (w >> 9)) - 0.99999994039535522f;
 }
 
 // sqrt(x) for x >= 0 as x * rsqrt(x): a few ulp, three instructions.
@@ -79,6 +95,13 @@ __device__ __forceinline__ float4 normals4(uint4 w) {
 __device__ __forceinline__ float4 noise_delta(uint32_t k, uint32_t j, uint32_t e, uint32_t c3,
                                               uint32_t k0, uint32_t k1, float4 sigma) {
   const float4 n = normals4(philox4x32_10(make_uint4(k, j, e, c3), k0, k1));
+  return make_float4(sigma.x * n.x, sigma.y * n.y, sigma.z * n.z, sigma.w * n.w);
+}
+
+// The same from the round keys (see philox4x32_10_rk).
+__device__ __forceinline__ float4 noise_delta_rk(uint32_t k, uint32_t j, uint32_t e, uint32_t c3,
+                                                 const uint32_t* rk, float4 sigma) {
+  const float4 n = normals4(philox4x32_10_rk(make_uint4(k, j, e, c3), rk));
   return make_float4(sigma.x * n.x, sigma.y * n.y, sigma.z * n.z, sigma.w * n.w);
 }
 

@@ -55,6 +55,7 @@ struct PartitionArgs {
   float rmax2;     // r_max * r_max in binary32
   int A, El;
   int check_lo, check_hi;
+  int filter;      // read a cone's key before its atomic minimum (dense clouds)
   unsigned long long* keys;
   int* item_flag;  // collision set = every kept point: 1 where the point is kept, else 0
   int2* counts;    // per block (batched: per chunk of points): {non-finite points, kept points}
@@ -129,6 +130,7 @@ struct RolloutArgs {
   float sigma[4], umin[4], umax[4];
   float x0[10];            // p = 0 (relative), q0, v0
   uint32_t key0, key1, ctr3;
+  uint32_t rk[20];         // Philox round keys: (key0, key1) + r (Weyl constants), r = 0..9
   DynParams dyn;
   CostParams cost;
   const float* u_nom;      // E x T x 4

@@ -99,7 +99,11 @@ __device__ __forceinline__ int partition_point(const PartitionArgs& a, const Sme
         const unsigned long long key =
             ((unsigned long long)__float_as_uint(r2) << 32) | (unsigned long long)(uint32_t)i;
         if (AERO_CHECK(c >= 0 && c < a.A * a.El, kChkFineCell)) {
-          atomicMin(a.keys + c, key);
+          // dense clouds: a key at or above the cone's current minimum cannot
+          // lower it, so the atomic is skipped.  Keys only decrease during the
+          // pass, so a value read earlier is never below the current one and
+          // the test skips no atomic that would lower the key.
+          if (!a.filter || key < __ldcg(a.keys + c)) atomicMin(a.keys + c, key);
           cell = c;
         }
       }

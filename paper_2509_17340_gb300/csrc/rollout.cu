@@ -81,13 +81,22 @@ __device__ __forceinline__ void rollout_unit(const RolloutArgs& a, int e, int b,
   CostSum S;
   // step j's control: prefetched noise, clamp, J_ctrl's
   // terms Q_c |u_j|^2 (j <= T-2) and Q_cd |u_j - u_{j-1}|^2 (1 <= j <= T-2)
-  float4 d_next = noise_delta(k, 0, e, ctr3, a.key0, a.key1, sigma);
+  // a single planner's arguments are kernel parameters: the Philox round keys
+  // are read as constant operands; the batched kernels' are in shared memory,
+  // where recomputing the schedule is cheaper than reading it
+  auto noise = [&](uint32_t kk, uint32_t j) {
+    if constexpr (kIdx)
+      return noise_delta_rk(kk, j, e, ctr3, a.rk, sigma);
+    else
+      return noise_delta(kk, j, e, ctr3, a.key0, a.key1, sigma);
+  };
+  float4 d_next = noise(k, 0);
   float4 un_next = s_un[0];
   float4 u_prev = make_float4(0.f, 0.f, 0.f, 0.f);
   auto control = [&](int j, float& c_ctrl) -> float4 {
     const float4 un = un_next, d = d_next;
     if (j + 1 < T) {
-      d_next = noise_delta(k, j + 1, e, ctr3, a.key0, a.key1, sigma);
+      d_next = noise(k, j + 1);
       un_next = s_un[j + 1];
     }
     const float4 u = clamp4(make_float4(un.x + d.x, un.y + d.y, un.z + d.z, un.w + d.w), umin, umax);
@@ -188,7 +197,7 @@ __device__ __forceinline__ void rollout_unit(const RolloutArgs& a, int e, int b,
     float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
     for (int i = r; i < nz; i += R) {
       const float w = s_lw[i];
-      const float4 d = noise_delta(s_lk[i], j, e, ctr3, a.key0, a.key1, sigma);
+      const float4 d = noise(s_lk[i], j);
       const float4 u = clamp4(make_float4(un.x + d.x, un.y + d.y, un.z + d.z, un.w + d.w), umin, umax);
       acc.x += w * (u.x - un.x);
       acc.y += w * (u.y - un.y);
