@@ -142,7 +142,7 @@ __device__ __forceinline__ float state_terms(const State& x, float gx, float gy,
       gs[6] += a * qg[2] - b * qg[1] + e * qg[0];
     }
     if (d2 < dmax2) {
-      const float d = sqrtf(d2);
+      const float d = fast_sqrt(d2);  // as jcol_from_d2 takes it: the same branch of J_col
       if (d >= cp.d_min && d > 0.0f) {
         const float s = -cp.a_col * jc / d;
         gs[0] += s * (x.p[0] - nearest.x);
