@@ -139,28 +139,38 @@ __device__ __forceinline__ void r_e3(float w, float x, float y, float z, float& 
   rz = 1.0f - 2.0f * (x * x + y * y);
 }
 
+// Half of R(q) e3: (xz + wy, yz - wx, 1/2 - x^2 - y^2); rk4_step folds the
+// factor 2 into its thrust coefficients.
+__device__ __forceinline__ void r_e3_half(float w, float x, float y, float z, float& rx, float& ry,
+                                          float& rz) {
+  rx = x * z + w * y;
+  ry = y * z - w * x;
+  rz = 0.5f - x * x - y * y;
+}
+
 __device__ __forceinline__ void rk4_step(State& x, float4 u, const DynParams& dp) {
   const float h = dp.dt;
-  const float wx = u.y, wy = u.z, wz = u.w;
+  // half rates: A q = 1/2 q (x) [0, w] = q (x) [0, w/2]
+  const float hx = 0.5f * u.y, hy = 0.5f * u.z, hz = 0.5f * u.w;
   const float* q = x.q;
-  // A q = 1/2 q (x) [0, w]
-  const float a0 = 0.5f * (-q[1] * wx - q[2] * wy - q[3] * wz);
-  const float a1 = 0.5f * (q[0] * wx + q[2] * wz - q[3] * wy);
-  const float a2 = 0.5f * (q[0] * wy - q[1] * wz + q[3] * wx);
-  const float a3 = 0.5f * (q[0] * wz + q[1] * wy - q[2] * wx);
-  const float s = 0.25f * (wx * wx + wy * wy + wz * wz);
+  const float a0 = -q[1] * hx - q[2] * hy - q[3] * hz;
+  const float a1 = q[0] * hx + q[2] * hz - q[3] * hy;
+  const float a2 = q[0] * hy - q[1] * hz + q[3] * hx;
+  const float a3 = q[0] * hz + q[1] * hy - q[2] * hx;
+  const float s = hx * hx + hy * hy + hz * hz;  // |w|^2 / 4
   const float hh = h * h * s;
   const float c3 = 1.0f - 0.25f * hh, c4 = 1.0f - 0.5f * hh;
   const float hb = 0.5f * h, h4 = h * c3;
+  const float b0 = hb * a0, b1 = hb * a1, b2 = hb * a2, b3 = hb * a3;
   float r1x, r1y, r1z, r2x, r2y, r2z, r3x, r3y, r3z, r4x, r4y, r4z;
-  r_e3(q[0], q[1], q[2], q[3], r1x, r1y, r1z);
-  r_e3(q[0] + hb * a0, q[1] + hb * a1, q[2] + hb * a2, q[3] + hb * a3, r2x, r2y, r2z);
-  r_e3(c3 * q[0] + hb * a0, c3 * q[1] + hb * a1, c3 * q[2] + hb * a2, c3 * q[3] + hb * a3, r3x,
-       r3y, r3z);
-  r_e3(c4 * q[0] + h4 * a0, c4 * q[1] + h4 * a1, c4 * q[2] + h4 * a2, c4 * q[3] + h4 * a3, r4x,
-       r4y, r4z);
+  r_e3_half(q[0], q[1], q[2], q[3], r1x, r1y, r1z);
+  r_e3_half(q[0] + b0, q[1] + b1, q[2] + b2, q[3] + b3, r2x, r2y, r2z);
+  r_e3_half(c3 * q[0] + b0, c3 * q[1] + b1, c3 * q[2] + b2, c3 * q[3] + b3, r3x, r3y, r3z);
+  r_e3_half(c4 * q[0] + h4 * a0, c4 * q[1] + h4 * a1, c4 * q[2] + h4 * a2, c4 * q[3] + h4 * a3, r4x,
+            r4y, r4z);
   const float f = u.x * dp.inv_mass;
-  const float fp = h * h * (1.0f / 6.0f) * f, fv = h * (1.0f / 6.0f) * f;
+  // h^2/6 f and h/6 f times R e3 = 2 (the half above)
+  const float fp = h * h * (1.0f / 3.0f) * f, fv = h * (1.0f / 3.0f) * f;
   const float gp = 0.5f * h * h * dp.g, gv = h * dp.g;
   x.p[0] += h * x.v[0] + fp * (r1x + r2x + r3x);
   x.p[1] += h * x.v[1] + fp * (r1y + r2y + r3y);
@@ -247,12 +257,14 @@ __device__ __forceinline__ void rk4_translation_increments(const float* q, float
 // the nearest point if that is below d_max^2, else d_max^2.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ int2 cell_range(float px, float py, float pz, const GridView& g) {
-  const float fx = (px - g.origin) * g.inv_h;
-  const float fy = (py - g.origin) * g.inv_h;
-  const float fz = (pz - g.origin) * g.inv_h;
-  const float Gf = (float)g.G;
-  if (fx >= 0.0f && fy >= 0.0f && fz >= 0.0f && fx < Gf && fy < Gf && fz < Gf)
-    return __ldg(g.range + ((int)fz * g.G + (int)fy) * g.G + (int)fx);
+  // (p - origin) / h as one multiply-add; a query rounded into a neighbouring
+  // cell is within rounding of that cell's box, inside the lists' reach margin
+  const float o = -g.origin * g.inv_h;
+  const int ix = __float2int_rd(fmaf(px, g.inv_h, o));
+  const int iy = __float2int_rd(fmaf(py, g.inv_h, o));
+  const int iz = __float2int_rd(fmaf(pz, g.inv_h, o));
+  if ((unsigned)ix < (unsigned)g.G && (unsigned)iy < (unsigned)g.G && (unsigned)iz < (unsigned)g.G)
+    return __ldg(g.range + (iz * g.G + iy) * g.G + ix);
   return make_int2(0, 0);
 }
 
