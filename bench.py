@@ -841,8 +841,7 @@ def bench_batched(aero, args, dev, stream, flush, rank: int, dist=None) -> dict:
     # one-off autotuning of the launch configuration (outside the timed region;
     # it writes only the batch's scratch buffers)
     if args.batch_config:
-        q, c, d, g = (int(x) for x in args.batch_config.split(","))
-        batch.set_config(q, c, d, g)
+        batch.set_config(*(int(x) for x in args.batch_config.split(",")))
         tuned, tune_ms = batch.config(), None
     else:
         tuned, tune_ms = batch.tune(plans[0], repeats=3, stream=stream)
@@ -1005,7 +1004,7 @@ def main():
                     help="batched workload: number of planners (64 is the measured configuration)")
     ap.add_argument("--batch-config", default="",
                     help="batched workload: fixed launch configuration 'quad_max,ctas_per_sm,"
-                         "dynamic,coarse' instead of autotuning")
+                         "dynamic,coarse[,samples_per_cta]' instead of autotuning")
     ap.add_argument("--reference-budget", type=float, default=REFERENCE_BUDGET_S,
                     help="reference arm: wall seconds its whole run aims at")
     ap.add_argument("--sweep-max", type=int, default=10**8,

@@ -273,12 +273,17 @@ typedef struct {
                                   entries to build, longer lists to scan); 0: edge d_max / 2 when
                                   the candidate array can hold it.  Results do not depend on it:
                                   every list holds the nearest point of every query within d_max */
+  int32_t samples_per_cta;     /* samples (threads) per CTA of the one-lane Stage I pass: 64, 128
+                                  or 256 (0 = 128); rollout_ctas_per_sm counts CTAs of 128
+                                  threads and is scaled for the other sizes.  The floating-point
+                                  results agree to rounding (the per-CTA partial sums group the
+                                  samples differently) */
 } aero_batch_config_t;
 
 /* Create a batch of up to n_max <= 256 item slots, each with a planner
  * workspace sized by `limits` (every item of a call must fit them; the limits'
  * debug_samples_max is ignored).  The default configuration is
- * {0, 0, 1, 0}.  Errors: INVALID_ARG, ALLOC, CUDA. */
+ * {0, 0, 1, 0, 0}.  Errors: INVALID_ARG, ALLOC, CUDA. */
 int aero_batch_create(const aero_limits_t* limits, int32_t n_max, aero_batch_t** out);
 
 /* Enqueue the n <= n_max steps of `items` (host array; item i uses slot i) on
@@ -294,8 +299,8 @@ int aero_batch_get_config(aero_batch_t* batch, aero_batch_config_t* config);
 
 /* Autotune: time every configuration of a small search space (quad_max_samples
  * in {0, 4096, 32768}; rollout_ctas_per_sm in {as many as fit, 6, half of the
- * fewest that fit};
- * dynamic_queue in {1, 0}; coarse_cells in {0, 1}) on `items`, `repeats` timed calls each after one
+ * fewest that fit}; dynamic_queue in {1, 0}; coarse_cells in {0, 1};
+ * samples_per_cta in {128, 64, 256}: 108 configurations) on `items`, `repeats` timed calls each after one
  * warm-up, keep the fastest as the batch's configuration and return it with
  * its mean time in *best_ms.  The items' clouds and states are read; the
  * outputs go to scratch buffers of the batch, so the items' u_nom_inout and

@@ -79,12 +79,13 @@ class BatchItem(C.Structure):
 
 class BatchConfig(C.Structure):
     _fields_ = [("quad_max_samples", C.c_int32), ("rollout_ctas_per_sm", C.c_int32),
-                ("dynamic_queue", C.c_int32), ("coarse_cells", C.c_int32)]
+                ("dynamic_queue", C.c_int32), ("coarse_cells", C.c_int32),
+                ("samples_per_cta", C.c_int32)]
 
     def as_dict(self) -> dict:
         return {"quad_max_samples": self.quad_max_samples,
                 "rollout_ctas_per_sm": self.rollout_ctas_per_sm, "dynamic_queue": self.dynamic_queue,
-                "coarse_cells": self.coarse_cells}
+                "coarse_cells": self.coarse_cells, "samples_per_cta": self.samples_per_cta}
 
 
 _vp = C.c_void_p
@@ -432,8 +433,9 @@ class Batch:
         return c.as_dict()
 
     def set_config(self, quad_max_samples=0, rollout_ctas_per_sm=0, dynamic_queue=1,
-                   coarse_cells=0) -> None:
-        c = BatchConfig(quad_max_samples, rollout_ctas_per_sm, dynamic_queue, coarse_cells)
+                   coarse_cells=0, samples_per_cta=0) -> None:
+        c = BatchConfig(quad_max_samples, rollout_ctas_per_sm, dynamic_queue, coarse_cells,
+                        samples_per_cta)
         _check(_lib.aero_batch_set_config(self._h, C.byref(c)), "aero_batch_set_config")
 
     def tune(self, items, repeats=3, stream=None):

@@ -397,7 +397,7 @@ int lanes_of(const aero_params_t& p, int64_t quad_max) {
 void make_step_args(aero_planner* pl, const aero_state_t* x0, const float* cloud, int64_t n,
                     const float* goal, const aero_params_t& p, float* u_nom, float* u_best,
                     float* cand, int32_t* best_idx, int lanes, bool coarse, bool idx_entries,
-                    StepArgs& a) {
+                    StepArgs& a, int samples_per_cta = kRolloutThreads) {
   a.ncell = p.fine_az * p.fine_el;
   // the edge tables depend only on the partition geometry: recomputed when it changes
   if (!pl->tab_valid || pl->tab_A != p.fine_az || pl->tab_El != p.fine_el || pl->tab_lo != p.el_lo ||
@@ -434,6 +434,8 @@ void make_step_args(aero_planner* pl, const aero_state_t* x0, const float* cloud
   pa.check_lo = a.check_lo;
   pa.check_hi = a.check_hi;
   pa.filter = n >= kPartFilterPointsPerCone * (int64_t)a.ncell;
+  pa.el_lo = p.el_lo;
+  pa.el_inv = (float)p.fine_el / (p.el_hi - p.el_lo);
   pa.keys = pl->keys;
   pa.item_flag = a.raw ? pl->item_flag : nullptr;
   pa.counts = pl->part_counts;
@@ -503,7 +505,8 @@ void make_step_args(aero_planner* pl, const aero_state_t* x0, const float* cloud
   const float x0v[10] = {0.0f, 0.0f, 0.0f, x0->q[0], x0->q[1], x0->q[2], x0->q[3],
                          x0->v[0], x0->v[1], x0->v[2]};
   a.lanes = lanes;
-  const int per_cta = kRolloutThreads / lanes;
+  // samples per Stage I CTA: 32 in the split pass, else the one-lane pass's CTA size
+  const int per_cta = lanes == 4 ? kRolloutThreads / 4 : samples_per_cta;
   a.nb = (p.K + per_cta - 1) / per_cta;
 
   RolloutArgs& ra = a.ra;
@@ -1245,11 +1248,13 @@ struct aero_batch {
   std::vector<aero_planner*> planners;  // one workspace per item slot
   aero_limits_t lim{};
   int sms = 0;
-  aero_batch_config_t cfg{0, 0, 1, 0};
+  aero_batch_config_t cfg{0, 0, 1, 0, 0};
   int last_n = 0;  // items of the last call (debug copies)
   // resident CTAs per SM of the batched kernels
   int occ_grid[4] = {1, 1, 1, 1};  // partition, count, scan, scatter
-  int occ_roll[4] = {1, 1, 1, 1};  // rollout (1 lane), rollout (4 lanes), update, rollout (1 lane, 6/SM)
+  // rollout (1 lane), rollout (4 lanes), update, rollout (1 lane, 6/SM), rollout (1 lane, 64
+  // samples per CTA), rollout (1 lane, 256 samples per CTA)
+  int occ_roll[6] = {1, 1, 1, 1, 1, 1};
   // device: the call's arguments (items, unit prefixes, rollout orders), the
   // slots' edge tables, the rollout work queues
   unsigned char* d_args = nullptr;
@@ -1348,16 +1353,22 @@ int check_item(aero_planner* pl, const aero_batch_item_t& it) {
   return AERO_OK;
 }
 
+// Samples per CTA of the one-lane Stage I pass of a configuration.
+int spc_of(const aero_batch_config_t& c) { return c.samples_per_cta == 0 ? kRolloutThreads : c.samples_per_cta; }
+
 int check_config(const aero_batch_config_t& c) {
   if (c.quad_max_samples < 0 || c.rollout_ctas_per_sm < 0 || c.rollout_ctas_per_sm > 64 ||
-      (c.dynamic_queue != 0 && c.dynamic_queue != 1) || (c.coarse_cells != 0 && c.coarse_cells != 1))
+      (c.dynamic_queue != 0 && c.dynamic_queue != 1) || (c.coarse_cells != 0 && c.coarse_cells != 1) ||
+      (c.samples_per_cta != 0 && c.samples_per_cta != 64 && c.samples_per_cta != 128 &&
+       c.samples_per_cta != 256))
     return AERO_ERR_INVALID_ARG;
   return AERO_OK;
 }
 
 bool same_cfg(const aero_batch_config_t& a, const aero_batch_config_t& b) {
   return a.quad_max_samples == b.quad_max_samples && a.rollout_ctas_per_sm == b.rollout_ctas_per_sm &&
-         a.dynamic_queue == b.dynamic_queue && a.coarse_cells == b.coarse_cells;
+         a.dynamic_queue == b.dynamic_queue && a.coarse_cells == b.coarse_cells &&
+         spc_of(a) == spc_of(b);
 }
 
 // The graph of one call shape: the four grid-stage launches, then per
@@ -1373,11 +1384,17 @@ cudaError_t batch_graph(aero_batch* b, int n, int max_iters, int has1, int has4,
     }
   const BatchView v = view_of(b, n);
   const int S = b->sms;
-  // rollout_ctas_per_sm >= 6 selects the one-lane kernel built for six CTAs per SM
-  const int six = cfg.rollout_ctas_per_sm >= 6 && b->occ_roll[3] >= 6;
+  // rollout_ctas_per_sm >= 6 selects the one-lane kernel built for six CTAs per
+  // SM (128 samples per CTA); it counts CTAs of 128 threads, so other CTA
+  // sizes of the one-lane pass scale it
+  const int spc = spc_of(cfg);
+  const int six = spc == kRolloutThreads && cfg.rollout_ctas_per_sm >= 6 && b->occ_roll[3] >= 6;
   auto roll_blocks = [&](int k) {
-    const int occ = k == 0 && six ? b->occ_roll[3] : b->occ_roll[k];
-    const int per = cfg.rollout_ctas_per_sm == 0 ? occ : cfg.rollout_ctas_per_sm;
+    int occ = b->occ_roll[k];
+    if (k == 0) occ = six ? b->occ_roll[3] : spc == 64 ? b->occ_roll[4] : spc == 256 ? b->occ_roll[5] : occ;
+    int per = occ;
+    if (cfg.rollout_ctas_per_sm != 0)
+      per = k == 0 ? cfg.rollout_ctas_per_sm * kRolloutThreads / spc : cfg.rollout_ctas_per_sm;
     return S * (per < 1 ? 1 : per);
   };
   cudaStream_t c = b->cap;
@@ -1392,13 +1409,14 @@ cudaError_t batch_graph(aero_batch* b, int n, int max_iters, int has1, int has4,
       le = cudaEventRecord(b->fork, c);
       if (le == cudaSuccess) le = cudaStreamWaitEvent(b->cap2, b->fork, 0);
       if (le == cudaSuccess)
-        le = launch_batch_rollout(v, 4, it, roll_blocks(1), cfg.dynamic_queue, 0, b->cap2);
-      if (le == cudaSuccess) le = launch_batch_rollout(v, 1, it, roll_blocks(0), cfg.dynamic_queue, six, c);
+        le = launch_batch_rollout(v, 4, it, roll_blocks(1), cfg.dynamic_queue, 0, spc, b->cap2);
+      if (le == cudaSuccess)
+        le = launch_batch_rollout(v, 1, it, roll_blocks(0), cfg.dynamic_queue, six, spc, c);
       if (le == cudaSuccess) le = cudaEventRecord(b->join, b->cap2);
       if (le == cudaSuccess) le = cudaStreamWaitEvent(c, b->join, 0);
     } else {
       le = launch_batch_rollout(v, has4 ? 4 : 1, it, roll_blocks(has4 ? 1 : 0), cfg.dynamic_queue,
-                                has4 ? 0 : six, c);
+                                has4 ? 0 : six, spc, c);
     }
     if (le == cudaSuccess) le = launch_batch_update(v, it, S * b->occ_roll[2], c);
   }
@@ -1460,7 +1478,7 @@ int batch_enqueue(aero_batch* b, const aero_batch_item_t* items, int n, cudaStre
     }
     StepArgs a;
     make_step_args(pl, &it.x0, it.cloud_xyz, it.n_points, it.goal, p, u_nom, u_best, cand, best,
-                   lanes_of(p, cfg.quad_max_samples), cfg.coarse_cells != 0, false, a);
+                   lanes_of(p, cfg.quad_max_samples), cfg.coarse_cells != 0, false, a, spc_of(cfg));
     BatchItem& bi = hi[i];
     bi.pa = a.pa;
     bi.ca = a.ca;
@@ -1664,11 +1682,13 @@ int aero_batch_tune(aero_batch_t* b, const aero_batch_item_t* items, int32_t n, 
   const int quad[3] = {0, 4096, 32768};
   const int lo = b->occ_roll[0] < b->occ_roll[1] ? b->occ_roll[0] : b->occ_roll[1];
   const int ctas[3] = {0, 6, lo / 2 > 0 ? lo / 2 : 1};
+  const int spcs[3] = {128, 64, 256};
+  for (int si = 0; si < 3; ++si)
   for (int qi = 0; qi < 3; ++qi)
     for (int ci = 0; ci < 3; ++ci)
       for (int dyn = 1; dyn >= 0; --dyn)
         for (int coarse = 0; coarse < 2; ++coarse) {
-          const aero_batch_config_t c{quad[qi], ctas[ci], dyn, coarse};
+          const aero_batch_config_t c{quad[qi], ctas[ci], dyn, coarse, spcs[si]};
           float total = 0.0f;
           for (int rep = 0; rep <= repeats; ++rep) {
             for (int i = 0; i < n; ++i) {

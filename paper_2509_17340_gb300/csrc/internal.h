@@ -56,6 +56,7 @@ struct PartitionArgs {
   int A, El;
   int check_lo, check_hi;
   int filter;      // read a cone's key before its atomic minimum (dense clouds)
+  float el_lo, el_inv;  // elevation span start and cones per radian (bin guesses only)
   unsigned long long* keys;
   int* item_flag;  // collision set = every kept point: 1 where the point is kept, else 0
   int2* counts;    // per block (batched: per chunk of points): {non-finite points, kept points}
@@ -227,15 +228,17 @@ cudaError_t launch_batch_scan(const BatchView& v, int blocks, cudaStream_t s);
 cudaError_t launch_batch_scatter(const BatchView& v, int blocks, cudaStream_t s);
 // lanes 1 or 4; dynamic: take units from the work queue, else stride by the grid;
 // six: the one-lane kernel compiled for six resident CTAs per SM (fewer
-// registers) instead of five
+// registers) instead of five; samples_per_cta: the one-lane pass's CTA size
+// (64, 128 or 256; the items' partial rows were laid out for it)
 cudaError_t launch_batch_rollout(const BatchView& v, int lanes, int it, int blocks, int dynamic,
-                                 int six, cudaStream_t s);
+                                 int six, int samples_per_cta, cudaStream_t s);
 cudaError_t launch_batch_update(const BatchView& v, int it, int blocks, cudaStream_t s);
 
 // Resident CTAs per SM: {partition, count, scan, scatter} and {rollout with one
-// lane per sample, with four, update, rollout with one lane compiled for six}.
+// lane per sample, with four, update, rollout with one lane compiled for six,
+// one lane with 64 samples per CTA, one lane with 256}.
 cudaError_t batch_grid_occupancy(int out[4]);
-cudaError_t batch_rollout_occupancy(int out[4], int T_max);
+cudaError_t batch_rollout_occupancy(int out[6], int T_max);
 
 // t: the edge tables in device memory
 cudaError_t launch_partition(const PartitionArgs& a, const PartTables* t, cudaStream_t s);

@@ -51,6 +51,63 @@ __device__ __forceinline__ int el_bin(const float* ce, const float* se, int El, 
   return lo;
 }
 
+// A guess of atan2(y, x), within about 0.004 rad, from the arctangent
+// approximation atan t ~ (pi/4) t + 0.273 t (1 - |t|) on |t| <= 1 (Rajan,
+// Wang, Inkol, Joyal, 2006) with the octant folded.  It only picks where the
+// exact predicates start: the bins below are decided by those predicates.
+__device__ __forceinline__ float atan2_guess(float y, float x) {
+  const float ax = fabsf(x), ay = fabsf(y);
+  const float mx = fmaxf(ax, ay), mn = fminf(ax, ay);
+  const float t = mx > 0.0f ? __fdividef(mn, mx) : 0.0f;
+  float r = t * (0.785398163f + 0.273f * (1.0f - t));
+  if (ay > ax) r = 1.570796327f - r;
+  if (x < 0.0f) r = 3.141592654f - r;
+  return y < 0.0f ? -r : r;
+}
+
+// The bisection's result -- the largest k in (lo, hi] whose predicate holds,
+// else lo -- found from a guess g: g is that index iff (g == lo or pred(g))
+// and (g == hi or not pred(g + 1)), which singles it out because the
+// predicate holds up to the point's direction and not after it (only the edge
+// nearest the point can be within rounding of it, and the same arithmetic
+// decides it either way).  A guess more than two edges off falls back to the
+// bisection.
+template <typename Pred>
+__device__ __forceinline__ int bin_from_guess(int g, int lo, int hi, Pred pred) {
+  g = min(max(g, lo), hi);
+#pragma unroll 1
+  for (int it = 0; it < 3; ++it) {
+    if (g > lo && !pred(g)) {
+      --g;
+    } else if (g < hi && pred(g + 1)) {
+      ++g;
+    } else {
+      return g;
+    }
+  }
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (pred(mid)) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+// az_bin and el_bin from an angle guess (the same results).
+__device__ __forceinline__ int az_bin_guess(const float* ca, const float* sa, int A, float bx, float by) {
+  const int half = A >> 1;
+  const bool upper = (by > 0.0f) || (by == 0.0f && bx > 0.0f);
+  const int g = __float2int_rd((atan2_guess(by, bx) + 3.141592654f) * ((float)A * 0.159154943f));
+  return bin_from_guess(g, upper ? half : 0, upper ? A - 1 : half - 1, [&](int k) {
+    return sub(mul(by, ca[k]), mul(bx, sa[k])) >= 0.0f;
+  });
+}
+
+__device__ __forceinline__ int el_bin_guess(const float* ce, const float* se, int El, float bz, float rho,
+                                            float el_lo, float el_inv) {
+  const int g = __float2int_rd((atan2_guess(bz, rho) - el_lo) * el_inv);
+  return bin_from_guess(g, 0, El - 1, [&](int k) { return sub(mul(bz, ce[k]), mul(rho, se[k])) >= 0.0f; });
+}
+
 // ---------------------------------------------------------------------------
 // K1: cone of every point and atomic minimum of its key per cone.
 // ---------------------------------------------------------------------------
@@ -93,8 +150,8 @@ __device__ __forceinline__ int partition_point(const PartitionArgs& a, const Sme
       if (a.check_lo && !(sub(mul(b[2], st.ce[0]), mul(rho, st.se[0])) >= 0.0f)) ok = false;
       if (a.check_hi && (sub(mul(b[2], st.ce[a.El]), mul(rho, st.se[a.El])) > 0.0f)) ok = false;
       if (ok) {
-        const int ia = az_bin(st.ca, st.sa, a.A, b[0], b[1]);
-        const int je = el_bin(st.ce, st.se, a.El, b[2], rho);
+        const int ia = az_bin_guess(st.ca, st.sa, a.A, b[0], b[1]);
+        const int je = el_bin_guess(st.ce, st.se, a.El, b[2], rho, a.el_lo, a.el_inv);
         const int c = je * a.A + ia;
         const unsigned long long key =
             ((unsigned long long)__float_as_uint(r2) << 32) | (unsigned long long)(uint32_t)i;

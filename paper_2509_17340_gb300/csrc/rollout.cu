@@ -22,7 +22,6 @@ namespace {
 
 constexpr int NT = kRolloutThreads;
 constexpr int NW = NT / 32;
-static_assert(kMaxT <= NT, "every step of the horizon has a thread in the weighted-sum pass");
 
 __device__ __forceinline__ float4 clamp4(float4 u, float4 lo, float4 hi) {
   return make_float4(fminf(fmaxf(u.x, lo.x), hi.x), fminf(fmaxf(u.y, lo.y), hi.y),
@@ -37,27 +36,30 @@ struct CostSum {
   __device__ __forceinline__ void add(float v) { s += v; }
 };
 
-// Samples [b * NT, (b + 1) * NT) of instance e; ctr3: the noise counter's
-// last word, (step_id << 8) | iteration.  kIdx: the grid's candidate entries
-// are item indices (a single planner's step), else points (batched steps).
-template <bool kIdx>
+// Samples [b * kNT, (b + 1) * kNT) of instance e, one per thread (kNT: the
+// CTA's threads, a multiple of 32); ctr3: the noise counter's last word,
+// (step_id << 8) | iteration.  kIdx: the grid's candidate entries are item
+// indices (a single planner's step), else points (batched steps).
+template <bool kIdx, int kNT = NT>
 __device__ __forceinline__ void rollout_unit(const RolloutArgs& a, int e, int b, uint32_t ctr3) {
+  constexpr int kNW = kNT / 32;
+  constexpr int kSW = kNT > kMaxT ? kNT : kMaxT;
   __shared__ float4 s_un[kMaxT];
   __shared__ float s_gd[kMaxT * 3];
-  __shared__ float s_red[NW];
-  __shared__ int s_nz[NW];       // weighted samples per warp
-  __shared__ int s_lk[NT];       // the CTA's samples of non-zero weight, in sample order
-  __shared__ float s_lw[NT];     // and their weights
-  __shared__ float4 s_w[NT];     // W_b partial sums [replica][step], NT >= replicas x T
+  __shared__ float s_red[kNW];
+  __shared__ int s_nz[kNW];      // weighted samples per warp
+  __shared__ int s_lk[kNT];      // the CTA's samples of non-zero weight, in sample order
+  __shared__ float s_lw[kNT];    // and their weights
+  __shared__ float4 s_w[kSW];    // W_b partial sums [replica][step]
 
   const int tid = threadIdx.x;
   const int lane = tid & 31, wid = tid >> 5;
   const int T = a.T;
-  for (int i = tid; i < T; i += NT) s_un[i] = reinterpret_cast<const float4*>(a.u_nom)[e * T + i];
-  for (int i = tid; i < 3 * T; i += NT) s_gd[i] = a.guides[e * T * 3 + i];
+  for (int i = tid; i < T; i += kNT) s_un[i] = reinterpret_cast<const float4*>(a.u_nom)[e * T + i];
+  for (int i = tid; i < 3 * T; i += kNT) s_gd[i] = a.guides[e * T * 3 + i];
   __syncthreads();
 
-  const int k = b * NT + tid;
+  const int k = b * kNT + tid;
   const bool active = k < a.K;
   const CostParams& cp = a.cost;
   const float dmax2 = cp.d_max * cp.d_max;
@@ -161,7 +163,7 @@ __device__ __forceinline__ void rollout_unit(const RolloutArgs& a, int e, int b,
   __syncthreads();
   float rho = s_red[0];
 #pragma unroll
-  for (int w = 1; w < NW; ++w) rho = fminf(rho, s_red[w]);
+  for (int w = 1; w < kNW; ++w) rho = fminf(rho, s_red[w]);
   __syncthreads();
   const float wk = active ? expf((rho - Sk) * a.inv_lambda) : 0.0f;
   const float ws = warp_sum(wk);
@@ -177,7 +179,7 @@ __device__ __forceinline__ void rollout_unit(const RolloutArgs& a, int e, int b,
   __syncthreads();
   int nz = 0, before = 0;
 #pragma unroll
-  for (int w = 0; w < NW; ++w) {
+  for (int w = 0; w < kNW; ++w) {
     before += w < wid ? s_nz[w] : 0;
     nz += s_nz[w];
   }
@@ -187,12 +189,13 @@ __device__ __forceinline__ void rollout_unit(const RolloutArgs& a, int e, int b,
     s_lw[pos] = wk;
   }
   __syncthreads();
-  // W_b[j] = sum over the listed samples of w_k du_k[j]: thread t takes step
+  // W_b[j] = sum over the listed samples of w_k du_k[j]: slot t takes step
   // j = t mod T and the listed samples i = r, r + R, ... of replica r = t / T
-  // (R = NT / T replicas; a fixed order, so the sums are reproducible)
-  const int R = T <= NT ? NT / T : 1;
-  if (tid < R * T) {
-    const int j = tid % T, r = tid / T;
+  // (R = max(1, kNT / T) replicas; the CTA's threads take the R T slots in
+  // turn; a fixed order, so the sums are reproducible)
+  const int R = T <= kNT ? kNT / T : 1;
+  for (int slot = tid; slot < R * T; slot += kNT) {
+    const int j = slot % T, r = slot / T;
     const float4 un = s_un[j];
     float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
     for (int i = r; i < nz; i += R) {
@@ -204,7 +207,7 @@ __device__ __forceinline__ void rollout_unit(const RolloutArgs& a, int e, int b,
       acc.z += w * (u.z - un.z);
       acc.w += w * (u.w - un.w);
     }
-    s_w[tid] = acc;
+    s_w[slot] = acc;
   }
   __syncthreads();
   float* out = a.partials + ((size_t)e * a.nb + b) * (4 + 4 * T);
@@ -212,11 +215,11 @@ __device__ __forceinline__ void rollout_unit(const RolloutArgs& a, int e, int b,
   if (tid == 0) {
     float eta = 0.0f;
 #pragma unroll
-    for (int w = 0; w < NW; ++w) eta += s_red[w];
+    for (int w = 0; w < kNW; ++w) eta += s_red[w];
     out[0] = rho;
     out[1] = eta;
   }
-  for (int i = tid; i < 4 * T; i += NT) {
+  for (int i = tid; i < 4 * T; i += kNT) {
     const int j = i >> 2, cc = i & 3;
     float s = 0.0f;
     for (int r = 0; r < R; ++r) s += reinterpret_cast<const float*>(&s_w[r * T + j])[cc];
@@ -842,8 +845,9 @@ __global__ void __launch_bounds__(UT) k_update(UpdateArgs a) {
 // resets it), else units are strided by the grid.  Planners whose iteration
 // count is at most `it` skip their units.
 // ---------------------------------------------------------------------------
-template <int kLanes, int kMinCtas>
-__global__ void __launch_bounds__(kLanes == 4 ? ST : NT, kMinCtas)
+// kNT: samples per CTA of the one-lane pass (the autotuner's choice).
+template <int kLanes, int kMinCtas, int kNT = NT>
+__global__ void __launch_bounds__(kLanes == 4 ? ST : kNT, kMinCtas)
     k_b_rollout(BatchView v, int it, int dynamic) {
   pdl_start();
   __shared__ long long s_pre[kBatchMax + 1];
@@ -879,7 +883,7 @@ __global__ void __launch_bounds__(kLanes == 4 ? ST : NT, kMinCtas)
       const long long l = u - s_pre[pos];
       const int e = (int)(l / s_a.nb), b = (int)(l % s_a.nb);
       if constexpr (kLanes == 1)
-        rollout_unit<false>(s_a, e, b, s_a.ctr3 | (uint32_t)it);
+        rollout_unit<false, kNT>(s_a, e, b, s_a.ctr3 | (uint32_t)it);
       else
         rollout_split_unit(s_a, e, b, s_a.ctr3 | (uint32_t)it);
     }
@@ -1014,7 +1018,7 @@ cudaError_t split_carveout(int T) {
   return e;
 }
 
-cudaError_t batch_rollout_occupancy(int out[4], int T_max) {
+cudaError_t batch_rollout_occupancy(int out[6], int T_max) {
   cudaError_t e = split_attributes();
   if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(out + 0, k_b_rollout<1, 5>, NT, 0);
   if (e == cudaSuccess)
@@ -1024,16 +1028,22 @@ cudaError_t batch_rollout_occupancy(int out[4], int T_max) {
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(out + 2, k_b_update, UT,
                                                       update_smem_bytes(T_max, UT / 32, true));
   if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(out + 3, k_b_rollout<1, 6>, NT, 0);
-  for (int i = 0; i < 4; ++i)
+  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(out + 4, k_b_rollout<1, 12, 64>, 64, 0);
+  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(out + 5, k_b_rollout<1, 3, 256>, 256, 0);
+  for (int i = 0; i < 6; ++i)
     if (out[i] < 1) out[i] = 1;
   return e;
 }
 
 cudaError_t launch_batch_rollout(const BatchView& v, int lanes, int it, int blocks, int dynamic,
-                                 int six, cudaStream_t s) {
+                                 int six, int samples_per_cta, cudaStream_t s) {
   if (lanes == 4)
     return launch_ks(k_b_rollout<4, 2>, dim3(blocks), dim3(ST), split_smem_bytes(v.T_max), s, true, v,
                      it, dynamic);
+  if (samples_per_cta == 64)
+    return launch_k(k_b_rollout<1, 12, 64>, dim3(blocks), dim3(64), s, true, v, it, dynamic);
+  if (samples_per_cta == 256)
+    return launch_k(k_b_rollout<1, 3, 256>, dim3(blocks), dim3(256), s, true, v, it, dynamic);
   if (six) return launch_k(k_b_rollout<1, 6>, dim3(blocks), dim3(NT), s, true, v, it, dynamic);
   return launch_k(k_b_rollout<1, 5>, dim3(blocks), dim3(NT), s, true, v, it, dynamic);
 }
