@@ -80,13 +80,20 @@ def test_params_default_is_table_I(so):
     assert abs(p.el_hi - math.pi / 2) < 1e-6 and p.q_goal[0] == 1.0
 
 
-def test_binding_struct_sizes_match_header():
+def test_binding_struct_sizes_match_header(tmp_path):
+    """The ctypes structures have the sizes the C compiler gives the header's."""
+    import subprocess
     from paper_2509_17340_gb300 import aero
-    assert C.sizeof(aero.State) == 40
-    assert C.sizeof(aero.Limits) == 32
-    assert C.sizeof(aero.Params) == 232
-    assert C.sizeof(aero.BatchItem) == 336
-    assert C.sizeof(aero.BatchConfig) == 16
+    src = tmp_path / "sizes.c"
+    src.write_text('#include <stdio.h>\n#include "aero_mppi.h"\nint main(void) {\n'
+                   '  printf("%zu %zu %zu %zu %zu\\n", sizeof(aero_state_t), sizeof(aero_limits_t),\n'
+                   '         sizeof(aero_params_t), sizeof(aero_batch_item_t), sizeof(aero_batch_config_t));\n'
+                   '  return 0;\n}\n')
+    exe = tmp_path / "sizes"
+    subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)])
+    sizes = [int(x) for x in subprocess.check_output([str(exe)], text=True).split()]
+    assert sizes == [C.sizeof(aero.State), C.sizeof(aero.Limits), C.sizeof(aero.Params),
+                     C.sizeof(aero.BatchItem), C.sizeof(aero.BatchConfig)]
 
 
 def test_allocation_test_hooks_without_cuda(so):

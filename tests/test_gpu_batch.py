@@ -158,6 +158,32 @@ def test_batch_mixed_iterations_collision_sets_and_degenerate_items(aero, orc):
     batch.close()
 
 
+@pytest.mark.parametrize("spc", [64, 256])
+def test_batch_samples_per_cta(aero, orc, spc):
+    """The one-lane Stage I pass with 64 or 256 samples per CTA (the autotuner's
+    choices besides 128): the partial rows are laid out for the CTA size, and
+    every slot still matches the planner's step and the oracle."""
+    import torch
+    dev = torch.device("cuda")
+    ws = I.batch_workloads(10, seed=6)
+    for w in ws:
+        w.params["lanes_per_sample"] = 1
+    ws[3].params.update(K=1, T=1)                       # a CTA with one active sample
+    ws[5].params.update(K=300, T=60)                    # ragged last CTA, T above 64
+    lim = _limits(ws)
+    batch = aero.Batch(len(ws), **lim)
+    batch.set_config(samples_per_cta=spc)
+    assert batch.config()["samples_per_cta"] == spc
+    pl = aero.Planner(debug_samples_max=0, **lim)
+    bufs = [_buffers(w, dev) for w in ws]
+    _batch_calls(aero, orc, batch, pl, ws, bufs, calls=1, oracle_budget=300_000)
+    assert batch.sync_status() == 0
+    with pytest.raises(aero.AeroError):
+        batch.set_config(samples_per_cta=96)
+    pl.close()
+    batch.close()
+
+
 def test_batch_tune_then_plan_agrees_with_oracle(aero, orc):
     import torch
     dev = torch.device("cuda")
