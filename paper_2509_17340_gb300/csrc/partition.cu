@@ -264,24 +264,48 @@ __device__ __forceinline__ void cand_task(const CandArgs& a, int64_t it, int lan
   const int nx = x1 - x0 + 1, ny = y1 - y0 + 1, nz = z1 - z0 + 1;
   if (nx <= 0 || ny <= 0 || nz <= 0) return;
   const int ncand = nx * ny * nz;
-  for (int o = lane; o < ncand; o += 32) {
+  // the cell of block offset o if the point is within reach of its box, else -1
+  auto cell_of = [&](int o) {
+    if (o >= ncand) return -1;
     const int x = x0 + o % nx, y = y0 + (o / nx) % ny, z = z0 + o / (nx * ny);
     const float d2 = gap2(px, g.origin + x * g.h, g.h) + gap2(py, g.origin + y * g.h, g.h) +
                      gap2(pz, g.origin + z * g.h, g.h);
-    if (d2 >= r2) continue;
+    if (d2 >= r2) return -1;
     const int c = (z * g.G + y) * g.G + x;
-    if (!AERO_CHECK(c >= 0 && c < g.G * g.G * g.G, kChkGridCell)) continue;
-    if (!kScatter) {
-      atomicAdd(a.count + c, 1);
-    } else {
-      const int pos = a.local[c] + a.tile_off[c >> kScanTileShift] + atomicAdd(a.fill + c, 1);
-      if (pos < g.cap) {
-        if constexpr (kIdx)
-          a.cand[pos] = (uint32_t)it;
-        else
-          a.cand4[pos] = make_float4(px, py, pz, __int_as_float((int)it));
-      } else
-        atomicOr(a.status, 2);
+    return AERO_CHECK(c >= 0 && c < g.G * g.G * g.G, kChkGridCell) ? c : -1;
+  };
+  if constexpr (!kScatter) {
+    for (int o = lane; o < ncand; o += 32) {
+      const int c = cell_of(o);
+      if (c >= 0) atomicAdd(a.count + c, 1);
+    }
+  } else {
+    // kB cells per lane at a time: their list offsets and fill tickets are all
+    // requested before the first is used, so the round trips overlap
+    constexpr int kB = 4;
+    for (int o0 = lane; o0 < ncand; o0 += 32 * kB) {
+      int c[kB], base[kB], ticket[kB];
+#pragma unroll
+      for (int b = 0; b < kB; ++b) c[b] = cell_of(o0 + 32 * b);
+#pragma unroll
+      for (int b = 0; b < kB; ++b)
+        if (c[b] >= 0) {
+          base[b] = a.local[c[b]] + a.tile_off[c[b] >> kScanTileShift];
+          ticket[b] = atomicAdd(a.fill + c[b], 1);
+        }
+#pragma unroll
+      for (int b = 0; b < kB; ++b) {
+        if (c[b] < 0) continue;
+        const int pos = base[b] + ticket[b];
+        if (pos < g.cap) {
+          if constexpr (kIdx)
+            a.cand[pos] = (uint32_t)it;
+          else
+            a.cand4[pos] = make_float4(px, py, pz, __int_as_float((int)it));
+        } else {
+          atomicOr(a.status, 2);
+        }
+      }
     }
   }
 }
