@@ -216,6 +216,62 @@ __device__ __forceinline__ void attitude_map(float4 m, float* q) {
   q[3] = n3 * inv;
 }
 
+// Quaternion product a (x) b, components (w, x, y, z) in (.x, .y, .z, .w).
+// attitude_map(m, q) is q (x) m renormalised, so a trajectory's attitudes
+// are the normalised prefix products q0 (x) m_0 (x) ... (x) m_j.
+__device__ __forceinline__ float4 quat_mul4(float4 a, float4 b) {
+  return make_float4(a.x * b.x - a.y * b.y - a.z * b.z - a.w * b.w,
+                     a.x * b.y + a.y * b.x + a.z * b.w - a.w * b.z,
+                     a.x * b.z - a.y * b.w + a.z * b.x + a.w * b.y,
+                     a.x * b.w + a.y * b.z - a.z * b.y + a.w * b.x);
+}
+
+__device__ __forceinline__ float4 shfl_up4(float4 v, int o) {
+  return make_float4(__shfl_up_sync(0xffffffffu, v.x, o), __shfl_up_sync(0xffffffffu, v.y, o),
+                     __shfl_up_sync(0xffffffffu, v.z, o), __shfl_up_sync(0xffffffffu, v.w, o));
+}
+
+// Inclusive prefix products x_0 (x) ... (x) x_t over the threads t of a CTA
+// of kWarps warps (order kept: earlier factors on the left); warp_tot: kWarps
+// float4 of shared memory.  Every thread of the CTA calls it.
+template <int kWarps>
+__device__ __forceinline__ float4 block_quat_scan(float4 x, float4* warp_tot) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const float4 y = shfl_up4(x, o);
+    if (lane >= o) x = quat_mul4(y, x);
+  }
+  if (lane == 31) warp_tot[wid] = x;
+  __syncthreads();
+  float4 pre = make_float4(1.f, 0.f, 0.f, 0.f);
+  for (int w = 0; w < wid; ++w) pre = quat_mul4(pre, warp_tot[w]);
+  __syncthreads();
+  return quat_mul4(pre, x);
+}
+
+// Inclusive prefix sums of three components over the threads of a CTA of
+// kWarps warps; warp_tot: kWarps float4 of shared memory.
+template <int kWarps>
+__device__ __forceinline__ float3 block_sum_scan3(float3 x, float4* warp_tot) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const float a = __shfl_up_sync(0xffffffffu, x.x, o), b = __shfl_up_sync(0xffffffffu, x.y, o),
+                c = __shfl_up_sync(0xffffffffu, x.z, o);
+    if (lane >= o) x = make_float3(a + x.x, b + x.y, c + x.z);
+  }
+  if (lane == 31) warp_tot[wid] = make_float4(x.x, x.y, x.z, 0.f);
+  __syncthreads();
+  float3 pre = make_float3(0.f, 0.f, 0.f);
+  for (int w = 0; w < wid; ++w) {
+    const float4 t = warp_tot[w];
+    pre = make_float3(pre.x + t.x, pre.y + t.y, pre.z + t.z);
+  }
+  __syncthreads();
+  return make_float3(pre.x + x.x, pre.y + x.y, pre.z + x.z);
+}
+
 // The position and velocity increments of one step from the step's start
 // attitude q and control u (the RK4 stage sums of rk4_step):
 // p+ = p + h v + inc[0..2], v+ = v + inc[3..5].
