@@ -372,10 +372,10 @@ __device__ float warp_cost_grad(const float4* u, float4* g, const float* guide, 
 }
 
 // ---------------------------------------------------------------------------
-// Gradient refinement by a whole CTA (the update kernels): the two serial
-// chains run on thread 0 (the forward RK4 steps; the backward vector-Jacobian
-// products, from stage states stored by the forward pass), everything else
-// over the CTA: the stage states of every step, the nearest point of every
+// Gradient refinement by a whole CTA (the update kernels): the forward
+// states by scans over the steps (rollout_by_scans); the serial backward chain
+// of vector-Jacobian products (from the stage states) on thread 0; everything
+// else over the CTA: the stage states of every step, the nearest point of every
 // state (candidate lists cut into items of kRefItem entries; a 64-bit atomic
 // minimum of (squared distance bits, item index) keeps the lowest item among
 // equidistant points, the collision set's order), the state terms and their
@@ -385,6 +385,7 @@ __device__ float warp_cost_grad(const float4* u, float4* g, const float* guide, 
 constexpr int kRefItem = 8;
 
 struct RefineScratch {
+  float4* tot;               // warps: scan totals of the forward rollout
   float4* g;                 // T: dS/du
   unsigned long long* key;   // T: (bits(d2) << 32) | item of the nearest point of x_{j+1}
   float4* near;              // T: that point (entries holding points: found by a second pass)
@@ -398,14 +399,15 @@ struct RefineScratch {
 };
 
 __host__ __device__ constexpr size_t refine_smem_bytes(int T, int warps) {
-  return 16 * (size_t)T + 8 * (size_t)T + 16 * (size_t)T + 8 * (size_t)T + 8 * (size_t)warps +
+  return 16 * (size_t)warps + 16 * (size_t)T + 8 * (size_t)T + 16 * (size_t)T + 8 * (size_t)T + 8 * (size_t)warps +
          4 * (size_t)(T + 1) * 10 + 4 * (size_t)T * 34 + 4 * (size_t)T * 10 + 4 * (size_t)(T + 1) +
          4 * (size_t)T;
 }
 
 __device__ __forceinline__ RefineScratch refine_layout(unsigned char* base, int T, int warps) {
   RefineScratch r;
-  r.g = reinterpret_cast<float4*>(base);
+  r.tot = reinterpret_cast<float4*>(base);
+  r.g = r.tot + warps;
   r.key = reinterpret_cast<unsigned long long*>(r.g + T);
   r.near = reinterpret_cast<float4*>(r.key + T);
   r.qrange = reinterpret_cast<int2*>(r.near + T);
@@ -431,16 +433,8 @@ __device__ void block_refine(float4* u, const float* guide, int T, const float* 
   const unsigned long long none =
       ((unsigned long long)__float_as_uint(dmax2) << 32) | 0xffffffffull;
   for (int r = 0; r < steps; ++r) {
-    // forward: the states x_0 .. x_T
-    if (tid == 0) {
-      State x = state_load(x0);
-      state_store(rs.xs, x);
-      for (int j = 0; j < T; ++j) {
-        rk4_step(x, u[j], dp);
-        state_store(rs.xs + (j + 1) * 10, x);
-      }
-    }
-    __syncthreads();
+    // forward: the states x_0 .. x_T, by scans over the steps
+    rollout_by_scans<kThreads / 32>(u, T, x0, dp, rs.xs, rs.tot);
     // step tid: its stage states and the candidate range of x_{tid+1}
     int2 rg = make_int2(0, 0);
     if (tid < T) {

@@ -305,6 +305,56 @@ __device__ __forceinline__ void rk4_translation_increments(const float* q, float
   inc[5] = fv * (r1z + 2.0f * (r2z + r3z) + r4z) - gv;
 }
 
+// The states x_0 .. x_T of the noise-free rollout of u (T <= kWarps * 32
+// steps, thread j takes step j) into xs [T + 1][10] (shared memory), the RK4
+// step split by dependence and every part a scan over the steps: the
+// attitude update is q_{j+1} = N(q_j (x) m_j) with m_j from u_j alone, so
+// q_{j+1} = N(q_0 (x) m_0 (x) ... (x) m_j), a prefix product; then each
+// step's position and velocity increments from q_j and u_j; then
+// v_{j+1} = v_0 + the velocity increments up to j and p_{j+1} = p_0 + the
+// sums of h v_i and the position increments up to j.  tot: kWarps float4 of
+// shared memory.  Every thread of the CTA calls it; xs is complete when it
+// returns.
+template <int kWarps>
+__device__ __forceinline__ void rollout_by_scans(const float4* u, int T, const float* x0,
+                                                 const DynParams& dp, float* xs, float4* tot) {
+  const int tid = threadIdx.x;
+  const bool on = tid < T;
+  const float h = dp.dt;
+  const float4 uj = on ? u[tid] : make_float4(0.f, 0.f, 0.f, 0.f);
+  const float4 m = on ? rk4_attitude_coefs(uj, dp) : make_float4(1.f, 0.f, 0.f, 0.f);
+  const float4 pm = block_quat_scan<kWarps>(m, tot);
+  if (on) {
+    const float4 q = quat_mul4(make_float4(x0[3], x0[4], x0[5], x0[6]), pm);
+    const float inv = rsqrtf(q.x * q.x + q.y * q.y + q.z * q.z + q.w * q.w);
+    float* X = xs + (tid + 1) * 10 + 3;
+    X[0] = q.x * inv;
+    X[1] = q.y * inv;
+    X[2] = q.z * inv;
+    X[3] = q.w * inv;
+  }
+  if (tid < 10) xs[tid] = x0[tid];
+  __syncthreads();
+  float inc[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+  if (on) rk4_translation_increments(xs + tid * 10 + 3, uj, dp, inc);
+  const float3 dv = block_sum_scan3<kWarps>(make_float3(inc[3], inc[4], inc[5]), tot);
+  // v_{j+1} = v0 + dv (inclusive); v_j = v_{j+1} - the step's own increment
+  const float3 v1 = make_float3(x0[7] + dv.x, x0[8] + dv.y, x0[9] + dv.z);
+  const float3 vj = make_float3(v1.x - inc[3], v1.y - inc[4], v1.z - inc[5]);
+  const float3 dpos =
+      block_sum_scan3<kWarps>(make_float3(h * vj.x + inc[0], h * vj.y + inc[1], h * vj.z + inc[2]), tot);
+  if (on) {
+    float* X = xs + (tid + 1) * 10;
+    X[0] = x0[0] + dpos.x;
+    X[1] = x0[1] + dpos.y;
+    X[2] = x0[2] + dpos.z;
+    X[7] = v1.x;
+    X[8] = v1.y;
+    X[9] = v1.z;
+  }
+  __syncthreads();
+}
+
 // ---------------------------------------------------------------------------
 // Collision queries on the candidate lists.  The list of the query's cell holds
 // every collision point closer than d_max to that cell's box, so the nearest

@@ -676,51 +676,11 @@ __device__ __forceinline__ void update_unit(const UpdateArgs& a, int e, bool fin
     __syncthreads();
   }
 
-  // Stage II: noise-free rollout of the (updated, refined) nominal, split by
-  // dependence, every part a scan over the steps (thread j takes step j):
-  // the attitude update is q_{j+1} = N(q_j (x) m_j) with m_j from u_j alone, so
-  // q_{j+1} = N(q_0 (x) m_0 (x) ... (x) m_j), a prefix product; then each
-  // step's position and velocity increments from q_j and u_j; then
-  // v_{j+1} = v_0 + the sum of the velocity increments up to j, and
-  // p_{j+1} = p_0 + the sum of h v_i + the position increments up to j.
+  // Stage II: noise-free rollout of the (updated, refined) nominal, by scans
+  // over the steps (rollout_by_scans); the merge's scratch (acc) is free again
+  // and holds the warps' scan totals
   static_assert(kMaxT <= UT, "one Stage II step per thread");
-  float4* const s_tot = sm.acc;  // the merge's scratch, free again: scan totals of the warps
-  {
-    const float h = a.dyn.dt;
-    const bool on = tid < T;
-    const float4 u = on ? s_u4[tid] : make_float4(0.f, 0.f, 0.f, 0.f);
-    const float4 m = on ? rk4_attitude_coefs(u, a.dyn) : make_float4(1.f, 0.f, 0.f, 0.f);
-    const float4 pm = block_quat_scan<UT / 32>(m, s_tot);
-    if (on) {
-      const float4 q = quat_mul4(make_float4(a.x0[3], a.x0[4], a.x0[5], a.x0[6]), pm);
-      const float inv = rsqrtf(q.x * q.x + q.y * q.y + q.z * q.z + q.w * q.w);
-      float* X = s_x + (tid + 1) * 10 + 3;
-      X[0] = q.x * inv;
-      X[1] = q.y * inv;
-      X[2] = q.z * inv;
-      X[3] = q.w * inv;
-    }
-    if (tid < 10) s_x[tid] = a.x0[tid];
-    __syncthreads();
-    float inc[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-    if (on) rk4_translation_increments(s_x + tid * 10 + 3, u, a.dyn, inc);
-    const float3 dv = block_sum_scan3<UT / 32>(make_float3(inc[3], inc[4], inc[5]), s_tot);
-    // v_{j+1} = v0 + dv (inclusive); v_j = v_{j+1} - the step's own increment
-    const float3 v1 = make_float3(a.x0[7] + dv.x, a.x0[8] + dv.y, a.x0[9] + dv.z);
-    const float3 vj = make_float3(v1.x - inc[3], v1.y - inc[4], v1.z - inc[5]);
-    const float3 dp = block_sum_scan3<UT / 32>(
-        make_float3(h * vj.x + inc[0], h * vj.y + inc[1], h * vj.z + inc[2]), s_tot);
-    if (on) {
-      float* X = s_x + (tid + 1) * 10;
-      X[0] = a.x0[0] + dp.x;
-      X[1] = a.x0[1] + dp.y;
-      X[2] = a.x0[2] + dp.z;
-      X[7] = v1.x;
-      X[8] = v1.y;
-      X[9] = v1.z;
-    }
-  }
-  __syncthreads();
+  rollout_by_scans<UT / 32>(s_u4, T, a.x0, a.dyn, s_x, sm.acc);
   // the nearest point of every state x_{j+1} (thread j): the non-empty
   // candidate lists cut into items of kItem entries, taken by all threads
   static_assert(kMaxT <= UT, "one Stage II query per thread");
