@@ -373,9 +373,11 @@ __device__ float warp_cost_grad(const float4* u, float4* g, const float* guide, 
 
 // ---------------------------------------------------------------------------
 // Gradient refinement by a whole CTA (the update kernels): the forward
-// states by scans over the steps (rollout_by_scans); the serial backward chain
-// of vector-Jacobian products (from the stage states) on thread 0; everything
-// else over the CTA: the stage states of every step, the nearest point of every
+// states by scans over the steps (rollout_by_scans); the backward pass split
+// by dependence (suffix sums for the position and velocity adjoints, the 4x4
+// attitude recurrence on one thread, the vector-Jacobian products of every
+// step in parallel); everything else over the CTA: the stage states of every
+// step, the nearest point of every
 // state (candidate lists cut into items of kRefItem entries; a 64-bit atomic
 // minimum of (squared distance bits, item index) keeps the lowest item among
 // equidistant points, the collision set's order), the state terms and their
@@ -512,18 +514,76 @@ __device__ void block_refine(float4* u, const float* guide, int T, const float* 
                         guide[3 * tid + 2], d2, nearest, cp, dmax2, rs.gs + tid * 10);
     }
     __syncthreads();
-    // backward: the serial vector-Jacobian products
-    if (tid == 0) {
-      float lam[10];
+    // backward.  With L_{k+1} = dS/dx_{k+1} (the state terms at x_{k+1} plus
+    // what flows back from later steps), L_{k+1} = gs[k] + J_{k+1}^T L_{k+2},
+    // J the step Jacobian.  Positions feed only positions and velocities only
+    // positions and velocities, so the position and velocity parts are
+    // suffix sums: Lp_{k+1} = sum_{i >= k} gs_p[i], Lv_{k+1} = sum_{i >= k}
+    // (gs_v[i] + h Lp_{i+2}).  The attitude part is the linear recurrence
+    // Lq_{k+1} = gs_q[k] + b_{k+1} + A_{k+1}^T Lq_{k+2}: b the attitude part of
+    // J^T (Lp, 0, Lv) (the step's vector-Jacobian product, in parallel), A the
+    // 4x4 attitude Jacobian, whose transpose is applied in closed form: the
+    // unnormalised y = q (x) m, so A^T l = ((l - yh (yh . l)) / |y|) (x) conj(m),
+    // yh = y / |y|; one thread chains it.  Then every step's dS/du_k is the
+    // control part of J_k^T L_{k+1}, in parallel.
+    {
+      const float h = dp.dt;
+      // (a) the suffix sums, thread t taking step k = T - 1 - t
+      const int k = T - 1 - tid;
+      const bool on = tid < T;
+      const float* g = rs.gs + (on ? k : 0) * 10;
+      const float3 gp = on ? make_float3(g[0], g[1], g[2]) : make_float3(0.f, 0.f, 0.f);
+      const float3 gv = on ? make_float3(g[7], g[8], g[9]) : make_float3(0.f, 0.f, 0.f);
+      const float3 lp = block_sum_scan3<kThreads / 32>(gp, rs.tot);
+      const float3 lp2 = make_float3(lp.x - gp.x, lp.y - gp.y, lp.z - gp.z);  // Lp_{k+2}
+      const float3 lv = block_sum_scan3<kThreads / 32>(
+          make_float3(gv.x + h * lp2.x, gv.y + h * lp2.y, gv.z + h * lp2.z), rs.tot);
+      if (on) {
+        float* L = rs.gs + k * 10;
+        L[0] = lp.x; L[1] = lp.y; L[2] = lp.z;
+        L[7] = lv.x; L[8] = lv.y; L[9] = lv.z;
+      }
+      __syncthreads();
+      // (b) b_k for every step k = tid, into rs.g
+      if (tid < T) {
+        const float* L = rs.gs + tid * 10;
+        float lam[10] = {L[0], L[1], L[2], 0.f, 0.f, 0.f, 0.f, L[7], L[8], L[9]};
+        float gu[4] = {0.f, 0.f, 0.f, 0.f};
+        const float* stk = rs.st + (size_t)tid * 34;
+        rk4_vjp_stages(rs.xs + tid * 10, stk, stk + 10, stk + 20, stk + 30, u[tid], dp, lam, gu);
+        rs.g[tid] = make_float4(lam[3], lam[4], lam[5], lam[6]);
+      }
+      __syncthreads();
+      // (c) the attitude recurrence on one thread
+      if (tid == 0) {
+        float* L = rs.gs + (T - 1) * 10 + 3;
+        float4 l = make_float4(L[0], L[1], L[2], L[3]);  // Lq_T = gs_q[T - 1]
+        for (int kk = T - 2; kk >= 0; --kk) {
+          const int j = kk + 1;  // A_j: the attitude Jacobian of step j
+          const float* y = rs.st + (size_t)j * 34 + 30;
+          const float inv = rsqrtf(y[0] * y[0] + y[1] * y[1] + y[2] * y[2] + y[3] * y[3]);
+          const float d = (y[0] * l.x + y[1] * l.y + y[2] * l.z + y[3] * l.w) * inv * inv;
+          const float4 pl = make_float4((l.x - y[0] * d) * inv, (l.y - y[1] * d) * inv,
+                                        (l.z - y[2] * d) * inv, (l.w - y[3] * d) * inv);
+          const float4 m = rk4_attitude_coefs(u[j], dp);
+          const float4 at = quat_mul4(pl, make_float4(m.x, -m.y, -m.z, -m.w));
+          const float4 b = rs.g[j];
+          float* Lk = rs.gs + kk * 10 + 3;
+          l = make_float4(Lk[0] + b.x + at.x, Lk[1] + b.y + at.y, Lk[2] + b.z + at.z,
+                          Lk[3] + b.w + at.w);
+          Lk[0] = l.x; Lk[1] = l.y; Lk[2] = l.z; Lk[3] = l.w;
+        }
+      }
+      __syncthreads();
+      // (d) dS/du_k = the control part of J_k^T L_{k+1}
+      if (tid < T) {
+        float lam[10];
 #pragma unroll
-      for (int i = 0; i < 10; ++i) lam[i] = 0.0f;
-      for (int k = T - 1; k >= 0; --k) {
-#pragma unroll
-        for (int i = 0; i < 10; ++i) lam[i] += rs.gs[k * 10 + i];
-        float gu[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-        const float* stk = rs.st + (size_t)k * 34;
-        rk4_vjp_stages(rs.xs + k * 10, stk, stk + 10, stk + 20, stk + 30, u[k], dp, lam, gu);
-        rs.g[k] = make_float4(gu[0], gu[1], gu[2], gu[3]);
+        for (int i = 0; i < 10; ++i) lam[i] = rs.gs[tid * 10 + i];
+        float gu[4] = {0.f, 0.f, 0.f, 0.f};
+        const float* stk = rs.st + (size_t)tid * 34;
+        rk4_vjp_stages(rs.xs + tid * 10, stk, stk + 10, stk + 20, stk + 30, u[tid], dp, lam, gu);
+        rs.g[tid] = make_float4(gu[0], gu[1], gu[2], gu[3]);
       }
     }
     __syncthreads();
