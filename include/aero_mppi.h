@@ -107,7 +107,8 @@ typedef struct {
                                (collision_set = 1) can be used: 0 = n_points_max, -1 = never
                                (its per-point arrays are then not allocated); otherwise
                                1 .. n_points_max.  A step with collision_set = 1 and more
-                               points returns AERO_ERR_EXCEEDS_LIMITS */
+                               points returns AERO_ERR_EXCEEDS_LIMITS.  The planner's
+                               candidate lists then take up to 864 bytes per point */
 } aero_limits_t;
 
 /* Parameters of one planning step; aero_params_default() fills Table I. */

@@ -663,6 +663,8 @@ int enqueue_step(aero_planner* pl, const aero_state_t* x0, const float* cloud, i
   return AERO_OK;
 }
 
+int create_planner(const aero_limits_t* limits, aero_planner_t** out, bool batch_slot);
+
 }  // namespace
 
 extern "C" {
@@ -718,6 +720,18 @@ void aero_params_default(aero_params_t* p) {
 }
 
 int aero_create(const aero_limits_t* limits, aero_planner_t** out) {
+  return create_planner(limits, out, false);
+}
+
+}  // extern "C"
+
+namespace {
+
+// batch_slot: the workspace of a batch's item slot, whose candidate entries
+// hold the points (16 bytes); a single planner's entries are 4-byte item
+// indices, so the same bytes hold four times the entries and the every-point
+// set gets room for the finer cells (216 entries per kept point).
+int create_planner(const aero_limits_t* limits, aero_planner_t** out, bool batch_slot) {
   if (!limits || !out) return AERO_ERR_INVALID_ARG;
   *out = nullptr;
   const aero_limits_t& L = *limits;
@@ -734,7 +748,7 @@ int aero_create(const aero_limits_t* limits, aero_planner_t** out) {
   // partial rows: one per rollout CTA, whose smallest sample count is 128 / 4
   const int64_t nbmax = (L.K_max + kRolloutThreads / 4 - 1) / (kRolloutThreads / 4);
   const int64_t cap_fine = (int64_t)kFineDup * L.fine_cells_max;
-  const int64_t cap_raw = (int64_t)kCoarseDup * pl->raw_max;
+  const int64_t cap_raw = (int64_t)(batch_slot ? kCoarseDup : kFineDup) * pl->raw_max;
   int64_t cap = cap_fine > cap_raw ? cap_fine : cap_raw;
   if (cap > 0x7FFFFFFFLL) cap = 0x7FFFFFFFLL;
   pl->cand_cap = (int)cap;
@@ -754,7 +768,7 @@ int aero_create(const aero_limits_t* limits, aero_planner_t** out) {
   chk(alloc(&pl->grid_local, kGridCellsMax + 1));
   chk(alloc(&pl->tile_sum, kMaxTiles));
   chk(alloc(&pl->tile_off, kMaxTiles + 1));
-  chk(alloc(&pl->cand, cap));
+  chk(dev_malloc((void**)&pl->cand, (batch_slot ? sizeof(float4) : sizeof(uint32_t)) * (size_t)(cap > 0 ? cap : 1)));
   chk(alloc(&pl->cand_pts, std::max<int64_t>(L.fine_cells_max, pl->raw_max)));
   chk(alloc(&pl->grid_range, kGridCellsMax));
   chk(alloc(&pl->partials, (size_t)L.E_max * nbmax * (4 + 4 * L.T_max)));
@@ -787,6 +801,10 @@ int aero_create(const aero_limits_t* limits, aero_planner_t** out) {
   *out = pl;
   return AERO_OK;
 }
+
+}  // namespace
+
+extern "C" {
 
 int aero_test_fail_alloc(int64_t n) {
   g_alloc_fail_after.store(n < 0 ? -1 : n);
@@ -1600,7 +1618,7 @@ int aero_batch_create(const aero_limits_t* limits, int32_t n_max, aero_batch_t**
   b->lim.debug_samples_max = 0;
   for (int i = 0; i < n_max; ++i) {
     aero_planner_t* pl = nullptr;
-    const int rc = aero_create(&b->lim, &pl);
+    const int rc = create_planner(&b->lim, &pl, true);
     if (rc != AERO_OK) {
       batch_free(b);
       return rc;
