@@ -60,12 +60,22 @@ __device__ __forceinline__ float uniform01(uint32_t w) {
   return __uint_as_float(0x3F800000u | (w >> 9)) - 0.99999994039535522f;
 }
 
-// sqrt(x) for x >= 0 by the hardware's approximate square root
-// (sqrt.approx.f32: one instruction, 0 at 0; its error is far below the
-// tolerances, which the GPU tests check on the normals and on the costs).
+// sqrt(x) for x >= 0 by the hardware's approximate square root, subnormal
+// inputs flushed to zero (sqrt.approx.ftz.f32: 0 at 0; a subnormal squared
+// norm is a length below 1e-19, taken as 0).  Its error is far below the
+// tolerances, which the GPU tests check on the normals and on the costs.
 __device__ __forceinline__ float fast_sqrt(float x) {
   float y;
-  asm("sqrt.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
+  asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+// 1/sqrt(x) by the hardware's approximation with subnormals flushed
+// (rsqrt.approx.ftz.f32), for the renormalisation of a quaternion whose
+// squared norm is close to 1.
+__device__ __forceinline__ float fast_rsqrt(float x) {
+  float y;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
   return y;
 }
 
@@ -182,7 +192,7 @@ __device__ __forceinline__ void rk4_step(State& x, float4 u, const DynParams& dp
   const float ca = h * (1.0f - hh * (1.0f / 6.0f));
   const float n0 = cq * q[0] + ca * a0, n1 = cq * q[1] + ca * a1;
   const float n2 = cq * q[2] + ca * a2, n3 = cq * q[3] + ca * a3;
-  const float inv = rsqrtf(n0 * n0 + n1 * n1 + n2 * n2 + n3 * n3);
+  const float inv = fast_rsqrt(n0 * n0 + n1 * n1 + n2 * n2 + n3 * n3);
   x.q[0] = n0 * inv;
   x.q[1] = n1 * inv;
   x.q[2] = n2 * inv;
