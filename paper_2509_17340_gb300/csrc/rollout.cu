@@ -21,7 +21,6 @@ namespace aero {
 namespace {
 
 constexpr int NT = kRolloutThreads;
-constexpr int NW = NT / 32;
 
 __device__ __forceinline__ float4 clamp4(float4 u, float4 lo, float4 hi) {
   return make_float4(fminf(fmaxf(u.x, lo.x), hi.x), fminf(fmaxf(u.y, lo.y), hi.y),
@@ -121,6 +120,12 @@ __device__ __forceinline__ void rollout_unit(const RolloutArgs& a, int e, int b,
   float4 u_j = control(0, c_ctrl);
   rk4_step(x, u_j, a.dyn);
   int2 range = cell_range(x.p[0], x.p[1], x.p[2], a.grid);
+  // a single planner: two steps per iteration, so that the state carried
+  // from one step to the next alternates between two register sets instead
+  // of being copied (the batched kernels, with their arguments in shared
+  // memory, would spill)
+  constexpr int kUnroll = kIdx ? 2 : 1;
+#pragma unroll kUnroll
   for (int j = 1; j <= T; ++j) {
     const int2 range_j = range;
     State xn = x;
