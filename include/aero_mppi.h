@@ -185,8 +185,9 @@ int aero_destroy(aero_planner_t* planner);
  * The call only enqueues work on `stream` (it neither allocates nor
  * synchronises), so it can be captured into a CUDA graph and replayed; the
  * graph replays the captured arguments (state, goal, step_id, buffers).
- * Errors (nothing is enqueued): INVALID_ARG, EXCEEDS_LIMITS, NOT_DEVICE_PTR;
- * CUDA if a launch fails. */
+ * Errors (nothing is enqueued): INVALID_ARG (also for a non-finite state,
+ * goal, sigma or scalar parameter), EXCEEDS_LIMITS, NOT_DEVICE_PTR; CUDA if a
+ * launch fails. */
 int aero_plan_step(aero_planner_t* planner, const aero_state_t* x0, const float* cloud_xyz,
                    int64_t n_points, const float goal[3], const aero_params_t* params,
                    float* u_nom_inout, float* u_best_out, float* cand_costs_out,
@@ -310,7 +311,8 @@ int aero_batch_tune(aero_batch_t* batch, const aero_batch_item_t* items, int32_t
                     void* stream, aero_batch_config_t* best, float* best_ms);
 
 /* OR of the status words of the batch's slots (bit 0: an update's normaliser
- * was not a positive finite number; bit 1: a candidate list overflowed) and, in
+ * was not a positive finite number; bit 1: a candidate list overflowed; bit 2:
+ * no candidate had a finite S(2), the first instance was taken) and, in
  * the checked build, of the index-check bits (1 << 8 and up, see
  * aero_sync_status), which are then cleared.  Synchronous. */
 int aero_batch_sync_status(aero_batch_t* batch, int32_t* status);
@@ -405,8 +407,11 @@ int aero_test_raise_check(int32_t bits);
 int aero_get_debug(aero_planner_t* planner, int32_t what, void* dst, size_t bytes, void* stream);
 
 /* Synchronise `stream`, then report the kernels' status word: AERO_OK, or
- * DEVICE_CHECK when a kernel recorded an internal inconsistency, or CUDA when
- * the stream holds an error.  Clears the status word.
+ * DEVICE_CHECK when a kernel recorded an internal inconsistency or a
+ * non-finite result (an update's normaliser not a positive finite number, a
+ * candidate list overflow, no candidate with a finite S(2): the first instance
+ * is then the one selected), or CUDA when the stream holds an error.  Clears
+ * the status word.
  * The checked build of the library (libaero_mppi_checked.so, compiled with
  * AERO_CHECKED) also guards the indices the kernels rely on (fine cell, grid
  * cell, candidate range, query slot and item, partial row, accumulation slot):

@@ -142,6 +142,7 @@ struct aero_planner {
   float* stage2_x = nullptr;
   unsigned int* counter = nullptr;
   int* status = nullptr;
+  float* warm = nullptr;      // the split pass's warm-up block's scratch (warm_words)
   float* dbg_u = nullptr;
   float* dbg_x = nullptr;
   float* dbg_d = nullptr;
@@ -284,8 +285,13 @@ int validate(const aero_planner* pl, const aero_params_t* p, int64_t n_points) {
   if (!(p->dt > 0) || !(p->lambda > 0) || !(p->mass > 0) || !(p->r_max > 0) || !(p->ell > 0) ||
       !(p->d_max > 0) || !(p->d_min < p->d_max) || !(p->el_lo < p->el_hi))
     return AERO_ERR_INVALID_ARG;
+  const float scalars[] = {p->dt, p->lambda, p->mass, p->r_max, p->ell, p->d_max, p->d_min,
+                           p->el_lo, p->el_hi};
+  for (float f : scalars)
+    if (!std::isfinite(f)) return AERO_ERR_INVALID_ARG;
   for (int c = 0; c < 4; ++c)
-    if (!(p->u_min[c] <= p->u_max[c]) || !(p->sigma[c] >= 0)) return AERO_ERR_INVALID_ARG;
+    if (!(p->u_min[c] <= p->u_max[c]) || !(p->sigma[c] >= 0) || !std::isfinite(p->sigma[c]))
+      return AERO_ERR_INVALID_ARG;
   if (p->collision_set != 0 && p->collision_set != 1) return AERO_ERR_INVALID_ARG;
   if (p->debug_samples < 0 || n_points < 0) return AERO_ERR_INVALID_ARG;
   if (p->lanes_per_sample != 0 && p->lanes_per_sample != 1 && p->lanes_per_sample != 4)
@@ -300,6 +306,15 @@ int validate(const aero_planner* pl, const aero_params_t* p, int64_t n_points) {
   return AERO_OK;
 }
 
+// A finite state and goal (a non-finite one makes every cost non-finite).
+bool finite_state_goal(const aero_state_t* x0, const float* goal) {
+  for (int i = 0; i < 3; ++i)
+    if (!std::isfinite(x0->p[i]) || !std::isfinite(x0->v[i]) || !std::isfinite(goal[i])) return false;
+  for (int i = 0; i < 4; ++i)
+    if (!std::isfinite(x0->q[i])) return false;
+  return true;
+}
+
 template <typename T>
 cudaError_t alloc(T** p, size_t count) {
   return dev_malloc((void**)p, sizeof(T) * (count > 0 ? count : 1));
@@ -312,7 +327,7 @@ void free_all(aero_planner* pl) {
                   pl->cand,     pl->cand_pts,   pl->grid_range, pl->partials,
                   pl->sample_costs, pl->stage2_x, pl->counter,   pl->status,   pl->dbg_u,
                   pl->dbg_x,    pl->dbg_d,      pl->stage_cloud,      pl->stage_out,
-                  pl->dbg_pre,      pl->part_counts,  pl->d_tab};
+                  pl->dbg_pre,      pl->part_counts,  pl->d_tab,  pl->warm};
   for (void* q : ptrs) dev_free(q);
   host_free(pl->h_out);
 }
@@ -567,6 +582,7 @@ void make_step_args(aero_planner* pl, const aero_state_t* x0, const float* cloud
   ua.counter = pl->counter;
   ua.inst_counter = pl->counter + 3;
   ua.status = pl->status;
+  ua.warm = pl->warm;
 }
 
 // The planner's state after a step has been enqueued.
@@ -776,6 +792,7 @@ int create_planner(const aero_limits_t* limits, aero_planner_t** out, bool batch
   chk(alloc(&pl->stage2_x, (size_t)L.E_max * (L.T_max + 1) * 10));
   chk(alloc(&pl->counter, kCounterWords));
   chk(alloc(&pl->status, 1));
+  if (!batch_slot) chk(alloc(&pl->warm, warm_words(L.E_max, L.T_max)));
   chk(alloc(&pl->dbg_u, (size_t)L.E_max * D * L.T_max * 4));
   chk(alloc(&pl->dbg_x, (size_t)L.E_max * D * (L.T_max + 1) * 10));
   chk(alloc(&pl->dbg_d, (size_t)L.E_max * D * L.T_max));
@@ -838,6 +855,7 @@ int aero_plan_step(aero_planner_t* pl, const aero_state_t* x0, const float* clou
   if (!pl || !x0 || !goal || !params || !u_nom || !u_best || !cand || !best_idx)
     return AERO_ERR_INVALID_ARG;
   if (n > 0 && !cloud) return AERO_ERR_INVALID_ARG;
+  if (!finite_state_goal(x0, goal)) return AERO_ERR_INVALID_ARG;
   int rc = validate(pl, params, n);
   if (rc != AERO_OK) return rc;
   if (reinterpret_cast<uintptr_t>(u_nom) % 16 != 0) return AERO_ERR_INVALID_ARG;
@@ -854,6 +872,7 @@ int aero_plan_step_host(aero_planner_t* pl, const aero_state_t* x0, const float*
   if (!pl || !x0 || !goal || !params || !u_nom || !u_best || !cand || !best_idx)
     return AERO_ERR_INVALID_ARG;
   if (n > 0 && !cloud) return AERO_ERR_INVALID_ARG;
+  if (!finite_state_goal(x0, goal)) return AERO_ERR_INVALID_ARG;
   int rc = validate(pl, params, n);
   if (rc != AERO_OK) return rc;
   cudaStream_t s = (cudaStream_t)stream;
@@ -1206,6 +1225,7 @@ int aero_plan_step_noalloc(const aero_state_t* x0, const float* cloud, int64_t n
   pl.lim.n_points_max = kNaPoints;
   pl.lim.debug_samples_max = 0;
   pl.raw_max = kNaPoints;
+  if (!finite_state_goal(x0, goal)) return AERO_ERR_INVALID_ARG;
   int rc = validate(&pl, params, n);
   if (rc != AERO_OK) return rc;
   if (params->collision_set != 0) return AERO_ERR_EXCEEDS_LIMITS;
@@ -1361,6 +1381,7 @@ int check_item(aero_planner* pl, const aero_batch_item_t& it) {
     return AERO_ERR_INVALID_ARG;
   if (it.n_points > 0 && !it.cloud_xyz) return AERO_ERR_INVALID_ARG;
   if (it.params.debug_samples != 0) return AERO_ERR_INVALID_ARG;
+  if (!finite_state_goal(&it.x0, it.goal)) return AERO_ERR_INVALID_ARG;
   const int rc = validate(pl, &it.params, it.n_points);
   if (rc != AERO_OK) return rc;
   if (reinterpret_cast<uintptr_t>(it.u_nom_inout) % 16 != 0) return AERO_ERR_INVALID_ARG;

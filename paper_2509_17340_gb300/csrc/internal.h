@@ -167,7 +167,16 @@ struct UpdateArgs {
   unsigned int* counter;   // last-CTA ticket, 0 between launches
   unsigned int* inst_counter;  // E tickets of the split Stage I pass, 0 between launches
   int* status;             // bit 0: a normaliser eta was not a positive finite number
+  float* warm;             // scratch of the split pass's warm-up block (warm_words floats), or
+                           // null: no warm-up block
 };
+
+// Scratch of the split pass's warm-up block for up to E instances of horizon T
+// (floats): nominals E x T x 4, Stage II states (T + 1) x 10, candidate costs E,
+// best sequence T x 4, then three words (best index, ticket, status).
+__host__ __device__ constexpr size_t warm_words(int E, int T) {
+  return (size_t)E * T * 4 + (size_t)(T + 1) * 10 + E + (size_t)T * 4 + 3;
+}
 
 // ---------------------------------------------------------------------------
 // Batched step: the planning steps of many independent planners, each stage one

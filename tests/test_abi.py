@@ -114,3 +114,40 @@ def test_checked_build_exports_every_declared_symbol():
     lib = C.CDLL(build.build(checked=True))
     for name in declared_functions():
         assert hasattr(lib, name), name
+
+
+def test_non_finite_inputs_are_rejected_before_any_device_call():
+    # the no-allocation entry point checks its arguments before any CUDA call:
+    # a non-finite state, goal, sigma or scalar parameter is INVALID_ARG
+    from paper_2509_17340_gb300 import aero
+    lib = aero._lib
+    bufs = [(C.c_float * 4096)() for _ in range(4)]
+    ptrs = [C.cast(b, C.c_void_p) for b in bufs]
+    cloud = (C.c_float * 3)(0.0, 0.0, 0.0)
+
+    def call(state, goal, params):
+        g = (C.c_float * 3)(*goal)
+        return lib.aero_plan_step_noalloc(C.byref(state), C.cast(cloud, C.c_void_p), C.c_int64(1), g,
+                                          C.byref(params), ptrs[0], ptrs[1], ptrs[2], ptrs[3], None)
+
+    def state(p=(0.0, 0.0, 1.0), q=(1.0, 0.0, 0.0, 0.0), v=(0.0, 0.0, 0.0)):
+        s = aero.State()
+        s.p[:] = list(p)
+        s.q[:] = list(q)
+        s.v[:] = list(v)
+        return s
+
+    nan, inf = float("nan"), float("inf")
+    P = aero.default_params_struct()
+    assert call(state(p=(nan, 0.0, 1.0)), (5.0, 0.0, 1.0), P) == -1
+    assert call(state(q=(1.0, 0.0, inf, 0.0)), (5.0, 0.0, 1.0), P) == -1
+    assert call(state(v=(0.0, -inf, 0.0)), (5.0, 0.0, 1.0), P) == -1
+    assert call(state(), (5.0, nan, 1.0), P) == -1
+    for field, value in [("dt", inf), ("lam", inf), ("d_max", inf), ("mass", inf), ("r_max", inf)]:
+        Q = aero.default_params_struct()
+        assert field in [f for f, _ in aero.Params._fields_]
+        setattr(Q, field, value)
+        assert call(state(), (5.0, 0.0, 1.0), Q) == -1, field
+    Q = aero.default_params_struct()
+    Q.sigma[1] = inf
+    assert call(state(), (5.0, 0.0, 1.0), Q) == -1

@@ -84,3 +84,27 @@ def test_planning_after_failed_creates(aero):
     assert torch.isfinite(ub).all() and torch.isfinite(cand).all()
     assert 0 <= int(best.cpu()[0]) < P["E"]
     pl.close()
+
+
+@pytest.mark.parametrize("lanes", [1, 4])
+def test_non_finite_costs_select_the_first_instance(aero, lanes):
+    # an infinite control weight makes every cost non-finite: the step still
+    # selects an instance in range (the first), the status word reports it,
+    # and the planner is usable afterwards
+    import torch
+    w = I.make_workload("ensemble")
+    P = dict(w.params, K=256, lanes_per_sample=lanes)
+    pl = aero.Planner(E_max=P["E"], K_max=P["K"], T_max=P["T"],
+                      fine_cells_max=P["fine_az"] * P["fine_el"], n_points_max=len(w.cloud))
+    cloud = torch.from_numpy(w.cloud).cuda()
+    u0 = torch.from_numpy(w.hover_nominal()).cuda()
+    bad = dict(P, Q_c=float("inf"))
+    u_best, cand, best = aero.plan_step(pl, w.p0, w.q0, w.v0, cloud, w.goal, bad, u0.clone())
+    assert pl.sync_status() == aero.ERR_DEVICE_CHECK
+    assert int(best.item()) == 0
+    assert not torch.isfinite(cand).any()
+    u_best, cand, best = aero.plan_step(pl, w.p0, w.q0, w.v0, cloud, w.goal, P, u0.clone())
+    assert pl.sync_status() == 0
+    assert torch.isfinite(cand).all() and 0 <= int(best.item()) < P["E"]
+    assert int(best.item()) == int(torch.argmin(cand).item())
+    pl.close()

@@ -149,3 +149,36 @@ def test_noalloc_first_call_inside_capture_is_refused(aero):
     r = subprocess.run([sys.executable, "-c", _FIRST_CALL_IN_CAPTURE, ROOT], capture_output=True,
                        text=True, timeout=600)
     assert r.returncode == 0 and r.stdout.strip().endswith("ok"), r.stdout + r.stderr
+
+
+@pytest.mark.parametrize("refine", [0, 5])
+def test_split_pass_outputs_equal_with_and_without_the_warm_up_block(aero, refine):
+    # a planner's split pass runs a warm-up block (the update's code on
+    # scratch at the start of the launch); the no-allocation entry point runs
+    # the same kernel without it.  The nearest-point distances do not depend
+    # on the grid's cell edge, and every sum runs in a fixed order, so the two
+    # agree bit for bit: the warm-up block writes nothing the step returns.
+    import torch
+    dev = torch.device("cuda")
+    w = I.make_workload("ensemble")
+    P = dict(w.params, lanes_per_sample=4, refine_steps=refine)
+    cloud = torch.from_numpy(w.cloud).to(dev)
+    state = aero.state_struct(w.p0, w.q0, w.v0)
+    pl = aero.Planner(E_max=P["E"], K_max=P["K"], T_max=P["T"],
+                      fine_cells_max=P["fine_az"] * P["fine_el"], n_points_max=len(w.cloud))
+    u_ref = torch.from_numpy(w.hover_nominal()).to(dev)
+    u_na = u_ref.clone()
+    for call in range(3):
+        P["step_id"] = 100 + call
+        prm = aero.params_struct(P)
+        ub_ref, c_ref, b_ref = _outputs(P, dev)
+        ub_na, c_na, b_na = _outputs(P, dev)
+        pl.plan_step(state, cloud, w.goal, prm, u_ref, ub_ref, c_ref, b_ref)
+        aero.plan_step_noalloc(state, cloud, w.goal, prm, u_na, ub_na, c_na, b_na)
+        torch.cuda.synchronize()
+        assert torch.equal(u_na, u_ref), call
+        assert torch.equal(ub_na, ub_ref), call
+        assert torch.equal(c_na, c_ref), call
+        assert torch.equal(b_na, b_ref), call
+    assert pl.sync_status() == 0
+    pl.close()
