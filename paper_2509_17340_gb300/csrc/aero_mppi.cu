@@ -142,7 +142,7 @@ struct aero_planner {
   float* stage2_x = nullptr;
   unsigned int* counter = nullptr;
   int* status = nullptr;
-  float* warm = nullptr;      // the split pass's warm-up block's scratch (warm_words)
+  float* warm = nullptr;      // warm-up scratch: E_max regions of warm_words(E_max, T_max)
   float* dbg_u = nullptr;
   float* dbg_x = nullptr;
   float* dbg_d = nullptr;
@@ -583,6 +583,8 @@ void make_step_args(aero_planner* pl, const aero_state_t* x0, const float* cloud
   ua.inst_counter = pl->counter + 3;
   ua.status = pl->status;
   ua.warm = pl->warm;
+  ua.done = pl->warm != nullptr ? pl->counter + kDoneWord : nullptr;
+  ra.done = ua.done;
 }
 
 // The planner's state after a step has been enqueued.
@@ -792,7 +794,7 @@ int create_planner(const aero_limits_t* limits, aero_planner_t** out, bool batch
   chk(alloc(&pl->stage2_x, (size_t)L.E_max * (L.T_max + 1) * 10));
   chk(alloc(&pl->counter, kCounterWords));
   chk(alloc(&pl->status, 1));
-  if (!batch_slot) chk(alloc(&pl->warm, warm_words(L.E_max, L.T_max)));
+  if (!batch_slot) chk(alloc(&pl->warm, (size_t)L.E_max * warm_words(L.E_max, L.T_max)));
   chk(alloc(&pl->dbg_u, (size_t)L.E_max * D * L.T_max * 4));
   chk(alloc(&pl->dbg_x, (size_t)L.E_max * D * (L.T_max + 1) * 10));
   chk(alloc(&pl->dbg_d, (size_t)L.E_max * D * L.T_max));

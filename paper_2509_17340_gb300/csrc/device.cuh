@@ -20,6 +20,12 @@ __device__ __forceinline__ void pdl_start() {
   asm volatile("griddepcontrol.wait;" ::: "memory");
 }
 
+// The first half of pdl_start alone: let the next kernel be scheduled, without
+// waiting for the predecessor.
+__device__ __forceinline__ void pdl_trigger() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 // ---------------------------------------------------------------------------
 // Philox4x32-10 (Salmon et al., SC'11): ten rounds of two 32x32 multiplies;
 // the key is bumped by the Weyl constants before every round but the first.

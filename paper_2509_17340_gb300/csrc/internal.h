@@ -14,7 +14,11 @@ constexpr int kMaxE = 64;
 // Tickets of last-CTA patterns, zero between launches: [0] the update's
 // selection, [1] unused, [2] the batched grid scan, [3 + e] the Stage I CTAs of
 // instance e in the split pass that also runs the update.
-constexpr int kCounterWords = 3 + kMaxE;
+// [0] selection ticket, [1], [2] grid counters, [3, 3 + kMaxE) the split pass's
+// instance tickets, then the one-lane pass's finished-CTA count and the update
+// launch's exit ticket
+constexpr int kCounterWords = 5 + kMaxE;
+constexpr int kDoneWord = 3 + kMaxE;
 constexpr int kMaxT = 128;
 constexpr int kGridMax = 96;         // collision-grid cells per axis, at most
 constexpr int kGridCellsMax = kGridMax * kGridMax * kGridMax;
@@ -143,6 +147,8 @@ struct RolloutArgs {
   float* dbg_u;            // E x D x T x 4
   float* dbg_x;            // E x D x (T+1) x 10
   float* dbg_d;            // E x D x T
+  unsigned int* done;      // the one-lane pass: its CTAs count themselves here when they finish
+                           // (read by the update launch), or null
 };
 
 struct UpdateArgs {
@@ -167,13 +173,15 @@ struct UpdateArgs {
   unsigned int* counter;   // last-CTA ticket, 0 between launches
   unsigned int* inst_counter;  // E tickets of the split Stage I pass, 0 between launches
   int* status;             // bit 0: a normaliser eta was not a positive finite number
-  float* warm;             // scratch of the split pass's warm-up block (warm_words floats), or
-                           // null: no warm-up block
+  float* warm;             // scratch of the warm-up runs of the update's code: E regions of
+                           // warm_words(E, T) floats; null: no warm-up runs
+  unsigned int* done;      // the update launch: {finished CTAs of the one-lane pass, exit
+                           // ticket}, both reset by its last CTA; or null
 };
 
-// Scratch of the split pass's warm-up block for up to E instances of horizon T
-// (floats): nominals E x T x 4, Stage II states (T + 1) x 10, candidate costs E,
-// best sequence T x 4, then three words (best index, ticket, status).
+// One region of the warm-up scratch for E instances of horizon T (floats):
+// nominals E x T x 4, Stage II states (T + 1) x 10, candidate costs E, best
+// sequence T x 4, then three words (best index, ticket, status).
 __host__ __device__ constexpr size_t warm_words(int E, int T) {
   return (size_t)E * T * 4 + (size_t)(T + 1) * 10 + E + (size_t)T * 4 + 3;
 }

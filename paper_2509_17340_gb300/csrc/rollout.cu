@@ -776,19 +776,46 @@ __device__ __forceinline__ void update_unit(const UpdateArgs& a, int e, bool fin
 __global__ void __launch_bounds__(NT, 6) k_rollout(RolloutArgs a) {
   pdl_start();
   rollout_unit<true>(a, blockIdx.y, blockIdx.x, a.ctr3);
+  if (a.done != nullptr) {
+    __syncthreads();
+    if (threadIdx.x == 0) atomicAdd(a.done, 1u);
+  }
+}
+
+// A warm-up run of the update's code on instance e's inputs: s_ua (a copy of
+// ua in shared memory) gets every output of the update (nominal, Stage II
+// states, costs, selection, tickets, status) in region e of ua.warm; instance
+// e's nominal is copied there first and the ticket set so that the selection
+// runs too.  The update runs once per launch, so without it its instructions
+// would be fetched cold (from DRAM once the L2 has been overwritten) on the
+// critical path; the warm-up run's results are discarded.  It may read
+// partials that other CTAs are writing: every access of the update stays in
+// bounds whatever the values read.  Every thread of the CTA calls it.
+__device__ __forceinline__ void warm_setup(UpdateArgs* s_ua, const UpdateArgs& ua, int e) {
+  const int E = ua.E, T = ua.T;
+  float* const sc = ua.warm + (size_t)e * warm_words(E, T);
+  if (threadIdx.x == 0) {
+    s_ua->u_nom = sc;
+    s_ua->stage2_x = sc + (size_t)E * T * 4;
+    s_ua->cand = s_ua->stage2_x + (size_t)(T + 1) * 10;
+    s_ua->u_best = s_ua->cand + E;
+    s_ua->best_idx = reinterpret_cast<int*>(s_ua->u_best + (size_t)T * 4);
+    s_ua->counter = reinterpret_cast<unsigned int*>(s_ua->best_idx + 1);
+    s_ua->status = reinterpret_cast<int*>(s_ua->counter + 1);
+    s_ua->dbg_pre = nullptr;
+    *s_ua->counter = (unsigned)(E - 1);
+  }
+  for (int i = threadIdx.x; i < 4 * T; i += blockDim.x) sc[(size_t)e * T * 4 + i] = ua.u_nom[(size_t)e * T * 4 + i];
+  __syncthreads();
 }
 
 // The split pass with the update of every instance run by the last of its
 // CTAs to finish (a ticket per instance, reset by that CTA): no update launch.
 // Block b >= w runs CTA (b - w) mod nb of instance (b - w) / nb.  With a
-// warm-up block (w = 1: ua.warm set), block 0 runs the same update code at
-// the start of the launch on instance 0's inputs with every output (nominal,
-// Stage II states, costs, selection, tickets, status) in ua.warm: the update
-// runs once per launch, so its instructions would otherwise be fetched cold
-// (from DRAM after the L2 has been overwritten) by the CTAs that finish last,
-// on the launch's critical path.  The warm-up block's results are discarded;
-// it reads the partials while other CTAs write them, and every access of the
-// update stays in bounds whatever the values read.
+// warm-up block (w = 1: ua.warm set), block 0 runs the same update code (one
+// call site) at the start of the launch as a warm-up run on instance 0's
+// inputs (warm_setup), so that the code is in L2 when the CTAs that finish
+// last reach it.
 __global__ void __launch_bounds__(ST, 2) k_rollout_split(RolloutArgs a, UpdateArgs ua) {
   pdl_start();
   __shared__ bool s_last_b;
@@ -809,24 +836,7 @@ __global__ void __launch_bounds__(ST, 2) k_rollout_split(RolloutArgs a, UpdateAr
   }
   block_copy_param(&s_ua, &ua);
   __syncthreads();
-  if (warm) {
-    // outputs into the scratch; the ticket set so that the selection runs too
-    float* const sc = ua.warm;
-    const int E = ua.E, T = ua.T;
-    if (threadIdx.x == 0) {
-      s_ua.u_nom = sc;
-      s_ua.stage2_x = sc + (size_t)E * T * 4;
-      s_ua.cand = s_ua.stage2_x + (size_t)(T + 1) * 10;
-      s_ua.u_best = s_ua.cand + E;
-      s_ua.best_idx = reinterpret_cast<int*>(s_ua.u_best + (size_t)T * 4);
-      s_ua.counter = reinterpret_cast<unsigned int*>(s_ua.best_idx + 1);
-      s_ua.status = reinterpret_cast<int*>(s_ua.counter + 1);
-      s_ua.dbg_pre = nullptr;
-      *s_ua.counter = (unsigned)(E - 1);
-    }
-    for (int i = threadIdx.x; i < 4 * T; i += ST) sc[i] = ua.u_nom[i];
-    __syncthreads();
-  }
+  if (warm) warm_setup(&s_ua, ua, 0);
   extern __shared__ __align__(16) unsigned char fused_smem[];  // the split pass's, free again
   update_unit<ST>(s_ua, e, s_ua.final_stage != 0, fused_smem);
 }
@@ -835,13 +845,39 @@ __global__ void __launch_bounds__(ST, 2) k_rollout_split(RolloutArgs a, UpdateAr
 // batched one does, so that both compile the same code (the Stage II costs
 // then agree bit for bit; from kernel parameters the compiler contracts some
 // products differently).
+//
+// With a.warm set, a CTA that starts while Stage I still runs first runs its
+// instance's update as a warm-up run (warm_setup) before it waits for Stage I:
+// the launch is programmatic, so its CTAs start as soon as the last CTAs of
+// Stage I have started, and the warm-up runs overlap Stage I's last wave; the
+// real update then finds its code in L2 and this SM's instruction caches.  A
+// CTA that starts after Stage I has finished (every one of its CTAs counted
+// in a.done[0]: the launch was not overlapped) skips the warm-up run.  One
+// call site for both runs (the same code).
 __global__ void __launch_bounds__(UT) k_update(UpdateArgs a) {
-  pdl_start();
   __shared__ UpdateArgs s_a;
-  block_copy_param(&s_a, &a);
-  __syncthreads();
+  __shared__ bool s_warm;
   extern __shared__ __align__(16) unsigned char upd_smem[];  // update_smem_bytes(T, UT / 32, refine)
-  update_unit<UT>(s_a, blockIdx.x, s_a.final_stage != 0, upd_smem);
+  if (threadIdx.x == 0)
+    s_warm = a.warm != nullptr &&
+             (a.done == nullptr || *reinterpret_cast<volatile unsigned int*>(a.done) < (unsigned)(a.nb * a.E));
+  __syncthreads();
+#pragma unroll 1
+  for (int run = s_warm ? 0 : 1; run < 2; ++run) {
+    if (run == 1) pdl_start();
+    else pdl_trigger();
+    block_copy_param(&s_a, &a);
+    __syncthreads();
+    if (run == 0) warm_setup(&s_a, a, blockIdx.x);
+    update_unit<UT>(s_a, blockIdx.x, s_a.final_stage != 0, upd_smem);
+    __syncthreads();  // s_a and the scratch free for the next run
+  }
+  // the last CTA to leave resets the count and the exit ticket (every CTA has
+  // read the count by then, and Stage I has finished)
+  if (a.done != nullptr && threadIdx.x == 0 && atomicAdd(a.done + 1, 1u) == gridDim.x - 1) {
+    a.done[0] = 0u;
+    a.done[1] = 0u;
+  }
 }
 
 // ---------------------------------------------------------------------------

@@ -151,17 +151,19 @@ def test_noalloc_first_call_inside_capture_is_refused(aero):
     assert r.returncode == 0 and r.stdout.strip().endswith("ok"), r.stdout + r.stderr
 
 
-@pytest.mark.parametrize("refine", [0, 5])
-def test_split_pass_outputs_equal_with_and_without_the_warm_up_block(aero, refine):
-    # a planner's split pass runs a warm-up block (the update's code on
-    # scratch at the start of the launch); the no-allocation entry point runs
-    # the same kernel without it.  The nearest-point distances do not depend
-    # on the grid's cell edge, and every sum runs in a fixed order, so the two
-    # agree bit for bit: the warm-up block writes nothing the step returns.
+@pytest.mark.parametrize("lanes,refine", [(4, 0), (4, 5), (1, 0), (1, 5)])
+def test_outputs_equal_with_and_without_the_fused_update_and_warm_up_block(aero, lanes, refine):
+    # a planner's Stage I launch runs a warm-up block (the update's code on
+    # scratch at the start of the launch) and, in the one-lane pass, the
+    # update in the last CTA of each instance; the no-allocation entry point
+    # runs neither (the one-lane pass's update is a launch of its own).  The
+    # nearest-point distances do not depend on the grid's cell edge, and every
+    # sum runs in a fixed order, so the two agree bit for bit: the warm-up
+    # block writes nothing the step returns.
     import torch
     dev = torch.device("cuda")
     w = I.make_workload("ensemble")
-    P = dict(w.params, lanes_per_sample=4, refine_steps=refine)
+    P = dict(w.params, lanes_per_sample=lanes, refine_steps=refine)
     cloud = torch.from_numpy(w.cloud).to(dev)
     state = aero.state_struct(w.p0, w.q0, w.v0)
     pl = aero.Planner(E_max=P["E"], K_max=P["K"], T_max=P["T"],
