@@ -553,8 +553,12 @@ class PlannerRun:
         return [a.elapsed_time(b) for a, b in gev]
 
     def e2e(self, n: int, warmup: int, dist=None) -> dict:
-        """End to end through aero_plan_step_host: pinned host cloud and warm
-        start in, nominals, best sequence, costs and index out, every step."""
+        """End to end through the C-ABI call aero_plan_step_host: pinned host
+        cloud and warm start in, nominals, best sequence, costs and index out,
+        every step.  The call's arguments are marshalled once (only the step
+        counter in the parameter struct changes); the timed region is the
+        call itself, which returns when the outputs are in the host buffers."""
+        import ctypes as C
         torch = self.torch
         P, w = self.P, self.w
         hc = torch.from_numpy(w.cloud.copy()).pin_memory()
@@ -563,8 +567,13 @@ class PlannerRun:
         hcand = torch.empty((P["E"],)).pin_memory()
         hbest = torch.empty((1,), dtype=torch.int32).pin_memory()
         times = []
-        ps = self.aero.params_struct(P)  # marshalled once; only the step counter changes
+        ps = self.aero.params_struct(P)
         h0 = torch.from_numpy(w.hover_nominal())
+        goal = (C.c_float * 3)(*[float(x) for x in w.goal])
+        call = self.aero.lib().aero_plan_step_host
+        args = (self.pl.handle, C.byref(self.state), hc.data_ptr(), hc.shape[0], goal, C.byref(ps),
+                hu.data_ptr(), hb.data_ptr(), hcand.data_ptr(), hbest.data_ptr(),
+                self.stream.cuda_stream)
         for i in range(warmup + n):
             with torch.cuda.stream(self.stream):
                 self.flush.fill_(float(i))
@@ -572,8 +581,10 @@ class PlannerRun:
             hu.copy_(h0)
             ps.step_id = 10_000 + i
             t0 = time.perf_counter()
-            self.pl.plan_step_host(self.state, hc, w.goal, ps, hu, hb, hcand, hbest, self.stream)
+            rc = call(*args)
             dt = time.perf_counter() - t0
+            if rc != 0:
+                raise RuntimeError(f"aero_plan_step_host returned {rc}")
             if i >= warmup:
                 times.append(dt)
         e_tot = max_over_ranks(sum(times), dist, self.dev)

@@ -194,11 +194,15 @@ int aero_plan_step(aero_planner_t* planner, const aero_state_t* x0, const float*
                    int32_t* best_idx_out, void* stream);
 
 /* The same step for callers whose data lives in host memory: every array
- * argument is a host pointer (a pinned cloud and warm start give the fastest
- * copies).  The cloud and the warm start are copied into the planner's device
- * buffers on `stream`, the step runs, its outputs come back in one copy into
- * the planner's pinned staging buffer, and the call returns after
- * synchronising the stream and copying them into the caller's buffers. */
+ * argument is a host pointer.  A cloud in page-locked (pinned or registered)
+ * host memory is read in place by the partition pass over the host link,
+ * which also stores the points in the planner's device buffer for the later
+ * passes; a pageable cloud is copied into that buffer first.  The warm start
+ * is copied into the planner's device buffer (pinned is fastest), the step
+ * runs on `stream`, its outputs come back in one copy into the planner's
+ * pinned staging buffer, and the call returns after synchronising the stream
+ * and copying them into the caller's buffers.  The cloud must not change
+ * during the call. */
 int aero_plan_step_host(aero_planner_t* planner, const aero_state_t* x0, const float* cloud_xyz,
                         int64_t n_points, const float goal[3], const aero_params_t* params,
                         float* u_nom_inout, float* u_best_out, float* cand_costs_out,

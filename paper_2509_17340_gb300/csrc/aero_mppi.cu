@@ -601,13 +601,20 @@ void note_step(aero_planner* pl, const aero_params_t& p, const StepArgs& a) {
   pl->last_n_points = a.pa.n;
 }
 
-// Enqueue one step; all pointers already validated.
+// Enqueue one step; all pointers already validated.  mapped: null, or the
+// device address of the cloud in page-locked host memory; the partition then
+// reads the points from there and stores them at `cloud` (a device array),
+// which the later passes read.
 int enqueue_step(aero_planner* pl, const aero_state_t* x0, const float* cloud, int64_t n,
                  const float* goal, const aero_params_t& p, float* u_nom, float* u_best,
-                 float* cand, int32_t* best_idx, cudaStream_t s) {
+                 float* cand, int32_t* best_idx, cudaStream_t s, const float* mapped = nullptr) {
   StepArgs a;
   make_step_args(pl, x0, cloud, n, goal, p, u_nom, u_best, cand, best_idx,
                  lanes_of(p, kQuadMaxSamples), false, true, a);
+  if (mapped) {
+    a.pa.cloud = mapped;
+    a.pa.copy_to = const_cast<float*>(cloud);
+  }
 
   cudaError_t e;
   aero_planner::ProfSlot* prof = prof_slot(pl, p.iters);
@@ -880,8 +887,20 @@ int aero_plan_step_host(aero_planner_t* pl, const aero_state_t* x0, const float*
   cudaStream_t s = (cudaStream_t)stream;
   const size_t nu = (size_t)params->E * params->T * 4;
   cudaError_t e;
-  if (n > 0 && (e = cudaMemcpyAsync(pl->stage_cloud, cloud, sizeof(float) * 3 * n,
-                                    cudaMemcpyHostToDevice, s)) != cudaSuccess)
+  // a cloud in page-locked host memory is read by the partition itself (over
+  // the host link, overlapped with its arithmetic); any other is copied first
+  const float* mapped = nullptr;
+  if (n > 0) {
+    cudaPointerAttributes at{};
+    if (cudaPointerGetAttributes(&at, cloud) == cudaSuccess && at.type == cudaMemoryTypeHost &&
+        at.devicePointer != nullptr)
+      mapped = static_cast<const float*>(at.devicePointer);
+    else
+      cudaGetLastError();  // an unregistered pointer is not an error here
+  }
+  if (n > 0 && !mapped &&
+      (e = cudaMemcpyAsync(pl->stage_cloud, cloud, sizeof(float) * 3 * n, cudaMemcpyHostToDevice, s)) !=
+          cudaSuccess)
     return cuda_fail(e);
   // outputs laid out back to back (each part stays 16-byte aligned)
   const size_t nb = (size_t)params->T * 4, ne = (size_t)params->E;
@@ -891,7 +910,8 @@ int aero_plan_step_host(aero_planner_t* pl, const aero_state_t* x0, const float*
   int32_t* d_best = reinterpret_cast<int32_t*>(d_cand + ne);
   if ((e = cudaMemcpyAsync(d_unom, u_nom, sizeof(float) * nu, cudaMemcpyHostToDevice, s)) != cudaSuccess)
     return cuda_fail(e);
-  rc = enqueue_step(pl, x0, pl->stage_cloud, n, goal, *params, d_unom, d_ubest, d_cand, d_best, s);
+  rc = enqueue_step(pl, x0, pl->stage_cloud, n, goal, *params, d_unom, d_ubest, d_cand, d_best, s,
+                    mapped);
   if (rc != AERO_OK) return rc;
   const size_t words = nu + nb + ne + 1;
   if ((e = cudaMemcpyAsync(pl->h_out, pl->stage_out, sizeof(float) * words, cudaMemcpyDeviceToHost,

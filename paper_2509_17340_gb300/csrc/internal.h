@@ -64,6 +64,8 @@ struct PartitionArgs {
   unsigned long long* keys;
   int* item_flag;  // collision set = every kept point: 1 where the point is kept, else 0
   int2* counts;    // per block (batched: per chunk of points): {non-finite points, kept points}
+  float* copy_to;  // or null; else every point read is stored here too (n x 3): a cloud read
+                   // from page-locked host memory leaves its device copy for the later passes
 };
 
 // Count and scatter passes of the candidate lists.

@@ -196,6 +196,11 @@ __global__ void __launch_bounds__(256) k_partition(PartitionArgs a, const PartTa
   __syncthreads();
   int nf = 0, kept = 0;
   for (; i < a.n; i += stride) {
+    if (a.copy_to) {
+      a.copy_to[3 * i] = pt.x;
+      a.copy_to[3 * i + 1] = pt.y;
+      a.copy_to[3 * i + 2] = pt.z;
+    }
     const int r = partition_point(a, st, i, pt);
     nf += r == 0;
     kept += r == 2;

@@ -383,13 +383,19 @@ def test_repeatable_bitwise(aero, planner):
     assert np.array_equal(a["u_nom"], b["u_nom"]) and np.array_equal(a["cand"], b["cand"])
 
 
-def test_host_api_matches_device_api(aero, planner):
+@pytest.mark.parametrize("name,pinned", [("plain", True), ("plain", False),
+                                         ("ensemble_small_l1", True), ("ensemble_small", False)])
+def test_host_api_matches_device_api(aero, planner, name, pinned):
+    # a cloud in page-locked memory is read by the partition in place (and
+    # copied to the device by it); a pageable one is copied first
     import torch
-    w = _case("plain")
+    w = _case(name)
     P = w.params
     u0 = w.hover_nominal()
     a = run_gpu(aero, planner, w, P, u0, debug=False)
-    cloud = torch.from_numpy(w.cloud).pin_memory()
+    cloud = torch.from_numpy(w.cloud.copy())
+    if pinned:
+        cloud = cloud.pin_memory()
     un = torch.from_numpy(u0.copy()).pin_memory()
     ub = torch.zeros((P["T"], 4)).pin_memory()
     cand = torch.zeros(P["E"]).pin_memory()
