@@ -407,6 +407,30 @@ def test_host_api_matches_device_api(aero, planner, name, pinned):
     assert np.array_equal(ub.numpy(), a["u_best"])
 
 
+@pytest.mark.parametrize("name", ["plain", "ensemble_small"])
+def test_unaligned_cloud_matches_aligned(aero, planner, name):
+    # a cloud at an address that is not 16-byte aligned gives the same keys
+    # and the same step
+    import torch
+    w = _case(name)
+    P = w.params
+    u0 = w.hover_nominal()
+    a = run_gpu(aero, planner, w, P, u0, debug=True)
+    n = len(w.cloud)
+    buf = torch.zeros((n + 1) * 3, dtype=torch.float32, device="cuda")
+    buf[3:] = torch.from_numpy(np.ascontiguousarray(w.cloud, np.float32).reshape(-1)).cuda()
+    cloud = buf[3:].view(n, 3)   # 12 bytes past a 256-byte boundary
+    assert cloud.data_ptr() % 16 != 0
+    un = torch.from_numpy(np.ascontiguousarray(u0, np.float32)).cuda()
+    u_best, cand, best = aero.plan_step(planner, w.p0, w.q0, w.v0, cloud, w.goal, P, un)
+    torch.cuda.synchronize()
+    assert planner.sync_status() == 0
+    assert np.array_equal(planner.debug("FINE_KEYS"), a["keys"])
+    assert np.array_equal(planner.debug("POINT_COUNTS"), a["point_counts"])
+    assert np.array_equal(un.cpu().numpy().astype(np.float64), a["u_nom"])
+    assert np.array_equal(cand.cpu().numpy(), a["cand"]) and int(best.cpu()[0]) == a["best"]
+
+
 def test_invalid_arguments_rejected(aero, planner):
     import torch
     w = _case("plain")
