@@ -151,15 +151,18 @@ def test_noalloc_first_call_inside_capture_is_refused(aero):
     assert r.returncode == 0 and r.stdout.strip().endswith("ok"), r.stdout + r.stderr
 
 
-@pytest.mark.parametrize("lanes,refine", [(4, 0), (4, 5), (1, 0), (1, 5)])
-def test_outputs_equal_with_and_without_the_fused_update_and_warm_up_block(aero, lanes, refine):
+@pytest.mark.parametrize("lanes,refine,events", [(4, 0, False), (4, 5, False), (1, 0, False),
+                                                  (1, 5, False), (1, 0, True), (4, 0, True)])
+def test_outputs_equal_with_and_without_the_fused_update_and_warm_up_block(aero, lanes, refine,
+                                                                           events):
     # a planner's Stage I launch runs a warm-up block (the update's code on
     # scratch at the start of the launch) and, in the one-lane pass, the
     # update in the last CTA of each instance; the no-allocation entry point
     # runs neither (the one-lane pass's update is a launch of its own).  The
     # nearest-point distances do not depend on the grid's cell edge, and every
     # sum runs in a fixed order, so the two agree bit for bit: the warm-up
-    # block writes nothing the step returns.
+    # block writes nothing the step returns.  With events around Stage I the
+    # update launch no longer overlaps it, and its CTAs skip the warm-up run.
     import torch
     dev = torch.device("cuda")
     w = I.make_workload("ensemble")
@@ -170,6 +173,8 @@ def test_outputs_equal_with_and_without_the_fused_update_and_warm_up_block(aero,
                       fine_cells_max=P["fine_az"] * P["fine_el"], n_points_max=len(w.cloud))
     u_ref = torch.from_numpy(w.hover_nominal()).to(dev)
     u_na = u_ref.clone()
+    if events:
+        pl.profile(["rollout"])
     for call in range(3):
         P["step_id"] = 100 + call
         prm = aero.params_struct(P)
