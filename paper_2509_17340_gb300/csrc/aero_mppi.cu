@@ -197,6 +197,9 @@ constexpr int kFineDup = 216, kCoarseDup = 27;
 // points per fine cone from which the partition reads a cone's key before its
 // atomic minimum: in dense clouds most points cannot lower their cone's key
 constexpr int64_t kPartFilterPointsPerCone = 32;
+// lists longer than this are scanned by the whole warp in the one-lane pass
+// when every kept point is the collision set
+constexpr int kWarpListThreshold = 8;
 
 int cuda_fail(cudaError_t e) {
   if (e == cudaSuccess) return AERO_OK;
@@ -530,6 +533,9 @@ void make_step_args(aero_planner* pl, const aero_state_t* x0, const float* cloud
   ra.T = p.T;
   ra.nb = a.nb;
   ra.lanes_per_sample = lanes;
+  // every kept point as the collision set: lists of tens to hundreds of
+  // entries, uneven across a warp's queries; P_f's are short (a few entries)
+  ra.list_thr = a.raw ? kWarpListThreshold : 0;
   ra.inv_lambda = 1.0f / p.lambda;
   for (int c = 0; c < 4; ++c) {
     ra.sigma[c] = p.sigma[c];

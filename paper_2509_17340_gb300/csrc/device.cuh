@@ -414,6 +414,44 @@ __device__ __forceinline__ float4 grid_point_of(const GridView& g, int e) {
     return __ldg(g.pts + e);
 }
 
+// min(dmax2, squared distances to the points of this lane's candidate list),
+// for the 32 lanes of a warp together (all call it): lists of at most thr
+// entries are scanned by their own lanes; each longer list is then scanned by
+// the whole warp, 32 entries per round, the lanes' minima combined with one
+// warp reduction over their bits (non-negative floats order as their bits;
+// a NaN distance, like fminf's operand, is never the minimum).  The result is
+// the exact minimum over the list, whatever the split; a warp whose lists
+// differ widely in length (every kept point as the collision set) no longer
+// runs its longest list on one lane while the others idle.
+template <bool kIdx>
+__device__ __forceinline__ float warp_split_min(const GridView& g, int2 range, float px, float py,
+                                                float pz, float dmax2, int thr) {
+  const int lane = threadIdx.x & 31;
+  const bool lng = range.y > thr;
+  float d2 = dmax2;
+  if (!lng)
+    for (int i = 0; i < range.y; ++i)
+      d2 = fminf(d2, dist2_to(grid_point_of<kIdx>(g, range.x + i), px, py, pz));
+  unsigned pend = __ballot_sync(0xffffffffu, lng);
+  while (pend) {
+    const int L = __ffs(pend) - 1;
+    pend &= pend - 1;
+    const int first = __shfl_sync(0xffffffffu, range.x, L);
+    const int n = __shfl_sync(0xffffffffu, range.y, L);
+    const float qx = __shfl_sync(0xffffffffu, px, L);
+    const float qy = __shfl_sync(0xffffffffu, py, L);
+    const float qz = __shfl_sync(0xffffffffu, pz, L);
+    unsigned best = __float_as_uint(dmax2);
+    for (int i = lane; i < n; i += 32) {
+      const float d = dist2_to(grid_point_of<kIdx>(g, first + i), qx, qy, qz);
+      if (d < dmax2) best = min(best, __float_as_uint(d));
+    }
+    best = __reduce_min_sync(0xffffffffu, best);
+    if (lane == L) d2 = __uint_as_float(best);
+  }
+  return d2;
+}
+
 // min(best, squared distances to the points of the n candidate entries from
 // `first`), kW entries per round so that kW loads are in flight; the last
 // round repeats its first entry in place of the missing ones (the minimum is

@@ -151,6 +151,9 @@ struct RolloutArgs {
   float* dbg_d;            // E x D x T
   unsigned int* done;      // the one-lane pass: its CTAs count themselves here when they finish
                            // (read by the update launch), or null
+  int list_thr;            // single planner's one-lane pass: lists longer than this are
+                           // scanned by the whole warp (warp_split_min, its own kernel
+                           // instance); 0: every lane scans its own list
 };
 
 struct UpdateArgs {

@@ -63,6 +63,9 @@ def _case(name):
     elif name == "raw":
         w = I.make_workload("ensemble")
         w.params.update(K=128, T=10, collision_set=1)
+    elif name == "raw_l1":                # one lane per sample: long lists scanned by the warp
+        w = I.make_workload("ensemble")
+        w.params.update(K=256, T=12, collision_set=1, lanes_per_sample=1)
     elif name == "empty":
         w = I.make_workload("plain")
         w.cloud = np.zeros((0, 3), np.float32)
@@ -104,7 +107,7 @@ def _case(name):
     return w
 
 
-CASES = ["plain", "ensemble_small", "ensemble_small_l1", "ensemble", "ragged", "ragged_l1", "raw",
+CASES = ["plain", "ensemble_small", "ensemble_small_l1", "ensemble", "ragged", "ragged_l1", "raw", "raw_l1",
          "empty", "single_point", "k1_t1", "degenerate", "goal_behind_iters3", "el_span",
          "max_sizes"]
 
