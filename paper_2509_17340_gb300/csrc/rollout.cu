@@ -610,6 +610,31 @@ __device__ __forceinline__ void update_unit(const UpdateArgs& a, int e, bool fin
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const float* P = a.partials + (size_t)e * a.nb * stride;
 
+  // the loads that do not wait for rho go out first, in one round trip with
+  // the first rows: the first kPre rows of this warp's weighted sums and this
+  // thread's nominal entries
+  constexpr int kW = UT / 32;
+  constexpr int kCol = kMaxT / 32;
+  constexpr int kPre = 4;
+  constexpr int kUn = (4 * kMaxT + UT - 1) / UT;
+  float4 pre[kPre][kCol];
+#pragma unroll
+  for (int r = 0; r < kPre; ++r) {
+    const int b = wid + r * kW;
+    const float4* row = reinterpret_cast<const float4*>(P + (size_t)b * stride + 4);
+#pragma unroll
+    for (int q = 0; q < kCol; ++q) {
+      const int c4 = lane + 32 * q;
+      pre[r][q] = b < a.nb && c4 < T ? __ldcg(row + c4) : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+  }
+  float* un = a.u_nom + (size_t)e * T * 4;
+  float un_pre[kUn];
+#pragma unroll
+  for (int r = 0; r < kUn; ++r) {
+    const int i = tid + r * UT;
+    un_pre[r] = i < 4 * T ? un[i] : 0.0f;
+  }
   // rho = min rho_b (a thread's first row keeps its rho_b and eta_b for the sum)
   float m = INFINITY;
   const float2 first_row = tid < a.nb ? __ldcg(reinterpret_cast<const float2*>(P + (size_t)tid * stride))
@@ -641,14 +666,30 @@ __device__ __forceinline__ void update_unit(const UpdateArgs& a, int e, bool fin
     return b < 1024 ? s_scale[b] : expf((rho - __ldcg(P + (size_t)b * stride)) * a.inv_lambda);
   };
   __syncthreads();  // s_scale complete
-  // sum_b scale_b W_b: warp w takes the rows b = w (mod 4), lane the float4
-  // columns lane, lane + 32, ...; all of a thread's loads are independent
-  constexpr int kCol = kMaxT / 32;
+  // sum_b scale_b W_b: warp w takes the rows b = w (mod kW) in order (the
+  // first kPre of them loaded above), lane the float4 columns lane, lane + 32,
+  // ...; all of a thread's loads are independent
   float4 acc[kCol];
 #pragma unroll
   for (int q = 0; q < kCol; ++q) acc[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+  for (int r = 0; r < kPre; ++r) {
+    const int b = wid + r * kW;
+    if (b < a.nb) {
+      const float sc = scale(b);
+#pragma unroll
+      for (int q = 0; q < kCol; ++q) {
+        if (lane + 32 * q < T) {
+          acc[q].x += sc * pre[r][q].x;
+          acc[q].y += sc * pre[r][q].y;
+          acc[q].z += sc * pre[r][q].z;
+          acc[q].w += sc * pre[r][q].w;
+        }
+      }
+    }
+  }
 #pragma unroll 4
-  for (int b = wid; b < a.nb; b += UT / 32) {
+  for (int b = wid + kPre * kW; b < a.nb; b += kW) {
     const float sc = scale(b);
     const float4* row = reinterpret_cast<const float4*>(P + (size_t)b * stride + 4);
 #pragma unroll
@@ -667,15 +708,18 @@ __device__ __forceinline__ void update_unit(const UpdateArgs& a, int e, bool fin
   for (int q = 0; q < kCol; ++q)
     if (lane + 32 * q < T) sm.acc[wid * T + lane + 32 * q] = acc[q];
   __syncthreads();
-  float* un = a.u_nom + (size_t)e * T * 4;
-  for (int i = tid; i < 4 * T; i += UT) {
-    const int j = i >> 2, c = i & 3;
-    float sum = 0.0f;
 #pragma unroll
-    for (int w = 0; w < UT / 32; ++w) sum += reinterpret_cast<const float*>(&sm.acc[w * T + j])[c];
-    const float v = un[i] + sum * inv_eta;
-    un[i] = v;
-    s_u[i] = v;
+  for (int r = 0; r < kUn; ++r) {
+    const int i = tid + r * UT;
+    if (i < 4 * T) {
+      const int j = i >> 2, c = i & 3;
+      float sum = 0.0f;
+#pragma unroll
+      for (int w = 0; w < kW; ++w) sum += reinterpret_cast<const float*>(&sm.acc[w * T + j])[c];
+      const float v = un_pre[r] + sum * inv_eta;
+      un[i] = v;
+      s_u[i] = v;
+    }
   }
   if (!final_stage) return;
   __syncthreads();
