@@ -104,16 +104,20 @@ def _sequence():
     return [ens, plain, empty, ens2]
 
 
-def test_bench_planner_consecutive_clouds_match_oracle(aero, orc):
+@pytest.mark.parametrize("lanes", [0, 1])
+def test_bench_planner_consecutive_clouds_match_oracle(aero, orc, lanes):
     """One planner, created as the benchmark creates it for the ensemble, plans
     the ensemble scene, the plain scene, an empty cloud and another ensemble
     scene in a row: each step equals the oracle's step on its own inputs, so
-    nothing of an earlier step (keys, counts, lists) leaks into the next."""
+    nothing of an earlier step (keys, counts, lists, the update launch's
+    finished-CTA count and tickets, the warm-up scratch) leaks into the next.
+    Both Stage I passes: the split pass these sizes select, and one lane per
+    sample with its own update launch."""
     seq = _sequence()
     P0 = seq[0].params
     pl = _bench_planner(aero, P0, max(len(w.cloud) for w in seq))
     for w in seq:
-        P = w.params
+        P = dict(w.params, lanes_per_sample=lanes)
         u0 = w.hover_nominal()
         g = _run(aero, pl, w, P, u0)
         o = orc.plan_step(w.cloud, w.p0, w.q0, w.v0, w.goal, P, u0)
