@@ -14,6 +14,9 @@
 #include <vector>
 
 #include "../../include/aero_mppi.h"
+#ifdef AERO_CHECKED
+#include <nvtx3/nvToolsExt.h>
+#endif
 #include "internal.h"
 
 using namespace aero;
@@ -607,6 +610,25 @@ void note_step(aero_planner* pl, const aero_params_t& p, const StepArgs& a) {
   pl->last_n_points = a.pa.n;
 }
 
+// NVTX ranges, one per stage, around the host's enqueue of a step (checked
+// build only; a no-op in the product build): next() closes the open range and
+// opens the next one, the destructor closes the last.
+struct StageRanges {
+#ifdef AERO_CHECKED
+  bool open = false;
+  void next(const char* name) {
+    if (open) nvtxRangePop();
+    nvtxRangePushA(name);
+    open = true;
+  }
+  ~StageRanges() {
+    if (open) nvtxRangePop();
+  }
+#else
+  void next(const char*) {}
+#endif
+};
+
 // Enqueue one step; all pointers already validated.  mapped: null, or the
 // device address of the cloud in page-locked host memory; the partition then
 // reads the points from there and stores them at `cloud` (a device array),
@@ -631,6 +653,8 @@ int enqueue_step(aero_planner* pl, const aero_state_t* x0, const float* cloud, i
       prof->last = i;
     }
   };
+  StageRanges ranges;
+  ranges.next("aero partition");
   mark(AERO_STAGE_PARTITION, 0);
   // A planner without debug buffers keeps its keys empty between steps (the
   // scatter pass empties each key it reads), so a step needs no fill; one with
@@ -660,6 +684,7 @@ int enqueue_step(aero_planner* pl, const aero_state_t* x0, const float* cloud, i
   }
   if ((e = launch_partition(a.pa, pl->d_tab, s)) != cudaSuccess) return cuda_fail(e);
   mark(AERO_STAGE_PARTITION, 1);
+  ranges.next("aero grid");
   mark(AERO_STAGE_GRID, 2);
   if (prof) {
     prof->launches[AERO_STAGE_PARTITION] = n > 0 ? 1 : 0;
@@ -682,9 +707,11 @@ int enqueue_step(aero_planner* pl, const aero_state_t* x0, const float* cloud, i
   for (int it = 0; it < p.iters; ++it) {
     a.ra.ctr3 = ctr_base | (uint32_t)it;
     a.ua.final_stage = it == p.iters - 1;
+    ranges.next("aero stage I");
     mark(AERO_STAGE_ROLLOUT, 4 + 4 * it);
     if ((e = launch_rollout(a.ra, a.ua, s)) != cudaSuccess) return cuda_fail(e);
     mark(AERO_STAGE_ROLLOUT, 5 + 4 * it);
+    ranges.next("aero update");
     mark(AERO_STAGE_UPDATE, 6 + 4 * it);
     if (!rollout_runs_update(a.ra) && (e = launch_update(a.ua, s)) != cudaSuccess) return cuda_fail(e);
     mark(AERO_STAGE_UPDATE, 7 + 4 * it);
