@@ -26,6 +26,12 @@ __device__ __forceinline__ void pdl_trigger() {
   asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 }
 
+// The second half alone: wait until the predecessor has completed and its
+// writes are visible (immediate once waited for).
+__device__ __forceinline__ void pdl_wait() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+
 // ---------------------------------------------------------------------------
 // Philox4x32-10 (Salmon et al., SC'11): ten rounds of two 32x32 multiplies;
 // the key is bumped by the Weyl constants before every round but the first.

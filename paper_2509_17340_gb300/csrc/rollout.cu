@@ -331,9 +331,6 @@ __device__ __forceinline__ void rollout_split_unit(const RolloutArgs& a, int e, 
   const int T = a.T;
   const SplitSmem m = split_layout(split_smem, T);
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-  for (int i = tid; i < T; i += ST) m.un[i] = reinterpret_cast<const float4*>(a.u_nom)[e * T + i];
-  for (int i = tid; i < 3 * T; i += ST) m.gd[i] = a.guides[e * T * 3 + i];
-
   const int k = b * QS + lane;  // this thread's sample in every phase
   const bool active = k < a.K;
   const CostParams& cp = a.cost;
@@ -358,16 +355,21 @@ __device__ __forceinline__ void rollout_split_unit(const RolloutArgs& a, int e, 
   const int wint = b & (SW - 1);
   const bool integrator = wid == wint;
   const int widx = (wid + SW - 1 - wint) & (SW - 1);
+  float S = 0.0f;  // every worker thread: the cost terms of its (sample, step) pairs
+
+  // the perturbations first: they read only the kernel's parameters, so they
+  // are drawn before the wait for the preceding launches (which may still
+  // write the nominal, the grid and the guides); then the nominal and the
+  // guides, and the clamped controls: each thread rereads only what it wrote
+  for (int j = wid; j < T; j += SW)
+    m.u[j * QS + lane] = noise_delta(k, j, e, ctr3, a.key0, a.key1, sigma);
+  pdl_wait();
   if (dbg >= 0 && integrator) {
     float* X = a.dbg_x + (size_t)dbg * (T + 1) * 10;
     for (int i = 0; i < 10; ++i) X[i] = a.x0[i];
   }
-  float S = 0.0f;  // every worker thread: the cost terms of its (sample, step) pairs
-
-  // the perturbations (independent of the nominal) while the nominal loads,
-  // then the clamped controls: each thread rereads only what it wrote
-  for (int j = wid; j < T; j += SW)
-    m.u[j * QS + lane] = noise_delta(k, j, e, ctr3, a.key0, a.key1, sigma);
+  for (int i = tid; i < T; i += ST) m.un[i] = reinterpret_cast<const float4*>(a.u_nom)[e * T + i];
+  for (int i = tid; i < 3 * T; i += ST) m.gd[i] = a.guides[e * T * 3 + i];
   __syncthreads();  // un, gd
   for (int j = wid; j < T; j += SW) {
     const float4 un = m.un[j], d = m.u[j * QS + lane];
@@ -872,7 +874,9 @@ __device__ __forceinline__ void warm_setup(UpdateArgs* s_ua, const UpdateArgs& u
 // inputs (warm_setup), so that the code is in L2 when the CTAs that finish
 // last reach it.
 __global__ void __launch_bounds__(ST, 2) k_rollout_split(RolloutArgs a, UpdateArgs ua) {
-  pdl_start();
+  // the wait for the preceding launches comes after the noise (in
+  // rollout_split_unit), so that drawing it overlaps them
+  pdl_trigger();
   __shared__ bool s_last_b;
   __shared__ UpdateArgs s_ua;
   const int w = ua.warm != nullptr ? 1 : 0;
@@ -889,6 +893,7 @@ __global__ void __launch_bounds__(ST, 2) k_rollout_split(RolloutArgs a, UpdateAr
     __threadfence();
     if (threadIdx.x == 0) ua.inst_counter[e] = 0u;
   }
+  if (warm) pdl_wait();  // the warm-up run reads the grid
   block_copy_param(&s_ua, &ua);
   __syncthreads();
   if (warm) warm_setup(&s_ua, ua, 0);
