@@ -398,12 +398,13 @@ struct RefineScratch {
   float* gs;                 // T x 10: state-term gradients at x_{j+1}
   int* qitem;                // T + 1: first item of each listed query
   int* qslot;                // T: step of each listed query
+  float* afm;                // 4 x 20: the attitude adjoint scan's warp compositions
 };
 
 __host__ __device__ constexpr size_t refine_smem_bytes(int T, int warps) {
   return 16 * (size_t)warps + 16 * (size_t)T + 8 * (size_t)T + 16 * (size_t)T + 8 * (size_t)T + 8 * (size_t)warps +
          4 * (size_t)(T + 1) * 10 + 4 * (size_t)T * 34 + 4 * (size_t)T * 10 + 4 * (size_t)(T + 1) +
-         4 * (size_t)T;
+         4 * (size_t)T + 4 * 80;
 }
 
 __device__ __forceinline__ RefineScratch refine_layout(unsigned char* base, int T, int warps) {
@@ -419,6 +420,7 @@ __device__ __forceinline__ RefineScratch refine_layout(unsigned char* base, int 
   r.gs = r.st + (size_t)T * 34;
   r.qitem = reinterpret_cast<int*>(r.gs + (size_t)T * 10);
   r.qslot = r.qitem + T + 1;
+  r.afm = reinterpret_cast<float*>(r.qslot + T);
   return r;
 }
 
@@ -554,24 +556,106 @@ __device__ void block_refine(float4* u, const float* guide, int T, const float* 
         rs.g[tid] = make_float4(lam[3], lam[4], lam[5], lam[6]);
       }
       __syncthreads();
-      // (c) the attitude recurrence on one thread
-      if (tid == 0) {
-        float* L = rs.gs + (T - 1) * 10 + 3;
-        float4 l = make_float4(L[0], L[1], L[2], L[3]);  // Lq_T = gs_q[T - 1]
-        for (int kk = T - 2; kk >= 0; --kk) {
+      // (c) the attitude recurrence Lq_k = C_k + A_{k+1}^T Lq_{k+1} (k = T-2
+      // .. 0; C_k = gs_q[k] + b_{k+1}; Lq_{T-1} = gs_q[T-1]) is affine in Lq:
+      // thread t = T-2-k holds the map x -> C_k + M x (M = A_{k+1}^T as a 4x4
+      // matrix, its columns the images of the unit vectors), and an inclusive
+      // scan composes the maps, later ones outside, so that thread t ends with
+      // the composition that takes Lq_{T-1} to Lq_k.  T - 1 <= 127 maps: up to
+      // four warps, each carrying the earlier warps' compositions.
+      static_assert(kMaxT - 1 <= 128 && kThreads >= 128, "the attitude adjoint scan spans four warps");
+      {
+        const int kk = T - 2 - tid, wid = tid >> 5;
+        const bool on = kk >= 0;
+        float M[16], c[4];
+#pragma unroll
+        for (int i = 0; i < 16; ++i) M[i] = (i % 5 == 0) ? 1.0f : 0.0f;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) c[i] = 0.0f;
+        if (on) {
           const int j = kk + 1;  // A_j: the attitude Jacobian of step j
           const float* y = rs.st + (size_t)j * 34 + 30;
           const float inv = rsqrtf(y[0] * y[0] + y[1] * y[1] + y[2] * y[2] + y[3] * y[3]);
-          const float d = (y[0] * l.x + y[1] * l.y + y[2] * l.z + y[3] * l.w) * inv * inv;
-          const float4 pl = make_float4((l.x - y[0] * d) * inv, (l.y - y[1] * d) * inv,
-                                        (l.z - y[2] * d) * inv, (l.w - y[3] * d) * inv);
           const float4 m = rk4_attitude_coefs(u[j], dp);
-          const float4 at = quat_mul4(pl, make_float4(m.x, -m.y, -m.z, -m.w));
+          const float4 mc = make_float4(m.x, -m.y, -m.z, -m.w);
+#pragma unroll
+          for (int col = 0; col < 4; ++col) {
+            // A_j^T e_col = ((e_col - yh (yh . e_col)) / |y|) (x) conj(m)
+            const float d = y[col] * inv * inv;
+            const float4 pl = make_float4(((col == 0 ? 1.f : 0.f) - y[0] * d) * inv,
+                                          ((col == 1 ? 1.f : 0.f) - y[1] * d) * inv,
+                                          ((col == 2 ? 1.f : 0.f) - y[2] * d) * inv,
+                                          ((col == 3 ? 1.f : 0.f) - y[3] * d) * inv);
+            const float4 at = quat_mul4(pl, mc);
+            M[col] = at.x;
+            M[4 + col] = at.y;
+            M[8 + col] = at.z;
+            M[12 + col] = at.w;
+          }
+          const float* Lk = rs.gs + kk * 10 + 3;
           const float4 b = rs.g[j];
+          c[0] = Lk[0] + b.x;
+          c[1] = Lk[1] + b.y;
+          c[2] = Lk[2] + b.z;
+          c[3] = Lk[3] + b.w;
+        }
+        // (M, c) o (M', c') = (M M', M c' + c)
+        auto compose = [&](const float* M2, const float* c2) {
+          float R[16], r[4];
+#pragma unroll
+          for (int i = 0; i < 4; ++i) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+              R[4 * i + q] = M[4 * i] * M2[q] + M[4 * i + 1] * M2[4 + q] + M[4 * i + 2] * M2[8 + q] +
+                             M[4 * i + 3] * M2[12 + q];
+            r[i] = M[4 * i] * c2[0] + M[4 * i + 1] * c2[1] + M[4 * i + 2] * c2[2] +
+                   M[4 * i + 3] * c2[3] + c[i];
+          }
+#pragma unroll
+          for (int i = 0; i < 16; ++i) M[i] = R[i];
+#pragma unroll
+          for (int i = 0; i < 4; ++i) c[i] = r[i];
+        };
+        if (wid < 4) {
+          const int lane = tid & 31;
+#pragma unroll
+          for (int o = 1; o < 32; o <<= 1) {
+            float M2[16], c2[4];
+#pragma unroll
+            for (int i = 0; i < 16; ++i) M2[i] = __shfl_up_sync(0xffffffffu, M[i], o);
+#pragma unroll
+            for (int i = 0; i < 4; ++i) c2[i] = __shfl_up_sync(0xffffffffu, c[i], o);
+            if (lane >= o) compose(M2, c2);
+          }
+          if (lane == 31) {
+#pragma unroll
+            for (int i = 0; i < 16; ++i) rs.afm[20 * wid + i] = M[i];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) rs.afm[20 * wid + 16 + i] = c[i];
+          }
+        }
+        __syncthreads();
+        if (on) {
+          // the earlier warps' compositions, the latest one first (inside)
+          for (int v = wid - 1; v >= 0; --v) {
+            float M2[16], c2[4];
+#pragma unroll
+            for (int i = 0; i < 16; ++i) M2[i] = rs.afm[20 * v + i];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) c2[i] = rs.afm[20 * v + 16 + i];
+            compose(M2, c2);
+          }
+        }
+        if (on) {
+          const float* L = rs.gs + (T - 1) * 10 + 3;  // Lq_{T-1}
+          const float l0 = L[0], l1 = L[1], l2 = L[2], l3 = L[3];
           float* Lk = rs.gs + kk * 10 + 3;
-          l = make_float4(Lk[0] + b.x + at.x, Lk[1] + b.y + at.y, Lk[2] + b.z + at.z,
-                          Lk[3] + b.w + at.w);
-          Lk[0] = l.x; Lk[1] = l.y; Lk[2] = l.z; Lk[3] = l.w;
+          float lo[4];
+#pragma unroll
+          for (int i = 0; i < 4; ++i)
+            lo[i] = M[4 * i] * l0 + M[4 * i + 1] * l1 + M[4 * i + 2] * l2 + M[4 * i + 3] * l3 + c[i];
+#pragma unroll
+          for (int i = 0; i < 4; ++i) Lk[i] = lo[i];
         }
       }
       __syncthreads();
