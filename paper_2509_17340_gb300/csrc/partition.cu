@@ -128,43 +128,85 @@ __device__ __forceinline__ float3 cloud_point(const PartitionArgs& a, int64_t i)
   return make_float3(__ldg(a.cloud + 3 * i), __ldg(a.cloud + 3 * i + 1), __ldg(a.cloud + 3 * i + 2));
 }
 
+constexpr int kNonFinite = -2;  // cone_of: a non-finite point
+constexpr int kOutside = -1;    // cone_of: outside the range or the elevation span
+
+// The fine cone of the point at pt, or kOutside / kNonFinite; *r2 its squared
+// range in binary32 (set for a cone only).
+__device__ __forceinline__ int cone_of(const PartitionArgs& a, const SmemTables& st, float3 pt,
+                                       float* r2_out) {
+  const float px = pt.x, py = pt.y, pz = pt.z;
+  if (!(isfinite(px) && isfinite(py) && isfinite(pz))) return kNonFinite;
+  const float dx = sub(px, a.p0[0]), dy = sub(py, a.p0[1]), dz = sub(pz, a.p0[2]);
+  float b[3];
+  to_body(a.R, dx, dy, dz, b);
+  const float rxy2 = add(mul(b[0], b[0]), mul(b[1], b[1]));
+  const float r2 = add(rxy2, mul(b[2], b[2]));
+  if (!(r2 > 0.0f && r2 <= a.rmax2)) return kOutside;
+  const float rho = __fsqrt_rn(rxy2);
+  if (a.check_lo && !(sub(mul(b[2], st.ce[0]), mul(rho, st.se[0])) >= 0.0f)) return kOutside;
+  if (a.check_hi && (sub(mul(b[2], st.ce[a.El]), mul(rho, st.se[a.El])) > 0.0f)) return kOutside;
+  const int ia = az_bin_guess(st.ca, st.sa, a.A, b[0], b[1]);
+  const int je = el_bin_guess(st.ce, st.se, a.El, b[2], rho, a.el_lo, a.el_inv);
+  const int c = je * a.A + ia;
+  if (!AERO_CHECK(c >= 0 && c < a.A * a.El, kChkFineCell)) return kOutside;
+  *r2_out = r2;
+  return c;
+}
+
+// The key of point i at squared range r2: the range bits above the index, so
+// that the minimum is the nearest point, the lowest index among equals.
+__device__ __forceinline__ unsigned long long cone_key(float r2, uint32_t i) {
+  return ((unsigned long long)__float_as_uint(r2) << 32) | (unsigned long long)i;
+}
+
 // Point i at (px, py, pz).  Returns 0 for a non-finite point, 1 for a point
 // outside the partition's range or elevation span, 2 for a kept point.
 __device__ __forceinline__ int partition_point(const PartitionArgs& a, const SmemTables& st,
                                                int64_t i, float3 pt) {
-  const float px = pt.x, py = pt.y, pz = pt.z;
-  int cell = -1;
-  const bool finite = isfinite(px) && isfinite(py) && isfinite(pz);
-  if (finite) {
-    const float dx = sub(px, a.p0[0]), dy = sub(py, a.p0[1]), dz = sub(pz, a.p0[2]);
-    float b[3];
-    to_body(a.R, dx, dy, dz, b);
-    const float rxy2 = add(mul(b[0], b[0]), mul(b[1], b[1]));
-    const float r2 = add(rxy2, mul(b[2], b[2]));
-    if (r2 > 0.0f && r2 <= a.rmax2) {
-      const float rho = __fsqrt_rn(rxy2);
-      bool ok = true;
-      if (a.check_lo && !(sub(mul(b[2], st.ce[0]), mul(rho, st.se[0])) >= 0.0f)) ok = false;
-      if (a.check_hi && (sub(mul(b[2], st.ce[a.El]), mul(rho, st.se[a.El])) > 0.0f)) ok = false;
-      if (ok) {
-        const int ia = az_bin_guess(st.ca, st.sa, a.A, b[0], b[1]);
-        const int je = el_bin_guess(st.ce, st.se, a.El, b[2], rho, a.el_lo, a.el_inv);
-        const int c = je * a.A + ia;
-        const unsigned long long key =
-            ((unsigned long long)__float_as_uint(r2) << 32) | (unsigned long long)(uint32_t)i;
-        if (AERO_CHECK(c >= 0 && c < a.A * a.El, kChkFineCell)) {
-          // dense clouds: a key at or above the cone's current minimum cannot
-          // lower it, so the atomic is skipped.  Keys only decrease during the
-          // pass, so a value read earlier is never below the current one and
-          // the test skips no atomic that would lower the key.
-          if (!a.filter || key < __ldcg(a.keys + c)) atomicMin(a.keys + c, key);
-          cell = c;
-        }
-      }
-    }
+  float r2 = 0.0f;
+  const int c = cone_of(a, st, pt, &r2);
+  if (c >= 0) {
+    const unsigned long long key = cone_key(r2, (uint32_t)i);
+    // dense clouds: a key at or above the cone's current minimum cannot
+    // lower it, so the atomic is skipped.  Keys only decrease during the
+    // pass, so a value read earlier is never below the current one and
+    // the test skips no atomic that would lower the key.
+    if (!a.filter || key < __ldcg(a.keys + c)) atomicMin(a.keys + c, key);
   }
-  if (a.item_flag) a.item_flag[i] = cell >= 0 ? 1 : 0;
-  return !finite ? 0 : cell >= 0 ? 2 : 1;
+  if (a.item_flag) a.item_flag[i] = c >= 0 ? 1 : 0;
+  return c == kNonFinite ? 0 : c >= 0 ? 2 : 1;
+}
+
+// Points 4 g .. 4 g + 3 (a 16-byte aligned cloud: three float4 loads).  The
+// four cones are found first and their keys read together, so that the four
+// reads of the current minima are in flight at once.
+__device__ __forceinline__ void partition_group(const PartitionArgs& a, const SmemTables& st,
+                                                int64_t g, float4 v0, float4 v1, float4 v2,
+                                                int& nf, int& kept) {
+  const float3 pt[4] = {make_float3(v0.x, v0.y, v0.z), make_float3(v0.w, v1.x, v1.y),
+                        make_float3(v1.z, v1.w, v2.x), make_float3(v2.y, v2.z, v2.w)};
+  const uint32_t i0 = (uint32_t)(4 * g);
+  int c[4];
+  unsigned long long key[4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    float r2 = 0.0f;
+    c[j] = cone_of(a, st, pt[j], &r2);
+    key[j] = cone_key(r2, i0 + j);
+  }
+  unsigned long long cur[4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) cur[j] = (a.filter && c[j] >= 0) ? __ldcg(a.keys + c[j]) : kEmpty;
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    if (c[j] >= 0 && key[j] < cur[j]) atomicMin(a.keys + c[j], key[j]);
+    nf += c[j] == kNonFinite;
+    kept += c[j] >= 0;
+  }
+  if (a.item_flag)
+    reinterpret_cast<int4*>(a.item_flag)[g] =
+        make_int4(c[0] >= 0 ? 1 : 0, c[1] >= 0 ? 1 : 0, c[2] >= 0 ? 1 : 0, c[3] >= 0 ? 1 : 0);
 }
 
 // The block's totals of (non-finite, kept) points, stored by thread 0 at *out.
@@ -185,26 +227,82 @@ __device__ __forceinline__ void block_count2(int nf, int kept, int2* out) {
   if (threadIdx.x == 0) *out = make_int2(s_nf, s_kept);
 }
 
+// Clouds of at least this many points (16-byte aligned) take four points per
+// thread (three float4 loads, the four cones' minima read together); smaller
+// ones, where the launch is latency bound and the occupancy of the one-point
+// instance (fewer registers) pays more, one.
+constexpr int64_t kPartVecMin = 4000000;
+constexpr int kPartBlocksPerSm = 16;
+
+
+// kGroups: four points per thread (launched for clouds of at least
+// kPartVecMin points whose buffers are 16-byte aligned), else one.
+template <bool kGroups>
 __global__ void __launch_bounds__(256) k_partition(PartitionArgs a, const PartTables* __restrict__ t) {
   pdl_start();
   __shared__ SmemTables st;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  // the first point is fetched while the edge tables load
-  float3 pt = i < a.n ? cloud_point(a, i) : make_float3(0.f, 0.f, 0.f);
-  load_tables(*t, a.A, a.El, st);
-  __syncthreads();
+  const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   int nf = 0, kept = 0;
-  for (; i < a.n; i += stride) {
-    if (a.copy_to) {
-      a.copy_to[3 * i] = pt.x;
-      a.copy_to[3 * i + 1] = pt.y;
-      a.copy_to[3 * i + 2] = pt.z;
+  if constexpr (kGroups) {
+    const int64_t ng = a.n >> 2;
+    const float4* c4 = reinterpret_cast<const float4*>(a.cloud);
+    float4 v0 = make_float4(0.f, 0.f, 0.f, 0.f), v1 = v0, v2 = v0;
+    int64_t g = tid;
+    // the first group is fetched while the edge tables load, each next one
+    // before the current one is partitioned
+    if (g < ng) {
+      v0 = __ldg(c4 + 3 * g);
+      v1 = __ldg(c4 + 3 * g + 1);
+      v2 = __ldg(c4 + 3 * g + 2);
     }
-    const int r = partition_point(a, st, i, pt);
-    nf += r == 0;
-    kept += r == 2;
-    if (i + stride < a.n) pt = cloud_point(a, i + stride);
+    load_tables(*t, a.A, a.El, st);
+    __syncthreads();
+    for (; g < ng; g += stride) {
+      const float4 w0 = v0, w1 = v1, w2 = v2;
+      if (g + stride < ng) {
+        v0 = __ldg(c4 + 3 * (g + stride));
+        v1 = __ldg(c4 + 3 * (g + stride) + 1);
+        v2 = __ldg(c4 + 3 * (g + stride) + 2);
+      }
+      if (a.copy_to) {
+        float4* d = reinterpret_cast<float4*>(a.copy_to) + 3 * g;
+        d[0] = w0;
+        d[1] = w1;
+        d[2] = w2;
+      }
+      partition_group(a, st, g, w0, w1, w2, nf, kept);
+    }
+    // the last n mod 4 points
+    const int64_t i = 4 * ng + tid;
+    if (i < a.n) {
+      const float3 pt = cloud_point(a, i);
+      if (a.copy_to) {
+        a.copy_to[3 * i] = pt.x;
+        a.copy_to[3 * i + 1] = pt.y;
+        a.copy_to[3 * i + 2] = pt.z;
+      }
+      const int r = partition_point(a, st, i, pt);
+      nf += r == 0;
+      kept += r == 2;
+    }
+  } else {
+    int64_t i = tid;
+    // the first point is fetched while the edge tables load
+    float3 pt = i < a.n ? cloud_point(a, i) : make_float3(0.f, 0.f, 0.f);
+    load_tables(*t, a.A, a.El, st);
+    __syncthreads();
+    for (; i < a.n; i += stride) {
+      if (a.copy_to) {
+        a.copy_to[3 * i] = pt.x;
+        a.copy_to[3 * i + 1] = pt.y;
+        a.copy_to[3 * i + 2] = pt.z;
+      }
+      const int r = partition_point(a, st, i, pt);
+      nf += r == 0;
+      kept += r == 2;
+      if (i + stride < a.n) pt = cloud_point(a, i + stride);
+    }
   }
   if (a.counts) block_count2(nf, kept, a.counts + blockIdx.x);
 }
@@ -786,13 +884,19 @@ int blocks_for(int64_t n, int threads, int cap) {
 }  // namespace
 
 int partition_blocks(int64_t n) {
-  const int cap = 16 * device_sms();
-  return n > 0 ? blocks_for(n, 256, cap < kPartBlocksMax ? cap : kPartBlocksMax) : 0;
+  const int cap = kPartBlocksPerSm * device_sms();
+  const int64_t threads = n >= kPartVecMin ? (n + 3) / 4 : n;  // four points per thread
+  return n > 0 ? blocks_for(threads, 256, cap < kPartBlocksMax ? cap : kPartBlocksMax) : 0;
 }
 
 cudaError_t launch_partition(const PartitionArgs& a, const PartTables* t, cudaStream_t s) {
   if (a.n == 0) return cudaSuccess;
-  return launch_k(k_partition, dim3(partition_blocks(a.n)), dim3(256), s, true, a, t);
+  const uintptr_t bits = reinterpret_cast<uintptr_t>(a.cloud) |
+                         reinterpret_cast<uintptr_t>(a.copy_to) |
+                         reinterpret_cast<uintptr_t>(a.item_flag);
+  if (a.n >= kPartVecMin && (bits & 15u) == 0)
+    return launch_k(k_partition<true>, dim3(partition_blocks(a.n)), dim3(256), s, true, a, t);
+  return launch_k(k_partition<false>, dim3(partition_blocks(a.n)), dim3(256), s, true, a, t);
 }
 
 cudaError_t launch_grid_count(const CandArgs& ca, const GuideArgs& ga, cudaStream_t s) {
