@@ -577,6 +577,58 @@ def test_plan_step_empty_cloud(orc):
     assert np.all(np.isfinite(out["cand"]))
 
 
+@pytest.mark.parametrize("iters", [1, 2])
+def test_plan_step_is_the_stated_composition(orc, iters):
+    """The whole step (Sec. IV) equals its stages composed by hand from the
+    separately pinned functions: partition, coarse argmax, goal and anchor
+    cells, anchors and quintic guides, then per iteration the clamped
+    perturbations of that iteration's counter, the rollouts, S(1) with the
+    instance's guide and the update of the iteration's nominal; then Stage II
+    (S(2) of the updated nominals) and the argmin.  A step that wired a stage
+    to the wrong instance, iteration, guide or cost stage fails here."""
+    w = I.make_workload("plain", seed=4)
+    P = I.workload_params("ensemble")
+    P.update(E=4, M_h=2, M_v=2, K=24, T=6, iters=iters, Q_track=15.0, step_id=9, seed=77)
+    rng = np.random.default_rng(4)
+    q0 = I.random_unit_quaternion(rng)
+    v0 = np.array([1.0, -0.4, 0.2], np.float32)
+    u0 = np.zeros((P["E"], P["T"], 4), np.float32)
+    u0[..., 0] = 9.81
+    u0[..., 1:] = rng.uniform(-0.5, 0.5, (P["E"], P["T"], 3))
+    out = orc.plan_step(w.cloud, w.p0, q0, v0, w.goal, P, u0)
+    x0 = np.concatenate([w.p0, q0, v0]).astype(np.float64)
+    goal = w.goal.astype(np.float64)
+    keys, _ = orc.partition(w.cloud, w.p0, q0, P)
+    assert np.array_equal(out["keys"], keys)
+    win, _ = orc.coarse(keys, P)
+    cells = orc.anchor_cells(orc.goal_fine_cell(w.goal, w.p0, q0, P), P)
+    pts = orc.collision_set(w.cloud, w.p0, q0, keys, P)
+    assert len(pts) > 0
+    lo, hi = np.array(P["u_min"]), np.array(P["u_max"])
+    K, T = P["K"], P["T"]
+    cand = np.zeros(P["E"])
+    for e in range(P["E"]):
+        pref = orc.anchor(x0[:3], x0[3:7], orc.cell_direction(P, int(win[cells[e]])), P["ell"])
+        assert np.abs(out["anchors"][e] - pref).max() < 1e-12
+        _, guide = orc.guide(x0[:3], x0[7:], pref, P)
+        assert np.abs(out["guides"][e] - guide).max() < 1e-12
+        un = u0[e].astype(np.float64)
+        for it in range(iters):
+            d = orc.noise_range(P, e, 0, K, it=it)
+            U = np.clip(un + d, lo, hi)
+            S = np.array([orc.cost_terms(orc.rollout(x0, U[k], P["dt"], P["mass"], P["g"]), U[k],
+                                         guide, goal, pts, P, stage=1)["S"] for k in range(K)])
+            un, _ = orc.mppi_update(S, (U - un).reshape(K, -1), P["lam"], un)
+        assert np.allclose(out["S1"][e], S, rtol=1e-12, atol=0)
+        assert np.abs(out["u_nom"][e] - un).max() < 1e-12
+        X2 = orc.rollout(x0, un, P["dt"], P["mass"], P["g"])
+        assert np.abs(out["X2"][e] - X2).max() < 1e-12
+        cand[e] = orc.cost_terms(X2, un, None, goal, pts, P, stage=2)["S"]
+    assert np.allclose(out["cand"], cand, rtol=1e-12, atol=0)
+    assert out["best"] == int(np.argmin(cand))
+    assert np.array_equal(out["u_best"], out["u_nom"][out["best"]])
+
+
 # ----------------------------------------------------------------- collision sets
 
 def _clean_cloud(rng, p0, R, P, n):
