@@ -518,10 +518,22 @@ __device__ __forceinline__ float norm3f(float a, float b, float c) {
   return fast_sqrt(a * a + b * b + c * c);
 }
 
+// A goal at rest: v_goal = 0 and q_goal = (1, 0, 0, 0), the defaults.  Then
+// the velocity error is |v| and the attitude error 2 sqrt(2) |vec(q)| (the
+// quaternion product's factors 0 and 1 are exact), which goal_term evaluates
+// without the product.  Decided once per kernel, before the step loop.
+__device__ __forceinline__ bool goal_at_rest(const CostParams& c) {
+  return c.v_goal[0] == 0.0f && c.v_goal[1] == 0.0f && c.v_goal[2] == 0.0f && c.q_goal[0] == 1.0f &&
+         c.q_goal[1] == 0.0f && c.q_goal[2] == 0.0f && c.q_goal[3] == 0.0f;
+}
+
 // Goal term of one step: Q_p |p - p_goal| + Q_v |v - v_goal| + Q_q ||R R_g^T - I||_F.
-__device__ __forceinline__ float goal_term(const State& x, const CostParams& c) {
-  return c.Q_p * norm3f(x.p[0] - c.goal_rel[0], x.p[1] - c.goal_rel[1], x.p[2] - c.goal_rel[2]) +
-         c.Q_v * norm3f(x.v[0] - c.v_goal[0], x.v[1] - c.v_goal[1], x.v[2] - c.v_goal[2]) +
+__device__ __forceinline__ float goal_term(const State& x, const CostParams& c, bool at_rest) {
+  const float tp = c.Q_p * norm3f(x.p[0] - c.goal_rel[0], x.p[1] - c.goal_rel[1], x.p[2] - c.goal_rel[2]);
+  if (at_rest)
+    return tp + c.Q_v * norm3f(x.v[0], x.v[1], x.v[2]) +
+           c.Q_q * (2.8284271247461903f * fast_sqrt(x.q[1] * x.q[1] + x.q[2] * x.q[2] + x.q[3] * x.q[3]));
+  return tp + c.Q_v * norm3f(x.v[0] - c.v_goal[0], x.v[1] - c.v_goal[1], x.v[2] - c.v_goal[2]) +
          c.Q_q * attitude_err(x.q, c.q_goal);
 }
 

@@ -65,6 +65,8 @@ __device__ __forceinline__ void rollout_unit(const RolloutArgs& a, int e, int b,
   const bool active = k < a.K;
   const CostParams& cp = a.cost;
   const float dmax2 = cp.d_max * cp.d_max;
+  const bool at_rest = kIdx && goal_at_rest(cp);  // the batched passes (arguments in
+  // shared memory) keep the general form: the test's registers made them spill
   const int dbg = (active && k < a.dbg_D) ? (e * a.dbg_D + k) : -1;
   const float4 sigma = make_float4(a.sigma[0], a.sigma[1], a.sigma[2], a.sigma[3]);
   const float4 umin = make_float4(a.umin[0], a.umin[1], a.umin[2], a.umin[3]);
@@ -154,7 +156,7 @@ __device__ __forceinline__ void rollout_unit(const RolloutArgs& a, int e, int b,
     float c = c_ctrl;
     c += cp.Q_track * norm3f(x.p[0] - gx, x.p[1] - gy, x.p[2] - gz);
     c += cp.Q_vnorm * (x.v[0] * x.v[0] + x.v[1] * x.v[1] + x.v[2] * x.v[2]);
-    c += goal_term(x, cp);
+    c += goal_term(x, cp, at_rest);
     c += jcol_from_d2(d2, cp, dmax2);
     S.add(c);
     if (dbg >= 0) {
@@ -335,6 +337,7 @@ __device__ __forceinline__ void rollout_split_unit(const RolloutArgs& a, int e, 
   const bool active = k < a.K;
   const CostParams& cp = a.cost;
   const float dmax2 = cp.d_max * cp.d_max;
+  const bool at_rest = goal_at_rest(cp);
   const int dbg = (active && k < a.dbg_D) ? (e * a.dbg_D + k) : -1;
   const float4 sigma = make_float4(a.sigma[0], a.sigma[1], a.sigma[2], a.sigma[3]);
   const float4 umin = make_float4(a.umin[0], a.umin[1], a.umin[2], a.umin[3]);
@@ -478,7 +481,7 @@ __device__ __forceinline__ void rollout_split_unit(const RolloutArgs& a, int e, 
       const float gx = m.gd[3 * j], gy = m.gd[3 * j + 1], gz = m.gd[3 * j + 2];
       cj += cp.Q_track * norm3f(y.p[0] - gx, y.p[1] - gy, y.p[2] - gz);
       cj += cp.Q_vnorm * (y.v[0] * y.v[0] + y.v[1] * y.v[1] + y.v[2] * y.v[2]);
-      cj += goal_term(y, cp);
+      cj += goal_term(y, cp, at_rest);
       const float d2 = __int_as_float(m.d2[jj * QS + lane]);
       cj += jcol_select(d2, cp, dmax2);
       cs[i] = jq < tc && active ? cj : 0.0f;
@@ -779,7 +782,7 @@ __device__ __forceinline__ void update_unit(const UpdateArgs& a, int e, bool fin
     for (int i = 0; i < 3; ++i) x.p[i] = X[i];
     for (int i = 0; i < 4; ++i) x.q[i] = X[3 + i];
     for (int i = 0; i < 3; ++i) x.v[i] = X[7 + i];
-    s_c[tid] = goal_term(x, a.cost) + jcol_from_d2(__int_as_float(s_d2[tid]), a.cost, dmax2);
+    s_c[tid] = goal_term(x, a.cost, goal_at_rest(a.cost)) + jcol_from_d2(__int_as_float(s_d2[tid]), a.cost, dmax2);
   }
   for (int i = tid; i < (T + 1) * 10; i += UT) a.stage2_x[(size_t)e * (T + 1) * 10 + i] = s_x[i];
   __syncthreads();
