@@ -65,8 +65,10 @@ __device__ __forceinline__ void rollout_unit(const RolloutArgs& a, int e, int b,
   const bool active = k < a.K;
   const CostParams& cp = a.cost;
   const float dmax2 = cp.d_max * cp.d_max;
-  const bool at_rest = kIdx && goal_at_rest(cp);  // the batched passes (arguments in
-  // shared memory) keep the general form: the test's registers made them spill
+  // the batched passes (arguments in shared memory) keep the general form: the
+  // test's registers made them spill; so does the every-point instance, which
+  // ran 17% slower with it
+  const bool at_rest = kIdx && !kWarpLists && goal_at_rest(cp);
   const int dbg = (active && k < a.dbg_D) ? (e * a.dbg_D + k) : -1;
   const float4 sigma = make_float4(a.sigma[0], a.sigma[1], a.sigma[2], a.sigma[3]);
   const float4 umin = make_float4(a.umin[0], a.umin[1], a.umin[2], a.umin[3]);

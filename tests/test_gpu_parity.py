@@ -95,6 +95,13 @@ def _case(name):
     elif name == "el_span":                # partition over a narrow elevation span
         w = I.make_workload("ensemble")
         w.params.update(K=128, T=8, el_lo=-0.5, el_hi=0.7)
+    elif name == "goal_moving":            # a goal with a velocity and an attitude (the
+        w = I.make_workload("ensemble")    # goal term's general form)
+        q = np.array([0.97, 0.05, -0.1, 0.2])
+        w.params.update(K=256, T=16, v_goal=[1.0, 0.2, -0.3], q_goal=list(q / np.linalg.norm(q)))
+    elif name == "goal_moving_l1":
+        w = _case("goal_moving")
+        w.params["lanes_per_sample"] = 1
     elif name == "max_sizes":              # E, T and the fine grid at their maxima
         w = I.make_workload("plain")
         c = I.random_cloud(8000, seed=9, centre=(0.0, 0.0, 1.5), spread=7.0)
@@ -109,7 +116,7 @@ def _case(name):
 
 CASES = ["plain", "ensemble_small", "ensemble_small_l1", "ensemble", "ragged", "ragged_l1", "raw", "raw_l1",
          "empty", "single_point", "k1_t1", "degenerate", "goal_behind_iters3", "el_span",
-         "max_sizes"]
+         "goal_moving", "goal_moving_l1", "max_sizes"]
 
 
 @pytest.fixture(scope="module")

@@ -1,7 +1,7 @@
 """Seeded random planning steps against the FP64 oracle: ragged sample
 counts, horizons from 1 step, uneven anchor grids and partitions, both
 collision sets, both Stage I passes (and the automatic choice), random start
-attitudes and velocities, clouds from empty to a few thousand points with the
+attitudes and velocities, goals at rest and moving, clouds from empty to a few thousand points with the
 start anywhere in them.  One planner (no debug buffers, room for the
 every-point set) plans them all in a row, so nothing of one step may leak into
 the next.  Checked per step: the partition's decisions and the anchor cells
@@ -54,6 +54,12 @@ def random_case(i: int) -> I.Workload:
              collision_set=int(rng.integers(0, 2)), Q_track=float(rng.choice([0.0, 15.0])),
              seed=int(rng.integers(1, 1 << 40)), step_id=int(rng.integers(0, 1000)))
     n = int(rng.choice([0, 40, 900, 4000]))
+    if i % 3 == 1:  # a goal with a velocity and an attitude (drawn apart: the rest stays)
+        grng = np.random.default_rng(9500 + i)
+        p.update(v_goal=[float(v) for v in grng.uniform(-2.0, 2.0, 3)],
+                 q_goal=[float(v) for v in I.random_unit_quaternion(grng)])
+        if i % 9 == 4:
+            p.update(lanes_per_sample=1)
     if i % 6 == 0:  # the every-point set with one lane per sample, a dense cloud
         p.update(collision_set=1, lanes_per_sample=1)
         n = 4000
