@@ -42,7 +42,7 @@ struct CostSum {
 // kWarpLists: long candidate lists scanned by the whole warp (warp_split_min,
 // lists longer than a.list_thr), for the every-point collision set; the
 // short lists of P_f keep the per-lane scan, compiled without that path.
-template <bool kIdx, int kNT = NT, bool kWarpLists = false>
+template <bool kIdx, int kNT = NT, bool kWarpLists = false, bool kRestForm = kIdx && !kWarpLists>
 __device__ __forceinline__ void rollout_unit(const RolloutArgs& a, int e, int b, uint32_t ctr3) {
   constexpr int kNW = kNT / 32;
   constexpr int kSW = kNT > kMaxT ? kNT : kMaxT;
@@ -65,10 +65,10 @@ __device__ __forceinline__ void rollout_unit(const RolloutArgs& a, int e, int b,
   const bool active = k < a.K;
   const CostParams& cp = a.cost;
   const float dmax2 = cp.d_max * cp.d_max;
-  // the batched passes (arguments in shared memory) keep the general form: the
-  // test's registers made them spill; so does the every-point instance, which
-  // ran 17% slower with it
-  const bool at_rest = kIdx && !kWarpLists && goal_at_rest(cp);
+  // kRestForm: the at-rest goal term compiled in.  Left out of the batched
+  // passes built for 80 registers (the test's registers made them spill) and
+  // of the every-point instance (17% slower with it)
+  const bool at_rest = kRestForm && goal_at_rest(cp);
   const int dbg = (active && k < a.dbg_D) ? (e * a.dbg_D + k) : -1;
   const float4 sigma = make_float4(a.sigma[0], a.sigma[1], a.sigma[2], a.sigma[3]);
   const float4 umin = make_float4(a.umin[0], a.umin[1], a.umin[2], a.umin[3]);
@@ -992,7 +992,7 @@ __global__ void __launch_bounds__(kLanes == 4 ? ST : kNT, kMinCtas)
       const long long l = u - s_pre[pos];
       const int e = (int)(l / s_a.nb), b = (int)(l % s_a.nb);
       if constexpr (kLanes == 1)
-        rollout_unit<false, kNT>(s_a, e, b, s_a.ctr3 | (uint32_t)it);
+        rollout_unit<false, kNT, false, (kMinCtas == 5 && kNT == NT)>(s_a, e, b, s_a.ctr3 | (uint32_t)it);
       else
         rollout_split_unit(s_a, e, b, s_a.ctr3 | (uint32_t)it);
     }
