@@ -151,3 +151,23 @@ def test_non_finite_inputs_are_rejected_before_any_device_call():
     Q = aero.default_params_struct()
     Q.sigma[1] = inf
     assert call(state(), (5.0, 0.0, 1.0), Q) == -1
+
+
+def test_missing_library_fails_loudly():
+    """The binding has no CPU fallback: without the CUDA library the import
+    raises (run in a child process so this one keeps its loaded library)."""
+    import subprocess
+    import sys
+    code = ("import paper_2509_17340_gb300 as p\n"
+            "p._library = 'libaero_mppi_absent.so'\n"
+            "try:\n"
+            "    import paper_2509_17340_gb300.aero\n"
+            "except ImportError as e:\n"
+            "    print('ImportError', e)\n"
+            "else:\n"
+            "    print('imported')\n")
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    out = subprocess.run([sys.executable, "-c", code], cwd=root, capture_output=True, text=True,
+                         timeout=300)
+    assert out.returncode == 0, out.stderr
+    assert out.stdout.startswith("ImportError") and "no CPU fallback" in out.stdout
